@@ -1,0 +1,108 @@
+"""Test-side helpers: grid geometry transforms and small model builders.
+
+These transform *inputs* (rotations of a grid instance); none of the
+mean-field arithmetic lives here.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def rot90_cw_grid(U: np.ndarray, w: np.ndarray, H: int, W: int, conn: int):
+    """Rotate a grid instance clockwise: pixel (y, x) -> (x, H-1-y).
+
+    Valid for a symmetric mu only (edges that change orientation keep mu).
+    Returns (U', w', H', W') with H' = W, W' = H.
+
+    Edge bookkeeping (direction k of the old grid -> new grid):
+      right      (y,x)->(y,x+1)    becomes down       from (x, H-1-y)
+      down       (y,x)->(y+1,x)    becomes right      from (x, H-2-y)  (reversed)
+      down-right (y,x)->(y+1,x+1)  becomes down-left  from (x, H-1-y)
+      down-left  (y,x)->(y+1,x-1)  becomes down-right from (x-1, H-2-y) (reversed)
+    """
+    L = U.shape[1]
+    Hn, Wn = W, H
+    Un = np.zeros((Hn * Wn, L), U.dtype)
+    for y in range(H):
+        for x in range(W):
+            Un[x * Wn + (H - 1 - y)] = U[y * W + x]
+    nd = w.shape[0]
+    wn = np.zeros((nd, Hn, Wn), w.dtype)
+    for y in range(H):
+        for x in range(W):
+            if x + 1 < W:
+                wn[1, x, H - 1 - y] = w[0, y, x]
+            if y + 1 < H:
+                wn[0, x, H - 2 - y] = w[1, y, x]
+            if conn == 8:
+                if y + 1 < H and x + 1 < W:
+                    wn[3, x, H - 1 - y] = w[2, y, x]
+                if y + 1 < H and x - 1 >= 0:
+                    wn[2, x - 1, H - 2 - y] = w[3, y, x]
+    return Un, wn, Hn, Wn
+
+
+def rot90_cw_field(a: np.ndarray, H: int, W: int) -> np.ndarray:
+    """Per-pixel field [H*W][...] rotated like rot90_cw_grid."""
+    out = np.zeros_like(a)
+    for y in range(H):
+        for x in range(W):
+            out[x * H + (H - 1 - y)] = a[y * W + x]
+    return out
+
+
+def rot180_grid(U: np.ndarray, w: np.ndarray, H: int, W: int, conn: int):
+    """Rotate by 180 degrees: (y, x) -> (H-1-y, W-1-x).  Every edge reverses its
+    orientation, so the rotated model takes mu^T."""
+    L = U.shape[1]
+    Un = U.reshape(H, W, L)[::-1, ::-1].reshape(H * W, L).copy()
+    nd = w.shape[0]
+    wn = np.zeros_like(w)
+    for y in range(H):
+        for x in range(W):
+            ny, nx = H - 1 - y, W - 1 - x
+            if x + 1 < W:      # right edge (y,x)->(y,x+1) -> from (ny, nx-1) right
+                wn[0, ny, nx - 1] = w[0, y, x]
+            if y + 1 < H:      # down edge -> from (ny-1, nx) down
+                wn[1, ny - 1, nx] = w[1, y, x]
+            if conn == 8:
+                if y + 1 < H and x + 1 < W:   # down-right -> from (ny-1, nx-1) down-right
+                    wn[2, ny - 1, nx - 1] = w[2, y, x]
+                if y + 1 < H and x - 1 >= 0:  # down-left -> from (ny-1, nx+1) down-left
+                    wn[3, ny - 1, nx + 1] = w[3, y, x]
+    return Un, wn
+
+
+def king_graph_lambda_min(H: int, W: int) -> float:
+    """Smallest adjacency eigenvalue of the 8-connected H x W grid (king's
+    graph): A = (I + P_H) (x) (I + P_W) - I, P the path adjacency."""
+    a = [1 + 2 * math.cos(k * math.pi / (H + 1)) for k in range(1, H + 1)]
+    b = [1 + 2 * math.cos(k * math.pi / (W + 1)) for k in range(1, W + 1)]
+    return min(x * y for x in a for y in b) - 1.0
+
+
+def grid4_lambda_max(H: int, W: int) -> float:
+    return 2 * math.cos(math.pi / (H + 1)) + 2 * math.cos(math.pi / (W + 1))
+
+
+def read_golden(name: str) -> dict:
+    out = {}
+    with open(os.path.join(ROOT, "tests", "golden", name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
+def softmax_rows(a: np.ndarray) -> np.ndarray:
+    z = a - a.max(axis=1, keepdims=True)
+    e = np.exp(z)
+    return e / e.sum(axis=1, keepdims=True)

@@ -1,0 +1,343 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test ties one part of the oracle to something other than itself:
+brute-force enumeration, closed-form spectra, special cases with a textbook
+answer, symmetry, and the descent guarantee of Sec. 3.2.  A dropped term, a
+wrong sign or index, or a transposed mu in the oracle fails at least one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1511_06103_gb300 import synth
+from tests import helpers as H
+
+
+def _f64(d, k):
+    return np.asarray(d[k], np.float64)
+
+
+def small_grid(oracle, Hh, Ww, L, conn, seed, symmetric=False, scale=1.0):
+    d = synth.random_grid(Hh, Ww, L, conn, seed, symmetric=symmetric, coupling_scale=scale)
+    return oracle.Model.grid(_f64(d, "U"), _f64(d, "mu"), _f64(d, "w"), Hh, Ww, conn), d
+
+
+def random_q(n, L, seed):
+    return np.exp(synth.random_logq(n, L, seed).astype(np.float64))
+
+
+def renorm(q):
+    return q / q.sum(axis=1, keepdims=True)
+
+
+# ---------------------------------------------------------------- P1 ----
+
+@pytest.mark.parametrize("conn,Hh,Ww,L", [(4, 3, 3, 3), (8, 3, 3, 3), (8, 2, 4, 3), (4, 4, 4, 2)])
+def test_free_energy_equals_enumeration(oracle_mod, conn, Hh, Ww, L):
+    """F(q) closed form == sum_x Q(x)[E(x) + log Q(x)] (Eq. related:mf-objective)."""
+    m, _ = small_grid(oracle_mod, Hh, Ww, L, conn, seed=3, symmetric=False)
+    for s in range(3):
+        q = renorm(random_q(Hh * Ww, L, 100 + s))
+        F = m.free_energy(q)
+        Fb = m.brute_free_energy(q)
+        assert abs(F - Fb) <= 1e-12 * max(1.0, abs(Fb))
+
+
+def test_free_energy_dense_enumeration(oracle_mod):
+    rng = np.random.default_rng(7)
+    n, L = 6, 3
+    U = rng.normal(size=(n, L))
+    mu = rng.uniform(-1, 1, size=(L, L))          # asymmetric on purpose
+    K = rng.uniform(0, 1, size=(n, n))
+    K = (K + K.T) / 2
+    m = oracle_mod.Model.dense(U, mu, K)
+    q = renorm(random_q(n, L, 5))
+    assert abs(m.free_energy(q) - m.brute_free_energy(q)) <= 1e-12 * abs(m.brute_free_energy(q))
+    assert np.allclose(cond_from_grad(m, q), m.brute_cond_energy(q), rtol=0, atol=1e-12)
+
+
+def cond_from_grad(m, q):
+    """E_{Q(X\\X_i)}[E(x) | x_i = l] = g_il + E(q) - q_i . g_i: the terms of E(x)
+    that involve x_i give g_il, the rest contribute their expectation, which
+    is E(q) minus the expectation of the x_i terms."""
+    g = m.grad(q)
+    return g + (m.energy(q) - (q * g).sum(axis=1, keepdims=True))
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_gradient_is_conditional_expected_energy(oracle_mod, conn):
+    """grad E(q) is the conditional expected energy E_{Q(X\\X_i)}[E(x) | x_i = l]
+    of Eq. related:sweep-update (theta* of Eq. method:update_natural) up to the
+    per-variable constant that the softmax removes, by enumeration."""
+    m, _ = small_grid(oracle_mod, 3, 3, 3, conn, seed=11, symmetric=False)
+    q = renorm(random_q(9, 3, 12))
+    gb = m.brute_cond_energy(q)
+    assert np.max(np.abs(cond_from_grad(m, q) - gb)) <= 1e-12 * max(1.0, np.max(np.abs(gb)))
+
+
+def test_gibbs_inequality_and_equality(oracle_mod):
+    """F(q) + log Z = KL(Q||P) >= 0 (Eq. related:kl), with equality for a
+    decoupled model at its exact marginals."""
+    m, d = small_grid(oracle_mod, 3, 3, 2, 8, seed=21)
+    logZ, marg = m.brute_force()
+    for s in range(5):
+        q = renorm(random_q(9, 2, 200 + s))
+        assert m.free_energy(q) + logZ >= -1e-12
+    U = _f64(d, "U")
+    m0 = oracle_mod.Model.grid(U, _f64(d, "mu"), np.zeros_like(_f64(d, "w")), 3, 3, 8)
+    logZ0, marg0 = m0.brute_force()
+    assert np.allclose(marg0, H.softmax_rows(-U), atol=1e-13)
+    assert abs(m0.free_energy(marg0) + logZ0) <= 1e-12
+
+
+def test_free_energy_finite_difference(oracle_mod):
+    """dF/dq_il = grad E_il + log q_il + 1 on the open orthant."""
+    m, _ = small_grid(oracle_mod, 3, 4, 3, 8, seed=31, symmetric=False)
+    q = renorm(random_q(12, 3, 32)) + 0.05
+    g = m.grad(q) + np.log(q) + 1.0
+    h = 1e-6
+    for (i, l) in [(0, 0), (5, 2), (11, 1), (7, 0)]:
+        qp = q.copy(); qp[i, l] += h
+        qm = q.copy(); qm[i, l] -= h
+        fd = (m.free_energy(qp) - m.free_energy(qm)) / (2 * h)
+        assert abs(fd - g[i, l]) <= 1e-6 * max(1.0, abs(g[i, l]))
+
+
+def test_dense_and_edge_list_agree(oracle_mod):
+    """The dense-matrix model and the same model as an i<j edge list agree."""
+    rng = np.random.default_rng(41)
+    n, L = 12, 4
+    U = rng.normal(size=(n, L))
+    mu = rng.uniform(-1, 1, size=(L, L))
+    feats = np.concatenate([rng.uniform(0, 5, (n, 2)), rng.uniform(0, 255, (n, 3))], axis=1)
+    K = oracle_mod.dense_gauss_kernel(feats, 3.0, 13.0)
+    assert np.all(np.diag(K) == 0) and np.allclose(K, K.T)
+    i0, j0 = 2, 7
+    d = feats[i0] - feats[j0]
+    assert math.isclose(K[i0, j0], math.exp(-(d[0] ** 2 + d[1] ** 2) / 18.0 - (d[2:] ** 2).sum() / 338.0),
+                        rel_tol=1e-14)
+    ei, ej = np.triu_indices(n, 1)
+    md = oracle_mod.Model.dense(U, mu, K)
+    ms = oracle_mod.Model.sparse(U, mu, ei, ej, K[ei, ej])
+    q = renorm(random_q(n, L, 42))
+    assert np.allclose(md.grad(q), ms.grad(q), atol=1e-13)
+    assert abs(md.free_energy(q) - ms.free_energy(q)) <= 1e-12 * abs(ms.free_energy(q))
+    s = np.log(q)
+    assert np.allclose(md.prox_step(0.3, s), ms.prox_step(0.3, s), atol=1e-13)
+
+
+def test_grid_edge_geometry(oracle_mod):
+    Hh, Ww = 5, 7
+    w = np.arange(4 * Hh * Ww, dtype=np.float64).reshape(4, Hh, Ww) + 1
+    ei, ej, ew = oracle_mod.grid_edges(Hh, Ww, 8, w)
+    assert ei.size == Hh * (Ww - 1) + (Hh - 1) * Ww + 2 * (Hh - 1) * (Ww - 1)
+    ei4, _, _ = oracle_mod.grid_edges(Hh, Ww, 4, w[:2])
+    assert ei4.size == Hh * (Ww - 1) + (Hh - 1) * Ww
+    pairs = {(int(a), int(b)): float(c) for a, b, c in zip(ei, ej, ew)}
+    y, x = 2, 3
+    p = y * Ww + x
+    assert pairs[(p, p + 1)] == w[0, y, x]
+    assert pairs[(p, p + Ww)] == w[1, y, x]
+    assert pairs[(p, p + Ww + 1)] == w[2, y, x]
+    assert pairs[(p, p + Ww - 1)] == w[3, y, x]
+
+
+# ---------------------------------------------------------------- P3 ----
+
+def test_decoupled_one_full_step_gives_exact_marginals(oracle_mod):
+    """w = 0: one undamped step lands on softmax(-U), the exact marginals."""
+    d = synth.random_grid(3, 3, 3, 4, seed=51)
+    U = _f64(d, "U")
+    m = oracle_mod.Model.grid(U, _f64(d, "mu"), np.zeros((2, 3, 3)), 3, 3, 4)
+    s0 = np.log(renorm(random_q(9, 3, 52)))
+    s1 = m.prox_step(1.0, s0)
+    _, marg = m.brute_force()
+    assert np.allclose(np.exp(s1), marg, atol=1e-14)
+
+
+def test_decoupled_geometric_convergence(oracle_mod):
+    """w = 0, eta < 1: the natural parameters contract geometrically,
+    s^t = logsoftmax((1-eta)^t s^0 + (1 - (1-eta)^t) s*), s* = logsoftmax(-U)."""
+    d = synth.random_grid(4, 4, 5, 8, seed=53)
+    U = _f64(d, "U")
+    m = oracle_mod.Model.grid(U, _f64(d, "mu"), np.zeros((4, 4, 4)), 4, 4, 8)
+    eta = 0.3
+    s0 = np.log(renorm(random_q(16, 5, 54)))
+    z = -U - (-U).max(axis=1, keepdims=True)
+    sstar = z - np.log(np.exp(z).sum(axis=1, keepdims=True))
+    s = s0.copy()
+    for t in range(1, 8):
+        s = m.prox_step(eta, s)
+        r = (1 - eta) ** t
+        a = r * s0 + (1 - r) * sstar
+        expect = a - a.max(axis=1, keepdims=True)
+        expect = expect - np.log(np.exp(expect).sum(axis=1, keepdims=True))
+        assert np.allclose(s, expect, atol=1e-13)
+
+
+def test_gauge_invariance(oracle_mod):
+    """Adding c_i to U_i, or a constant c to mu, leaves the q trajectory
+    unchanged and shifts F by sum_i c_i, resp. c * sum of edge weights."""
+    Hh, Ww, L, conn = 5, 4, 3, 8
+    d = synth.random_grid(Hh, Ww, L, conn, seed=61, symmetric=False)
+    U, mu, w = _f64(d, "U"), _f64(d, "mu"), _f64(d, "w")
+    m = oracle_mod.Model.grid(U, mu, w, Hh, Ww, conn)
+    ci = np.random.default_rng(62).normal(size=(Hh * Ww, 1))
+    mU = oracle_mod.Model.grid(U + ci, mu, w, Hh, Ww, conn)
+    mM = oracle_mod.Model.grid(U, mu + 0.7, w, Hh, Ww, conn)
+    s0 = m.init_logq()
+    sa, Fa = m.parallel_prox(0.2, 6, s0)
+    sb, Fb = mU.parallel_prox(0.2, 6, s0)
+    sc, Fc = mM.parallel_prox(0.2, 6, s0)
+    assert np.allclose(sa, sb, atol=1e-12) and np.allclose(sa, sc, atol=1e-12)
+    assert np.allclose(Fb - Fa, ci.sum(), atol=1e-10)
+    assert np.allclose(Fc - Fa, 0.7 * w.sum(), atol=1e-10)
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_rotation_equivariance(oracle_mod, conn):
+    """Rotating a grid instance by 90 degrees (symmetric mu) or 180 degrees
+    (mu -> mu^T) rotates the whole trajectory: pins the grid geometry."""
+    Hh, Ww, L = 5, 7, 3
+    d = synth.random_grid(Hh, Ww, L, conn, seed=71, symmetric=True)
+    U, mu, w = _f64(d, "U"), _f64(d, "mu"), _f64(d, "w")
+    m = oracle_mod.Model.grid(U, mu, w, Hh, Ww, conn)
+    s, F = m.parallel_prox(0.15, 5)
+    Ur, wr, Hr, Wr = H.rot90_cw_grid(U, w, Hh, Ww, conn)
+    mr = oracle_mod.Model.grid(Ur, mu, wr, Hr, Wr, conn)
+    sr, Fr = mr.parallel_prox(0.15, 5)
+    assert np.allclose(sr, H.rot90_cw_field(s, Hh, Ww), atol=1e-12)
+    assert np.allclose(F, Fr, rtol=1e-12)
+    da = synth.random_grid(Hh, Ww, L, conn, seed=72, symmetric=False)
+    U, mu, w = _f64(da, "U"), _f64(da, "mu"), _f64(da, "w")
+    m = oracle_mod.Model.grid(U, mu, w, Hh, Ww, conn)
+    s, F = m.parallel_prox(0.15, 5)
+    U2, w2 = H.rot180_grid(U, w, Hh, Ww, conn)
+    m2 = oracle_mod.Model.grid(U2, mu.T.copy(), w2, Hh, Ww, conn)
+    s2, F2 = m2.parallel_prox(0.15, 5)
+    assert np.allclose(s2, s.reshape(Hh, Ww, L)[::-1, ::-1].reshape(-1, L), atol=1e-12)
+    assert np.allclose(F, F2, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- P2 ----
+
+@pytest.mark.parametrize("Hh,Ww,L,c", [(6, 5, 2, 0.8), (5, 4, 3, 0.7), (4, 6, 4, 1.3)])
+def test_step_constant_closed_form_grid4(oracle_mod, Hh, Ww, L, c):
+    """Potts on a uniform 4-connected grid: the tangent-space Hessian is
+    A (x) (-c I), so Lambda = c * (2cos(pi/(H+1)) + 2cos(pi/(W+1))); without the
+    projection the top eigenvalue is c (L-1) times the same grid value."""
+    U = np.zeros((Hh * Ww, L))
+    w = synth.constant_edge_weights(Hh, Ww, 4, 1.0)
+    m = oracle_mod.Model.grid(U, synth.potts(L, c), w, Hh, Ww, 4)
+    lam_grid = H.grid4_lambda_max(Hh, Ww)
+    ev = m.hessian_eigenvalues(projected=True)
+    assert math.isclose(ev[-1], c * lam_grid, rel_tol=1e-10)
+    ev_full = m.hessian_eigenvalues(projected=False)
+    assert math.isclose(ev_full[-1], c * (L - 1) * lam_grid, rel_tol=1e-10)
+
+
+def test_step_constant_closed_form_grid8(oracle_mod):
+    """8-connected (king's graph) Potts grid: Lambda = c |lambda_min(A_king)|."""
+    Hh, Ww, L, c = 5, 6, 3, 0.6
+    U = np.zeros((Hh * Ww, L))
+    w = synth.constant_edge_weights(Hh, Ww, 8, 1.0)
+    m = oracle_mod.Model.grid(U, synth.potts(L, c), w, Hh, Ww, 8)
+    ev = m.hessian_eigenvalues(projected=True)
+    assert math.isclose(ev[-1], -c * H.king_graph_lambda_min(Hh, Ww), rel_tol=1e-10)
+
+
+def test_step_constant_binary_denoising_golden(oracle_mod):
+    """The 64x64 binary denoising model: Lanczos on the tangent Hessian matches
+    the closed form stored in tests/golden (Sec. 3.2, Sec. 4.3)."""
+    g = H.read_golden("step_size_closed_form.txt")
+    d = synth.binary_denoising()
+    m = oracle_mod.Model.grid(_f64(d, "U"), _f64(d, "mu"), _f64(d, "w"), 64, 64, 4)
+    lo, hi, k = m.lanczos(260, synth.lanczos_start(64 * 64, 2))
+    assert math.isclose(hi, g["Lambda"], rel_tol=1e-8), (hi, g["Lambda"], k)
+    assert math.isclose(oracle_mod.step_size(hi), g["eta"], rel_tol=1e-8)
+    assert math.isclose(-lo, g["Lambda"], rel_tol=1e-8)   # bipartite: symmetric spectrum
+
+
+def test_lanczos_matches_dense_eigensolve(oracle_mod):
+    m, _ = small_grid(oracle_mod, 6, 5, 4, 8, seed=81, symmetric=False)
+    ev = m.hessian_eigenvalues(projected=True)
+    lo, hi, _ = m.lanczos(120, synth.lanczos_start(30, 4, seed=3))
+    # the tangent space has dimension n (L-1); the remaining n eigenvalues are 0
+    assert math.isclose(hi, ev[-1], rel_tol=1e-9) and math.isclose(lo, ev[0], rel_tol=1e-9)
+
+
+def test_step_size_rule(oracle_mod):
+    assert oracle_mod.step_size(-2.0) == 1.0          # NSD potential matrix: full step
+    assert oracle_mod.step_size(0.0) == 1.0
+    assert math.isclose(oracle_mod.step_size(3.0), 0.25)
+
+
+# ---------------------------------------------------------------- P4 ----
+
+def test_parallel_fixed_point_is_sweep_stationary(oracle_mod):
+    """A converged parallel-prox point satisfies q = softmax(-grad E(q)): one
+    SWEEP pass leaves it unchanged."""
+    d = synth.binary_denoising(H=20, W=20, coupling=0.8, seed=5)
+    m = oracle_mod.Model.grid(_f64(d, "U"), _f64(d, "mu"), _f64(d, "w"), 20, 20, 4)
+    lam = 0.8 * H.grid4_lambda_max(20, 20)
+    s, F = m.parallel_prox(1 / (1 + lam), 1500)
+    s2 = m.sweep(1, s)
+    assert np.max(np.abs(np.exp(s2) - np.exp(s))) <= 1e-10
+
+
+def test_weak_coupling_sweep_and_parallel_agree(oracle_mod):
+    """Weak coupling (tangent Hessian norm < 1) makes F strictly convex on the
+    simplex product: SWEEP and parallel prox reach the same unique minimiser."""
+    Hh = Ww = 24
+    d = synth.binary_denoising(H=Hh, W=Ww, coupling=0.2, seed=6)
+    m = oracle_mod.Model.grid(_f64(d, "U"), _f64(d, "mu"), _f64(d, "w"), Hh, Ww, 4)
+    lam = 0.2 * H.grid4_lambda_max(Hh, Ww)
+    assert lam < 1
+    sp, _ = m.parallel_prox(1 / (1 + lam), 400)
+    ss = m.sweep(200)
+    assert np.max(np.abs(np.exp(sp) - np.exp(ss))) <= 1e-10
+
+
+# ---------------------------------------------------------------- P5 ----
+
+def test_monotone_free_energy_binary_denoising(oracle_mod):
+    """d >= Lambda: F never increases (Sec. 3.2).  The closed-form constant
+    is the same for the attractive model and its repulsive mirror
+    (mu -> -mu); undamped updates (eta = 1) on the repulsive one oscillate and
+    F goes up, the failure of FULL-PARALLEL on repulsive grids (Sec. 4.3)."""
+    g = H.read_golden("step_size_closed_form.txt")
+    d = synth.binary_denoising()
+    for sign in (1.0, -1.0):
+        m = oracle_mod.Model.grid(_f64(d, "U"), sign * _f64(d, "mu"), _f64(d, "w"), 64, 64, 4)
+        _, F = m.parallel_prox(g["eta"], 50)
+        assert np.all(np.diff(F) <= 1e-12 * np.abs(F[1:]))
+    _, F1 = m.parallel_prox(1.0, 50)
+    assert np.any(np.diff(F1) > 1e-3 * np.abs(F1[1:]))
+
+
+def test_monotone_free_energy_repulsive_grid(oracle_mod):
+    m, d = small_grid(oracle_mod, 7, 6, 5, 8, seed=91, symmetric=False, scale=2.0)
+    lam = m.hessian_eigenvalues(projected=True)[-1]
+    _, F = m.parallel_prox(oracle_mod.step_size(lam), 60)
+    assert np.all(np.diff(F) <= 1e-12 * np.abs(F[1:]))
+
+
+def test_monotone_free_energy_dense(oracle_mod):
+    d = synth.dense_gaussian(side=6, L=4, seed=92)
+    K = oracle_mod.dense_gauss_kernel(_f64(d, "feats"), *d["theta"])
+    m = oracle_mod.Model.dense(_f64(d, "U"), 3.0 * _f64(d, "mu"), K)
+    lam = m.hessian_eigenvalues(projected=True)[-1]
+    assert lam > 0
+    _, F = m.parallel_prox(oracle_mod.step_size(lam), 60)
+    assert np.all(np.diff(F) <= 1e-12 * np.abs(F[1:]))
+
+
+# ---------------------------------------------------------------- P6 ----
+
+def test_normalisation(oracle_mod):
+    m, _ = small_grid(oracle_mod, 9, 8, 6, 8, seed=95, symmetric=False)
+    s, _ = m.parallel_prox(0.1, 10)
+    q = np.exp(s)
+    assert np.all(q >= 0)
+    assert np.max(np.abs(q.sum(axis=1) - 1)) <= 1e-12
