@@ -1,0 +1,161 @@
+/*
+ * proxmf.h -- C ABI of the GB300 parallel proximal mean-field library.
+ *
+ * The library minimises the variational free energy
+ *     F(q) = E_Q[E(x)] + sum_i sum_l q_il log q_il          (Sec. 2.2.1, Eq. related:mf-objective)
+ * of a pairwise discrete random field (Sec. 2.1, Eq. related:pairwise-mrf)
+ * over factorised distributions Q(x) = prod_i q_{i,x_i} (Eq. related:q-factorized),
+ * with the fully parallel KL-proximal update of Sec. 3.1-3.2
+ * (Eq. method:update_mean / method:update_natural, Eq. fixedStepSize):
+ *     theta^{t+1} = eta grad E(q^t) + (1 - eta) theta^t,   q_il ∝ exp(-theta_il),
+ *     eta = 1/(1+d), d = max(Lambda, 0),
+ * where Lambda bounds the curvature of E on the simplex (Sec. 3.2).
+ *
+ * Energy convention (costs; the paper's potentials are phi = -cost):
+ *     E(x) = sum_i U[i, x_i] + sum_{edges i->j} w_ij mu[x_i, x_j].
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a crf_status; nothing aborts or throws across the ABI.
+ *   - A handle owns all of its device memory; inputs are copied when set; the
+ *     caller owns every output buffer.
+ *   - Work is ordered on the handle's stream (crf_desc.stream).  Calls that
+ *     return host values synchronise that stream before returning.
+ *   - Pointers flagged is_device = 1 are device pointers of the current CUDA
+ *     device; is_device = 0 means host memory (pinned or pageable).
+ *   - External layout of per-variable arrays is [batch][N][L] row-major, N =
+ *     height*width, variable p = y*width + x.  The internal device layout is
+ *     private (label-planar) and converted when data is set or read.
+ *   - A handle is used by one host thread at a time.
+ *   - A CUDA error is reported as CRF_E_CUDA and makes the handle unusable
+ *     (later calls return CRF_E_STATE).
+ */
+#ifndef PROXMF_H
+#define PROXMF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct crf_s *crf_t;
+
+typedef enum {
+    CRF_OK = 0,
+    CRF_E_INVALID = -1,     /* bad argument, size or call order              */
+    CRF_E_OOM = -2,         /* device allocation failed                      */
+    CRF_E_CUDA = -3,        /* a CUDA call failed; the handle is now broken  */
+    CRF_E_STATE = -4,       /* handle broken by an earlier CUDA error        */
+    CRF_E_TIMEOUT = -5,     /* a bounded wait ran out                        */
+    CRF_E_NUMERIC = -6,     /* a non-finite free energy was produced         */
+    CRF_E_UNSUPPORTED = -7  /* valid request outside what this build covers  */
+} crf_status;
+
+typedef enum {
+    CRF_GRID4 = 0,          /* 4-connected H x W grid                         */
+    CRF_GRID8 = 1,          /* 8-connected H x W grid                         */
+    CRF_DENSE_GAUSS = 2     /* fully connected, Gaussian kernel over features */
+} crf_topology;
+
+typedef enum {
+    CRF_FP32 = 0,           /* FP32 messages, FP32 state                     */
+    CRF_BF16 = 1            /* BF16 tensor-core messages, FP32 state         */
+} crf_precision;
+
+typedef struct {
+    int32_t topology;       /* crf_topology                                   */
+    int32_t n_labels;       /* L: 1..32                                       */
+    int32_t batch;          /* independent instances with the same shape, >= 1 */
+    int32_t precision;      /* crf_precision                                  */
+    int64_t height;         /* grid rows; dense: N = height*width variables   */
+    int64_t width;          /* grid columns                                   */
+    void *stream;           /* cudaStream_t; NULL = the legacy default stream */
+} crf_desc;
+
+/* crf_create -- allocate a handle and its device storage for desc.
+ * Defines the model of Sec. 2.1 (Eq. related:pairwise-mrf) on the given
+ * topology.  Fails with CRF_E_INVALID for sizes out of range, CRF_E_OOM if
+ * the device storage cannot be allocated.  *out is NULL on failure. */
+crf_status crf_create(const crf_desc *desc, crf_t *out);
+
+/* crf_destroy -- synchronise the handle's stream and free everything.
+ * NULL is accepted. */
+crf_status crf_destroy(crf_t h);
+
+/* crf_set_unary -- unary energies U = -phi_i of Eq. related:pairwise-mrf,
+ * [batch][N][L] float32.  Copied into the handle; the mean-field state is
+ * reset to q^0 = softmax(-U) (the unary-only marginals). */
+crf_status crf_set_unary(crf_t h, const float *U, int is_device);
+
+/* crf_set_pairwise -- the pairwise term phi_ij = -w_ij mu[x_i, x_j].
+ *   mu   [L][L] float32, shared by all instances; mu[l*L+m] is the cost of
+ *        (x_i = l, x_j = m) on an edge oriented i -> j.
+ *   grid: w_or_feats = w [batch][n_dirs][H][W] float32 (n_dirs = 2 for GRID4:
+ *        right, down; 4 for GRID8: right, down, down-right, down-left); the
+ *        entry at (y, x) weights the edge leaving (y, x) in that direction;
+ *        entries whose edge would leave the image are ignored.  theta unused.
+ *   dense: w_or_feats = features [batch][N][5] (x, y, r, g, b) and theta[2] =
+ *        {theta_pos, theta_rgb}; w_ij = exp(-|dp|^2/(2 theta_pos^2)
+ *        - |dc|^2/(2 theta_rgb^2)) for i != j; mu must be symmetric.
+ * Invalidates the cached step-size constant (recomputed on demand). */
+crf_status crf_set_pairwise(crf_t h, const float *mu, const float *w_or_feats,
+                            const float *theta, int is_device);
+
+/* crf_set_state -- import a mean-field state as log q, [batch][N][L] float32
+ * (each row should be a normalised log-distribution; it is used as given).
+ * Checkpoint / resume, and identical starting points for parity checks. */
+crf_status crf_set_state(crf_t h, const float *logq, int is_device);
+
+typedef struct {
+    double eta;             /* > 0: fixed step eta (1 = FULL-PARALLEL);        */
+                            /* <= 0: eta = 1/(1+max(Lambda,0)) (Sec. 3.2)       */
+    int32_t max_iters;      /* iterations to run (>= 0)                         */
+    int32_t reset;          /* 1: restart from q^0 = softmax(-U) first          */
+    double rel_tol;         /* > 0: instance b stops after the step at which    */
+                            /* |F^t - F^{t-1}| <= rel_tol |F^t| (stopping rule  */
+                            /* on the objective, Sec. 3.1); 0: fixed count      */
+    int32_t refine_fp32;    /* BF16 form: extra FP32 iterations at the end      */
+    int32_t reserved;
+} mf_params;
+
+/* mf_iterate -- run the parallel proximal iteration of Eq. method:update_natural.
+ * Each step computes grad E(q^t) (expected pairwise energy plus unaries),
+ * takes the log-domain proximal step, renormalises every variable, and
+ * records F(q^t).  iters_done (host, [batch], may be NULL) receives the
+ * number of steps each instance actually took.  Requires unary and pairwise
+ * terms to be set. */
+crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done);
+
+/* mf_free_energy -- F(q) of the current state per instance (Eq.
+ * related:mf-objective), FP64, host array [batch]. */
+crf_status mf_free_energy(crf_t h, double *F);
+
+/* mf_free_energy_trace -- F(q^t), t = 0 .. n-1, recorded by the last
+ * mf_iterate call, host array [batch][n]; n <= that call's max_iters.
+ * Entries after an instance stopped early are left as recorded (stale). */
+crf_status mf_free_energy_trace(crf_t h, double *F, int32_t n);
+
+/* mf_marginals -- q (Eq. related:definition_q), [batch][N][L] float32. */
+crf_status mf_marginals(crf_t h, float *q, int is_device);
+
+/* mf_log_marginals -- log q, [batch][N][L] float32 (the log-domain state). */
+crf_status mf_log_marginals(crf_t h, float *logq, int is_device);
+
+/* mf_lipschitz -- the step-size constant Lambda (largest eigenvalue of the
+ * constant Hessian of E restricted to the tangent space of the simplex
+ * product, Sec. 3.2) and eta = 1/(1+max(Lambda,0)), one per instance: host
+ * arrays [batch] (either may be NULL).  Computed on the device by a Lanczos
+ * iteration on first use after crf_set_pairwise; synchronises the stream. */
+crf_status mf_lipschitz(crf_t h, double *Lambda, double *eta);
+
+/* crf_error_string -- static description of a status code. */
+const char *crf_error_string(crf_status s);
+
+/* crf_version -- library version string. */
+const char *crf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PROXMF_H */

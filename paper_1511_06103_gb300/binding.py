@@ -1,0 +1,271 @@
+"""Thin ctypes binding of the C ABI in include/proxmf.h.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  If the compiled library is missing, loading fails loudly -- there
+is no CPU fallback.
+
+Two levels:
+  - module functions with the C names (crf_create, crf_set_unary, ...),
+    taking raw pointers / ctypes objects and raising ProxMFError on a
+    non-zero status;
+  - ``CRF``, a small convenience wrapper taking torch tensors (device or
+    host) or numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libproxmf.so")
+
+CRF_GRID4, CRF_GRID8, CRF_DENSE_GAUSS = 0, 1, 2
+CRF_FP32, CRF_BF16 = 0, 1
+
+STATUS = {
+    0: "CRF_OK", -1: "CRF_E_INVALID", -2: "CRF_E_OOM", -3: "CRF_E_CUDA", -4: "CRF_E_STATE",
+    -5: "CRF_E_TIMEOUT", -6: "CRF_E_NUMERIC", -7: "CRF_E_UNSUPPORTED",
+}
+
+
+class ProxMFError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({error_string(status)})")
+
+
+class crf_desc(C.Structure):
+    _fields_ = [("topology", C.c_int32), ("n_labels", C.c_int32), ("batch", C.c_int32),
+                ("precision", C.c_int32), ("height", C.c_int64), ("width", C.c_int64),
+                ("stream", C.c_void_p)]
+
+
+class mf_params(C.Structure):
+    _fields_ = [("eta", C.c_double), ("max_iters", C.c_int32), ("reset", C.c_int32),
+                ("rel_tol", C.c_double), ("refine_fp32", C.c_int32), ("reserved", C.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = C.c_void_p
+_i = C.c_int
+_SIGS = {
+    "crf_create": [C.POINTER(crf_desc), C.POINTER(_vp)],
+    "crf_destroy": [_vp],
+    "crf_set_unary": [_vp, _vp, _i],
+    "crf_set_pairwise": [_vp, _vp, _vp, _vp, _i],
+    "crf_set_state": [_vp, _vp, _i],
+    "mf_iterate": [_vp, C.POINTER(mf_params), _vp],
+    "mf_free_energy": [_vp, _vp],
+    "mf_free_energy_trace": [_vp, _vp, C.c_int32],
+    "mf_marginals": [_vp, _vp, _i],
+    "mf_log_marginals": [_vp, _vp, _i],
+    "mf_lipschitz": [_vp, _vp, _vp],
+}
+
+
+def lib():
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run paper_1511_06103_gb300.build.build())")
+        h = C.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(h, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        h.crf_error_string.argtypes = [C.c_int]
+        h.crf_error_string.restype = C.c_char_p
+        h.crf_version.argtypes = []
+        h.crf_version.restype = C.c_char_p
+        _lib = h
+        return h
+
+
+def error_string(status: int) -> str:
+    try:
+        return lib().crf_error_string(int(status)).decode()
+    except Exception:  # noqa: BLE001 - message only
+        return "?"
+
+
+def _call(name: str, *args) -> None:
+    rc = getattr(lib(), name)(*args)
+    if rc != 0:
+        raise ProxMFError(rc, name)
+
+
+# -- C-named entry points ------------------------------------------------------
+
+def crf_create(desc: crf_desc) -> int:
+    h = _vp()
+    _call("crf_create", C.byref(desc), C.byref(h))
+    return h.value
+
+
+def crf_destroy(h: int) -> None:
+    _call("crf_destroy", h)
+
+
+def crf_set_unary(h, U_ptr, is_device: int) -> None:
+    _call("crf_set_unary", h, U_ptr, is_device)
+
+
+def crf_set_pairwise(h, mu_ptr, w_ptr, theta_ptr, is_device: int) -> None:
+    _call("crf_set_pairwise", h, mu_ptr, w_ptr, theta_ptr, is_device)
+
+
+def crf_set_state(h, logq_ptr, is_device: int) -> None:
+    _call("crf_set_state", h, logq_ptr, is_device)
+
+
+def mf_iterate(h, params: mf_params, iters_done_ptr=None) -> None:
+    _call("mf_iterate", h, C.byref(params), iters_done_ptr)
+
+
+def mf_free_energy(h, F_ptr) -> None:
+    _call("mf_free_energy", h, F_ptr)
+
+
+def mf_free_energy_trace(h, F_ptr, n: int) -> None:
+    _call("mf_free_energy_trace", h, F_ptr, n)
+
+
+def mf_marginals(h, q_ptr, is_device: int) -> None:
+    _call("mf_marginals", h, q_ptr, is_device)
+
+
+def mf_log_marginals(h, logq_ptr, is_device: int) -> None:
+    _call("mf_log_marginals", h, logq_ptr, is_device)
+
+
+def mf_lipschitz(h, Lambda_ptr, eta_ptr) -> None:
+    _call("mf_lipschitz", h, Lambda_ptr, eta_ptr)
+
+
+def crf_version() -> str:
+    return lib().crf_version().decode()
+
+
+# -- convenience wrapper -------------------------------------------------------
+
+def _as_buffer(a):
+    """(pointer, is_device, keepalive) for a float32 torch tensor or numpy array."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float32 or not a.is_contiguous():
+                raise ValueError("expected a contiguous float32 tensor")
+            return a.data_ptr(), int(a.is_cuda), a
+    except ImportError:  # pragma: no cover
+        pass
+    arr = np.ascontiguousarray(a, dtype=np.float32)
+    return arr.ctypes.data, 0, arr
+
+
+def current_stream_handle() -> int | None:
+    import torch
+    if torch.cuda.is_available() and torch.cuda.is_initialized():
+        return torch.cuda.current_stream().cuda_stream
+    return None
+
+
+class CRF:
+    """One handle of the library: a batch of same-shaped grid CRFs."""
+
+    def __init__(self, topology: int, n_labels: int, height: int, width: int, batch: int = 1,
+                 precision: int = CRF_FP32, stream: int | None = None):
+        if stream is None:
+            stream = current_stream_handle()
+        self.desc = crf_desc(topology, n_labels, batch, precision, height, width, stream)
+        self.L, self.H, self.W, self.B = n_labels, height, width, batch
+        self.N = height * width
+        self.h = crf_create(self.desc)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            crf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_unary(self, U) -> None:
+        p, dev, keep = _as_buffer(U)
+        crf_set_unary(self.h, p, dev)
+
+    def set_pairwise(self, mu, w, theta=None) -> None:
+        pm, dm, km = _as_buffer(mu)
+        pw, dw, kw = _as_buffer(w)
+        if dm != dw:
+            # mu and w travel with one is_device flag; bring mu to w's side
+            import torch
+            km = torch.as_tensor(np.asarray(km.cpu() if hasattr(km, "cpu") else km, np.float32))
+            if dw:
+                km = km.cuda()
+            pm, dm, km = _as_buffer(km)
+        pt = None
+        if theta is not None:
+            th = np.ascontiguousarray(theta, np.float32)
+            pt = th.ctypes.data
+        crf_set_pairwise(self.h, pm, pw, pt, dw)
+
+    def set_state(self, logq) -> None:
+        p, dev, keep = _as_buffer(logq)
+        crf_set_state(self.h, p, dev)
+
+    def iterate(self, max_iters: int, eta: float = 0.0, reset: bool = False, rel_tol: float = 0.0,
+                refine_fp32: int = 0, want_iters: bool = False):
+        prm = mf_params(float(eta), int(max_iters), int(bool(reset)), float(rel_tol), int(refine_fp32), 0)
+        if want_iters:
+            out = np.zeros(self.B, np.int32)
+            mf_iterate(self.h, prm, out.ctypes.data)
+            return out
+        mf_iterate(self.h, prm, None)
+        return None
+
+    def free_energy(self) -> np.ndarray:
+        F = np.zeros(self.B, np.float64)
+        mf_free_energy(self.h, F.ctypes.data)
+        return F
+
+    def free_energy_trace(self, n: int) -> np.ndarray:
+        F = np.zeros((self.B, n), np.float64)
+        mf_free_energy_trace(self.h, F.ctypes.data, n)
+        return F
+
+    def _export(self, fn, out):
+        if out is None:
+            out = np.zeros((self.B, self.N, self.L), np.float32)
+        p, dev, keep = _as_buffer(out)
+        fn(self.h, p, dev)
+        return out
+
+    def marginals(self, out=None):
+        return self._export(mf_marginals, out)
+
+    def log_marginals(self, out=None):
+        return self._export(mf_log_marginals, out)
+
+    def lipschitz(self):
+        lam = np.zeros(self.B, np.float64)
+        eta = np.zeros(self.B, np.float64)
+        mf_lipschitz(self.h, lam.ctypes.data, eta.ctypes.data)
+        return lam, eta

@@ -1,0 +1,453 @@
+// api.cu -- the C ABI (include/proxmf.h): handle, device storage, call order,
+// status mapping.  Host code here only sequences device work; every step of
+// the method runs in the kernels of grid_step*.cu, layout.cu and lanczos.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/proxmf.h"
+#include "internal.h"
+
+using namespace proxmf;
+
+struct crf_s {
+    crf_desc d{};
+    int B = 0, L = 0, H = 0, W = 0, P = 0, nd = 0, conn = 4;
+    int nblk = 0;
+    cudaStream_t st = nullptr;
+    float *U = nullptr;          // planar unaries
+    float *s[2] = {nullptr, nullptr};  // planar log q, ping-pong
+    float *w = nullptr;          // planar weights
+    float *eta_fixed = nullptr;  // [B]
+    float *eta_auto = nullptr;   // [B]
+    double *Lambda = nullptr;    // [B]
+    double *partial = nullptr;   // [B][nblk] free-energy partials
+    unsigned *counter = nullptr; // [B]
+    double *ftrace = nullptr;    // [B][trace_cap]
+    double *fcur = nullptr;      // [B]
+    int *done = nullptr;         // [B]
+    int *status = nullptr;       // device error word
+    float *staging = nullptr;    // [B][N][L] row-layout staging
+    int trace_cap = 0;
+    int last_iters = 0;
+    int cur = 0;
+    std::vector<float> mu;
+    bool mu_sym = true;
+    bool has_unary = false, has_pairwise = false, lambda_valid = false, broken = false;
+    int lanczos_steps = 0;
+};
+
+namespace {
+
+crf_status fail_cuda(crf_t h, cudaError_t e) {
+    if (e == cudaSuccess) return CRF_OK;
+    if (h) h->broken = true;
+    (void)cudaGetLastError();
+    return CRF_E_CUDA;
+}
+
+#define CK(h, x)                                 \
+    do {                                         \
+        cudaError_t e_ = (x);                    \
+        if (e_ != cudaSuccess) return fail_cuda(h, e_); \
+    } while (0)
+
+crf_status check_handle(crf_t h) {
+    if (!h) return CRF_E_INVALID;
+    if (h->broken) return CRF_E_STATE;
+    return CRF_OK;
+}
+
+size_t n_rows(const crf_t h) { return (size_t)h->B * h->H * h->W * h->L; }
+size_t n_planar(const crf_t h) { return (size_t)h->B * h->L * h->H * h->P; }
+
+void free_all(crf_t h) {
+    float *fs[] = {h->U, h->s[0], h->s[1], h->w, h->eta_fixed, h->eta_auto, h->staging};
+    for (float *p : fs)
+        if (p) cudaFree(p);
+    double *ds[] = {h->Lambda, h->partial, h->ftrace, h->fcur};
+    for (double *p : ds)
+        if (p) cudaFree(p);
+    if (h->counter) cudaFree(h->counter);
+    if (h->done) cudaFree(h->done);
+    if (h->status) cudaFree(h->status);
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n) {
+    return cudaMalloc((void **)p, (n ? n : 1) * sizeof(T));
+}
+
+crf_status ensure_trace(crf_t h, int iters) {
+    if (iters <= h->trace_cap) return CRF_OK;
+    int cap = h->trace_cap > 0 ? h->trace_cap : 64;
+    while (cap < iters) cap *= 2;
+    double *nt = nullptr;
+    if (dalloc(&nt, (size_t)h->B * cap) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return CRF_E_OOM;
+    }
+    CK(h, cudaMemsetAsync(nt, 0, (size_t)h->B * cap * sizeof(double), h->st));
+    if (h->ftrace) {
+        CK(h, cudaStreamSynchronize(h->st));
+        cudaFree(h->ftrace);
+    }
+    h->ftrace = nt;
+    h->trace_cap = cap;
+    return CRF_OK;
+}
+
+GridStepLaunch step_args(crf_t h, const float *eta, int t, int update, double rel_tol) {
+    GridStepLaunch a{};
+    a.s_in = h->s[h->cur];
+    a.s_out = h->s[h->cur ^ 1];
+    a.U = h->U;
+    a.w = h->w;
+    a.eta = eta;
+    a.partial = h->partial;
+    a.counter = h->counter;
+    a.f_trace = h->ftrace;
+    a.f_cur = h->fcur;
+    a.done = update ? h->done : nullptr;
+    a.status = h->status;
+    a.B = h->B;
+    a.L = h->L;
+    a.H = h->H;
+    a.W = h->W;
+    a.P = h->P;
+    a.conn = h->conn;
+    a.t = t;
+    a.trace_cap = h->trace_cap;
+    a.update = update;
+    a.rel_tol = rel_tol;
+    a.mu_sym = h->mu_sym;
+    a.mu_host = h->mu.data();
+    return a;
+}
+
+crf_status ensure_lambda(crf_t h) {
+    if (h->lambda_valid) return CRF_OK;
+    LipschitzJob job{};
+    job.w = h->w;
+    job.mu_host = h->mu.data();
+    job.mu_sym = h->mu_sym;
+    job.B = h->B;
+    job.L = h->L;
+    job.H = h->H;
+    job.W = h->W;
+    job.P = h->P;
+    job.conn = h->conn;
+    job.Lambda = h->Lambda;
+    job.eta = h->eta_auto;
+    job.max_steps = 4000;
+    job.tol = 1e-12;
+    int steps = 0;
+    const int rc = estimate_lipschitz_grid(job, h->st, &steps);
+    if (rc != 0) return fail_cuda(h, cudaErrorUnknown);
+    h->lanczos_steps = steps;
+    h->lambda_valid = true;
+    return CRF_OK;
+}
+
+crf_status read_status(crf_t h) {
+    int s = 0;
+    CK(h, cudaMemcpyAsync(&s, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    if (s != 0) {
+        CK(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
+        return (crf_status)s;
+    }
+    return CRF_OK;
+}
+
+}  // namespace
+
+namespace proxmf {
+
+cudaError_t launch_grid_step(const GridStepLaunch &a, cudaStream_t st) {
+    if (a.L <= 2) return launch_grid_step_l2(a, st);
+    if (a.L <= 4) return launch_grid_step_l4(a, st);
+    if (a.L <= 8) return launch_grid_step_l8(a, st);
+    if (a.L <= 16) return launch_grid_step_l16(a, st);
+    if (a.L <= 21) return launch_grid_step_l21(a, st);
+    return launch_grid_step_l32(a, st);
+}
+
+}  // namespace proxmf
+
+extern "C" {
+
+const char *crf_version(void) { return "proxmf 0.1 (sm_103a)"; }
+
+const char *crf_error_string(crf_status s) {
+    switch (s) {
+    case CRF_OK: return "ok";
+    case CRF_E_INVALID: return "invalid argument, size or call order";
+    case CRF_E_OOM: return "device allocation failed";
+    case CRF_E_CUDA: return "CUDA error (handle is now unusable)";
+    case CRF_E_STATE: return "handle unusable after an earlier CUDA error";
+    case CRF_E_TIMEOUT: return "bounded wait ran out";
+    case CRF_E_NUMERIC: return "non-finite free energy";
+    case CRF_E_UNSUPPORTED: return "request outside what this build supports";
+    }
+    return "unknown status";
+}
+
+crf_status crf_create(const crf_desc *desc, crf_t *out) {
+    if (!out) return CRF_E_INVALID;
+    *out = nullptr;
+    if (!desc) return CRF_E_INVALID;
+    const crf_desc &d = *desc;
+    if (d.n_labels < 1 || d.n_labels > kMaxLabels || d.batch < 1 || d.height < 1 || d.width < 1)
+        return CRF_E_INVALID;
+    if (d.precision != CRF_FP32 && d.precision != CRF_BF16) return CRF_E_INVALID;
+    if (d.topology == CRF_DENSE_GAUSS) return CRF_E_UNSUPPORTED;
+    if (d.topology != CRF_GRID4 && d.topology != CRF_GRID8) return CRF_E_INVALID;
+    if (d.precision == CRF_BF16) return CRF_E_UNSUPPORTED;
+    if (d.height > (1 << 20) || d.width > (1 << 20) || d.batch > 65535) return CRF_E_INVALID;
+    const long long pitch = (d.width + 31) / 32 * 32;
+    if ((long long)d.batch * d.n_labels * d.height * pitch > (1ll << 40)) return CRF_E_INVALID;
+
+    crf_t h = new (std::nothrow) crf_s();
+    if (!h) return CRF_E_OOM;
+    h->d = d;
+    h->B = d.batch;
+    h->L = d.n_labels;
+    h->H = (int)d.height;
+    h->W = (int)d.width;
+    h->P = (int)pitch;
+    h->conn = d.topology == CRF_GRID8 ? 8 : 4;
+    h->nd = h->conn == 8 ? 4 : 2;
+    h->st = (cudaStream_t)d.stream;
+    int nbx, nby;
+    grid_tiles(h->H, h->W, &nbx, &nby);
+    h->nblk = nbx * nby;
+    h->mu.assign((size_t)h->L * h->L, 0.f);
+
+    bool ok = true;
+    ok = ok && dalloc(&h->U, n_planar(h)) == cudaSuccess;
+    ok = ok && dalloc(&h->s[0], n_planar(h)) == cudaSuccess;
+    ok = ok && dalloc(&h->s[1], n_planar(h)) == cudaSuccess;
+    ok = ok && dalloc(&h->w, (size_t)h->B * h->nd * h->H * h->P) == cudaSuccess;
+    ok = ok && dalloc(&h->eta_fixed, h->B) == cudaSuccess;
+    ok = ok && dalloc(&h->eta_auto, h->B) == cudaSuccess;
+    ok = ok && dalloc(&h->Lambda, h->B) == cudaSuccess;
+    ok = ok && dalloc(&h->partial, (size_t)h->B * h->nblk) == cudaSuccess;
+    ok = ok && dalloc(&h->counter, h->B) == cudaSuccess;
+    ok = ok && dalloc(&h->fcur, h->B) == cudaSuccess;
+    ok = ok && dalloc(&h->done, h->B) == cudaSuccess;
+    ok = ok && dalloc(&h->status, 1) == cudaSuccess;
+    ok = ok && dalloc(&h->staging, n_rows(h)) == cudaSuccess;
+    if (!ok) {
+        (void)cudaGetLastError();
+        free_all(h);
+        delete h;
+        return CRF_E_OOM;
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->U, 0, n_planar(h) * sizeof(float), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->s[0], 0, n_planar(h) * sizeof(float), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->s[1], 0, n_planar(h) * sizeof(float), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->w, 0, (size_t)h->B * h->nd * h->H * h->P * sizeof(float), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->counter, 0, h->B * sizeof(unsigned), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->done, 0, h->B * sizeof(int), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->fcur, 0, h->B * sizeof(double), h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        free_all(h);
+        delete h;
+        return CRF_E_CUDA;
+    }
+    crf_status rc = ensure_trace(h, 64);
+    if (rc != CRF_OK) {
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return CRF_OK;
+}
+
+crf_status crf_destroy(crf_t h) {
+    if (!h) return CRF_OK;
+    cudaStreamSynchronize(h->st);
+    free_all(h);
+    delete h;
+    return CRF_OK;
+}
+
+crf_status crf_set_unary(crf_t h, const float *U, int is_device) {
+    crf_status rc = check_handle(h);
+    if (rc != CRF_OK) return rc;
+    if (!U) return CRF_E_INVALID;
+    const float *src = U;
+    if (!is_device) {
+        CK(h, cudaMemcpyAsync(h->staging, U, n_rows(h) * sizeof(float), cudaMemcpyHostToDevice, h->st));
+        src = h->staging;
+    }
+    CK(h, launch_rows_to_planar(src, h->U, h->B, h->L, h->H, h->W, h->P, h->st));
+    CK(h, launch_init_logq(h->U, h->s[0], h->B, h->L, h->H, h->W, h->P, h->st));
+    h->cur = 0;
+    if (!is_device) CK(h, cudaStreamSynchronize(h->st));
+    h->has_unary = true;
+    return CRF_OK;
+}
+
+crf_status crf_set_pairwise(crf_t h, const float *mu, const float *w_or_feats, const float *theta,
+                            int is_device) {
+    (void)theta;
+    crf_status rc = check_handle(h);
+    if (rc != CRF_OK) return rc;
+    if (!mu || !w_or_feats) return CRF_E_INVALID;
+    const size_t LL = (size_t)h->L * h->L;
+    std::vector<float> m(LL);
+    if (is_device) {
+        CK(h, cudaMemcpyAsync(m.data(), mu, LL * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+        CK(h, cudaStreamSynchronize(h->st));
+    } else {
+        std::memcpy(m.data(), mu, LL * sizeof(float));
+    }
+    for (float v : m)
+        if (!std::isfinite(v)) return CRF_E_INVALID;
+    bool sym = true;
+    for (int i = 0; i < h->L; ++i)
+        for (int k = i + 1; k < h->L; ++k)
+            if (m[i * h->L + k] != m[k * h->L + i]) sym = false;
+    const size_t nw = (size_t)h->B * h->nd * h->H * h->W;
+    const float *src = w_or_feats;
+    if (!is_device) {
+        // the staging buffer holds B*N*L floats >= B*nd*N only when L >= nd
+        if (nw > n_rows(h)) {
+            float *tmp = nullptr;
+            CK(h, cudaMalloc((void **)&tmp, nw * sizeof(float)));
+            cudaError_t e = cudaMemcpyAsync(tmp, w_or_feats, nw * sizeof(float), cudaMemcpyHostToDevice, h->st);
+            if (e == cudaSuccess) e = launch_weights_to_planar(tmp, h->w, h->B, h->nd, h->H, h->W, h->P, h->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+            cudaFree(tmp);
+            CK(h, e);
+        } else {
+            CK(h, cudaMemcpyAsync(h->staging, w_or_feats, nw * sizeof(float), cudaMemcpyHostToDevice, h->st));
+            CK(h, launch_weights_to_planar(h->staging, h->w, h->B, h->nd, h->H, h->W, h->P, h->st));
+            CK(h, cudaStreamSynchronize(h->st));
+        }
+    } else {
+        CK(h, launch_weights_to_planar(src, h->w, h->B, h->nd, h->H, h->W, h->P, h->st));
+    }
+    h->mu = m;
+    h->mu_sym = sym;
+    h->has_pairwise = true;
+    h->lambda_valid = false;
+    return CRF_OK;
+}
+
+crf_status crf_set_state(crf_t h, const float *logq, int is_device) {
+    crf_status rc = check_handle(h);
+    if (rc != CRF_OK) return rc;
+    if (!logq) return CRF_E_INVALID;
+    const float *src = logq;
+    if (!is_device) {
+        CK(h, cudaMemcpyAsync(h->staging, logq, n_rows(h) * sizeof(float), cudaMemcpyHostToDevice, h->st));
+        src = h->staging;
+    }
+    CK(h, launch_rows_to_planar(src, h->s[h->cur], h->B, h->L, h->H, h->W, h->P, h->st));
+    if (!is_device) CK(h, cudaStreamSynchronize(h->st));
+    return CRF_OK;
+}
+
+crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
+    crf_status rc = check_handle(h);
+    if (rc != CRF_OK) return rc;
+    if (!p || p->max_iters < 0 || p->rel_tol < 0 || !std::isfinite(p->eta) || p->eta > 1.0)
+        return CRF_E_INVALID;
+    if (!h->has_unary || !h->has_pairwise) return CRF_E_INVALID;
+    const float *eta = nullptr;
+    if (p->eta > 0) {
+        CK(h, launch_fill_eta(h->eta_fixed, h->B, p->eta, h->st));
+        eta = h->eta_fixed;
+    } else {
+        rc = ensure_lambda(h);
+        if (rc != CRF_OK) return rc;
+        eta = h->eta_auto;
+    }
+    if (p->reset) CK(h, launch_init_logq(h->U, h->s[h->cur], h->B, h->L, h->H, h->W, h->P, h->st));
+    rc = ensure_trace(h, p->max_iters);
+    if (rc != CRF_OK) return rc;
+    CK(h, cudaMemsetAsync(h->done, 0, h->B * sizeof(int), h->st));
+    for (int t = 0; t < p->max_iters; ++t) {
+        GridStepLaunch a = step_args(h, eta, t, 1, p->rel_tol);
+        CK(h, launch_grid_step(a, h->st));
+        h->cur ^= 1;
+    }
+    h->last_iters = p->max_iters;
+    if (iters_done) {
+        std::vector<int> dn(h->B);
+        CK(h, cudaMemcpyAsync(dn.data(), h->done, h->B * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        CK(h, cudaStreamSynchronize(h->st));
+        for (int b = 0; b < h->B; ++b) iters_done[b] = dn[b] ? dn[b] : p->max_iters;
+    }
+    return CRF_OK;
+}
+
+crf_status mf_free_energy(crf_t h, double *F) {
+    crf_status rc = check_handle(h);
+    if (rc != CRF_OK) return rc;
+    if (!F) return CRF_E_INVALID;
+    if (!h->has_unary || !h->has_pairwise) return CRF_E_INVALID;
+    GridStepLaunch a = step_args(h, h->eta_fixed, 0, 0, 0.0);
+    CK(h, launch_fill_eta(h->eta_fixed, h->B, 1.0, h->st));
+    CK(h, launch_grid_step(a, h->st));
+    CK(h, cudaMemcpyAsync(F, h->fcur, h->B * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    return read_status(h);
+}
+
+crf_status mf_free_energy_trace(crf_t h, double *F, int32_t n) {
+    crf_status rc = check_handle(h);
+    if (rc != CRF_OK) return rc;
+    if (!F || n < 0 || n > h->last_iters || n > h->trace_cap) return CRF_E_INVALID;
+    if (n == 0) return CRF_OK;
+    CK(h, cudaMemcpy2DAsync(F, n * sizeof(double), h->ftrace, h->trace_cap * sizeof(double),
+                            n * sizeof(double), h->B, cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    return CRF_OK;
+}
+
+static crf_status export_state(crf_t h, float *dst, int is_device, int mode) {
+    crf_status rc = check_handle(h);
+    if (rc != CRF_OK) return rc;
+    if (!dst) return CRF_E_INVALID;
+    float *out = is_device ? dst : h->staging;
+    CK(h, launch_planar_to_rows(h->s[h->cur], out, h->B, h->L, h->H, h->W, h->P, mode, h->st));
+    if (!is_device) {
+        CK(h, cudaMemcpyAsync(dst, h->staging, n_rows(h) * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+        CK(h, cudaStreamSynchronize(h->st));
+    }
+    return CRF_OK;
+}
+
+crf_status mf_marginals(crf_t h, float *q, int is_device) { return export_state(h, q, is_device, CONV_EXP); }
+
+crf_status mf_log_marginals(crf_t h, float *logq, int is_device) {
+    return export_state(h, logq, is_device, CONV_COPY);
+}
+
+crf_status mf_lipschitz(crf_t h, double *Lambda, double *eta) {
+    crf_status rc = check_handle(h);
+    if (rc != CRF_OK) return rc;
+    if (!h->has_pairwise) return CRF_E_INVALID;
+    rc = ensure_lambda(h);
+    if (rc != CRF_OK) return rc;
+    std::vector<float> e(h->B);
+    if (Lambda) CK(h, cudaMemcpyAsync(Lambda, h->Lambda, h->B * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaMemcpyAsync(e.data(), h->eta_auto, h->B * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    if (eta)
+        for (int b = 0; b < h->B; ++b) eta[b] = e[b];
+    return CRF_OK;
+}
+
+}  // extern "C"

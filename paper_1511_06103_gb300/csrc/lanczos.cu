@@ -1,0 +1,503 @@
+// lanczos.cu -- the step-size constant Lambda of Sec. 3.2, on the device.
+//
+// For a pairwise model E(q) is quadratic, so its Hessian H (the paper's
+// "potential matrix") is constant, and the paper takes its largest eigenvalue
+// as the Lipschitz constant of grad E (Sec. 3.2), computed by an iterative
+// eigen-solver (the power method, Sec. 4.3).  The update only moves q inside
+// the tangent space T = {v : sum_l v_il = 0 for all i} of the simplex product,
+// so the constant that governs descent is the top eigenvalue of H restricted
+// to T, H_T = C H C with (C v)_il = v_il - mean_l v_il.  It is never larger
+// than the unrestricted one, is invariant to constant shifts of mu (which do
+// not change the iteration), and is <= 0 exactly when the restricted potential
+// matrix is negative semi-definite, where the full parallel update (eta = 1)
+// is safe (Sec. 3.2).
+//
+// Two forms:
+//  - symmetric mu: H = W (x) mu with W the symmetric weighted adjacency, so
+//    H_T = W (x) (C mu C) and its spectrum is {lambda(W) nu} with nu the
+//    eigenvalues of C mu C.  Lanczos runs on the scalar field W (N unknowns)
+//    and a one-thread Jacobi solve gives nu; Lambda is the largest product of
+//    the extreme values.
+//  - otherwise: Lanczos on H_T itself (N*L unknowns), the matrix-vector
+//    product being the message computation of the step kernel in FP64.
+// Lanczos runs without re-orthogonalisation; its extreme Ritz values converge
+// to the extreme eigenvalues from inside.  Every instance of a batch gets its
+// own constant.  All arithmetic is on the device; the host only sequences
+// launches and reads back convergence flags.
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "internal.h"
+
+namespace proxmf {
+
+namespace {
+
+constexpr int kLzThreads = 256;
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+    // SplitMix64 (Steele, Lea, Flood, OOPSLA 2014).
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-level sum, then last-block-of-instance finalisation in fixed order.
+// Returns true in the (single) thread that holds the instance total in *tot.
+__device__ bool instance_reduce(double v, double *partial, unsigned *counter, int b, int nblk,
+                                double *tot) {
+    __shared__ double red[kLzThreads / 32];
+    __shared__ int last;
+    const int tid = threadIdx.x;
+    v = warp_sum(v);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int k = 0; k < kLzThreads / 32; ++k) s += red[k];
+        partial[(size_t)b * nblk + blockIdx.x] = s;
+        __threadfence();
+        last = atomicAdd(counter + b, 1u) == (unsigned)(nblk - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double acc = 0.0;
+    for (int k = tid; k < nblk; k += kLzThreads) acc += __ldcg(partial + (size_t)b * nblk + k);
+    acc = warp_sum(acc);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid != 0) return false;
+    double s = 0.0;
+    for (int k = 0; k < kLzThreads / 32; ++k) s += red[k];
+    *tot = s;
+    counter[b] = 0u;
+    return true;
+}
+
+struct LzGeom {
+    int B, Lv, L, H, W, P, conn;   // Lv = 1 (scalar W) or L (full H_T)
+    int nblk;                      // blocks per instance over H*W pixels
+};
+
+__device__ __forceinline__ void dir_off(int k, int *dy, int *dx) {
+    *dy = k == 0 ? 0 : 1;
+    *dx = k == 0 ? 1 : (k == 1 ? 0 : (k == 2 ? 1 : -1));
+}
+
+// v = random start vector (uniform in [-1, 1] from SplitMix64), centred over
+// labels in the full form; padding columns are 0.
+__global__ void lz_init_kernel(double *v, LzGeom g, unsigned long long seed) {
+    const int b = blockIdx.y;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.H * g.W) return;
+    const int y = p / g.W, x = p - y * g.W;
+    const size_t plane = (size_t)g.H * g.P;
+    double *vb = v + (size_t)b * g.Lv * plane + (size_t)y * g.P + x;
+    double mean = 0.0;
+    for (int l = 0; l < g.Lv; ++l) {
+        const unsigned long long h =
+            splitmix64(seed ^ splitmix64(((unsigned long long)b * g.Lv + l) * 0x100000000ull + (unsigned)p));
+        const double r = (double)(h >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+        vb[l * plane] = r;
+        mean += r;
+    }
+    if (g.Lv > 1) {
+        mean /= g.Lv;
+        for (int l = 0; l < g.Lv; ++l) vb[l * plane] -= mean;
+    }
+}
+
+// out = A v and alpha[b][k] = v . out.  A = W (scalar) or C H C (full).
+__global__ void __launch_bounds__(kLzThreads)
+lz_matvec_kernel(const double *__restrict__ v, double *__restrict__ out, const float *__restrict__ w,
+                 const float *__restrict__ mu, LzGeom g, const int *stop, double *partial,
+                 unsigned *counter, double *alpha, int ld, int k) {
+    const int b = blockIdx.y;
+    if (stop[b]) return;
+    __shared__ double mus[kMaxLabels * kMaxLabels];
+    if (g.Lv > 1)
+        for (int i = threadIdx.x; i < g.L * g.L; i += blockDim.x) mus[i] = (double)mu[i];
+    __syncthreads();
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nd = g.conn == 8 ? 4 : 2;
+    const size_t plane = (size_t)g.H * g.P;
+    double dot = 0.0;
+    if (p < g.H * g.W) {
+        const int y = p / g.W, x = p - y * g.W;
+        const double *vb = v + (size_t)b * g.Lv * plane;
+        const float *wb = w + (size_t)b * nd * plane;
+        const size_t pix = (size_t)y * g.P + x;
+        double So[kMaxLabels], Si[kMaxLabels];
+        for (int l = 0; l < g.Lv; ++l) So[l] = Si[l] = 0.0;
+        for (int d = 0; d < nd; ++d) {
+            int dy, dx;
+            dir_off(d, &dy, &dx);
+            const int yo = y + dy, xo = x + dx;           // out-going edge to (yo, xo)
+            if (yo >= 0 && yo < g.H && xo >= 0 && xo < g.W) {
+                const double wo = (double)wb[d * plane + pix];
+                const size_t po = (size_t)yo * g.P + xo;
+                for (int l = 0; l < g.Lv; ++l) So[l] += wo * vb[l * plane + po];
+            }
+            const int yi = y - dy, xi = x - dx;           // in-coming edge from (yi, xi)
+            if (yi >= 0 && yi < g.H && xi >= 0 && xi < g.W) {
+                const size_t pi = (size_t)yi * g.P + xi;
+                const double wi = (double)wb[d * plane + pi];
+                for (int l = 0; l < g.Lv; ++l) Si[l] += wi * vb[l * plane + pi];
+            }
+        }
+        double *ob = out + (size_t)b * g.Lv * plane;
+        if (g.Lv == 1) {
+            const double r = So[0] + Si[0];
+            ob[pix] = r;
+            dot = r * vb[pix];
+        } else {
+            double m[kMaxLabels];
+            double mean = 0.0;
+            for (int l = 0; l < g.L; ++l) {
+                double t = 0.0;
+                for (int q = 0; q < g.L; ++q) t += mus[l * g.L + q] * So[q] + mus[q * g.L + l] * Si[q];
+                m[l] = t;
+                mean += t;
+            }
+            mean /= g.L;
+            for (int l = 0; l < g.L; ++l) {
+                const double r = m[l] - mean;
+                ob[l * plane + pix] = r;
+                dot += r * vb[l * plane + pix];
+            }
+        }
+    }
+    double tot;
+    if (instance_reduce(dot, partial, counter, b, g.nblk, &tot)) alpha[(size_t)b * ld + k] = tot;
+}
+
+// wv = wv - alpha_k v - beta_{k-1} vp ; beta[b][k] = |wv|.
+__global__ void __launch_bounds__(kLzThreads)
+lz_axpy_norm_kernel(double *__restrict__ wv, const double *__restrict__ v, const double *__restrict__ vp,
+                    LzGeom g, const int *stop, double *partial, unsigned *counter, const double *alpha,
+                    double *beta, int ld, int k) {
+    const int b = blockIdx.y;
+    if (stop[b]) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t plane = (size_t)g.H * g.P;
+    const double a = alpha[(size_t)b * ld + k];
+    const double bp = k > 0 ? beta[(size_t)b * ld + k - 1] : 0.0;
+    double nrm = 0.0;
+    if (p < g.H * g.W) {
+        const int y = p / g.W, x = p - y * g.W;
+        const size_t off = (size_t)b * g.Lv * plane + (size_t)y * g.P + x;
+        for (int l = 0; l < g.Lv; ++l) {
+            const size_t i = off + l * plane;
+            double r = wv[i] - a * v[i];
+            if (k > 0) r -= bp * vp[i];
+            wv[i] = r;
+            nrm += r * r;
+        }
+    }
+    double tot;
+    if (instance_reduce(nrm, partial, counter, b, g.nblk, &tot)) beta[(size_t)b * ld + k] = sqrt(tot);
+}
+
+// wv /= beta_k, or stop the instance at a (near) invariant subspace.
+__global__ void lz_scale_kernel(double *wv, LzGeom g, int *stop, const double *alpha, const double *beta,
+                                int ld, int k) {
+    const int b = blockIdx.y;
+    if (stop[b]) return;
+    const double bk = beta[(size_t)b * ld + k];
+    const double ref = fabs(alpha[(size_t)b * ld + k]) + (k > 0 ? beta[(size_t)b * ld + k - 1] : 0.0);
+    if (!(bk > 1e-13 * ref) || !(bk > 1e-300)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) stop[b] = k + 1;
+        return;
+    }
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.H * g.W) return;
+    const size_t plane = (size_t)g.H * g.P;
+    const int y = p / g.W, x = p - y * g.W;
+    const size_t off = (size_t)b * g.Lv * plane + (size_t)y * g.P + x;
+    const double inv = 1.0 / bk;
+    for (int l = 0; l < g.Lv; ++l) wv[off + l * plane] *= inv;
+}
+
+// Sturm count: number of eigenvalues of the symmetric tridiagonal (a, c) < x.
+__device__ int sturm_count(const double *a, const double *c, int n, double x, double pivmin) {
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < n; ++i) {
+        const double off = i > 0 ? c[i - 1] * c[i - 1] / d : 0.0;
+        d = a[i] - x - off;
+        if (fabs(d) < pivmin) d = -pivmin;
+        if (d < 0.0) ++cnt;
+    }
+    return cnt;
+}
+
+// Extreme eigenvalues of the Lanczos tridiagonal of each instance, by
+// multisection: warp 0 finds the largest, warp 1 the smallest; each round the
+// 32 lanes test 32 interior points of the bracket.
+__global__ void lz_ritz_kernel(const double *alpha, const double *beta, int ld, int kcur, const int *stop,
+                               double *rmin, double *rmax) {
+    const int b = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int n = kcur;
+    if (stop[b] && stop[b] < n) n = stop[b];
+    if (n <= 0) return;
+    const double *a = alpha + (size_t)b * ld;
+    const double *c = beta + (size_t)b * ld;
+    double lo = INFINITY, hi = -INFINITY, amax = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double r = (i > 0 ? fabs(c[i - 1]) : 0.0) + (i + 1 < n ? fabs(c[i]) : 0.0);
+        lo = fmin(lo, a[i] - r);
+        hi = fmax(hi, a[i] + r);
+        amax = fmax(amax, fabs(a[i]) + r);
+    }
+    const double pivmin = 1e-300 + amax * 1e-300;
+    const bool want_max = wid == 0;
+    for (int round = 0; round < 64; ++round) {
+        if (!(hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)) + 1e-300)) break;
+        const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+        const int cnt = sturm_count(a, c, n, x, pivmin);
+        // max: lambda_max >= x  <=>  cnt < n ; min: lambda_min < x  <=>  cnt >= 1
+        const bool below = want_max ? (cnt < n) : (cnt < 1);
+        const unsigned m = __ballot_sync(0xffffffffu, below);
+        // "below" holds for a prefix of lanes (counts grow with x)
+        const int nb = __popc(m);
+        const double step = (hi - lo) / 33.0;
+        const double nlo = nb > 0 ? lo + step * nb : lo;
+        const double nhi = nb < 32 ? lo + step * (nb + 1) : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    if (lane == 0) {
+        if (want_max)
+            rmax[b] = 0.5 * (lo + hi);
+        else
+            rmin[b] = 0.5 * (lo + hi);
+    }
+}
+
+// Eigenvalues of C mu C (L x L, symmetric part) by cyclic Jacobi; one thread.
+__global__ void mu_tilde_extremes_kernel(const float *mu, int L, double *nu) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double A[kMaxLabels * kMaxLabels];
+    double rm[kMaxLabels], cm[kMaxLabels], tm = 0.0;
+    for (int i = 0; i < L; ++i) {
+        rm[i] = cm[i] = 0.0;
+    }
+    for (int i = 0; i < L; ++i)
+        for (int j = 0; j < L; ++j) {
+            const double v = 0.5 * ((double)mu[i * L + j] + (double)mu[j * L + i]);
+            rm[i] += v / L;
+            cm[j] += v / L;
+            tm += v / ((double)L * L);
+        }
+    for (int i = 0; i < L; ++i)
+        for (int j = 0; j < L; ++j)
+            A[i * L + j] = 0.5 * ((double)mu[i * L + j] + (double)mu[j * L + i]) - rm[i] - cm[j] + tm;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < L; ++i)
+            for (int j = 0; j < L; ++j) {
+                tot += A[i * L + j] * A[i * L + j];
+                if (i != j) off += A[i * L + j] * A[i * L + j];
+            }
+        if (off <= 1e-32 * (tot > 0 ? tot : 1.0)) break;
+        for (int p = 0; p < L; ++p)
+            for (int r = p + 1; r < L; ++r) {
+                const double apr = A[p * L + r];
+                if (fabs(apr) < 1e-300) continue;
+                const double theta = (A[r * L + r] - A[p * L + p]) / (2.0 * apr);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < L; ++k) {
+                    const double akp = A[k * L + p], akr = A[k * L + r];
+                    A[k * L + p] = cs * akp - sn * akr;
+                    A[k * L + r] = sn * akp + cs * akr;
+                }
+                for (int k = 0; k < L; ++k) {
+                    const double apk = A[p * L + k], ark = A[r * L + k];
+                    A[p * L + k] = cs * apk - sn * ark;
+                    A[r * L + k] = sn * apk + cs * ark;
+                }
+            }
+    }
+    double lo = INFINITY, hi = -INFINITY;
+    for (int i = 0; i < L; ++i) {
+        lo = fmin(lo, A[i * L + i]);
+        hi = fmax(hi, A[i * L + i]);
+    }
+    nu[0] = lo;
+    nu[1] = hi;
+}
+
+// Lambda_b and eta_b = 1/(1 + max(Lambda_b, 0)).
+__global__ void lz_finalize_kernel(const double *rmin, const double *rmax, const double *nu, int separable,
+                                   int B, double *Lambda, float *eta) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double lam;
+    if (separable) {
+        const double p0 = rmax[b] * nu[1], p1 = rmax[b] * nu[0], p2 = rmin[b] * nu[1], p3 = rmin[b] * nu[0];
+        lam = fmax(fmax(p0, p1), fmax(p2, p3));
+    } else {
+        lam = rmax[b];
+    }
+    Lambda[b] = lam;
+    eta[b] = (float)(1.0 / (1.0 + (lam > 0.0 ? lam : 0.0)));
+}
+
+__global__ void set_lambda_zero_kernel(int B, double *Lambda, float *eta) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    Lambda[b] = 0.0;
+    eta[b] = 1.0f;
+}
+
+}  // namespace
+
+#define LZ_CHECK(x)                      \
+    do {                                 \
+        cudaError_t e_ = (x);            \
+        if (e_ != cudaSuccess) {         \
+            rc = -3;                     \
+            goto done;                   \
+        }                                \
+    } while (0)
+
+int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps_out) {
+    const int B = job.B;
+    if (steps_out) *steps_out = 0;
+    if (job.L <= 1) {
+        set_lambda_zero_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, job.Lambda, job.eta);
+        return cudaGetLastError() == cudaSuccess ? 0 : -3;
+    }
+    LzGeom g;
+    g.B = B;
+    g.L = job.L;
+    g.Lv = job.mu_sym ? 1 : job.L;
+    g.H = job.H;
+    g.W = job.W;
+    g.P = job.P;
+    g.conn = job.conn;
+    g.nblk = (job.H * job.W + kLzThreads - 1) / kLzThreads;
+    const long long dim = (long long)job.H * job.W * (job.mu_sym ? 1 : (job.L - 1));
+    const int kmax = (int)std::min<long long>(dim, (long long)job.max_steps);
+    const int ld = kmax + 1;
+    const size_t vec = (size_t)B * g.Lv * job.H * job.P;
+    int rc = 0;
+    double *V[3] = {nullptr, nullptr, nullptr};
+    double *alpha = nullptr, *beta = nullptr, *partial = nullptr, *rmin = nullptr, *rmax = nullptr,
+           *nu = nullptr;
+    unsigned *counter = nullptr;
+    int *stop = nullptr;
+    float *mu_dev = nullptr;
+    std::vector<double> hmin(B), hmax(B), pmin(B, NAN), pmax(B, NAN);
+    std::vector<int> hstop(B);
+    int k = 0;
+    dim3 gridp(g.nblk, B);
+    for (int i = 0; i < 3; ++i) {
+        LZ_CHECK(cudaMallocAsync((void **)&V[i], vec * sizeof(double), st));
+        LZ_CHECK(cudaMemsetAsync(V[i], 0, vec * sizeof(double), st));
+    }
+    LZ_CHECK(cudaMallocAsync((void **)&alpha, (size_t)B * ld * sizeof(double), st));
+    LZ_CHECK(cudaMallocAsync((void **)&beta, (size_t)B * ld * sizeof(double), st));
+    LZ_CHECK(cudaMallocAsync((void **)&partial, (size_t)B * g.nblk * sizeof(double), st));
+    LZ_CHECK(cudaMallocAsync((void **)&rmin, (size_t)B * sizeof(double), st));
+    LZ_CHECK(cudaMallocAsync((void **)&rmax, (size_t)B * sizeof(double), st));
+    LZ_CHECK(cudaMallocAsync((void **)&nu, 2 * sizeof(double), st));
+    LZ_CHECK(cudaMallocAsync((void **)&counter, (size_t)B * sizeof(unsigned), st));
+    LZ_CHECK(cudaMallocAsync((void **)&stop, (size_t)B * sizeof(int), st));
+    LZ_CHECK(cudaMallocAsync((void **)&mu_dev, (size_t)job.L * job.L * sizeof(float), st));
+    LZ_CHECK(cudaMemsetAsync(alpha, 0, (size_t)B * ld * sizeof(double), st));
+    LZ_CHECK(cudaMemsetAsync(beta, 0, (size_t)B * ld * sizeof(double), st));
+    LZ_CHECK(cudaMemsetAsync(counter, 0, (size_t)B * sizeof(unsigned), st));
+    LZ_CHECK(cudaMemsetAsync(stop, 0, (size_t)B * sizeof(int), st));
+    LZ_CHECK(cudaMemcpyAsync(mu_dev, job.mu_host, (size_t)job.L * job.L * sizeof(float),
+                             cudaMemcpyHostToDevice, st));
+    LZ_CHECK(cudaStreamSynchronize(st));  // mu_host is pageable and owned by the caller
+
+    // start vector, normalised by a first "scale" through the norm kernels
+    lz_init_kernel<<<gridp, kLzThreads, 0, st>>>(V[1], g, 0x5eed5eedull);
+    LZ_CHECK(cudaGetLastError());
+    {
+        // beta[-1] slot: reuse alpha[.,0] = 0 and compute |v| into beta[.,0]
+        lz_axpy_norm_kernel<<<gridp, kLzThreads, 0, st>>>(V[1], V[0], V[0], g, stop, partial, counter,
+                                                         alpha, beta, ld, 0);
+        LZ_CHECK(cudaGetLastError());
+        lz_scale_kernel<<<gridp, kLzThreads, 0, st>>>(V[1], g, stop, alpha, beta, ld, 0);
+        LZ_CHECK(cudaGetLastError());
+        LZ_CHECK(cudaMemsetAsync(beta, 0, (size_t)B * ld * sizeof(double), st));
+    }
+    {
+        double *vp = V[0], *v = V[1], *wv = V[2];
+        for (k = 0; k < kmax; ++k) {
+            lz_matvec_kernel<<<gridp, kLzThreads, 0, st>>>(v, wv, job.w, mu_dev, g, stop, partial, counter,
+                                                           alpha, ld, k);
+            LZ_CHECK(cudaGetLastError());
+            lz_axpy_norm_kernel<<<gridp, kLzThreads, 0, st>>>(wv, v, vp, g, stop, partial, counter, alpha,
+                                                             beta, ld, k);
+            LZ_CHECK(cudaGetLastError());
+            lz_scale_kernel<<<gridp, kLzThreads, 0, st>>>(wv, g, stop, alpha, beta, ld, k);
+            LZ_CHECK(cudaGetLastError());
+            double *t = vp;
+            vp = v;
+            v = wv;
+            wv = t;
+            const bool last = (k + 1 == kmax);
+            if (((k + 1) % 64) == 0 || last) {
+                lz_ritz_kernel<<<B, 64, 0, st>>>(alpha, beta, ld, k + 1, stop, rmin, rmax);
+                LZ_CHECK(cudaGetLastError());
+                LZ_CHECK(cudaMemcpyAsync(hmin.data(), rmin, B * sizeof(double), cudaMemcpyDeviceToHost, st));
+                LZ_CHECK(cudaMemcpyAsync(hmax.data(), rmax, B * sizeof(double), cudaMemcpyDeviceToHost, st));
+                LZ_CHECK(cudaMemcpyAsync(hstop.data(), stop, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+                LZ_CHECK(cudaStreamSynchronize(st));
+                bool all = true;
+                for (int b = 0; b < B; ++b) {
+                    const double sc = fmax(fmax(fabs(hmin[b]), fabs(hmax[b])), 1e-300);
+                    const bool conv = hstop[b] != 0 ||
+                                      (fabs(hmax[b] - pmax[b]) <= job.tol * sc &&
+                                       fabs(hmin[b] - pmin[b]) <= job.tol * sc);
+                    all = all && conv;
+                    pmin[b] = hmin[b];
+                    pmax[b] = hmax[b];
+                }
+                if (all) {
+                    ++k;
+                    break;
+                }
+            }
+        }
+    }
+    if (job.mu_sym) {
+        mu_tilde_extremes_kernel<<<1, 1, 0, st>>>(mu_dev, job.L, nu);
+        LZ_CHECK(cudaGetLastError());
+    }
+    lz_finalize_kernel<<<(B + 127) / 128, 128, 0, st>>>(rmin, rmax, nu, job.mu_sym ? 1 : 0, B, job.Lambda,
+                                                      job.eta);
+    LZ_CHECK(cudaGetLastError());
+    if (steps_out) *steps_out = k;
+done:
+    for (int i = 0; i < 3; ++i)
+        if (V[i]) cudaFreeAsync(V[i], st);
+    if (alpha) cudaFreeAsync(alpha, st);
+    if (beta) cudaFreeAsync(beta, st);
+    if (partial) cudaFreeAsync(partial, st);
+    if (rmin) cudaFreeAsync(rmin, st);
+    if (rmax) cudaFreeAsync(rmax, st);
+    if (nu) cudaFreeAsync(nu, st);
+    if (counter) cudaFreeAsync(counter, st);
+    if (stop) cudaFreeAsync(stop, st);
+    if (mu_dev) cudaFreeAsync(mu_dev, st);
+    return rc;
+}
+
+}  // namespace proxmf
