@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the parallel proximal mean-field solve on one GB300 (or N replicas).
+
+Workload: the segmentation-shaped grid CRF -- 512 x 512 pixels, L = 21
+labels, 8-connected, unaries -log softmax(N(0, 2^2) logits), symmetric mu
+U(-1,1) with zero diagonal, colour-contrast edge weights -- solved with 100
+parallel proximal iterations at the step eta = 1/(1+Lambda) (Sec. 3.2).
+
+A step is one full solve: q^0 = softmax(-U), 100 fused iterations (messages,
+proximal step, renormalisation, free energy of each iterate) and the free
+energy of the final iterate, with the model (and its step-size constant)
+already resident in HBM.  The metric counts variable-label updates:
+N * L * iterations per solve.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own instance (replicas, weak scaling);
+the reported time is the maximum over ranks.  --impl reference times the
+FP64 CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "mean-field updates/s (vars·labels·iters); p50/p99 solve latency; vs FP32 plain"
+UNIT = "updates/s"
+H, W, L, CONN, ITERS = 512, 512, 21, 8, 100
+SEED = 1
+L2_FLUSH_BYTES = 256 << 20
+WORKLOAD = ("segmentation-shaped grid CRF 512x512, L=21, 8-connected, 100 parallel proximal "
+            "iterations, FP32 messages and state")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--batch", type=int, default=1,
+                   help="instances per GPU (1 = the benchmark workload; >1 for profiling captures)")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# -- clocks ------------------------------------------------------------------
+
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={CLOCK_QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001 - clocks are best effort
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:  # noqa: BLE001
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -- oracle baselines ----------------------------------------------------------
+
+def oracle_solve_rate(side: int, iters: int, seed: int = SEED) -> tuple[float, float, dict]:
+    """Time the FP64 oracle on a side x side instance of the same recipe."""
+    import oracle
+    from paper_1511_06103_gb300 import synth
+    d = synth.segmentation_grid(H=side, W=side, L=L, conn=CONN, seed=seed)
+    m = oracle.Model.grid(d["U"].astype(np.float64), d["mu"].astype(np.float64),
+                          d["w"].astype(np.float64), side, side, CONN)
+    eta = 0.04
+    t0 = time.perf_counter()
+    m.parallel_prox(eta, iters)
+    dt = time.perf_counter() - t0
+    units = side * side * L * iters
+    return units / dt, dt, {"side": side, "iters": iters}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    side, iters = 64, ITERS
+    for _ in range(args.warmup):
+        oracle_solve_rate(side, iters)
+    times = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, dt, _ = oracle_solve_rate(side, iters)
+        times.append(dt)
+    wall = time.perf_counter() - t0
+    units = side * side * L * iters * args.steps
+    value = units / sum(times)
+    cores = oracle.num_threads()
+    sample = (f"{side}x{side} crop of the same recipe (L=21, 8-connected), {iters} iterations per step, "
+              "F evaluated every iteration")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle (plain C, OpenMP)",
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# -- our arm -------------------------------------------------------------------
+
+def algorithmic_bytes_per_launch() -> int:
+    """One grid-step launch reads log q and U and writes log q (4 B each per
+    variable-label) and reads the n_dirs edge-weight planes (4 B per pixel each)."""
+    nd = 4 if CONN == 8 else 2
+    return 12 * H * W * L + 4 * nd * H * W
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1511_06103_gb300 import binding, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    torch.cuda.init()
+    stream = torch.cuda.current_stream(dev)
+    B = args.batch
+    ds = [synth.segmentation_grid(H=H, W=W, L=L, conn=CONN, seed=SEED + rank * B + b) for b in range(B)]
+    d = ds[0]
+    U = torch.from_numpy(np.stack([x["U"] for x in ds])).to(dev)
+    mu = torch.from_numpy(d["mu"]).to(dev)
+    wts = torch.from_numpy(np.stack([x["w"] for x in ds])).to(dev)
+    crf = binding.CRF(binding.CRF_GRID8, L, H, W, batch=B, stream=stream.cuda_stream)
+    crf.set_unary(U)
+    crf.set_pairwise(mu, wts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n0 = crf.launch_count()
+    lam, eta = crf.lipschitz()           # a7: step-size constant, once per model
+    setup_ms = 1000 * (time.perf_counter() - t0)
+    setup_launches = crf.launch_count() - n0
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        crf.iterate(ITERS, eta=0.0, reset=True, final_free_energy=True)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    crf.profile(True)
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    loop_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = crf.launch_count()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    gpu_index = int(vis[local]) if len(vis) > local and vis[local].isdigit() else local
+    with ClockSampler(gpu_index) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            ev_s[k].record(stream)
+            step()
+            ev_e[k].record(stream)
+            ms, n = crf.profile_read()
+            loop_ms.append(ms / n)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        wall1 = time.perf_counter()
+    launches = crf.launch_count() - launches0
+    crf.profile(False)
+    step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units_per_step = B * H * W * L * ITERS
+    value = world * units_per_step * args.steps / (total_ms / 1000.0)
+    F_final = float(crf.free_energy()[0])
+    kern_ms = float(np.mean(loop_ms))
+    peak, peak_kind = measured_peaks()
+    bytes_launch = B * algorithmic_bytes_per_launch()
+    achieved = bytes_launch / (kern_ms / 1000.0) / 1e9
+
+    # end to end through the public API with host buffers: upload U and the
+    # pairwise term, solve (the step-size constant is recomputed because the
+    # pairwise term changed), download q and F.
+    e2e = None
+    if not args.no_e2e:
+        U_h = U.cpu().pin_memory()
+        mu_h = mu.cpu().pin_memory()
+        w_h = wts.cpu().pin_memory()
+        q_h = torch.empty((B, H * W, L), dtype=torch.float32).pin_memory()
+        n_e2e = max(3, min(args.steps, 10))
+
+        def e2e_step():
+            crf.set_unary(U_h)
+            crf.set_pairwise(mu_h, w_h)
+            crf.iterate(ITERS, eta=0.0, final_free_energy=True)
+            crf.marginals(q_h)
+            return crf.free_energy()
+
+        e2e_step()
+        times = []
+        for _ in range(n_e2e):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            times.append(time.perf_counter() - t0)
+        e2e_s = float(np.mean(times))
+        if world > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * units_per_step / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(U_h.numel() * 4 + mu_h.numel() * 4 + w_h.numel() * 4),
+               "d2h_bytes_per_step": int(q_h.numel() * 4 + 8),
+               "ms_per_step": 1000 * e2e_s,
+               "includes": "H2D of U and w, step-size constant (Lanczos), 100 iterations, D2H of q and F"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        side, iters = 160, ITERS
+        rate, dt, _ = oracle_solve_rate(side, iters)
+        cpu = {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{side}x{side} crop of the same recipe (L=21, 8-connected), {iters} iterations, "
+                         f"F every iteration; {dt:.1f} s of CPU work"}
+
+    clocks = clk.summary()
+    if rank == 0:
+        srt = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "H": H, "W": W, "L": L, "conn": CONN, "iters": ITERS,
+                       "batch_per_gpu": B, "seed": SEED, "parallelism": "replicas" if world > 1 else "single",
+                       "eta": float(eta[0]), "Lambda": float(lam[0]),
+                       "l2": "flushed before every step (256 MiB write); within a solve the 70 MB working "
+                             "set stays L2-resident across its 100 iterations"},
+            "latency_ms": {"p50": float(np.percentile(srt, 50)), "p99": float(np.percentile(srt, 99))},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "grid_prox_step_kernel<21,8,sym>",
+                         "bytes_per_launch": bytes_launch, "avg_launch_ms": kern_ms,
+                         "peak_kind": peak_kind},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "setup_ms": setup_ms,
+            "setup_launches": int(setup_launches),
+            "final_F": F_final,
+            "wall_ms_timed": 1000 * (wall1 - wall0),
+        }
+        print(json.dumps(line), flush=True)
+    crf.close()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    try:
+        run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

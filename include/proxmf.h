@@ -115,7 +115,9 @@ typedef struct {
                             /* |F^t - F^{t-1}| <= rel_tol |F^t| (stopping rule  */
                             /* on the objective, Sec. 3.1); 0: fixed count      */
     int32_t refine_fp32;    /* BF16 form: extra FP32 iterations at the end      */
-    int32_t reserved;
+    int32_t final_free_energy; /* 1: also evaluate F(q^K) on the device at the */
+                            /* end (mf_free_energy then returns it without a    */
+                            /* recomputation); no host synchronisation          */
 } mf_params;
 
 /* mf_iterate -- run the parallel proximal iteration of Eq. method:update_natural.
@@ -147,6 +149,19 @@ crf_status mf_log_marginals(crf_t h, float *logq, int is_device);
  * arrays [batch] (either may be NULL).  Computed on the device by a Lanczos
  * iteration on first use after crf_set_pairwise; synchronises the stream. */
 crf_status mf_lipschitz(crf_t h, double *Lambda, double *eta);
+
+/* mf_profile -- enable (1) or disable (0) event timing of the iteration
+ * loop: while enabled, mf_iterate brackets its step launches with two CUDA
+ * events on the handle's stream.  No synchronisation. */
+crf_status mf_profile(crf_t h, int32_t enable);
+
+/* mf_profile_read -- device time of the last profiled iteration loop in ms
+ * and the number of step launches it contained (host scalars).  Waits for
+ * the loop's end event. */
+crf_status mf_profile_read(crf_t h, double *loop_ms, int32_t *launches);
+
+/* crf_launch_count -- number of kernels this handle has launched so far. */
+crf_status crf_launch_count(crf_t h, int64_t *n);
 
 /* crf_error_string -- static description of a status code. */
 const char *crf_error_string(crf_status s);

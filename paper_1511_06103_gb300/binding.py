@@ -45,7 +45,8 @@ class crf_desc(C.Structure):
 
 class mf_params(C.Structure):
     _fields_ = [("eta", C.c_double), ("max_iters", C.c_int32), ("reset", C.c_int32),
-                ("rel_tol", C.c_double), ("refine_fp32", C.c_int32), ("reserved", C.c_int32)]
+                ("rel_tol", C.c_double), ("refine_fp32", C.c_int32),
+                ("final_free_energy", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -65,6 +66,9 @@ _SIGS = {
     "mf_marginals": [_vp, _vp, _i],
     "mf_log_marginals": [_vp, _vp, _i],
     "mf_lipschitz": [_vp, _vp, _vp],
+    "mf_profile": [_vp, C.c_int32],
+    "mf_profile_read": [_vp, _vp, _vp],
+    "crf_launch_count": [_vp, _vp],
 }
 
 
@@ -151,6 +155,23 @@ def mf_lipschitz(h, Lambda_ptr, eta_ptr) -> None:
     _call("mf_lipschitz", h, Lambda_ptr, eta_ptr)
 
 
+def mf_profile(h, enable: int) -> None:
+    _call("mf_profile", h, int(enable))
+
+
+def mf_profile_read(h) -> tuple[float, int]:
+    ms = C.c_double(0.0)
+    n = C.c_int32(0)
+    _call("mf_profile_read", h, C.byref(ms), C.byref(n))
+    return ms.value, n.value
+
+
+def crf_launch_count(h) -> int:
+    n = C.c_int64(0)
+    _call("crf_launch_count", h, C.byref(n))
+    return n.value
+
+
 def crf_version() -> str:
     return lib().crf_version().decode()
 
@@ -232,8 +253,9 @@ class CRF:
         crf_set_state(self.h, p, dev)
 
     def iterate(self, max_iters: int, eta: float = 0.0, reset: bool = False, rel_tol: float = 0.0,
-                refine_fp32: int = 0, want_iters: bool = False):
-        prm = mf_params(float(eta), int(max_iters), int(bool(reset)), float(rel_tol), int(refine_fp32), 0)
+                refine_fp32: int = 0, want_iters: bool = False, final_free_energy: bool = False):
+        prm = mf_params(float(eta), int(max_iters), int(bool(reset)), float(rel_tol), int(refine_fp32),
+                        int(bool(final_free_energy)))
         if want_iters:
             out = np.zeros(self.B, np.int32)
             mf_iterate(self.h, prm, out.ctypes.data)
@@ -263,6 +285,15 @@ class CRF:
 
     def log_marginals(self, out=None):
         return self._export(mf_log_marginals, out)
+
+    def profile(self, enable: bool = True) -> None:
+        mf_profile(self.h, int(enable))
+
+    def profile_read(self) -> tuple[float, int]:
+        return mf_profile_read(self.h)
+
+    def launch_count(self) -> int:
+        return crf_launch_count(self.h)
 
     def lipschitz(self):
         lam = np.zeros(self.B, np.float64)

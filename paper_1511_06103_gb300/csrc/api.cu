@@ -37,6 +37,12 @@ struct crf_s {
     bool mu_sym = true;
     bool has_unary = false, has_pairwise = false, lambda_valid = false, broken = false;
     int lanczos_steps = 0;
+    bool profile = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int prof_launches = 0;
+    bool prof_valid = false;
+    long long launches = 0;
+    bool fcur_valid = false;
 };
 
 namespace {
@@ -73,6 +79,8 @@ void free_all(crf_t h) {
     if (h->counter) cudaFree(h->counter);
     if (h->done) cudaFree(h->done);
     if (h->status) cudaFree(h->status);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
 }
 
 template <typename T>
@@ -144,7 +152,9 @@ crf_status ensure_lambda(crf_t h) {
     job.max_steps = 4000;
     job.tol = 1e-12;
     int steps = 0;
-    const int rc = estimate_lipschitz_grid(job, h->st, &steps);
+    long long nl = 0;
+    const int rc = estimate_lipschitz_grid(job, h->st, &steps, &nl);
+    h->launches += nl;
     if (rc != 0) return fail_cuda(h, cudaErrorUnknown);
     h->lanczos_steps = steps;
     h->lambda_valid = true;
@@ -206,7 +216,8 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
     if (d.topology == CRF_DENSE_GAUSS) return CRF_E_UNSUPPORTED;
     if (d.topology != CRF_GRID4 && d.topology != CRF_GRID8) return CRF_E_INVALID;
     if (d.precision == CRF_BF16) return CRF_E_UNSUPPORTED;
-    if (d.height > (1 << 20) || d.width > (1 << 20) || d.batch > 65535) return CRF_E_INVALID;
+    // grid dimensions: y tiles <= 65535, batch <= 65535 (CUDA grid limits)
+    if (d.height > 65535ll * GY || d.width > (1 << 24) || d.batch > 65535) return CRF_E_INVALID;
     const long long pitch = (d.width + 31) / 32 * 32;
     if ((long long)d.batch * d.n_labels * d.height * pitch > (1ll << 40)) return CRF_E_INVALID;
 
@@ -291,7 +302,9 @@ crf_status crf_set_unary(crf_t h, const float *U, int is_device) {
     }
     CK(h, launch_rows_to_planar(src, h->U, h->B, h->L, h->H, h->W, h->P, h->st));
     CK(h, launch_init_logq(h->U, h->s[0], h->B, h->L, h->H, h->W, h->P, h->st));
+    h->launches += 2;
     h->cur = 0;
+    h->fcur_valid = false;
     if (!is_device) CK(h, cudaStreamSynchronize(h->st));
     h->has_unary = true;
     return CRF_OK;
@@ -337,8 +350,10 @@ crf_status crf_set_pairwise(crf_t h, const float *mu, const float *w_or_feats, c
     } else {
         CK(h, launch_weights_to_planar(src, h->w, h->B, h->nd, h->H, h->W, h->P, h->st));
     }
+    h->launches++;
     h->mu = m;
     h->mu_sym = sym;
+    h->fcur_valid = false;
     h->has_pairwise = true;
     h->lambda_valid = false;
     return CRF_OK;
@@ -354,6 +369,8 @@ crf_status crf_set_state(crf_t h, const float *logq, int is_device) {
         src = h->staging;
     }
     CK(h, launch_rows_to_planar(src, h->s[h->cur], h->B, h->L, h->H, h->W, h->P, h->st));
+    h->launches++;
+    h->fcur_valid = false;
     if (!is_device) CK(h, cudaStreamSynchronize(h->st));
     return CRF_OK;
 }
@@ -367,22 +384,41 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
     const float *eta = nullptr;
     if (p->eta > 0) {
         CK(h, launch_fill_eta(h->eta_fixed, h->B, p->eta, h->st));
+        h->launches++;
         eta = h->eta_fixed;
     } else {
         rc = ensure_lambda(h);
         if (rc != CRF_OK) return rc;
         eta = h->eta_auto;
     }
-    if (p->reset) CK(h, launch_init_logq(h->U, h->s[h->cur], h->B, h->L, h->H, h->W, h->P, h->st));
+    if (p->reset) {
+        CK(h, launch_init_logq(h->U, h->s[h->cur], h->B, h->L, h->H, h->W, h->P, h->st));
+        h->launches++;
+    }
     rc = ensure_trace(h, p->max_iters);
     if (rc != CRF_OK) return rc;
-    CK(h, cudaMemsetAsync(h->done, 0, h->B * sizeof(int), h->st));
+    if (p->rel_tol > 0) CK(h, cudaMemsetAsync(h->done, 0, h->B * sizeof(int), h->st));
+    if (h->profile) CK(h, cudaEventRecord(h->ev0, h->st));
     for (int t = 0; t < p->max_iters; ++t) {
         GridStepLaunch a = step_args(h, eta, t, 1, p->rel_tol);
+        if (p->rel_tol <= 0) a.done = nullptr;
         CK(h, launch_grid_step(a, h->st));
         h->cur ^= 1;
     }
+    h->launches += p->max_iters;
+    if (h->profile) {
+        CK(h, cudaEventRecord(h->ev1, h->st));
+        h->prof_launches = p->max_iters;
+        h->prof_valid = true;
+    }
     h->last_iters = p->max_iters;
+    h->fcur_valid = false;
+    if (p->final_free_energy) {
+        GridStepLaunch a = step_args(h, eta, 0, 0, 0.0);
+        CK(h, launch_grid_step(a, h->st));
+        h->launches++;
+        h->fcur_valid = true;
+    }
     if (iters_done) {
         std::vector<int> dn(h->B);
         CK(h, cudaMemcpyAsync(dn.data(), h->done, h->B * sizeof(int), cudaMemcpyDeviceToHost, h->st));
@@ -397,9 +433,13 @@ crf_status mf_free_energy(crf_t h, double *F) {
     if (rc != CRF_OK) return rc;
     if (!F) return CRF_E_INVALID;
     if (!h->has_unary || !h->has_pairwise) return CRF_E_INVALID;
-    GridStepLaunch a = step_args(h, h->eta_fixed, 0, 0, 0.0);
-    CK(h, launch_fill_eta(h->eta_fixed, h->B, 1.0, h->st));
-    CK(h, launch_grid_step(a, h->st));
+    if (!h->fcur_valid) {
+        GridStepLaunch a = step_args(h, h->eta_fixed, 0, 0, 0.0);
+        CK(h, launch_fill_eta(h->eta_fixed, h->B, 1.0, h->st));
+        CK(h, launch_grid_step(a, h->st));
+        h->launches += 2;
+        h->fcur_valid = true;
+    }
     CK(h, cudaMemcpyAsync(F, h->fcur, h->B * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     CK(h, cudaStreamSynchronize(h->st));
     return read_status(h);
@@ -422,6 +462,7 @@ static crf_status export_state(crf_t h, float *dst, int is_device, int mode) {
     if (!dst) return CRF_E_INVALID;
     float *out = is_device ? dst : h->staging;
     CK(h, launch_planar_to_rows(h->s[h->cur], out, h->B, h->L, h->H, h->W, h->P, mode, h->st));
+    h->launches++;
     if (!is_device) {
         CK(h, cudaMemcpyAsync(dst, h->staging, n_rows(h) * sizeof(float), cudaMemcpyDeviceToHost, h->st));
         CK(h, cudaStreamSynchronize(h->st));
@@ -447,6 +488,36 @@ crf_status mf_lipschitz(crf_t h, double *Lambda, double *eta) {
     CK(h, cudaStreamSynchronize(h->st));
     if (eta)
         for (int b = 0; b < h->B; ++b) eta[b] = e[b];
+    return CRF_OK;
+}
+
+crf_status mf_profile(crf_t h, int32_t enable) {
+    crf_status rc = check_handle(h);
+    if (rc != CRF_OK) return rc;
+    if (enable && !h->ev0) {
+        CK(h, cudaEventCreate(&h->ev0));
+        CK(h, cudaEventCreate(&h->ev1));
+    }
+    h->profile = enable != 0;
+    h->prof_valid = false;
+    return CRF_OK;
+}
+
+crf_status mf_profile_read(crf_t h, double *loop_ms, int32_t *launches) {
+    crf_status rc = check_handle(h);
+    if (rc != CRF_OK) return rc;
+    if (!h->prof_valid) return CRF_E_INVALID;
+    CK(h, cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    if (loop_ms) *loop_ms = ms;
+    if (launches) *launches = h->prof_launches;
+    return CRF_OK;
+}
+
+crf_status crf_launch_count(crf_t h, int64_t *n) {
+    if (!h || !n) return CRF_E_INVALID;
+    *n = h->launches;
     return CRF_OK;
 }
 

@@ -80,6 +80,7 @@ struct LipschitzJob {
     int max_steps;
     double tol;
 };
-int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps_out);
+int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps_out,
+                            long long *launches_out);
 
 }  // namespace proxmf

@@ -373,11 +373,15 @@ __global__ void set_lambda_zero_kernel(int B, double *Lambda, float *eta) {
         }                                \
     } while (0)
 
-int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps_out) {
+int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps_out,
+                            long long *launches_out) {
     const int B = job.B;
     if (steps_out) *steps_out = 0;
+    if (launches_out) *launches_out = 0;
+    long long nl = 0;
     if (job.L <= 1) {
         set_lambda_zero_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, job.Lambda, job.eta);
+        if (launches_out) *launches_out = 1;
         return cudaGetLastError() == cudaSuccess ? 0 : -3;
     }
     LzGeom g;
@@ -427,6 +431,7 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
 
     // start vector, normalised by a first "scale" through the norm kernels
     lz_init_kernel<<<gridp, kLzThreads, 0, st>>>(V[1], g, 0x5eed5eedull);
+    nl += 3;
     LZ_CHECK(cudaGetLastError());
     {
         // beta[-1] slot: reuse alpha[.,0] = 0 and compute |v| into beta[.,0]
@@ -448,6 +453,7 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
             LZ_CHECK(cudaGetLastError());
             lz_scale_kernel<<<gridp, kLzThreads, 0, st>>>(wv, g, stop, alpha, beta, ld, k);
             LZ_CHECK(cudaGetLastError());
+            nl += 3;
             double *t = vp;
             vp = v;
             v = wv;
@@ -456,6 +462,7 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
             if (((k + 1) % 64) == 0 || last) {
                 lz_ritz_kernel<<<B, 64, 0, st>>>(alpha, beta, ld, k + 1, stop, rmin, rmax);
                 LZ_CHECK(cudaGetLastError());
+                nl += 1;
                 LZ_CHECK(cudaMemcpyAsync(hmin.data(), rmin, B * sizeof(double), cudaMemcpyDeviceToHost, st));
                 LZ_CHECK(cudaMemcpyAsync(hmax.data(), rmax, B * sizeof(double), cudaMemcpyDeviceToHost, st));
                 LZ_CHECK(cudaMemcpyAsync(hstop.data(), stop, B * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -484,7 +491,9 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
     lz_finalize_kernel<<<(B + 127) / 128, 128, 0, st>>>(rmin, rmax, nu, job.mu_sym ? 1 : 0, B, job.Lambda,
                                                       job.eta);
     LZ_CHECK(cudaGetLastError());
+    nl += job.mu_sym ? 2 : 1;
     if (steps_out) *steps_out = k;
+    if (launches_out) *launches_out = nl;
 done:
     for (int i = 0; i < 3; ++i)
         if (V[i]) cudaFreeAsync(V[i], st);

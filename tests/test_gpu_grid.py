@@ -18,6 +18,16 @@ TOL_Q = 1e-5
 TOL_F = 1e-6
 
 
+def f_close(F, F_ref, n_vars):
+    """|dF| <= 1e-6 |F|, with |F| floored at one nat per variable: F is a sum
+    of n_vars per-variable terms of order one that can cancel to near zero
+    (with unaries -log softmax(logits) the unary-only free energy is exactly
+    0), where a purely relative test would ask for more than FP32 messages
+    carry."""
+    F, F_ref = np.asarray(F, np.float64), np.asarray(F_ref, np.float64)
+    return bool(np.all(np.abs(F - F_ref) <= TOL_F * np.maximum(np.abs(F_ref), n_vars)))
+
+
 @pytest.fixture(scope="module")
 def env():
     import torch
@@ -83,7 +93,7 @@ def test_single_step_parity(env, Hh, Ww, L, conn, sym):
     F_ref = m.free_energy(np.exp(f64(s0)))
     s, _, trace = gpu_run(binding, torch, d, 0.37, 1, s0=s0)
     assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q_STEP
-    assert abs(trace[0] - F_ref) <= TOL_F * max(1.0, abs(F_ref))
+    assert f_close(trace[0], F_ref, Hh * Ww)
 
 
 @pytest.mark.parametrize("Hh,Ww,L,conn,sym,eta,iters", [
@@ -96,8 +106,8 @@ def test_trajectory_parity(env, Hh, Ww, L, conn, sym, eta, iters):
     s_ref, F_ref = m.parallel_prox(eta, iters)
     s, F, trace = gpu_run(binding, torch, d, eta, iters)
     assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q
-    assert np.all(np.abs(trace - F_ref[:-1]) <= TOL_F * np.abs(F_ref[:-1]))
-    assert abs(F - F_ref[-1]) <= TOL_F * abs(F_ref[-1])
+    assert f_close(trace, F_ref[:-1], Hh * Ww)
+    assert f_close(F, F_ref[-1], Hh * Ww)
 
 
 def test_binary_denoising_trajectory(env):
@@ -109,8 +119,8 @@ def test_binary_denoising_trajectory(env):
     s_ref, F_ref = m.parallel_prox(g["eta"], 50)
     s, F, trace = gpu_run(binding, torch, d, g["eta"], 50)
     assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q
-    assert abs(F - F_ref[-1]) <= TOL_F * abs(F_ref[-1])
-    assert np.all(np.abs(trace - F_ref[:-1]) <= TOL_F * np.abs(F_ref[:-1]))
+    assert f_close(F, F_ref[-1], 64 * 64)
+    assert f_close(trace, F_ref[:-1], 64 * 64)
 
 
 def test_segmentation_grid_full_size_first_steps(env):
@@ -123,7 +133,8 @@ def test_segmentation_grid_full_size_first_steps(env):
     s_ref, F_ref = m.parallel_prox(eta, 8)
     s, F, trace = gpu_run(binding, torch, d, eta, 8)
     assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q
-    assert abs(F - F_ref[-1]) <= TOL_F * abs(F_ref[-1])
+    assert f_close(F, F_ref[-1], 512 * 512)
+    assert f_close(trace, F_ref[:-1], 512 * 512)
 
 
 def test_step_constant_binary_denoising(env):
