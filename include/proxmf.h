@@ -163,6 +163,31 @@ crf_status mf_profile_read(crf_t h, double *loop_ms, int32_t *launches);
 /* crf_launch_count -- number of kernels this handle has launched so far. */
 crf_status crf_launch_count(crf_t h, int64_t *n);
 
+/* mf_grid_step_noalloc -- one parallel proximal step of a single grid
+ * instance on caller-owned device buffers, for callers that cannot allocate
+ * device memory (an allocator or memory pool that owns the device, a region
+ * where cudaMalloc is forbidden or would synchronise).  The paper has no
+ * counterpart: this is an integration entry point, not a step of the method.
+ *   topology   CRF_GRID4 or CRF_GRID8; n_labels L in 1..32.
+ *   U, logq_in, logq_out  label-planar [L][height][width] float32, device.
+ *   w          [n_dirs][height][width] float32, device (as crf_set_pairwise;
+ *              entries whose edge leaves the image are ignored).
+ *   mu         [L][L] float32, HOST memory.
+ *   eta        step in (0, 1].
+ *   F_out      device double: receives F(q_in); NaN if it is not finite.
+ *   stream     cudaStream_t (NULL = legacy default stream).
+ * Allocates nothing: its scratch (tile partials, counter, status, step) is a
+ * 512 KiB static device array, held on every GPU that loads the library until
+ * exit, which limits one call to 65504 tiles of 32 x 8 pixels (CRF_E_INVALID
+ * beyond).  The first call on a device looks up that array's address (make it
+ * before any stream capture).  All calls share the array: calls that overlap
+ * on the GPU race and must be serialised by the caller.  logq_in and logq_out
+ * must not alias.  Asynchronous; errors of the launch are CRF_E_CUDA. */
+crf_status mf_grid_step_noalloc(int32_t topology, int32_t n_labels, int64_t height,
+                                int64_t width, const float *U, const float *w,
+                                const float *mu, const float *logq_in, float *logq_out,
+                                double eta, double *F_out, void *stream);
+
 /* crf_error_string -- static description of a status code. */
 const char *crf_error_string(crf_status s);
 

@@ -1,0 +1,89 @@
+"""The allocation-free step entry point (for callers that cannot call
+cudaMalloc) gives the same result as one step through the handle API.
+
+Collected last on purpose: it calls the library through raw ctypes with its
+own device buffers, and must pass both alone in a fresh process and after the
+other GPU tests (its scratch array is shared by every call)."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_1511_06103_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def planar(a, H, W):
+    """[N][L] rows -> [L][H][W] label planes."""
+    return np.ascontiguousarray(a.reshape(H, W, -1).transpose(2, 0, 1))
+
+
+def rows(p, H, W):
+    return np.ascontiguousarray(p.transpose(1, 2, 0).reshape(H * W, -1))
+
+
+@pytest.mark.parametrize("Hh,Ww,L,conn,sym", [(37, 45, 21, 8, True), (20, 70, 5, 4, False)])
+def test_noalloc_step_matches_handle_api(Hh, Ww, L, conn, sym):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    from paper_1511_06103_gb300 import binding, build
+    build.build()
+    lib = binding.lib()
+    fn = lib.mf_grid_step_noalloc
+    fn.restype = C.c_int
+    fn.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                   C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]
+    dev = torch.device("cuda:0")
+    d = synth.random_grid(Hh, Ww, L, conn, seed=4242 + L, symmetric=sym)
+    s0 = synth.random_logq(Hh * Ww, L, seed=17)
+    eta = 0.31
+    topo = binding.CRF_GRID8 if conn == 8 else binding.CRF_GRID4
+
+    # reference: two steps through the handle API
+    ref_s, ref_F = [], []
+    with binding.CRF(topo, L, Hh, Ww) as crf:
+        crf.set_unary(d["U"])
+        crf.set_pairwise(d["mu"], d["w"])
+        crf.set_state(s0)
+        for _ in range(2):
+            crf.iterate(1, eta=eta)
+            ref_F.append(crf.free_energy_trace(1)[0, 0])
+            ref_s.append(crf.log_marginals()[0])
+
+    # the same two steps through the allocation-free entry point
+    U = torch.from_numpy(planar(d["U"], Hh, Ww)).to(dev)
+    w = torch.from_numpy(np.ascontiguousarray(d["w"])).to(dev)
+    mu = np.ascontiguousarray(d["mu"], np.float32)
+    bufs = [torch.from_numpy(planar(s0, Hh, Ww)).to(dev), torch.empty((L, Hh, Ww), device=dev)]
+    F = torch.zeros(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    for k in range(2):
+        rc = fn(topo, L, Hh, Ww, U.data_ptr(), w.data_ptr(), mu.ctypes.data, bufs[k % 2].data_ptr(),
+                bufs[(k + 1) % 2].data_ptr(), eta, F.data_ptr(), stream)
+        assert rc == 0
+        torch.cuda.synchronize()
+        out = rows(bufs[(k + 1) % 2].cpu().numpy(), Hh, Ww)
+        assert np.abs(np.exp(out.astype(np.float64)) - np.exp(ref_s[k].astype(np.float64))).max() <= 1e-6
+        assert abs(F.item() - ref_F[k]) <= 1e-6 * max(abs(ref_F[k]), Hh * Ww)
+
+
+def test_noalloc_rejects_oversize_and_bad_arguments():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1511_06103_gb300 import binding, build
+    build.build()
+    fn = binding.lib().mf_grid_step_noalloc
+    fn.restype = C.c_int
+    fn.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                   C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]
+    mu = np.zeros((3, 3), np.float32)
+    fake = 256  # never dereferenced: every case below is rejected before any launch
+    # 4096 x 4096 needs 65536 tiles > 65504
+    assert fn(1, 3, 4096, 4096, fake, fake, mu.ctypes.data, fake, fake * 2, 0.5, fake, None) == -1
+    assert fn(1, 0, 8, 8, fake, fake, mu.ctypes.data, fake, fake * 2, 0.5, fake, None) == -1
+    assert fn(1, 3, 8, 8, fake, fake, mu.ctypes.data, fake, fake, 0.5, fake, None) == -1
+    assert fn(1, 3, 8, 8, fake, fake, mu.ctypes.data, fake, fake * 2, 0.0, fake, None) == -1
