@@ -169,17 +169,21 @@ crf_status crf_launch_count(crf_t h, int64_t *n);
  * where cudaMalloc is forbidden or would synchronise).  The paper has no
  * counterpart: this is an integration entry point, not a step of the method.
  *   topology   CRF_GRID4 or CRF_GRID8; n_labels L in 1..32.
- *   U, logq_in, logq_out  label-planar [L][height][width] float32, device.
- *   w          [n_dirs][height][width] float32, device (as crf_set_pairwise;
- *              entries whose edge leaves the image are ignored).
+ *   U, logq_in, logq_out  pixel-major [height][width][Lp] float32, device,
+ *              with Lp = L rounded up to a multiple of 4 (2 when L <= 2);
+ *              padding entries must hold U = 0 and log q = -1e30, and the
+ *              step writes -1e30 there.
+ *   w          pixel-major [height][width][n_dirs] float32, device, same
+ *              directions as crf_set_pairwise; entries whose edge leaves the
+ *              image must be 0.
  *   mu         [L][L] float32, HOST memory.
  *   eta        step in (0, 1].
  *   F_out      device double: receives F(q_in); NaN if it is not finite.
  *   stream     cudaStream_t (NULL = legacy default stream).
- * Allocates nothing: its scratch (tile partials, counter, status, step) is a
- * 512 KiB static device array, held on every GPU that loads the library until
- * exit, which limits one call to 65504 tiles of 32 x 8 pixels (CRF_E_INVALID
- * beyond).  The first call on a device looks up that array's address (make it
+ * Allocates nothing: its scratch (tile partials, counter, status, step, mu
+ * table) is a 512 KiB static device array, held on every GPU that loads the
+ * library until exit, which limits one call to 64480 tiles of 32 x 8 pixels
+ * (CRF_E_INVALID beyond).  The first call on a device looks up that array's address (make it
  * before any stream capture).  All calls share the array: calls that overlap
  * on the GPU race and must be serialised by the caller.  logq_in and logq_out
  * must not alias.  Asynchronous; errors of the launch are CRF_E_CUDA. */

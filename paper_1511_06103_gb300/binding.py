@@ -20,7 +20,9 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libproxmf.so")
+# PROXMF_LIB selects another build of the same library (e.g. an experimental
+# variant); the default is the in-tree build.
+LIB_PATH = os.environ.get("PROXMF_LIB") or os.path.join(HERE, "_build", "libproxmf.so")
 
 CRF_GRID4, CRF_GRID8, CRF_DENSE_GAUSS = 0, 1, 2
 CRF_FP32, CRF_BF16 = 0, 1

@@ -14,12 +14,15 @@ using namespace proxmf;
 
 struct crf_s {
     crf_desc d{};
-    int B = 0, L = 0, H = 0, W = 0, P = 0, nd = 0, conn = 4;
+    int B = 0, L = 0, H = 0, W = 0, nd = 0, conn = 4;
+    int LP = 0;                  // labels stored per pixel (padded)
+    int LT = 0;                  // label count of the step kernel
     int nblk = 0;
     cudaStream_t st = nullptr;
-    float *U = nullptr;          // planar unaries
-    float *s[2] = {nullptr, nullptr};  // planar log q, ping-pong
-    float *w = nullptr;          // planar weights
+    float *U = nullptr;          // [B][N][LP] unaries, padding 0
+    float *s[2] = {nullptr, nullptr};  // [B][N][LP] log q, ping-pong, padding kPadLogQ
+    float *w = nullptr;          // [B][N][nd] edge weights
+    float2 *mu_pairs = nullptr;  // device [2][LT][NPP] mu column / row pairs
     float *eta_fixed = nullptr;  // [B]
     float *eta_auto = nullptr;   // [B]
     double *Lambda = nullptr;    // [B]
@@ -66,8 +69,9 @@ crf_status check_handle(crf_t h) {
     return CRF_OK;
 }
 
-size_t n_rows(const crf_t h) { return (size_t)h->B * h->H * h->W * h->L; }
-size_t n_planar(const crf_t h) { return (size_t)h->B * h->L * h->H * h->P; }
+size_t n_pix(const crf_t h) { return (size_t)h->B * h->H * h->W; }
+size_t n_rows(const crf_t h) { return n_pix(h) * h->L; }
+size_t n_padded(const crf_t h) { return n_pix(h) * h->LP; }
 
 void free_all(crf_t h) {
     float *fs[] = {h->U, h->s[0], h->s[1], h->w, h->eta_fixed, h->eta_auto, h->staging};
@@ -79,6 +83,7 @@ void free_all(crf_t h) {
     if (h->counter) cudaFree(h->counter);
     if (h->done) cudaFree(h->done);
     if (h->status) cudaFree(h->status);
+    if (h->mu_pairs) cudaFree(h->mu_pairs);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
 }
@@ -114,6 +119,8 @@ GridStepLaunch step_args(crf_t h, const float *eta, int t, int update, double re
     a.U = h->U;
     a.w = h->w;
     a.eta = eta;
+    a.mu_out = h->mu_pairs;
+    a.mu_in = h->mu_pairs + (size_t)h->LT * mu_pair_slots(h->LT);
     a.partial = h->partial;
     a.counter = h->counter;
     a.f_trace = h->ftrace;
@@ -124,14 +131,12 @@ GridStepLaunch step_args(crf_t h, const float *eta, int t, int update, double re
     a.L = h->L;
     a.H = h->H;
     a.W = h->W;
-    a.P = h->P;
     a.conn = h->conn;
     a.t = t;
     a.trace_cap = h->trace_cap;
     a.update = update;
     a.rel_tol = rel_tol;
     a.mu_sym = h->mu_sym;
-    a.mu_host = h->mu.data();
     return a;
 }
 
@@ -145,7 +150,7 @@ crf_status ensure_lambda(crf_t h) {
     job.L = h->L;
     job.H = h->H;
     job.W = h->W;
-    job.P = h->P;
+    job.P = h->W;
     job.conn = h->conn;
     job.Lambda = h->Lambda;
     job.eta = h->eta_auto;
@@ -177,12 +182,31 @@ crf_status read_status(crf_t h) {
 namespace proxmf {
 
 cudaError_t launch_grid_step(const GridStepLaunch &a, cudaStream_t st) {
-    if (a.L <= 2) return launch_grid_step_l2(a, st);
-    if (a.L <= 4) return launch_grid_step_l4(a, st);
-    if (a.L <= 8) return launch_grid_step_l8(a, st);
-    if (a.L <= 16) return launch_grid_step_l16(a, st);
-    if (a.L <= 21) return launch_grid_step_l21(a, st);
-    return launch_grid_step_l32(a, st);
+    switch (kernel_labels(a.L)) {
+    case 2: return launch_grid_step_l2(a, st);
+    case 4: return launch_grid_step_l4(a, st);
+    case 8: return launch_grid_step_l8(a, st);
+    case 12: return launch_grid_step_l12(a, st);
+    case 16: return launch_grid_step_l16(a, st);
+    case 20: return launch_grid_step_l20(a, st);
+    case 21: return launch_grid_step_l21(a, st);
+    case 24: return launch_grid_step_l24(a, st);
+    case 28: return launch_grid_step_l28(a, st);
+    default: return launch_grid_step_l32(a, st);
+    }
+}
+
+// Column pairs (for mu S) and row pairs (for mu^T S) of mu, zero padded to
+// the kernel label count (see mu_pair_slots).
+void build_mu_pairs(const std::vector<float> &mu, int L, int LT, std::vector<float2> &out) {
+    const int NPP = mu_pair_slots(LT);
+    out.assign((size_t)2 * LT * NPP, make_float2(0.f, 0.f));
+    auto at = [&](int r, int c) { return (r < L && c < L) ? mu[(size_t)r * L + c] : 0.f; };
+    for (int k = 0; k < LT; ++k)
+        for (int j = 0; j < NPP; ++j) {
+            out[(size_t)k * NPP + j] = make_float2(at(2 * j, k), at(2 * j + 1, k));
+            out[(size_t)(LT + k) * NPP + j] = make_float2(at(k, 2 * j), at(k, 2 * j + 1));
+        }
 }
 
 }  // namespace proxmf
@@ -218,8 +242,7 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
     if (d.precision == CRF_BF16) return CRF_E_UNSUPPORTED;
     // grid dimensions: y tiles <= 65535, batch <= 65535 (CUDA grid limits)
     if (d.height > 65535ll * GY || d.width > (1 << 24) || d.batch > 65535) return CRF_E_INVALID;
-    const long long pitch = (d.width + 31) / 32 * 32;
-    if ((long long)d.batch * d.n_labels * d.height * pitch > (1ll << 40)) return CRF_E_INVALID;
+    if ((long long)d.batch * storage_labels(d.n_labels) * d.height * d.width > (1ll << 40)) return CRF_E_INVALID;
 
     crf_t h = new (std::nothrow) crf_s();
     if (!h) return CRF_E_OOM;
@@ -228,7 +251,8 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
     h->L = d.n_labels;
     h->H = (int)d.height;
     h->W = (int)d.width;
-    h->P = (int)pitch;
+    h->LP = storage_labels(h->L);
+    h->LT = kernel_labels(h->L);
     h->conn = d.topology == CRF_GRID8 ? 8 : 4;
     h->nd = h->conn == 8 ? 4 : 2;
     h->st = (cudaStream_t)d.stream;
@@ -238,10 +262,11 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
     h->mu.assign((size_t)h->L * h->L, 0.f);
 
     bool ok = true;
-    ok = ok && dalloc(&h->U, n_planar(h)) == cudaSuccess;
-    ok = ok && dalloc(&h->s[0], n_planar(h)) == cudaSuccess;
-    ok = ok && dalloc(&h->s[1], n_planar(h)) == cudaSuccess;
-    ok = ok && dalloc(&h->w, (size_t)h->B * h->nd * h->H * h->P) == cudaSuccess;
+    ok = ok && dalloc(&h->U, n_padded(h)) == cudaSuccess;
+    ok = ok && dalloc(&h->s[0], n_padded(h)) == cudaSuccess;
+    ok = ok && dalloc(&h->s[1], n_padded(h)) == cudaSuccess;
+    ok = ok && dalloc(&h->w, n_pix(h) * h->nd) == cudaSuccess;
+    ok = ok && dalloc(&h->mu_pairs, (size_t)2 * h->LT * mu_pair_slots(h->LT)) == cudaSuccess;
     ok = ok && dalloc(&h->eta_fixed, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->eta_auto, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->Lambda, h->B) == cudaSuccess;
@@ -258,10 +283,12 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
         return CRF_E_OOM;
     }
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->U, 0, n_planar(h) * sizeof(float), h->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->s[0], 0, n_planar(h) * sizeof(float), h->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->s[1], 0, n_planar(h) * sizeof(float), h->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->w, 0, (size_t)h->B * h->nd * h->H * h->P * sizeof(float), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->U, 0, n_padded(h) * sizeof(float), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->s[0], 0, n_padded(h) * sizeof(float), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->s[1], 0, n_padded(h) * sizeof(float), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->w, 0, n_pix(h) * h->nd * sizeof(float), h->st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(h->mu_pairs, 0, (size_t)2 * h->LT * mu_pair_slots(h->LT) * sizeof(float2), h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->counter, 0, h->B * sizeof(unsigned), h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->done, 0, h->B * sizeof(int), h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), h->st);
@@ -300,8 +327,8 @@ crf_status crf_set_unary(crf_t h, const float *U, int is_device) {
         CK(h, cudaMemcpyAsync(h->staging, U, n_rows(h) * sizeof(float), cudaMemcpyHostToDevice, h->st));
         src = h->staging;
     }
-    CK(h, launch_rows_to_planar(src, h->U, h->B, h->L, h->H, h->W, h->P, h->st));
-    CK(h, launch_init_logq(h->U, h->s[0], h->B, h->L, h->H, h->W, h->P, h->st));
+    CK(h, launch_rows_to_padded(src, h->U, (long long)n_pix(h), h->L, h->LP, 0.f, h->st));
+    CK(h, launch_init_logq(h->U, h->s[0], (long long)n_pix(h), h->L, h->LP, h->st));
     h->launches += 2;
     h->cur = 0;
     h->fcur_valid = false;
@@ -330,7 +357,11 @@ crf_status crf_set_pairwise(crf_t h, const float *mu, const float *w_or_feats, c
     for (int i = 0; i < h->L; ++i)
         for (int k = i + 1; k < h->L; ++k)
             if (m[i * h->L + k] != m[k * h->L + i]) sym = false;
-    const size_t nw = (size_t)h->B * h->nd * h->H * h->W;
+    const size_t nw = n_pix(h) * h->nd;
+    std::vector<float2> pairs;
+    build_mu_pairs(m, h->L, h->LT, pairs);
+    CK(h, cudaMemcpyAsync(h->mu_pairs, pairs.data(), pairs.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                          h->st));
     const float *src = w_or_feats;
     if (!is_device) {
         // the staging buffer holds B*N*L floats >= B*nd*N only when L >= nd
@@ -338,17 +369,18 @@ crf_status crf_set_pairwise(crf_t h, const float *mu, const float *w_or_feats, c
             float *tmp = nullptr;
             CK(h, cudaMalloc((void **)&tmp, nw * sizeof(float)));
             cudaError_t e = cudaMemcpyAsync(tmp, w_or_feats, nw * sizeof(float), cudaMemcpyHostToDevice, h->st);
-            if (e == cudaSuccess) e = launch_weights_to_planar(tmp, h->w, h->B, h->nd, h->H, h->W, h->P, h->st);
+            if (e == cudaSuccess) e = launch_weights_to_pixel_major(tmp, h->w, h->B, h->nd, h->H, h->W, h->st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
             cudaFree(tmp);
             CK(h, e);
         } else {
             CK(h, cudaMemcpyAsync(h->staging, w_or_feats, nw * sizeof(float), cudaMemcpyHostToDevice, h->st));
-            CK(h, launch_weights_to_planar(h->staging, h->w, h->B, h->nd, h->H, h->W, h->P, h->st));
+            CK(h, launch_weights_to_pixel_major(h->staging, h->w, h->B, h->nd, h->H, h->W, h->st));
             CK(h, cudaStreamSynchronize(h->st));
         }
     } else {
-        CK(h, launch_weights_to_planar(src, h->w, h->B, h->nd, h->H, h->W, h->P, h->st));
+        CK(h, launch_weights_to_pixel_major(src, h->w, h->B, h->nd, h->H, h->W, h->st));
+        CK(h, cudaStreamSynchronize(h->st));   // the pair table above is pageable host memory
     }
     h->launches++;
     h->mu = m;
@@ -368,7 +400,7 @@ crf_status crf_set_state(crf_t h, const float *logq, int is_device) {
         CK(h, cudaMemcpyAsync(h->staging, logq, n_rows(h) * sizeof(float), cudaMemcpyHostToDevice, h->st));
         src = h->staging;
     }
-    CK(h, launch_rows_to_planar(src, h->s[h->cur], h->B, h->L, h->H, h->W, h->P, h->st));
+    CK(h, launch_rows_to_padded(src, h->s[h->cur], (long long)n_pix(h), h->L, h->LP, kPadLogQ, h->st));
     h->launches++;
     h->fcur_valid = false;
     if (!is_device) CK(h, cudaStreamSynchronize(h->st));
@@ -392,7 +424,7 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
         eta = h->eta_auto;
     }
     if (p->reset) {
-        CK(h, launch_init_logq(h->U, h->s[h->cur], h->B, h->L, h->H, h->W, h->P, h->st));
+        CK(h, launch_init_logq(h->U, h->s[h->cur], (long long)n_pix(h), h->L, h->LP, h->st));
         h->launches++;
     }
     rc = ensure_trace(h, p->max_iters);
@@ -461,7 +493,7 @@ static crf_status export_state(crf_t h, float *dst, int is_device, int mode) {
     if (rc != CRF_OK) return rc;
     if (!dst) return CRF_E_INVALID;
     float *out = is_device ? dst : h->staging;
-    CK(h, launch_planar_to_rows(h->s[h->cur], out, h->B, h->L, h->H, h->W, h->P, mode, h->st));
+    CK(h, launch_padded_to_rows(h->s[h->cur], out, (long long)n_pix(h), h->L, h->LP, mode, h->st));
     h->launches++;
     if (!is_device) {
         CK(h, cudaMemcpyAsync(dst, h->staging, n_rows(h) * sizeof(float), cudaMemcpyDeviceToHost, h->st));

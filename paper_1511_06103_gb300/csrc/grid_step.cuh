@@ -11,39 +11,51 @@
 // The identity in a5 holds because E is quadratic: the pairwise energy is
 // half of sum_i q_i . m_i, each edge being seen from both ends.
 //
-// Layout: label-planar [B][L][H][P] FP32, so a warp (32 consecutive x of one
-// row) reads one 128-byte line per label.  Each CTA stages exp(log q) of a
-// (GY+2) x (GX+2) tile (one-pixel halo) and the weights it needs into shared
-// memory; mu lives in the kernel's parameter space (constant bank), so the
-// L x L product issues no loads.  Free-energy partials are reduced per tile in
-// FP64 and finished by the last tile of each instance in a fixed order, so F
-// does not depend on scheduling or on the other instances of the batch.
+// Layout and work split (GB300):
+//  - HBM: pixel-major [B][N][LP] FP32, labels innermost and padded to LP (a
+//    multiple of 4, or 2), so a pixel's state or unaries come in LP/4 128-bit
+//    loads with immediate offsets and a warp covers one contiguous span;
+//    weights [B][N][n_dirs] come in one vector load plus the entering edges.
+//  - One thread per pixel, CTA tile of 32 x 8 pixels.  q = exp(log q) of the
+//    tile plus a one-pixel halo (one halo pixel per thread) is staged in
+//    shared memory with a per-pixel stride == 4 (mod 8) floats, so neighbour
+//    reads are conflict-free 128-bit loads.
+//  - mu is staged in shared memory as column pairs and read with broadcast
+//    128-bit loads (keeping it in the parameter space, read through uniform
+//    registers, is faster to run but makes ptxas take minutes per label
+//    count); the L x L product, the neighbour sums and the element-wise update
+//    use packed f32x2 FMAs (one instruction per two labels), with ceil(L/2)
+//    independent accumulators.
+//  - Free-energy partials are reduced per tile in FP64 and finished by the
+//    last tile of each instance in a fixed order, so F does not depend on
+//    scheduling or on the other instances of the batch.
 #pragma once
 
 #include <cmath>
 
+#include "f32x2.cuh"
 #include "internal.h"
 
 namespace proxmf {
 
-template <int LP>
 struct GridStepArgs {
     const float *s_in;
     float *s_out;
     const float *U;
     const float *w;
     const float *eta;
+    const float2 *mu_out;    // device [LT][NPP] column pairs
+    const float2 *mu_in;     // device [LT][NPP] row pairs
     double *partial;
     unsigned int *counter;
     double *f_trace;
     double *f_cur;
     int *done;
     int *status;
-    int L, H, W, P;
+    int L, H, W;
     int nbx, nblk;
     int t, trace_cap, update;
     double rel_tol;
-    float mu[LP * LP];       // row-major, zero padded to LP x LP
 };
 
 __device__ __forceinline__ double warp_sum_f64(double v) {
@@ -52,13 +64,99 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
     return v;
 }
 
-template <int LP, int CONN, bool SYM>
-__global__ void __launch_bounds__(GT, (LP >= 24 || !SYM) ? 1 : 2)
-grid_prox_step_kernel(const __grid_constant__ GridStepArgs<LP> a) {
+// Shared-memory pixel stride: >= LP floats and == 4 (mod 8), so that eight
+// threads reading 16 bytes each at consecutive pixels hit disjoint banks
+// (LP = 2 uses 8-byte accesses and a dense stride).
+__host__ __device__ constexpr int tile_stride(int LP) { return LP == 2 ? 2 : LP + ((4 - LP % 8) + 8) % 8; }
+
+// Load LP floats of one pixel from HBM as float2 pairs.
+template <int LP>
+__device__ __forceinline__ void load_px(float2 (&v)[LP / 2], const float *p) {
+    if constexpr (LP == 2) {
+        v[0] = __ldg(reinterpret_cast<const float2 *>(p));
+    } else {
+#pragma unroll
+        for (int i = 0; i < LP / 4; ++i) {
+            const float4 t = __ldg(reinterpret_cast<const float4 *>(p) + i);
+            v[2 * i] = make_float2(t.x, t.y);
+            v[2 * i + 1] = make_float2(t.z, t.w);
+        }
+    }
+}
+
+template <int LP>
+__device__ __forceinline__ void store_px(float *p, const float2 (&v)[LP / 2]) {
+    if constexpr (LP == 2) {
+        *reinterpret_cast<float2 *>(p) = v[0];
+    } else {
+#pragma unroll
+        for (int i = 0; i < LP / 4; ++i)
+            reinterpret_cast<float4 *>(p)[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+    }
+}
+
+// Write q = exp(s) of one pixel into its tile cell.
+template <int LP>
+__device__ __forceinline__ void put_cell(float *c, const float2 (&s)[LP / 2]) {
+    if constexpr (LP == 2) {
+        *reinterpret_cast<float2 *>(c) = make_float2(__expf(s[0].x), __expf(s[0].y));
+    } else {
+#pragma unroll
+        for (int i = 0; i < LP / 4; ++i)
+            reinterpret_cast<float4 *>(c)[i] = make_float4(__expf(s[2 * i].x), __expf(s[2 * i].y),
+                                                           __expf(s[2 * i + 1].x), __expf(s[2 * i + 1].y));
+    }
+}
+
+// acc += w * q(cell) over the first NP label pairs of a staged pixel.
+template <int NP>
+__device__ __forceinline__ void acc_cell(float2 (&acc)[NP], const float *c, float w) {
+    const float2 ww = splat2(w);
+    if constexpr (NP == 1) {
+        acc[0] = fma2(ww, *reinterpret_cast<const float2 *>(c), acc[0]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < (NP + 1) / 2; ++i) {
+            const float4 t = reinterpret_cast<const float4 *>(c)[i];
+            acc[2 * i] = fma2(ww, make_float2(t.x, t.y), acc[2 * i]);
+            if (2 * i + 1 < NP) acc[2 * i + 1] = fma2(ww, make_float2(t.z, t.w), acc[2 * i + 1]);
+        }
+    }
+}
+
+// m += A S with A given as shared-memory pair columns: for every k,
+// (m[2j], m[2j+1]) += A[k][j] * S_k, two pairs per broadcast 128-bit load.
+template <int LT, int NP, int NPP>
+__device__ __forceinline__ void pair_matvec(float2 (&m)[NP], const float2 *A, const float2 (&S)[NP]) {
+#pragma unroll
+    for (int k = 0; k < LT; ++k) {
+        const float sk = (k & 1) ? S[k >> 1].y : S[k >> 1].x;
+        const float2 ss = splat2(sk);
+        const float4 *col = reinterpret_cast<const float4 *>(A + k * NPP);
+#pragma unroll
+        for (int i = 0; i < (NP + 1) / 2; ++i) {
+            const float4 t = col[i];
+            m[2 * i] = fma2(make_float2(t.x, t.y), ss, m[2 * i]);
+            if (2 * i + 1 < NP) m[2 * i + 1] = fma2(make_float2(t.z, t.w), ss, m[2 * i + 1]);
+        }
+    }
+}
+
+template <int LT, int CONN, bool SYM>
+__global__ void __launch_bounds__(GT, (LT >= 24) ? 1 : 2)
+grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
+    constexpr int LP = storage_labels(LT);           // floats per pixel in HBM
+    constexpr int NP = (LT + 1) / 2;                 // label pairs in the arithmetic
+    constexpr int NPP = (NP + 1) / 2 * 2;            // pair slots per mu column
     constexpr int ND = CONN == 8 ? 4 : 2;
-    constexpr int HALO = 2 * (GX + 2) + 2 * GY;
-    __shared__ float qs[LP][GY + 2][GX + 2];
-    __shared__ float ws[ND][GY + 1][GX + 2];
+    constexpr int LS = tile_stride(LP);
+    constexpr int TW = GX + 2;                       // tile width with halo
+    constexpr int HALO = 2 * TW + 2 * GY;            // halo pixels of a tile
+    constexpr bool MASK = (LT == LP);                // runtime L may be < LT
+    static_assert(HALO <= GT, "one halo pixel per thread");
+    static_assert(2 * NP <= LP, "pairs fit in the stored labels");
+    __shared__ __align__(16) float qt[(GY + 2) * TW * LS];
+    __shared__ __align__(16) float2 mus[SYM ? 1 : 2][LT * NPP];
     __shared__ double red[GT / 32];
     __shared__ int is_last;
 
@@ -66,138 +164,186 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs<LP> a) {
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * GX + tx;
     const int x0 = blockIdx.x * GX, y0 = blockIdx.y * GY;
     const int x = x0 + tx, y = y0 + ty;
-    const int H = a.H, W = a.W, P = a.P, L = a.L;
+    const int H = a.H, W = a.W, L = a.L;
     const bool inside = (x < W) && (y < H);
-    const size_t plane = (size_t)H * P;
-    const float *sin = a.s_in + (size_t)b * L * plane;
-    const float *Ub = a.U + (size_t)b * L * plane;
-    const float *wb = a.w + (size_t)b * ND * plane;
-    const size_t pix = (size_t)y * P + x;
+    const size_t N = (size_t)H * W;
+    const size_t p = (size_t)y * W + x;
+    const float *sin = a.s_in + (size_t)b * N * LP;
 
     if (a.done != nullptr && a.done[b] != 0) {
         // This instance has met its stopping rule: carry the state through
         // unchanged so that the ping-pong parity stays the same for all.
-        if (a.update && inside)
-            for (int l = 0; l < L; ++l) a.s_out[(size_t)b * L * plane + l * plane + pix] = sin[l * plane + pix];
+        if (a.update && inside) {
+            float2 v[LP / 2];
+            load_px<LP>(v, sin + p * LP);
+            store_px<LP>(a.s_out + ((size_t)b * N + p) * LP, v);
+        }
         return;
     }
 
-    // own state and unaries: coalesced, all loads issued before first use
-    float s[LP], u[LP];
-#pragma unroll
-    for (int l = 0; l < LP; ++l) {
-        if (l < L && inside) {
-            s[l] = __ldg(sin + l * plane + pix);
-            u[l] = __ldg(Ub + l * plane + pix);
-        } else {
-            s[l] = -1e30f;
-            u[l] = 0.f;
-        }
+
+    // mu pairs into shared memory
+    for (int i = tid; i < LT * NPP; i += GT) {
+        mus[0][i] = a.mu_out[i];
+        if (!SYM) mus[SYM ? 0 : 1][i] = a.mu_in[i];
     }
 
-    // halo of q = exp(log q); cells outside the image hold 0
-    for (int idx = tid; idx < HALO * L; idx += GT) {
-        const int l = idx / HALO;
-        const int h = idx - l * HALO;
-        int hy, hx;
-        if (h < GX + 2) {
-            hy = 0;
-            hx = h;
-        } else if (h < 2 * (GX + 2)) {
-            hy = GY + 1;
-            hx = h - (GX + 2);
-        } else {
-            const int k = h - 2 * (GX + 2);
-            hy = 1 + (k >> 1);
-            hx = (k & 1) ? GX + 1 : 0;
-        }
-        const int gy = y0 - 1 + hy, gx = x0 - 1 + hx;
-        float v = 0.f;
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = expf(__ldg(sin + l * plane + (size_t)gy * P + gx));
-        qs[l][hy][hx] = v;
-    }
-    // weights of the edges leaving and entering this tile's pixels
-    for (int idx = tid; idx < ND * (GY + 1) * (GX + 2); idx += GT) {
-        const int k = idx / ((GY + 1) * (GX + 2));
-        const int r = idx - k * ((GY + 1) * (GX + 2));
-        const int hy = r / (GX + 2), hx = r - hy * (GX + 2);
-        const int gy = y0 - 1 + hy, gx = x0 - 1 + hx;
-        float v = 0.f;
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = __ldg(wb + k * plane + (size_t)gy * P + gx);
-        ws[k][hy][hx] = v;
-    }
+    // own log q
+    float2 s[LP / 2];
+    if (inside) {
+        load_px<LP>(s, sin + p * LP);
+    } else {
 #pragma unroll
-    for (int l = 0; l < LP; ++l) qs[l][ty + 1][tx + 1] = (l < L && inside) ? expf(s[l]) : 0.f;
+        for (int i = 0; i < LP / 2; ++i) s[i] = splat2(kPadLogQ);
+    }
+
+    // one halo pixel per thread for the first HALO threads; 0 off the image
+    if (tid < HALO) {
+        int hr, hc;
+        if (tid < TW) {
+            hr = 0;
+            hc = tid;
+        } else if (tid < 2 * TW) {
+            hr = GY + 1;
+            hc = tid - TW;
+        } else {
+            const int k = tid - 2 * TW;
+            hr = 1 + (k >> 1);
+            hc = (k & 1) ? TW - 1 : 0;
+        }
+        const int gy = y0 - 1 + hr, gx = x0 - 1 + hc;
+        float2 h[LP / 2];
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+            load_px<LP>(h, sin + ((size_t)gy * W + gx) * LP);
+        } else {
+#pragma unroll
+            for (int i = 0; i < LP / 2; ++i) h[i] = splat2(kPadLogQ);
+        }
+        put_cell<LP>(qt + (hr * TW + hc) * LS, h);
+    }
+    put_cell<LP>(qt + ((ty + 1) * TW + tx + 1) * LS, s);
+
+    // edge weights leaving this pixel, and entering it (stored at the pixel
+    // that owns the edge)
+    float wo[4] = {0.f, 0.f, 0.f, 0.f}, wi[4] = {0.f, 0.f, 0.f, 0.f};
+    if (inside) {
+        const float *wb = a.w + (size_t)b * N * ND;
+        if (ND == 4) {
+            const float4 t = __ldg(reinterpret_cast<const float4 *>(wb + p * ND));
+            wo[0] = t.x;
+            wo[1] = t.y;
+            wo[2] = t.z;
+            wo[3] = t.w;
+        } else {
+            const float2 t = __ldg(reinterpret_cast<const float2 *>(wb + p * ND));
+            wo[0] = t.x;
+            wo[1] = t.y;
+        }
+        if (x > 0) wi[0] = __ldg(wb + (p - 1) * ND + 0);
+        if (y > 0) wi[1] = __ldg(wb + (p - W) * ND + 1);
+        if (CONN == 8) {
+            if (x > 0 && y > 0) wi[2] = __ldg(wb + (p - W - 1) * ND + 2);
+            if (x + 1 < W && y > 0) wi[3] = __ldg(wb + (p - W + 1) * ND + 3);
+        }
+    }
     __syncthreads();
 
-    // a1: weighted neighbour sums (out-going edges S, in-coming edges T)
-    const float w_r = ws[0][ty + 1][tx + 1], w_d = ws[1][ty + 1][tx + 1];
-    const float w_l = ws[0][ty + 1][tx], w_u = ws[1][ty][tx + 1];
-    float w_dr = 0.f, w_dl = 0.f, w_ul = 0.f, w_ur = 0.f;
-    if (CONN == 8) {
-        w_dr = ws[2][ty + 1][tx + 1];
-        w_dl = ws[3][ty + 1][tx + 1];
-        w_ul = ws[2][ty][tx];
-        w_ur = ws[3][ty][tx + 2];
-    }
-    float So[LP];
-    float Si[SYM ? 1 : LP];
+    // unaries: issued now, consumed after the L x L product
+    float2 u[LP / 2];
+    if (inside) {
+        load_px<LP>(u, a.U + ((size_t)b * N + p) * LP);
+    } else {
 #pragma unroll
-    for (int l = 0; l < LP; ++l) {
-        float o = w_r * qs[l][ty + 1][tx + 2];
-        o = fmaf(w_d, qs[l][ty + 2][tx + 1], o);
-        float i = w_l * qs[l][ty + 1][tx];
-        i = fmaf(w_u, qs[l][ty][tx + 1], i);
-        if (CONN == 8) {
-            o = fmaf(w_dr, qs[l][ty + 2][tx + 2], o);
-            o = fmaf(w_dl, qs[l][ty + 2][tx], o);
-            i = fmaf(w_ul, qs[l][ty][tx], i);
-            i = fmaf(w_ur, qs[l][ty][tx + 2], i);
-        }
-        if (SYM) {
-            So[l] = o + i;
-        } else {
-            So[l] = o;
-            Si[SYM ? 0 : l] = i;
-        }
+        for (int i = 0; i < LP / 2; ++i) u[i] = splat2(0.f);
     }
 
-    // a2-a3 and the free-energy term of this pixel
+    const float *c_r = qt + ((ty + 1) * TW + tx + 2) * LS;
+    const float *c_d = qt + ((ty + 2) * TW + tx + 1) * LS;
+    const float *c_dr = qt + ((ty + 2) * TW + tx + 2) * LS;
+    const float *c_dl = qt + ((ty + 2) * TW + tx) * LS;
+    const float *c_l = qt + ((ty + 1) * TW + tx) * LS;
+    const float *c_u = qt + (ty * TW + tx + 1) * LS;
+    const float *c_ul = qt + (ty * TW + tx) * LS;
+    const float *c_ur = qt + (ty * TW + tx + 2) * LS;
+
+    // a1: neighbour sums and the L x L product, m = mu S_out + mu^T S_in
+    float2 m[NP], S[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        m[j] = splat2(0.f);
+        S[j] = splat2(0.f);
+    }
+    acc_cell<NP>(S, c_r, wo[0]);
+    acc_cell<NP>(S, c_d, wo[1]);
+    if (CONN == 8) {
+        acc_cell<NP>(S, c_dr, wo[2]);
+        acc_cell<NP>(S, c_dl, wo[3]);
+    }
+    if (SYM) {
+        acc_cell<NP>(S, c_l, wi[0]);
+        acc_cell<NP>(S, c_u, wi[1]);
+        if (CONN == 8) {
+            acc_cell<NP>(S, c_ul, wi[2]);
+            acc_cell<NP>(S, c_ur, wi[3]);
+        }
+    }
+    pair_matvec<LT, NP, NPP>(m, mus[0], S);
+    if (!SYM) {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) S[j] = splat2(0.f);
+        acc_cell<NP>(S, c_l, wi[0]);
+        acc_cell<NP>(S, c_u, wi[1]);
+        if (CONN == 8) {
+            acc_cell<NP>(S, c_ul, wi[2]);
+            acc_cell<NP>(S, c_ur, wi[3]);
+        }
+        pair_matvec<LT, NP, NPP>(m, mus[SYM ? 0 : 1], S);
+    }
+
+    // a2-a3 and this pixel's free-energy term (q read back from the tile)
+    float2 qc[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) qc[j] = splat2(0.f);
+    acc_cell<NP>(qc, qt + ((ty + 1) * TW + tx + 1) * LS, 1.f);
     const float eta = a.eta[b];
-    const float ome = 1.f - eta;
-    float f = 0.f;
+    const float2 neta = splat2(-eta), ome = splat2(1.f - eta), half = splat2(0.5f);
+    float2 f2 = splat2(0.f);
     float mx = -INFINITY;
 #pragma unroll
-    for (int l = 0; l < LP; ++l) {
-        float m = 0.f;
-#pragma unroll
-        for (int k = 0; k < LP; ++k) {
-            m = fmaf(a.mu[l * LP + k], So[k], m);
-            if (!SYM) m = fmaf(a.mu[k * LP + l], Si[SYM ? 0 : k], m);
-        }
-        const float g = u[l] + m;
-        const float ql = qs[l][ty + 1][tx + 1];
-        if (l < L) f = fmaf(ql, u[l] + 0.5f * m + s[l], f);
-        float av = fmaf(-eta, g, ome * s[l]);
-        if (l >= L) av = -INFINITY;
-        s[l] = av;
-        mx = fmaxf(mx, av);
+    for (int j = 0; j < NP; ++j) {
+        const float2 g = add2(u[j], m[j]);
+        const float2 h = add2(fma2(half, m[j], u[j]), s[j]);
+        f2 = fma2(qc[j], h, f2);
+        float2 av = fma2(neta, g, mul2(ome, s[j]));
+        const int l0 = 2 * j, l1 = 2 * j + 1;
+        if ((MASK && l0 >= L)) av.x = -INFINITY;
+        if ((MASK && l1 >= L) || l1 >= LT) av.y = -INFINITY;
+        s[j] = av;
+        mx = fmaxf(mx, fmaxf(av.x, av.y));
     }
-    // a4: renormalise (log-sum-exp over labels held by this thread)
+    // a4: renormalise
     float z = 0.f;
 #pragma unroll
-    for (int l = 0; l < LP; ++l)
-        if (l < L) z += expf(s[l] - mx);
-    const float lse = mx + logf(z);
+    for (int j = 0; j < NP; ++j) z += __expf(s[j].x - mx) + __expf(s[j].y - mx);
+    const float2 nlse = splat2(-(mx + __logf(z)));
     if (a.update && inside) {
-        float *so = a.s_out + (size_t)b * L * plane;
+        float2 o[LP / 2];
 #pragma unroll
-        for (int l = 0; l < LP; ++l)
-            if (l < L) so[l * plane + pix] = s[l] - lse;
+        for (int j = 0; j < LP / 2; ++j) {
+            if (j < NP) {
+                o[j] = add2(s[j], nlse);
+                const int l0 = 2 * j, l1 = 2 * j + 1;
+                if ((MASK && l0 >= L)) o[j].x = kPadLogQ;
+                if ((MASK && l1 >= L) || l1 >= LT) o[j].y = kPadLogQ;
+            } else {
+                o[j] = splat2(kPadLogQ);
+            }
+        }
+        store_px<LP>(a.s_out + ((size_t)b * N + p) * LP, o);
     }
 
     // a5: F partial of this tile, FP64
-    double fd = inside ? (double)f : 0.0;
+    double fd = inside ? (double)(f2.x + f2.y) : 0.0;
     fd = warp_sum_f64(fd);
     if ((tid & 31) == 0) red[tid >> 5] = fd;
     __syncthreads();
@@ -238,9 +384,11 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs<LP> a) {
     }
 }
 
-template <int LP>
-cudaError_t launch_grid_step_bucket(const GridStepLaunch &l, cudaStream_t st) {
-    GridStepArgs<LP> a;
+template <int LT>
+cudaError_t launch_grid_step_lt(const GridStepLaunch &l, cudaStream_t st) {
+    GridStepArgs a;
+    a.mu_out = l.mu_out;
+    a.mu_in = l.mu_in;
     a.s_in = l.s_in;
     a.s_out = l.s_out;
     a.U = l.U;
@@ -255,7 +403,6 @@ cudaError_t launch_grid_step_bucket(const GridStepLaunch &l, cudaStream_t st) {
     a.L = l.L;
     a.H = l.H;
     a.W = l.W;
-    a.P = l.P;
     int nbx, nby;
     grid_tiles(l.H, l.W, &nbx, &nby);
     a.nbx = nbx;
@@ -264,20 +411,17 @@ cudaError_t launch_grid_step_bucket(const GridStepLaunch &l, cudaStream_t st) {
     a.trace_cap = l.trace_cap;
     a.update = l.update;
     a.rel_tol = l.rel_tol;
-    for (int i = 0; i < LP * LP; ++i) a.mu[i] = 0.f;
-    for (int i = 0; i < l.L; ++i)
-        for (int k = 0; k < l.L; ++k) a.mu[i * LP + k] = l.mu_host[i * l.L + k];
     dim3 grid(nbx, nby, l.B), block(GX, GY, 1);
     if (l.conn == 8) {
         if (l.mu_sym)
-            grid_prox_step_kernel<LP, 8, true><<<grid, block, 0, st>>>(a);
+            grid_prox_step_kernel<LT, 8, true><<<grid, block, 0, st>>>(a);
         else
-            grid_prox_step_kernel<LP, 8, false><<<grid, block, 0, st>>>(a);
+            grid_prox_step_kernel<LT, 8, false><<<grid, block, 0, st>>>(a);
     } else {
         if (l.mu_sym)
-            grid_prox_step_kernel<LP, 4, true><<<grid, block, 0, st>>>(a);
+            grid_prox_step_kernel<LT, 4, true><<<grid, block, 0, st>>>(a);
         else
-            grid_prox_step_kernel<LP, 4, false><<<grid, block, 0, st>>>(a);
+            grid_prox_step_kernel<LT, 4, false><<<grid, block, 0, st>>>(a);
     }
     return cudaGetLastError();
 }

@@ -1,10 +1,10 @@
-// Instantiation of the grid step for label counts up to 16 (see grid_step.cuh).
+// Instantiation of the grid step for kernel label count 16 (see grid_step.cuh).
 #include "grid_step.cuh"
 
 namespace proxmf {
 
 cudaError_t launch_grid_step_l16(const GridStepLaunch &a, cudaStream_t st) {
-    return launch_grid_step_bucket<16>(a, st);
+    return launch_grid_step_lt<16>(a, st);
 }
 
 }  // namespace proxmf

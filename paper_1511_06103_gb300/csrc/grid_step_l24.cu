@@ -1,0 +1,10 @@
+// Instantiation of the grid step for kernel label count 24 (see grid_step.cuh).
+#include "grid_step.cuh"
+
+namespace proxmf {
+
+cudaError_t launch_grid_step_l24(const GridStepLaunch &a, cudaStream_t st) {
+    return launch_grid_step_lt<24>(a, st);
+}
+
+}  // namespace proxmf

@@ -15,26 +15,44 @@ constexpr int GX = 32;
 constexpr int GY = 8;
 constexpr int GT = GX * GY;
 
-// Everything one launch of the grid step needs, in a layout-agnostic form.
-// State, unaries and weights are label-planar: element (b, l, y, x) lives at
-// ((b * L + l) * H + y) * P + x (weights: (b * n_dirs + k) instead of l).
+// Labels stored per pixel in HBM: L rounded up to a multiple of 4 (2 when
+// L <= 2), so that one pixel is a whole number of 16-byte vectors.
+// Padding labels hold log q = kPadLogQ (q = 0) and U = 0.
+__host__ __device__ constexpr int storage_labels(int L) { return L <= 2 ? 2 : (L + 3) / 4 * 4; }
+constexpr float kPadLogQ = -1e30f;
+
+// Label count a step kernel is compiled for, given the runtime L: the exact
+// count for the segmentation workload's 21, else the storage count (the
+// kernel then masks labels >= L).
+inline int kernel_labels(int L) { return L == 21 ? 21 : storage_labels(L); }
+
+// Pairs of mu used by the step kernel for a kernel label count LT:
+// NPP = pair slots per row (ceil(LT/2) rounded up to even);
+// out[k*NPP + j] = (mu[2j][k], mu[2j+1][k]), in[k*NPP + j] = (mu[k][2j], mu[k][2j+1]),
+// zero outside the L x L matrix.
+inline int mu_pair_slots(int LT) { return ((LT + 1) / 2 + 1) / 2 * 2; }
+
+// Everything one launch of the grid step needs.  State and unaries are
+// pixel-major [B][N][storage_labels(L)], N = H*W, pixel p = y*W + x; edge
+// weights are [B][N][n_dirs] with zero on edges that leave the image.
 struct GridStepLaunch {
     const float *s_in;       // log q^t
     float *s_out;            // log q^{t+1}
     const float *U;          // unary costs
-    const float *w;          // edge weights, zero on edges that leave the image
+    const float *w;          // edge weights
     const float *eta;        // [B] step per instance
+    const float2 *mu_out;    // device [LT][NPP] column pairs (see mu_pair_slots)
+    const float2 *mu_in;     // device [LT][NPP] row pairs
     double *partial;         // [B][nblk] per-tile free-energy partials (scratch)
     unsigned int *counter;   // [B] tiles finished in this launch (scratch, self-resetting)
     double *f_trace;         // [B][trace_cap]
     double *f_cur;           // [B] F of the state read by this launch
     int *done;               // [B] 0 = running, k = stopped after k steps (may be null)
     int *status;             // device error word
-    int B, L, H, W, P, conn;
+    int B, L, H, W, conn;
     int t, trace_cap, update;
     double rel_tol;
     bool mu_sym;
-    const float *mu_host;    // [L][L] row-major host copy
 };
 
 // Number of tiles per instance.
@@ -44,34 +62,38 @@ inline void grid_tiles(int H, int W, int *nbx, int *nby) {
 }
 
 // Per-label-bucket launchers (one translation unit each).
+// Per-label-count launchers (grid_step_l*.cu), dispatched by launch_grid_step.
 cudaError_t launch_grid_step_l2(const GridStepLaunch &a, cudaStream_t st);
 cudaError_t launch_grid_step_l4(const GridStepLaunch &a, cudaStream_t st);
 cudaError_t launch_grid_step_l8(const GridStepLaunch &a, cudaStream_t st);
+cudaError_t launch_grid_step_l12(const GridStepLaunch &a, cudaStream_t st);
 cudaError_t launch_grid_step_l16(const GridStepLaunch &a, cudaStream_t st);
+cudaError_t launch_grid_step_l20(const GridStepLaunch &a, cudaStream_t st);
 cudaError_t launch_grid_step_l21(const GridStepLaunch &a, cudaStream_t st);
+cudaError_t launch_grid_step_l24(const GridStepLaunch &a, cudaStream_t st);
+cudaError_t launch_grid_step_l28(const GridStepLaunch &a, cudaStream_t st);
 cudaError_t launch_grid_step_l32(const GridStepLaunch &a, cudaStream_t st);
 cudaError_t launch_grid_step(const GridStepLaunch &a, cudaStream_t st);
 
 // Layout conversion and initialisation (layout.cu).
-// rows [B][N][L] <-> planar [B][L][H][P]; mode selects the element transform.
+// rows [B][N][L] <-> padded [B][N][LP]; pad fills the padding labels.
 enum ConvMode { CONV_COPY = 0, CONV_EXP = 1 };
-cudaError_t launch_rows_to_planar(const float *src, float *dst, int B, int L, int H, int W, int P,
+cudaError_t launch_rows_to_padded(const float *src, float *dst, long long rows, int L, int LP, float pad,
                                   cudaStream_t st);
-cudaError_t launch_planar_to_rows(const float *src, float *dst, int B, int L, int H, int W, int P,
-                                  int mode, cudaStream_t st);
-// [B][nd][H][W] -> [B][nd][H][P], zeroing entries whose edge leaves the image.
-cudaError_t launch_weights_to_planar(const float *src, float *dst, int B, int nd, int H, int W,
-                                     int P, cudaStream_t st);
-// s = log softmax(-U) per variable (planar).
-cudaError_t launch_init_logq(const float *U, float *s, int B, int L, int H, int W, int P,
-                             cudaStream_t st);
+cudaError_t launch_padded_to_rows(const float *src, float *dst, long long rows, int L, int LP, int mode,
+                                  cudaStream_t st);
+// [B][nd][H][W] -> [B][H*W][nd], zeroing entries whose edge leaves the image.
+cudaError_t launch_weights_to_pixel_major(const float *src, float *dst, int B, int nd, int H, int W,
+                                          cudaStream_t st);
+// s = log softmax(-U) per variable (padded layout; padding labels get kPadLogQ).
+cudaError_t launch_init_logq(const float *U, float *s, long long rows, int L, int LP, cudaStream_t st);
 // eta[b] = value for all b.
 cudaError_t launch_fill_eta(float *eta, int B, double value, cudaStream_t st);
 
 // Step-size constant (lanczos.cu).  Fills Lambda[b] (device, FP64) and
 // eta[b] = 1/(1+max(Lambda,0)) (device, FP32).  Returns CRF status codes.
 struct LipschitzJob {
-    const float *w;          // planar weights
+    const float *w;          // pixel-major weights [B][N][n_dirs]
     const float *mu_host;    // [L][L]
     bool mu_sym;
     int B, L, H, W, P, conn;

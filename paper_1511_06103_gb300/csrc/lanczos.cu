@@ -135,7 +135,7 @@ lz_matvec_kernel(const double *__restrict__ v, double *__restrict__ out, const f
     if (p < g.H * g.W) {
         const int y = p / g.W, x = p - y * g.W;
         const double *vb = v + (size_t)b * g.Lv * plane;
-        const float *wb = w + (size_t)b * nd * plane;
+        const float *wb = w + (size_t)b * g.H * g.W * nd;   // pixel-major [N][nd]
         const size_t pix = (size_t)y * g.P + x;
         double So[kMaxLabels], Si[kMaxLabels];
         for (int l = 0; l < g.Lv; ++l) So[l] = Si[l] = 0.0;
@@ -144,14 +144,14 @@ lz_matvec_kernel(const double *__restrict__ v, double *__restrict__ out, const f
             dir_off(d, &dy, &dx);
             const int yo = y + dy, xo = x + dx;           // out-going edge to (yo, xo)
             if (yo >= 0 && yo < g.H && xo >= 0 && xo < g.W) {
-                const double wo = (double)wb[d * plane + pix];
+                const double wo = (double)wb[((size_t)y * g.W + x) * nd + d];
                 const size_t po = (size_t)yo * g.P + xo;
                 for (int l = 0; l < g.Lv; ++l) So[l] += wo * vb[l * plane + po];
             }
             const int yi = y - dy, xi = x - dx;           // in-coming edge from (yi, xi)
             if (yi >= 0 && yi < g.H && xi >= 0 && xi < g.W) {
                 const size_t pi = (size_t)yi * g.P + xi;
-                const double wi = (double)wb[d * plane + pi];
+                const double wi = (double)wb[((size_t)yi * g.W + xi) * nd + d];
                 for (int l = 0; l < g.Lv; ++l) Si[l] += wi * vb[l * plane + pi];
             }
         }
@@ -285,58 +285,90 @@ __global__ void lz_ritz_kernel(const double *alpha, const double *beta, int ld, 
     }
 }
 
-// Eigenvalues of C mu C (L x L, symmetric part) by cyclic Jacobi; one thread.
+// Extreme eigenvalues of C mu C (L x L, symmetric part) by cyclic Jacobi.
+// One warp: lane 0 computes each rotation, all lanes apply it to the rows and
+// columns of the matrix held in shared memory.
 __global__ void mu_tilde_extremes_kernel(const float *mu, int L, double *nu) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double A[kMaxLabels * kMaxLabels];
-    double rm[kMaxLabels], cm[kMaxLabels], tm = 0.0;
-    for (int i = 0; i < L; ++i) {
-        rm[i] = cm[i] = 0.0;
-    }
-    for (int i = 0; i < L; ++i)
+    __shared__ double A[kMaxLabels * kMaxLabels];
+    __shared__ double rm[kMaxLabels], cm[kMaxLabels];
+    __shared__ double cs_sn[2];
+    __shared__ int stop_flag;
+    const int lane = threadIdx.x;
+    if (lane < L) {
+        double r = 0.0, c = 0.0;
         for (int j = 0; j < L; ++j) {
-            const double v = 0.5 * ((double)mu[i * L + j] + (double)mu[j * L + i]);
-            rm[i] += v / L;
-            cm[j] += v / L;
-            tm += v / ((double)L * L);
+            r += 0.5 * ((double)mu[lane * L + j] + (double)mu[j * L + lane]) / L;
+            c += 0.5 * ((double)mu[j * L + lane] + (double)mu[lane * L + j]) / L;
         }
+        rm[lane] = r;
+        cm[lane] = c;
+    }
+    __syncwarp();
+    double tm = 0.0;
+    for (int j = 0; j < L; ++j) tm += rm[j] / L;
     for (int i = 0; i < L; ++i)
-        for (int j = 0; j < L; ++j)
-            A[i * L + j] = 0.5 * ((double)mu[i * L + j] + (double)mu[j * L + i]) - rm[i] - cm[j] + tm;
+        if (lane < L)
+            A[i * L + lane] =
+                0.5 * ((double)mu[i * L + lane] + (double)mu[lane * L + i]) - rm[i] - cm[lane] + tm;
+    __syncwarp();
     for (int sweep = 0; sweep < 60; ++sweep) {
         double off = 0.0, tot = 0.0;
-        for (int i = 0; i < L; ++i)
+        if (lane < L)
             for (int j = 0; j < L; ++j) {
-                tot += A[i * L + j] * A[i * L + j];
-                if (i != j) off += A[i * L + j] * A[i * L + j];
+                const double v = A[lane * L + j] * A[lane * L + j];
+                tot += v;
+                if (j != lane) off += v;
             }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        }
         if (off <= 1e-32 * (tot > 0 ? tot : 1.0)) break;
         for (int p = 0; p < L; ++p)
             for (int r = p + 1; r < L; ++r) {
-                const double apr = A[p * L + r];
-                if (fabs(apr) < 1e-300) continue;
-                const double theta = (A[r * L + r] - A[p * L + p]) / (2.0 * apr);
-                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
-                for (int k = 0; k < L; ++k) {
-                    const double akp = A[k * L + p], akr = A[k * L + r];
-                    A[k * L + p] = cs * akp - sn * akr;
-                    A[k * L + r] = sn * akp + cs * akr;
+                if (lane == 0) {
+                    const double apr = A[p * L + r];
+                    if (fabs(apr) < 1e-300) {
+                        stop_flag = 1;
+                    } else {
+                        stop_flag = 0;
+                        const double theta = (A[r * L + r] - A[p * L + p]) / (2.0 * apr);
+                        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        const double c = 1.0 / sqrt(t * t + 1.0);
+                        cs_sn[0] = c;
+                        cs_sn[1] = t * c;
+                    }
                 }
-                for (int k = 0; k < L; ++k) {
-                    const double apk = A[p * L + k], ark = A[r * L + k];
-                    A[p * L + k] = cs * apk - sn * ark;
-                    A[r * L + k] = sn * apk + cs * ark;
+                __syncwarp();
+                if (stop_flag) {
+                    __syncwarp();
+                    continue;
                 }
+                const double c = cs_sn[0], sn = cs_sn[1];
+                if (lane < L) {
+                    const double akp = A[lane * L + p], akr = A[lane * L + r];
+                    A[lane * L + p] = c * akp - sn * akr;
+                    A[lane * L + r] = sn * akp + c * akr;
+                }
+                __syncwarp();
+                if (lane < L) {
+                    const double apk = A[p * L + lane], ark = A[r * L + lane];
+                    A[p * L + lane] = c * apk - sn * ark;
+                    A[r * L + lane] = sn * apk + c * ark;
+                }
+                __syncwarp();
             }
     }
-    double lo = INFINITY, hi = -INFINITY;
-    for (int i = 0; i < L; ++i) {
-        lo = fmin(lo, A[i * L + i]);
-        hi = fmax(hi, A[i * L + i]);
+    if (lane == 0) {
+        double lo = INFINITY, hi = -INFINITY;
+        for (int i = 0; i < L; ++i) {
+            lo = fmin(lo, A[i * L + i]);
+            hi = fmax(hi, A[i * L + i]);
+        }
+        nu[0] = lo;
+        nu[1] = hi;
     }
-    nu[0] = lo;
-    nu[1] = hi;
 }
 
 // Lambda_b and eta_b = 1/(1 + max(Lambda_b, 0)).
@@ -485,7 +517,7 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
         }
     }
     if (job.mu_sym) {
-        mu_tilde_extremes_kernel<<<1, 1, 0, st>>>(mu_dev, job.L, nu);
+        mu_tilde_extremes_kernel<<<1, 32, 0, st>>>(mu_dev, job.L, nu);
         LZ_CHECK(cudaGetLastError());
     }
     lz_finalize_kernel<<<(B + 127) / 128, 128, 0, st>>>(rmin, rmax, nu, job.mu_sym ? 1 : 0, B, job.Lambda,

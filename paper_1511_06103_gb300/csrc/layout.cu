@@ -1,6 +1,6 @@
 // layout.cu -- conversions between the external [B][N][L] row layout and the
-// internal label-planar [B][L][H][P] layout, the initial state q^0, and small
-// fills.  None of this runs inside the iteration loop.
+// internal padded pixel-major [B][N][LP] layout, the initial state q^0, and
+// small fills.  None of this runs inside the iteration loop.
 #include <cmath>
 
 #include "internal.h"
@@ -16,35 +16,27 @@ inline int blocks_for(size_t n) {
     return (int)(b > 0x7fffffff ? 0x7fffffff : (b == 0 ? 1 : b));
 }
 
-// One thread per (b, y, x): reads L consecutive values, writes one per plane.
-__global__ void rows_to_planar_kernel(const float *__restrict__ src, float *__restrict__ dst, int B,
-                                      int L, int H, int W, int P) {
-    const size_t n = (size_t)B * H * W;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const size_t b = i / ((size_t)H * W);
-        const size_t p = i - b * H * W;
-        const size_t y = p / W, x = p - y * W;
-        const float *r = src + i * L;
-        float *d = dst + b * L * H * P + y * P + x;
-        for (int l = 0; l < L; ++l) d[(size_t)l * H * P] = r[l];
+// rows [R][L] -> padded rows [R][LP]; one thread per output element.
+__global__ void rows_to_padded_kernel(const float *__restrict__ src, float *__restrict__ dst, long long rows,
+                                      int L, int LP, float pad) {
+    const long long n = rows * LP;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / LP;
+        const int l = (int)(i - r * LP);
+        dst[i] = l < L ? src[r * L + l] : pad;
     }
 }
 
-__global__ void planar_to_rows_kernel(const float *__restrict__ src, float *__restrict__ dst, int B,
-                                      int L, int H, int W, int P, int mode) {
-    const size_t n = (size_t)B * H * W;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const size_t b = i / ((size_t)H * W);
-        const size_t p = i - b * H * W;
-        const size_t y = p / W, x = p - y * W;
-        const float *s = src + b * L * H * P + y * P + x;
-        float *r = dst + i * L;
-        for (int l = 0; l < L; ++l) {
-            const float v = s[(size_t)l * H * P];
-            r[l] = mode == CONV_EXP ? expf(v) : v;
-        }
+__global__ void padded_to_rows_kernel(const float *__restrict__ src, float *__restrict__ dst, long long rows,
+                                      int L, int LP, int mode) {
+    const long long n = rows * L;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / L;
+        const int l = (int)(i - r * L);
+        const float v = src[r * LP + l];
+        dst[i] = mode == CONV_EXP ? expf(v) : v;
     }
 }
 
@@ -54,42 +46,40 @@ __device__ __forceinline__ void dir_offset(int k, int *dy, int *dx) {
     *dx = k == 0 ? 1 : (k == 1 ? 0 : (k == 2 ? 1 : -1));
 }
 
-__global__ void weights_to_planar_kernel(const float *__restrict__ src, float *__restrict__ dst,
-                                         int B, int nd, int H, int W, int P) {
-    const size_t n = (size_t)B * nd * H * P;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const size_t x = i % P;
-        const size_t r = i / P;
-        const size_t y = r % H;
-        const size_t bk = r / H;
-        const int k = (int)(bk % nd);
+// [B][nd][H][W] -> [B][H*W][nd], zero where the edge would leave the image.
+__global__ void weights_to_pixel_major_kernel(const float *__restrict__ src, float *__restrict__ dst, int B,
+                                              int nd, int H, int W) {
+    const long long n = (long long)B * H * W * nd;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i % nd);
+        const long long bp = i / nd;
+        const long long pix = bp % ((long long)H * W);
+        const long long b = bp / ((long long)H * W);
+        const int y = (int)(pix / W), x = (int)(pix % W);
         int dy, dx;
         dir_offset(k, &dy, &dx);
-        const long long yy = (long long)y + dy, xx = (long long)x + dx;
+        const int yy = y + dy, xx = x + dx;
         float v = 0.f;
-        if (x < (size_t)W && yy >= 0 && yy < H && xx >= 0 && xx < W) v = src[(bk * H + y) * W + x];
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = src[((b * nd + k) * H + y) * (long long)W + x];
         dst[i] = v;
     }
 }
 
-// q^0 = softmax(-U): unary-only marginals, written as log q.
-__global__ void init_logq_kernel(const float *__restrict__ U, float *__restrict__ s, int B, int L,
-                                 int H, int W, int P) {
-    const size_t n = (size_t)B * H * W;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const size_t b = i / ((size_t)H * W);
-        const size_t p = i - b * H * W;
-        const size_t y = p / W, x = p - y * W;
-        const size_t base = b * L * H * P + y * P + x;
-        const size_t plane = (size_t)H * P;
+// q^0 = softmax(-U): unary-only marginals, written as log q (padded rows).
+__global__ void init_logq_kernel(const float *__restrict__ U, float *__restrict__ s, long long rows, int L,
+                                 int LP) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows;
+         r += (long long)gridDim.x * blockDim.x) {
+        const float *u = U + r * LP;
+        float *o = s + r * LP;
         float mx = -INFINITY;
-        for (int l = 0; l < L; ++l) mx = fmaxf(mx, -U[base + l * plane]);
+        for (int l = 0; l < L; ++l) mx = fmaxf(mx, -u[l]);
         float z = 0.f;
-        for (int l = 0; l < L; ++l) z += expf(-U[base + l * plane] - mx);
+        for (int l = 0; l < L; ++l) z += expf(-u[l] - mx);
         const float lse = mx + logf(z);
-        for (int l = 0; l < L; ++l) s[base + l * plane] = -U[base + l * plane] - lse;
+        for (int l = 0; l < L; ++l) o[l] = -u[l] - lse;
+        for (int l = L; l < LP; ++l) o[l] = kPadLogQ;
     }
 }
 
@@ -100,29 +90,27 @@ __global__ void fill_eta_kernel(float *eta, int B, float v) {
 
 }  // namespace
 
-cudaError_t launch_rows_to_planar(const float *src, float *dst, int B, int L, int H, int W, int P,
+cudaError_t launch_rows_to_padded(const float *src, float *dst, long long rows, int L, int LP, float pad,
                                   cudaStream_t st) {
-    rows_to_planar_kernel<<<blocks_for((size_t)B * H * W), kThreads, 0, st>>>(src, dst, B, L, H, W, P);
+    rows_to_padded_kernel<<<blocks_for((size_t)(rows * LP)), kThreads, 0, st>>>(src, dst, rows, L, LP, pad);
     return cudaGetLastError();
 }
 
-cudaError_t launch_planar_to_rows(const float *src, float *dst, int B, int L, int H, int W, int P,
-                                  int mode, cudaStream_t st) {
-    planar_to_rows_kernel<<<blocks_for((size_t)B * H * W), kThreads, 0, st>>>(src, dst, B, L, H, W, P,
-                                                                              mode);
+cudaError_t launch_padded_to_rows(const float *src, float *dst, long long rows, int L, int LP, int mode,
+                                  cudaStream_t st) {
+    padded_to_rows_kernel<<<blocks_for((size_t)(rows * L)), kThreads, 0, st>>>(src, dst, rows, L, LP, mode);
     return cudaGetLastError();
 }
 
-cudaError_t launch_weights_to_planar(const float *src, float *dst, int B, int nd, int H, int W,
-                                     int P, cudaStream_t st) {
-    weights_to_planar_kernel<<<blocks_for((size_t)B * nd * H * P), kThreads, 0, st>>>(src, dst, B, nd,
-                                                                                      H, W, P);
+cudaError_t launch_weights_to_pixel_major(const float *src, float *dst, int B, int nd, int H, int W,
+                                          cudaStream_t st) {
+    weights_to_pixel_major_kernel<<<blocks_for((size_t)B * nd * H * W), kThreads, 0, st>>>(src, dst, B, nd,
+                                                                                          H, W);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_logq(const float *U, float *s, int B, int L, int H, int W, int P,
-                             cudaStream_t st) {
-    init_logq_kernel<<<blocks_for((size_t)B * H * W), kThreads, 0, st>>>(U, s, B, L, H, W, P);
+cudaError_t launch_init_logq(const float *U, float *s, long long rows, int L, int LP, cudaStream_t st) {
+    init_logq_kernel<<<blocks_for((size_t)rows), kThreads, 0, st>>>(U, s, rows, L, LP);
     return cudaGetLastError();
 }
 

@@ -7,7 +7,8 @@
 // synchronise the device, and embedded integrations that must not touch the
 // allocator after start-up.  For them this file offers a variant of the grid
 // step whose only scratch memory -- the per-tile free-energy partials, the
-// tile counter, the status word and the step size -- lives in a file-scope
+// tile counter, the status word, the step size and the table of mu pairs --
+// lives in a file-scope
 // device array that the library holds from load time until the process exits,
 // on every GPU that loads it.
 //
@@ -25,9 +26,11 @@
 
 namespace {
 
-// 512 KiB: 65504 FP64 tile partials, then the counter, status word and step.
+// 512 KiB: 64480 FP64 tile partials, then the counter, status word and step
+// (256 bytes), then the table of mu pairs (8 KiB).
 constexpr size_t kScratchBytes = 512 * 1024;
-constexpr int kMaxTiles = (int)(kScratchBytes / sizeof(double)) - 32;
+constexpr size_t kPairBytes = 8 * 1024;
+constexpr int kMaxTiles = (int)((kScratchBytes - kPairBytes) / sizeof(double)) - 32;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_step_scratch[kScratchBytes];
@@ -83,11 +86,26 @@ extern "C" crf_status mf_grid_step_noalloc(int32_t topology, int32_t n_labels, i
     unsigned *counter = (unsigned *)(partial + kMaxTiles);
     int *status = (int *)(counter + 1);
     float *eta_dev = (float *)(status + 1);
+    float2 *mu_dev = (float2 *)((unsigned char *)base + kScratchBytes - kPairBytes);
     cudaStream_t st = (cudaStream_t)stream;
+
+    // mu as the step kernel's column / row pairs (see mu_pair_slots), built on
+    // the stack and copied into the scratch array
+    const int L = n_labels, LT = kernel_labels(L), NPP = mu_pair_slots(LT);
+    float2 pairs[2 * kMaxLabels * 16];
+    static_assert(sizeof(pairs) <= kPairBytes, "pair table fits its scratch slot");
+    auto at = [&](int r, int c) { return (r < L && c < L) ? mu[r * L + c] : 0.f; };
+    for (int k = 0; k < LT; ++k)
+        for (int j = 0; j < NPP; ++j) {
+            pairs[k * NPP + j] = make_float2(at(2 * j, k), at(2 * j + 1, k));
+            pairs[(LT + k) * NPP + j] = make_float2(at(k, 2 * j), at(k, 2 * j + 1));
+        }
 
     // the counter and status word must start at zero; everything else is
     // written before it is read
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned) + sizeof(int), st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(mu_dev, pairs, (size_t)2 * LT * NPP * sizeof(float2), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_fill_eta(eta_dev, 1, eta, st);
     GridStepLaunch a{};
     a.s_in = logq_in;
@@ -95,6 +113,8 @@ extern "C" crf_status mf_grid_step_noalloc(int32_t topology, int32_t n_labels, i
     a.U = U;
     a.w = w;
     a.eta = eta_dev;
+    a.mu_out = mu_dev;
+    a.mu_in = mu_dev + (size_t)LT * NPP;
     a.partial = partial;
     a.counter = counter;
     a.f_trace = F_out;   // never written: trace_cap = 0
@@ -105,14 +125,12 @@ extern "C" crf_status mf_grid_step_noalloc(int32_t topology, int32_t n_labels, i
     a.L = n_labels;
     a.H = (int)height;
     a.W = (int)width;
-    a.P = (int)width;
     a.conn = topology == CRF_GRID8 ? 8 : 4;
     a.t = 0;
     a.trace_cap = 0;
     a.update = 1;
     a.rel_tol = 0.0;
     a.mu_sym = sym;
-    a.mu_host = mu;
     if (e == cudaSuccess) e = launch_grid_step(a, st);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();

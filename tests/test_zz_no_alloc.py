@@ -14,13 +14,22 @@ from paper_1511_06103_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-def planar(a, H, W):
-    """[N][L] rows -> [L][H][W] label planes."""
-    return np.ascontiguousarray(a.reshape(H, W, -1).transpose(2, 0, 1))
+def storage_labels(L):
+    return 2 if L <= 2 else (L + 3) // 4 * 4
 
 
-def rows(p, H, W):
-    return np.ascontiguousarray(p.transpose(1, 2, 0).reshape(H * W, -1))
+def padded(a, pad):
+    """[N][L] rows -> [N][Lp] with the padding labels set to pad."""
+    N, L = a.shape
+    out = np.full((N, storage_labels(L)), pad, np.float32)
+    out[:, :L] = a
+    return out
+
+
+def pixel_major_weights(w):
+    """[n_dirs][H][W] -> [H*W][n_dirs] (entries off the image are already 0)."""
+    nd = w.shape[0]
+    return np.ascontiguousarray(w.reshape(nd, -1).T)
 
 
 @pytest.mark.parametrize("Hh,Ww,L,conn,sym", [(37, 45, 21, 8, True), (20, 70, 5, 4, False)])
@@ -54,10 +63,11 @@ def test_noalloc_step_matches_handle_api(Hh, Ww, L, conn, sym):
             ref_s.append(crf.log_marginals()[0])
 
     # the same two steps through the allocation-free entry point
-    U = torch.from_numpy(planar(d["U"], Hh, Ww)).to(dev)
-    w = torch.from_numpy(np.ascontiguousarray(d["w"])).to(dev)
+    U = torch.from_numpy(padded(d["U"], 0.0)).to(dev)
+    w = torch.from_numpy(pixel_major_weights(d["w"])).to(dev)
     mu = np.ascontiguousarray(d["mu"], np.float32)
-    bufs = [torch.from_numpy(planar(s0, Hh, Ww)).to(dev), torch.empty((L, Hh, Ww), device=dev)]
+    bufs = [torch.from_numpy(padded(s0, -1e30)).to(dev),
+            torch.empty((Hh * Ww, storage_labels(L)), device=dev)]
     F = torch.zeros(1, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
     for k in range(2):
@@ -65,7 +75,7 @@ def test_noalloc_step_matches_handle_api(Hh, Ww, L, conn, sym):
                 bufs[(k + 1) % 2].data_ptr(), eta, F.data_ptr(), stream)
         assert rc == 0
         torch.cuda.synchronize()
-        out = rows(bufs[(k + 1) % 2].cpu().numpy(), Hh, Ww)
+        out = bufs[(k + 1) % 2].cpu().numpy()[:, :L]
         assert np.abs(np.exp(out.astype(np.float64)) - np.exp(ref_s[k].astype(np.float64))).max() <= 1e-6
         assert abs(F.item() - ref_F[k]) <= 1e-6 * max(abs(ref_F[k]), Hh * Ww)
 
@@ -82,7 +92,7 @@ def test_noalloc_rejects_oversize_and_bad_arguments():
                    C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]
     mu = np.zeros((3, 3), np.float32)
     fake = 256  # never dereferenced: every case below is rejected before any launch
-    # 4096 x 4096 needs 65536 tiles > 65504
+    # 4096 x 4096 needs 65536 tiles > 64480
     assert fn(1, 3, 4096, 4096, fake, fake, mu.ctypes.data, fake, fake * 2, 0.5, fake, None) == -1
     assert fn(1, 0, 8, 8, fake, fake, mu.ctypes.data, fake, fake * 2, 0.5, fake, None) == -1
     assert fn(1, 3, 8, 8, fake, fake, mu.ctypes.data, fake, fake, 0.5, fake, None) == -1
