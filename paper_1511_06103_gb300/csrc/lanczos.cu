@@ -117,17 +117,73 @@ __global__ void lz_init_kernel(double *v, LzGeom g, unsigned long long seed) {
     }
 }
 
-// out = A v and alpha[b][k] = v . out.  A = W (scalar) or C H C (full).
+// Lanczos state.  Raw vectors u_k live in R[k % 3]; v_k = u_k / nrm[k] is
+// never written out (normalisation is applied on the fly).  The step index k
+// is read from *kdev, so that a CUDA graph of many steps can be replayed.
+struct LzState {
+    double *R0, *R1, *R2;
+    double *alpha, *nrm;   // [B][ld]: alpha_k, nrm[k] = |u_k| (nrm[k+1] = beta_k)
+    int *kdev;
+    int *stop;
+    double *partial;
+    unsigned *counter;
+    int ld;
+};
+
+__device__ __forceinline__ double *lz_buf(const LzState &s, int i) {
+    return i == 0 ? s.R0 : (i == 1 ? s.R1 : s.R2);
+}
+
+// Step part A: t = A v_k into R[(k+1) % 3] and alpha_k = v_k . t, with
+// A = W (scalar form) or C H C (full form).
+// Scalar form (symmetric mu): t = W v_k, one value per pixel.
 __global__ void __launch_bounds__(kLzThreads)
-lz_matvec_kernel(const double *__restrict__ v, double *__restrict__ out, const float *__restrict__ w,
-                 const float *__restrict__ mu, LzGeom g, const int *stop, double *partial,
-                 unsigned *counter, double *alpha, int ld, int k) {
+lz_step_a_scalar_kernel(LzState st, const float *__restrict__ w, LzGeom g) {
     const int b = blockIdx.y;
-    if (stop[b]) return;
+    const int k = *st.kdev;
+    if (st.stop[b] || k >= st.ld - 1) return;
+    const double *v = lz_buf(st, k % 3) + (size_t)b * g.H * g.P;
+    double *out = lz_buf(st, (k + 1) % 3) + (size_t)b * g.H * g.P;
+    const double inv = 1.0 / st.nrm[(size_t)b * st.ld + k];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nd = g.conn == 8 ? 4 : 2;
+    double dot = 0.0;
+    if (p < g.H * g.W) {
+        const int y = p / g.W, x = p - y * g.W;
+        const float *wb = w + (size_t)b * g.H * g.W * nd;
+        double acc = 0.0;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            if (d >= nd) break;
+            const int dy = d == 0 ? 0 : 1, dx = d == 0 ? 1 : (d == 1 ? 0 : (d == 2 ? 1 : -1));
+            const int yo = y + dy, xo = x + dx;
+            if (yo < g.H && xo >= 0 && xo < g.W)
+                acc += (double)wb[((size_t)y * g.W + x) * nd + d] * v[(size_t)yo * g.P + xo];
+            const int yi = y - dy, xi = x - dx;
+            if (yi >= 0 && xi >= 0 && xi < g.W)
+                acc += (double)wb[((size_t)yi * g.W + xi) * nd + d] * v[(size_t)yi * g.P + xi];
+        }
+        const double r = acc * inv;
+        out[(size_t)y * g.P + x] = r;
+        dot = r * v[(size_t)y * g.P + x] * inv;
+    }
+    double tot;
+    if (instance_reduce(dot, st.partial, st.counter, b, g.nblk, &tot)) st.alpha[(size_t)b * st.ld + k] = tot;
+}
+
+// Full form (any mu): t = C H C v_k over N*L unknowns.
+__global__ void __launch_bounds__(kLzThreads)
+lz_step_a_kernel(LzState st, const float *__restrict__ w, const float *__restrict__ mu, LzGeom g) {
+    const int b = blockIdx.y;
+    const int k = *st.kdev;
+    if (st.stop[b] || k >= st.ld - 1) return;
     __shared__ double mus[kMaxLabels * kMaxLabels];
     if (g.Lv > 1)
         for (int i = threadIdx.x; i < g.L * g.L; i += blockDim.x) mus[i] = (double)mu[i];
     __syncthreads();
+    const double *v = lz_buf(st, k % 3);
+    double *out = lz_buf(st, (k + 1) % 3);
+    const double inv = 1.0 / st.nrm[(size_t)b * st.ld + k];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const int nd = g.conn == 8 ? 4 : 2;
     const size_t plane = (size_t)g.H * g.P;
@@ -157,75 +213,115 @@ lz_matvec_kernel(const double *__restrict__ v, double *__restrict__ out, const f
         }
         double *ob = out + (size_t)b * g.Lv * plane;
         if (g.Lv == 1) {
-            const double r = So[0] + Si[0];
+            const double r = (So[0] + Si[0]) * inv;
             ob[pix] = r;
-            dot = r * vb[pix];
+            dot = r * vb[pix] * inv;
         } else {
             double m[kMaxLabels];
             double mean = 0.0;
             for (int l = 0; l < g.L; ++l) {
                 double t = 0.0;
                 for (int q = 0; q < g.L; ++q) t += mus[l * g.L + q] * So[q] + mus[q * g.L + l] * Si[q];
-                m[l] = t;
-                mean += t;
+                m[l] = t * inv;
+                mean += m[l];
             }
             mean /= g.L;
             for (int l = 0; l < g.L; ++l) {
                 const double r = m[l] - mean;
                 ob[l * plane + pix] = r;
-                dot += r * vb[l * plane + pix];
+                dot += r * vb[l * plane + pix] * inv;
             }
         }
     }
     double tot;
-    if (instance_reduce(dot, partial, counter, b, g.nblk, &tot)) alpha[(size_t)b * ld + k] = tot;
+    if (instance_reduce(dot, st.partial, st.counter, b, g.nblk, &tot)) st.alpha[(size_t)b * st.ld + k] = tot;
 }
 
-// wv = wv - alpha_k v - beta_{k-1} vp ; beta[b][k] = |wv|.
+// Step part B: u_{k+1} = t - alpha_k v_k - nrm[k] v_{k-1} in place of t, and
+// nrm[k+1] = |u_{k+1}|; the last block of the last instance advances k.
+// An instance whose new norm collapses (an invariant subspace) stops.
 __global__ void __launch_bounds__(kLzThreads)
-lz_axpy_norm_kernel(double *__restrict__ wv, const double *__restrict__ v, const double *__restrict__ vp,
-                    LzGeom g, const int *stop, double *partial, unsigned *counter, const double *alpha,
-                    double *beta, int ld, int k) {
+lz_step_b_kernel(LzState st, LzGeom g) {
     const int b = blockIdx.y;
-    if (stop[b]) return;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = *st.kdev;
+    const bool active = !st.stop[b] && k < st.ld - 1;
+    double nrm2 = 0.0;
+    if (active) {
+        const size_t plane = (size_t)g.H * g.P;
+        double *t = lz_buf(st, (k + 1) % 3);
+        const double *uk = lz_buf(st, k % 3);
+        const double *um = lz_buf(st, (k + 2) % 3);
+        const double a = st.alpha[(size_t)b * st.ld + k];
+        const double nk = st.nrm[(size_t)b * st.ld + k];
+        const double ik = 1.0 / nk;
+        const double im = k > 0 ? 1.0 / st.nrm[(size_t)b * st.ld + k - 1] : 0.0;
+        const int p = blockIdx.x * blockDim.x + threadIdx.x;
+        if (p < g.H * g.W) {
+            const int y = p / g.W, x = p - y * g.W;
+            const size_t off = (size_t)b * g.Lv * plane + (size_t)y * g.P + x;
+            for (int l = 0; l < g.Lv; ++l) {
+                const size_t i = off + l * plane;
+                double r = t[i] - a * (uk[i] * ik);
+                if (k > 0) r -= nk * (um[i] * im);
+                t[i] = r;
+                nrm2 += r * r;
+            }
+        }
+    }
+    // every block takes part in the counter so that the last one can advance k
+    __shared__ double red[kLzThreads / 32];
+    __shared__ int last_inst;
+    double v = warp_sum(nrm2);
+    const int tid = threadIdx.x;
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int i = 0; i < kLzThreads / 32; ++i) s += red[i];
+        st.partial[(size_t)b * g.nblk + blockIdx.x] = s;
+        __threadfence();
+        last_inst = atomicAdd(st.counter + b, 1u) == (unsigned)(g.nblk - 1);
+    }
+    __syncthreads();
+    if (!last_inst) return;
+    __threadfence();
+    double acc = 0.0;
+    for (int i = tid; i < g.nblk; i += kLzThreads) acc += __ldcg(st.partial + (size_t)b * g.nblk + i);
+    acc = warp_sum(acc);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid != 0) return;
+    double s = 0.0;
+    for (int i = 0; i < kLzThreads / 32; ++i) s += red[i];
+    st.counter[b] = 0u;
+    if (active) {
+        const double bk = sqrt(s);
+        const double ref = fabs(st.alpha[(size_t)b * st.ld + k]) + st.nrm[(size_t)b * st.ld + k];
+        st.nrm[(size_t)b * st.ld + k + 1] = bk;
+        if (!(bk > 1e-13 * ref) || !(bk > 1e-300)) st.stop[b] = k + 1;
+    }
+    // the instances finish in any order: the last one advances the step
+    __threadfence();
+    if (atomicAdd(st.counter + g.B, 1u) == (unsigned)(g.B - 1)) {
+        st.counter[g.B] = 0u;
+        *st.kdev = k + 1;
+    }
+}
+
+// nrm[0] = |u_0| (start vector).
+__global__ void __launch_bounds__(kLzThreads) lz_norm0_kernel(LzState st, LzGeom g) {
+    const int b = blockIdx.y;
     const size_t plane = (size_t)g.H * g.P;
-    const double a = alpha[(size_t)b * ld + k];
-    const double bp = k > 0 ? beta[(size_t)b * ld + k - 1] : 0.0;
-    double nrm = 0.0;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    double n2 = 0.0;
     if (p < g.H * g.W) {
         const int y = p / g.W, x = p - y * g.W;
         const size_t off = (size_t)b * g.Lv * plane + (size_t)y * g.P + x;
-        for (int l = 0; l < g.Lv; ++l) {
-            const size_t i = off + l * plane;
-            double r = wv[i] - a * v[i];
-            if (k > 0) r -= bp * vp[i];
-            wv[i] = r;
-            nrm += r * r;
-        }
+        for (int l = 0; l < g.Lv; ++l) n2 += st.R0[off + l * plane] * st.R0[off + l * plane];
     }
     double tot;
-    if (instance_reduce(nrm, partial, counter, b, g.nblk, &tot)) beta[(size_t)b * ld + k] = sqrt(tot);
-}
-
-// wv /= beta_k, or stop the instance at a (near) invariant subspace.
-__global__ void lz_scale_kernel(double *wv, LzGeom g, int *stop, const double *alpha, const double *beta,
-                                int ld, int k) {
-    const int b = blockIdx.y;
-    if (stop[b]) return;
-    const double bk = beta[(size_t)b * ld + k];
-    const double ref = fabs(alpha[(size_t)b * ld + k]) + (k > 0 ? beta[(size_t)b * ld + k - 1] : 0.0);
-    if (!(bk > 1e-13 * ref) || !(bk > 1e-300)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) stop[b] = k + 1;
-        return;
-    }
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= g.H * g.W) return;
-    const size_t plane = (size_t)g.H * g.P;
-    const int y = p / g.W, x = p - y * g.W;
-    const size_t off = (size_t)b * g.Lv * plane + (size_t)y * g.P + x;
-    const double inv = 1.0 / bk;
-    for (int l = 0; l < g.Lv; ++l) wv[off + l * plane] *= inv;
+    if (instance_reduce(n2, st.partial, st.counter, b, g.nblk, &tot)) st.nrm[(size_t)b * st.ld] = sqrt(tot);
 }
 
 // Sturm count: number of eigenvalues of the symmetric tridiagonal (a, c) < x.
@@ -252,7 +348,7 @@ __global__ void lz_ritz_kernel(const double *alpha, const double *beta, int ld, 
     if (stop[b] && stop[b] < n) n = stop[b];
     if (n <= 0) return;
     const double *a = alpha + (size_t)b * ld;
-    const double *c = beta + (size_t)b * ld;
+    const double *c = beta + (size_t)b * ld + 1;   // beta_k = nrm[k+1]
     double lo = INFINITY, hi = -INFINITY, amax = 0.0;
     for (int i = 0; i < n; ++i) {
         const double r = (i > 0 ? fabs(c[i - 1]) : 0.0) + (i + 1 < n ? fabs(c[i]) : 0.0);
@@ -324,12 +420,15 @@ __global__ void mu_tilde_extremes_kernel(const float *mu, int L, double *nu) {
             off += __shfl_xor_sync(0xffffffffu, off, o);
             tot += __shfl_xor_sync(0xffffffffu, tot, o);
         }
-        if (off <= 1e-32 * (tot > 0 ? tot : 1.0)) break;
+        // off-diagonal mass below (1e-13 |A|)^2: the diagonal then holds the
+        // eigenvalues to ~1e-26 relative (the error is second order in it)
+        if (off <= 1e-26 * (tot > 0 ? tot : 1.0)) break;
+        const double tiny = 1e-18 * sqrt(tot);
         for (int p = 0; p < L; ++p)
             for (int r = p + 1; r < L; ++r) {
                 if (lane == 0) {
                     const double apr = A[p * L + r];
-                    if (fabs(apr) < 1e-300) {
+                    if (fabs(apr) <= tiny) {
                         stop_flag = 1;
                     } else {
                         stop_flag = 0;
@@ -429,92 +528,82 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
     const int kmax = (int)std::min<long long>(dim, (long long)job.max_steps);
     const int ld = kmax + 1;
     const size_t vec = (size_t)B * g.Lv * job.H * job.P;
+    constexpr int kChunk = 96;   // steps per graph replay between convergence checks
     int rc = 0;
-    double *V[3] = {nullptr, nullptr, nullptr};
-    double *alpha = nullptr, *beta = nullptr, *partial = nullptr, *rmin = nullptr, *rmax = nullptr,
-           *nu = nullptr;
-    unsigned *counter = nullptr;
-    int *stop = nullptr;
+    LzState S{};
+    double *rmin = nullptr, *rmax = nullptr, *nu = nullptr;
     float *mu_dev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
     std::vector<double> hmin(B), hmax(B), pmin(B, NAN), pmax(B, NAN);
     std::vector<int> hstop(B);
     int k = 0;
     dim3 gridp(g.nblk, B);
-    for (int i = 0; i < 3; ++i) {
-        LZ_CHECK(cudaMallocAsync((void **)&V[i], vec * sizeof(double), st));
-        LZ_CHECK(cudaMemsetAsync(V[i], 0, vec * sizeof(double), st));
-    }
-    LZ_CHECK(cudaMallocAsync((void **)&alpha, (size_t)B * ld * sizeof(double), st));
-    LZ_CHECK(cudaMallocAsync((void **)&beta, (size_t)B * ld * sizeof(double), st));
-    LZ_CHECK(cudaMallocAsync((void **)&partial, (size_t)B * g.nblk * sizeof(double), st));
+    S.ld = ld;
+    LZ_CHECK(cudaMallocAsync((void **)&S.R0, vec * sizeof(double), st));
+    LZ_CHECK(cudaMallocAsync((void **)&S.R1, vec * sizeof(double), st));
+    LZ_CHECK(cudaMallocAsync((void **)&S.R2, vec * sizeof(double), st));
+    LZ_CHECK(cudaMemsetAsync(S.R1, 0, vec * sizeof(double), st));
+    LZ_CHECK(cudaMemsetAsync(S.R2, 0, vec * sizeof(double), st));
+    LZ_CHECK(cudaMallocAsync((void **)&S.alpha, (size_t)B * ld * sizeof(double), st));
+    LZ_CHECK(cudaMallocAsync((void **)&S.nrm, (size_t)B * (ld + 1) * sizeof(double), st));
+    LZ_CHECK(cudaMallocAsync((void **)&S.partial, (size_t)B * g.nblk * sizeof(double), st));
+    LZ_CHECK(cudaMallocAsync((void **)&S.counter, (size_t)(B + 1) * sizeof(unsigned), st));
+    LZ_CHECK(cudaMallocAsync((void **)&S.stop, (size_t)B * sizeof(int), st));
+    LZ_CHECK(cudaMallocAsync((void **)&S.kdev, sizeof(int), st));
     LZ_CHECK(cudaMallocAsync((void **)&rmin, (size_t)B * sizeof(double), st));
     LZ_CHECK(cudaMallocAsync((void **)&rmax, (size_t)B * sizeof(double), st));
     LZ_CHECK(cudaMallocAsync((void **)&nu, 2 * sizeof(double), st));
-    LZ_CHECK(cudaMallocAsync((void **)&counter, (size_t)B * sizeof(unsigned), st));
-    LZ_CHECK(cudaMallocAsync((void **)&stop, (size_t)B * sizeof(int), st));
     LZ_CHECK(cudaMallocAsync((void **)&mu_dev, (size_t)job.L * job.L * sizeof(float), st));
-    LZ_CHECK(cudaMemsetAsync(alpha, 0, (size_t)B * ld * sizeof(double), st));
-    LZ_CHECK(cudaMemsetAsync(beta, 0, (size_t)B * ld * sizeof(double), st));
-    LZ_CHECK(cudaMemsetAsync(counter, 0, (size_t)B * sizeof(unsigned), st));
-    LZ_CHECK(cudaMemsetAsync(stop, 0, (size_t)B * sizeof(int), st));
+    LZ_CHECK(cudaMemsetAsync(S.alpha, 0, (size_t)B * ld * sizeof(double), st));
+    LZ_CHECK(cudaMemsetAsync(S.nrm, 0, (size_t)B * (ld + 1) * sizeof(double), st));
+    LZ_CHECK(cudaMemsetAsync(S.counter, 0, (size_t)(B + 1) * sizeof(unsigned), st));
+    LZ_CHECK(cudaMemsetAsync(S.stop, 0, (size_t)B * sizeof(int), st));
+    LZ_CHECK(cudaMemsetAsync(S.kdev, 0, sizeof(int), st));
     LZ_CHECK(cudaMemcpyAsync(mu_dev, job.mu_host, (size_t)job.L * job.L * sizeof(float),
                              cudaMemcpyHostToDevice, st));
     LZ_CHECK(cudaStreamSynchronize(st));  // mu_host is pageable and owned by the caller
 
-    // start vector, normalised by a first "scale" through the norm kernels
-    lz_init_kernel<<<gridp, kLzThreads, 0, st>>>(V[1], g, 0x5eed5eedull);
-    nl += 3;
+    lz_init_kernel<<<gridp, kLzThreads, 0, st>>>(S.R0, g, 0x5eed5eedull);
     LZ_CHECK(cudaGetLastError());
-    {
-        // beta[-1] slot: reuse alpha[.,0] = 0 and compute |v| into beta[.,0]
-        lz_axpy_norm_kernel<<<gridp, kLzThreads, 0, st>>>(V[1], V[0], V[0], g, stop, partial, counter,
-                                                         alpha, beta, ld, 0);
-        LZ_CHECK(cudaGetLastError());
-        lz_scale_kernel<<<gridp, kLzThreads, 0, st>>>(V[1], g, stop, alpha, beta, ld, 0);
-        LZ_CHECK(cudaGetLastError());
-        LZ_CHECK(cudaMemsetAsync(beta, 0, (size_t)B * ld * sizeof(double), st));
+    lz_norm0_kernel<<<gridp, kLzThreads, 0, st>>>(S, g);
+    LZ_CHECK(cudaGetLastError());
+    nl += 2;
+
+    // one graph of kChunk steps, captured once and replayed
+    LZ_CHECK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    LZ_CHECK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < kChunk; ++i) {
+        if (g.Lv == 1)
+            lz_step_a_scalar_kernel<<<gridp, kLzThreads, 0, cap>>>(S, job.w, g);
+        else
+            lz_step_a_kernel<<<gridp, kLzThreads, 0, cap>>>(S, job.w, mu_dev, g);
+        lz_step_b_kernel<<<gridp, kLzThreads, 0, cap>>>(S, g);
     }
-    {
-        double *vp = V[0], *v = V[1], *wv = V[2];
-        for (k = 0; k < kmax; ++k) {
-            lz_matvec_kernel<<<gridp, kLzThreads, 0, st>>>(v, wv, job.w, mu_dev, g, stop, partial, counter,
-                                                           alpha, ld, k);
-            LZ_CHECK(cudaGetLastError());
-            lz_axpy_norm_kernel<<<gridp, kLzThreads, 0, st>>>(wv, v, vp, g, stop, partial, counter, alpha,
-                                                             beta, ld, k);
-            LZ_CHECK(cudaGetLastError());
-            lz_scale_kernel<<<gridp, kLzThreads, 0, st>>>(wv, g, stop, alpha, beta, ld, k);
-            LZ_CHECK(cudaGetLastError());
-            nl += 3;
-            double *t = vp;
-            vp = v;
-            v = wv;
-            wv = t;
-            const bool last = (k + 1 == kmax);
-            if (((k + 1) % 64) == 0 || last) {
-                lz_ritz_kernel<<<B, 64, 0, st>>>(alpha, beta, ld, k + 1, stop, rmin, rmax);
-                LZ_CHECK(cudaGetLastError());
-                nl += 1;
-                LZ_CHECK(cudaMemcpyAsync(hmin.data(), rmin, B * sizeof(double), cudaMemcpyDeviceToHost, st));
-                LZ_CHECK(cudaMemcpyAsync(hmax.data(), rmax, B * sizeof(double), cudaMemcpyDeviceToHost, st));
-                LZ_CHECK(cudaMemcpyAsync(hstop.data(), stop, B * sizeof(int), cudaMemcpyDeviceToHost, st));
-                LZ_CHECK(cudaStreamSynchronize(st));
-                bool all = true;
-                for (int b = 0; b < B; ++b) {
-                    const double sc = fmax(fmax(fabs(hmin[b]), fabs(hmax[b])), 1e-300);
-                    const bool conv = hstop[b] != 0 ||
-                                      (fabs(hmax[b] - pmax[b]) <= job.tol * sc &&
-                                       fabs(hmin[b] - pmin[b]) <= job.tol * sc);
-                    all = all && conv;
-                    pmin[b] = hmin[b];
-                    pmax[b] = hmax[b];
-                }
-                if (all) {
-                    ++k;
-                    break;
-                }
-            }
+    LZ_CHECK(cudaStreamEndCapture(cap, &graph));
+    LZ_CHECK(cudaGraphInstantiate(&exec, graph, 0));
+    while (k < kmax) {
+        LZ_CHECK(cudaGraphLaunch(exec, st));
+        nl += 2 * kChunk;
+        k = std::min(k + kChunk, kmax);
+        lz_ritz_kernel<<<B, 64, 0, st>>>(S.alpha, S.nrm, ld, k, S.stop, rmin, rmax);
+        LZ_CHECK(cudaGetLastError());
+        nl += 1;
+        LZ_CHECK(cudaMemcpyAsync(hmin.data(), rmin, B * sizeof(double), cudaMemcpyDeviceToHost, st));
+        LZ_CHECK(cudaMemcpyAsync(hmax.data(), rmax, B * sizeof(double), cudaMemcpyDeviceToHost, st));
+        LZ_CHECK(cudaMemcpyAsync(hstop.data(), S.stop, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+        LZ_CHECK(cudaStreamSynchronize(st));
+        bool all = true;
+        for (int b = 0; b < B; ++b) {
+            const double sc = fmax(fmax(fabs(hmin[b]), fabs(hmax[b])), 1e-300);
+            const bool conv = hstop[b] != 0 || (fabs(hmax[b] - pmax[b]) <= job.tol * sc &&
+                                                fabs(hmin[b] - pmin[b]) <= job.tol * sc);
+            all = all && conv;
+            pmin[b] = hmin[b];
+            pmax[b] = hmax[b];
         }
+        if (all) break;
     }
     if (job.mu_sym) {
         mu_tilde_extremes_kernel<<<1, 32, 0, st>>>(mu_dev, job.L, nu);
@@ -527,16 +616,15 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
     if (steps_out) *steps_out = k;
     if (launches_out) *launches_out = nl;
 done:
-    for (int i = 0; i < 3; ++i)
-        if (V[i]) cudaFreeAsync(V[i], st);
-    if (alpha) cudaFreeAsync(alpha, st);
-    if (beta) cudaFreeAsync(beta, st);
-    if (partial) cudaFreeAsync(partial, st);
-    if (rmin) cudaFreeAsync(rmin, st);
-    if (rmax) cudaFreeAsync(rmax, st);
-    if (nu) cudaFreeAsync(nu, st);
-    if (counter) cudaFreeAsync(counter, st);
-    if (stop) cudaFreeAsync(stop, st);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    double *ds[] = {S.R0, S.R1, S.R2, S.alpha, S.nrm, S.partial, rmin, rmax, nu};
+    for (double *p : ds)
+        if (p) cudaFreeAsync(p, st);
+    if (S.counter) cudaFreeAsync(S.counter, st);
+    if (S.stop) cudaFreeAsync(S.stop, st);
+    if (S.kdev) cudaFreeAsync(S.kdev, st);
     if (mu_dev) cudaFreeAsync(mu_dev, st);
     return rc;
 }
