@@ -64,7 +64,7 @@ typedef enum {
 
 typedef struct {
     int32_t topology;       /* crf_topology                                   */
-    int32_t n_labels;       /* L: 1..32                                       */
+    int32_t n_labels;       /* L: 1..32 (grids), 1..24 (fully connected)      */
     int32_t batch;          /* independent instances with the same shape, >= 1 */
     int32_t precision;      /* crf_precision                                  */
     int64_t height;         /* grid rows; dense: N = height*width variables   */

@@ -66,6 +66,7 @@ def _load():
             "orc_init_logq": (None, [_vp, _vp]),
             "orc_prox_step": (None, [_vp, _d, _vp, _vp]),
             "orc_parallel_prox": (None, [_vp, _d, _i32, _vp, _vp]),
+            "orc_prox_step_rows": (None, [_vp, _d, _vp, _vp, _i64, _vp]),
             "orc_sweep": (None, [_vp, _i32, _vp]),
             "orc_state_energy": (_d, [_vp, _vp]),
             "orc_brute_force": (C.c_int, [_vp, _vp, _vp]),
@@ -227,6 +228,14 @@ class Model:
         s = self._nl(s)
         out = np.zeros_like(s)
         _load().orc_prox_step(self._h, float(eta), _ptr(s), _ptr(out))
+        return out
+
+    def prox_step_rows(self, eta: float, s, rows) -> np.ndarray:
+        """One proximal step evaluated for the listed variables only."""
+        s = self._nl(s)
+        rows = np.ascontiguousarray(rows, np.int64)
+        out = np.zeros((rows.size, self.L))
+        _load().orc_prox_step_rows(self._h, float(eta), _ptr(s), _ptr(rows), rows.size, _ptr(out))
         return out
 
     def parallel_prox(self, eta: float, iters: int, s=None, trace: bool = True):

@@ -400,6 +400,33 @@ void orc_prox_step(const orc_model *m, double eta, const double *s_in, double *s
     free(g);
 }
 
+/* The same step for the listed variables only (rows[r] in 0..n-1): out gets
+ * log q^{t+1} of those variables, one row of L values each. */
+void orc_prox_step_rows(const orc_model *m, double eta, const double *s_in, const int64_t *rows,
+                        int64_t nrows, double *out)
+{
+    const int L = m->L;
+    const int64_t nl = m->n * L;
+    double *q = (double *)malloc(sizeof(double) * (size_t)nl);
+    for (int64_t k = 0; k < nl; ++k) q[k] = exp(s_in[k]);
+#pragma omp parallel
+    {
+        double *g = (double *)xcalloc((size_t)L, sizeof(double));
+        double *a = (double *)xcalloc((size_t)L, sizeof(double));
+#pragma omp for schedule(static)
+        for (int64_t r = 0; r < nrows; ++r) {
+            const int64_t i = rows[r];
+            pair_grad_var(m, q, i, g);
+            for (int l = 0; l < L; ++l)
+                a[l] = -eta * (g[l] + m->U[i * L + l]) + (1.0 - eta) * s_in[i * L + l];
+            log_softmax(a, out + r * L, L);
+        }
+        free(g);
+        free(a);
+    }
+    free(q);
+}
+
 /* iters parallel proximal steps on s (in place).  F_trace, if given, gets
  * F(q^t) for t = 0..iters (iters+1 values). */
 void orc_parallel_prox(const orc_model *m, double eta, int32_t iters, double *s,

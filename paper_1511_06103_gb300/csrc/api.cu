@@ -23,6 +23,16 @@ struct crf_s {
     float *s[2] = {nullptr, nullptr};  // [B][N][LP] log q, ping-pong, padding kPadLogQ
     float *w = nullptr;          // [B][N][nd] edge weights
     float2 *mu_pairs = nullptr;  // device [2][LT][NPP] mu column / row pairs
+    // fully connected model
+    bool dense = false;
+    int N = 0;                   // variables per instance
+    float *K32 = nullptr;        // [B][N][N]
+    __nv_bfloat16 *K16 = nullptr;  // [B][N][N] (tensor-core form)
+    float *q32[2] = {nullptr, nullptr};            // [B][N][LP] + padding
+    __nv_bfloat16 *qt16[2] = {nullptr, nullptr};   // [B][32][N]
+    float *feats = nullptr;      // [B][N][5]
+    float *mu_dev = nullptr;     // [L][L]
+    double theta[2] = {0.0, 0.0};
     float *eta_fixed = nullptr;  // [B]
     float *eta_auto = nullptr;   // [B]
     double *Lambda = nullptr;    // [B]
@@ -84,6 +94,12 @@ void free_all(crf_t h) {
     if (h->done) cudaFree(h->done);
     if (h->status) cudaFree(h->status);
     if (h->mu_pairs) cudaFree(h->mu_pairs);
+    float *fd[] = {h->K32, h->q32[0], h->q32[1], h->feats, h->mu_dev};
+    for (float *p : fd)
+        if (p) cudaFree(p);
+    __nv_bfloat16 *bd[] = {h->K16, h->qt16[0], h->qt16[1]};
+    for (__nv_bfloat16 *p : bd)
+        if (p) cudaFree(p);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
 }
@@ -140,17 +156,67 @@ GridStepLaunch step_args(crf_t h, const float *eta, int t, int update, double re
     return a;
 }
 
+DenseStepLaunch dense_args(crf_t h, const float *eta, int t, int update, double rel_tol) {
+    DenseStepLaunch a{};
+    a.K32 = h->K32;
+    a.K16 = h->K16;
+    a.q_in = h->q32[h->cur];
+    a.qt_in = h->qt16[h->cur];
+    a.s_in = h->s[h->cur];
+    a.U = h->U;
+    a.s_out = h->s[h->cur ^ 1];
+    a.q_out = h->q32[h->cur ^ 1];
+    a.qt_out = h->qt16[h->cur ^ 1];
+    a.eta = eta;
+    a.mu = h->mu_dev;
+    a.partial = h->partial;
+    a.counter = h->counter;
+    a.f_trace = h->ftrace;
+    a.f_cur = h->fcur;
+    a.done = update ? h->done : nullptr;
+    a.status = h->status;
+    a.B = h->B;
+    a.N = h->N;
+    a.L = h->L;
+    a.t = t;
+    a.trace_cap = h->trace_cap;
+    a.update = update;
+    a.rel_tol = rel_tol;
+    return a;
+}
+
+// One step (update = 1) or a free-energy-only pass (update = 0) of either model.
+cudaError_t launch_step(crf_t h, const float *eta, int t, int update, double rel_tol) {
+    if (h->dense) {
+        DenseStepLaunch a = dense_args(h, eta, t, update, rel_tol);
+        if (!update || rel_tol <= 0) a.done = nullptr;
+        return launch_dense_step_f32(a, h->st);
+    }
+    GridStepLaunch a = step_args(h, eta, t, update, rel_tol);
+    if (!update || rel_tol <= 0) a.done = nullptr;
+    return launch_grid_step(a, h->st);
+}
+
+// After the state buffer s[cur] changed outside a step: refresh the dense
+// model's q copies.
+cudaError_t refresh_q(crf_t h) {
+    if (!h->dense) return cudaSuccess;
+    h->launches++;
+    return launch_dense_export_q(h->s[h->cur], h->q32[h->cur], h->qt16[h->cur], h->B, h->N, h->L, h->LP, h->st);
+}
+
 crf_status ensure_lambda(crf_t h) {
     if (h->lambda_valid) return CRF_OK;
     LipschitzJob job{};
     job.w = h->w;
+    job.Kdense = h->dense ? h->K32 : nullptr;
     job.mu_host = h->mu.data();
     job.mu_sym = h->mu_sym;
     job.B = h->B;
     job.L = h->L;
-    job.H = h->H;
-    job.W = h->W;
-    job.P = h->W;
+    job.H = h->dense ? 1 : h->H;
+    job.W = h->dense ? h->N : h->W;
+    job.P = job.W;
     job.conn = h->conn;
     job.Lambda = h->Lambda;
     job.eta = h->eta_auto;
@@ -237,12 +303,21 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
     if (d.n_labels < 1 || d.n_labels > kMaxLabels || d.batch < 1 || d.height < 1 || d.width < 1)
         return CRF_E_INVALID;
     if (d.precision != CRF_FP32 && d.precision != CRF_BF16) return CRF_E_INVALID;
-    if (d.topology == CRF_DENSE_GAUSS) return CRF_E_UNSUPPORTED;
-    if (d.topology != CRF_GRID4 && d.topology != CRF_GRID8) return CRF_E_INVALID;
+    if (d.topology != CRF_GRID4 && d.topology != CRF_GRID8 && d.topology != CRF_DENSE_GAUSS)
+        return CRF_E_INVALID;
     if (d.precision == CRF_BF16) return CRF_E_UNSUPPORTED;
-    // grid dimensions: y tiles <= 65535, batch <= 65535 (CUDA grid limits)
-    if (d.height > 65535ll * GY || d.width > (1 << 24) || d.batch > 65535) return CRF_E_INVALID;
-    if ((long long)d.batch * storage_labels(d.n_labels) * d.height * d.width > (1ll << 40)) return CRF_E_INVALID;
+    const bool dense = d.topology == CRF_DENSE_GAUSS;
+    if (dense) {
+        // the dense step keeps up to 24 labels per row; N x N weights per instance
+        if (d.n_labels > 24) return CRF_E_UNSUPPORTED;
+        const long long N = d.height * d.width;
+        if (N > 65536 || d.batch > 65535 || (long long)d.batch * N * N * 4 > (64ll << 30)) return CRF_E_INVALID;
+    } else {
+        // grid dimensions: y tiles <= 65535, batch <= 65535 (CUDA grid limits)
+        if (d.height > 65535ll * GY || d.width > (1 << 24) || d.batch > 65535) return CRF_E_INVALID;
+        if ((long long)d.batch * storage_labels(d.n_labels) * d.height * d.width > (1ll << 40))
+            return CRF_E_INVALID;
+    }
 
     crf_t h = new (std::nothrow) crf_s();
     if (!h) return CRF_E_OOM;
@@ -259,6 +334,12 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
     int nbx, nby;
     grid_tiles(h->H, h->W, &nbx, &nby);
     h->nblk = nbx * nby;
+    h->dense = dense;
+    h->N = h->H * h->W;
+    if (dense) {
+        h->nd = 0;
+        h->nblk = dense_nblk(h->N);
+    }
     h->mu.assign((size_t)h->L * h->L, 0.f);
 
     bool ok = true;
@@ -266,6 +347,18 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
     ok = ok && dalloc(&h->s[0], n_padded(h)) == cudaSuccess;
     ok = ok && dalloc(&h->s[1], n_padded(h)) == cudaSuccess;
     ok = ok && dalloc(&h->w, n_pix(h) * h->nd) == cudaSuccess;
+    if (dense) {
+        const size_t qn = n_padded(h) + 64 * (size_t)h->LP;   // rows past N read as zero
+        ok = ok && dalloc(&h->K32, (size_t)h->B * h->N * h->N) == cudaSuccess;
+        ok = ok && dalloc(&h->q32[0], qn) == cudaSuccess;
+        ok = ok && dalloc(&h->q32[1], qn) == cudaSuccess;
+        ok = ok && dalloc(&h->feats, (size_t)h->B * h->N * 5) == cudaSuccess;
+        ok = ok && dalloc(&h->mu_dev, (size_t)h->L * h->L) == cudaSuccess;
+        if (ok) {
+            ok = cudaMemsetAsync(h->q32[0], 0, qn * sizeof(float), h->st) == cudaSuccess &&
+                 cudaMemsetAsync(h->q32[1], 0, qn * sizeof(float), h->st) == cudaSuccess;
+        }
+    }
     ok = ok && dalloc(&h->mu_pairs, (size_t)2 * h->LT * mu_pair_slots(h->LT)) == cudaSuccess;
     ok = ok && dalloc(&h->eta_fixed, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->eta_auto, h->B) == cudaSuccess;
@@ -331,15 +424,49 @@ crf_status crf_set_unary(crf_t h, const float *U, int is_device) {
     CK(h, launch_init_logq(h->U, h->s[0], (long long)n_pix(h), h->L, h->LP, h->st));
     h->launches += 2;
     h->cur = 0;
+    CK(h, refresh_q(h));
     h->fcur_valid = false;
     if (!is_device) CK(h, cudaStreamSynchronize(h->st));
     h->has_unary = true;
     return CRF_OK;
 }
 
+// Fully connected model: features and bandwidths in, K (and its BF16 copy
+// for the tensor-core form) built on the device.
+static crf_status set_pairwise_dense(crf_t h, const std::vector<float> &m, const float *feats,
+                                     const float *theta, int is_device) {
+    double th[2];
+    if (!theta) return CRF_E_INVALID;
+    if (is_device) {
+        float t2[2];
+        CK(h, cudaMemcpyAsync(t2, theta, sizeof(t2), cudaMemcpyDeviceToHost, h->st));
+        CK(h, cudaStreamSynchronize(h->st));
+        th[0] = t2[0];
+        th[1] = t2[1];
+    } else {
+        th[0] = theta[0];
+        th[1] = theta[1];
+    }
+    if (!(th[0] > 0) || !(th[1] > 0) || !std::isfinite(th[0]) || !std::isfinite(th[1])) return CRF_E_INVALID;
+    const size_t nf = (size_t)h->B * h->N * 5;
+    CK(h, cudaMemcpyAsync(h->feats, feats, nf * sizeof(float),
+                          is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+    CK(h, cudaMemcpyAsync(h->mu_dev, m.data(), m.size() * sizeof(float), cudaMemcpyHostToDevice, h->st));
+    CK(h, launch_dense_kernel_build(h->feats, h->K32, h->K16, h->B, h->N, th[0], th[1], h->st));
+    h->launches += h->K16 ? 2 : 1;
+    CK(h, cudaStreamSynchronize(h->st));   // m and a host feats buffer are pageable
+    h->theta[0] = th[0];
+    h->theta[1] = th[1];
+    h->mu = m;
+    h->mu_sym = true;
+    h->has_pairwise = true;
+    h->lambda_valid = false;
+    h->fcur_valid = false;
+    return CRF_OK;
+}
+
 crf_status crf_set_pairwise(crf_t h, const float *mu, const float *w_or_feats, const float *theta,
                             int is_device) {
-    (void)theta;
     crf_status rc = check_handle(h);
     if (rc != CRF_OK) return rc;
     if (!mu || !w_or_feats) return CRF_E_INVALID;
@@ -357,6 +484,11 @@ crf_status crf_set_pairwise(crf_t h, const float *mu, const float *w_or_feats, c
     for (int i = 0; i < h->L; ++i)
         for (int k = i + 1; k < h->L; ++k)
             if (m[i * h->L + k] != m[k * h->L + i]) sym = false;
+    if (h->dense) {
+        // pairs of a fully connected model have no orientation: mu must be symmetric
+        if (!sym) return CRF_E_INVALID;
+        return set_pairwise_dense(h, m, w_or_feats, theta, is_device);
+    }
     const size_t nw = n_pix(h) * h->nd;
     std::vector<float2> pairs;
     build_mu_pairs(m, h->L, h->LT, pairs);
@@ -402,6 +534,7 @@ crf_status crf_set_state(crf_t h, const float *logq, int is_device) {
     }
     CK(h, launch_rows_to_padded(src, h->s[h->cur], (long long)n_pix(h), h->L, h->LP, kPadLogQ, h->st));
     h->launches++;
+    CK(h, refresh_q(h));
     h->fcur_valid = false;
     if (!is_device) CK(h, cudaStreamSynchronize(h->st));
     return CRF_OK;
@@ -426,15 +559,14 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
     if (p->reset) {
         CK(h, launch_init_logq(h->U, h->s[h->cur], (long long)n_pix(h), h->L, h->LP, h->st));
         h->launches++;
+        CK(h, refresh_q(h));
     }
     rc = ensure_trace(h, p->max_iters);
     if (rc != CRF_OK) return rc;
     if (p->rel_tol > 0) CK(h, cudaMemsetAsync(h->done, 0, h->B * sizeof(int), h->st));
     if (h->profile) CK(h, cudaEventRecord(h->ev0, h->st));
     for (int t = 0; t < p->max_iters; ++t) {
-        GridStepLaunch a = step_args(h, eta, t, 1, p->rel_tol);
-        if (p->rel_tol <= 0) a.done = nullptr;
-        CK(h, launch_grid_step(a, h->st));
+        CK(h, launch_step(h, eta, t, 1, p->rel_tol));
         h->cur ^= 1;
     }
     h->launches += p->max_iters;
@@ -446,8 +578,7 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
     h->last_iters = p->max_iters;
     h->fcur_valid = false;
     if (p->final_free_energy) {
-        GridStepLaunch a = step_args(h, eta, 0, 0, 0.0);
-        CK(h, launch_grid_step(a, h->st));
+        CK(h, launch_step(h, eta, 0, 0, 0.0));
         h->launches++;
         h->fcur_valid = true;
     }
@@ -466,9 +597,8 @@ crf_status mf_free_energy(crf_t h, double *F) {
     if (!F) return CRF_E_INVALID;
     if (!h->has_unary || !h->has_pairwise) return CRF_E_INVALID;
     if (!h->fcur_valid) {
-        GridStepLaunch a = step_args(h, h->eta_fixed, 0, 0, 0.0);
         CK(h, launch_fill_eta(h->eta_fixed, h->B, 1.0, h->st));
-        CK(h, launch_grid_step(a, h->st));
+        CK(h, launch_step(h, h->eta_fixed, 0, 0, 0.0));
         h->launches += 2;
         h->fcur_valid = true;
     }

@@ -1,0 +1,350 @@
+// dense.cu -- fully connected CRF with a Gaussian appearance kernel
+// (the dense segmentation model of Sec. 4.2), FP32 CUDA-core form.
+//
+// The pairwise weights are K_ij = exp(-|p_i-p_j|^2/(2 theta_pos^2)
+// - |c_i-c_j|^2/(2 theta_rgb^2)) for i != j over (x, y, r, g, b) features, each
+// unordered pair counted once, with one symmetric label matrix mu.  One step:
+//   a1  S = K Q (N x N times N x L), m_i = mu S_i
+//   a2  g_i = U_i + m_i
+//   a3  a_i = -eta g_i + (1 - eta) log q_i
+//   a4  log q'_i = a_i - logsumexp(a_i)
+//   a5  F = sum_i q_i . (U_i + m_i / 2 + log q_i)
+//
+// K is materialised once per model ([B][N][N], FP32 here; BF16 for the
+// tensor-core form in dense_tc.cu), so a step streams it from HBM: the FP32
+// form reads 4 N^2 bytes per iteration and is bound by HBM bandwidth.
+// A CTA owns 64 rows of K and all label columns; K is read in 32 x 64
+// chunks (32-byte sectors per thread), transposed through shared memory so
+// that each thread's 4 rows x 6 labels micro-tile is fed by one 128-bit and
+// three 64-bit shared loads per k, and the 256 threads split each chunk four
+// ways along k.  The next chunks are prefetched into registers while the
+// current one is multiplied.  The epilogue (mu product, update,
+// renormalisation, free energy) runs on the CTA's 64 rows.
+#include <cmath>
+
+#include "dense_common.cuh"
+#include "f32x2.cuh"
+#include "internal.h"
+
+namespace proxmf {
+
+namespace {
+
+constexpr int kDR = 64;        // rows of K per CTA
+constexpr int kDK = 32;        // k per chunk
+constexpr int kDT = 256;       // threads per CTA
+constexpr int kKsStride = kDR + 4;
+
+// ---------------------------------------------------------------- K build --
+
+template <typename T>
+__device__ __forceinline__ T to_out(float v);
+template <>
+__device__ __forceinline__ float to_out<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// K[b][i][j] from features [b][N][5]; one thread per (i, 4 consecutive j).
+template <typename T>
+__global__ void dense_kernel_build_kernel(const float *__restrict__ feats, T *__restrict__ K, int N,
+                                          float inv2p, float inv2c) {
+    const int b = blockIdx.z;
+    const int i = blockIdx.y;
+    const float *f = feats + (size_t)b * N * 5;
+    const float xi = f[i * 5 + 0], yi = f[i * 5 + 1], ri = f[i * 5 + 2], gi = f[i * 5 + 3], bi = f[i * 5 + 4];
+    T *row = K + ((size_t)b * N + i) * N;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+        const float dx = xi - f[j * 5 + 0], dy = yi - f[j * 5 + 1];
+        const float dr = ri - f[j * 5 + 2], dg = gi - f[j * 5 + 3], db = bi - f[j * 5 + 4];
+        const float p2 = dx * dx + dy * dy, c2 = dr * dr + dg * dg + db * db;
+        const float v = (j == i) ? 0.f : expf(-p2 * inv2p - c2 * inv2c);
+        row[j] = to_out<T>(v);
+    }
+}
+
+// q = exp(log q) as FP32 rows [B][N][LP] (padding 0) and, if qt16 is given,
+// BF16 label-major [B][32][N] (labels >= L zero) for the tensor-core form.
+__global__ void dense_export_q_kernel(const float *__restrict__ s, float *__restrict__ q32,
+                                      __nv_bfloat16 *__restrict__ qt16, int B, int N, int L, int LP) {
+    const long long n = (long long)B * N * LP;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int l = (int)(idx % LP);
+        const long long bi = idx / LP;
+        const int b = (int)(bi / N), i = (int)(bi % N);
+        const float q = l < L ? expf(s[idx]) : 0.f;
+        if (q32) q32[idx] = q;
+        if (qt16 && l < 32) qt16[((size_t)b * 32 + l) * N + i] = __float2bfloat16_rn(q);
+    }
+}
+
+// ---------------------------------------------------------------- step --
+
+struct DenseStepArgs {
+    const float *K;          // [B][N][N]
+    const float *q_in;       // [B][N][LP] q of the state read
+    const float *s_in;       // [B][N][LP] log q
+    const float *U;          // [B][N][LP]
+    float *s_out;            // [B][N][LP]
+    float *q_out;            // [B][N][LP] q of the new state (for the next step)
+    __nv_bfloat16 *qt_out;   // [B][32][N] BF16 copy of q_out (tensor-core form) or null
+    const float *eta;        // [B]
+    const float *mu;         // [L][L] device
+    double *partial;         // [B][nblk]
+    unsigned *counter;       // [B]
+    double *f_trace, *f_cur;
+    int *done, *status;
+    int N, L, nblk;
+    int t, trace_cap, update;
+    double rel_tol;
+};
+
+}  // namespace
+
+namespace {
+
+template <int LP>
+__global__ void __launch_bounds__(kDT, 1) dense_step_f32_kernel(const __grid_constant__ DenseStepArgs a) {
+    constexpr int NC = (LP + 5) / 6;             // column groups of 6 (last may be partial)
+    constexpr int CG = 4;                        // column groups handled by the thread grid
+    static_assert(NC <= CG, "LP <= 24");
+    __shared__ __align__(16) float Ks[2][kDK][kKsStride];
+    __shared__ __align__(16) float Qs[2][kDK][LP];
+    __shared__ __align__(16) float Sred[kDR][LP + 1];
+    __shared__ float mus[kMaxLabels * kMaxLabels];
+    __shared__ double red[kDT / 32];
+    __shared__ int is_last;
+
+    const int b = blockIdx.y;
+    const int tid = threadIdx.x;
+    const int N = a.N, L = a.L;
+    const int row0 = blockIdx.x * kDR;
+    const float *Kb = a.K + (size_t)b * N * N;
+    const float *qb = a.q_in + (size_t)b * N * LP;
+
+    if (a.done != nullptr && a.done[b] != 0) {
+        if (a.update)
+            for (int idx = tid; idx < kDR * LP; idx += kDT) {
+                const int r = row0 + idx / LP;
+                if (r < N) {
+                    const size_t o = ((size_t)b * N + r) * LP + idx % LP;
+                    a.s_out[o] = a.s_in[o];
+                    a.q_out[o] = a.q_in[o];
+                }
+            }
+        return;
+    }
+
+    for (int i = tid; i < L * L; i += kDT) mus[(i / L) * kMaxLabels + (i % L)] = a.mu[i];
+
+    // micro-tile: rows 4*ig .. 4*ig+3, label columns 6*cg .. 6*cg+5, k slice ks
+    const int ig = tid & 15, cg = (tid >> 4) & 3, ks = tid >> 6;
+    // loader mapping: warp w loads rows (w & 1)*32 + lane, k = 8*(w >> 1) .. +7
+    const int lw = tid >> 5, lane = tid & 31;
+    const int lrow = (lw & 1) * 32 + lane, lk = 8 * (lw >> 1);
+    const int grow = min(row0 + lrow, N - 1);
+    const float *ksrc = Kb + (size_t)grow * N + lk;
+
+    float2 acc[4][3];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[r][c] = splat2(0.f);
+
+    const int nchunk = (N + kDK - 1) / kDK;
+    // register ring of kDepth chunks in flight: chunk x lives in slot x % kDepth
+    constexpr int kDepth = 4;
+    float4 pa[kDepth], pb[kDepth], pq[kDepth];
+#pragma unroll
+    for (int d = 0; d < kDepth; ++d) pq[d] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool qloader = tid < kDK * LP / 4;
+    const int qk = qloader ? (tid * 4) / LP : 0, ql = qloader ? (tid * 4) % LP : 0;
+    auto load_chunk = [&](int c, float4 &ra, float4 &rb, float4 &rq) {
+        const int k0 = c * kDK;
+        if (k0 + lk + 8 <= N && (N % 4) == 0) {
+            ra = __ldg(reinterpret_cast<const float4 *>(ksrc + k0));
+            rb = __ldg(reinterpret_cast<const float4 *>(ksrc + k0) + 1);
+        } else {
+            float t[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) t[e] = (k0 + lk + e < N) ? __ldg(ksrc + k0 + e) : 0.f;
+            ra = make_float4(t[0], t[1], t[2], t[3]);
+            rb = make_float4(t[4], t[5], t[6], t[7]);
+        }
+        if (row0 + lrow >= N) ra = rb = make_float4(0.f, 0.f, 0.f, 0.f);
+        // q rows past N read the zero padding of the buffer (multiplied by K = 0)
+        if (qloader) rq = __ldg(reinterpret_cast<const float4 *>(qb + (size_t)(k0 + qk) * LP + ql));
+    };
+    auto store_chunk = [&](int buf, const float4 &ra, const float4 &rb, const float4 &rq) {
+        const float v[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+#pragma unroll
+        for (int e = 0; e < 8; ++e) Ks[buf][lk + e][lrow] = v[e];
+        if (qloader) *reinterpret_cast<float4 *>(&Qs[buf][qk][ql]) = rq;
+    };
+    auto compute_chunk = [&](int buf) {
+        if (cg >= NC) return;
+#pragma unroll
+        for (int kk = 0; kk < kDK / 4; ++kk) {
+            const int k = ks * (kDK / 4) + kk;
+            const float4 kv = *reinterpret_cast<const float4 *>(&Ks[buf][k][4 * ig]);
+            const float kr[4] = {kv.x, kv.y, kv.z, kv.w};
+            float2 qv[3];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                const int col = 6 * cg + 2 * p;
+                qv[p] = col + 1 < LP ? *reinterpret_cast<const float2 *>(&Qs[buf][k][col]) : splat2(0.f);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float2 kk2 = splat2(kr[r]);
+#pragma unroll
+                for (int p = 0; p < 3; ++p) acc[r][p] = fma2(kk2, qv[p], acc[r][p]);
+            }
+        }
+    };
+
+#pragma unroll
+    for (int d = 0; d < kDepth; ++d)
+        if (d < nchunk) load_chunk(d, pa[d], pb[d], pq[d]);
+    store_chunk(0, pa[0], pb[0], pq[0]);
+    __syncthreads();
+    for (int c = 0; c < nchunk; c += kDepth) {
+#pragma unroll
+        for (int d = 0; d < kDepth; ++d) {
+            const int cc = c + d;
+            if (cc < nchunk) {
+                compute_chunk(cc & 1);
+                constexpr int dummy = 0;
+                (void)dummy;
+                const int nx = (d + 1) % kDepth;
+                if (cc + 1 < nchunk) store_chunk((cc + 1) & 1, pa[nx], pb[nx], pq[nx]);
+                if (cc + kDepth < nchunk) load_chunk(cc + kDepth, pa[d], pb[d], pq[d]);
+                __syncthreads();
+            }
+        }
+    }
+
+    // reduce the four k slices: slice 0 writes, 1..3 add, in a fixed order
+    for (int sl = 0; sl < 4; ++sl) {
+        if (ks == sl && cg < NC) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    const int col = 6 * cg + 2 * p;
+                    if (col + 1 < LP) {
+                        float *d = &Sred[4 * ig + r][col];
+                        if (sl == 0) {
+                            d[0] = acc[r][p].x;
+                            d[1] = acc[r][p].y;
+                        } else {
+                            d[0] += acc[r][p].x;
+                            d[1] += acc[r][p].y;
+                        }
+                    }
+                }
+        }
+        __syncthreads();
+    }
+
+    // epilogue: one thread per row
+    float f = 0.f;
+    if (tid < kDR && row0 + tid < N) {
+        const int i = row0 + tid;
+        const size_t o = ((size_t)b * N + i) * LP;
+        f = dense_row_update<LP>(Sred[tid], mus, L, a.eta[b], a.s_in + o, a.U + o, a.s_out + o, a.q_out + o,
+                                 a.qt_out ? a.qt_out + (size_t)b * 32 * N + i : nullptr, (size_t)N,
+                                 a.update != 0);
+    }
+    double fd = (double)f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) fd += __shfl_down_sync(0xffffffffu, fd, off);
+    if ((tid & 31) == 0) red[tid >> 5] = fd;
+    __syncthreads();
+    if (tid == 0) {
+        double bs = 0.0;
+        for (int k = 0; k < kDT / 32; ++k) bs += red[k];
+        a.partial[(size_t)b * a.nblk + blockIdx.x] = bs;
+        __threadfence();
+        is_last = atomicAdd(a.counter + b, 1u) == (unsigned)(a.nblk - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (tid == 0) {
+        double F = 0.0;
+        for (int k = 0; k < a.nblk; ++k) F += __ldcg(a.partial + (size_t)b * a.nblk + k);
+        a.f_cur[b] = F;
+        if (!isfinite(F)) atomicExch(a.status, -6);
+        if (a.update) {
+            if (a.t < a.trace_cap) a.f_trace[(size_t)b * a.trace_cap + a.t] = F;
+            if (a.rel_tol > 0.0 && a.t > 0 && a.t - 1 < a.trace_cap && a.done != nullptr) {
+                const double Fp = a.f_trace[(size_t)b * a.trace_cap + a.t - 1];
+                if (fabs(F - Fp) <= a.rel_tol * fabs(F)) a.done[b] = a.t + 1;
+            }
+        }
+        a.counter[b] = 0u;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_dense_kernel_build(const float *feats, float *K32, __nv_bfloat16 *K16, int B, int N,
+                                      double theta_pos, double theta_rgb, cudaStream_t st) {
+    const float inv2p = (float)(1.0 / (2.0 * theta_pos * theta_pos));
+    const float inv2c = (float)(1.0 / (2.0 * theta_rgb * theta_rgb));
+    dim3 grid((N + 255) / 256 < 8 ? (N + 255) / 256 : 8, N, B);
+    if (K32) dense_kernel_build_kernel<float><<<grid, 256, 0, st>>>(feats, K32, N, inv2p, inv2c);
+    if (K16) dense_kernel_build_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(feats, K16, N, inv2p, inv2c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_export_q(const float *s, float *q32, __nv_bfloat16 *qt16, int B, int N, int L, int LP,
+                                  cudaStream_t st) {
+    const long long n = (long long)B * N * LP;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 1 << 20);
+    dense_export_q_kernel<<<blocks, 256, 0, st>>>(s, q32, qt16, B, N, L, LP);
+    return cudaGetLastError();
+}
+
+int dense_nblk(int N) { return (N + kDR - 1) / kDR; }
+
+cudaError_t launch_dense_step_f32(const DenseStepLaunch &l, cudaStream_t st) {
+    DenseStepArgs a;
+    a.K = l.K32;
+    a.q_in = l.q_in;
+    a.s_in = l.s_in;
+    a.U = l.U;
+    a.s_out = l.s_out;
+    a.q_out = l.q_out;
+    a.qt_out = l.qt_out;
+    a.eta = l.eta;
+    a.mu = l.mu;
+    a.partial = l.partial;
+    a.counter = l.counter;
+    a.f_trace = l.f_trace;
+    a.f_cur = l.f_cur;
+    a.done = l.done;
+    a.status = l.status;
+    a.N = l.N;
+    a.L = l.L;
+    a.nblk = dense_nblk(l.N);
+    a.t = l.t;
+    a.trace_cap = l.trace_cap;
+    a.update = l.update;
+    a.rel_tol = l.rel_tol;
+    dim3 grid(a.nblk, l.B);
+    switch (storage_labels(l.L)) {
+    case 2: dense_step_f32_kernel<2><<<grid, kDT, 0, st>>>(a); break;
+    case 4: dense_step_f32_kernel<4><<<grid, kDT, 0, st>>>(a); break;
+    case 8: dense_step_f32_kernel<8><<<grid, kDT, 0, st>>>(a); break;
+    case 12: dense_step_f32_kernel<12><<<grid, kDT, 0, st>>>(a); break;
+    case 16: dense_step_f32_kernel<16><<<grid, kDT, 0, st>>>(a); break;
+    case 20: dense_step_f32_kernel<20><<<grid, kDT, 0, st>>>(a); break;
+    case 24: dense_step_f32_kernel<24><<<grid, kDT, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace proxmf

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace proxmf {
@@ -90,10 +91,39 @@ cudaError_t launch_init_logq(const float *U, float *s, long long rows, int L, in
 // eta[b] = value for all b.
 cudaError_t launch_fill_eta(float *eta, int B, double value, cudaStream_t st);
 
+// Fully connected Gaussian model (dense.cu, dense_tc.cu).
+struct DenseStepLaunch {
+    const float *K32;            // [B][N][N] FP32 weights (FP32 form)
+    const __nv_bfloat16 *K16;    // [B][N][N] BF16 weights (tensor-core form)
+    const float *q_in;           // [B][N][LP] q of the state read
+    const __nv_bfloat16 *qt_in;  // [B][32][N] BF16 q, label-major (tensor-core form)
+    const float *s_in;           // [B][N][LP]
+    const float *U;              // [B][N][LP]
+    float *s_out;                // [B][N][LP]
+    float *q_out;                // [B][N][LP]
+    __nv_bfloat16 *qt_out;       // [B][32][N] or null
+    const float *eta;            // [B]
+    const float *mu;             // [L][L] device
+    double *partial;             // [B][dense_nblk(N)]
+    unsigned *counter;           // [B]
+    double *f_trace, *f_cur;
+    int *done, *status;
+    int B, N, L;
+    int t, trace_cap, update;
+    double rel_tol;
+};
+int dense_nblk(int N);
+cudaError_t launch_dense_kernel_build(const float *feats, float *K32, __nv_bfloat16 *K16, int B, int N,
+                                      double theta_pos, double theta_rgb, cudaStream_t st);
+cudaError_t launch_dense_export_q(const float *s, float *q32, __nv_bfloat16 *qt16, int B, int N, int L, int LP,
+                                  cudaStream_t st);
+cudaError_t launch_dense_step_f32(const DenseStepLaunch &a, cudaStream_t st);
+
 // Step-size constant (lanczos.cu).  Fills Lambda[b] (device, FP64) and
 // eta[b] = 1/(1+max(Lambda,0)) (device, FP32).  Returns CRF status codes.
 struct LipschitzJob {
     const float *w;          // pixel-major weights [B][N][n_dirs]
+    const float *Kdense;     // dense model: FP32 weights [B][N][N] (then H = 1, W = N)
     const float *mu_host;    // [L][L]
     bool mu_sym;
     int B, L, H, W, P, conn;

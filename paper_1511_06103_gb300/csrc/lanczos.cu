@@ -171,6 +171,35 @@ lz_step_a_scalar_kernel(LzState st, const float *__restrict__ w, LzGeom g) {
     if (instance_reduce(dot, st.partial, st.counter, b, g.nblk, &tot)) st.alpha[(size_t)b * st.ld + k] = tot;
 }
 
+// Dense scalar form: t = K v_k, one warp per row of the FP32 weight matrix
+// (FP64 accumulation); alpha_k from one partial per block.
+__global__ void __launch_bounds__(kLzThreads)
+lz_step_a_dense_kernel(LzState st, const float *__restrict__ K, LzGeom g, int nblk_a) {
+    const int b = blockIdx.y;
+    const int k = *st.kdev;
+    if (st.stop[b] || k >= st.ld - 1) return;
+    const int N = g.W;
+    const double *v = lz_buf(st, k % 3) + (size_t)b * N;
+    double *out = lz_buf(st, (k + 1) % 3) + (size_t)b * N;
+    const double inv = 1.0 / st.nrm[(size_t)b * st.ld + k];
+    const int row = blockIdx.x * (kLzThreads / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    double dot = 0.0;
+    if (row < N) {
+        const float *kr = K + ((size_t)b * N + row) * N;
+        double acc = 0.0;
+        for (int j = lane; j < N; j += 32) acc += (double)kr[j] * v[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const double r = acc * inv;
+        if (lane == 0) {
+            out[row] = r;
+            dot = r * v[row] * inv;
+        }
+    }
+    double tot;
+    if (instance_reduce(dot, st.partial, st.counter, b, nblk_a, &tot)) st.alpha[(size_t)b * st.ld + k] = tot;
+}
+
 // Full form (any mu): t = C H C v_k over N*L unknowns.
 __global__ void __launch_bounds__(kLzThreads)
 lz_step_a_kernel(LzState st, const float *__restrict__ w, const float *__restrict__ mu, LzGeom g) {
@@ -540,6 +569,7 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
     std::vector<int> hstop(B);
     int k = 0;
     dim3 gridp(g.nblk, B);
+    const int nblk_dense = (job.W + kLzThreads / 32 - 1) / (kLzThreads / 32);
     S.ld = ld;
     LZ_CHECK(cudaMallocAsync((void **)&S.R0, vec * sizeof(double), st));
     LZ_CHECK(cudaMallocAsync((void **)&S.R1, vec * sizeof(double), st));
@@ -548,7 +578,8 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
     LZ_CHECK(cudaMemsetAsync(S.R2, 0, vec * sizeof(double), st));
     LZ_CHECK(cudaMallocAsync((void **)&S.alpha, (size_t)B * ld * sizeof(double), st));
     LZ_CHECK(cudaMallocAsync((void **)&S.nrm, (size_t)B * (ld + 1) * sizeof(double), st));
-    LZ_CHECK(cudaMallocAsync((void **)&S.partial, (size_t)B * g.nblk * sizeof(double), st));
+    LZ_CHECK(cudaMallocAsync((void **)&S.partial,
+                             (size_t)B * (g.nblk + job.W / (kLzThreads / 32) + 1) * sizeof(double), st));
     LZ_CHECK(cudaMallocAsync((void **)&S.counter, (size_t)(B + 1) * sizeof(unsigned), st));
     LZ_CHECK(cudaMallocAsync((void **)&S.stop, (size_t)B * sizeof(int), st));
     LZ_CHECK(cudaMallocAsync((void **)&S.kdev, sizeof(int), st));
@@ -575,7 +606,9 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
     LZ_CHECK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     LZ_CHECK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < kChunk; ++i) {
-        if (g.Lv == 1)
+        if (job.Kdense)
+            lz_step_a_dense_kernel<<<dim3(nblk_dense, B), kLzThreads, 0, cap>>>(S, job.Kdense, g, nblk_dense);
+        else if (g.Lv == 1)
             lz_step_a_scalar_kernel<<<gridp, kLzThreads, 0, cap>>>(S, job.w, g);
         else
             lz_step_a_kernel<<<gridp, kLzThreads, 0, cap>>>(S, job.w, mu_dev, g);

@@ -1,0 +1,145 @@
+"""GPU parity of the fully connected (dense Gaussian kernel) path against the
+FP64 oracle, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1511_06103_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_Q_STEP = 1e-6
+TOL_Q = 1e-5
+TOL_F = 1e-6
+
+
+def f_close(F, F_ref, n_vars):
+    """|dF| <= 1e-6 max(|F|, N): see the grid tests for the floor."""
+    F, F_ref = np.asarray(F, np.float64), np.asarray(F_ref, np.float64)
+    return bool(np.all(np.abs(F - F_ref) <= TOL_F * np.maximum(np.abs(F_ref), n_vars)))
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    from paper_1511_06103_gb300 import binding, build
+    build.build()
+    import oracle
+    oracle.build()
+    return binding, oracle, torch
+
+
+def f64(a):
+    return np.asarray(a, np.float64)
+
+
+def oracle_model(oracle, d):
+    K = oracle.dense_gauss_kernel(f64(d["feats"]), *d["theta"])
+    return oracle.Model.dense(f64(d["U"]), f64(d["mu"]), K)
+
+
+def make(binding, d, batch=1):
+    side = int(round(math.sqrt(d["N"])))
+    return binding.CRF(binding.CRF_DENSE_GAUSS, d["L"], side, d["N"] // side, batch=batch)
+
+
+def gpu_run(binding, torch, d, eta, iters, s0=None):
+    dev = torch.device("cuda:0")
+    with make(binding, d) as crf:
+        crf.set_unary(torch.from_numpy(d["U"]).to(dev))
+        crf.set_pairwise(torch.from_numpy(d["mu"]).to(dev), torch.from_numpy(d["feats"]).to(dev),
+                         theta=np.array(d["theta"], np.float32))
+        if s0 is not None:
+            crf.set_state(torch.from_numpy(np.ascontiguousarray(s0, np.float32)).to(dev))
+        crf.iterate(iters, eta=eta)
+        s = crf.log_marginals()[0].astype(np.float64)
+        F = crf.free_energy()[0]
+        trace = crf.free_energy_trace(iters)[0] if iters > 0 else np.zeros(0)
+        torch.cuda.synchronize()
+        return s, F, trace
+
+
+@pytest.mark.parametrize("side,L", [(10, 2), (10, 3), (9, 5), (12, 8), (10, 21), (11, 24), (7, 1)])
+def test_dense_single_step_parity(env, side, L):
+    binding, oracle, torch = env
+    d = synth.dense_gaussian(side=side, L=L, seed=side * 31 + L)
+    s0 = synth.random_logq(d["N"], L, seed=3 + L)
+    m = oracle_model(oracle, d)
+    s_ref = m.prox_step(0.3, f64(s0))
+    F_ref = m.free_energy(np.exp(f64(s0)))
+    s, _, trace = gpu_run(binding, torch, d, 0.3, 1, s0=s0)
+    assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q_STEP
+    assert f_close(trace[0], F_ref, d["N"])
+
+
+def test_dense_trajectory_parity(env):
+    binding, oracle, torch = env
+    d = synth.dense_gaussian(side=16, L=21, seed=5)
+    m = oracle_model(oracle, d)
+    lam = m.hessian_eigenvalues(projected=True)[-1] if d["N"] * d["L"] <= 2048 else None
+    eta = 0.2 if lam is None else oracle.step_size(lam)
+    s_ref, F_ref = m.parallel_prox(eta, 30)
+    s, F, trace = gpu_run(binding, torch, d, eta, 30)
+    assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q
+    assert f_close(trace, F_ref[:-1], d["N"])
+    assert f_close(F, F_ref[-1], d["N"])
+
+
+def test_dense_full_size_first_step_sampled(env):
+    """N = 96 x 96 = 9216, L = 21 (the fully connected workload): one step from
+    q^0 = softmax(-U), compared on sampled variables, and F(q^0)."""
+    binding, oracle, torch = env
+    d = synth.dense_gaussian()
+    m = oracle_model(oracle, d)
+    s0 = m.init_logq()
+    rows = np.random.default_rng(0).choice(d["N"], size=64, replace=False)
+    eta = 0.05
+    s_ref = m.prox_step_rows(eta, s0, rows)
+    s, F, trace = gpu_run(binding, torch, d, eta, 1)
+    assert np.abs(np.exp(s[rows]) - np.exp(s_ref)).max() <= TOL_Q_STEP
+    F0 = m.free_energy(np.exp(s0))
+    assert f_close(trace[0], F0, d["N"])
+
+
+def test_dense_step_constant(env):
+    binding, oracle, torch = env
+    d = synth.dense_gaussian(side=6, L=4, seed=92)
+    d["mu"] = (3.0 * d["mu"]).astype(np.float32)
+    lam_ref = oracle_model(oracle, d).hessian_eigenvalues(projected=True)[-1]
+    with make(binding, d) as crf:
+        crf.set_unary(d["U"])
+        crf.set_pairwise(d["mu"], d["feats"], theta=np.array(d["theta"], np.float32))
+        lam, _ = crf.lipschitz()
+    # the device builds K in FP32: agreement to FP32 rounding of the weights
+    assert math.isclose(lam[0], lam_ref, rel_tol=2e-6)
+
+
+def test_dense_batch_independent(env):
+    binding, oracle, torch = env
+    ds = [synth.dense_gaussian(side=8, L=5, seed=40 + i) for i in range(2)]
+    for d in ds:
+        d["mu"] = ds[0]["mu"]
+    with binding.CRF(binding.CRF_DENSE_GAUSS, 5, 8, 8, batch=2) as crf:
+        crf.set_unary(np.stack([d["U"] for d in ds]))
+        crf.set_pairwise(ds[0]["mu"], np.stack([d["feats"] for d in ds]), theta=np.array(ds[0]["theta"], np.float32))
+        crf.iterate(10, eta=0.3)
+        sb = crf.log_marginals()
+    for i, d in enumerate(ds):
+        s, _, _ = gpu_run(binding, torch, d, 0.3, 10)
+        assert np.array_equal(sb[i].astype(np.float64), s)
+
+
+def test_dense_rejects_asymmetric_mu(env):
+    binding, oracle, torch = env
+    d = synth.dense_gaussian(side=4, L=3, seed=1)
+    mu = d["mu"].copy()
+    mu[0, 1] += 0.5
+    with make(binding, d) as crf:
+        crf.set_unary(d["U"])
+        with pytest.raises(binding.ProxMFError) as e:
+            crf.set_pairwise(mu, d["feats"], theta=np.array(d["theta"], np.float32))
+        assert e.value.status == -1

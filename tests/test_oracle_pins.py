@@ -341,3 +341,14 @@ def test_normalisation(oracle_mod):
     q = np.exp(s)
     assert np.all(q >= 0)
     assert np.max(np.abs(q.sum(axis=1) - 1)) <= 1e-12
+
+
+def test_step_rows_matches_full_step(oracle_mod):
+    """The row-subset step is the full step restricted to those rows."""
+    d = synth.dense_gaussian(side=5, L=3, seed=97)
+    K = oracle_mod.dense_gauss_kernel(_f64(d, "feats"), *d["theta"])
+    m = oracle_mod.Model.dense(_f64(d, "U"), _f64(d, "mu"), K)
+    s0 = np.log(renorm(random_q(25, 3, 98)))
+    full = m.prox_step(0.4, s0)
+    rows = np.array([0, 7, 24, 13])
+    assert np.array_equal(m.prox_step_rows(0.4, s0, rows), full[rows])
