@@ -59,7 +59,9 @@ typedef enum {
 
 typedef enum {
     CRF_FP32 = 0,           /* FP32 messages, FP32 state                     */
-    CRF_BF16 = 1            /* BF16 tensor-core messages, FP32 state         */
+    CRF_BF16 = 1            /* BF16 tensor-core messages, FP32 state (fully  */
+                            /* connected models); free energies are always   */
+                            /* evaluated with FP32 messages                  */
 } crf_precision;
 
 typedef struct {
@@ -114,7 +116,8 @@ typedef struct {
     double rel_tol;         /* > 0: instance b stops after the step at which    */
                             /* |F^t - F^{t-1}| <= rel_tol |F^t| (stopping rule  */
                             /* on the objective, Sec. 3.1); 0: fixed count      */
-    int32_t refine_fp32;    /* BF16 form: extra FP32 iterations at the end      */
+    int32_t refine_fp32;    /* BF16 form: FP32 iterations run after max_iters   */
+                            /* (counted in iters_done and the F trace)          */
     int32_t final_free_energy; /* 1: also evaluate F(q^K) on the device at the */
                             /* end (mf_free_energy then returns it without a    */
                             /* recomputation); no host synchronisation          */

@@ -33,6 +33,8 @@ struct crf_s {
     float *feats = nullptr;      // [B][N][5]
     float *mu_dev = nullptr;     // [L][L]
     double theta[2] = {0.0, 0.0};
+    bool bf16 = false;           // tensor-core form
+    DenseTcBuffers tcb{nullptr, nullptr};
     float *eta_fixed = nullptr;  // [B]
     float *eta_auto = nullptr;   // [B]
     double *Lambda = nullptr;    // [B]
@@ -100,6 +102,8 @@ void free_all(crf_t h) {
     __nv_bfloat16 *bd[] = {h->K16, h->qt16[0], h->qt16[1]};
     for (__nv_bfloat16 *p : bd)
         if (p) cudaFree(p);
+    if (h->tcb.split_part) cudaFree(h->tcb.split_part);
+    if (h->tcb.tile_count) cudaFree(h->tcb.tile_count);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
 }
@@ -185,11 +189,14 @@ DenseStepLaunch dense_args(crf_t h, const float *eta, int t, int update, double 
     return a;
 }
 
-// One step (update = 1) or a free-energy-only pass (update = 0) of either model.
-cudaError_t launch_step(crf_t h, const float *eta, int t, int update, double rel_tol) {
+// One step (update = 1) or a free-energy-only pass (update = 0) of either
+// model.  fp32 = 1 forces the FP32 form (refinement steps, and every
+// free-energy-only pass, which is evaluated with FP32 messages).
+cudaError_t launch_step(crf_t h, const float *eta, int t, int update, double rel_tol, int fp32 = 0) {
     if (h->dense) {
         DenseStepLaunch a = dense_args(h, eta, t, update, rel_tol);
         if (!update || rel_tol <= 0) a.done = nullptr;
+        if (h->bf16 && update && !fp32) return launch_dense_step_tc(a, h->tcb, h->st);
         return launch_dense_step_f32(a, h->st);
     }
     GridStepLaunch a = step_args(h, eta, t, update, rel_tol);
@@ -305,8 +312,8 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
     if (d.precision != CRF_FP32 && d.precision != CRF_BF16) return CRF_E_INVALID;
     if (d.topology != CRF_GRID4 && d.topology != CRF_GRID8 && d.topology != CRF_DENSE_GAUSS)
         return CRF_E_INVALID;
-    if (d.precision == CRF_BF16) return CRF_E_UNSUPPORTED;
     const bool dense = d.topology == CRF_DENSE_GAUSS;
+    if (d.precision == CRF_BF16 && !dense) return CRF_E_UNSUPPORTED;
     if (dense) {
         // the dense step keeps up to 24 labels per row; N x N weights per instance
         if (d.n_labels > 24) return CRF_E_UNSUPPORTED;
@@ -357,6 +364,20 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
         if (ok) {
             ok = cudaMemsetAsync(h->q32[0], 0, qn * sizeof(float), h->st) == cudaSuccess &&
                  cudaMemsetAsync(h->q32[1], 0, qn * sizeof(float), h->st) == cudaSuccess;
+        }
+        if (ok && d.precision == CRF_BF16) {
+            h->bf16 = true;
+            const size_t pitch = dense_tc_pitch(h->N);
+            const size_t tiles = (size_t)h->B * dense_tc_tiles(h->N);
+            ok = ok && dalloc(&h->K16, (size_t)h->B * h->N * pitch) == cudaSuccess;
+            ok = ok && dalloc(&h->qt16[0], (size_t)h->B * 32 * pitch) == cudaSuccess;
+            ok = ok && dalloc(&h->qt16[1], (size_t)h->B * 32 * pitch) == cudaSuccess;
+            ok = ok && dalloc(&h->tcb.split_part, tiles * 2 * 128 * 32) == cudaSuccess;
+            ok = ok && dalloc(&h->tcb.tile_count, tiles) == cudaSuccess;
+            if (ok)
+                ok = cudaMemsetAsync(h->qt16[0], 0, (size_t)h->B * 32 * pitch * 2, h->st) == cudaSuccess &&
+                     cudaMemsetAsync(h->qt16[1], 0, (size_t)h->B * 32 * pitch * 2, h->st) == cudaSuccess &&
+                     cudaMemsetAsync(h->tcb.tile_count, 0, tiles * sizeof(unsigned), h->st) == cudaSuccess;
         }
     }
     ok = ok && dalloc(&h->mu_pairs, (size_t)2 * h->LT * mu_pair_slots(h->LT)) == cudaSuccess;
@@ -561,24 +582,26 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
         h->launches++;
         CK(h, refresh_q(h));
     }
-    rc = ensure_trace(h, p->max_iters);
+    const int refine = (h->bf16 && p->refine_fp32 > 0) ? p->refine_fp32 : 0;
+    if (p->refine_fp32 < 0) return CRF_E_INVALID;
+    rc = ensure_trace(h, p->max_iters + refine);
     if (rc != CRF_OK) return rc;
     if (p->rel_tol > 0) CK(h, cudaMemsetAsync(h->done, 0, h->B * sizeof(int), h->st));
     if (h->profile) CK(h, cudaEventRecord(h->ev0, h->st));
-    for (int t = 0; t < p->max_iters; ++t) {
-        CK(h, launch_step(h, eta, t, 1, p->rel_tol));
+    for (int t = 0; t < p->max_iters + refine; ++t) {
+        CK(h, launch_step(h, eta, t, 1, p->rel_tol, t >= p->max_iters));
         h->cur ^= 1;
     }
-    h->launches += p->max_iters;
+    h->launches += p->max_iters + refine;
     if (h->profile) {
         CK(h, cudaEventRecord(h->ev1, h->st));
-        h->prof_launches = p->max_iters;
+        h->prof_launches = p->max_iters + refine;
         h->prof_valid = true;
     }
-    h->last_iters = p->max_iters;
+    h->last_iters = p->max_iters + refine;
     h->fcur_valid = false;
     if (p->final_free_energy) {
-        CK(h, launch_step(h, eta, 0, 0, 0.0));
+        CK(h, launch_step(h, eta, 0, 0, 0.0, 1));
         h->launches++;
         h->fcur_valid = true;
     }
@@ -586,7 +609,7 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
         std::vector<int> dn(h->B);
         CK(h, cudaMemcpyAsync(dn.data(), h->done, h->B * sizeof(int), cudaMemcpyDeviceToHost, h->st));
         CK(h, cudaStreamSynchronize(h->st));
-        for (int b = 0; b < h->B; ++b) iters_done[b] = dn[b] ? dn[b] : p->max_iters;
+        for (int b = 0; b < h->B; ++b) iters_done[b] = dn[b] ? dn[b] : p->max_iters + refine;
     }
     return CRF_OK;
 }
@@ -598,7 +621,7 @@ crf_status mf_free_energy(crf_t h, double *F) {
     if (!h->has_unary || !h->has_pairwise) return CRF_E_INVALID;
     if (!h->fcur_valid) {
         CK(h, launch_fill_eta(h->eta_fixed, h->B, 1.0, h->st));
-        CK(h, launch_step(h, h->eta_fixed, 0, 0, 0.0));
+        CK(h, launch_step(h, h->eta_fixed, 0, 0, 0.0, 1));
         h->launches += 2;
         h->fcur_valid = true;
     }

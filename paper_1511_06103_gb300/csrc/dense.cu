@@ -46,14 +46,18 @@ __device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16>(float v) { return
 
 // K[b][i][j] from features [b][N][5]; one thread per (i, 4 consecutive j).
 template <typename T>
-__global__ void dense_kernel_build_kernel(const float *__restrict__ feats, T *__restrict__ K, int N,
+__global__ void dense_kernel_build_kernel(const float *__restrict__ feats, T *__restrict__ K, int N, int pitch,
                                           float inv2p, float inv2c) {
     const int b = blockIdx.z;
     const int i = blockIdx.y;
     const float *f = feats + (size_t)b * N * 5;
     const float xi = f[i * 5 + 0], yi = f[i * 5 + 1], ri = f[i * 5 + 2], gi = f[i * 5 + 3], bi = f[i * 5 + 4];
-    T *row = K + ((size_t)b * N + i) * N;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+    T *row = K + ((size_t)b * N + i) * pitch;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < pitch; j += gridDim.x * blockDim.x) {
+        if (j >= N) {
+            row[j] = to_out<T>(0.f);
+            continue;
+        }
         const float dx = xi - f[j * 5 + 0], dy = yi - f[j * 5 + 1];
         const float dr = ri - f[j * 5 + 2], dg = gi - f[j * 5 + 3], db = bi - f[j * 5 + 4];
         const float p2 = dx * dx + dy * dy, c2 = dr * dr + dg * dg + db * db;
@@ -63,9 +67,9 @@ __global__ void dense_kernel_build_kernel(const float *__restrict__ feats, T *__
 }
 
 // q = exp(log q) as FP32 rows [B][N][LP] (padding 0) and, if qt16 is given,
-// BF16 label-major [B][32][N] (labels >= L zero) for the tensor-core form.
+// BF16 label-major [B][32][pitch] (labels >= L zero) for the tensor-core form.
 __global__ void dense_export_q_kernel(const float *__restrict__ s, float *__restrict__ q32,
-                                      __nv_bfloat16 *__restrict__ qt16, int B, int N, int L, int LP) {
+                                      __nv_bfloat16 *__restrict__ qt16, int B, int N, int L, int LP, int pitch) {
     const long long n = (long long)B * N * LP;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -74,7 +78,7 @@ __global__ void dense_export_q_kernel(const float *__restrict__ s, float *__rest
         const int b = (int)(bi / N), i = (int)(bi % N);
         const float q = l < L ? expf(s[idx]) : 0.f;
         if (q32) q32[idx] = q;
-        if (qt16 && l < 32) qt16[((size_t)b * 32 + l) * N + i] = __float2bfloat16_rn(q);
+        if (qt16 && l < 32) qt16[((size_t)b * 32 + l) * pitch + i] = __float2bfloat16_rn(q);
     }
 }
 
@@ -87,14 +91,14 @@ struct DenseStepArgs {
     const float *U;          // [B][N][LP]
     float *s_out;            // [B][N][LP]
     float *q_out;            // [B][N][LP] q of the new state (for the next step)
-    __nv_bfloat16 *qt_out;   // [B][32][N] BF16 copy of q_out (tensor-core form) or null
+    __nv_bfloat16 *qt_out;   // [B][32][pitch] BF16 copy of q_out (tensor-core form) or null
     const float *eta;        // [B]
     const float *mu;         // [L][L] device
     double *partial;         // [B][nblk]
     unsigned *counter;       // [B]
     double *f_trace, *f_cur;
     int *done, *status;
-    int N, L, nblk;
+    int N, L, nblk, pitch;
     int t, trace_cap, update;
     double rel_tol;
 };
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(kDT, 1) dense_step_f32_kernel(const __grid_con
         const int i = row0 + tid;
         const size_t o = ((size_t)b * N + i) * LP;
         f = dense_row_update<LP>(Sred[tid], mus, L, a.eta[b], a.s_in + o, a.U + o, a.s_out + o, a.q_out + o,
-                                 a.qt_out ? a.qt_out + (size_t)b * 32 * N + i : nullptr, (size_t)N,
+                                 a.qt_out ? a.qt_out + (size_t)b * 32 * a.pitch + i : nullptr, (size_t)a.pitch,
                                  a.update != 0);
     }
     double fd = (double)f;
@@ -294,8 +298,9 @@ cudaError_t launch_dense_kernel_build(const float *feats, float *K32, __nv_bfloa
     const float inv2p = (float)(1.0 / (2.0 * theta_pos * theta_pos));
     const float inv2c = (float)(1.0 / (2.0 * theta_rgb * theta_rgb));
     dim3 grid((N + 255) / 256 < 8 ? (N + 255) / 256 : 8, N, B);
-    if (K32) dense_kernel_build_kernel<float><<<grid, 256, 0, st>>>(feats, K32, N, inv2p, inv2c);
-    if (K16) dense_kernel_build_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(feats, K16, N, inv2p, inv2c);
+    if (K32) dense_kernel_build_kernel<float><<<grid, 256, 0, st>>>(feats, K32, N, N, inv2p, inv2c);
+    if (K16)
+        dense_kernel_build_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(feats, K16, N, dense_tc_pitch(N), inv2p, inv2c);
     return cudaGetLastError();
 }
 
@@ -303,7 +308,7 @@ cudaError_t launch_dense_export_q(const float *s, float *q32, __nv_bfloat16 *qt1
                                   cudaStream_t st) {
     const long long n = (long long)B * N * LP;
     const int blocks = (int)std::min<long long>((n + 255) / 256, 1 << 20);
-    dense_export_q_kernel<<<blocks, 256, 0, st>>>(s, q32, qt16, B, N, L, LP);
+    dense_export_q_kernel<<<blocks, 256, 0, st>>>(s, q32, qt16, B, N, L, LP, dense_tc_pitch(N));
     return cudaGetLastError();
 }
 
@@ -329,6 +334,7 @@ cudaError_t launch_dense_step_f32(const DenseStepLaunch &l, cudaStream_t st) {
     a.N = l.N;
     a.L = l.L;
     a.nblk = dense_nblk(l.N);
+    a.pitch = dense_tc_pitch(l.N);
     a.t = l.t;
     a.trace_cap = l.trace_cap;
     a.update = l.update;

@@ -1,0 +1,410 @@
+// dense_tc.cu -- tensor-core (tcgen05) form of the fully connected step.
+//
+// The message S = K Q of the dense model is an (N x N) by (N x L) product:
+// here K and Q are BF16 and the product runs on the 5th-generation tensor
+// cores with FP32 accumulation in tensor memory (TMEM); the proximal update,
+// renormalisation and free energy stay in FP32 (dense_common.cuh).
+//
+// Per CTA: one tile of M = 128 rows of K, all 32 label columns (L padded),
+// and half of the k range (split-K 2, so N = 9216 gives 144 CTAs for the 152
+// SMs).  Warp 0 lane 0 issues TMA loads of 128 x 64 BF16 tiles of K and
+// 32 x 64 tiles of Q^T (both K-major, 128-byte swizzle) into a 6-stage ring
+// guarded by mbarriers; warp 1 lane 0 issues tcgen05.mma (M=128, N=32, K=16,
+// kind::f16) into a 32-column TMEM accumulator and releases each stage with
+// tcgen05.commit.  The four warps then read the accumulator rows with
+// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31).  The two k-halves of a
+// tile meet in global memory: the second CTA to finish adds the first one's
+// partial (a + b is commutative, so the result does not depend on which one
+// finishes first) and runs the row epilogue for the tile's 128 rows.
+//
+// Every wait is bounded by a clock budget; on expiry the kernel records
+// CRF_E_TIMEOUT, drains its own copies in flight (bounded), frees its TMEM
+// and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "dense_common.cuh"
+#include "internal.h"
+
+namespace proxmf {
+
+namespace {
+
+constexpr int kTM = 128;                 // rows per tile (MMA M)
+constexpr int kTN = 32;                  // label columns (MMA N)
+constexpr int kTK = 64;                  // k per stage (128 bytes of BF16)
+constexpr int kStages = 6;
+constexpr int kStageA = kTM * kTK * 2;   // 16 KiB
+constexpr int kStageB = kTN * kTK * 2;   // 4 KiB
+constexpr int kStageBytes = kStageA + kStageB;
+constexpr int kThreads = 128;
+constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false (and CRF_E_TIMEOUT recorded) on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) {
+            atomicExch(status, -5);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand in 128-byte swizzle, 8-row
+// atoms of 1024 bytes (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(16 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major,
+// N = 32, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
+                            ((uint32_t)(kTM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+          "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct DenseTcArgs {
+    const float *s_in;
+    const float *U;
+    float *s_out;
+    float *q_out;
+    __nv_bfloat16 *qt_out;
+    const float *eta;
+    const float *mu;
+    float *split_part;       // [B][ntiles][2][128][32]
+    unsigned *tile_count;    // [B][ntiles]
+    double *partial;         // [B][ntiles]
+    unsigned *counter;       // [B]
+    double *f_trace, *f_cur;
+    int *done, *status;
+    int N, Np, L, ntiles, nchunk;
+    int t, trace_cap, update;
+    double rel_tol;
+};
+
+template <int LP>
+__global__ void __launch_bounds__(kThreads, 1)
+dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmK, const __grid_constant__ CUtensorMap tmQ,
+                     const __grid_constant__ DenseTcArgs a) {
+    extern __shared__ __align__(1024) uint8_t dsm[];
+    __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], tmem_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ float mus[kMaxLabels * kMaxLabels];
+    __shared__ double red[kThreads / 32];
+    __shared__ int is_second, is_last, abort_flag;
+
+    const int tile = blockIdx.x, split = blockIdx.y, b = blockIdx.z;
+    const int nsplit = gridDim.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const int N = a.N, L = a.L;
+    const int row0 = tile * kTM;
+    // k range of this CTA
+    const int c_begin = (a.nchunk * split) / nsplit, c_end = (a.nchunk * (split + 1)) / nsplit;
+    const int nc = c_end - c_begin;
+
+    if (a.done != nullptr && a.done[b] != 0) {
+        // stopping rule met: carry the state through (split 0 copies)
+        if (a.update && split == 0)
+            for (int idx = tid; idx < kTM * LP; idx += kThreads) {
+                const int r = row0 + idx / LP;
+                if (r < N) {
+                    const size_t o = ((size_t)b * N + r) * LP + idx % LP;
+                    a.s_out[o] = a.s_in[o];
+                    const float q = idx % LP < L ? __expf(a.s_in[o]) : 0.f;
+                    a.q_out[o] = q;
+                    if (a.qt_out) a.qt_out[((size_t)b * 32 + idx % LP) * a.Np + r] = __float2bfloat16_rn(q);
+                }
+            }
+        return;
+    }
+
+    uint8_t *ring = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
+    for (int i = tid; i < L * L; i += kThreads) mus[(i / L) * kMaxLabels + (i % L)] = a.mu[i];
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&tmem_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kTN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0 && lane == 0 && nc > 0) {
+        // producer: TMA loads into the ring
+        int issued = 0;
+        for (int c = 0; c < nc; ++c) {
+            const int s = c % kStages;
+            if (c >= kStages && !mbar_wait(&empty_bar[s], ((c / kStages) - 1) & 1, a.status)) break;
+            if (abort_flag) break;
+            uint8_t *sa = ring + s * kStageBytes;
+            mbar_expect_tx(&full_bar[s], kStageBytes);
+            const int kc = (c_begin + c) * kTK;
+            tma_load_2d(sa, &tmK, &full_bar[s], kc, b * N + row0);
+            tma_load_2d(sa + kStageA, &tmQ, &full_bar[s], kc, b * 32);
+            ++issued;
+        }
+        if (issued < nc) {
+            abort_flag = 1;
+            // drain: wait (bounded) for the copies already issued
+            for (int c = (issued > kStages ? issued - kStages : 0); c < issued; ++c)
+                mbar_wait(&full_bar[c % kStages], (c / kStages) & 1, a.status);
+        }
+    } else if (warp == 1 && lane == 0 && nc > 0) {
+        // MMA issuer
+        int c = 0;
+        for (; c < nc; ++c) {
+            const int s = c % kStages;
+            if (!mbar_wait(&full_bar[s], (c / kStages) & 1, a.status)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = smem_u32(ring + s * kStageBytes);
+            const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + kStageA);
+#pragma unroll
+            for (int kk = 0; kk < kTK / 16; ++kk)
+                mma_bf16(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), (c > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(&empty_bar[s]);
+        }
+        if (c < nc) abort_flag = 1;
+        mma_commit(&tmem_bar);
+    }
+    __syncwarp();
+
+    // epilogue: this thread's row of the partial sum
+    float S[32];
+    bool ok = true;
+    if (nc > 0) {
+        ok = mbar_wait(&tmem_bar, 0, a.status) && !abort_flag;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok) tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), S);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) S[i] = 0.f;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTN));
+    if (!ok || abort_flag) return;
+
+    const int r = warp * 32 + lane;   // row within the tile
+    const size_t tile_id = (size_t)b * a.ntiles + tile;
+    if (nsplit > 1) {
+        float *mine = a.split_part + ((tile_id * 2 + split) * kTM + r) * 32;
+#pragma unroll
+        for (int i = 0; i < 32; i += 4) *reinterpret_cast<float4 *>(mine + i) = make_float4(S[i], S[i + 1], S[i + 2], S[i + 3]);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) is_second = atomicAdd(a.tile_count + tile_id, 1u) == 1u;
+        __syncthreads();
+        if (!is_second) return;
+        __threadfence();
+        const float *other = a.split_part + ((tile_id * 2 + (split ^ 1)) * kTM + r) * 32;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) S[i] += __ldcg(other + i);
+        if (tid == 0) a.tile_count[tile_id] = 0u;
+    }
+
+    // row epilogue on the tile's rows
+    float f = 0.f;
+    const int i = row0 + r;
+    if (i < N) {
+        const size_t o = ((size_t)b * N + i) * LP;
+        f = dense_row_update<LP>(S, mus, L, a.eta[b], a.s_in + o, a.U + o, a.s_out + o, a.q_out + o,
+                                 a.qt_out ? a.qt_out + (size_t)b * 32 * a.Np + i : nullptr, (size_t)a.Np,
+                                 a.update != 0);
+    }
+    double fd = (double)f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) fd += __shfl_down_sync(0xffffffffu, fd, off);
+    if (lane == 0) red[warp] = fd;
+    __syncthreads();
+    if (tid == 0) {
+        double bs = 0.0;
+        for (int k = 0; k < kThreads / 32; ++k) bs += red[k];
+        a.partial[(size_t)b * a.ntiles + tile] = bs;
+        __threadfence();
+        is_last = atomicAdd(a.counter + b, 1u) == (unsigned)(a.ntiles - 1);
+    }
+    __syncthreads();
+    if (!is_last || tid != 0) return;
+    __threadfence();
+    double F = 0.0;
+    for (int k = 0; k < a.ntiles; ++k) F += __ldcg(a.partial + (size_t)b * a.ntiles + k);
+    a.f_cur[b] = F;
+    if (!isfinite(F)) atomicExch(a.status, -6);
+    if (a.update) {
+        if (a.t < a.trace_cap) a.f_trace[(size_t)b * a.trace_cap + a.t] = F;
+        if (a.rel_tol > 0.0 && a.t > 0 && a.t - 1 < a.trace_cap && a.done != nullptr) {
+            const double Fp = a.f_trace[(size_t)b * a.trace_cap + a.t - 1];
+            if (fabs(F - Fp) <= a.rel_tol * fabs(F)) a.done[b] = a.t + 1;
+        }
+    }
+    a.counter[b] = 0u;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+cudaError_t get_encoder() {
+    if (g_encode) return cudaSuccess;
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return cudaSuccess;
+}
+
+// 2-D BF16 view [rows][Np] with a box of box_rows x 64 and 128-byte swizzle.
+cudaError_t encode_2d(CUtensorMap *map, const void *base, long long rows, int Np, int box_rows) {
+    cudaError_t e = get_encoder();
+    if (e != cudaSuccess) return e;
+    cuuint64_t dims[2] = {(cuuint64_t)Np, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)Np * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+int dense_tc_tiles(int N) { return (N + kTM - 1) / kTM; }
+int dense_tc_pitch(int N) { return (N + kTK - 1) / kTK * kTK; }
+
+cudaError_t launch_dense_step_tc(const DenseStepLaunch &l, const DenseTcBuffers &tb, cudaStream_t st) {
+    CUtensorMap tmK, tmQ;
+    const int Np = dense_tc_pitch(l.N);
+    cudaError_t e = encode_2d(&tmK, l.K16, (long long)l.B * l.N, Np, kTM);
+    if (e != cudaSuccess) return e;
+    e = encode_2d(&tmQ, l.qt_in, (long long)l.B * 32, Np, kTN);
+    if (e != cudaSuccess) return e;
+    DenseTcArgs a;
+    a.s_in = l.s_in;
+    a.U = l.U;
+    a.s_out = l.s_out;
+    a.q_out = l.q_out;
+    a.qt_out = l.qt_out;
+    a.eta = l.eta;
+    a.mu = l.mu;
+    a.split_part = tb.split_part;
+    a.tile_count = tb.tile_count;
+    a.partial = l.partial;
+    a.counter = l.counter;
+    a.f_trace = l.f_trace;
+    a.f_cur = l.f_cur;
+    a.done = l.done;
+    a.status = l.status;
+    a.N = l.N;
+    a.Np = Np;
+    a.L = l.L;
+    a.ntiles = dense_tc_tiles(l.N);
+    a.nchunk = Np / kTK;
+    a.t = l.t;
+    a.trace_cap = l.trace_cap;
+    a.update = l.update;
+    a.rel_tol = l.rel_tol;
+    const int nsplit = a.nchunk >= 2 ? 2 : 1;
+    dim3 grid(a.ntiles, nsplit, l.B);
+    const size_t smem = (size_t)kStages * kStageBytes + 1024;
+    switch (storage_labels(l.L)) {
+#define PROXMF_TC_CASE(LPV)                                                                                   \
+    case LPV:                                                                                                 \
+        e = cudaFuncSetAttribute(dense_step_tc_kernel<LPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                       \
+        dense_step_tc_kernel<LPV><<<grid, kThreads, smem, st>>>(tmK, tmQ, a);                                 \
+        break;
+        PROXMF_TC_CASE(2)
+        PROXMF_TC_CASE(4)
+        PROXMF_TC_CASE(8)
+        PROXMF_TC_CASE(12)
+        PROXMF_TC_CASE(16)
+        PROXMF_TC_CASE(20)
+        PROXMF_TC_CASE(24)
+#undef PROXMF_TC_CASE
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace proxmf

@@ -113,11 +113,20 @@ struct DenseStepLaunch {
     double rel_tol;
 };
 int dense_nblk(int N);
+int dense_tc_tiles(int N);
+int dense_tc_pitch(int N);   // row pitch (elements) of the BF16 K and q^T copies
+// K32 [B][N][N] and/or K16 [B][N][pitch] (padding columns zero)
 cudaError_t launch_dense_kernel_build(const float *feats, float *K32, __nv_bfloat16 *K16, int B, int N,
                                       double theta_pos, double theta_rgb, cudaStream_t st);
+// q = exp(s): FP32 [B][N][LP] and/or BF16 label-major [B][32][pitch]
 cudaError_t launch_dense_export_q(const float *s, float *q32, __nv_bfloat16 *qt16, int B, int N, int L, int LP,
                                   cudaStream_t st);
 cudaError_t launch_dense_step_f32(const DenseStepLaunch &a, cudaStream_t st);
+struct DenseTcBuffers {
+    float *split_part;       // [B][tiles][2][128][32] split-K partial sums
+    unsigned *tile_count;    // [B][tiles] (zero, self-resetting)
+};
+cudaError_t launch_dense_step_tc(const DenseStepLaunch &a, const DenseTcBuffers &tb, cudaStream_t st);
 
 // Step-size constant (lanczos.cu).  Fills Lambda[b] (device, FP64) and
 // eta[b] = 1/(1+max(Lambda,0)) (device, FP32).  Returns CRF status codes.

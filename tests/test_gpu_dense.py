@@ -143,3 +143,66 @@ def test_dense_rejects_asymmetric_mu(env):
         with pytest.raises(binding.ProxMFError) as e:
             crf.set_pairwise(mu, d["feats"], theta=np.array(d["theta"], np.float32))
         assert e.value.status == -1
+
+
+# ---------------------------------------------------------------- BF16 form
+# BF16 tensor-core messages, FP32 state; tolerances after FP32 refinement:
+# |dq|max <= 1e-2 and |dF|/|F| <= 1e-3.
+
+TOL_Q_BF16 = 1e-2
+TOL_F_BF16 = 1e-3
+
+
+def gpu_run_bf16(binding, torch, d, eta, iters, refine=0, s0=None):
+    dev = torch.device("cuda:0")
+    side = int(round(math.sqrt(d["N"])))
+    with binding.CRF(binding.CRF_DENSE_GAUSS, d["L"], side, d["N"] // side, precision=binding.CRF_BF16) as crf:
+        crf.set_unary(torch.from_numpy(d["U"]).to(dev))
+        crf.set_pairwise(torch.from_numpy(d["mu"]).to(dev), torch.from_numpy(d["feats"]).to(dev),
+                         theta=np.array(d["theta"], np.float32))
+        if s0 is not None:
+            crf.set_state(torch.from_numpy(np.ascontiguousarray(s0, np.float32)).to(dev))
+        crf.iterate(iters, eta=eta, refine_fp32=refine)
+        s = crf.log_marginals()[0].astype(np.float64)
+        F = crf.free_energy()[0]
+        trace = crf.free_energy_trace(iters + refine)[0]
+        torch.cuda.synchronize()
+        return s, F, trace
+
+
+@pytest.mark.parametrize("side,L", [(10, 21), (12, 5), (9, 2)])
+def test_dense_bf16_single_step(env, side, L):
+    binding, oracle, torch = env
+    d = synth.dense_gaussian(side=side, L=L, seed=side * 7 + L)
+    s0 = synth.random_logq(d["N"], L, seed=11 + L)
+    m = oracle_model(oracle, d)
+    s_ref = m.prox_step(0.3, f64(s0))
+    s, _, _ = gpu_run_bf16(binding, torch, d, 0.3, 1, s0=s0)
+    assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q_BF16
+    assert np.all(np.isfinite(s))
+
+
+def test_dense_bf16_trajectory_refined(env):
+    binding, oracle, torch = env
+    d = synth.dense_gaussian(side=16, L=21, seed=5)
+    m = oracle_model(oracle, d)
+    s_ref, F_ref = m.parallel_prox(0.2, 35)
+    s, F, trace = gpu_run_bf16(binding, torch, d, 0.2, 30, refine=5)
+    assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q_BF16
+    assert abs(F - F_ref[-1]) <= TOL_F_BF16 * max(abs(F_ref[-1]), d["N"])
+
+
+def test_dense_bf16_full_size_sampled(env):
+    """N = 9216, L = 21: one BF16 step from q^0 on sampled rows, and the
+    tensor-core run is deterministic."""
+    binding, oracle, torch = env
+    d = synth.dense_gaussian()
+    m = oracle_model(oracle, d)
+    s0 = m.init_logq()
+    rows = np.random.default_rng(1).choice(d["N"], size=64, replace=False)
+    s_ref = m.prox_step_rows(0.05, s0, rows)
+    s, _, _ = gpu_run_bf16(binding, torch, d, 0.05, 1)
+    assert np.abs(np.exp(s[rows]) - np.exp(s_ref)).max() <= TOL_Q_BF16
+    s1, F1, _ = gpu_run_bf16(binding, torch, d, 0.05, 6, refine=1)
+    s2, F2, _ = gpu_run_bf16(binding, torch, d, 0.05, 6, refine=1)
+    assert np.array_equal(s1, s2) and F1 == F2
