@@ -51,6 +51,10 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-dense", action="store_true",
+                   help="skip the fully connected (N=9216, L=21) FP32 / BF16 measurements")
+    p.add_argument("--dense-only", action="store_true",
+                   help="run only the fully connected measurements (profiling captures)")
     p.add_argument("--batch", type=int, default=1,
                    help="instances per GPU (1 = the benchmark workload; >1 for profiling captures)")
     return p.parse_args()
@@ -192,6 +196,67 @@ def algorithmic_bytes_per_launch() -> int:
     return 12 * H * W * L + 4 * nd * H * W
 
 
+DENSE_SIDE, DENSE_L, DENSE_ITERS = 96, 21, 30
+
+
+def run_dense(args, dev, precision, peak):
+    """Fully connected Gaussian CRF, N = 96 x 96 = 9216, L = 21, 30 iterations:
+    device-timed solves (q^0, 30 steps, final F) with the model resident."""
+    import torch
+
+    from paper_1511_06103_gb300 import binding, synth
+    d = synth.dense_gaussian(side=DENSE_SIDE, L=DENSE_L)
+    stream = torch.cuda.current_stream(dev)
+    crf = binding.CRF(binding.CRF_DENSE_GAUSS, DENSE_L, DENSE_SIDE, DENSE_SIDE, precision=precision,
+                      stream=stream.cuda_stream)
+    crf.set_unary(torch.from_numpy(d["U"]).to(dev))
+    crf.set_pairwise(torch.from_numpy(d["mu"]).to(dev), torch.from_numpy(d["feats"]).to(dev),
+                     theta=np.array(d["theta"], np.float32))
+    lam, eta = crf.lipschitz()
+    # the BF16 form spends the last `refine` of the 30 iterations in FP32
+    refine = 2 if precision == binding.CRF_BF16 else 0
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        crf.iterate(DENSE_ITERS - refine, eta=0.0, reset=True, final_free_energy=True, refine_fp32=refine)
+
+    for _ in range(max(1, args.warmup)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    crf.profile(True)
+    times, kern = [], []
+    n = max(3, min(args.steps, 10))
+    for _ in range(n):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        ms, launches = crf.profile_read()
+        kern.append(ms / launches)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    crf.profile(False)
+    F = float(crf.free_energy()[0])
+    q = crf.marginals()
+    crf.close()
+    N = DENSE_SIDE * DENSE_SIDE
+    ms_step = float(np.mean(times))
+    iters = DENSE_ITERS
+    kbytes = N * N * (2 if precision == binding.CRF_BF16 else 4)
+    kms = float(np.mean(kern))
+    return {"value": N * DENSE_L * iters / (ms_step / 1000.0), "unit": UNIT, "ms_per_solve": ms_step,
+            "iters": DENSE_ITERS, "refine_fp32": refine, "avg_launch_ms": kms,
+            "roofline": {"bound": "hbm", "achieved": kbytes / (kms / 1000.0) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": kbytes / (kms / 1000.0) / 1e9 / peak,
+                         "bytes_per_launch": kbytes,
+                         "note": "K streamed once per iteration; launch average includes the FP32 "
+                                 "refinement steps of the BF16 form"},
+            "final_F": F, "eta": float(eta[0]), "Lambda": float(lam[0]), "q": q}
+
+
 def run_ours(args, world, rank, local):
     import torch
     import torch.distributed as dist
@@ -202,6 +267,13 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     torch.cuda.init()
     stream = torch.cuda.current_stream(dev)
+    if args.dense_only:
+        peak, _ = measured_peaks()
+        for prec in (binding.CRF_FP32, binding.CRF_BF16):
+            r = run_dense(args, dev, prec, peak)
+            r.pop("q")
+            print(json.dumps({"dense_precision": "bf16" if prec else "f32", **r}), flush=True)
+        return
     B = args.batch
     ds = [synth.segmentation_grid(H=H, W=W, L=L, conn=CONN, seed=SEED + rank * B + b) for b in range(B)]
     d = ds[0]
@@ -314,6 +386,17 @@ def run_ours(args, world, rank, local):
                          f"F every iteration; {dt:.1f} s of CPU work"}
 
     clocks = clk.summary()
+    dense = None
+    if not args.no_dense and world == 1:
+        r32 = run_dense(args, dev, binding.CRF_FP32, peak)
+        r16 = run_dense(args, dev, binding.CRF_BF16, peak)
+        dq = float(np.abs(r32.pop("q") - r16.pop("q")).max())
+        dense = {"workload": "fully connected Gaussian CRF, N=96x96=9216, L=21, 30 iterations "
+                             "(theta_pos=3, theta_rgb=13), model resident; the BF16 form runs 28 "
+                             "tensor-core steps and 2 FP32 refinement steps",
+                 "f32": r32, "bf16_tc": r16, "bf16_speedup": r16["value"] / r32["value"],
+                 "final_F_rel_diff": abs(r16["final_F"] - r32["final_F"]) / abs(r32["final_F"]),
+                 "q_max_abs_diff": dq}
     if rank == 0:
         srt = sorted(step_ms)
         line = {
@@ -339,6 +422,7 @@ def run_ours(args, world, rank, local):
             "setup_launches": int(setup_launches),
             "final_F": F_final,
             "wall_ms_timed": 1000 * (wall1 - wall0),
+            "dense": dense,
         }
         print(json.dumps(line), flush=True)
     crf.close()

@@ -206,3 +206,24 @@ def test_dense_bf16_full_size_sampled(env):
     s1, F1, _ = gpu_run_bf16(binding, torch, d, 0.05, 6, refine=1)
     s2, F2, _ = gpu_run_bf16(binding, torch, d, 0.05, 6, refine=1)
     assert np.array_equal(s1, s2) and F1 == F2
+
+
+def test_dense_mid_size_trajectories(env):
+    """N = 40 x 40 = 1600, L = 21, 30 steps at the step-size constant: the FP32
+    form within the FP32 tolerances, the BF16 form (28 tensor-core + 2 FP32
+    steps) within the BF16 ones."""
+    binding, oracle, torch = env
+    d = synth.dense_gaussian(side=40, L=21, seed=8)
+    with make(binding, d) as crf:
+        crf.set_unary(d["U"])
+        crf.set_pairwise(d["mu"], d["feats"], theta=np.array(d["theta"], np.float32))
+        _, eta = crf.lipschitz()
+    eta = float(np.float32(eta[0]))
+    m = oracle_model(oracle, d)
+    s_ref, F_ref = m.parallel_prox(eta, 30)
+    s, F, _ = gpu_run(binding, torch, d, eta, 30)
+    assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q
+    assert f_close(F, F_ref[-1], d["N"])
+    s, F, _ = gpu_run_bf16(binding, torch, d, eta, 28, refine=2)
+    assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q_BF16
+    assert abs(F - F_ref[-1]) <= TOL_F_BF16 * max(abs(F_ref[-1]), d["N"])
