@@ -7,15 +7,17 @@
 //
 // Per CTA: one tile of M = 128 rows of K, all 32 label columns (L padded),
 // and half of the k range (split-K 2, so N = 9216 gives 144 CTAs for the 152
-// SMs).  Warp 0 lane 0 issues TMA loads of 128 x 64 BF16 tiles of K and
-// 32 x 64 tiles of Q^T (both K-major, 128-byte swizzle) into a 6-stage ring
+// SMs; a four-way split with two CTAs per SM measured slower, its serial
+// epilogue tail growing more than the streaming overlap gained).  Warp 0
+// lane 0 issues TMA loads of 128 x 64 BF16 tiles of K and 32 x 64 tiles of
+// Q^T (both K-major, 128-byte swizzle) into a 6-stage ring
 // guarded by mbarriers; warp 1 lane 0 issues tcgen05.mma (M=128, N=32, K=16,
 // kind::f16) into a 32-column TMEM accumulator and releases each stage with
 // tcgen05.commit.  The four warps then read the accumulator rows with
-// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31).  The two k-halves of a
-// tile meet in global memory: the second CTA to finish adds the first one's
-// partial (a + b is commutative, so the result does not depend on which one
-// finishes first) and runs the row epilogue for the tile's 128 rows.
+// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31).  The k ranges of a tile
+// meet in global memory: the last CTA to finish sums the partials in range
+// order (so the result does not depend on which one finishes last) and runs
+// the row epilogue for the tile's 128 rows.
 //
 // Every wait is bounded by a clock budget; on expiry the kernel records
 // CRF_E_TIMEOUT, drains its own copies in flight (bounded), frees its TMEM
@@ -42,6 +44,7 @@ constexpr int kStageB = kTN * kTK * 2;   // 4 KiB
 constexpr int kStageBytes = kStageA + kStageB;
 constexpr int kThreads = 128;
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
+constexpr int kSplit = 2;                // k ranges per tile
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -141,7 +144,7 @@ struct DenseTcArgs {
     __nv_bfloat16 *qt_out;
     const float *eta;
     const float *mu;
-    float *split_part;       // [B][ntiles][2][128][32]
+    float *split_part;       // [B][ntiles][kSplit][128][32]
     unsigned *tile_count;    // [B][ntiles]
     double *partial;         // [B][ntiles]
     unsigned *counter;       // [B]
@@ -267,18 +270,24 @@ dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmK, const __grid_const
     const int r = warp * 32 + lane;   // row within the tile
     const size_t tile_id = (size_t)b * a.ntiles + tile;
     if (nsplit > 1) {
-        float *mine = a.split_part + ((tile_id * 2 + split) * kTM + r) * 32;
+        float *mine = a.split_part + ((tile_id * kSplit + split) * kTM + r) * 32;
 #pragma unroll
-        for (int i = 0; i < 32; i += 4) *reinterpret_cast<float4 *>(mine + i) = make_float4(S[i], S[i + 1], S[i + 2], S[i + 3]);
+        for (int i = 0; i < 32; i += 4)
+            *reinterpret_cast<float4 *>(mine + i) = make_float4(S[i], S[i + 1], S[i + 2], S[i + 3]);
         __threadfence();
         __syncthreads();
-        if (tid == 0) is_second = atomicAdd(a.tile_count + tile_id, 1u) == 1u;
+        if (tid == 0) is_second = atomicAdd(a.tile_count + tile_id, 1u) == (unsigned)(nsplit - 1);
         __syncthreads();
         if (!is_second) return;
         __threadfence();
-        const float *other = a.split_part + ((tile_id * 2 + (split ^ 1)) * kTM + r) * 32;
+        // the last of the k ranges sums all partials in split order
 #pragma unroll
-        for (int i = 0; i < 32; ++i) S[i] += __ldcg(other + i);
+        for (int i = 0; i < 32; ++i) S[i] = 0.f;
+        for (int sp = 0; sp < nsplit; ++sp) {
+            const float *part = a.split_part + ((tile_id * kSplit + sp) * kTM + r) * 32;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) S[i] += __ldcg(part + i);
+        }
         if (tid == 0) a.tile_count[tile_id] = 0u;
     }
 
@@ -383,7 +392,7 @@ cudaError_t launch_dense_step_tc(const DenseStepLaunch &l, const DenseTcBuffers 
     a.trace_cap = l.trace_cap;
     a.update = l.update;
     a.rel_tol = l.rel_tol;
-    const int nsplit = a.nchunk >= 2 ? 2 : 1;
+    const int nsplit = a.nchunk >= 2 * kSplit ? kSplit : 1;
     dim3 grid(a.ntiles, nsplit, l.B);
     const size_t smem = (size_t)kStages * kStageBytes + 1024;
     switch (storage_labels(l.L)) {
