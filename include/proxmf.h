@@ -195,6 +195,50 @@ crf_status mf_grid_step_noalloc(int32_t topology, int32_t n_labels, int64_t heig
                                 const float *mu, const float *logq_in, float *logq_out,
                                 double eta, double *F_out, void *stream);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of many grid CRFs on one GPU (the request loop of a
+ * serving deployment).  A server owns one device pool of budget_bytes; each
+ * request (one grid CRF: batch 1, FP32) is copied on submit and queued.
+ * mf_server_step retires finished requests (q copied to the request's q_out,
+ * slot and pool memory returned), admits queued requests in arrival order as
+ * slots and pool memory allow, and then advances every in-flight request by
+ * `iters` proximal steps -- one persistent launch per label class per step,
+ * replayed from a CUDA graph.  A request stops after max_iters steps or when
+ * |F^t - F^{t-1}| <= rel_tol |F^t| (Sec. 3.1), exactly as mf_iterate would
+ * stop it, and its arithmetic does not depend on the other requests.
+ * eta <= 0 asks for eta = 1/(1 + D max|nu|) with D the largest weighted degree
+ * and nu the eigenvalues of C mu C: an upper bound of the step-size constant
+ * of Sec. 3.2 (so the descent guarantee holds) that costs no iteration; it
+ * needs a symmetric mu.  One server is driven by one host thread. */
+typedef struct mf_server_s *mf_server_t;
+
+/* mf_server_create -- max_slots in 1..256 requests in flight; stream as in
+ * crf_desc.  CRF_E_OOM if the pool cannot be allocated. */
+crf_status mf_server_create(int64_t budget_bytes, int32_t max_slots, void *stream, mf_server_t *out);
+
+/* mf_server_destroy -- waits for the stream, frees the pool. */
+crf_status mf_server_destroy(mf_server_t s);
+
+/* mf_server_submit -- queue one request.  d: GRID4/GRID8, batch 1, FP32.
+ * U [N][L], mu [L][L], w [n_dirs][H][W]: host arrays, copied now.  q_out:
+ * host [N][L] receiving the marginals when the request finishes (may be
+ * NULL), must stay valid until then.  *ticket identifies the request.
+ * CRF_E_OOM if the request alone exceeds the pool. */
+crf_status mf_server_submit(mf_server_t s, const crf_desc *d, const float *U, const float *mu, const float *w,
+                            const mf_params *p, float *q_out, uint64_t *ticket);
+
+/* mf_server_step -- retire, admit, then run `iters` steps of every in-flight
+ * request (asynchronous on the stream).  Reports the requests in flight and
+ * still queued. */
+crf_status mf_server_step(mf_server_t s, int32_t iters, int32_t *in_flight, int32_t *queued);
+
+/* mf_server_poll -- state of a request: 0 queued, 1 running, 2 done (its q_out
+ * written); F is F(q^{K-1}) of its last step and iters the steps it took. */
+crf_status mf_server_poll(mf_server_t s, uint64_t ticket, int32_t *state, double *F, int32_t *iters);
+
+/* mf_server_sync -- wait for the server's stream. */
+crf_status mf_server_sync(mf_server_t s);
+
 /* crf_error_string -- static description of a status code. */
 const char *crf_error_string(crf_status s);
 

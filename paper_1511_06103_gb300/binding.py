@@ -68,6 +68,13 @@ _SIGS = {
     "mf_marginals": [_vp, _vp, _i],
     "mf_log_marginals": [_vp, _vp, _i],
     "mf_lipschitz": [_vp, _vp, _vp],
+    "mf_server_create": [C.c_int64, C.c_int32, _vp, C.POINTER(_vp)],
+    "mf_server_destroy": [_vp],
+    "mf_server_submit": [_vp, C.POINTER(crf_desc), _vp, _vp, _vp, C.POINTER(mf_params), _vp,
+                         C.POINTER(C.c_uint64)],
+    "mf_server_step": [_vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+    "mf_server_poll": [_vp, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.POINTER(C.c_int32)],
+    "mf_server_sync": [_vp],
     "mf_profile": [_vp, C.c_int32],
     "mf_profile_read": [_vp, _vp, _vp],
     "crf_launch_count": [_vp, _vp],
@@ -302,3 +309,68 @@ class CRF:
         eta = np.zeros(self.B, np.float64)
         mf_lipschitz(self.h, lam.ctypes.data, eta.ctypes.data)
         return lam, eta
+
+
+# -- serving -------------------------------------------------------------------
+
+class Server:
+    """Continuous-batching server over the mf_server_* calls."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 64, stream: int | None = None):
+        if stream is None:
+            stream = current_stream_handle()
+        h = _vp()
+        _call("mf_server_create", int(budget_bytes), int(max_slots), stream, C.byref(h))
+        self.h = h.value
+        self._keep = {}
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            _call("mf_server_destroy", self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, U, mu, w, H: int, W: int, conn: int, eta: float = 0.0, max_iters: int = 1000,
+               rel_tol: float = 0.0) -> int:
+        L = mu.shape[0]
+        topo = CRF_GRID8 if conn == 8 else CRF_GRID4
+        d = crf_desc(topo, L, 1, CRF_FP32, H, W, None)
+        prm = mf_params(float(eta), int(max_iters), 1, float(rel_tol), 0, 0)
+        U = np.ascontiguousarray(U, np.float32)
+        mu = np.ascontiguousarray(mu, np.float32)
+        w = np.ascontiguousarray(w, np.float32)
+        q = np.zeros((H * W, L), np.float32)
+        t = C.c_uint64(0)
+        _call("mf_server_submit", self.h, C.byref(d), U.ctypes.data, mu.ctypes.data, w.ctypes.data,
+              C.byref(prm), q.ctypes.data, C.byref(t))
+        self._keep[t.value] = q
+        return t.value
+
+    def step(self, iters: int = 1) -> tuple[int, int]:
+        a = C.c_int32(0)
+        b = C.c_int32(0)
+        _call("mf_server_step", self.h, int(iters), C.byref(a), C.byref(b))
+        return a.value, b.value
+
+    def poll(self, ticket: int):
+        """(state, F, iters, q or None): state 0 queued, 1 running, 2 done."""
+        st = C.c_int32(0)
+        F = C.c_double(0.0)
+        it = C.c_int32(0)
+        _call("mf_server_poll", self.h, C.c_uint64(ticket), C.byref(st), C.byref(F), C.byref(it))
+        q = self._keep.get(ticket) if st.value == 2 else None
+        return st.value, F.value, it.value, q
+
+    def sync(self) -> None:
+        _call("mf_server_sync", self.h)

@@ -254,6 +254,22 @@ crf_status read_status(crf_t h) {
 
 namespace proxmf {
 
+cudaError_t launch_serve(int LT, int conn, bool sym, ServeSlot *slots, const ServeBucket *bucket,
+                         ServeResult *res, int grid, cudaStream_t st) {
+    switch (LT) {
+    case 2: return launch_serve_l2(conn, sym, slots, bucket, res, grid, st);
+    case 4: return launch_serve_l4(conn, sym, slots, bucket, res, grid, st);
+    case 8: return launch_serve_l8(conn, sym, slots, bucket, res, grid, st);
+    case 12: return launch_serve_l12(conn, sym, slots, bucket, res, grid, st);
+    case 16: return launch_serve_l16(conn, sym, slots, bucket, res, grid, st);
+    case 20: return launch_serve_l20(conn, sym, slots, bucket, res, grid, st);
+    case 21: return launch_serve_l21(conn, sym, slots, bucket, res, grid, st);
+    case 24: return launch_serve_l24(conn, sym, slots, bucket, res, grid, st);
+    case 28: return launch_serve_l28(conn, sym, slots, bucket, res, grid, st);
+    default: return launch_serve_l32(conn, sym, slots, bucket, res, grid, st);
+    }
+}
+
 cudaError_t launch_grid_step(const GridStepLaunch &a, cudaStream_t st) {
     switch (kernel_labels(a.L)) {
     case 2: return launch_grid_step_l2(a, st);
@@ -271,15 +287,19 @@ cudaError_t launch_grid_step(const GridStepLaunch &a, cudaStream_t st) {
 
 // Column pairs (for mu S) and row pairs (for mu^T S) of mu, zero padded to
 // the kernel label count (see mu_pair_slots).
-void build_mu_pairs(const std::vector<float> &mu, int L, int LT, std::vector<float2> &out) {
+void build_mu_pairs_host(const float *mu, int L, int LT, float2 *out) {
     const int NPP = mu_pair_slots(LT);
-    out.assign((size_t)2 * LT * NPP, make_float2(0.f, 0.f));
     auto at = [&](int r, int c) { return (r < L && c < L) ? mu[(size_t)r * L + c] : 0.f; };
     for (int k = 0; k < LT; ++k)
         for (int j = 0; j < NPP; ++j) {
             out[(size_t)k * NPP + j] = make_float2(at(2 * j, k), at(2 * j + 1, k));
             out[(size_t)(LT + k) * NPP + j] = make_float2(at(k, 2 * j), at(k, 2 * j + 1));
         }
+}
+
+void build_mu_pairs(const std::vector<float> &mu, int L, int LT, std::vector<float2> &out) {
+    out.assign((size_t)2 * LT * mu_pair_slots(LT), make_float2(0.f, 0.f));
+    build_mu_pairs_host(mu.data(), L, LT, out.data());
 }
 
 }  // namespace proxmf

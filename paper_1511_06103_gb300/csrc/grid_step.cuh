@@ -142,9 +142,25 @@ __device__ __forceinline__ void pair_matvec(float2 (&m)[NP], const float2 *A, co
     }
 }
 
+// One instance as seen by one tile: pointers already offset to the instance.
+struct TileJob {
+    const float *s_in;
+    float *s_out;
+    const float *U;
+    const float *w;
+    const float2 *mu_out;
+    const float2 *mu_in;
+    float eta;
+    int L, H, W;
+    int update;
+};
+
+// One 32 x 8 tile of one instance: a1-a4 for its pixels (state written when
+// j.update), and the tile's free-energy partial, returned in thread 0.
+// All threads of the block must call it; it may be called repeatedly by a
+// persistent block (shared memory is reused).
 template <int LT, int CONN, bool SYM>
-__global__ void __launch_bounds__(GT, (LT >= 24) ? 1 : 2)
-grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
+__device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by) {
     constexpr int LP = storage_labels(LT);           // floats per pixel in HBM
     constexpr int NP = (LT + 1) / 2;                 // label pairs in the arithmetic
     constexpr int NPP = (NP + 1) / 2 * 2;            // pair slots per mu column
@@ -158,34 +174,20 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
     __shared__ __align__(16) float qt[(GY + 2) * TW * LS];
     __shared__ __align__(16) float2 mus[SYM ? 1 : 2][LT * NPP];
     __shared__ double red[GT / 32];
-    __shared__ int is_last;
 
-    const int b = blockIdx.z;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * GX + tx;
-    const int x0 = blockIdx.x * GX, y0 = blockIdx.y * GY;
+    const int x0 = bx * GX, y0 = by * GY;
     const int x = x0 + tx, y = y0 + ty;
-    const int H = a.H, W = a.W, L = a.L;
+    const int H = j.H, W = j.W, L = j.L;
     const bool inside = (x < W) && (y < H);
-    const size_t N = (size_t)H * W;
     const size_t p = (size_t)y * W + x;
-    const float *sin = a.s_in + (size_t)b * N * LP;
-
-    if (a.done != nullptr && a.done[b] != 0) {
-        // This instance has met its stopping rule: carry the state through
-        // unchanged so that the ping-pong parity stays the same for all.
-        if (a.update && inside) {
-            float2 v[LP / 2];
-            load_px<LP>(v, sin + p * LP);
-            store_px<LP>(a.s_out + ((size_t)b * N + p) * LP, v);
-        }
-        return;
-    }
-
+    const float *sin = j.s_in;
+    __syncthreads();   // shared memory of a previous tile is no longer read
 
     // mu pairs into shared memory
     for (int i = tid; i < LT * NPP; i += GT) {
-        mus[0][i] = a.mu_out[i];
-        if (!SYM) mus[SYM ? 0 : 1][i] = a.mu_in[i];
+        mus[0][i] = j.mu_out[i];
+        if (!SYM) mus[SYM ? 0 : 1][i] = j.mu_in[i];
     }
 
     // own log q
@@ -227,7 +229,7 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
     // that owns the edge)
     float wo[4] = {0.f, 0.f, 0.f, 0.f}, wi[4] = {0.f, 0.f, 0.f, 0.f};
     if (inside) {
-        const float *wb = a.w + (size_t)b * N * ND;
+        const float *wb = j.w;
         if (ND == 4) {
             const float4 t = __ldg(reinterpret_cast<const float4 *>(wb + p * ND));
             wo[0] = t.x;
@@ -251,7 +253,7 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
     // unaries: issued now, consumed after the L x L product
     float2 u[LP / 2];
     if (inside) {
-        load_px<LP>(u, a.U + ((size_t)b * N + p) * LP);
+        load_px<LP>(u, j.U + p * LP);
     } else {
 #pragma unroll
         for (int i = 0; i < LP / 2; ++i) u[i] = splat2(0.f);
@@ -305,7 +307,7 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
 #pragma unroll
     for (int j = 0; j < NP; ++j) qc[j] = splat2(0.f);
     acc_cell<NP>(qc, qt + ((ty + 1) * TW + tx + 1) * LS, 1.f);
-    const float eta = a.eta[b];
+    const float eta = j.eta;
     const float2 neta = splat2(-eta), ome = splat2(1.f - eta), half = splat2(0.5f);
     float2 f2 = splat2(0.f);
     float mx = -INFINITY;
@@ -326,7 +328,7 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
 #pragma unroll
     for (int j = 0; j < NP; ++j) z += __expf(s[j].x - mx) + __expf(s[j].y - mx);
     const float2 nlse = splat2(-(mx + __logf(z)));
-    if (a.update && inside) {
+    if (j.update && inside) {
         float2 o[LP / 2];
 #pragma unroll
         for (int j = 0; j < LP / 2; ++j) {
@@ -339,7 +341,7 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
                 o[j] = splat2(kPadLogQ);
             }
         }
-        store_px<LP>(a.s_out + ((size_t)b * N + p) * LP, o);
+        store_px<LP>(j.s_out + p * LP, o);
     }
 
     // a5: F partial of this tile, FP64
@@ -347,11 +349,51 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
     fd = warp_sum_f64(fd);
     if ((tid & 31) == 0) red[tid >> 5] = fd;
     __syncthreads();
-    const int blk = blockIdx.y * a.nbx + blockIdx.x;
+    double bs = 0.0;
     if (tid == 0) {
-        double bs = 0.0;
 #pragma unroll
         for (int k = 0; k < GT / 32; ++k) bs += red[k];
+    }
+    return bs;
+}
+
+template <int LT, int CONN, bool SYM>
+__global__ void __launch_bounds__(GT, (LT >= 24) ? 1 : 2)
+grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
+    constexpr int LP = storage_labels(LT);
+    __shared__ double red[GT / 32];
+    __shared__ int is_last;
+    const int b = blockIdx.z;
+    const int tid = threadIdx.y * GX + threadIdx.x;
+    const size_t N = (size_t)a.H * a.W;
+    if (a.done != nullptr && a.done[b] != 0) {
+        // This instance has met its stopping rule: carry the state through
+        // unchanged so that the ping-pong parity stays the same for all.
+        const int x = blockIdx.x * GX + threadIdx.x, y = blockIdx.y * GY + threadIdx.y;
+        if (a.update && x < a.W && y < a.H) {
+            const size_t p = (size_t)y * a.W + x;
+            float2 v[LP / 2];
+            load_px<LP>(v, a.s_in + ((size_t)b * N + p) * LP);
+            store_px<LP>(a.s_out + ((size_t)b * N + p) * LP, v);
+        }
+        return;
+    }
+    TileJob j;
+    j.s_in = a.s_in + (size_t)b * N * LP;
+    j.s_out = a.s_out + (size_t)b * N * LP;
+    j.U = a.U + (size_t)b * N * LP;
+    j.w = a.w + (size_t)b * N * (CONN == 8 ? 4 : 2);
+    j.mu_out = a.mu_out;
+    j.mu_in = a.mu_in;
+    j.eta = a.eta[b];
+    j.L = a.L;
+    j.H = a.H;
+    j.W = a.W;
+    j.update = a.update;
+    const double bs = grid_tile<LT, CONN, SYM>(j, blockIdx.x, blockIdx.y);
+
+    const int blk = blockIdx.y * a.nbx + blockIdx.x;
+    if (tid == 0) {
         a.partial[(size_t)b * a.nblk + blk] = bs;
         __threadfence();
         const unsigned prev = atomicAdd(a.counter + b, 1u);

@@ -10,6 +10,7 @@
 namespace proxmf {
 
 constexpr int kMaxLabels = 32;
+constexpr int kMaxServeSlots = 256;   // requests in flight in one server
 
 // Grid tile of the step kernel: GX x GY pixels, one thread per pixel.
 constexpr int GX = 32;
@@ -63,6 +64,30 @@ inline void grid_tiles(int H, int W, int *nbx, int *nby) {
 }
 
 // Per-label-bucket launchers (one translation unit each).
+// Column / row pairs of mu for a kernel label count LT (api.cu).
+void build_mu_pairs_host(const float *mu, int L, int LT, float2 *out);
+
+// Serving (serve.cuh, serve.cu): persistent per-bucket step over a slot table.
+struct ServeSlot;
+struct ServeBucket;
+struct ServeResult;
+cudaError_t launch_serve(int LT, int conn, bool sym, ServeSlot *slots, const ServeBucket *bucket,
+                         ServeResult *res, int grid, cudaStream_t st);
+cudaError_t launch_serve_l2(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
+cudaError_t launch_serve_l4(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
+cudaError_t launch_serve_l8(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
+cudaError_t launch_serve_l12(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
+cudaError_t launch_serve_l16(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
+cudaError_t launch_serve_l20(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
+cudaError_t launch_serve_l21(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
+cudaError_t launch_serve_l24(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
+cudaError_t launch_serve_l28(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
+cudaError_t launch_serve_l32(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
+// Step-size bound for serving: eta = 1/(1 + D max|nu|), D the largest weighted
+// degree, nu the eigenvalues of C mu C (symmetric mu).
+cudaError_t launch_eta_bound(const float *w, int H, int W, int nd, const float *mu, int L, float *eta,
+                             double *scratch, cudaStream_t st);
+
 // Per-label-count launchers (grid_step_l*.cu), dispatched by launch_grid_step.
 cudaError_t launch_grid_step_l2(const GridStepLaunch &a, cudaStream_t st);
 cudaError_t launch_grid_step_l4(const GridStepLaunch &a, cudaStream_t st);
@@ -127,6 +152,9 @@ struct DenseTcBuffers {
     unsigned *tile_count;    // [B][tiles] (zero, self-resetting)
 };
 cudaError_t launch_dense_step_tc(const DenseStepLaunch &a, const DenseTcBuffers &tb, cudaStream_t st);
+
+// Extreme eigenvalues of C mu C into nu[0] (min), nu[1] (max) (lanczos.cu).
+cudaError_t launch_mu_tilde_extremes(const float *mu_dev, int L, double *nu, cudaStream_t st);
 
 // Step-size constant (lanczos.cu).  Fills Lambda[b] (device, FP64) and
 // eta[b] = 1/(1+max(Lambda,0)) (device, FP32).  Returns CRF status codes.

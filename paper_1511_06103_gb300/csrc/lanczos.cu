@@ -524,6 +524,11 @@ __global__ void set_lambda_zero_kernel(int B, double *Lambda, float *eta) {
 
 }  // namespace
 
+cudaError_t launch_mu_tilde_extremes(const float *mu_dev, int L, double *nu, cudaStream_t st) {
+    mu_tilde_extremes_kernel<<<1, 32, 0, st>>>(mu_dev, L, nu);
+    return cudaGetLastError();
+}
+
 #define LZ_CHECK(x)                      \
     do {                                 \
         cudaError_t e_ = (x);            \
