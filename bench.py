@@ -55,6 +55,9 @@ def parse():
                    help="skip the fully connected (N=9216, L=21) FP32 / BF16 measurements")
     p.add_argument("--dense-only", action="store_true",
                    help="run only the fully connected measurements (profiling captures)")
+    p.add_argument("--serve-requests", type=int, default=128,
+                   help="requests of the serving measurement (0 skips it)")
+    p.add_argument("--serve-only", action="store_true")
     p.add_argument("--batch", type=int, default=1,
                    help="instances per GPU (1 = the benchmark workload; >1 for profiling captures)")
     return p.parse_args()
@@ -189,6 +192,11 @@ def run_reference(args, world, rank):
 
 # -- our arm -------------------------------------------------------------------
 
+# dram__bytes_read.sum + dram__bytes_write.sum of grid_prox_step_kernel<21,8,sym>
+# per instance-launch (4-instance capture / 4, see profiles/)
+GRID_TRAFFIC_PER_INSTANCE = (218159616 + 72714496) // 4
+
+
 def algorithmic_bytes_per_launch() -> int:
     """One grid-step launch reads log q and U and writes log q (4 B each per
     variable-label) and reads the n_dirs edge-weight planes (4 B per pixel each)."""
@@ -257,6 +265,100 @@ def run_dense(args, dev, precision, peak):
             "final_F": F, "eta": float(eta[0]), "Lambda": float(lam[0]), "q": q}
 
 
+SERVE_SIZES = (64, 86, 116, 156, 210, 283, 380, 512)   # log-uniform sides in [64, 512], quantised
+
+
+def serving_requests(n, seed=7):
+    """n requests: square side log-uniform in [64, 512] (quantised to 8 sizes
+    so edge weights can be reused), L in {2, 8, 21}; L = 2 uses the binary
+    denoising recipe, L = 8 and 21 the segmentation recipe; unaries are drawn
+    fresh for every request."""
+    from paper_1511_06103_gb300 import synth
+    rng = np.random.default_rng(seed)
+    cache = {}
+    out = []
+    for _ in range(n):
+        side = SERVE_SIZES[int(rng.integers(0, len(SERVE_SIZES)))]
+        L = int(rng.choice([2, 8, 21]))
+        key = (side, L)
+        if key not in cache:
+            if L == 2:
+                cache[key] = synth.binary_denoising(H=side, W=side, seed=1000 + side)
+            else:
+                cache[key] = synth.segmentation_grid(H=side, W=side, L=L, conn=8, seed=2000 + side + L)
+        base = cache[key]
+        if L == 2:
+            U = base["U"]
+        else:
+            U = synth.unary_from_logits(rng.normal(0.0, 2.0, size=(side * side, L))).astype(np.float32)
+        out.append(dict(base, U=np.ascontiguousarray(U, np.float32)))
+    return out
+
+
+def run_serving(n_req, max_iters=1000, rel_tol=1e-6):
+    """Continuous batching with Poisson arrivals at 0.8x the saturated rate;
+    p50/p99 latency (arrival to result) and throughput, against the same
+    requests solved one at a time."""
+    from paper_1511_06103_gb300 import binding
+    reqs = serving_requests(n_req)
+    budget = 16 << 30
+
+    def drive(srv, arrivals, iters_per_step=4):
+        t0 = time.perf_counter()
+        sub, lat, done_iters = {}, {}, {}
+        tickets = []
+        i = 0
+        while len(lat) < len(reqs):
+            now = time.perf_counter() - t0
+            while i < len(reqs) and arrivals[i] <= now:
+                d = reqs[i]
+                t = srv.submit(d["U"], d["mu"], d["w"], d["H"], d["W"], d["conn"], eta=0.0, max_iters=max_iters,
+                               rel_tol=rel_tol)
+                sub[t] = time.perf_counter()
+                tickets.append((t, i))
+                i += 1
+            srv.step(iters_per_step)
+            for t, k in tickets:
+                if t in lat:
+                    continue
+                st, _, it, _ = srv.poll(t)
+                if st == 2:
+                    lat[t] = time.perf_counter() - sub[t]
+                    done_iters[k] = it
+            if i < len(reqs) and all(t in lat for t, _ in tickets):
+                time.sleep(max(0.0, min(0.001, arrivals[i] - (time.perf_counter() - t0))))
+        srv.sync()
+        return time.perf_counter() - t0, lat, done_iters
+
+    with binding.Server(budget, max_slots=128) as srv:          # saturated: all at once
+        t_sat, _, _ = drive(srv, [0.0] * len(reqs))
+    rate = 0.8 * len(reqs) / t_sat
+    arrivals = np.cumsum(np.random.default_rng(11).exponential(1.0 / rate, size=len(reqs)))
+    with binding.Server(budget, max_slots=128) as srv:
+        t_run, lat, iters_run = drive(srv, arrivals)
+    upd = sum(r["H"] * r["W"] * r["L"] * iters_run[k] for k, r in enumerate(reqs))
+    t1 = time.perf_counter()
+    with binding.Server(budget, max_slots=1) as srv:           # one at a time
+        for d in reqs:
+            t = srv.submit(d["U"], d["mu"], d["w"], d["H"], d["W"], d["conn"], eta=0.0, max_iters=max_iters,
+                           rel_tol=rel_tol)
+            while srv.poll(t)[0] != 2:
+                srv.step(8)
+        srv.sync()
+    t_one = time.perf_counter() - t1
+    ms = np.array(sorted(lat.values())) * 1000
+    return {"workload": f"{len(reqs)} grid-CRF requests, square side log-uniform in [64,512] (8 sizes), "
+                        "L in {2,8,21}, Poisson arrivals at 0.8x the saturated rate, retirement at "
+                        "dF/|F| <= 1e-6 or 1000 steps, step size from the degree bound",
+            "requests": len(reqs), "arrival_rate_rps": rate, "saturated_s": t_sat, "run_s": t_run,
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
+                           "mean": float(ms.mean())},
+            "throughput_rps": len(reqs) / t_run, "updates_per_s": upd / t_run,
+            "saturated_throughput_rps": len(reqs) / t_sat,
+            "one_at_a_time": {"s": t_one, "throughput_rps": len(reqs) / t_one, "updates_per_s": upd / t_one},
+            "mean_iters": float(np.mean(list(iters_run.values())))}
+
+
 def run_ours(args, world, rank, local):
     import torch
     import torch.distributed as dist
@@ -267,6 +369,9 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     torch.cuda.init()
     stream = torch.cuda.current_stream(dev)
+    if args.serve_only:
+        print(json.dumps({"serving": run_serving(max(1, args.serve_requests))}), flush=True)
+        return
     if args.dense_only:
         peak, _ = measured_peaks()
         for prec in (binding.CRF_FP32, binding.CRF_BF16):
@@ -397,6 +502,9 @@ def run_ours(args, world, rank, local):
                  "f32": r32, "bf16_tc": r16, "bf16_speedup": r16["value"] / r32["value"],
                  "final_F_rel_diff": abs(r16["final_F"] - r32["final_F"]) / abs(r32["final_F"]),
                  "q_max_abs_diff": dq}
+    serving = None
+    if args.serve_requests > 0 and world == 1:
+        serving = run_serving(args.serve_requests)
     if rank == 0:
         srt = sorted(step_ms)
         line = {
@@ -410,7 +518,9 @@ def run_ours(args, world, rank, local):
                              "set stays L2-resident across its 100 iterations"},
             "latency_ms": {"p50": float(np.percentile(srt, 50)), "p99": float(np.percentile(srt, 99))},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": B * GRID_TRAFFIC_PER_INSTANCE,
+                         "traffic_note": "dram read+write of one launch per instance, from a 4-instance "
+                                         "ncu capture (larger than L2) divided by 4",
                          "kernel": "grid_prox_step_kernel<21,8,sym>",
                          "bytes_per_launch": bytes_launch, "avg_launch_ms": kern_ms,
                          "peak_kind": peak_kind},
@@ -423,6 +533,7 @@ def run_ours(args, world, rank, local):
             "final_F": F_final,
             "wall_ms_timed": 1000 * (wall1 - wall0),
             "dense": dense,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     crf.close()
