@@ -76,6 +76,8 @@ def _load():
             "orc_hessian_eigenvalues": (C.c_int, [_vp, C.c_int, _vp]),
             "orc_lanczos_tangent": (_i32, [_vp, _i32, _vp, _vp, _vp]),
             "orc_step_size": (_d, [_d]),
+            "orc_unrolled_loss_grad": (_d, [_vp, _d, _i32, _vp, _vp, _vp, _vp]),
+            "orc_unrolled_loss": (_d, [_vp, _d, _i32, _vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -273,6 +275,20 @@ class Model:
         if _load().orc_brute_cond_energy(self._h, _ptr(q), _ptr(out)) != 0:
             raise ValueError("model too large to enumerate")
         return out
+
+    def unrolled_loss(self, eta: float, K: int, y) -> float:
+        """-(1/n) sum_i log q^K_{i,y_i} after K steps from softmax(-U)."""
+        y = np.ascontiguousarray(y, np.int32)
+        return float(_load().orc_unrolled_loss(self._h, float(eta), int(K), _ptr(y)))
+
+    def unrolled_grad(self, eta: float, K: int, y, n_edges: int):
+        """(loss, dU [n][L], dmu [L][L], dw [n_edges]) by reverse mode."""
+        y = np.ascontiguousarray(y, np.int32)
+        dU = np.zeros((self.n, self.L))
+        dmu = np.zeros((self.L, self.L))
+        dw = np.zeros(max(1, n_edges))
+        loss = _load().orc_unrolled_loss_grad(self._h, float(eta), int(K), _ptr(y), _ptr(dU), _ptr(dmu), _ptr(dw))
+        return float(loss), dU, dmu, dw[:n_edges]
 
     def hessian_eigenvalues(self, projected: bool = True) -> np.ndarray:
         ev = np.zeros(self.n * self.L)

@@ -471,6 +471,110 @@ void orc_sweep(const orc_model *m, int32_t sweeps, double *s)
 }
 
 /* ------------------------------------------------------------------ */
+/* reverse-mode gradient of K unrolled steps                           */
+/* ------------------------------------------------------------------ */
+
+/* Loss of K unrolled parallel proximal steps from q^0 = softmax(-U), with a
+ * fixed step eta: loss = -(1/n) sum_i log q^K_{i, y_i} (cross-entropy against
+ * the label map y).  Returns the loss; fills dU [n][L], dmu [L][L] and dw
+ * [n_edges] with its gradient, by the chain rule through every step taken
+ * backwards in time (the step constant is held fixed).  Each step is
+ *   q = exp(s),  m = H q (pairwise part of grad E),  a = -eta (U + m) + (1-eta) s,
+ *   s' = a - logsumexp(a). */
+double orc_unrolled_loss_grad(const orc_model *m, double eta, int32_t K, const int32_t *y,
+                              double *dU, double *dmu, double *dw)
+{
+    const int L = m->L;
+    const int64_t n = m->n, nl = n * L;
+    double *S = (double *)malloc(sizeof(double) * (size_t)nl * (size_t)(K + 1));   /* s^0..s^K */
+    double *q = (double *)malloc(sizeof(double) * (size_t)nl);
+    double *gs = (double *)xcalloc((size_t)nl, sizeof(double));    /* d loss / d s^t */
+    double *ga = (double *)xcalloc((size_t)nl, sizeof(double));
+    double *gm = (double *)xcalloc((size_t)nl, sizeof(double));
+    double *hq = (double *)xcalloc((size_t)nl, sizeof(double));
+    double *qt = (double *)malloc(sizeof(double) * (size_t)nl);
+    double *mq = (double *)malloc(sizeof(double) * (size_t)L);
+    memset(dU, 0, sizeof(double) * (size_t)nl);
+    memset(dmu, 0, sizeof(double) * (size_t)L * L);
+    if (!m->K) memset(dw, 0, sizeof(double) * (size_t)m->ne);
+    /* forward, keeping every state */
+    orc_init_logq(m, S);
+    for (int32_t t = 0; t < K; ++t) orc_prox_step(m, eta, S + (size_t)t * nl, S + (size_t)(t + 1) * nl);
+    double loss = 0.0;
+    for (int64_t i = 0; i < n; ++i) loss -= S[(size_t)K * nl + i * L + y[i]] / (double)n;
+    for (int64_t i = 0; i < n; ++i) gs[i * L + y[i]] = -1.0 / (double)n;
+    /* backward */
+    for (int32_t t = K - 1; t >= 0; --t) {
+        const double *st = S + (size_t)t * nl, *sn = S + (size_t)(t + 1) * nl;
+        /* through s^{t+1} = a - logsumexp(a): ga = gs - q^{t+1} sum_l gs */
+        for (int64_t i = 0; i < n; ++i) {
+            double sum = 0.0;
+            for (int l = 0; l < L; ++l) sum += gs[i * L + l];
+            for (int l = 0; l < L; ++l) ga[i * L + l] = gs[i * L + l] - exp(sn[i * L + l]) * sum;
+        }
+        /* through a = -eta (U + m) + (1-eta) s */
+        for (int64_t k = 0; k < nl; ++k) {
+            dU[k] += -eta * ga[k];
+            gm[k] = -eta * ga[k];
+        }
+        for (int64_t k = 0; k < nl; ++k) q[k] = exp(st[k]);
+        /* through m = H q: H is symmetric, so dq = H gm; parameters by product rule */
+        orc_hess_vec(m, gm, hq);
+        if (m->K) {
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t j = i + 1; j < n; ++j) {
+                    const double kij = m->K[i * n + j];
+                    for (int a = 0; a < L; ++a)
+                        for (int b = 0; b < L; ++b)
+                            dmu[a * L + b] += kij * (gm[i * L + a] * q[j * L + b] + q[i * L + a] * gm[j * L + b]);
+                }
+        } else {
+            for (int64_t e = 0; e < m->ne; ++e) {
+                const int64_t i = m->ei[e], j = m->ej[e];
+                const double *qi = q + i * L, *qj = q + j * L, *gi = gm + i * L, *gj = gm + j * L;
+                /* edge energy w q_i^T mu q_j enters m_i as w mu q_j and m_j as w mu^T q_i */
+                dw[e] += bilinear(gi, m->mu, qj, L) + bilinear(qi, m->mu, gj, L);
+                for (int a = 0; a < L; ++a)
+                    for (int b = 0; b < L; ++b)
+                        dmu[a * L + b] += m->ew[e] * (gi[a] * qj[b] + qi[a] * gj[b]);
+            }
+        }
+        /* through q = exp(s) and the direct (1-eta) s term */
+        for (int64_t k = 0; k < nl; ++k) gs[k] = (1.0 - eta) * ga[k] + q[k] * hq[k];
+    }
+    /* through s^0 = logsoftmax(-U) */
+    for (int64_t i = 0; i < n; ++i) {
+        double sum = 0.0;
+        for (int l = 0; l < L; ++l) sum += gs[i * L + l];
+        for (int l = 0; l < L; ++l) {
+            const double q0 = exp(S[i * L + l]);
+            dU[i * L + l] += -(gs[i * L + l] - q0 * sum);
+        }
+    }
+    (void)qt; (void)mq;
+    free(S); free(q); free(gs); free(ga); free(gm); free(hq); free(qt); free(mq);
+    return loss;
+}
+
+/* The loss alone (for finite differences). */
+double orc_unrolled_loss(const orc_model *m, double eta, int32_t K, const int32_t *y)
+{
+    const int L = m->L;
+    const int64_t nl = m->n * L;
+    double *s = (double *)malloc(sizeof(double) * (size_t)nl);
+    double *t = (double *)malloc(sizeof(double) * (size_t)nl);
+    orc_init_logq(m, s);
+    for (int32_t k = 0; k < K; ++k) {
+        orc_prox_step(m, eta, s, t);
+        memcpy(s, t, sizeof(double) * (size_t)nl);
+    }
+    double loss = 0.0;
+    for (int64_t i = 0; i < m->n; ++i) loss -= s[i * L + y[i]] / (double)m->n;
+    free(s); free(t);
+    return loss;
+}
+
+/* ------------------------------------------------------------------ */
 /* brute-force enumeration (tiny models only)                          */
 /* ------------------------------------------------------------------ */
 

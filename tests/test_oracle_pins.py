@@ -352,3 +352,40 @@ def test_step_rows_matches_full_step(oracle_mod):
     full = m.prox_step(0.4, s0)
     rows = np.array([0, 7, 24, 13])
     assert np.array_equal(m.prox_step_rows(0.4, s0, rows), full[rows])
+
+
+# ---------------------------------------------------------------- P7 ----
+
+@pytest.mark.parametrize("conn,sym", [(4, False), (8, True)])
+def test_unrolled_gradient_matches_finite_differences(oracle_mod, conn, sym):
+    """Reverse mode through K = 10 unrolled steps (fixed eta) against FP64
+    central differences on an 8 x 8, L = 3 grid: unaries, mu and edge weights."""
+    Hh = Ww = 8
+    d = synth.random_grid(Hh, Ww, 3, conn, seed=123, symmetric=sym, coupling_scale=1.5)
+    U, mu, w = _f64(d, "U"), _f64(d, "mu"), _f64(d, "w")
+    y = np.random.default_rng(5).integers(0, 3, size=Hh * Ww)
+    eta, K, h = 0.2, 10, 1e-6
+    # central differences carry ~eps |loss| / h = 2e-10 of round-off: absolute floor 1e-9
+    ei, ej, ew = oracle_mod.grid_edges(Hh, Ww, conn, w)
+    m = oracle_mod.Model.sparse(U, mu, ei, ej, ew)
+    loss, dU, dmu, dw = m.unrolled_grad(eta, K, y, ei.size)
+    assert math.isclose(loss, m.unrolled_loss(eta, K, y), rel_tol=1e-14)
+
+    def fd(make):
+        return (make(h).unrolled_loss(eta, K, y) - make(-h).unrolled_loss(eta, K, y)) / (2 * h)
+
+    for (i, l) in [(0, 0), (27, 2), (63, 1)]:
+        def mk(dh, i=i, l=l):
+            U2 = U.copy(); U2[i, l] += dh
+            return oracle_mod.Model.sparse(U2, mu, ei, ej, ew)
+        assert abs(fd(mk) - dU[i, l]) <= 1e-7 * abs(dU[i, l]) + 1e-9
+    for (a, b) in [(0, 1), (2, 0), (1, 1)]:
+        def mk(dh, a=a, b=b):
+            mu2 = mu.copy(); mu2[a, b] += dh
+            return oracle_mod.Model.sparse(U, mu2, ei, ej, ew)
+        assert abs(fd(mk) - dmu[a, b]) <= 1e-7 * abs(dmu[a, b]) + 1e-9
+    for e in [0, 17, ei.size - 1]:
+        def mk(dh, e=e):
+            ew2 = ew.copy(); ew2[e] += dh
+            return oracle_mod.Model.sparse(U, mu, ei, ej, ew2)
+        assert abs(fd(mk) - dw[e]) <= 1e-7 * abs(dw[e]) + 1e-9
