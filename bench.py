@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--serve-requests", type=int, default=128,
                    help="requests of the serving measurement (0 skips it)")
     p.add_argument("--serve-only", action="store_true")
+    p.add_argument("--no-unrolled", action="store_true",
+                   help="skip the unrolled-inference (forward + reverse) measurement")
+    p.add_argument("--unrolled-only", action="store_true")
     p.add_argument("--batch", type=int, default=1,
                    help="instances per GPU (1 = the benchmark workload; >1 for profiling captures)")
     return p.parse_args()
@@ -265,6 +268,97 @@ def run_dense(args, dev, precision, peak):
             "final_F": F, "eta": float(eta[0]), "Lambda": float(lam[0]), "q": q}
 
 
+UNR_B, UNR_SIDE, UNR_L, UNR_CONN, UNR_K = 16, 256, 21, 4, 10
+
+
+def run_unrolled(args, dev, peak):
+    """Training step through K = 10 unrolled proximal steps on a batch of 16
+    4-connected 256 x 256 grids, L = 21: forward with per-step checkpoints,
+    export of log q^K, cross-entropy gradient, reverse pass to dU, dmu, dw.
+    Inputs resident on the device; the 1.1 GB of checkpoints exceed L2."""
+    import torch
+
+    from paper_1511_06103_gb300 import binding, synth
+    d = synth.unrolled_batch(B=UNR_B, H=UNR_SIDE, W=UNR_SIDE, L=UNR_L, conn=UNR_CONN)
+    B, N, L, K = UNR_B, UNR_SIDE * UNR_SIDE, UNR_L, UNR_K
+    stream = torch.cuda.current_stream(dev)
+    crf = binding.CRF(binding.CRF_GRID4, L, UNR_SIDE, UNR_SIDE, batch=B, stream=stream.cuda_stream)
+    crf.set_unary(torch.from_numpy(d["U"]).to(dev))
+    crf.set_pairwise(torch.from_numpy(d["mu"]).to(dev), torch.from_numpy(d["w"]).to(dev))
+    lam, eta_b = crf.lipschitz()
+    eta = float(np.min(eta_b))         # one step for the batch
+    ckpt = torch.empty(crf.checkpoint_floats(K), dtype=torch.float32, device=dev)
+    logq = torch.empty((B, N, L), dtype=torch.float32, device=dev)
+    y = torch.from_numpy(d["y"].astype(np.int64)).to(dev)
+    g = torch.empty_like(logq)
+    dU = torch.empty_like(logq)
+    dmu = torch.empty((L, L), dtype=torch.float32, device=dev)
+    dw = torch.empty((B, 2, UNR_SIDE, UNR_SIDE), dtype=torch.float32, device=dev)
+    scale = -1.0 / (B * N)
+
+    def step(prof=None):
+        crf.unrolled_forward(K, eta, ckpt)
+        if prof is not None:
+            prof.append(crf.profile_read())
+        crf.log_marginals(logq)
+        g.zero_()
+        g.scatter_(2, y[:, :, None], scale)
+        crf.unrolled_backward(K, eta, ckpt, g, dU, dmu, dw)
+        if prof is not None:
+            prof.append(crf.profile_read())
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    times = []
+    n = max(3, min(args.steps, 10))
+    for _ in range(n):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    # per-step device times of the two loops (a separate pass: reading the
+    # loop events waits on the host between forward and reverse)
+    crf.profile(True)
+    fwd, bwd = [], []
+    for _ in range(n):
+        prof = []
+        step(prof)
+        fwd.append(prof[0][0] / prof[0][1])
+        bwd.append(prof[1][0] / prof[1][1])
+    crf.profile(False)
+    loss = float(-(logq.gather(2, y[:, :, None])).mean().item())
+    launches = crf.launch_count()
+    crf.close()
+    ms = float(np.mean(times))
+    fwd_ms, bwd_ms = float(np.mean(fwd)), float(np.mean(bwd))
+    # algorithmic bytes of one reverse step (both kernels), per pixel: the
+    # softmax part reads gs, log q^{t+1}, dU and writes gm, gs, dU (6 x 4L);
+    # the message part reads gm, log q^t, gs, w, dw and writes gs, dw
+    # (4 x 4L + 3 x 4 n_dirs)
+    bwd_bytes = B * N * (40 * L + 12 * 2)
+    fwd_bytes = B * N * (12 * L + 4 * 2)
+    return {"workload": "unrolled inference, batch 16 of 4-connected 256x256 grids, L=21, K=10, "
+                        "FP32 messages; forward with per-step checkpoints + cross-entropy gradient + "
+                        "reverse pass to dU, dmu, dw",
+            "value": B * N * L * K / (ms / 1000.0), "unit": "updates/s (forward + reverse per update)",
+            "train_steps_per_s": 1000.0 / ms, "ms_per_train_step": ms,
+            "forward_step_ms": fwd_ms, "reverse_step_ms": bwd_ms, "eta": eta, "loss": loss,
+            "roofline_reverse": {"bound": "hbm", "achieved": bwd_bytes / (bwd_ms / 1000.0) / 1e9,
+                                 "peak": peak, "unit": "GB/s",
+                                 "frac": bwd_bytes / (bwd_ms / 1000.0) / 1e9 / peak,
+                                 "bytes_per_step": bwd_bytes,
+                                 "kernels": "adj_softmax_kernel<24> + adj_message_kernel<24>"},
+            "roofline_forward": {"bound": "hbm", "achieved": fwd_bytes / (fwd_ms / 1000.0) / 1e9,
+                                 "peak": peak, "unit": "GB/s",
+                                 "frac": fwd_bytes / (fwd_ms / 1000.0) / 1e9 / peak,
+                                 "bytes_per_step": fwd_bytes, "kernel": "grid_prox_step_kernel<21,4,sym>"},
+            "launches_total": int(launches)}
+
+
 SERVE_SIZES = (64, 86, 116, 156, 210, 283, 380, 512)   # log-uniform sides in [64, 512], quantised
 
 
@@ -371,6 +465,10 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     if args.serve_only:
         print(json.dumps({"serving": run_serving(max(1, args.serve_requests))}), flush=True)
+        return
+    if args.unrolled_only:
+        peak, _ = measured_peaks()
+        print(json.dumps({"unrolled": run_unrolled(args, dev, peak)}), flush=True)
         return
     if args.dense_only:
         peak, _ = measured_peaks()
@@ -502,6 +600,9 @@ def run_ours(args, world, rank, local):
                  "f32": r32, "bf16_tc": r16, "bf16_speedup": r16["value"] / r32["value"],
                  "final_F_rel_diff": abs(r16["final_F"] - r32["final_F"]) / abs(r32["final_F"]),
                  "q_max_abs_diff": dq}
+    unrolled = None
+    if not args.no_unrolled and world == 1:
+        unrolled = run_unrolled(args, dev, peak)
     serving = None
     if args.serve_requests > 0 and world == 1:
         serving = run_serving(args.serve_requests)
@@ -533,6 +634,7 @@ def run_ours(args, world, rank, local):
             "final_F": F_final,
             "wall_ms_timed": 1000 * (wall1 - wall0),
             "dense": dense,
+            "unrolled": unrolled,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)

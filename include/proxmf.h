@@ -24,7 +24,8 @@
  *     device; is_device = 0 means host memory (pinned or pageable).
  *   - External layout of per-variable arrays is [batch][N][L] row-major, N =
  *     height*width, variable p = y*width + x.  The internal device layout is
- *     private (label-planar) and converted when data is set or read.
+ *     private (pixel-major, label count padded) and converted when data is
+ *     set or read.
  *   - A handle is used by one host thread at a time.
  *   - A CUDA error is reported as CRF_E_CUDA and makes the handle unusable
  *     (later calls return CRF_E_STATE).
@@ -154,8 +155,10 @@ crf_status mf_log_marginals(crf_t h, float *logq, int is_device);
 crf_status mf_lipschitz(crf_t h, double *Lambda, double *eta);
 
 /* mf_profile -- enable (1) or disable (0) event timing of the iteration
- * loop: while enabled, mf_iterate brackets its step launches with two CUDA
- * events on the handle's stream.  No synchronisation. */
+ * loop: while enabled, mf_iterate, mf_unrolled_forward and
+ * mf_unrolled_backward bracket their step launches (K forward steps; K
+ * reverse steps of two kernels each) with two CUDA events on the handle's
+ * stream.  No synchronisation. */
 crf_status mf_profile(crf_t h, int32_t enable);
 
 /* mf_profile_read -- device time of the last profiled iteration loop in ms
@@ -165,6 +168,48 @@ crf_status mf_profile_read(crf_t h, double *loop_ms, int32_t *launches);
 
 /* crf_launch_count -- number of kernels this handle has launched so far. */
 crf_status crf_launch_count(crf_t h, int64_t *n);
+
+/* Differentiable unrolled inference (reverse mode through K steps).
+ *
+ * The paper derives the forward iteration only (Sec. 3.1-3.2); the reverse
+ * pass is the chain rule through K parallel proximal steps (Eq.
+ * method:update_natural) taken from q^0 = softmax(-U) with a step eta that is
+ * held constant (not differentiated through Lambda).  Grid topologies only,
+ * n_labels <= 24; other handles return CRF_E_UNSUPPORTED.
+ *
+ * mf_unrolled_checkpoint_floats -- number of floats (4 bytes each) the
+ *   checkpoint buffer of a K-step forward needs: (K+1) states s^0..s^K in
+ *   the private padded layout.  The caller owns that device buffer (for
+ *   autograd it lives as long as the saved tensors).
+ *
+ * mf_unrolled_forward -- reset to s^0 = log softmax(-U), take K steps
+ *   (1 <= K <= 4096) with step eta (0 < eta <= 1: the same eta for every
+ *   instance; eta <= 0: each instance's 1/(1+max(Lambda,0)), computed once
+ *   as in mf_iterate), write s^0..s^K into ckpt (device, at least
+ *   mf_unrolled_checkpoint_floats(K) floats, 16-byte aligned), and leave
+ *   the handle's state at s^K (mf_marginals / mf_log_marginals read it;
+ *   mf_free_energy_trace(K) gives F(q^0..q^{K-1})).  The handle's unary and
+ *   pairwise terms must be set.
+ *
+ * mf_unrolled_backward -- gradients of a scalar loss given dlogq = d loss /
+ *   d log q^K ([batch][N][L], external layout).  Needs the ckpt of a forward
+ *   with the same K and eta on this handle, with unary and pairwise terms
+ *   unchanged since.  Writes
+ *     dU   [batch][N][L]            d loss / d U
+ *     dmu  [L][L]                   d loss / d mu (summed over the batch,
+ *                                   since mu is shared)
+ *     dw   [batch][n_dirs][H][W]    d loss / d w, layout of crf_set_pairwise
+ *                                   (zero for edges that leave the grid).
+ *   Any output may be NULL (not written).  All four arrays are device
+ *   pointers if is_device = 1, else host.  Accumulation order is fixed, so
+ *   results repeat bit for bit.  Scratch memory (about 3 states, the
+ *   weights and (B*N/128) L x L partials) is allocated on first use and kept
+ *   by the handle.
+ */
+crf_status mf_unrolled_checkpoint_floats(crf_t h, int32_t K, int64_t *n_floats);
+crf_status mf_unrolled_forward(crf_t h, int32_t K, double eta, float *ckpt);
+crf_status mf_unrolled_backward(crf_t h, int32_t K, double eta, const float *ckpt, const float *dlogq,
+                                float *dU, float *dmu, float *dw, int32_t is_device);
 
 /* mf_grid_step_noalloc -- one parallel proximal step of a single grid
  * instance on caller-owned device buffers, for callers that cannot allocate

@@ -78,6 +78,9 @@ _SIGS = {
     "mf_profile": [_vp, C.c_int32],
     "mf_profile_read": [_vp, _vp, _vp],
     "crf_launch_count": [_vp, _vp],
+    "mf_unrolled_checkpoint_floats": [_vp, C.c_int32, _vp],
+    "mf_unrolled_forward": [_vp, C.c_int32, C.c_double, _vp],
+    "mf_unrolled_backward": [_vp, C.c_int32, C.c_double, _vp, _vp, _vp, _vp, _vp, C.c_int32],
 }
 
 
@@ -179,6 +182,22 @@ def crf_launch_count(h) -> int:
     n = C.c_int64(0)
     _call("crf_launch_count", h, C.byref(n))
     return n.value
+
+
+def mf_unrolled_checkpoint_floats(h, K: int) -> int:
+    n = C.c_int64(0)
+    _call("mf_unrolled_checkpoint_floats", h, int(K), C.byref(n))
+    return n.value
+
+
+def mf_unrolled_forward(h, K: int, eta: float, ckpt_ptr) -> None:
+    _call("mf_unrolled_forward", h, int(K), float(eta), ckpt_ptr)
+
+
+def mf_unrolled_backward(h, K: int, eta: float, ckpt_ptr, dlogq_ptr, dU_ptr, dmu_ptr, dw_ptr,
+                         is_device: int) -> None:
+    _call("mf_unrolled_backward", h, int(K), float(eta), ckpt_ptr, dlogq_ptr, dU_ptr, dmu_ptr, dw_ptr,
+          int(is_device))
 
 
 def crf_version() -> str:
@@ -303,6 +322,39 @@ class CRF:
 
     def launch_count(self) -> int:
         return crf_launch_count(self.h)
+
+    def checkpoint_floats(self, K: int) -> int:
+        return mf_unrolled_checkpoint_floats(self.h, K)
+
+    def unrolled_forward(self, K: int, eta: float, ckpt) -> None:
+        """K steps from softmax(-U), states s^0..s^K into ``ckpt`` (a device
+        float32 tensor of checkpoint_floats(K) elements)."""
+        p, dev, keep = _as_buffer(ckpt)
+        if not dev:
+            raise ValueError("checkpoints live on the device")
+        mf_unrolled_forward(self.h, K, eta, p)
+
+    def unrolled_backward(self, K: int, eta: float, ckpt, dlogq, dU=None, dmu=None, dw=None):
+        """(dU, dmu, dw) from d loss / d log q^K.  Outputs are allocated like
+        ``dlogq`` (device tensor or host array) when not given."""
+        pc, dc, kc = _as_buffer(ckpt)
+        pg, dg, kg = _as_buffer(dlogq)
+        nd = 4 if self.desc.topology == CRF_GRID8 else 2
+        if dg:
+            import torch
+            dev = kg.device
+            dU = torch.empty((self.B, self.N, self.L), dtype=torch.float32, device=dev) if dU is None else dU
+            dmu = torch.empty((self.L, self.L), dtype=torch.float32, device=dev) if dmu is None else dmu
+            dw = torch.empty((self.B, nd, self.H, self.W), dtype=torch.float32, device=dev) if dw is None else dw
+        else:
+            dU = np.zeros((self.B, self.N, self.L), np.float32) if dU is None else dU
+            dmu = np.zeros((self.L, self.L), np.float32) if dmu is None else dmu
+            dw = np.zeros((self.B, nd, self.H, self.W), np.float32) if dw is None else dw
+        bufs = [_as_buffer(a) for a in (dU, dmu, dw)]
+        if any(b[1] != dg for b in bufs):
+            raise ValueError("gradient outputs must be on the same side as dlogq")
+        mf_unrolled_backward(self.h, K, eta, pc, pg, bufs[0][0], bufs[1][0], bufs[2][0], dg)
+        return dU, dmu, dw
 
     def lipschitz(self):
         lam = np.zeros(self.B, np.float64)

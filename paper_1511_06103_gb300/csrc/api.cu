@@ -2,6 +2,7 @@
 // status mapping.  Host code here only sequences device work; every step of
 // the method runs in the kernels of grid_step*.cu, layout.cu and lanczos.cu.
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -58,6 +59,14 @@ struct crf_s {
     bool prof_valid = false;
     long long launches = 0;
     bool fcur_valid = false;
+    // reverse mode (allocated on first mf_unrolled_backward)
+    float *adj_gs = nullptr;     // [B][N][LP]
+    float *adj_gm = nullptr;     // [B][N][LP]
+    float *adj_dU = nullptr;     // [B][N][LP]
+    float *adj_dw = nullptr;     // [B][N][nd]
+    float *adj_dwx = nullptr;    // [B][nd][H][W] (host-output staging)
+    float *adj_part = nullptr;   // [adjoint_blocks][L][L]
+    float *adj_mu = nullptr;     // [L][L] (+ [L][L] dmu result)
 };
 
 namespace {
@@ -104,6 +113,9 @@ void free_all(crf_t h) {
         if (p) cudaFree(p);
     if (h->tcb.split_part) cudaFree(h->tcb.split_part);
     if (h->tcb.tile_count) cudaFree(h->tcb.tile_count);
+    float *ad[] = {h->adj_gs, h->adj_gm, h->adj_dU, h->adj_dw, h->adj_dwx, h->adj_part, h->adj_mu};
+    for (float *p : ad)
+        if (p) cudaFree(p);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
 }
@@ -380,7 +392,6 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
         ok = ok && dalloc(&h->q32[0], qn) == cudaSuccess;
         ok = ok && dalloc(&h->q32[1], qn) == cudaSuccess;
         ok = ok && dalloc(&h->feats, (size_t)h->B * h->N * 5) == cudaSuccess;
-        ok = ok && dalloc(&h->mu_dev, (size_t)h->L * h->L) == cudaSuccess;
         if (ok) {
             ok = cudaMemsetAsync(h->q32[0], 0, qn * sizeof(float), h->st) == cudaSuccess &&
                  cudaMemsetAsync(h->q32[1], 0, qn * sizeof(float), h->st) == cudaSuccess;
@@ -401,6 +412,7 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
         }
     }
     ok = ok && dalloc(&h->mu_pairs, (size_t)2 * h->LT * mu_pair_slots(h->LT)) == cudaSuccess;
+    ok = ok && dalloc(&h->mu_dev, (size_t)h->L * h->L) == cudaSuccess;
     ok = ok && dalloc(&h->eta_fixed, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->eta_auto, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->Lambda, h->B) == cudaSuccess;
@@ -535,6 +547,7 @@ crf_status crf_set_pairwise(crf_t h, const float *mu, const float *w_or_feats, c
     build_mu_pairs(m, h->L, h->LT, pairs);
     CK(h, cudaMemcpyAsync(h->mu_pairs, pairs.data(), pairs.size() * sizeof(float2), cudaMemcpyHostToDevice,
                           h->st));
+    CK(h, cudaMemcpyAsync(h->mu_dev, m.data(), LL * sizeof(float), cudaMemcpyHostToDevice, h->st));
     const float *src = w_or_feats;
     if (!is_device) {
         // the staging buffer holds B*N*L floats >= B*nd*N only when L >= nd
@@ -723,6 +736,171 @@ crf_status mf_profile_read(crf_t h, double *loop_ms, int32_t *launches) {
 crf_status crf_launch_count(crf_t h, int64_t *n) {
     if (!h || !n) return CRF_E_INVALID;
     *n = h->launches;
+    return CRF_OK;
+}
+
+// ---- reverse mode through K unrolled steps --------------------------------
+
+static crf_status unrolled_check(crf_t h, int32_t K) {
+    crf_status rc = check_handle(h);
+    if (rc != CRF_OK) return rc;
+    if (h->dense || h->L > kAdjointMaxLabels) return CRF_E_UNSUPPORTED;
+    if (K < 1 || K > 4096) return CRF_E_INVALID;
+    return CRF_OK;
+}
+
+static size_t state_floats(const crf_t h) { return n_padded(h); }
+
+static crf_status unrolled_eta(crf_t h, double eta, const float **out) {
+    if (!std::isfinite(eta) || eta > 1.0) return CRF_E_INVALID;
+    if (eta > 0) {
+        CK(h, launch_fill_eta(h->eta_fixed, h->B, eta, h->st));
+        h->launches++;
+        *out = h->eta_fixed;
+        return CRF_OK;
+    }
+    crf_status rc = ensure_lambda(h);
+    if (rc != CRF_OK) return rc;
+    *out = h->eta_auto;
+    return CRF_OK;
+}
+
+crf_status mf_unrolled_checkpoint_floats(crf_t h, int32_t K, int64_t *n_floats) {
+    crf_status rc = unrolled_check(h, K);
+    if (rc != CRF_OK) return rc;
+    if (!n_floats) return CRF_E_INVALID;
+    *n_floats = (int64_t)(K + 1) * (int64_t)state_floats(h);
+    return CRF_OK;
+}
+
+crf_status mf_unrolled_forward(crf_t h, int32_t K, double eta, float *ckpt) {
+    crf_status rc = unrolled_check(h, K);
+    if (rc != CRF_OK) return rc;
+    if (!ckpt || ((uintptr_t)ckpt & 15)) return CRF_E_INVALID;
+    if (!h->has_unary || !h->has_pairwise) return CRF_E_INVALID;
+    const float *e = nullptr;
+    rc = unrolled_eta(h, eta, &e);
+    if (rc != CRF_OK) return rc;
+    rc = ensure_trace(h, K);
+    if (rc != CRF_OK) return rc;
+    const size_t S = state_floats(h);
+    CK(h, launch_init_logq(h->U, ckpt, (long long)n_pix(h), h->L, h->LP, h->st));
+    if (h->profile) CK(h, cudaEventRecord(h->ev0, h->st));
+    for (int t = 0; t < K; ++t) {
+        GridStepLaunch a = step_args(h, e, t, 1, 0.0);
+        a.done = nullptr;
+        a.s_in = ckpt + (size_t)t * S;
+        a.s_out = ckpt + (size_t)(t + 1) * S;
+        CK(h, launch_grid_step(a, h->st));
+    }
+    if (h->profile) {
+        CK(h, cudaEventRecord(h->ev1, h->st));
+        h->prof_launches = K;
+        h->prof_valid = true;
+    }
+    CK(h, cudaMemcpyAsync(h->s[h->cur], ckpt + (size_t)K * S, S * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+    h->launches += 1 + K;
+    h->last_iters = K;
+    h->fcur_valid = false;
+    return CRF_OK;
+}
+
+crf_status mf_unrolled_backward(crf_t h, int32_t K, double eta, const float *ckpt, const float *dlogq,
+                                float *dU, float *dmu, float *dw, int32_t is_device) {
+    crf_status rc = unrolled_check(h, K);
+    if (rc != CRF_OK) return rc;
+    if (!ckpt || !dlogq || ((uintptr_t)ckpt & 15)) return CRF_E_INVALID;
+    if (!h->has_pairwise) return CRF_E_INVALID;
+    const size_t S = state_floats(h);
+    const size_t nw = n_pix(h) * h->nd;
+    const size_t LL = (size_t)h->L * h->L;
+    const int nblk = adjoint_blocks((long long)n_pix(h));
+    if (!h->adj_gs) {
+        bool ok = true;
+        ok = ok && dalloc(&h->adj_gs, S) == cudaSuccess;
+        ok = ok && dalloc(&h->adj_gm, S) == cudaSuccess;
+        ok = ok && dalloc(&h->adj_dU, S) == cudaSuccess;
+        ok = ok && dalloc(&h->adj_dw, nw) == cudaSuccess;
+        ok = ok && dalloc(&h->adj_dwx, nw) == cudaSuccess;
+        ok = ok && dalloc(&h->adj_part, (size_t)nblk * LL) == cudaSuccess;
+        ok = ok && dalloc(&h->adj_mu, LL) == cudaSuccess;
+        if (!ok) {
+            (void)cudaGetLastError();
+            float *ad[] = {h->adj_gs, h->adj_gm, h->adj_dU, h->adj_dw, h->adj_dwx, h->adj_part, h->adj_mu};
+            for (float *p : ad)
+                if (p) cudaFree(p);
+            h->adj_gs = h->adj_gm = h->adj_dU = h->adj_dw = h->adj_dwx = h->adj_part = h->adj_mu = nullptr;
+            return CRF_E_OOM;
+        }
+    }
+    const float *e = nullptr;
+    rc = unrolled_eta(h, eta, &e);
+    if (rc != CRF_OK) return rc;
+    const float *src = dlogq;
+    if (!is_device) {
+        CK(h, cudaMemcpyAsync(h->staging, dlogq, n_rows(h) * sizeof(float), cudaMemcpyHostToDevice, h->st));
+        src = h->staging;
+    }
+    CK(h, launch_rows_to_padded(src, h->adj_gs, (long long)n_pix(h), h->L, h->LP, 0.f, h->st));
+    CK(h, cudaMemsetAsync(h->adj_gm, 0, S * sizeof(float), h->st));
+    CK(h, cudaMemsetAsync(h->adj_dU, 0, S * sizeof(float), h->st));
+    CK(h, cudaMemsetAsync(h->adj_dw, 0, nw * sizeof(float), h->st));
+    CK(h, cudaMemsetAsync(h->adj_part, 0, (size_t)nblk * LL * sizeof(float), h->st));
+    h->launches++;
+    AdjointStep a{};
+    a.gs = h->adj_gs;
+    a.gm = h->adj_gm;
+    a.dU = h->adj_dU;
+    a.dw = h->adj_dw;
+    a.dmu_part = h->adj_part;
+    a.w = h->w;
+    a.mu = h->mu_dev;
+    a.eta = e;
+    a.B = h->B;
+    a.L = h->L;
+    a.H = h->H;
+    a.W = h->W;
+    a.conn = h->conn;
+    if (h->profile) CK(h, cudaEventRecord(h->ev0, h->st));
+    for (int t = K - 1; t >= 0; --t) {
+        a.s = ckpt + (size_t)t * S;
+        a.s_next = ckpt + (size_t)(t + 1) * S;
+        CK(h, launch_adjoint_step(a, h->st));
+    }
+    if (h->profile) {
+        CK(h, cudaEventRecord(h->ev1, h->st));
+        h->prof_launches = K;
+        h->prof_valid = true;
+    }
+    h->launches += 2ll * K;
+    AdjointFinish f{};
+    f.gs = h->adj_gs;
+    f.s0 = ckpt;
+    f.dU = h->adj_dU;
+    f.dw = h->adj_dw;
+    f.dw_out = (is_device && dw) ? dw : h->adj_dwx;
+    f.dmu_part = h->adj_part;
+    f.dmu_out = h->adj_mu;
+    f.B = h->B;
+    f.L = h->L;
+    f.H = h->H;
+    f.W = h->W;
+    f.conn = h->conn;
+    CK(h, launch_adjoint_finish(f, h->st));
+    h->launches += 3;
+    if (dU) {
+        float *out = is_device ? dU : h->staging;
+        CK(h, launch_padded_to_rows(h->adj_dU, out, (long long)n_pix(h), h->L, h->LP, CONV_COPY, h->st));
+        h->launches++;
+        if (!is_device)
+            CK(h, cudaMemcpyAsync(dU, h->staging, n_rows(h) * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+    }
+    if (dmu)
+        CK(h, cudaMemcpyAsync(dmu, h->adj_mu, LL * sizeof(float),
+                              is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+    if (dw && !is_device)
+        CK(h, cudaMemcpyAsync(dw, h->adj_dwx, nw * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+    if (!is_device) CK(h, cudaStreamSynchronize(h->st));
     return CRF_OK;
 }
 

@@ -172,4 +172,35 @@ struct LipschitzJob {
 int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps_out,
                             long long *launches_out);
 
+
+// Reverse mode through unrolled grid steps (adjoint.cu).  All arrays are in
+// the padded pixel-major layout of the step kernel; L <= 24.
+constexpr int kAdjointMaxLabels = 24;
+struct AdjointStep {
+    float *gs;               // [B][N][LP] in: d/ds^{t+1}; out: d/ds^t
+    float *gm;               // [B][N][LP] scratch: d/dm
+    float *dU;               // [B][N][LP] accumulated
+    float *dw;               // [B][N][n_dirs] accumulated
+    float *dmu_part;         // [adjoint_blocks][L][L] accumulated per-block partials
+    const float *s;          // s^t
+    const float *s_next;     // s^{t+1}
+    const float *w;          // [B][N][n_dirs]
+    const float *mu;         // [L][L] device
+    const float *eta;        // [B]
+    int B, L, H, W, conn;
+};
+struct AdjointFinish {
+    const float *gs;         // d/ds^0
+    const float *s0;         // s^0 = log softmax(-U)
+    float *dU;               // accumulated, padded layout
+    const float *dw;         // pixel-major accumulated
+    float *dw_out;           // [B][n_dirs][H][W]
+    const float *dmu_part;
+    float *dmu_out;          // [L][L]
+    int B, L, H, W, conn;
+};
+int adjoint_blocks(long long rows);
+cudaError_t launch_adjoint_step(const AdjointStep &a, cudaStream_t st);
+cudaError_t launch_adjoint_finish(const AdjointFinish &a, cudaStream_t st);
+
 }  // namespace proxmf

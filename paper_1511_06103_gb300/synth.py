@@ -155,6 +155,25 @@ def segmentation_grid(H: int = 512, W: int = 512, L: int = 21, conn: int = 8,
                 seed=seed)
 
 
+def unrolled_batch(B: int = 16, H: int = 256, W: int = 256, L: int = 21, conn: int = 4,
+                   logit_std: float = 2.0, sigma_rgb: float = 0.1, seed: int = 4) -> dict:
+    """A batch for training through unrolled inference: per-instance unaries
+    and colour-derived edge weights (as segmentation_grid), one mu shared by
+    the batch, and a seeded label map y per instance (argmax of a smooth
+    random field, so labels come in regions like a segmentation)."""
+    rng = np.random.default_rng(seed)
+    m = symmetric_uniform(L, rng)
+    U = np.empty((B, H * W, L))
+    w = np.empty((B, n_dirs(conn), H, W))
+    y = np.empty((B, H * W), np.int32)
+    for b in range(B):
+        U[b] = unary_from_logits(rng.normal(0.0, logit_std, size=(H * W, L)))
+        w[b] = edge_weights_from_colour(smooth_field(H, W, 3, rng), conn, sigma_rgb)
+        y[b] = np.argmax(smooth_field(H, W, L, rng), axis=0).reshape(-1)
+    return dict(kind="grid", B=B, H=H, W=W, L=L, conn=conn, U=_f32(U), mu=_f32(m), w=_f32(w), y=y,
+                seed=seed)
+
+
 def random_grid(H: int, W: int, L: int, conn: int, seed: int, symmetric: bool = True,
                 coupling_scale: float = 1.0, unary_scale: float = 2.0) -> dict:
     """Generic test instance: random unaries, random (a)symmetric mu, random w."""
