@@ -7,15 +7,22 @@
 // Backward, with gs = d loss / d s' given:
 //   ga = gs - q' sum_l gs                     (log-softmax)
 //   dU += -eta ga,  gm = -eta ga              (affine step)
-//   gs_prev = (1 - eta) ga + q (.) (H gm)     (H is symmetric)
+//   gs_prev = (1 - eta) ga + q (.) (H gm)     (H is symmetric as a whole)
 //   dw_{i->j} += gm_i^T mu q_j + q_i^T mu gm_j
-//   dmu += sum_i gm_i S_i^T + T_i gm_i^T,  S_i = sum_{i->j} w q_j, T_i = sum_{k->i} w q_k
-// and finally through s^0: dU += -(gs - q^0 sum_l gs).
+//   dmu += sum_i gm_i S_i^T + q_i Gout_i^T,  S_i = sum_{i->j} w q_j, Gout_i = sum_{i->j} w gm_j
+// (every edge counted once, at its source), and finally through s^0:
+// dU += -(gs - q^0 sum_l gs).
+//
+// One fused kernel per reverse step.  A block owns a 32 x 4 tile of pixels
+// and stages ga and q^t of the tile and a one-pixel halo in shared memory
+// (ga of the halo is recomputed from gs and s^{t+1}, which is cheaper than a
+// separate pass over the pixels); gm = -eta ga is applied as a factor at the
+// end of each product.  The dmu contribution of the tile is a small block
+// GEMM [ga | q]^T [S | Gout] over its 128 pixels, register-tiled 4 x 4.
 // The forward keeps every s^t (checkpoints) so the backward needs no
-// recomputation of the trajectory; each backward step is two kernels over the
-// pixels.  Every gradient is accumulated by the thread or block that owns it
-// (dmu through per-block partials reduced in a fixed order), so results do
-// not depend on scheduling.
+// recomputation of the trajectory.  Every gradient is accumulated by the
+// thread or block that owns it (dmu through per-block partials reduced in a
+// fixed order), so results do not depend on scheduling.
 #include <cmath>
 
 #include "internal.h"
@@ -24,166 +31,309 @@ namespace proxmf {
 
 namespace {
 
-constexpr int kAT = 128;   // 3 x kAT x 24 floats of shared memory stay under 48 KB
+template <int LT>
+struct AdjCfg {
+    static constexpr int LP = storage_labels(LT);
+    static constexpr int VW = LP % 4 == 0 ? 4 : 2;          // vector width of a row access
+    static constexpr int LS = LP % 8 == 0 ? LP + 4 : LP;    // row stride of the halo rows
+    static constexpr int LSS = LP;                          // row stride of the S / Gout rows
+    static constexpr int TX = 32, TY = 4, NT = TX * TY;
+    static constexpr int HX = TX + 2, HY = TY + 2, HR = HX * HY;
+    static constexpr int TS = VW;                           // dmu register tile TS x TS
+    static constexpr int NTB = LP / TS, NTILE = NTB * NTB;
+    static constexpr int NG = NT / NTILE > 0 ? NT / NTILE : 1;   // pixel groups of the dmu GEMM
+    __host__ __device__ static constexpr int mu_floats(bool sym) { return (sym ? 1 : 2) * LP * LP; }
+    __host__ __device__ static constexpr size_t smem_bytes(bool sym) {
+        return sizeof(float) * ((size_t)mu_floats(sym) + 2 * (size_t)HR * LS + 2 * (size_t)NT * LSS);
+    }
+    // the dmu reduction scratch reuses everything after mu
+    static_assert(NG * LP * LP <= 2 * HR * LS + 2 * NT * LSS, "dmu scratch does not fit");
+};
 
-__device__ __forceinline__ void adj_dir(int k, int *dy, int *dx) {
-    *dy = k == 0 ? 0 : 1;
-    *dx = k == 0 ? 1 : (k == 1 ? 0 : (k == 2 ? 1 : -1));
+template <int VW>
+__device__ __forceinline__ void vget(const float *p, float *v) {
+    if constexpr (VW == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    } else {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        v[0] = t.x, v[1] = t.y;
+    }
 }
 
+template <int VW>
+__device__ __forceinline__ void vput(float *p, const float *v) {
+    if constexpr (VW == 4)
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+}
+
+// Direction d of an edge leaving a pixel: 0 right, 1 down, 2 down-right, 3 down-left.
+__host__ __device__ constexpr int dir_dy(int d) { return d == 0 ? 0 : 1; }
+__host__ __device__ constexpr int dir_dx(int d) { return d == 0 ? 1 : (d == 1 ? 0 : (d == 2 ? 1 : -1)); }
+
 // Keeps the compiler from carrying shared-memory loads (the L x L matrix)
-// in registers from one phase of a kernel to the next.
+// in registers from one phase of the kernel to the next.
 __device__ __forceinline__ void reload_fence() { asm volatile("" ::: "memory"); }
 
-// ga = gs - q' sum gs; gm = -eta ga; gs <- (1 - eta) ga; dU += -eta ga.
-template <int LP>
-__global__ void adj_softmax_kernel(float *gs, float *gm, float *dU, const float *s_next, const float *eta, int B,
-                                   int N, int L) {
-    const long long n = (long long)B * N;
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
-         r += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(r / N);
-        const float e = eta[b];
-        const size_t o = (size_t)r * LP;
-        float g[LP], sum = 0.f;
+template <int LT, int CONN, bool SYM>
+__global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep a) {
+    using C = AdjCfg<LT>;
+    constexpr int LP = C::LP, VW = C::VW, LS = C::LS, LSS = C::LSS, TX = C::TX, HX = C::HX, NT = C::NT;
+    constexpr int ND = CONN == 8 ? 4 : 2;
+    extern __shared__ __align__(16) float smem[];
+    float *mus = smem;                                     // mu [LP][LP], row k = mu[k][.]
+    float *muT = smem + LP * LP;                           // mu^T (asymmetric mu only)
+    float *sga = smem + C::mu_floats(SYM);                 // [HR][LS] ga of tile + halo
+    float *sq = sga + C::HR * LS;                          // [HR][LS] q^t of tile + halo
+    float *sS = sq + C::HR * LS;                           // [NT][LSS] S_i
+    float *sG = sS + NT * LSS;                             // [NT][LSS] sum_{i->j} w ga_j
+
+    const int tid = threadIdx.x;
+    const int b = blockIdx.z;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * C::TY;
+    const int H = a.H, W = a.W, L = a.L;
+    const size_t N = (size_t)H * W;
+    const size_t base = (size_t)b * N;
+    const float eta = a.eta[b];
+
+    for (int i = tid; i < LP * LP; i += NT) {
+        const int r = i / LP, c = i - r * LP;
+        const float v = (r < L && c < L) ? a.mu[r * L + c] : 0.f;
+        mus[i] = v;
+        if (!SYM) muT[c * LP + r] = v;
+    }
+    // Phase 1: ga and q^t of the tile and its halo (zero outside the image).
+    for (int r = tid; r < C::HR; r += NT) {
+        const int hy = r / HX, hx = r - hy * HX;
+        const int y = y0 - 1 + hy, x = x0 - 1 + hx;
+        float *gr = sga + r * LS, *qr = sq + r * LS;
+        if (y < 0 || y >= H || x < 0 || x >= W) {
+            float z[VW] = {};
+#pragma unroll
+            for (int l = 0; l < LP; l += VW) {
+                vput<VW>(gr + l, z);
+                vput<VW>(qr + l, z);
+            }
+            continue;
+        }
+        const size_t o = (base + (size_t)y * W + x) * LP;
+        float g[LP], qn[LP];
+        float sum = 0.f;
+#pragma unroll
+        for (int l = 0; l < LP; l += VW) {
+            vget<VW>(a.gs_in + o + l, g + l);
+            vget<VW>(a.s_next + o + l, qn + l);
+        }
 #pragma unroll
         for (int l = 0; l < LP; ++l) {
-            g[l] = l < L ? gs[o + l] : 0.f;
+            g[l] = l < L ? g[l] : 0.f;
             sum += g[l];
         }
 #pragma unroll
-        for (int l = 0; l < LP; ++l) {
-            if (l >= L) continue;
-            const float ga = g[l] - __expf(s_next[o + l]) * sum;
-            gm[o + l] = -e * ga;
-            gs[o + l] = (1.f - e) * ga;
-            dU[o + l] += -e * ga;
-        }
-    }
-}
-
-// gs += q (.) (H gm); dw and the per-block dmu partial.  Per-thread
-// registers hold at most four label vectors at a time; S, T and gm of the
-// block's pixels go to shared memory ([label][pixel], stride kAT + 1 so that
-// both the per-pixel and the per-entry access patterns are conflict free).
-template <int LP>
-__global__ void __launch_bounds__(kAT) adj_message_kernel(float *gs, const float *gm, const float *s, const float *w,
-                                                        const float *mu, float *dw, float *dmu_part, int B, int H,
-                                                        int W, int L, int conn) {
-    constexpr int SP = kAT + 1;
-    __shared__ float mus[LP * LP];   // mu zero padded to LP x LP
-    __shared__ float sg[LP * SP], sS[LP * SP], sT[LP * SP];
-    const int nd = conn == 8 ? 4 : 2;
-    for (int i = threadIdx.x; i < LP * LP; i += blockDim.x) {
-        const int r = i / LP, c = i - r * LP;
-        mus[i] = (r < L && c < L) ? mu[r * L + c] : 0.f;
-    }
-    const int N = H * W;
-    const int tid = threadIdx.x;
-    const long long r = blockIdx.x * (long long)kAT + tid;
-    const bool act = r < (long long)B * N;
-    const int b = act ? (int)(r / N) : 0;
-    const int p = act ? (int)(r - (long long)b * N) : 0;
-    const int y = p / W, x = p - y * W;
-    const size_t base = (size_t)b * N;
-    const size_t o = (base + p) * LP;
-    float qi[LP], v1[LP], v2[LP];
+        for (int l = 0; l < LP; ++l) g[l] = l < L ? g[l] - __expf(qn[l]) * sum : 0.f;
 #pragma unroll
-    for (int l = 0; l < LP; ++l) {
-        const float g = (act && l < L) ? gm[o + l] : 0.f;
-        sg[l * SP + tid] = g;
-        sS[l * SP + tid] = 0.f;
-        sT[l * SP + tid] = 0.f;
-        qi[l] = (act && l < L) ? __expf(s[o + l]) : 0.f;
+        for (int l = 0; l < LP; l += VW) vput<VW>(gr + l, g + l);
+#pragma unroll
+        for (int l = 0; l < LP; l += VW) vget<VW>(a.s + o + l, qn + l);
+#pragma unroll
+        for (int l = 0; l < LP; ++l) qn[l] = l < L ? __expf(qn[l]) : 0.f;
+#pragma unroll
+        for (int l = 0; l < LP; l += VW) vput<VW>(qr + l, qn + l);
     }
     __syncthreads();
-    // v1 = mu^T gm_i, v2 = mu^T q_i (edge gradients of out-going edges)
-#pragma unroll
-    for (int l = 0; l < LP; ++l) {
-        float a1 = 0.f, a2 = 0.f;
-#pragma unroll
-        for (int k = 0; k < LP; ++k) {
-            a1 = fmaf(mus[k * LP + l], sg[k * SP + tid], a1);
-            a2 = fmaf(mus[k * LP + l], qi[k], a2);
-        }
-        v1[l] = a1;
-        v2[l] = a2;
-    }
-    float hacc[LP];
-    reload_fence();
+
+    // Phase 2: own pixel.
+    const int tx = tid % TX, ty = tid / TX;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool act = x < W && y < H;
+    const size_t p = base + (size_t)(act ? y : 0) * W + (act ? x : 0);
+    const int ri = (ty + 1) * HX + (tx + 1);
+    const float *ga_i = sga + ri * LS;
+    const float *q_i = sq + ri * LS;
+    float h[LP];
     {
-        float G[LP];
+        // v1 = mu^T ga_i, v2 = mu^T q_i
+        float v1[LP], v2[LP];
 #pragma unroll
-        for (int l = 0; l < LP; ++l) G[l] = 0.f;
-        for (int d = 0; act && d < nd; ++d) {                    // out-going edges p -> j
-            int dy, dx;
-            adj_dir(d, &dy, &dx);
-            const int yo = y + dy, xo = x + dx;
-            if (yo >= H || xo < 0 || xo >= W) continue;
-            const size_t j = (base + (size_t)yo * W + xo) * LP;
-            const float wv = w[(base + p) * nd + d];
+        for (int l = 0; l < LP; ++l) v1[l] = v2[l] = 0.f;
+#pragma unroll
+        for (int k = 0; k < LT; ++k) {
+            const float gk = ga_i[k], qk = q_i[k];
+#pragma unroll
+            for (int l = 0; l < LP; l += VW) {
+                float m[VW];
+                vget<VW>(mus + k * LP + l, m);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) {
+                    v1[l + u] = fmaf(m[u], gk, v1[l + u]);
+                    v2[l + u] = fmaf(m[u], qk, v2[l + u]);
+                }
+            }
+        }
+        reload_fence();
+        float G[LP], S[LP];
+#pragma unroll
+        for (int l = 0; l < LP; ++l) G[l] = S[l] = 0.f;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {                   // out-going edges i -> j
+            const int yj = y + dir_dy(d), xj = x + dir_dx(d);
+            const bool ok = act && yj < H && xj >= 0 && xj < W;
+            const float wv = ok ? a.w[p * ND + d] : 0.f;
+            const float *gj = sga + (ri + dir_dy(d) * HX + dir_dx(d)) * LS;
+            const float *qj = sq + (ri + dir_dy(d) * HX + dir_dx(d)) * LS;
             float de = 0.f;
 #pragma unroll
-            for (int l = 0; l < LP; ++l) {
-                if (l >= L) continue;
-                const float gj = gm[j + l], qj = __expf(s[j + l]);
-                G[l] = fmaf(wv, gj, G[l]);
-                sS[l * SP + tid] = fmaf(wv, qj, sS[l * SP + tid]);
-                de = fmaf(v1[l], qj, fmaf(v2[l], gj, de));
+            for (int l = 0; l < LP; l += VW) {
+                float gv[VW], qv[VW];
+                vget<VW>(gj + l, gv);
+                vget<VW>(qj + l, qv);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) {
+                    G[l + u] = fmaf(wv, gv[u], G[l + u]);
+                    S[l + u] = fmaf(wv, qv[u], S[l + u]);
+                    de = fmaf(v1[l + u], qv[u], fmaf(v2[l + u], gv[u], de));
+                }
             }
-            dw[(base + p) * nd + d] += de;
+            if (ok) a.dw[p * ND + d] += -eta * de;
+        }
+#pragma unroll
+        for (int l = 0; l < LP; l += VW) {
+            vput<VW>(sS + tid * LSS + l, S + l);
+            vput<VW>(sG + tid * LSS + l, G + l);
         }
         reload_fence();
 #pragma unroll
-        for (int l = 0; l < LP; ++l) {                          // hacc = mu G
-            float h = 0.f;
+        for (int l = 0; l < LP; ++l) h[l] = 0.f;
+        if (!SYM) {
+            // h = mu Gout = sum_k mu^T[k][.] Gout[k]
 #pragma unroll
-            for (int k = 0; k < LP; ++k) h = fmaf(mus[l * LP + k], G[k], h);
-            hacc[l] = h;
+            for (int k = 0; k < LT; ++k) {
+#pragma unroll
+                for (int l = 0; l < LP; l += VW) {
+                    float m[VW];
+                    vget<VW>(muT + k * LP + l, m);
+#pragma unroll
+                    for (int u = 0; u < VW; ++u) h[l + u] = fmaf(m[u], G[k], h[l + u]);
+                }
+            }
         }
     }
     reload_fence();
     {
+        // in-coming edges k -> i; symmetric mu folds Gout in: h = mu (Gout + Gin)
         float G[LP];
 #pragma unroll
-        for (int l = 0; l < LP; ++l) G[l] = 0.f;
-        for (int d = 0; act && d < nd; ++d) {                    // in-coming edges k -> p
-            int dy, dx;
-            adj_dir(d, &dy, &dx);
-            const int yi = y - dy, xi = x - dx;
-            if (yi < 0 || xi < 0 || xi >= W) continue;
-            const size_t k = base + (size_t)yi * W + xi;
-            const float wv = w[k * nd + d];
+        for (int l = 0; l < LP; ++l) G[l] = SYM ? sG[tid * LSS + l] : 0.f;
 #pragma unroll
-            for (int l = 0; l < LP; ++l) {
-                if (l >= L) continue;
-                G[l] = fmaf(wv, gm[k * LP + l], G[l]);
-                sT[l * SP + tid] = fmaf(wv, __expf(s[k * LP + l]), sT[l * SP + tid]);
+        for (int d = 0; d < ND; ++d) {
+            const int yk = y - dir_dy(d), xk = x - dir_dx(d);
+            const bool ok = act && yk >= 0 && xk >= 0 && xk < W;
+            const float wv = ok ? a.w[(base + (size_t)yk * W + xk) * ND + d] : 0.f;
+            const float *gk = sga + (ri - dir_dy(d) * HX - dir_dx(d)) * LS;
+#pragma unroll
+            for (int l = 0; l < LP; l += VW) {
+                float gv[VW];
+                vget<VW>(gk + l, gv);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) G[l + u] = fmaf(wv, gv[u], G[l + u]);
             }
         }
         reload_fence();
+        // h += mu^T G  (= sum_k mu[k][.] G[k])
 #pragma unroll
-        for (int l = 0; l < LP; ++l) {                          // hacc += mu^T G
-            float h = hacc[l];
+        for (int k = 0; k < LT; ++k) {
 #pragma unroll
-            for (int k = 0; k < LP; ++k) h = fmaf(mus[k * LP + l], G[k], h);
-            hacc[l] = h;
+            for (int l = 0; l < LP; l += VW) {
+                float m[VW];
+                vget<VW>(mus + k * LP + l, m);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) h[l + u] = fmaf(m[u], G[k], h[l + u]);
+            }
         }
     }
     if (act) {
+        const size_t o = p * LP;
+        const float c1 = 1.f - eta;
 #pragma unroll
-        for (int l = 0; l < LP; ++l)
-            if (l < L) gs[o + l] += qi[l] * hacc[l];
+        for (int l = 0; l < LP; l += VW) {
+            float gv[VW], qv[VW], out[VW], du[VW];
+            vget<VW>(ga_i + l, gv);
+            vget<VW>(q_i + l, qv);
+            vget<VW>(a.dU + o + l, du);
+#pragma unroll
+            for (int u = 0; u < VW; ++u) {
+                out[u] = fmaf(c1, gv[u], -eta * qv[u] * h[l + u]);
+                du[u] = fmaf(-eta, gv[u], du[u]);
+            }
+            vput<VW>(a.gs_out + o + l, out);
+            vput<VW>(a.dU + o + l, du);
+        }
     }
     __syncthreads();
-    // dmu partial of this block: sum over its pixels of gm_i S_i^T + T_i gm_i^T
-    for (int e = tid; e < L * L; e += kAT) {
-        const int a = e / L, c = e - a * L;
-        float acc = 0.f;
-        for (int t = 0; t < kAT; ++t)
-            acc = fmaf(sg[a * SP + t], sS[c * SP + t], fmaf(sT[a * SP + t], sg[c * SP + t], acc));
-        dmu_part[(size_t)blockIdx.x * L * L + e] += acc;
+
+    // Phase 3: dmu partial = -eta ([ga | q]^T [S | Gout]) over the tile's pixels.
+    constexpr int TS = C::TS, NTB = C::NTB, NTILE = C::NTILE, NG = C::NG;
+    float acc[TS][TS];
+#pragma unroll
+    for (int i = 0; i < TS; ++i)
+#pragma unroll
+        for (int j = 0; j < TS; ++j) acc[i][j] = 0.f;
+    const int tile = tid % NTILE, grp = tid / NTILE;
+    const int a0 = (tile / NTB) * TS, c0 = (tile % NTB) * TS;
+    if (grp < NG) {
+        for (int i = grp; i < NT; i += NG) {
+            const int r = (i / TX + 1) * HX + (i % TX + 1);
+            float ga[TS], qa[TS], sv[TS], gv[TS];
+            vget<TS>(sga + r * LS + a0, ga);
+            vget<TS>(sq + r * LS + a0, qa);
+            vget<TS>(sS + i * LSS + c0, sv);
+            vget<TS>(sG + i * LSS + c0, gv);
+#pragma unroll
+            for (int u = 0; u < TS; ++u)
+#pragma unroll
+                for (int v = 0; v < TS; ++v) acc[u][v] = fmaf(ga[u], sv[v], fmaf(qa[u], gv[v], acc[u][v]));
+        }
     }
+    __syncthreads();
+    float *red = sga;                                      // [NG][LP][LP], reuses the ga rows
+    if (grp < NG) {
+#pragma unroll
+        for (int u = 0; u < TS; ++u)
+#pragma unroll
+            for (int v = 0; v < TS; ++v) red[(grp * LP + a0 + u) * LP + c0 + v] = acc[u][v];
+    }
+    __syncthreads();
+    const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    for (int e = tid; e < L * L; e += NT) {
+        const int ea = e / L, ec = e - ea * L;
+        float t = 0.f;
+        for (int g = 0; g < NG; ++g) t += red[(g * LP + ea) * LP + ec];
+        a.dmu_part[blk * L * L + e] += -eta * t;
+    }
+}
+
+template <int LT, int CONN, bool SYM>
+cudaError_t launch_adj(const AdjointStep &a, cudaStream_t st) {
+    using C = AdjCfg<LT>;
+    const size_t smem = C::smem_bytes(SYM);
+    static bool attr = false;   // set once per instantiation (first use on this device)
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(adj_step_kernel<LT, CONN, SYM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((a.W + C::TX - 1) / C::TX, (a.H + C::TY - 1) / C::TY, a.B);
+    adj_step_kernel<LT, CONN, SYM><<<grid, C::NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int LT>
+cudaError_t launch_adj_lt(const AdjointStep &a, cudaStream_t st) {
+    if (a.conn == 8) return a.mu_sym ? launch_adj<LT, 8, true>(a, st) : launch_adj<LT, 8, false>(a, st);
+    return a.mu_sym ? launch_adj<LT, 4, true>(a, st) : launch_adj<LT, 4, false>(a, st);
 }
 
 // Through s^0 = logsoftmax(-U): dU += -(gs - q^0 sum gs).
@@ -233,33 +383,24 @@ inline int nb(long long n, int t) { return (int)std::min<long long>((n + t - 1) 
 
 }  // namespace
 
-cudaError_t launch_adjoint_step(const AdjointStep &a, cudaStream_t st) {
-    const long long rows = (long long)a.B * a.H * a.W;
-    const int LP = storage_labels(a.L);
-    const int nblk = (int)((rows + kAT - 1) / kAT);
-#define PROXMF_ADJ(LPV)                                                                                         \
-    case LPV:                                                                                                   \
-        adj_softmax_kernel<LPV><<<nb(rows, 256), 256, 0, st>>>(a.gs, a.gm, a.dU, a.s_next, a.eta, a.B,          \
-                                                               a.H * a.W, a.L);                                \
-        adj_message_kernel<LPV><<<nblk, kAT, 0, st>>>(a.gs, a.gm, a.s, a.w, a.mu, a.dw, a.dmu_part, a.B, a.H,   \
-                                                      a.W, a.L, a.conn);                                        \
-        break;
-    switch (LP) {
-        PROXMF_ADJ(2)
-        PROXMF_ADJ(4)
-        PROXMF_ADJ(8)
-        PROXMF_ADJ(12)
-        PROXMF_ADJ(16)
-        PROXMF_ADJ(20)
-        PROXMF_ADJ(24)
-    default:
-        return cudaErrorInvalidValue;
-    }
-#undef PROXMF_ADJ
-    return cudaGetLastError();
+int adjoint_blocks(int B, int H, int W) {
+    using C = AdjCfg<2>;
+    return B * ((H + C::TY - 1) / C::TY) * ((W + C::TX - 1) / C::TX);
 }
 
-int adjoint_blocks(long long rows) { return (int)((rows + kAT - 1) / kAT); }
+cudaError_t launch_adjoint_step(const AdjointStep &a, cudaStream_t st) {
+    switch (kernel_labels(a.L)) {
+    case 2: return launch_adj_lt<2>(a, st);
+    case 4: return launch_adj_lt<4>(a, st);
+    case 8: return launch_adj_lt<8>(a, st);
+    case 12: return launch_adj_lt<12>(a, st);
+    case 16: return launch_adj_lt<16>(a, st);
+    case 20: return launch_adj_lt<20>(a, st);
+    case 21: return launch_adj_lt<21>(a, st);
+    case 24: return launch_adj_lt<24>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_adjoint_finish(const AdjointFinish &a, cudaStream_t st) {
     const long long rows = (long long)a.B * a.H * a.W;
@@ -274,7 +415,8 @@ cudaError_t launch_adjoint_finish(const AdjointFinish &a, cudaStream_t st) {
     case 24: adj_init_kernel<24><<<nb(rows, 256), 256, 0, st>>>(a.gs, a.s0, a.dU, rows, a.L); break;
     default: return cudaErrorInvalidValue;
     }
-    adj_dmu_reduce_kernel<<<a.L * a.L, 256, 0, st>>>(a.dmu_part, adjoint_blocks(rows), a.L * a.L, a.dmu_out);
+    adj_dmu_reduce_kernel<<<a.L * a.L, 256, 0, st>>>(a.dmu_part, adjoint_blocks(a.B, a.H, a.W), a.L * a.L,
+                                                     a.dmu_out);
     const int nd = a.conn == 8 ? 4 : 2;
     adj_dw_out_kernel<<<nb(rows * nd, 256), 256, 0, st>>>(a.dw, a.dw_out, a.B, nd, a.H, a.W);
     return cudaGetLastError();

@@ -61,7 +61,7 @@ struct crf_s {
     bool fcur_valid = false;
     // reverse mode (allocated on first mf_unrolled_backward)
     float *adj_gs = nullptr;     // [B][N][LP]
-    float *adj_gm = nullptr;     // [B][N][LP]
+    float *adj_gs2 = nullptr;    // [B][N][LP] (ping-pong with adj_gs)
     float *adj_dU = nullptr;     // [B][N][LP]
     float *adj_dw = nullptr;     // [B][N][nd]
     float *adj_dwx = nullptr;    // [B][nd][H][W] (host-output staging)
@@ -113,7 +113,7 @@ void free_all(crf_t h) {
         if (p) cudaFree(p);
     if (h->tcb.split_part) cudaFree(h->tcb.split_part);
     if (h->tcb.tile_count) cudaFree(h->tcb.tile_count);
-    float *ad[] = {h->adj_gs, h->adj_gm, h->adj_dU, h->adj_dw, h->adj_dwx, h->adj_part, h->adj_mu};
+    float *ad[] = {h->adj_gs, h->adj_gs2, h->adj_dU, h->adj_dw, h->adj_dwx, h->adj_part, h->adj_mu};
     for (float *p : ad)
         if (p) cudaFree(p);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -745,6 +745,7 @@ static crf_status unrolled_check(crf_t h, int32_t K) {
     crf_status rc = check_handle(h);
     if (rc != CRF_OK) return rc;
     if (h->dense || h->L > kAdjointMaxLabels) return CRF_E_UNSUPPORTED;
+    if (h->H > 4 * 65535) return CRF_E_UNSUPPORTED;   // reverse-step grid: 4-row tiles in gridDim.y
     if (K < 1 || K > 4096) return CRF_E_INVALID;
     return CRF_OK;
 }
@@ -814,11 +815,11 @@ crf_status mf_unrolled_backward(crf_t h, int32_t K, double eta, const float *ckp
     const size_t S = state_floats(h);
     const size_t nw = n_pix(h) * h->nd;
     const size_t LL = (size_t)h->L * h->L;
-    const int nblk = adjoint_blocks((long long)n_pix(h));
+    const int nblk = adjoint_blocks(h->B, h->H, h->W);
     if (!h->adj_gs) {
         bool ok = true;
         ok = ok && dalloc(&h->adj_gs, S) == cudaSuccess;
-        ok = ok && dalloc(&h->adj_gm, S) == cudaSuccess;
+        ok = ok && dalloc(&h->adj_gs2, S) == cudaSuccess;
         ok = ok && dalloc(&h->adj_dU, S) == cudaSuccess;
         ok = ok && dalloc(&h->adj_dw, nw) == cudaSuccess;
         ok = ok && dalloc(&h->adj_dwx, nw) == cudaSuccess;
@@ -826,10 +827,10 @@ crf_status mf_unrolled_backward(crf_t h, int32_t K, double eta, const float *ckp
         ok = ok && dalloc(&h->adj_mu, LL) == cudaSuccess;
         if (!ok) {
             (void)cudaGetLastError();
-            float *ad[] = {h->adj_gs, h->adj_gm, h->adj_dU, h->adj_dw, h->adj_dwx, h->adj_part, h->adj_mu};
+            float *ad[] = {h->adj_gs, h->adj_gs2, h->adj_dU, h->adj_dw, h->adj_dwx, h->adj_part, h->adj_mu};
             for (float *p : ad)
                 if (p) cudaFree(p);
-            h->adj_gs = h->adj_gm = h->adj_dU = h->adj_dw = h->adj_dwx = h->adj_part = h->adj_mu = nullptr;
+            h->adj_gs = h->adj_gs2 = h->adj_dU = h->adj_dw = h->adj_dwx = h->adj_part = h->adj_mu = nullptr;
             return CRF_E_OOM;
         }
     }
@@ -842,14 +843,12 @@ crf_status mf_unrolled_backward(crf_t h, int32_t K, double eta, const float *ckp
         src = h->staging;
     }
     CK(h, launch_rows_to_padded(src, h->adj_gs, (long long)n_pix(h), h->L, h->LP, 0.f, h->st));
-    CK(h, cudaMemsetAsync(h->adj_gm, 0, S * sizeof(float), h->st));
     CK(h, cudaMemsetAsync(h->adj_dU, 0, S * sizeof(float), h->st));
     CK(h, cudaMemsetAsync(h->adj_dw, 0, nw * sizeof(float), h->st));
     CK(h, cudaMemsetAsync(h->adj_part, 0, (size_t)nblk * LL * sizeof(float), h->st));
     h->launches++;
     AdjointStep a{};
-    a.gs = h->adj_gs;
-    a.gm = h->adj_gm;
+    float *gsb[2] = {h->adj_gs, h->adj_gs2};
     a.dU = h->adj_dU;
     a.dw = h->adj_dw;
     a.dmu_part = h->adj_part;
@@ -861,8 +860,11 @@ crf_status mf_unrolled_backward(crf_t h, int32_t K, double eta, const float *ckp
     a.H = h->H;
     a.W = h->W;
     a.conn = h->conn;
+    a.mu_sym = h->mu_sym;
     if (h->profile) CK(h, cudaEventRecord(h->ev0, h->st));
-    for (int t = K - 1; t >= 0; --t) {
+    for (int t = K - 1, c = 0; t >= 0; --t, c ^= 1) {
+        a.gs_in = gsb[c];
+        a.gs_out = gsb[c ^ 1];
         a.s = ckpt + (size_t)t * S;
         a.s_next = ckpt + (size_t)(t + 1) * S;
         CK(h, launch_adjoint_step(a, h->st));
@@ -872,9 +874,9 @@ crf_status mf_unrolled_backward(crf_t h, int32_t K, double eta, const float *ckp
         h->prof_launches = K;
         h->prof_valid = true;
     }
-    h->launches += 2ll * K;
+    h->launches += K;
     AdjointFinish f{};
-    f.gs = h->adj_gs;
+    f.gs = gsb[K & 1];
     f.s0 = ckpt;
     f.dU = h->adj_dU;
     f.dw = h->adj_dw;

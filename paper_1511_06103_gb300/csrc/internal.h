@@ -177,8 +177,8 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
 // the padded pixel-major layout of the step kernel; L <= 24.
 constexpr int kAdjointMaxLabels = 24;
 struct AdjointStep {
-    float *gs;               // [B][N][LP] in: d/ds^{t+1}; out: d/ds^t
-    float *gm;               // [B][N][LP] scratch: d/dm
+    const float *gs_in;      // [B][N][LP] d loss / d s^{t+1} (padding 0)
+    float *gs_out;           // [B][N][LP] d loss / d s^t (padding written 0)
     float *dU;               // [B][N][LP] accumulated
     float *dw;               // [B][N][n_dirs] accumulated
     float *dmu_part;         // [adjoint_blocks][L][L] accumulated per-block partials
@@ -188,6 +188,7 @@ struct AdjointStep {
     const float *mu;         // [L][L] device
     const float *eta;        // [B]
     int B, L, H, W, conn;
+    bool mu_sym;
 };
 struct AdjointFinish {
     const float *gs;         // d/ds^0
@@ -199,7 +200,8 @@ struct AdjointFinish {
     float *dmu_out;          // [L][L]
     int B, L, H, W, conn;
 };
-int adjoint_blocks(long long rows);
+// Blocks of one reverse-step launch (32 x 4 pixel tiles per instance).
+int adjoint_blocks(int B, int H, int W);
 cudaError_t launch_adjoint_step(const AdjointStep &a, cudaStream_t st);
 cudaError_t launch_adjoint_finish(const AdjointFinish &a, cudaStream_t st);
 

@@ -102,6 +102,23 @@ def test_adjoint_matches_oracle_8x8_L3(env, conn, sym, eta):
     assert close(dw[0], dwr)
 
 
+@pytest.mark.parametrize("L,conn,sym", [(2, 4, True), (2, 8, False), (12, 8, True), (16, 4, False),
+                                         (20, 8, True), (24, 4, True), (24, 8, False)])
+def test_adjoint_label_counts(env, L, conn, sym):
+    """Every label-count instantiation; 13 x 70 grids span three 32-wide
+    and four 4-high tiles with ragged tails."""
+    binding, oracle, torch = env
+    H, W, K, eta = 13, 70, 4, 0.3
+    d = synth.random_grid(H, W, L, conn, seed=200 + L + conn, symmetric=sym)
+    d["y"] = np.random.default_rng(L).integers(0, L, H * W).astype(np.int32)
+    loss, dU, dmu, dw = gpu_grads(binding, torch, d, eta, K)
+    lref, dUr, dmur, dwr = oracle_grads(oracle, d["U"], d["mu"], d["w"], H, W, conn, eta, K, d["y"])
+    assert abs(loss - lref) <= 1e-5 * abs(lref)
+    assert close(dU[0], dUr)
+    assert close(dmu, dmur)
+    assert close(dw[0], dwr)
+
+
 def test_adjoint_matches_finite_differences(env):
     """Direct FP64 central differences of the oracle's loss at a few
     coordinates of U, mu and w (h = 1e-6)."""
