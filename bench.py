@@ -335,11 +335,9 @@ def run_unrolled(args, dev, peak):
     crf.close()
     ms = float(np.mean(times))
     fwd_ms, bwd_ms = float(np.mean(fwd)), float(np.mean(bwd))
-    # algorithmic bytes of one reverse step (both kernels), per pixel: the
-    # softmax part reads gs, log q^{t+1}, dU and writes gm, gs, dU (6 x 4L);
-    # the message part reads gm, log q^t, gs, w, dw and writes gs, dw
-    # (4 x 4L + 3 x 4 n_dirs)
-    bwd_bytes = B * N * (40 * L + 12 * 2)
+    # algorithmic bytes of one reverse step, per pixel: read d/ds^{t+1},
+    # log q^{t+1}, log q^t, dU, w, dw; write d/ds^t, dU, dw
+    bwd_bytes = B * N * (24 * L + 12 * 2)
     fwd_bytes = B * N * (12 * L + 4 * 2)
     return {"workload": "unrolled inference, batch 16 of 4-connected 256x256 grids, L=21, K=10, "
                         "FP32 messages; forward with per-step checkpoints + cross-entropy gradient + "
@@ -351,7 +349,7 @@ def run_unrolled(args, dev, peak):
                                  "peak": peak, "unit": "GB/s",
                                  "frac": bwd_bytes / (bwd_ms / 1000.0) / 1e9 / peak,
                                  "bytes_per_step": bwd_bytes,
-                                 "kernels": "adj_softmax_kernel<24> + adj_message_kernel<24>"},
+                                 "kernel": "adj_step_kernel<21,4,sym>"},
             "roofline_forward": {"bound": "hbm", "achieved": fwd_bytes / (fwd_ms / 1000.0) / 1e9,
                                  "peak": peak, "unit": "GB/s",
                                  "frac": fwd_bytes / (fwd_ms / 1000.0) / 1e9 / peak,

@@ -25,6 +25,7 @@
 // fixed order), so results do not depend on scheduling.
 #include <cmath>
 
+#include "f32x2.cuh"
 #include "internal.h"
 
 namespace proxmf {
@@ -48,6 +49,8 @@ struct AdjCfg {
     }
     // the dmu reduction scratch reuses everything after mu
     static_assert(NG * LP * LP <= 2 * HR * LS + 2 * NT * LSS, "dmu scratch does not fit");
+    // the raw s^{t+1} rows are staged where S and Gout live later
+    static_assert(HR * LP <= 2 * NT * LSS, "raw staging does not fit");
 };
 
 template <int VW>
@@ -77,10 +80,21 @@ __host__ __device__ constexpr int dir_dx(int d) { return d == 0 ? 1 : (d == 1 ? 
 // in registers from one phase of the kernel to the next.
 __device__ __forceinline__ void reload_fence() { asm volatile("" ::: "memory"); }
 
+// 16- or 8-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros.
+template <int VW>
+__device__ __forceinline__ void cp_async_row(float *dst, const float *src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (VW == 4)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(src_bytes));
+}
+
 template <int LT, int CONN, bool SYM>
 __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep a) {
     using C = AdjCfg<LT>;
     constexpr int LP = C::LP, VW = C::VW, LS = C::LS, LSS = C::LSS, TX = C::TX, HX = C::HX, NT = C::NT;
+    constexpr int NP = LP / 2;                             // label pairs
     constexpr int ND = CONN == 8 ? 4 : 2;
     extern __shared__ __align__(16) float smem[];
     float *mus = smem;                                     // mu [LP][LP], row k = mu[k][.]
@@ -89,6 +103,7 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep
     float *sq = sga + C::HR * LS;                          // [HR][LS] q^t of tile + halo
     float *sS = sq + C::HR * LS;                           // [NT][LSS] S_i
     float *sG = sS + NT * LSS;                             // [NT][LSS] sum_{i->j} w ga_j
+    float *sraw = sS;                                      // [HR][LP] raw s^{t+1} (before S, G exist)
 
     const int tid = threadIdx.x;
     const int b = blockIdx.z;
@@ -98,33 +113,38 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep
     const size_t base = (size_t)b * N;
     const float eta = a.eta[b];
 
+    // Phase 1a: raw rows of the tile and its halo, all copies in flight at
+    // once (rows outside the image are zero-filled).
+    for (int r = tid; r < C::HR; r += NT) {
+        const int hy = r / HX, hx = r - hy * HX;
+        const int y = y0 - 1 + hy, x = x0 - 1 + hx;
+        const bool in = y >= 0 && y < H && x >= 0 && x < W;
+        const size_t o = in ? (base + (size_t)y * W + x) * LP : 0;
+        const int nbytes = in ? VW * 4 : 0;
+#pragma unroll
+        for (int l = 0; l < LP; l += VW) {
+            cp_async_row<VW>(sga + r * LS + l, a.gs_in + o + l, nbytes);
+            cp_async_row<VW>(sq + r * LS + l, a.s + o + l, nbytes);
+            cp_async_row<VW>(sraw + r * LP + l, a.s_next + o + l, nbytes);
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
     for (int i = tid; i < LP * LP; i += NT) {
         const int r = i / LP, c = i - r * LP;
         const float v = (r < L && c < L) ? a.mu[r * L + c] : 0.f;
         mus[i] = v;
         if (!SYM) muT[c * LP + r] = v;
     }
-    // Phase 1: ga and q^t of the tile and its halo (zero outside the image).
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    // Phase 1b: ga = gs - q' sum gs and q = exp(s) in place (padding -> 0).
     for (int r = tid; r < C::HR; r += NT) {
-        const int hy = r / HX, hx = r - hy * HX;
-        const int y = y0 - 1 + hy, x = x0 - 1 + hx;
-        float *gr = sga + r * LS, *qr = sq + r * LS;
-        if (y < 0 || y >= H || x < 0 || x >= W) {
-            float z[VW] = {};
-#pragma unroll
-            for (int l = 0; l < LP; l += VW) {
-                vput<VW>(gr + l, z);
-                vput<VW>(qr + l, z);
-            }
-            continue;
-        }
-        const size_t o = (base + (size_t)y * W + x) * LP;
-        float g[LP], qn[LP];
+        float g[LP], t[LP];
         float sum = 0.f;
 #pragma unroll
         for (int l = 0; l < LP; l += VW) {
-            vget<VW>(a.gs_in + o + l, g + l);
-            vget<VW>(a.s_next + o + l, qn + l);
+            vget<VW>(sga + r * LS + l, g + l);
+            vget<VW>(sraw + r * LP + l, t + l);
         }
 #pragma unroll
         for (int l = 0; l < LP; ++l) {
@@ -132,15 +152,16 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep
             sum += g[l];
         }
 #pragma unroll
-        for (int l = 0; l < LP; ++l) g[l] = l < L ? g[l] - __expf(qn[l]) * sum : 0.f;
+        for (int l = 0; l < LP; ++l) g[l] = l < L ? g[l] - __expf(t[l]) * sum : 0.f;
 #pragma unroll
-        for (int l = 0; l < LP; l += VW) vput<VW>(gr + l, g + l);
+        for (int l = 0; l < LP; l += VW) {
+            vput<VW>(sga + r * LS + l, g + l);
+            vget<VW>(sq + r * LS + l, t + l);
+        }
 #pragma unroll
-        for (int l = 0; l < LP; l += VW) vget<VW>(a.s + o + l, qn + l);
+        for (int l = 0; l < LP; ++l) t[l] = l < L ? __expf(t[l]) : 0.f;
 #pragma unroll
-        for (int l = 0; l < LP; ++l) qn[l] = l < L ? __expf(qn[l]) : 0.f;
-#pragma unroll
-        for (int l = 0; l < LP; l += VW) vput<VW>(qr + l, qn + l);
+        for (int l = 0; l < LP; l += VW) vput<VW>(sq + r * LS + l, t + l);
     }
     __syncthreads();
 
@@ -152,70 +173,75 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep
     const int ri = (ty + 1) * HX + (tx + 1);
     const float *ga_i = sga + ri * LS;
     const float *q_i = sq + ri * LS;
-    float h[LP];
+    float2 h[NP];
     {
         // v1 = mu^T ga_i, v2 = mu^T q_i
-        float v1[LP], v2[LP];
+        float2 v1[NP], v2[NP];
 #pragma unroll
-        for (int l = 0; l < LP; ++l) v1[l] = v2[l] = 0.f;
+        for (int j = 0; j < NP; ++j) v1[j] = v2[j] = splat2(0.f);
 #pragma unroll
         for (int k = 0; k < LT; ++k) {
-            const float gk = ga_i[k], qk = q_i[k];
+            const float2 gk = splat2(ga_i[k]), qk = splat2(q_i[k]);
 #pragma unroll
             for (int l = 0; l < LP; l += VW) {
                 float m[VW];
                 vget<VW>(mus + k * LP + l, m);
 #pragma unroll
-                for (int u = 0; u < VW; ++u) {
-                    v1[l + u] = fmaf(m[u], gk, v1[l + u]);
-                    v2[l + u] = fmaf(m[u], qk, v2[l + u]);
+                for (int u = 0; u < VW; u += 2) {
+                    const float2 m2 = make_float2(m[u], m[u + 1]);
+                    v1[(l + u) / 2] = fma2(m2, gk, v1[(l + u) / 2]);
+                    v2[(l + u) / 2] = fma2(m2, qk, v2[(l + u) / 2]);
                 }
             }
         }
         reload_fence();
-        float G[LP], S[LP];
+        float2 G[NP], S[NP];
 #pragma unroll
-        for (int l = 0; l < LP; ++l) G[l] = S[l] = 0.f;
+        for (int j = 0; j < NP; ++j) G[j] = S[j] = splat2(0.f);
 #pragma unroll
         for (int d = 0; d < ND; ++d) {                   // out-going edges i -> j
             const int yj = y + dir_dy(d), xj = x + dir_dx(d);
             const bool ok = act && yj < H && xj >= 0 && xj < W;
-            const float wv = ok ? a.w[p * ND + d] : 0.f;
+            const float2 wv = splat2(ok ? a.w[p * ND + d] : 0.f);
             const float *gj = sga + (ri + dir_dy(d) * HX + dir_dx(d)) * LS;
             const float *qj = sq + (ri + dir_dy(d) * HX + dir_dx(d)) * LS;
-            float de = 0.f;
+            float2 de = splat2(0.f);
 #pragma unroll
             for (int l = 0; l < LP; l += VW) {
                 float gv[VW], qv[VW];
                 vget<VW>(gj + l, gv);
                 vget<VW>(qj + l, qv);
 #pragma unroll
-                for (int u = 0; u < VW; ++u) {
-                    G[l + u] = fmaf(wv, gv[u], G[l + u]);
-                    S[l + u] = fmaf(wv, qv[u], S[l + u]);
-                    de = fmaf(v1[l + u], qv[u], fmaf(v2[l + u], gv[u], de));
+                for (int u = 0; u < VW; u += 2) {
+                    const int j = (l + u) / 2;
+                    const float2 g2 = make_float2(gv[u], gv[u + 1]), q2 = make_float2(qv[u], qv[u + 1]);
+                    G[j] = fma2(wv, g2, G[j]);
+                    S[j] = fma2(wv, q2, S[j]);
+                    de = fma2(v1[j], q2, fma2(v2[j], g2, de));
                 }
             }
-            if (ok) a.dw[p * ND + d] += -eta * de;
+            if (ok) a.dw[p * ND + d] += -eta * (de.x + de.y);
         }
 #pragma unroll
-        for (int l = 0; l < LP; l += VW) {
-            vput<VW>(sS + tid * LSS + l, S + l);
-            vput<VW>(sG + tid * LSS + l, G + l);
+        for (int j = 0; j < NP; ++j) {
+            *reinterpret_cast<float2 *>(sS + tid * LSS + 2 * j) = S[j];
+            *reinterpret_cast<float2 *>(sG + tid * LSS + 2 * j) = G[j];
         }
         reload_fence();
 #pragma unroll
-        for (int l = 0; l < LP; ++l) h[l] = 0.f;
+        for (int j = 0; j < NP; ++j) h[j] = splat2(0.f);
         if (!SYM) {
             // h = mu Gout = sum_k mu^T[k][.] Gout[k]
 #pragma unroll
             for (int k = 0; k < LT; ++k) {
+                const float2 gk = splat2(k & 1 ? G[k / 2].y : G[k / 2].x);
 #pragma unroll
                 for (int l = 0; l < LP; l += VW) {
                     float m[VW];
                     vget<VW>(muT + k * LP + l, m);
 #pragma unroll
-                    for (int u = 0; u < VW; ++u) h[l + u] = fmaf(m[u], G[k], h[l + u]);
+                    for (int u = 0; u < VW; u += 2)
+                        h[(l + u) / 2] = fma2(make_float2(m[u], m[u + 1]), gk, h[(l + u) / 2]);
                 }
             }
         }
@@ -223,33 +249,37 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep
     reload_fence();
     {
         // in-coming edges k -> i; symmetric mu folds Gout in: h = mu (Gout + Gin)
-        float G[LP];
+        float2 G[NP];
 #pragma unroll
-        for (int l = 0; l < LP; ++l) G[l] = SYM ? sG[tid * LSS + l] : 0.f;
+        for (int j = 0; j < NP; ++j)
+            G[j] = SYM ? *reinterpret_cast<const float2 *>(sG + tid * LSS + 2 * j) : splat2(0.f);
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
             const int yk = y - dir_dy(d), xk = x - dir_dx(d);
             const bool ok = act && yk >= 0 && xk >= 0 && xk < W;
-            const float wv = ok ? a.w[(base + (size_t)yk * W + xk) * ND + d] : 0.f;
+            const float2 wv = splat2(ok ? a.w[(base + (size_t)yk * W + xk) * ND + d] : 0.f);
             const float *gk = sga + (ri - dir_dy(d) * HX - dir_dx(d)) * LS;
 #pragma unroll
             for (int l = 0; l < LP; l += VW) {
                 float gv[VW];
                 vget<VW>(gk + l, gv);
 #pragma unroll
-                for (int u = 0; u < VW; ++u) G[l + u] = fmaf(wv, gv[u], G[l + u]);
+                for (int u = 0; u < VW; u += 2)
+                    G[(l + u) / 2] = fma2(wv, make_float2(gv[u], gv[u + 1]), G[(l + u) / 2]);
             }
         }
         reload_fence();
         // h += mu^T G  (= sum_k mu[k][.] G[k])
 #pragma unroll
         for (int k = 0; k < LT; ++k) {
+            const float2 gk = splat2(k & 1 ? G[k / 2].y : G[k / 2].x);
 #pragma unroll
             for (int l = 0; l < LP; l += VW) {
                 float m[VW];
                 vget<VW>(mus + k * LP + l, m);
 #pragma unroll
-                for (int u = 0; u < VW; ++u) h[l + u] = fmaf(m[u], G[k], h[l + u]);
+                for (int u = 0; u < VW; u += 2)
+                    h[(l + u) / 2] = fma2(make_float2(m[u], m[u + 1]), gk, h[(l + u) / 2]);
             }
         }
     }
@@ -264,7 +294,8 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep
             vget<VW>(a.dU + o + l, du);
 #pragma unroll
             for (int u = 0; u < VW; ++u) {
-                out[u] = fmaf(c1, gv[u], -eta * qv[u] * h[l + u]);
+                const float hv = (u & 1) ? h[(l + u) / 2].y : h[(l + u) / 2].x;
+                out[u] = fmaf(c1, gv[u], -eta * qv[u] * hv);
                 du[u] = fmaf(-eta, gv[u], du[u]);
             }
             vput<VW>(a.gs_out + o + l, out);
@@ -275,11 +306,11 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep
 
     // Phase 3: dmu partial = -eta ([ga | q]^T [S | Gout]) over the tile's pixels.
     constexpr int TS = C::TS, NTB = C::NTB, NTILE = C::NTILE, NG = C::NG;
-    float acc[TS][TS];
+    float2 acc[TS][TS / 2];
 #pragma unroll
     for (int i = 0; i < TS; ++i)
 #pragma unroll
-        for (int j = 0; j < TS; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < TS / 2; ++j) acc[i][j] = splat2(0.f);
     const int tile = tid % NTILE, grp = tid / NTILE;
     const int a0 = (tile / NTB) * TS, c0 = (tile % NTB) * TS;
     if (grp < NG) {
@@ -293,16 +324,19 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep
 #pragma unroll
             for (int u = 0; u < TS; ++u)
 #pragma unroll
-                for (int v = 0; v < TS; ++v) acc[u][v] = fmaf(ga[u], sv[v], fmaf(qa[u], gv[v], acc[u][v]));
+                for (int v = 0; v < TS; v += 2)
+                    acc[u][v / 2] = fma2(splat2(ga[u]), make_float2(sv[v], sv[v + 1]),
+                                         fma2(splat2(qa[u]), make_float2(gv[v], gv[v + 1]), acc[u][v / 2]));
         }
     }
     __syncthreads();
-    float *red = sga;                                      // [NG][LP][LP], reuses the ga rows
+    float *red = sga;                                      // [NG][LP][LP], reuses the rows after mu
     if (grp < NG) {
 #pragma unroll
         for (int u = 0; u < TS; ++u)
 #pragma unroll
-            for (int v = 0; v < TS; ++v) red[(grp * LP + a0 + u) * LP + c0 + v] = acc[u][v];
+            for (int v = 0; v < TS; v += 2)
+                *reinterpret_cast<float2 *>(red + (grp * LP + a0 + u) * LP + c0 + v) = acc[u][v / 2];
     }
     __syncthreads();
     const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
