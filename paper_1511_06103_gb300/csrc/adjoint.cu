@@ -25,7 +25,6 @@
 // fixed order), so results do not depend on scheduling.
 #include <cmath>
 
-#include "f32x2.cuh"
 #include "internal.h"
 
 namespace proxmf {
@@ -75,6 +74,14 @@ __device__ __forceinline__ void vput(float *p, const float *v) {
 // Direction d of an edge leaving a pixel: 0 right, 1 down, 2 down-right, 3 down-left.
 __host__ __device__ constexpr int dir_dy(int d) { return d == 0 ? 0 : 1; }
 __host__ __device__ constexpr int dir_dx(int d) { return d == 0 ? 1 : (d == 1 ? 0 : (d == 2 ? 1 : -1)); }
+
+// Lane-wise a * b + c on a pair as two scalar FMAs (the packed f32x2 form
+// measured slower in this kernel: the pairs here are built from vector loads
+// and splats, which costs register moves).
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
 
 // Keeps the compiler from carrying shared-memory loads (the L x L matrix)
 // in registers from one phase of the kernel to the next.
@@ -189,8 +196,8 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep
 #pragma unroll
                 for (int u = 0; u < VW; u += 2) {
                     const float2 m2 = make_float2(m[u], m[u + 1]);
-                    v1[(l + u) / 2] = fma2(m2, gk, v1[(l + u) / 2]);
-                    v2[(l + u) / 2] = fma2(m2, qk, v2[(l + u) / 2]);
+                    v1[(l + u) / 2] = pfma(m2, gk, v1[(l + u) / 2]);
+                    v2[(l + u) / 2] = pfma(m2, qk, v2[(l + u) / 2]);
                 }
             }
         }
@@ -215,9 +222,9 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep
                 for (int u = 0; u < VW; u += 2) {
                     const int j = (l + u) / 2;
                     const float2 g2 = make_float2(gv[u], gv[u + 1]), q2 = make_float2(qv[u], qv[u + 1]);
-                    G[j] = fma2(wv, g2, G[j]);
-                    S[j] = fma2(wv, q2, S[j]);
-                    de = fma2(v1[j], q2, fma2(v2[j], g2, de));
+                    G[j] = pfma(wv, g2, G[j]);
+                    S[j] = pfma(wv, q2, S[j]);
+                    de = pfma(v1[j], q2, pfma(v2[j], g2, de));
                 }
             }
             if (ok) a.dw[p * ND + d] += -eta * (de.x + de.y);
@@ -241,7 +248,7 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep
                     vget<VW>(muT + k * LP + l, m);
 #pragma unroll
                     for (int u = 0; u < VW; u += 2)
-                        h[(l + u) / 2] = fma2(make_float2(m[u], m[u + 1]), gk, h[(l + u) / 2]);
+                        h[(l + u) / 2] = pfma(make_float2(m[u], m[u + 1]), gk, h[(l + u) / 2]);
                 }
             }
         }
@@ -265,7 +272,7 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep
                 vget<VW>(gk + l, gv);
 #pragma unroll
                 for (int u = 0; u < VW; u += 2)
-                    G[(l + u) / 2] = fma2(wv, make_float2(gv[u], gv[u + 1]), G[(l + u) / 2]);
+                    G[(l + u) / 2] = pfma(wv, make_float2(gv[u], gv[u + 1]), G[(l + u) / 2]);
             }
         }
         reload_fence();
@@ -279,7 +286,7 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep
                 vget<VW>(mus + k * LP + l, m);
 #pragma unroll
                 for (int u = 0; u < VW; u += 2)
-                    h[(l + u) / 2] = fma2(make_float2(m[u], m[u + 1]), gk, h[(l + u) / 2]);
+                    h[(l + u) / 2] = pfma(make_float2(m[u], m[u + 1]), gk, h[(l + u) / 2]);
             }
         }
     }
@@ -325,8 +332,8 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep
             for (int u = 0; u < TS; ++u)
 #pragma unroll
                 for (int v = 0; v < TS; v += 2)
-                    acc[u][v / 2] = fma2(splat2(ga[u]), make_float2(sv[v], sv[v + 1]),
-                                         fma2(splat2(qa[u]), make_float2(gv[v], gv[v + 1]), acc[u][v / 2]));
+                    acc[u][v / 2] = pfma(splat2(ga[u]), make_float2(sv[v], sv[v + 1]),
+                                         pfma(splat2(qa[u]), make_float2(gv[v], gv[v + 1]), acc[u][v / 2]));
         }
     }
     __syncthreads();
