@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--serve-requests", type=int, default=128,
                    help="requests of the serving measurement (0 skips it)")
     p.add_argument("--serve-only", action="store_true")
+    p.add_argument("--no-grid-bf16", action="store_true",
+                   help="skip the BF16 tensor-core form of the segmentation workload")
+    p.add_argument("--grid-bf16-only", action="store_true")
     p.add_argument("--no-unrolled", action="store_true",
                    help="skip the unrolled-inference (forward + reverse) measurement")
     p.add_argument("--unrolled-only", action="store_true")
@@ -268,6 +271,64 @@ def run_dense(args, dev, precision, peak):
             "final_F": F, "eta": float(eta[0]), "Lambda": float(lam[0]), "q": q}
 
 
+def run_grid_precision(args, dev, peak):
+    """The segmentation workload solved by the FP32 form (100 steps) and by
+    the BF16 tensor-core form (98 tensor-core steps + 2 FP32 refinement
+    steps) at the same step size; device-timed solves, L2 flushed before
+    each, average step launch from the profiled loop."""
+    import torch
+
+    from paper_1511_06103_gb300 import binding, synth
+    d = synth.segmentation_grid(H=H, W=W, L=L, conn=CONN, seed=SEED)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, prec, iters, refine in (("f32", binding.CRF_FP32, ITERS, 0),
+                                      ("bf16_tc", binding.CRF_BF16, ITERS - 2, 2)):
+        crf = binding.CRF(binding.CRF_GRID8, L, H, W, precision=prec, stream=stream.cuda_stream)
+        crf.set_unary(torch.from_numpy(d["U"]).to(dev))
+        crf.set_pairwise(torch.from_numpy(d["mu"]).to(dev), torch.from_numpy(d["w"]).to(dev))
+        crf.lipschitz()
+
+        def solve():
+            crf.iterate(iters, eta=0.0, reset=True, final_free_energy=True, refine_fp32=refine)
+
+        for _ in range(max(3, args.warmup)):
+            flush.zero_()
+            solve()
+        torch.cuda.synchronize()
+        times, kern = [], []
+        crf.profile(True)
+        for _ in range(max(3, min(args.steps, 10))):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solve()
+            e1.record(stream)
+            ms, n = crf.profile_read()
+            kern.append(ms / n)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        crf.profile(False)
+        ms = float(np.mean(times))
+        kms = float(np.mean(kern))
+        bl = algorithmic_bytes_per_launch()
+        out[name] = {"value": H * W * L * ITERS / (ms / 1000.0), "unit": UNIT, "ms_per_solve": ms,
+                     "tc_steps": iters if refine else 0, "fp32_steps": refine if refine else iters,
+                     "avg_launch_ms": kms,
+                     "roofline": {"bound": "hbm", "achieved": bl / (kms / 1000.0) / 1e9, "peak": peak,
+                                  "unit": "GB/s", "frac": bl / (kms / 1000.0) / 1e9 / peak,
+                                  "bytes_per_launch": bl},
+                     "final_F": float(crf.free_energy()[0]), "q": crf.marginals()}
+        crf.close()
+    q32, q16 = out["f32"].pop("q"), out["bf16_tc"].pop("q")
+    return {"workload": WORKLOAD + "; FP32 form vs BF16 tensor-core messages (98 + 2 FP32 refinement steps)",
+            **out, "bf16_speedup": out["bf16_tc"]["value"] / out["f32"]["value"],
+            "final_F_rel_diff": abs(out["bf16_tc"]["final_F"] - out["f32"]["final_F"]) / abs(out["f32"]["final_F"]),
+            "q_max_abs_diff": float(np.abs(q32 - q16).max())}
+
+
 UNR_B, UNR_SIDE, UNR_L, UNR_CONN, UNR_K = 16, 256, 21, 4, 10
 
 
@@ -464,6 +525,10 @@ def run_ours(args, world, rank, local):
     if args.serve_only:
         print(json.dumps({"serving": run_serving(max(1, args.serve_requests))}), flush=True)
         return
+    if args.grid_bf16_only:
+        peak, _ = measured_peaks()
+        print(json.dumps({"grid_precision": run_grid_precision(args, dev, peak)}), flush=True)
+        return
     if args.unrolled_only:
         peak, _ = measured_peaks()
         print(json.dumps({"unrolled": run_unrolled(args, dev, peak)}), flush=True)
@@ -598,6 +663,9 @@ def run_ours(args, world, rank, local):
                  "f32": r32, "bf16_tc": r16, "bf16_speedup": r16["value"] / r32["value"],
                  "final_F_rel_diff": abs(r16["final_F"] - r32["final_F"]) / abs(r32["final_F"]),
                  "q_max_abs_diff": dq}
+    grid_prec = None
+    if not args.no_grid_bf16 and world == 1:
+        grid_prec = run_grid_precision(args, dev, peak)
     unrolled = None
     if not args.no_unrolled and world == 1:
         unrolled = run_unrolled(args, dev, peak)
@@ -632,6 +700,7 @@ def run_ours(args, world, rank, local):
             "final_F": F_final,
             "wall_ms_timed": 1000 * (wall1 - wall0),
             "dense": dense,
+            "grid_precision": grid_prec,
             "unrolled": unrolled,
             "serving": serving,
         }

@@ -60,9 +60,12 @@ typedef enum {
 
 typedef enum {
     CRF_FP32 = 0,           /* FP32 messages, FP32 state                     */
-    CRF_BF16 = 1            /* BF16 tensor-core messages, FP32 state (fully  */
-                            /* connected models); free energies are always   */
-                            /* evaluated with FP32 messages                  */
+    CRF_BF16 = 1            /* BF16 tensor-core messages, FP32 state: dense  */
+                            /* N x N product (fully connected) or the L x L  */
+                            /* product (grids); FP32 accumulation.  The F    */
+                            /* trace of a BF16 step uses its BF16 messages;  */
+                            /* mf_free_energy and final_free_energy always   */
+                            /* use FP32 messages                             */
 } crf_precision;
 
 typedef struct {
@@ -189,7 +192,9 @@ crf_status crf_launch_count(crf_t h, int64_t *n);
  *   mf_unrolled_checkpoint_floats(K) floats, 16-byte aligned), and leave
  *   the handle's state at s^K (mf_marginals / mf_log_marginals read it;
  *   mf_free_energy_trace(K) gives F(q^0..q^{K-1})).  The handle's unary and
- *   pairwise terms must be set.
+ *   pairwise terms must be set.  A CRF_BF16 handle takes the K steps with
+ *   BF16 tensor-core messages; the reverse pass is then the FP32 adjoint of
+ *   the step map evaluated along that trajectory.
  *
  * mf_unrolled_backward -- gradients of a scalar loss given dlogq = d loss /
  *   d log q^K ([batch][N][L], external layout).  Needs the ckpt of a forward

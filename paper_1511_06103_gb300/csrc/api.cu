@@ -24,6 +24,7 @@ struct crf_s {
     float *s[2] = {nullptr, nullptr};  // [B][N][LP] log q, ping-pong, padding kPadLogQ
     float *w = nullptr;          // [B][N][nd] edge weights
     float2 *mu_pairs = nullptr;  // device [2][LT][NPP] mu column / row pairs
+    uint8_t *mu_tc = nullptr;    // device BF16 operand images of mu, mu^T (grid, BF16 form)
     // fully connected model
     bool dense = false;
     int N = 0;                   // variables per instance
@@ -105,6 +106,7 @@ void free_all(crf_t h) {
     if (h->done) cudaFree(h->done);
     if (h->status) cudaFree(h->status);
     if (h->mu_pairs) cudaFree(h->mu_pairs);
+    if (h->mu_tc) cudaFree(h->mu_tc);
     float *fd[] = {h->K32, h->q32[0], h->q32[1], h->feats, h->mu_dev};
     for (float *p : fd)
         if (p) cudaFree(p);
@@ -153,6 +155,7 @@ GridStepLaunch step_args(crf_t h, const float *eta, int t, int update, double re
     a.eta = eta;
     a.mu_out = h->mu_pairs;
     a.mu_in = h->mu_pairs + (size_t)h->LT * mu_pair_slots(h->LT);
+    a.mu_tc = reinterpret_cast<const uint4 *>(h->mu_tc);
     a.partial = h->partial;
     a.counter = h->counter;
     a.f_trace = h->ftrace;
@@ -213,6 +216,7 @@ cudaError_t launch_step(crf_t h, const float *eta, int t, int update, double rel
     }
     GridStepLaunch a = step_args(h, eta, t, update, rel_tol);
     if (!update || rel_tol <= 0) a.done = nullptr;
+    a.tc = h->bf16 && update && !fp32;
     return launch_grid_step(a, h->st);
 }
 
@@ -309,6 +313,23 @@ void build_mu_pairs_host(const float *mu, int L, int LT, float2 *out) {
         }
 }
 
+// BF16 B-operand images for the tensor-core grid step: B[n][k] = mu[n][k]
+// (m = mu S_out) followed by B'[n][k] = mu[k][n] (m += mu^T S_in), each
+// KP x KP in the core-matrix layout of tc_sbo, zero outside L x L.
+void build_mu_tc_image(const std::vector<float> &mu, int L, int KP, std::vector<uint8_t> &out) {
+    out.assign((size_t)2 * KP * KP * 2, 0);
+    const int sbo = tc_sbo(KP);
+    for (int part = 0; part < 2; ++part)
+        for (int n = 0; n < L; ++n)
+            for (int k = 0; k < L; ++k) {
+                const float v = part == 0 ? mu[(size_t)n * L + k] : mu[(size_t)k * L + n];
+                const __nv_bfloat16 bv = __float2bfloat16_rn(v);
+                const size_t off = (size_t)part * KP * KP * 2 + (size_t)(n / 8) * sbo + (k / 8) * 128 + (n % 8) * 16 +
+                                   (k % 8) * 2;
+                std::memcpy(out.data() + off, &bv, 2);
+            }
+}
+
 void build_mu_pairs(const std::vector<float> &mu, int L, int LT, std::vector<float2> &out) {
     out.assign((size_t)2 * LT * mu_pair_slots(LT), make_float2(0.f, 0.f));
     build_mu_pairs_host(mu.data(), L, LT, out.data());
@@ -345,7 +366,6 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
     if (d.topology != CRF_GRID4 && d.topology != CRF_GRID8 && d.topology != CRF_DENSE_GAUSS)
         return CRF_E_INVALID;
     const bool dense = d.topology == CRF_DENSE_GAUSS;
-    if (d.precision == CRF_BF16 && !dense) return CRF_E_UNSUPPORTED;
     if (dense) {
         // the dense step keeps up to 24 labels per row; N x N weights per instance
         if (d.n_labels > 24) return CRF_E_UNSUPPORTED;
@@ -413,6 +433,11 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
     }
     ok = ok && dalloc(&h->mu_pairs, (size_t)2 * h->LT * mu_pair_slots(h->LT)) == cudaSuccess;
     ok = ok && dalloc(&h->mu_dev, (size_t)h->L * h->L) == cudaSuccess;
+    if (!dense && d.precision == CRF_BF16) {
+        h->bf16 = true;
+        ok = ok && dalloc(&h->mu_tc, kTcImageBytes) == cudaSuccess;
+        if (ok) ok = cudaMemsetAsync(h->mu_tc, 0, kTcImageBytes, h->st) == cudaSuccess;
+    }
     ok = ok && dalloc(&h->eta_fixed, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->eta_auto, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->Lambda, h->B) == cudaSuccess;
@@ -548,6 +573,11 @@ crf_status crf_set_pairwise(crf_t h, const float *mu, const float *w_or_feats, c
     CK(h, cudaMemcpyAsync(h->mu_pairs, pairs.data(), pairs.size() * sizeof(float2), cudaMemcpyHostToDevice,
                           h->st));
     CK(h, cudaMemcpyAsync(h->mu_dev, m.data(), LL * sizeof(float), cudaMemcpyHostToDevice, h->st));
+    std::vector<uint8_t> img;
+    if (h->bf16) {
+        build_mu_tc_image(m, h->L, tc_k(h->LT), img);
+        CK(h, cudaMemcpyAsync(h->mu_tc, img.data(), img.size(), cudaMemcpyHostToDevice, h->st));
+    }
     const float *src = w_or_feats;
     if (!is_device) {
         // the staging buffer holds B*N*L floats >= B*nd*N only when L >= nd
@@ -790,6 +820,7 @@ crf_status mf_unrolled_forward(crf_t h, int32_t K, double eta, float *ckpt) {
     for (int t = 0; t < K; ++t) {
         GridStepLaunch a = step_args(h, e, t, 1, 0.0);
         a.done = nullptr;
+        a.tc = h->bf16;   // BF16 handles: tensor-core messages in the forward steps
         a.s_in = ckpt + (size_t)t * S;
         a.s_out = ckpt + (size_t)(t + 1) * S;
         CK(h, launch_grid_step(a, h->st));

@@ -33,12 +33,16 @@
 
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "f32x2.cuh"
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace proxmf {
 
 struct GridStepArgs {
+    const uint4 *mu_tc;      // tensor-core form: BF16 images of mu (and mu^T), see tc_k
     const float *s_in;
     float *s_out;
     const float *U;
@@ -142,6 +146,41 @@ __device__ __forceinline__ void pair_matvec(float2 (&m)[NP], const float2 *A, co
     }
 }
 
+// Tensor-core form of the L x L product (BF16 operands, FP32 accumulation):
+// the neighbour sums S of a tile's 256 pixels form the A operand (two
+// M = 128 halves, K = tc_k labels), mu the B operand (N = tc_k labels), and
+// D = A B^T = (mu S)^T lands in TMEM, one pixel per lane.
+// (tc_k, tc_sbo and the operand layout: internal.h)
+
+struct TcTile {
+    float *qt;               // q tile with halo (dynamic shared memory)
+    uint8_t *A;              // [SYM ? 1 : 2][2 halves][128 x KP] BF16 operands
+    const uint8_t *B;        // [SYM ? 1 : 2][KP x KP] BF16 mu, mu^T
+    uint32_t tmem;           // 2 x KP FP32 columns
+    uint64_t *bar;           // MMA completion
+    int *status;
+};
+
+// One pixel's row of A (a tc_k-label BF16 vector) from FP32 label pairs.
+template <int NP, int KP>
+__device__ __forceinline__ void put_a_row(uint8_t *row, const float2 (&S)[NP]) {
+#pragma unroll
+    for (int c = 0; c < KP / 8; ++c) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int p = 4 * c + i;
+            if (p < NP) {
+                const __nv_bfloat162 v = __floats2bfloat162_rn(S[p].x, S[p].y);
+                w[i] = *reinterpret_cast<const uint32_t *>(&v);
+            } else {
+                w[i] = 0u;
+            }
+        }
+        *reinterpret_cast<uint4 *>(row + c * 128) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
 // One instance as seen by one tile: pointers already offset to the instance.
 struct TileJob {
     const float *s_in;
@@ -159,8 +198,8 @@ struct TileJob {
 // j.update), and the tile's free-energy partial, returned in thread 0.
 // All threads of the block must call it; it may be called repeatedly by a
 // persistent block (shared memory is reused).
-template <int LT, int CONN, bool SYM>
-__device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by) {
+template <int LT, int CONN, bool SYM, bool TC = false>
+__device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, const TcTile *tcx = nullptr) {
     constexpr int LP = storage_labels(LT);           // floats per pixel in HBM
     constexpr int NP = (LT + 1) / 2;                 // label pairs in the arithmetic
     constexpr int NPP = (NP + 1) / 2 * 2;            // pair slots per mu column
@@ -171,8 +210,9 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by) {
     constexpr bool MASK = (LT == LP);                // runtime L may be < LT
     static_assert(HALO <= GT, "one halo pixel per thread");
     static_assert(2 * NP <= LP, "pairs fit in the stored labels");
-    __shared__ __align__(16) float qt[(GY + 2) * TW * LS];
-    __shared__ __align__(16) float2 mus[SYM ? 1 : 2][LT * NPP];
+    __shared__ __align__(16) float qt_s[TC ? 4 : (GY + 2) * TW * LS];
+    __shared__ __align__(16) float2 mus[SYM ? 1 : 2][TC ? 2 : LT * NPP];
+    float *qt = TC ? tcx->qt : qt_s;
     __shared__ double red[GT / 32];
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * GX + tx;
@@ -185,7 +225,7 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by) {
     __syncthreads();   // shared memory of a previous tile is no longer read
 
     // mu pairs into shared memory
-    for (int i = tid; i < LT * NPP; i += GT) {
+    for (int i = tid; !TC && i < LT * NPP; i += GT) {
         mus[0][i] = j.mu_out[i];
         if (!SYM) mus[SYM ? 0 : 1][i] = j.mu_in[i];
     }
@@ -289,17 +329,74 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by) {
             acc_cell<NP>(S, c_ur, wi[3]);
         }
     }
-    pair_matvec<LT, NP, NPP>(m, mus[0], S);
-    if (!SYM) {
+    if constexpr (!TC) {
+        pair_matvec<LT, NP, NPP>(m, mus[0], S);
+        if (!SYM) {
 #pragma unroll
-        for (int j = 0; j < NP; ++j) S[j] = splat2(0.f);
-        acc_cell<NP>(S, c_l, wi[0]);
-        acc_cell<NP>(S, c_u, wi[1]);
-        if (CONN == 8) {
-            acc_cell<NP>(S, c_ul, wi[2]);
-            acc_cell<NP>(S, c_ur, wi[3]);
+            for (int j = 0; j < NP; ++j) S[j] = splat2(0.f);
+            acc_cell<NP>(S, c_l, wi[0]);
+            acc_cell<NP>(S, c_u, wi[1]);
+            if (CONN == 8) {
+                acc_cell<NP>(S, c_ul, wi[2]);
+                acc_cell<NP>(S, c_ur, wi[3]);
+            }
+            pair_matvec<LT, NP, NPP>(m, mus[SYM ? 0 : 1], S);
         }
-        pair_matvec<LT, NP, NPP>(m, mus[SYM ? 0 : 1], S);
+    } else {
+        constexpr int KP = tc_k(LT), SBO = tc_sbo(KP);
+        constexpr int AHALF = 128 * KP * 2;        // bytes of one M = 128 operand
+        const int half = tid >> 7, hrow = tid & 127;
+        uint8_t *arow = tcx->A + half * AHALF + (hrow >> 3) * SBO + (hrow & 7) * 16;
+        put_a_row<NP, KP>(arow, S);
+        if (!SYM) {
+#pragma unroll
+            for (int j = 0; j < NP; ++j) S[j] = splat2(0.f);
+            acc_cell<NP>(S, c_l, wi[0]);
+            acc_cell<NP>(S, c_u, wi[1]);
+            if (CONN == 8) {
+                acc_cell<NP>(S, c_ul, wi[2]);
+                acc_cell<NP>(S, c_ur, wi[3]);
+            }
+            put_a_row<NP, KP>(arow + 2 * AHALF, S);
+        }
+        tc::fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a0 = tc::smem_u32(tcx->A), b0 = tc::smem_u32(tcx->B);
+            constexpr uint32_t idesc = tc::idesc_bf16(128, KP);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                for (int ks = 0; ks < KP / 16; ++ks)
+                    tc::mma_bf16(tcx->tmem + h * KP, tc::smem_desc(a0 + h * AHALF + ks * 256, 128, SBO, 0),
+                                 tc::smem_desc(b0 + ks * 256, 128, SBO, 0), idesc, ks > 0 ? 1u : 0u);
+                if (!SYM) {
+#pragma unroll
+                    for (int ks = 0; ks < KP / 16; ++ks)
+                        tc::mma_bf16(tcx->tmem + h * KP,
+                                     tc::smem_desc(a0 + 2 * AHALF + h * AHALF + ks * 256, 128, SBO, 0),
+                                     tc::smem_desc(b0 + KP * KP * 2 + ks * 256, 128, SBO, 0), idesc, 1u);
+                }
+            }
+            tc::mma_commit(tcx->bar);
+        }
+        __syncwarp();
+        const bool ok = tc::mbar_wait(tcx->bar, 0, tcx->status);
+        tc::fence_after_sync();
+        float mm[KP];
+        const uint32_t taddr = tcx->tmem + ((uint32_t)(((tid >> 5) & 3) * 32) << 16) + (uint32_t)(half * KP);
+        if (ok) {
+            if constexpr (KP == 32)
+                tc::tmem_ld32(taddr, mm);
+            else
+                tc::tmem_ld16(taddr, mm);
+        } else {
+#pragma unroll
+            for (int i = 0; i < KP; ++i) mm[i] = 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < NP; ++j) m[j] = make_float2(mm[2 * j], mm[2 * j + 1]);
     }
 
     // a2-a3 and this pixel's free-energy term (q read back from the tile)
@@ -348,6 +445,7 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by) {
     double fd = inside ? (double)(f2.x + f2.y) : 0.0;
     fd = warp_sum_f64(fd);
     if ((tid & 31) == 0) red[tid >> 5] = fd;
+    if constexpr (TC) tc::fence_before_sync();   // TMEM reads done before the block syncs
     __syncthreads();
     double bs = 0.0;
     if (tid == 0) {
@@ -357,7 +455,18 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by) {
     return bs;
 }
 
-template <int LT, int CONN, bool SYM>
+// Dynamic shared memory of the tensor-core form: q tile, A and B operands.
+template <int LT, bool SYM>
+struct GridTcSmem {
+    static constexpr int LP = storage_labels(LT), LS = tile_stride(LP), KP = tc_k(LT);
+    static constexpr int QT = ((GY + 2) * (GX + 2) * LS * 4 + 1023) / 1024 * 1024;
+    static constexpr int A = (SYM ? 1 : 2) * 2 * 128 * KP * 2;
+    static constexpr int B = (SYM ? 1 : 2) * KP * KP * 2;
+    static constexpr int NCOL = 2 * KP < 32 ? 32 : 2 * KP;   // TMEM columns (power of two)
+    static constexpr int bytes = QT + A + B + 1024;           // + alignment slack
+};
+
+template <int LT, int CONN, bool SYM, bool TC>
 __global__ void __launch_bounds__(GT, (LT >= 24) ? 1 : 2)
 grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
     constexpr int LP = storage_labels(LT);
@@ -378,6 +487,30 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
         }
         return;
     }
+    TcTile tct{};
+    if constexpr (TC) {
+        using SM = GridTcSmem<LT, SYM>;
+        extern __shared__ __align__(1024) uint8_t gsm[];
+        __shared__ __align__(8) uint64_t bar;
+        __shared__ uint32_t tmem_slot;
+        uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gsm) + 1023) & ~(uintptr_t)1023);
+        tct.qt = reinterpret_cast<float *>(base);
+        tct.A = base + SM::QT;
+        tct.B = tct.A + SM::A;
+        for (int i = tid; i < SM::B / 16; i += GT) reinterpret_cast<uint4 *>(tct.A + SM::A)[i] = a.mu_tc[i];
+        if (tid == 0) {
+            tc::mbar_init(&bar, 1);
+            tc::mbar_init_fence();
+        }
+        if (tid < 32) tc::tmem_alloc(&tmem_slot, SM::NCOL);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        tct.tmem = tmem_slot;
+        tct.bar = &bar;
+        tct.status = a.status;
+    }
     TileJob j;
     j.s_in = a.s_in + (size_t)b * N * LP;
     j.s_out = a.s_out + (size_t)b * N * LP;
@@ -390,7 +523,12 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
     j.H = a.H;
     j.W = a.W;
     j.update = a.update;
-    const double bs = grid_tile<LT, CONN, SYM>(j, blockIdx.x, blockIdx.y);
+    const double bs = grid_tile<LT, CONN, SYM, TC>(j, blockIdx.x, blockIdx.y, &tct);
+    if constexpr (TC) {
+        // every thread's TMEM reads finished before the block sync inside grid_tile
+        tc::fence_after_sync();
+        if (tid < 32) tc::tmem_dealloc(tct.tmem, GridTcSmem<LT, SYM>::NCOL);
+    }
 
     const int blk = blockIdx.y * a.nbx + blockIdx.x;
     if (tid == 0) {
@@ -426,6 +564,20 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
     }
 }
 
+template <int LT, int CONN, bool SYM>
+cudaError_t launch_grid_tc(const GridStepArgs &a, dim3 grid, dim3 block, cudaStream_t st) {
+    constexpr int bytes = GridTcSmem<LT, SYM>::bytes;
+    static bool attr = false;   // set once per instantiation
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(grid_prox_step_kernel<LT, CONN, SYM, true>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    grid_prox_step_kernel<LT, CONN, SYM, true><<<grid, block, bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int LT>
 cudaError_t launch_grid_step_lt(const GridStepLaunch &l, cudaStream_t st) {
     GridStepArgs a;
@@ -453,17 +605,23 @@ cudaError_t launch_grid_step_lt(const GridStepLaunch &l, cudaStream_t st) {
     a.trace_cap = l.trace_cap;
     a.update = l.update;
     a.rel_tol = l.rel_tol;
+    a.mu_tc = l.mu_tc;
     dim3 grid(nbx, nby, l.B), block(GX, GY, 1);
+    if (l.tc) {
+        if (l.conn == 8)
+            return l.mu_sym ? launch_grid_tc<LT, 8, true>(a, grid, block, st) : launch_grid_tc<LT, 8, false>(a, grid, block, st);
+        return l.mu_sym ? launch_grid_tc<LT, 4, true>(a, grid, block, st) : launch_grid_tc<LT, 4, false>(a, grid, block, st);
+    }
     if (l.conn == 8) {
         if (l.mu_sym)
-            grid_prox_step_kernel<LT, 8, true><<<grid, block, 0, st>>>(a);
+            grid_prox_step_kernel<LT, 8, true, false><<<grid, block, 0, st>>>(a);
         else
-            grid_prox_step_kernel<LT, 8, false><<<grid, block, 0, st>>>(a);
+            grid_prox_step_kernel<LT, 8, false, false><<<grid, block, 0, st>>>(a);
     } else {
         if (l.mu_sym)
-            grid_prox_step_kernel<LT, 4, true><<<grid, block, 0, st>>>(a);
+            grid_prox_step_kernel<LT, 4, true, false><<<grid, block, 0, st>>>(a);
         else
-            grid_prox_step_kernel<LT, 4, false><<<grid, block, 0, st>>>(a);
+            grid_prox_step_kernel<LT, 4, false, false><<<grid, block, 0, st>>>(a);
     }
     return cudaGetLastError();
 }

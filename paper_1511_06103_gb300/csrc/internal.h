@@ -34,6 +34,16 @@ inline int kernel_labels(int L) { return L == 21 ? 21 : storage_labels(L); }
 // zero outside the L x L matrix.
 inline int mu_pair_slots(int LT) { return ((LT + 1) / 2 + 1) / 2 * 2; }
 
+// Tensor-core form of the grid step: the L x L product runs as BF16 MMAs
+// with K = N = tc_k(LT) labels.  Operands use the no-swizzle K-major layout:
+// 8 x 8 BF16 core matrices of 128 contiguous bytes, K-adjacent core matrices
+// 128 bytes apart (leading byte offset), 8-row groups tc_sbo bytes apart
+// (stride byte offset).  Element (r, k) of an operand sits at byte
+// (r / 8) * tc_sbo + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2.
+__host__ __device__ constexpr int tc_k(int LT) { return LT <= 16 ? 16 : 32; }
+__host__ __device__ constexpr int tc_sbo(int KP) { return KP / 8 * 128; }
+constexpr int kTcImageBytes = 2 * 32 * 32 * 2;   // mu and mu^T images at the largest tc_k
+
 // Everything one launch of the grid step needs.  State and unaries are
 // pixel-major [B][N][storage_labels(L)], N = H*W, pixel p = y*W + x; edge
 // weights are [B][N][n_dirs] with zero on edges that leave the image.
@@ -45,6 +55,8 @@ struct GridStepLaunch {
     const float *eta;        // [B] step per instance
     const float2 *mu_out;    // device [LT][NPP] column pairs (see mu_pair_slots)
     const float2 *mu_in;     // device [LT][NPP] row pairs
+    const uint4 *mu_tc;      // tensor-core form: device BF16 operand images of mu, mu^T
+    bool tc;                 // BF16 tensor-core messages (else FP32)
     double *partial;         // [B][nblk] per-tile free-energy partials (scratch)
     unsigned int *counter;   // [B] tiles finished in this launch (scratch, self-resetting)
     double *f_trace;         // [B][trace_cap]

@@ -57,13 +57,13 @@ def oracle_grads(oracle, U, mu, w, H, W, conn, eta, K, y):
     return loss, dU, dmu, dw
 
 
-def gpu_grads(binding, torch, d, eta, K, on_device=True):
+def gpu_grads(binding, torch, d, eta, K, on_device=True, precision=0):
     B = d["U"].shape[0] if d["U"].ndim == 3 else 1
     U = d["U"].reshape(B, d["H"] * d["W"], d["L"])
     w = d["w"].reshape(B, -1, d["H"], d["W"])
     y = np.asarray(d["y"]).reshape(B, -1)
     topo = binding.CRF_GRID8 if d["conn"] == 8 else binding.CRF_GRID4
-    crf = binding.CRF(topo, d["L"], d["H"], d["W"], batch=B)
+    crf = binding.CRF(topo, d["L"], d["H"], d["W"], batch=B, precision=precision)
     crf.set_unary(torch.from_numpy(U).cuda())
     crf.set_pairwise(torch.from_numpy(d["mu"]).cuda(), torch.from_numpy(np.ascontiguousarray(w)).cuda())
     ckpt = torch.empty(crf.checkpoint_floats(K), dtype=torch.float32, device="cuda")
@@ -225,6 +225,26 @@ def test_adjoint_full_size_sampled(env):
         _, dUr, _, dwr = oracle_grads(oracle, d["U"][b], d["mu"], d["w"][b], H, W, 4, eta, K, d["y"][b])
         assert close(dU[b], dUr / B)
         assert close(dw[b], dwr / B)
+
+
+def test_adjoint_bf16_forward(env):
+    """BF16 tensor-core messages in the forward steps (16 x 64 x 64, L = 21,
+    4-connected, K = 10): the loss and the gradients stay within 2% of the
+    FP64 reference (the trajectory itself carries the BF16 message error)."""
+    binding, oracle, torch = env
+    d = synth.unrolled_batch(B=2, H=64, W=64, L=21, conn=4, seed=9)
+    K, eta = 10, 0.25
+    loss, dU, dmu, dw = gpu_grads(binding, torch, d, eta, K, precision=binding.CRF_BF16)
+    dmu_ref = np.zeros((21, 21))
+    lref = 0.0
+    for b in range(2):
+        lb, dUr, dmur, dwr = oracle_grads(oracle, d["U"][b], d["mu"], d["w"][b], 64, 64, 4, eta, K, d["y"][b])
+        assert np.abs(dU[b] - dUr / 2).max() <= 2e-2 * np.abs(dUr / 2).max()
+        assert np.abs(dw[b] - dwr / 2).max() <= 2e-2 * np.abs(dwr / 2).max()
+        dmu_ref += dmur / 2
+        lref += lb / 2
+    assert np.abs(dmu - dmu_ref).max() <= 2e-2 * np.abs(dmu_ref).max()
+    assert abs(loss - lref) <= 1e-3 * abs(lref)
 
 
 def test_adjoint_rejects_unsupported(env):
