@@ -31,7 +31,6 @@
 //    scheduling or on the other instances of the batch.
 #pragma once
 
-#include <algorithm>
 #include <cmath>
 
 #include <cuda_bf16.h>
@@ -58,7 +57,7 @@ struct GridStepArgs {
     int *done;
     int *status;
     int L, H, W;
-    int nbx, nblk, nbatch;
+    int nbx, nblk;
     int t, trace_cap, update;
     double rel_tol;
 };
@@ -456,336 +455,6 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, co
     return bs;
 }
 
-// ---------------------------------------------------------------------------
-// Persistent, software-pipelined form of the FP32 step (the default path).
-//
-// A fixed grid of CTAs (two per SM) walks the tiles of all instances with a
-// stride of the grid size.  While a CTA computes tile n, the log q rows of
-// tile n+1 and its halo are already on their way into the other of two
-// shared-memory stages (cp.async), so the load latency that dominates the
-// one-tile-per-CTA form is hidden behind the arithmetic.  Each staged cell is
-// copied and later converted to q = exp(log q) by the same thread, so only
-// two barriers per tile remain: after the conversion (neighbours are read)
-// and at the end of the tile (the stage is free again).
-
-// cp.async of one pixel's LP floats (16-byte pieces; 8 bytes when LP = 2).
-template <int LP>
-__device__ __forceinline__ void cp_async_px(float *dst, const float *src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    if constexpr (LP == 2) {
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-    } else {
-#pragma unroll
-        for (int i = 0; i < LP / 4; ++i)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16 * i), "l"(src + 4 * i) : "memory");
-    }
-}
-
-// Cell (row, column) of the tile-with-halo handled by thread tid as its
-// halo cell (tid < HALO), in the order of grid_tile.
-__device__ __forceinline__ void halo_cell(int tid, int *hr, int *hc) {
-    constexpr int TW = GX + 2;
-    if (tid < TW) {
-        *hr = 0;
-        *hc = tid;
-    } else if (tid < 2 * TW) {
-        *hr = GY + 1;
-        *hc = tid - TW;
-    } else {
-        const int k = tid - 2 * TW;
-        *hr = 1 + (k >> 1);
-        *hc = (k & 1) ? TW - 1 : 0;
-    }
-}
-
-template <int LT>
-struct PipeSmem {
-    static constexpr int LP = storage_labels(LT), LS = tile_stride(LP);
-    static constexpr int CELLS = (GY + 2) * (GX + 2);
-    static constexpr int NPP = mu_pair_slots_c(LT);
-    static constexpr size_t stage_floats = (size_t)CELLS * LS;
-    static constexpr size_t bytes(bool sym) {
-        return 2 * stage_floats * sizeof(float) + (size_t)(sym ? 1 : 2) * LT * NPP * sizeof(float2);
-    }
-};
-
-template <int LT, int CONN, bool SYM>
-__global__ void __launch_bounds__(GT, (LT >= 24) ? 1 : 2)
-grid_step_pipe_kernel(const __grid_constant__ GridStepArgs a) {
-    using PS = PipeSmem<LT>;
-    constexpr int LP = PS::LP, LS = PS::LS, NPP = PS::NPP;
-    constexpr int NP = (LT + 1) / 2;
-    constexpr int ND = CONN == 8 ? 4 : 2;
-    constexpr int TW = GX + 2;
-    constexpr int HALO = 2 * TW + 2 * GY;
-    constexpr bool MASK = (LT == LP);
-    extern __shared__ __align__(16) float psm[];
-    float *stage0 = psm;
-    float2 *mus = reinterpret_cast<float2 *>(psm + 2 * PS::stage_floats);   // [SYM ? 1 : 2][LT * NPP]
-    __shared__ double red[GT / 32];
-    __shared__ int is_last;
-
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * GX + tx;
-    const int H = a.H, W = a.W, L = a.L;
-    const size_t N = (size_t)H * W;
-    const int tiles = a.nblk * a.nbatch;
-    int hr = 0, hc = 0;
-    if (tid < HALO) halo_cell(tid, &hr, &hc);
-
-    for (int i = tid; i < LT * NPP; i += GT) {
-        mus[i] = a.mu_out[i];
-        if (!SYM) mus[LT * NPP + i] = a.mu_in[i];
-    }
-
-    // issue the copies of tile t into stage st (cells outside the image are
-    // not copied; the conversion writes q = 0 there)
-    auto issue = [&](int t, int st) {
-        const int b = t / a.nblk, blk = t - b * a.nblk;
-        const int by = blk / a.nbx, bx = blk - by * a.nbx;
-        const int x0 = bx * GX, y0 = by * GY;
-        const float *sin = a.s_in + (size_t)b * N * LP;
-        float *dst = stage0 + (size_t)st * PS::stage_floats;
-        const int x = x0 + tx, y = y0 + ty;
-        if (x < W && y < H) cp_async_px<LP>(dst + ((ty + 1) * TW + tx + 1) * LS, sin + ((size_t)y * W + x) * LP);
-        if (tid < HALO) {
-            const int gy = y0 - 1 + hr, gx = x0 - 1 + hc;
-            if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-                cp_async_px<LP>(dst + (hr * TW + hc) * LS, sin + ((size_t)gy * W + gx) * LP);
-        }
-    };
-
-    int t = blockIdx.x;
-    if (t < tiles) issue(t, 0);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    for (int it = 0; t < tiles; ++it, t += gridDim.x) {
-        const int st = it & 1;
-        if (t + (int)gridDim.x < tiles) issue(t + gridDim.x, st ^ 1);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-
-        const int b = t / a.nblk, blk = t - b * a.nblk;
-        const int by = blk / a.nbx, bx = blk - by * a.nbx;
-        const int x = bx * GX + tx, y = by * GY + ty;
-        const bool inside = (x < W) && (y < H);
-        const size_t p = (size_t)y * W + x;
-        const size_t ib = (size_t)b * N;
-        float *qt = stage0 + (size_t)st * PS::stage_floats;
-        const bool skip = a.done != nullptr && a.done[b] != 0;
-
-        // unaries and edge weights of this tile (in flight during the wait)
-        float2 u[LP / 2];
-        float wo[4] = {0.f, 0.f, 0.f, 0.f}, wi[4] = {0.f, 0.f, 0.f, 0.f};
-        if (inside && !skip) {
-            load_px<LP>(u, a.U + (ib + p) * LP);
-            const float *wb = a.w + ib * ND;
-            if (ND == 4) {
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(wb + p * ND));
-                wo[0] = v.x;
-                wo[1] = v.y;
-                wo[2] = v.z;
-                wo[3] = v.w;
-            } else {
-                const float2 v = __ldg(reinterpret_cast<const float2 *>(wb + p * ND));
-                wo[0] = v.x;
-                wo[1] = v.y;
-            }
-            if (x > 0) wi[0] = __ldg(wb + (p - 1) * ND + 0);
-            if (y > 0) wi[1] = __ldg(wb + (p - W) * ND + 1);
-            if (CONN == 8) {
-                if (x > 0 && y > 0) wi[2] = __ldg(wb + (p - W - 1) * ND + 2);
-                if (x + 1 < W && y > 0) wi[3] = __ldg(wb + (p - W + 1) * ND + 3);
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < LP / 2; ++k) u[k] = splat2(0.f);
-        }
-
-        // this thread's own copies of tile t are complete
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-
-        // own log q from the stage, then q = exp(log q) in place (own cell
-        // and this thread's halo cell)
-        float2 s[LP / 2];
-        float *own = qt + ((ty + 1) * TW + tx + 1) * LS;
-        if (inside) {
-            if constexpr (LP == 2) {
-                s[0] = *reinterpret_cast<const float2 *>(own);
-            } else {
-#pragma unroll
-                for (int k = 0; k < LP / 4; ++k) {
-                    const float4 v = reinterpret_cast<const float4 *>(own)[k];
-                    s[2 * k] = make_float2(v.x, v.y);
-                    s[2 * k + 1] = make_float2(v.z, v.w);
-                }
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < LP / 2; ++k) s[k] = splat2(kPadLogQ);
-        }
-        put_cell<LP>(own, s);
-        if (tid < HALO) {
-            float *c = qt + (hr * TW + hc) * LS;
-            const int gy = by * GY - 1 + hr, gx = bx * GX - 1 + hc;
-            float2 h[LP / 2];
-            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-                if constexpr (LP == 2) {
-                    h[0] = *reinterpret_cast<const float2 *>(c);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < LP / 4; ++k) {
-                        const float4 v = reinterpret_cast<const float4 *>(c)[k];
-                        h[2 * k] = make_float2(v.x, v.y);
-                        h[2 * k + 1] = make_float2(v.z, v.w);
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < LP / 2; ++k) h[k] = splat2(kPadLogQ);
-            }
-            put_cell<LP>(c, h);
-        }
-        __syncthreads();
-
-        double fd = 0.0;
-        if (skip) {
-            // stopping rule met: carry the state through unchanged
-            if (a.update && inside) {
-                float2 v[LP / 2];
-                load_px<LP>(v, a.s_in + (ib + p) * LP);
-                store_px<LP>(a.s_out + (ib + p) * LP, v);
-            }
-        } else {
-            const float *c_r = qt + ((ty + 1) * TW + tx + 2) * LS;
-            const float *c_d = qt + ((ty + 2) * TW + tx + 1) * LS;
-            const float *c_dr = qt + ((ty + 2) * TW + tx + 2) * LS;
-            const float *c_dl = qt + ((ty + 2) * TW + tx) * LS;
-            const float *c_l = qt + ((ty + 1) * TW + tx) * LS;
-            const float *c_u = qt + (ty * TW + tx + 1) * LS;
-            const float *c_ul = qt + (ty * TW + tx) * LS;
-            const float *c_ur = qt + (ty * TW + tx + 2) * LS;
-
-            // a1: neighbour sums and the L x L product, m = mu S_out + mu^T S_in
-            float2 m[NP], S[NP];
-#pragma unroll
-            for (int k = 0; k < NP; ++k) {
-                m[k] = splat2(0.f);
-                S[k] = splat2(0.f);
-            }
-            acc_cell<NP>(S, c_r, wo[0]);
-            acc_cell<NP>(S, c_d, wo[1]);
-            if (CONN == 8) {
-                acc_cell<NP>(S, c_dr, wo[2]);
-                acc_cell<NP>(S, c_dl, wo[3]);
-            }
-            if (SYM) {
-                acc_cell<NP>(S, c_l, wi[0]);
-                acc_cell<NP>(S, c_u, wi[1]);
-                if (CONN == 8) {
-                    acc_cell<NP>(S, c_ul, wi[2]);
-                    acc_cell<NP>(S, c_ur, wi[3]);
-                }
-            }
-            pair_matvec<LT, NP, NPP>(m, mus, S);
-            if (!SYM) {
-#pragma unroll
-                for (int k = 0; k < NP; ++k) S[k] = splat2(0.f);
-                acc_cell<NP>(S, c_l, wi[0]);
-                acc_cell<NP>(S, c_u, wi[1]);
-                if (CONN == 8) {
-                    acc_cell<NP>(S, c_ul, wi[2]);
-                    acc_cell<NP>(S, c_ur, wi[3]);
-                }
-                pair_matvec<LT, NP, NPP>(m, mus + (SYM ? 0 : LT * NPP), S);
-            }
-
-            // a2-a3 and this pixel's free-energy term
-            float2 qc[NP];
-#pragma unroll
-            for (int k = 0; k < NP; ++k) qc[k] = splat2(0.f);
-            acc_cell<NP>(qc, own, 1.f);
-            const float eta = a.eta[b];
-            const float2 neta = splat2(-eta), ome = splat2(1.f - eta), half = splat2(0.5f);
-            float2 f2 = splat2(0.f);
-            float mx = -INFINITY;
-#pragma unroll
-            for (int k = 0; k < NP; ++k) {
-                const float2 g = add2(u[k], m[k]);
-                const float2 hh = add2(fma2(half, m[k], u[k]), s[k]);
-                f2 = fma2(qc[k], hh, f2);
-                float2 av = fma2(neta, g, mul2(ome, s[k]));
-                const int l0 = 2 * k, l1 = 2 * k + 1;
-                if ((MASK && l0 >= L)) av.x = -INFINITY;
-                if ((MASK && l1 >= L) || l1 >= LT) av.y = -INFINITY;
-                s[k] = av;
-                mx = fmaxf(mx, fmaxf(av.x, av.y));
-            }
-            // a4: renormalise
-            float z = 0.f;
-#pragma unroll
-            for (int k = 0; k < NP; ++k) z += __expf(s[k].x - mx) + __expf(s[k].y - mx);
-            const float2 nlse = splat2(-(mx + __logf(z)));
-            if (a.update && inside) {
-                float2 o[LP / 2];
-#pragma unroll
-                for (int k = 0; k < LP / 2; ++k) {
-                    if (k < NP) {
-                        o[k] = add2(s[k], nlse);
-                        const int l0 = 2 * k, l1 = 2 * k + 1;
-                        if ((MASK && l0 >= L)) o[k].x = kPadLogQ;
-                        if ((MASK && l1 >= L) || l1 >= LT) o[k].y = kPadLogQ;
-                    } else {
-                        o[k] = splat2(kPadLogQ);
-                    }
-                }
-                store_px<LP>(a.s_out + (ib + p) * LP, o);
-            }
-            fd = inside ? (double)(f2.x + f2.y) : 0.0;
-        }
-
-        // a5: F partial of this tile, FP64; the last tile of the instance
-        // reduces all partials in a fixed order
-        fd = warp_sum_f64(fd);
-        if ((tid & 31) == 0) red[tid >> 5] = fd;
-        __syncthreads();   // also: the stage of tile t is no longer read
-        if (!skip) {
-            if (tid == 0) {
-                double bs = 0.0;
-#pragma unroll
-                for (int k = 0; k < GT / 32; ++k) bs += red[k];
-                a.partial[(size_t)b * a.nblk + blk] = bs;
-                __threadfence();
-                const unsigned prev = atomicAdd(a.counter + b, 1u);
-                is_last = (prev == (unsigned)(a.nblk - 1));
-            }
-            __syncthreads();
-            if (is_last) {
-                __threadfence();
-                double acc = 0.0;
-                for (int k = tid; k < a.nblk; k += GT) acc += __ldcg(a.partial + (size_t)b * a.nblk + k);
-                acc = warp_sum_f64(acc);
-                if ((tid & 31) == 0) red[tid >> 5] = acc;
-                __syncthreads();
-                if (tid == 0) {
-                    double F = 0.0;
-#pragma unroll
-                    for (int k = 0; k < GT / 32; ++k) F += red[k];
-                    a.f_cur[b] = F;
-                    if (!isfinite(F)) atomicExch(a.status, -6);
-                    if (a.update) {
-                        if (a.t < a.trace_cap) a.f_trace[(size_t)b * a.trace_cap + a.t] = F;
-                        if (a.rel_tol > 0.0 && a.t > 0 && a.t - 1 < a.trace_cap && a.done != nullptr) {
-                            const double Fp = a.f_trace[(size_t)b * a.trace_cap + a.t - 1];
-                            if (fabs(F - Fp) <= a.rel_tol * fabs(F)) a.done[b] = a.t + 1;
-                        }
-                    }
-                    a.counter[b] = 0u;
-                }
-                __syncthreads();   // red is reused by the next tile
-            }
-        }
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
 // Dynamic shared memory of the tensor-core form: q tile, A and B operands.
 template <int LT, bool SYM>
 struct GridTcSmem {
@@ -909,31 +578,6 @@ cudaError_t launch_grid_tc(const GridStepArgs &a, dim3 grid, dim3 block, cudaStr
     return cudaGetLastError();
 }
 
-// Persistent launch: as many CTAs as fit on the device at once (never more
-// than there are tiles).
-template <int LT, int CONN, bool SYM>
-cudaError_t launch_grid_pipe(const GridStepArgs &a, cudaStream_t st) {
-    constexpr size_t bytes = PipeSmem<LT>::bytes(SYM);
-    static int per_sm = 0, sms = 0, dev_seen = -1;   // per instantiation, first use on a device
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev != dev_seen) {
-        e = cudaFuncSetAttribute(grid_step_pipe_kernel<LT, CONN, SYM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)bytes);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grid_step_pipe_kernel<LT, CONN, SYM>, GT, bytes);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        dev_seen = dev;
-    }
-    const long long tiles = (long long)a.nblk * a.nbatch;
-    const int grid = (int)std::min<long long>(tiles, (long long)per_sm * sms);
-    grid_step_pipe_kernel<LT, CONN, SYM><<<grid, dim3(GX, GY, 1), bytes, st>>>(a);
-    return cudaGetLastError();
-}
-
 template <int LT>
 cudaError_t launch_grid_step_lt(const GridStepLaunch &l, cudaStream_t st) {
     GridStepArgs a;
@@ -968,10 +612,17 @@ cudaError_t launch_grid_step_lt(const GridStepLaunch &l, cudaStream_t st) {
             return l.mu_sym ? launch_grid_tc<LT, 8, true>(a, grid, block, st) : launch_grid_tc<LT, 8, false>(a, grid, block, st);
         return l.mu_sym ? launch_grid_tc<LT, 4, true>(a, grid, block, st) : launch_grid_tc<LT, 4, false>(a, grid, block, st);
     }
-    a.nbatch = l.B;
-    if (l.conn == 8)
-        return l.mu_sym ? launch_grid_pipe<LT, 8, true>(a, st) : launch_grid_pipe<LT, 8, false>(a, st);
-    return l.mu_sym ? launch_grid_pipe<LT, 4, true>(a, st) : launch_grid_pipe<LT, 4, false>(a, st);
+    if (l.conn == 8) {
+        if (l.mu_sym)
+            grid_prox_step_kernel<LT, 8, true, false><<<grid, block, 0, st>>>(a);
+        else
+            grid_prox_step_kernel<LT, 8, false, false><<<grid, block, 0, st>>>(a);
+    } else {
+        if (l.mu_sym)
+            grid_prox_step_kernel<LT, 4, true, false><<<grid, block, 0, st>>>(a);
+        else
+            grid_prox_step_kernel<LT, 4, false, false><<<grid, block, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

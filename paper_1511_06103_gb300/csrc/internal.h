@@ -33,7 +33,6 @@ inline int kernel_labels(int L) { return L == 21 ? 21 : storage_labels(L); }
 // out[k*NPP + j] = (mu[2j][k], mu[2j+1][k]), in[k*NPP + j] = (mu[k][2j], mu[k][2j+1]),
 // zero outside the L x L matrix.
 inline int mu_pair_slots(int LT) { return ((LT + 1) / 2 + 1) / 2 * 2; }
-__host__ __device__ constexpr int mu_pair_slots_c(int LT) { return ((LT + 1) / 2 + 1) / 2 * 2; }
 
 // Tensor-core form of the grid step: the L x L product runs as BF16 MMAs
 // with K = N = tc_k(LT) labels.  Operands use the no-swizzle K-major layout:
