@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--serve-requests", type=int, default=128,
                    help="requests of the serving measurement (0 skips it)")
     p.add_argument("--serve-only", action="store_true")
+    p.add_argument("--no-denoising", action="store_true",
+                   help="skip the 64x64 binary denoising measurement")
+    p.add_argument("--denoising-only", action="store_true")
     p.add_argument("--no-grid-bf16", action="store_true",
                    help="skip the BF16 tensor-core form of the segmentation workload")
     p.add_argument("--grid-bf16-only", action="store_true")
@@ -329,10 +332,52 @@ def run_grid_precision(args, dev, peak):
             "q_max_abs_diff": float(np.abs(q32 - q16).max())}
 
 
+def run_denoising(args, dev):
+    """Binary denoising CRF, 64 x 64, L = 2, 4-connected, 50 steps at the
+    step-size constant: device time per solve with launches issued one by
+    one and with the step loop replayed as a CUDA graph."""
+    import torch
+
+    from paper_1511_06103_gb300 import binding, synth
+    d = synth.binary_denoising()
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for mode in ("eager", "graph"):
+        crf = binding.CRF(binding.CRF_GRID4, 2, 64, 64, stream=stream.cuda_stream)
+        crf.use_graphs(mode == "graph")
+        crf.set_unary(torch.from_numpy(d["U"]).to(dev))
+        crf.set_pairwise(torch.from_numpy(d["mu"]).to(dev), torch.from_numpy(d["w"]).to(dev))
+        _, eta = crf.lipschitz()
+
+        def solve():
+            crf.iterate(50, eta=0.0, reset=True, final_free_energy=True)
+
+        for _ in range(max(3, args.warmup)):
+            solve()
+        torch.cuda.synchronize()
+        n = 50
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(n):
+            solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / n
+        ms = e0.elapsed_time(e1) / n
+        out[mode] = {"us_per_solve": 1000.0 * ms, "host_us_per_solve": 1e6 * wall,
+                     "value": 64 * 64 * 2 * 50 / (ms / 1000.0), "unit": UNIT,
+                     "final_F": float(crf.free_energy()[0])}
+        crf.close()
+    return {"workload": "binary denoising CRF 64x64, L=2, 4-connected, 50 parallel proximal steps at "
+                        "eta = 1/(1+Lambda) (0.2383), back-to-back solves", "eta": float(eta[0]), **out}
+
+
 UNR_B, UNR_SIDE, UNR_L, UNR_CONN, UNR_K = 16, 256, 21, 4, 10
 
 
-def run_unrolled(args, dev, peak):
+def run_unrolled(args, dev, peak, precision=0):
     """Training step through K = 10 unrolled proximal steps on a batch of 16
     4-connected 256 x 256 grids, L = 21: forward with per-step checkpoints,
     export of log q^K, cross-entropy gradient, reverse pass to dU, dmu, dw.
@@ -343,7 +388,8 @@ def run_unrolled(args, dev, peak):
     d = synth.unrolled_batch(B=UNR_B, H=UNR_SIDE, W=UNR_SIDE, L=UNR_L, conn=UNR_CONN)
     B, N, L, K = UNR_B, UNR_SIDE * UNR_SIDE, UNR_L, UNR_K
     stream = torch.cuda.current_stream(dev)
-    crf = binding.CRF(binding.CRF_GRID4, L, UNR_SIDE, UNR_SIDE, batch=B, stream=stream.cuda_stream)
+    crf = binding.CRF(binding.CRF_GRID4, L, UNR_SIDE, UNR_SIDE, batch=B, precision=precision,
+                      stream=stream.cuda_stream)
     crf.set_unary(torch.from_numpy(d["U"]).to(dev))
     crf.set_pairwise(torch.from_numpy(d["mu"]).to(dev), torch.from_numpy(d["w"]).to(dev))
     lam, eta_b = crf.lipschitz()
@@ -401,8 +447,9 @@ def run_unrolled(args, dev, peak):
     bwd_bytes = B * N * (24 * L + 12 * 2)
     fwd_bytes = B * N * (12 * L + 4 * 2)
     return {"workload": "unrolled inference, batch 16 of 4-connected 256x256 grids, L=21, K=10, "
-                        "FP32 messages; forward with per-step checkpoints + cross-entropy gradient + "
-                        "reverse pass to dU, dmu, dw",
+                        + ("BF16 tensor-core messages" if precision else "FP32 messages")
+                        + "; forward with per-step checkpoints + cross-entropy gradient + "
+                        "reverse pass to dU, dmu, dw (FP32)",
             "value": B * N * L * K / (ms / 1000.0), "unit": "updates/s (forward + reverse per update)",
             "train_steps_per_s": 1000.0 / ms, "ms_per_train_step": ms,
             "forward_step_ms": fwd_ms, "reverse_step_ms": bwd_ms, "eta": eta, "loss": loss,
@@ -525,13 +572,17 @@ def run_ours(args, world, rank, local):
     if args.serve_only:
         print(json.dumps({"serving": run_serving(max(1, args.serve_requests))}), flush=True)
         return
+    if args.denoising_only:
+        print(json.dumps({"denoising": run_denoising(args, dev)}), flush=True)
+        return
     if args.grid_bf16_only:
         peak, _ = measured_peaks()
         print(json.dumps({"grid_precision": run_grid_precision(args, dev, peak)}), flush=True)
         return
     if args.unrolled_only:
         peak, _ = measured_peaks()
-        print(json.dumps({"unrolled": run_unrolled(args, dev, peak)}), flush=True)
+        print(json.dumps({"unrolled": {"f32": run_unrolled(args, dev, peak),
+                                       "bf16_tc": run_unrolled(args, dev, peak, 1)}}), flush=True)
         return
     if args.dense_only:
         peak, _ = measured_peaks()
@@ -663,12 +714,15 @@ def run_ours(args, world, rank, local):
                  "f32": r32, "bf16_tc": r16, "bf16_speedup": r16["value"] / r32["value"],
                  "final_F_rel_diff": abs(r16["final_F"] - r32["final_F"]) / abs(r32["final_F"]),
                  "q_max_abs_diff": dq}
+    denoise = None
+    if not args.no_denoising and world == 1:
+        denoise = run_denoising(args, dev)
     grid_prec = None
     if not args.no_grid_bf16 and world == 1:
         grid_prec = run_grid_precision(args, dev, peak)
     unrolled = None
     if not args.no_unrolled and world == 1:
-        unrolled = run_unrolled(args, dev, peak)
+        unrolled = {"f32": run_unrolled(args, dev, peak), "bf16_tc": run_unrolled(args, dev, peak, 1)}
     serving = None
     if args.serve_requests > 0 and world == 1:
         serving = run_serving(args.serve_requests)
@@ -700,6 +754,7 @@ def run_ours(args, world, rank, local):
             "final_F": F_final,
             "wall_ms_timed": 1000 * (wall1 - wall0),
             "dense": dense,
+            "denoising": denoise,
             "grid_precision": grid_prec,
             "unrolled": unrolled,
             "serving": serving,

@@ -169,6 +169,16 @@ crf_status mf_profile(crf_t h, int32_t enable);
  * the loop's end event. */
 crf_status mf_profile_read(crf_t h, double *loop_ms, int32_t *launches);
 
+/* mf_use_graphs -- 1: mf_iterate records its step launches into a CUDA
+ * graph the first time a configuration (max_iters, refine_fp32, rel_tol, the
+ * step-size source, the parity of the state buffers) is seen and replays the
+ * graph afterwards, which removes the host launch cost per step (small
+ * problems are launch-bound); 0 (default): launches are issued one by one.
+ * Graphs hold the handle's device buffers and are dropped when the free-
+ * energy trace is regrown or the handle is destroyed.  Results are identical
+ * either way. */
+crf_status mf_use_graphs(crf_t h, int32_t enable);
+
 /* crf_launch_count -- number of kernels this handle has launched so far. */
 crf_status crf_launch_count(crf_t h, int64_t *n);
 

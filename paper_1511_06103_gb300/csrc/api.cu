@@ -60,6 +60,15 @@ struct crf_s {
     bool prof_valid = false;
     long long launches = 0;
     bool fcur_valid = false;
+    // CUDA graphs of the mf_iterate launch sequence, one per configuration
+    struct GraphEntry {
+        int iters, refine, cur;
+        double rel_tol;
+        const float *eta;
+        cudaGraphExec_t exec;
+    };
+    bool use_graphs = false;
+    std::vector<GraphEntry> graphs;
     // reverse mode (allocated on first mf_unrolled_backward)
     float *adj_gs = nullptr;     // [B][N][LP]
     float *adj_gs2 = nullptr;    // [B][N][LP] (ping-pong with adj_gs)
@@ -118,6 +127,8 @@ void free_all(crf_t h) {
     float *ad[] = {h->adj_gs, h->adj_gs2, h->adj_dU, h->adj_dw, h->adj_dwx, h->adj_part, h->adj_mu};
     for (float *p : ad)
         if (p) cudaFree(p);
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
 }
@@ -143,6 +154,8 @@ crf_status ensure_trace(crf_t h, int iters) {
     }
     h->ftrace = nt;
     h->trace_cap = cap;
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);   // they captured the old trace buffer
+    h->graphs.clear();
     return CRF_OK;
 }
 
@@ -649,13 +662,51 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
     if (p->refine_fp32 < 0) return CRF_E_INVALID;
     rc = ensure_trace(h, p->max_iters + refine);
     if (rc != CRF_OK) return rc;
-    if (p->rel_tol > 0) CK(h, cudaMemsetAsync(h->done, 0, h->B * sizeof(int), h->st));
-    if (h->profile) CK(h, cudaEventRecord(h->ev0, h->st));
-    for (int t = 0; t < p->max_iters + refine; ++t) {
-        CK(h, launch_step(h, eta, t, 1, p->rel_tol, t >= p->max_iters));
-        h->cur ^= 1;
+    const int nsteps = p->max_iters + refine;
+    // the step loop: eager, or captured once per configuration and replayed
+    auto body = [&]() -> cudaError_t {
+        if (p->rel_tol > 0) {
+            cudaError_t e = cudaMemsetAsync(h->done, 0, h->B * sizeof(int), h->st);
+            if (e != cudaSuccess) return e;
+        }
+        for (int t = 0; t < nsteps; ++t) {
+            cudaError_t e = launch_step(h, eta, t, 1, p->rel_tol, t >= p->max_iters);
+            if (e != cudaSuccess) return e;
+            h->cur ^= 1;
+        }
+        return cudaSuccess;
+    };
+    cudaGraphExec_t exec = nullptr;
+    if (h->use_graphs && nsteps > 0) {
+        for (auto &g : h->graphs)
+            if (g.iters == p->max_iters && g.refine == refine && g.cur == h->cur && g.rel_tol == p->rel_tol &&
+                g.eta == eta)
+                exec = g.exec;
+        if (!exec) {
+            const int cur0 = h->cur;
+            CK(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed));
+            const cudaError_t e = body();
+            cudaGraph_t graph = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(h->st, &graph);
+            h->cur = cur0;   // nothing ran yet
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return fail_cuda(h, e != cudaSuccess ? e : e2);
+            }
+            const cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            CK(h, e3);
+            h->graphs.push_back({p->max_iters, refine, cur0, p->rel_tol, eta, exec});
+        }
     }
-    h->launches += p->max_iters + refine;
+    if (h->profile) CK(h, cudaEventRecord(h->ev0, h->st));
+    if (exec) {
+        CK(h, cudaGraphLaunch(exec, h->st));
+        h->cur ^= nsteps & 1;
+    } else {
+        CK(h, body());
+    }
+    h->launches += nsteps;
     if (h->profile) {
         CK(h, cudaEventRecord(h->ev1, h->st));
         h->prof_launches = p->max_iters + refine;
@@ -760,6 +811,13 @@ crf_status mf_profile_read(crf_t h, double *loop_ms, int32_t *launches) {
     CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
     if (loop_ms) *loop_ms = ms;
     if (launches) *launches = h->prof_launches;
+    return CRF_OK;
+}
+
+crf_status mf_use_graphs(crf_t h, int32_t enable) {
+    crf_status rc = check_handle(h);
+    if (rc != CRF_OK) return rc;
+    h->use_graphs = enable != 0;
     return CRF_OK;
 }
 

@@ -265,3 +265,32 @@ def test_rotation_equivariance_gpu(env):
     sr, Fr, _ = gpu_run(binding, torch, dr, 0.3, 7)
     assert np.abs(np.exp(sr) - np.exp(H.rot90_cw_field(s, d["H"], d["W"]))).max() <= 1e-6
     assert abs(F - Fr) <= 1e-6 * abs(F)
+
+
+@pytest.mark.parametrize("rel_tol", [0.0, 1e-6])
+def test_graph_replay_matches_eager(env, rel_tol):
+    """mf_use_graphs: captured and replayed step loops give bit-identical
+    states, traces and iteration counts (first replay and cached replays)."""
+    binding, oracle, torch = env
+    d = synth.binary_denoising()
+    res = []
+    for graphs in (False, True):
+        with make(binding, torch, d) as crf:
+            crf.use_graphs(graphs)
+            crf.set_unary(d["U"])
+            crf.set_pairwise(d["mu"], d["w"])
+            out = []
+            for _ in range(3):
+                its = crf.iterate(50, eta=0.0, reset=True, rel_tol=rel_tol, want_iters=True)
+                out.append((crf.log_marginals().copy(), crf.free_energy_trace(50).copy(), its.copy()))
+            # an odd count flips the buffer parity; the next call needs another graph
+            crf.iterate(7, eta=0.3)
+            out.append((crf.log_marginals().copy(), crf.free_energy_trace(7).copy(), None))
+            crf.iterate(7, eta=0.3)
+            out.append((crf.log_marginals().copy(), crf.free_energy_trace(7).copy(), None))
+            res.append(out)
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(a[0], b[0])
+        assert np.array_equal(a[1], b[1])
+        if a[2] is not None:
+            assert np.array_equal(a[2], b[2])
