@@ -69,6 +69,7 @@ struct crf_s {
     };
     bool use_graphs = false;
     std::vector<GraphEntry> graphs;
+    cudaStream_t cap_st = nullptr;   // private stream to record on (the legacy stream cannot be captured)
     // reverse mode (allocated on first mf_unrolled_backward)
     float *adj_gs = nullptr;     // [B][N][LP]
     float *adj_gs2 = nullptr;    // [B][N][LP] (ping-pong with adj_gs)
@@ -129,6 +130,7 @@ void free_all(crf_t h) {
         if (p) cudaFree(p);
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
+    if (h->cap_st) cudaStreamDestroy(h->cap_st);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
 }
@@ -684,10 +686,15 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
                 exec = g.exec;
         if (!exec) {
             const int cur0 = h->cur;
-            CK(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed));
-            const cudaError_t e = body();
+            if (!h->cap_st) CK(h, cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+            // record the loop on the private stream; the graph is launched on the handle's stream
+            cudaStream_t st0 = h->st;
+            h->st = h->cap_st;
+            cudaError_t e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed);
+            if (e == cudaSuccess) e = body();
             cudaGraph_t graph = nullptr;
             const cudaError_t e2 = cudaStreamEndCapture(h->st, &graph);
+            h->st = st0;
             h->cur = cur0;   // nothing ran yet
             if (e != cudaSuccess || e2 != cudaSuccess) {
                 if (graph) cudaGraphDestroy(graph);
