@@ -26,6 +26,9 @@
 //    count); the L x L product, the neighbour sums and the element-wise update
 //    use packed f32x2 FMAs (one instruction per two labels), with ceil(L/2)
 //    independent accumulators.
+//  - The FP32 form keeps the pixel's own log q in shared memory and loads
+//    the unaries after the L x L product, so that three CTAs fit per SM
+//    (measured 4.5 % faster than two CTAs holding both in registers).
 //  - Free-energy partials are reduced per tile in FP64 and finished by the
 //    last tile of each instance in a fixed order, so F does not depend on
 //    scheduling or on the other instances of the batch.
@@ -211,6 +214,7 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, co
     static_assert(HALO <= GT, "one halo pixel per thread");
     static_assert(2 * NP <= LP, "pairs fit in the stored labels");
     __shared__ __align__(16) float qt_s[TC ? 4 : (GY + 2) * TW * LS];
+    __shared__ __align__(16) float sown[TC ? 4 : GT * LS];
     __shared__ __align__(16) float2 mus[SYM ? 1 : 2][TC ? 2 : LT * NPP];
     float *qt = TC ? tcx->qt : qt_s;
     __shared__ double red[GT / 32];
@@ -264,6 +268,7 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, co
         put_cell<LP>(qt + (hr * TW + hc) * LS, h);
     }
     put_cell<LP>(qt + ((ty + 1) * TW + tx + 1) * LS, s);
+    if constexpr (!TC) store_px<LP>(sown + tid * LS, s);
 
     // edge weights leaving this pixel, and entering it (stored at the pixel
     // that owns the edge)
@@ -290,13 +295,15 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, co
     }
     __syncthreads();
 
-    // unaries: issued now, consumed after the L x L product
+    // unaries: the FP32 form loads them after the L x L product
     float2 u[LP / 2];
-    if (inside) {
-        load_px<LP>(u, j.U + p * LP);
-    } else {
+    if (TC) {
+        if (inside) {
+            load_px<LP>(u, j.U + p * LP);
+        } else {
 #pragma unroll
-        for (int i = 0; i < LP / 2; ++i) u[i] = splat2(0.f);
+            for (int i = 0; i < LP / 2; ++i) u[i] = splat2(0.f);
+        }
     }
 
     const float *c_r = qt + ((ty + 1) * TW + tx + 2) * LS;
@@ -399,6 +406,24 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, co
         for (int j = 0; j < NP; ++j) m[j] = make_float2(mm[2 * j], mm[2 * j + 1]);
     }
 
+    if constexpr (!TC) {
+        if (inside) {
+            load_px<LP>(u, j.U + p * LP);
+        } else {
+#pragma unroll
+            for (int i = 0; i < LP / 2; ++i) u[i] = splat2(0.f);
+        }
+        if constexpr (LP == 2) {
+            s[0] = *reinterpret_cast<const float2 *>(sown + tid * LS);
+        } else {
+#pragma unroll
+            for (int i = 0; i < LP / 4; ++i) {
+                const float4 v = reinterpret_cast<const float4 *>(sown + tid * LS)[i];
+                s[2 * i] = make_float2(v.x, v.y);
+                s[2 * i + 1] = make_float2(v.z, v.w);
+            }
+        }
+    }
     // a2-a3 and this pixel's free-energy term (q read back from the tile)
     float2 qc[NP];
 #pragma unroll
@@ -467,7 +492,7 @@ struct GridTcSmem {
 };
 
 template <int LT, int CONN, bool SYM, bool TC>
-__global__ void __launch_bounds__(GT, (LT >= 24) ? 1 : 2)
+__global__ void __launch_bounds__(GT, (LT >= 24) ? 1 : 3)
 grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
     constexpr int LP = storage_labels(LT);
     __shared__ double red[GT / 32];
