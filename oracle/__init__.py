@@ -66,6 +66,8 @@ def _load():
             "orc_init_logq": (None, [_vp, _vp]),
             "orc_prox_step": (None, [_vp, _d, _vp, _vp]),
             "orc_parallel_prox": (None, [_vp, _d, _i32, _vp, _vp]),
+            "orc_prox_step_adaptive": (_i32, [_vp, _d, _vp, _vp]),
+            "orc_parallel_prox_adaptive": (_i32, [_vp, _d, _i32, _vp, _vp]),
             "orc_prox_step_rows": (None, [_vp, _d, _vp, _vp, _i64, _vp]),
             "orc_sweep": (None, [_vp, _i32, _vp]),
             "orc_state_energy": (_d, [_vp, _vp]),
@@ -246,6 +248,23 @@ class Model:
         F = np.zeros(iters + 1) if trace else None
         _load().orc_parallel_prox(self._h, float(eta), int(iters), _ptr(s),
                                   _ptr(F) if trace else None)
+        return s, F
+
+    def prox_step_adaptive(self, d: float, s) -> np.ndarray:
+        """One adaptive step of a binary model (Sec. 3.3): eta_i = 1/(1 + d q_i0 q_i1)."""
+        s = self._nl(s)
+        out = np.zeros_like(s)
+        if _load().orc_prox_step_adaptive(self._h, float(d), _ptr(s), _ptr(out)) != 0:
+            raise ValueError("the adaptive step is defined for binary models only")
+        return out
+
+    def parallel_prox_adaptive(self, d: float, iters: int, s=None, trace: bool = True):
+        """(s after iters adaptive steps, F(q^t) for t = 0..iters)."""
+        s = self.init_logq() if s is None else self._nl(s).copy()
+        F = np.zeros(iters + 1) if trace else None
+        if _load().orc_parallel_prox_adaptive(self._h, float(d), int(iters), _ptr(s),
+                                              _ptr(F) if trace else None) != 0:
+            raise ValueError("the adaptive step is defined for binary models only")
         return s, F
 
     def sweep(self, sweeps: int, s=None) -> np.ndarray:

@@ -448,6 +448,52 @@ void orc_parallel_prox(const orc_model *m, double eta, int32_t iters, double *s,
     free(t);
 }
 
+/* Adaptive step for binary models (Sec. 3.3, Eq. hessian): the proximal
+ * weights are d_{i,0} = d_{i,1} = d q_{i,0} q_{i,1}, taken from q^t, and
+ * the update is Eq. method:update_mean with eta_i = 1/(1 + d_{i,l}).
+ * Returns -1 (nothing written) unless L == 2. */
+int32_t orc_prox_step_adaptive(const orc_model *m, double d, const double *s_in, double *s_out)
+{
+    if (m->L != 2) return -1;
+    const int64_t nl = m->n * 2;
+    double *q = (double *)malloc(sizeof(double) * (size_t)nl);
+    double *g = (double *)malloc(sizeof(double) * (size_t)nl);
+    for (int64_t k = 0; k < nl; ++k) q[k] = exp(s_in[k]);
+    orc_grad(m, q, g);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m->n; ++i) {
+        const double di = d * q[2 * i] * q[2 * i + 1];
+        const double eta = 1.0 / (1.0 + di);
+        double a[2];
+        for (int l = 0; l < 2; ++l) a[l] = -eta * g[2 * i + l] + (1.0 - eta) * s_in[2 * i + l];
+        log_softmax(a, s_out + 2 * i, 2);
+    }
+    free(q);
+    free(g);
+    return 0;
+}
+
+/* iters adaptive steps on s (in place); F_trace as in orc_parallel_prox. */
+int32_t orc_parallel_prox_adaptive(const orc_model *m, double d, int32_t iters, double *s, double *F_trace)
+{
+    if (m->L != 2) return -1;
+    const int64_t nl = m->n * 2;
+    double *q = (double *)malloc(sizeof(double) * (size_t)nl);
+    double *t = (double *)malloc(sizeof(double) * (size_t)nl);
+    for (int32_t it = 0; it <= iters; ++it) {
+        if (F_trace) {
+            for (int64_t k = 0; k < nl; ++k) q[k] = exp(s[k]);
+            F_trace[it] = orc_free_energy(m, q);
+        }
+        if (it == iters) break;
+        orc_prox_step_adaptive(m, d, s, t);
+        memcpy(s, t, sizeof(double) * (size_t)nl);
+    }
+    free(q);
+    free(t);
+    return 0;
+}
+
 /* SWEEP coordinate descent (Sec. 2.2.1, Eq. related:sweep-update): variables
  * in index (raster) order, each set to softmax(-grad E) computed from the
  * current values of all the others.  One call = sweeps full passes. */

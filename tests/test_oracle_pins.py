@@ -389,3 +389,68 @@ def test_unrolled_gradient_matches_finite_differences(oracle_mod, conn, sym):
             ew2 = ew.copy(); ew2[e] += dh
             return oracle_mod.Model.sparse(U, mu, ei, ej, ew2)
         assert abs(fd(mk) - dw[e]) <= 1e-7 * abs(dw[e]) + 1e-9
+
+
+# ---------------------------------------------------------------- P8 ----
+# Adaptive binary step (Sec. 3.3, Eq. hessian): the proximal weights are
+# d_i = d q_i0 q_i1, taken from q^t.
+
+def _golden_min(f, lo, hi, tol=1e-14):
+    """Minimiser of a strictly convex f on [lo, hi] by golden-section search."""
+    r = (math.sqrt(5.0) - 1.0) / 2.0
+    a, b = lo, hi
+    c, e = b - r * (b - a), a + r * (b - a)
+    fc, fe = f(c), f(e)
+    while b - a > tol:
+        if fc < fe:
+            b, e, fe = e, c, fc
+            c = b - r * (b - a)
+            fc = f(c)
+        else:
+            a, c, fc = c, e, fe
+            e = a + r * (b - a)
+            fe = f(e)
+    return 0.5 * (a + b)
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_adaptive_step_is_the_proximal_argmin(oracle_mod, conn):
+    """Each variable's adaptive update equals the minimiser over the simplex
+    of <q_i, grad E(q^t)_i> - H(q_i) + d_i KL(q_i || q_i^t) (Eq.
+    method:proxUpdateOurs with D^t of Eq. hessian), found by brute-force
+    golden-section search on p = q_i0."""
+    m, d = small_grid(oracle_mod, 5, 6, 2, conn, seed=41, symmetric=False, scale=1.5)
+    n = 30
+    s0 = synth.random_logq(n, 2, seed=42).astype(np.float64)
+    q0 = np.exp(s0)
+    dd = 3.7
+    s1 = m.prox_step_adaptive(dd, s0)
+    g = m.grad(q0)
+    for i in range(n):
+        di = dd * q0[i, 0] * q0[i, 1]
+
+        def f(p):
+            qa, qb = p, 1.0 - p
+            return (qa * g[i, 0] + qb * g[i, 1] + qa * math.log(qa) + qb * math.log(qb)
+                    + di * (qa * math.log(qa / q0[i, 0]) + qb * math.log(qb / q0[i, 1])))
+
+        p = _golden_min(f, 1e-15, 1.0 - 1e-15)
+        assert abs(math.exp(s1[i, 0]) - p) <= 1e-7
+
+
+def test_adaptive_rejects_multilabel(oracle_mod):
+    m, _ = small_grid(oracle_mod, 3, 3, 3, 4, seed=43)
+    with pytest.raises(ValueError):
+        m.prox_step_adaptive(2.0, m.init_logq())
+
+
+def test_adaptive_fixed_point_is_sweep_stationary(oracle_mod):
+    """Converged adaptive iterates are mean-field stationary points: one SWEEP
+    pass leaves them unchanged."""
+    d = synth.binary_denoising(H=20, W=20, coupling=0.8, seed=5)
+    m = oracle_mod.Model.grid(_f64(d, "U"), _f64(d, "mu"), _f64(d, "w"), 20, 20, 4)
+    lam = 0.8 * H.grid4_lambda_max(20, 20)
+    s, F = m.parallel_prox_adaptive(lam, 1500)
+    s2 = m.sweep(1, s)
+    assert np.max(np.abs(np.exp(s2) - np.exp(s))) <= 1e-10
+    assert np.all(np.isfinite(F))
