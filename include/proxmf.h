@@ -125,9 +125,20 @@ typedef struct {
     int32_t final_free_energy; /* 1: also evaluate F(q^K) on the device at the */
                             /* end (mf_free_energy then returns it without a    */
                             /* recomputation); no host synchronisation          */
+    int32_t rule;           /* MF_RULE_FIXED (0): one eta for all variables     */
+                            /* (Eq. fixedStepSize); MF_RULE_ADAPTIVE (1):        */
+                            /* binary grids only, per-variable                   */
+                            /* eta_i = 1/(1 + d q_i0 q_i1) from q^t (Sec. 3.3,   */
+                            /* Eq. hessian); eta is then ignored                 */
+    double d;               /* MF_RULE_ADAPTIVE: d > 0 as given; d <= 0: the     */
+                            /* step-size constant max(Lambda, 0)                 */
 } mf_params;
 
+enum { MF_RULE_FIXED = 0, MF_RULE_ADAPTIVE = 1 };
+
 /* mf_iterate -- run the parallel proximal iteration of Eq. method:update_natural.
+ * rule = MF_RULE_ADAPTIVE on a model that is not a binary grid returns
+ * CRF_E_UNSUPPORTED.
  * Each step computes grad E(q^t) (expected pairwise energy plus unaries),
  * takes the log-domain proximal step, renormalises every variable, and
  * records F(q^t).  iters_done (host, [batch], may be NULL) receives the
@@ -283,7 +294,8 @@ crf_status mf_server_destroy(mf_server_t s);
  * U [N][L], mu [L][L], w [n_dirs][H][W]: host arrays, copied now.  q_out:
  * host [N][L] receiving the marginals when the request finishes (may be
  * NULL), must stay valid until then.  *ticket identifies the request.
- * CRF_E_OOM if the request alone exceeds the pool. */
+ * CRF_E_OOM if the request alone exceeds the pool; CRF_E_UNSUPPORTED for a
+ * rule other than MF_RULE_FIXED. */
 crf_status mf_server_submit(mf_server_t s, const crf_desc *d, const float *U, const float *mu, const float *w,
                             const mf_params *p, float *q_out, uint64_t *ticket);
 

@@ -38,6 +38,8 @@ struct crf_s {
     bool bf16 = false;           // tensor-core form
     DenseTcBuffers tcb{nullptr, nullptr};
     float *eta_fixed = nullptr;  // [B]
+    float *adapt_d = nullptr;    // [B] d of the adaptive binary step
+    bool adapt_active = false;   // set while mf_iterate runs the adaptive rule
     float *eta_auto = nullptr;   // [B]
     double *Lambda = nullptr;    // [B]
     double *partial = nullptr;   // [B][nblk] free-energy partials
@@ -62,7 +64,7 @@ struct crf_s {
     bool fcur_valid = false;
     // CUDA graphs of the mf_iterate launch sequence, one per configuration
     struct GraphEntry {
-        int iters, refine, cur;
+        int iters, refine, cur, rule;
         double rel_tol;
         const float *eta;
         cudaGraphExec_t exec;
@@ -106,7 +108,7 @@ size_t n_rows(const crf_t h) { return n_pix(h) * h->L; }
 size_t n_padded(const crf_t h) { return n_pix(h) * h->LP; }
 
 void free_all(crf_t h) {
-    float *fs[] = {h->U, h->s[0], h->s[1], h->w, h->eta_fixed, h->eta_auto, h->staging};
+    float *fs[] = {h->U, h->s[0], h->s[1], h->w, h->eta_fixed, h->eta_auto, h->staging, h->adapt_d};
     for (float *p : fs)
         if (p) cudaFree(p);
     double *ds[] = {h->Lambda, h->partial, h->ftrace, h->fcur};
@@ -171,6 +173,7 @@ GridStepLaunch step_args(crf_t h, const float *eta, int t, int update, double re
     a.mu_out = h->mu_pairs;
     a.mu_in = h->mu_pairs + (size_t)h->LT * mu_pair_slots(h->LT);
     a.mu_tc = reinterpret_cast<const uint4 *>(h->mu_tc);
+    a.adapt_d = h->adapt_active ? h->adapt_d : nullptr;
     a.partial = h->partial;
     a.counter = h->counter;
     a.f_trace = h->ftrace;
@@ -454,6 +457,7 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
         if (ok) ok = cudaMemsetAsync(h->mu_tc, 0, kTcImageBytes, h->st) == cudaSuccess;
     }
     ok = ok && dalloc(&h->eta_fixed, h->B) == cudaSuccess;
+    ok = ok && dalloc(&h->adapt_d, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->eta_auto, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->Lambda, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->partial, (size_t)h->B * h->nblk) == cudaSuccess;
@@ -645,8 +649,23 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
     if (!p || p->max_iters < 0 || p->rel_tol < 0 || !std::isfinite(p->eta) || p->eta > 1.0)
         return CRF_E_INVALID;
     if (!h->has_unary || !h->has_pairwise) return CRF_E_INVALID;
+    if (p->rule != MF_RULE_FIXED && p->rule != MF_RULE_ADAPTIVE) return CRF_E_INVALID;
+    if (p->rule == MF_RULE_ADAPTIVE) {
+        if (h->dense || h->L != 2) return CRF_E_UNSUPPORTED;
+        if (!std::isfinite(p->d)) return CRF_E_INVALID;
+        if (p->d > 0) {
+            CK(h, launch_fill_eta(h->adapt_d, h->B, p->d, h->st));
+        } else {
+            const crf_status lr = ensure_lambda(h);
+            if (lr != CRF_OK) return lr;
+            CK(h, launch_lambda_to_d(h->Lambda, h->adapt_d, h->B, h->st));
+        }
+        h->launches++;
+    }
     const float *eta = nullptr;
-    if (p->eta > 0) {
+    if (p->rule == MF_RULE_ADAPTIVE) {
+        eta = h->eta_fixed;   // unused by the adaptive epilogue
+    } else if (p->eta > 0) {
         CK(h, launch_fill_eta(h->eta_fixed, h->B, p->eta, h->st));
         h->launches++;
         eta = h->eta_fixed;
@@ -678,11 +697,12 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
         }
         return cudaSuccess;
     };
+    h->adapt_active = p->rule == MF_RULE_ADAPTIVE;
     cudaGraphExec_t exec = nullptr;
     if (h->use_graphs && nsteps > 0) {
         for (auto &g : h->graphs)
             if (g.iters == p->max_iters && g.refine == refine && g.cur == h->cur && g.rel_tol == p->rel_tol &&
-                g.eta == eta)
+                g.eta == eta && g.rule == p->rule)
                 exec = g.exec;
         if (!exec) {
             const int cur0 = h->cur;
@@ -697,21 +717,26 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
             h->st = st0;
             h->cur = cur0;   // nothing ran yet
             if (e != cudaSuccess || e2 != cudaSuccess) {
+                h->adapt_active = false;
                 if (graph) cudaGraphDestroy(graph);
                 return fail_cuda(h, e != cudaSuccess ? e : e2);
             }
             const cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
             cudaGraphDestroy(graph);
+            if (e3 != cudaSuccess) h->adapt_active = false;
             CK(h, e3);
-            h->graphs.push_back({p->max_iters, refine, cur0, p->rel_tol, eta, exec});
+            h->graphs.push_back({p->max_iters, refine, cur0, p->rule, p->rel_tol, eta, exec});
         }
     }
     if (h->profile) CK(h, cudaEventRecord(h->ev0, h->st));
     if (exec) {
+        h->adapt_active = false;
         CK(h, cudaGraphLaunch(exec, h->st));
         h->cur ^= nsteps & 1;
     } else {
-        CK(h, body());
+        const cudaError_t e = body();
+        h->adapt_active = false;
+        CK(h, e);
     }
     h->launches += nsteps;
     if (h->profile) {

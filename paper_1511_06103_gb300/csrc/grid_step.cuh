@@ -45,6 +45,7 @@
 namespace proxmf {
 
 struct GridStepArgs {
+    const float *adapt_d;    // [B] adaptive binary step (null: fixed eta)
     const uint4 *mu_tc;      // tensor-core form: BF16 images of mu (and mu^T), see tc_k
     const float *s_in;
     float *s_out;
@@ -193,6 +194,8 @@ struct TileJob {
     const float2 *mu_out;
     const float2 *mu_in;
     float eta;
+    float adapt_d;           // adaptive binary step parameter d (when adaptive)
+    bool adaptive;
     int L, H, W;
     int update;
 };
@@ -429,7 +432,11 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, co
 #pragma unroll
     for (int j = 0; j < NP; ++j) qc[j] = splat2(0.f);
     acc_cell<NP>(qc, qt + ((ty + 1) * TW + tx + 1) * LS, 1.f);
-    const float eta = j.eta;
+    float eta = j.eta;
+    if constexpr (LT == 2) {
+        // adaptive binary step (Sec. 3.3, Eq. hessian): d_i = d q_i0 q_i1
+        if (j.adaptive) eta = 1.f / fmaf(j.adapt_d * qc[0].x, qc[0].y, 1.f);
+    }
     const float2 neta = splat2(-eta), ome = splat2(1.f - eta), half = splat2(0.5f);
     float2 f2 = splat2(0.f);
     float mx = -INFINITY;
@@ -544,6 +551,8 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
     j.mu_out = a.mu_out;
     j.mu_in = a.mu_in;
     j.eta = a.eta[b];
+    j.adaptive = a.adapt_d != nullptr;
+    j.adapt_d = j.adaptive ? a.adapt_d[b] : 0.f;
     j.L = a.L;
     j.H = a.H;
     j.W = a.W;
@@ -631,6 +640,7 @@ cudaError_t launch_grid_step_lt(const GridStepLaunch &l, cudaStream_t st) {
     a.update = l.update;
     a.rel_tol = l.rel_tol;
     a.mu_tc = l.mu_tc;
+    a.adapt_d = l.adapt_d;
     dim3 grid(nbx, nby, l.B), block(GX, GY, 1);
     if (l.tc) {
         if (l.conn == 8)

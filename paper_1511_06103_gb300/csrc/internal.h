@@ -57,6 +57,7 @@ struct GridStepLaunch {
     const float2 *mu_in;     // device [LT][NPP] row pairs
     const uint4 *mu_tc;      // tensor-core form: device BF16 operand images of mu, mu^T
     bool tc;                 // BF16 tensor-core messages (else FP32)
+    const float *adapt_d;    // [B] adaptive binary step: eta_i = 1/(1 + d q_i0 q_i1); null = fixed eta
     double *partial;         // [B][nblk] per-tile free-energy partials (scratch)
     unsigned int *counter;   // [B] tiles finished in this launch (scratch, self-resetting)
     double *f_trace;         // [B][trace_cap]
@@ -127,6 +128,8 @@ cudaError_t launch_weights_to_pixel_major(const float *src, float *dst, int B, i
 cudaError_t launch_init_logq(const float *U, float *s, long long rows, int L, int LP, cudaStream_t st);
 // eta[b] = value for all b.
 cudaError_t launch_fill_eta(float *eta, int B, double value, cudaStream_t st);
+// d[b] = max(Lambda[b], 0) (FP32)
+cudaError_t launch_lambda_to_d(const double *Lambda, float *d, int B, cudaStream_t st);
 
 // Fully connected Gaussian model (dense.cu, dense_tc.cu).
 struct DenseStepLaunch {

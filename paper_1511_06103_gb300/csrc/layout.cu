@@ -83,6 +83,11 @@ __global__ void init_logq_kernel(const float *__restrict__ U, float *__restrict_
     }
 }
 
+__global__ void lambda_to_d_kernel(const double *Lambda, float *d, int B) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < B) d[i] = (float)fmax(Lambda[i], 0.0);
+}
+
 __global__ void fill_eta_kernel(float *eta, int B, float v) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < B) eta[i] = v;
@@ -111,6 +116,11 @@ cudaError_t launch_weights_to_pixel_major(const float *src, float *dst, int B, i
 
 cudaError_t launch_init_logq(const float *U, float *s, long long rows, int L, int LP, cudaStream_t st) {
     init_logq_kernel<<<blocks_for((size_t)rows), kThreads, 0, st>>>(U, s, rows, L, LP);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lambda_to_d(const double *Lambda, float *d, int B, cudaStream_t st) {
+    lambda_to_d_kernel<<<(B + 127) / 128, 128, 0, st>>>(Lambda, d, B);
     return cudaGetLastError();
 }
 

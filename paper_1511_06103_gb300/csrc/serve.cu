@@ -444,6 +444,7 @@ crf_status mf_server_submit(mf_server_t s, const crf_desc *d, const float *U, co
     if (d->n_labels < 1 || d->n_labels > kMaxLabels || d->height < 1 || d->width < 1) return CRF_E_INVALID;
     if (d->height > 65535ll * GY || d->width > (1 << 20)) return CRF_E_INVALID;
     if (p->max_iters < 0 || p->rel_tol < 0 || !(p->eta <= 1.0)) return CRF_E_INVALID;
+    if (p->rule != MF_RULE_FIXED) return CRF_E_UNSUPPORTED;   // the server runs the fixed-step rule
     Request r;
     r.ticket = s->next_ticket++;
     r.H = (int)d->height;

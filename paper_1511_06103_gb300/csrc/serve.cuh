@@ -77,6 +77,8 @@ serve_step_kernel(ServeSlot *slots, const ServeBucket *bucket, ServeResult *resu
         j.mu_out = sl.mu_out;
         j.mu_in = sl.mu_in;
         j.eta = *sl.eta;
+        j.adaptive = false;
+        j.adapt_d = 0.f;
         j.L = sl.L;
         j.H = sl.H;
         j.W = sl.W;
