@@ -46,7 +46,7 @@ WORKLOAD = ("segmentation-shaped grid CRF 512x512, L=21, 8-connected, 100 parall
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -107,7 +107,11 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={CLOCK_QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "-lms", "25", "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+            # start timing only once the sampler is producing lines
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.01)
         except Exception:  # noqa: BLE001 - clocks are best effort
             self.proc = None
         return self
