@@ -494,6 +494,88 @@ int32_t orc_parallel_prox_adaptive(const orc_model *m, double d, int32_t iters, 
     return 0;
 }
 
+/* OURS-MOMENTUM (Sec. 3.4, Eq. momentumUpdate): the gradient of Eq.
+ * method:update_natural is replaced by its exponentially weighted average
+ *   m^{t+1} = gamma1 m^t + (1 - gamma1) grad E(q^t),
+ *   theta^{t+1} = eta m^{t+1} + (1 - eta) theta^t,
+ * using the freshly formed m^{t+1}; the average starts from the first
+ * gradient (m^1 = grad E(q^0)).  iters steps on s in place; F_trace as in
+ * orc_parallel_prox. */
+void orc_parallel_prox_momentum(const orc_model *m, double eta, double gamma1, int32_t iters, double *s,
+                                double *F_trace)
+{
+    const int L = m->L;
+    const int64_t nl = m->n * L;
+    double *q = (double *)malloc(sizeof(double) * (size_t)nl);
+    double *g = (double *)malloc(sizeof(double) * (size_t)nl);
+    double *mom = (double *)malloc(sizeof(double) * (size_t)nl);
+    double *a = (double *)malloc(sizeof(double) * (size_t)L);
+    for (int32_t it = 0; it <= iters; ++it) {
+        for (int64_t k = 0; k < nl; ++k) q[k] = exp(s[k]);
+        if (F_trace) F_trace[it] = orc_free_energy(m, q);
+        if (it == iters) break;
+        orc_grad(m, q, g);
+        for (int64_t k = 0; k < nl; ++k) mom[k] = it == 0 ? g[k] : gamma1 * mom[k] + (1.0 - gamma1) * g[k];
+        for (int64_t i = 0; i < m->n; ++i) {
+            for (int l = 0; l < L; ++l) a[l] = -eta * mom[i * L + l] + (1.0 - eta) * s[i * L + l];
+            log_softmax(a, s + i * L, L);
+        }
+    }
+    free(q);
+    free(g);
+    free(mom);
+    free(a);
+}
+
+/* OURS-ADAM (Sec. 3.5, Eq. adamStepSize) with the momentum average above and
+ * a per-(variable, label) proximal weight from the second moment of the
+ * natural gradient.  Readings: the natural gradient is grad E + log q
+ * centred over each variable's labels (zero exactly at a mean-field fixed
+ * point, where log q = -grad E + const); v starts at 1 (the paper asks for a
+ * strictly positive start) and is averaged as
+ *   v^{t+1} = gamma2 v^t + (1 - gamma2) r^2;
+ * d_{i,l} = sqrt(v^{t+1}) d0 + eps - 1, floored at 0 so that eta <= 1;
+ * eta_{i,l} = 1/(1 + d_{i,l}) in Eq. method:update_natural with m^{t+1}. */
+void orc_parallel_prox_adam(const orc_model *m, double d0, double gamma1, double gamma2, double eps,
+                            int32_t iters, double *s, double *F_trace)
+{
+    const int L = m->L;
+    const int64_t nl = m->n * L;
+    double *q = (double *)malloc(sizeof(double) * (size_t)nl);
+    double *g = (double *)malloc(sizeof(double) * (size_t)nl);
+    double *mom = (double *)malloc(sizeof(double) * (size_t)nl);
+    double *v = (double *)malloc(sizeof(double) * (size_t)nl);
+    double *a = (double *)malloc(sizeof(double) * (size_t)L);
+    for (int64_t k = 0; k < nl; ++k) v[k] = 1.0;
+    for (int32_t it = 0; it <= iters; ++it) {
+        for (int64_t k = 0; k < nl; ++k) q[k] = exp(s[k]);
+        if (F_trace) F_trace[it] = orc_free_energy(m, q);
+        if (it == iters) break;
+        orc_grad(m, q, g);
+        for (int64_t i = 0; i < m->n; ++i) {
+            double mean = 0.0;
+            for (int l = 0; l < L; ++l) mean += g[i * L + l] + s[i * L + l];
+            mean /= L;
+            for (int l = 0; l < L; ++l) {
+                const int64_t k = i * L + l;
+                const double r = g[k] + s[k] - mean;
+                mom[k] = it == 0 ? g[k] : gamma1 * mom[k] + (1.0 - gamma1) * g[k];
+                v[k] = gamma2 * v[k] + (1.0 - gamma2) * r * r;
+                double dk = sqrt(v[k]) * d0 + eps - 1.0;
+                if (dk < 0.0) dk = 0.0;
+                const double eta = 1.0 / (1.0 + dk);
+                a[l] = -eta * mom[k] + (1.0 - eta) * s[k];
+            }
+            log_softmax(a, s + i * L, L);
+        }
+    }
+    free(q);
+    free(g);
+    free(mom);
+    free(v);
+    free(a);
+}
+
 /* SWEEP coordinate descent (Sec. 2.2.1, Eq. related:sweep-update): variables
  * in index (raster) order, each set to softmax(-grad E) computed from the
  * current values of all the others.  One call = sweeps full passes. */

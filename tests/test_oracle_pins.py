@@ -454,3 +454,55 @@ def test_adaptive_fixed_point_is_sweep_stationary(oracle_mod):
     s2 = m.sweep(1, s)
     assert np.max(np.abs(np.exp(s2) - np.exp(s))) <= 1e-10
     assert np.all(np.isfinite(F))
+
+
+# ---------------------------------------------------------------- P9 ----
+# OURS-MOMENTUM and OURS-ADAM (Sec. 3.4-3.5).
+
+def test_momentum_without_memory_is_the_fixed_step(oracle_mod):
+    """gamma1 = 0 turns the average into the current gradient: the iterates
+    are exactly those of the fixed step."""
+    m, _ = small_grid(oracle_mod, 6, 5, 3, 8, seed=51, symmetric=False, scale=1.5)
+    s1, F1 = m.parallel_prox_momentum(0.3, 0.0, 25)
+    s2, F2 = m.parallel_prox(0.3, 25)
+    assert np.array_equal(s1, s2) and np.array_equal(F1, F2)
+
+
+def test_momentum_on_a_decoupled_model(oracle_mod):
+    """Without edges the gradient is U at every step, so the average stays U
+    and the trajectory is the fixed step's closed form."""
+    d = synth.random_grid(4, 5, 3, 4, seed=52)
+    m = oracle_mod.Model.grid(_f64(d, "U"), _f64(d, "mu"), 0.0 * _f64(d, "w"), 4, 5, 4)
+    eta, T = 0.35, 12
+    s, _ = m.parallel_prox_momentum(eta, 0.95, T)
+    s0 = m.init_logq()
+    a = (1 - eta) ** T * s0 + (1 - (1 - eta) ** T) * (-_f64(d, "U"))
+    ref = a - np.log(np.exp(a).sum(axis=1, keepdims=True))
+    assert np.max(np.abs(s - ref)) <= 1e-12
+
+
+def test_adam_special_cases(oracle_mod):
+    """d0 = 0 floors d at 0 (eta = 1, FULL-PARALLEL); gamma2 = 1 keeps v at
+    its start 1, so d = d0 + eps - 1 and eta = 1/(d0 + eps): with gamma1 = 0
+    both are fixed steps."""
+    m, _ = small_grid(oracle_mod, 5, 6, 3, 4, seed=53, symmetric=True, scale=0.7)
+    s1, _ = m.parallel_prox_adam(0.0, 0.0, 0.999, 1e-8, 15)
+    s2, _ = m.parallel_prox(1.0, 15)
+    assert np.max(np.abs(s1 - s2)) <= 1e-12
+    d0 = 4.2
+    s1, _ = m.parallel_prox_adam(d0, 0.0, 1.0, 1e-8, 15)
+    s2, _ = m.parallel_prox(1.0 / (d0 + 1e-8), 15)
+    assert np.max(np.abs(s1 - s2)) <= 1e-12
+
+
+@pytest.mark.parametrize("rule", ["momentum", "adam"])
+def test_momentum_and_adam_fixed_points_are_sweep_stationary(oracle_mod, rule):
+    d = synth.binary_denoising(H=16, W=16, coupling=0.4, seed=7)
+    m = oracle_mod.Model.grid(_f64(d, "U"), _f64(d, "mu"), _f64(d, "w"), 16, 16, 4)
+    lam = 0.4 * H.grid4_lambda_max(16, 16)
+    if rule == "momentum":
+        s, F = m.parallel_prox_momentum(1 / (1 + lam), 0.95, 3000)
+    else:
+        s, F = m.parallel_prox_adam(1 + lam, 0.99, 0.999, 1e-8, 6000)   # gamma1 = 0.99 settles slowly
+    s2 = m.sweep(1, s)
+    assert np.max(np.abs(np.exp(s2) - np.exp(s))) <= 1e-9
