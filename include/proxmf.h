@@ -129,16 +129,30 @@ typedef struct {
                             /* (Eq. fixedStepSize); MF_RULE_ADAPTIVE (1):        */
                             /* binary grids only, per-variable                   */
                             /* eta_i = 1/(1 + d q_i0 q_i1) from q^t (Sec. 3.3,   */
-                            /* Eq. hessian); eta is then ignored                 */
-    double d;               /* MF_RULE_ADAPTIVE: d > 0 as given; d <= 0: the     */
-                            /* step-size constant max(Lambda, 0)                 */
+                            /* Eq. hessian), eta ignored; MF_RULE_MOMENTUM (2):  */
+                            /* the gradient replaced by its running average      */
+                            /* m' = gamma1 m + (1-gamma1) grad E, started at the */
+                            /* first gradient (Sec. 3.4, Eq. momentumUpdate);    */
+                            /* MF_RULE_ADAM (3): momentum plus a per-label eta   */
+                            /* = 1/(1 + max(sqrt(v') d + epsilon - 1, 0)) from   */
+                            /* v' = gamma2 v + (1-gamma2) r^2, r the natural     */
+                            /* gradient grad E + log q centred over labels, v    */
+                            /* starting at 1 (Sec. 3.5, Eq. adamStepSize), eta   */
+                            /* ignored.  Rules 2 and 3: FP32 grids only; each    */
+                            /* mf_iterate call starts a new run (no history).    */
+    double d;               /* MF_RULE_ADAPTIVE, MF_RULE_ADAM: d > 0 as given;   */
+                            /* d <= 0: the step-size constant max(Lambda, 0)     */
+    double gamma1;          /* MF_RULE_MOMENTUM, MF_RULE_ADAM: in [0, 1]         */
+    double gamma2;          /* MF_RULE_ADAM: in [0, 1]                           */
+    double epsilon;         /* MF_RULE_ADAM: >= 0                                */
 } mf_params;
 
-enum { MF_RULE_FIXED = 0, MF_RULE_ADAPTIVE = 1 };
+enum { MF_RULE_FIXED = 0, MF_RULE_ADAPTIVE = 1, MF_RULE_MOMENTUM = 2, MF_RULE_ADAM = 3 };
 
 /* mf_iterate -- run the parallel proximal iteration of Eq. method:update_natural.
- * rule = MF_RULE_ADAPTIVE on a model that is not a binary grid returns
- * CRF_E_UNSUPPORTED.
+ * rule = MF_RULE_ADAPTIVE on a model that is not a binary grid, and rules
+ * MF_RULE_MOMENTUM / MF_RULE_ADAM on a fully connected or BF16 handle,
+ * return CRF_E_UNSUPPORTED.
  * Each step computes grad E(q^t) (expected pairwise energy plus unaries),
  * takes the log-domain proximal step, renormalises every variable, and
  * records F(q^t).  iters_done (host, [batch], may be NULL) receives the

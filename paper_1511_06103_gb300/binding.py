@@ -45,13 +45,14 @@ class crf_desc(C.Structure):
                 ("stream", C.c_void_p)]
 
 
-MF_RULE_FIXED, MF_RULE_ADAPTIVE = 0, 1
+MF_RULE_FIXED, MF_RULE_ADAPTIVE, MF_RULE_MOMENTUM, MF_RULE_ADAM = 0, 1, 2, 3
 
 
 class mf_params(C.Structure):
     _fields_ = [("eta", C.c_double), ("max_iters", C.c_int32), ("reset", C.c_int32),
                 ("rel_tol", C.c_double), ("refine_fp32", C.c_int32),
-                ("final_free_energy", C.c_int32), ("rule", C.c_int32), ("d", C.c_double)]
+                ("final_free_energy", C.c_int32), ("rule", C.c_int32), ("d", C.c_double),
+                ("gamma1", C.c_double), ("gamma2", C.c_double), ("epsilon", C.c_double)]
 
 
 _lock = threading.Lock()
@@ -286,9 +287,11 @@ class CRF:
 
     def iterate(self, max_iters: int, eta: float = 0.0, reset: bool = False, rel_tol: float = 0.0,
                 refine_fp32: int = 0, want_iters: bool = False, final_free_energy: bool = False,
-                rule: int = MF_RULE_FIXED, d: float = 0.0):
+                rule: int = MF_RULE_FIXED, d: float = 0.0, gamma1: float = 0.95, gamma2: float = 0.999,
+                epsilon: float = 1e-8):
         prm = mf_params(float(eta), int(max_iters), int(bool(reset)), float(rel_tol), int(refine_fp32),
-                        int(bool(final_free_energy)), int(rule), float(d))
+                        int(bool(final_free_energy)), int(rule), float(d), float(gamma1), float(gamma2),
+                        float(epsilon))
         if want_iters:
             out = np.zeros(self.B, np.int32)
             mf_iterate(self.h, prm, out.ctypes.data)
@@ -406,7 +409,7 @@ class Server:
         L = mu.shape[0]
         topo = CRF_GRID8 if conn == 8 else CRF_GRID4
         d = crf_desc(topo, L, 1, CRF_FP32, H, W, None)
-        prm = mf_params(float(eta), int(max_iters), 1, float(rel_tol), 0, 0, MF_RULE_FIXED, 0.0)
+        prm = mf_params(float(eta), int(max_iters), 1, float(rel_tol), 0, 0, MF_RULE_FIXED, 0.0, 0.0, 0.0, 0.0)
         U = np.ascontiguousarray(U, np.float32)
         mu = np.ascontiguousarray(mu, np.float32)
         w = np.ascontiguousarray(w, np.float32)

@@ -38,8 +38,11 @@ struct crf_s {
     bool bf16 = false;           // tensor-core form
     DenseTcBuffers tcb{nullptr, nullptr};
     float *eta_fixed = nullptr;  // [B]
-    float *adapt_d = nullptr;    // [B] d of the adaptive binary step
+    float *adapt_d = nullptr;    // [B] d of the adaptive binary step (or d0 of Adam)
     bool adapt_active = false;   // set while mf_iterate runs the adaptive rule
+    float *mom = nullptr, *vv = nullptr;   // [B][N][LP] momentum / Adam state (allocated on first use)
+    int rule_kernel = 0;         // 1 momentum, 2 Adam while mf_iterate runs them
+    float gamma1 = 0.f, gamma2 = 0.f, eps = 0.f;
     float *eta_auto = nullptr;   // [B]
     double *Lambda = nullptr;    // [B]
     double *partial = nullptr;   // [B][nblk] free-energy partials
@@ -65,7 +68,7 @@ struct crf_s {
     // CUDA graphs of the mf_iterate launch sequence, one per configuration
     struct GraphEntry {
         int iters, refine, cur, rule;
-        double rel_tol;
+        double rel_tol, gamma1, gamma2, eps;
         const float *eta;
         cudaGraphExec_t exec;
     };
@@ -108,7 +111,7 @@ size_t n_rows(const crf_t h) { return n_pix(h) * h->L; }
 size_t n_padded(const crf_t h) { return n_pix(h) * h->LP; }
 
 void free_all(crf_t h) {
-    float *fs[] = {h->U, h->s[0], h->s[1], h->w, h->eta_fixed, h->eta_auto, h->staging, h->adapt_d};
+    float *fs[] = {h->U, h->s[0], h->s[1], h->w, h->eta_fixed, h->eta_auto, h->staging, h->adapt_d, h->mom, h->vv};
     for (float *p : fs)
         if (p) cudaFree(p);
     double *ds[] = {h->Lambda, h->partial, h->ftrace, h->fcur};
@@ -173,7 +176,14 @@ GridStepLaunch step_args(crf_t h, const float *eta, int t, int update, double re
     a.mu_out = h->mu_pairs;
     a.mu_in = h->mu_pairs + (size_t)h->LT * mu_pair_slots(h->LT);
     a.mu_tc = reinterpret_cast<const uint4 *>(h->mu_tc);
-    a.adapt_d = h->adapt_active ? h->adapt_d : nullptr;
+    a.adapt_d = (h->adapt_active || (update && h->rule_kernel == 2)) ? h->adapt_d : nullptr;
+    a.rule = update ? h->rule_kernel : 0;
+    a.mom = h->mom;
+    a.vv = h->vv;
+    a.gamma1 = h->gamma1;
+    a.gamma2 = h->gamma2;
+    a.eps = h->eps;
+    a.rule_first = t == 0;
     a.partial = h->partial;
     a.counter = h->counter;
     a.f_trace = h->ftrace;
@@ -649,7 +659,31 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
     if (!p || p->max_iters < 0 || p->rel_tol < 0 || !std::isfinite(p->eta) || p->eta > 1.0)
         return CRF_E_INVALID;
     if (!h->has_unary || !h->has_pairwise) return CRF_E_INVALID;
-    if (p->rule != MF_RULE_FIXED && p->rule != MF_RULE_ADAPTIVE) return CRF_E_INVALID;
+    if (p->rule < MF_RULE_FIXED || p->rule > MF_RULE_ADAM) return CRF_E_INVALID;
+    if (p->rule == MF_RULE_MOMENTUM || p->rule == MF_RULE_ADAM) {
+        if (h->dense || h->bf16) return CRF_E_UNSUPPORTED;
+        if (!(p->gamma1 >= 0 && p->gamma1 <= 1)) return CRF_E_INVALID;
+        if (p->rule == MF_RULE_ADAM &&
+            (!(p->gamma2 >= 0 && p->gamma2 <= 1) || !(p->epsilon >= 0) || !std::isfinite(p->epsilon) ||
+             !std::isfinite(p->d)))
+            return CRF_E_INVALID;
+        if (!h->mom) {
+            if (dalloc(&h->mom, n_padded(h)) != cudaSuccess || dalloc(&h->vv, n_padded(h)) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return CRF_E_OOM;
+            }
+        }
+        if (p->rule == MF_RULE_ADAM) {
+            if (p->d > 0) {
+                CK(h, launch_fill_eta(h->adapt_d, h->B, p->d, h->st));
+            } else {
+                const crf_status lr = ensure_lambda(h);
+                if (lr != CRF_OK) return lr;
+                CK(h, launch_lambda_to_d(h->Lambda, h->adapt_d, h->B, h->st));
+            }
+            h->launches++;
+        }
+    }
     if (p->rule == MF_RULE_ADAPTIVE) {
         if (h->dense || h->L != 2) return CRF_E_UNSUPPORTED;
         if (!std::isfinite(p->d)) return CRF_E_INVALID;
@@ -663,8 +697,8 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
         h->launches++;
     }
     const float *eta = nullptr;
-    if (p->rule == MF_RULE_ADAPTIVE) {
-        eta = h->eta_fixed;   // unused by the adaptive epilogue
+    if (p->rule == MF_RULE_ADAPTIVE || p->rule == MF_RULE_ADAM) {
+        eta = h->eta_fixed;   // unused by these epilogues
     } else if (p->eta > 0) {
         CK(h, launch_fill_eta(h->eta_fixed, h->B, p->eta, h->st));
         h->launches++;
@@ -698,11 +732,16 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
         return cudaSuccess;
     };
     h->adapt_active = p->rule == MF_RULE_ADAPTIVE;
+    h->rule_kernel = p->rule == MF_RULE_MOMENTUM ? 1 : (p->rule == MF_RULE_ADAM ? 2 : 0);
+    h->gamma1 = (float)p->gamma1;
+    h->gamma2 = (float)p->gamma2;
+    h->eps = (float)p->epsilon;
     cudaGraphExec_t exec = nullptr;
     if (h->use_graphs && nsteps > 0) {
         for (auto &g : h->graphs)
             if (g.iters == p->max_iters && g.refine == refine && g.cur == h->cur && g.rel_tol == p->rel_tol &&
-                g.eta == eta && g.rule == p->rule)
+                g.eta == eta && g.rule == p->rule && g.gamma1 == p->gamma1 && g.gamma2 == p->gamma2 &&
+                g.eps == p->epsilon)
                 exec = g.exec;
         if (!exec) {
             const int cur0 = h->cur;
@@ -718,24 +757,31 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
             h->cur = cur0;   // nothing ran yet
             if (e != cudaSuccess || e2 != cudaSuccess) {
                 h->adapt_active = false;
+                h->rule_kernel = 0;
                 if (graph) cudaGraphDestroy(graph);
                 return fail_cuda(h, e != cudaSuccess ? e : e2);
             }
             const cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
             cudaGraphDestroy(graph);
-            if (e3 != cudaSuccess) h->adapt_active = false;
+            if (e3 != cudaSuccess) {
+                h->adapt_active = false;
+                h->rule_kernel = 0;
+            }
             CK(h, e3);
-            h->graphs.push_back({p->max_iters, refine, cur0, p->rule, p->rel_tol, eta, exec});
+            h->graphs.push_back({p->max_iters, refine, cur0, p->rule, p->rel_tol, p->gamma1, p->gamma2, p->epsilon,
+                                 eta, exec});
         }
     }
     if (h->profile) CK(h, cudaEventRecord(h->ev0, h->st));
     if (exec) {
         h->adapt_active = false;
+        h->rule_kernel = 0;
         CK(h, cudaGraphLaunch(exec, h->st));
         h->cur ^= nsteps & 1;
     } else {
         const cudaError_t e = body();
         h->adapt_active = false;
+        h->rule_kernel = 0;
         CK(h, e);
     }
     h->launches += nsteps;

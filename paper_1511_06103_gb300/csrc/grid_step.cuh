@@ -45,7 +45,10 @@
 namespace proxmf {
 
 struct GridStepArgs {
-    const float *adapt_d;    // [B] adaptive binary step (null: fixed eta)
+    const float *adapt_d;    // [B] adaptive binary step (null: fixed eta); Adam: d0 per instance
+    float *mom, *vv;         // momentum / Adam state [B][N][LP]
+    float gamma1, gamma2, eps;
+    int rule_first;
     const uint4 *mu_tc;      // tensor-core form: BF16 images of mu (and mu^T), see tc_k
     const float *s_in;
     float *s_out;
@@ -196,6 +199,10 @@ struct TileJob {
     float eta;
     float adapt_d;           // adaptive binary step parameter d (when adaptive)
     bool adaptive;
+    // momentum / Adam state (RULE 1, 2): pixel-major like the log q
+    float *mom, *vv;
+    float gamma1, gamma2, eps, d0;
+    bool first;              // first step of a run: no history yet
     int L, H, W;
     int update;
 };
@@ -204,7 +211,7 @@ struct TileJob {
 // j.update), and the tile's free-energy partial, returned in thread 0.
 // All threads of the block must call it; it may be called repeatedly by a
 // persistent block (shared memory is reused).
-template <int LT, int CONN, bool SYM, bool TC = false>
+template <int LT, int CONN, bool SYM, bool TC = false, int RULE = 0>
 __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, const TcTile *tcx = nullptr) {
     constexpr int LP = storage_labels(LT);           // floats per pixel in HBM
     constexpr int NP = (LT + 1) / 2;                 // label pairs in the arithmetic
@@ -440,34 +447,100 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, co
     const float2 neta = splat2(-eta), ome = splat2(1.f - eta), half = splat2(0.5f);
     float2 f2 = splat2(0.f);
     float mx = -INFINITY;
+    if constexpr (RULE == 0) {
 #pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        const float2 g = add2(u[j], m[j]);
-        const float2 h = add2(fma2(half, m[j], u[j]), s[j]);
-        f2 = fma2(qc[j], h, f2);
-        float2 av = fma2(neta, g, mul2(ome, s[j]));
-        const int l0 = 2 * j, l1 = 2 * j + 1;
-        if ((MASK && l0 >= L)) av.x = -INFINITY;
-        if ((MASK && l1 >= L) || l1 >= LT) av.y = -INFINITY;
-        s[j] = av;
-        mx = fmaxf(mx, fmaxf(av.x, av.y));
+        for (int k = 0; k < NP; ++k) {
+            const float2 g = add2(u[k], m[k]);
+            const float2 h = add2(fma2(half, m[k], u[k]), s[k]);
+            f2 = fma2(qc[k], h, f2);
+            float2 av = fma2(neta, g, mul2(ome, s[k]));
+            const int l0 = 2 * k, l1 = 2 * k + 1;
+            if ((MASK && l0 >= L)) av.x = -INFINITY;
+            if ((MASK && l1 >= L) || l1 >= LT) av.y = -INFINITY;
+            s[k] = av;
+            mx = fmaxf(mx, fmaxf(av.x, av.y));
+        }
+    } else {
+        // OURS-MOMENTUM (RULE 1, Sec. 3.4): the gradient is replaced by its
+        // running average mo' = g1 mo + (1 - g1) g (mo' = g on the first step).
+        // OURS-ADAM (RULE 2, Sec. 3.5): in addition eta per label from the
+        // second moment v' = g2 v + (1 - g2) r^2 of the centred natural
+        // gradient r = g + log q - mean(g + log q) (v = 1 at the start):
+        // d = max(sqrt(v') d0 + eps - 1, 0), eta = 1/(1 + d).
+        float2 mo[LP / 2], vo[LP / 2];
+#pragma unroll
+        for (int k = 0; k < LP / 2; ++k) {
+            mo[k] = splat2(0.f);
+            vo[k] = splat2(1.f);
+        }
+        if (inside && !j.first) {
+            load_px<LP>(mo, j.mom + p * LP);
+            if (RULE == 2) load_px<LP>(vo, j.vv + p * LP);
+        }
+        float mean = 0.f;
+        if constexpr (RULE == 2) {
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const float2 t = add2(add2(u[k], m[k]), s[k]);
+                const int l0 = 2 * k, l1 = 2 * k + 1;
+                if (!(MASK && l0 >= L)) mean += t.x;
+                if (!((MASK && l1 >= L) || l1 >= LT)) mean += t.y;
+            }
+            mean /= (float)L;
+        }
+        const float2 g1 = splat2(j.gamma1), og1 = splat2(1.f - j.gamma1);
+        const float2 g2 = splat2(j.gamma2), og2 = splat2(1.f - j.gamma2);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const float2 g = add2(u[k], m[k]);
+            const float2 h = add2(fma2(half, m[k], u[k]), s[k]);
+            f2 = fma2(qc[k], h, f2);
+            const float2 mn = j.first ? g : fma2(g1, mo[k], mul2(og1, g));
+            const int l0 = 2 * k, l1 = 2 * k + 1;
+            const bool dead0 = (MASK && l0 >= L), dead1 = (MASK && l1 >= L) || l1 >= LT;
+            float2 av;
+            if constexpr (RULE == 1) {
+                av = fma2(neta, mn, mul2(ome, s[k]));
+            } else {
+                float2 r = add2(add2(g, s[k]), splat2(-mean));
+                if (dead0) r.x = 0.f;
+                if (dead1) r.y = 0.f;
+                const float2 vn = fma2(g2, vo[k], mul2(og2, mul2(r, r)));
+                const float d0 = fmaxf(fmaf(sqrtf(vn.x), j.d0, j.eps - 1.f), 0.f);
+                const float d1 = fmaxf(fmaf(sqrtf(vn.y), j.d0, j.eps - 1.f), 0.f);
+                const float e0 = 1.f / (1.f + d0), e1 = 1.f / (1.f + d1);
+                av = make_float2(fmaf(-e0, mn.x, (1.f - e0) * s[k].x), fmaf(-e1, mn.y, (1.f - e1) * s[k].y));
+                vo[k] = make_float2(dead0 ? 0.f : vn.x, dead1 ? 0.f : vn.y);
+            }
+            mo[k] = make_float2(dead0 ? 0.f : mn.x, dead1 ? 0.f : mn.y);
+            if (dead0) av.x = -INFINITY;
+            if (dead1) av.y = -INFINITY;
+            s[k] = av;
+            mx = fmaxf(mx, fmaxf(av.x, av.y));
+        }
+        if (j.update && inside) {
+#pragma unroll
+            for (int k = NP; k < LP / 2; ++k) mo[k] = vo[k] = splat2(0.f);
+            store_px<LP>(j.mom + p * LP, mo);
+            if (RULE == 2) store_px<LP>(j.vv + p * LP, vo);
+        }
     }
     // a4: renormalise
     float z = 0.f;
 #pragma unroll
-    for (int j = 0; j < NP; ++j) z += __expf(s[j].x - mx) + __expf(s[j].y - mx);
+    for (int k = 0; k < NP; ++k) z += __expf(s[k].x - mx) + __expf(s[k].y - mx);
     const float2 nlse = splat2(-(mx + __logf(z)));
     if (j.update && inside) {
         float2 o[LP / 2];
 #pragma unroll
-        for (int j = 0; j < LP / 2; ++j) {
-            if (j < NP) {
-                o[j] = add2(s[j], nlse);
-                const int l0 = 2 * j, l1 = 2 * j + 1;
-                if ((MASK && l0 >= L)) o[j].x = kPadLogQ;
-                if ((MASK && l1 >= L) || l1 >= LT) o[j].y = kPadLogQ;
+        for (int k = 0; k < LP / 2; ++k) {
+            if (k < NP) {
+                o[k] = add2(s[k], nlse);
+                const int l0 = 2 * k, l1 = 2 * k + 1;
+                if ((MASK && l0 >= L)) o[k].x = kPadLogQ;
+                if ((MASK && l1 >= L) || l1 >= LT) o[k].y = kPadLogQ;
             } else {
-                o[j] = splat2(kPadLogQ);
+                o[k] = splat2(kPadLogQ);
             }
         }
         store_px<LP>(j.s_out + p * LP, o);
@@ -498,8 +571,8 @@ struct GridTcSmem {
     static constexpr int bytes = QT + A + B + 1024;           // + alignment slack
 };
 
-template <int LT, int CONN, bool SYM, bool TC>
-__global__ void __launch_bounds__(GT, (LT >= 24) ? 1 : 3)
+template <int LT, int CONN, bool SYM, bool TC, int RULE = 0>
+__global__ void __launch_bounds__(GT, (LT >= 24 || RULE == 2) ? 1 : (RULE ? 2 : 3))
 grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
     constexpr int LP = storage_labels(LT);
     __shared__ double red[GT / 32];
@@ -551,13 +624,20 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
     j.mu_out = a.mu_out;
     j.mu_in = a.mu_in;
     j.eta = a.eta[b];
-    j.adaptive = a.adapt_d != nullptr;
+    j.adaptive = RULE == 0 && a.adapt_d != nullptr;
     j.adapt_d = j.adaptive ? a.adapt_d[b] : 0.f;
+    j.mom = RULE ? a.mom + (size_t)b * N * LP : nullptr;
+    j.vv = RULE == 2 ? a.vv + (size_t)b * N * LP : nullptr;
+    j.gamma1 = a.gamma1;
+    j.gamma2 = a.gamma2;
+    j.eps = a.eps;
+    j.d0 = RULE == 2 ? a.adapt_d[b] : 0.f;
+    j.first = a.rule_first != 0;
     j.L = a.L;
     j.H = a.H;
     j.W = a.W;
     j.update = a.update;
-    const double bs = grid_tile<LT, CONN, SYM, TC>(j, blockIdx.x, blockIdx.y, &tct);
+    const double bs = grid_tile<LT, CONN, SYM, TC, RULE>(j, blockIdx.x, blockIdx.y, &tct);
     if constexpr (TC) {
         // every thread's TMEM reads finished before the block sync inside grid_tile
         tc::fence_after_sync();
@@ -612,6 +692,12 @@ cudaError_t launch_grid_tc(const GridStepArgs &a, dim3 grid, dim3 block, cudaStr
     return cudaGetLastError();
 }
 
+template <int LT, int CONN, bool SYM, int RULE>
+cudaError_t launch_grid_rule(const GridStepArgs &a, dim3 grid, dim3 block, cudaStream_t st) {
+    grid_prox_step_kernel<LT, CONN, SYM, false, RULE><<<grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int LT>
 cudaError_t launch_grid_step_lt(const GridStepLaunch &l, cudaStream_t st) {
     GridStepArgs a;
@@ -641,7 +727,27 @@ cudaError_t launch_grid_step_lt(const GridStepLaunch &l, cudaStream_t st) {
     a.rel_tol = l.rel_tol;
     a.mu_tc = l.mu_tc;
     a.adapt_d = l.adapt_d;
+    a.mom = l.mom;
+    a.vv = l.vv;
+    a.gamma1 = l.gamma1;
+    a.gamma2 = l.gamma2;
+    a.eps = l.eps;
+    a.rule_first = l.rule_first;
     dim3 grid(nbx, nby, l.B), block(GX, GY, 1);
+    if (l.rule == 1 || l.rule == 2) {
+        if (l.conn == 8) {
+            if (l.rule == 1)
+                return l.mu_sym ? launch_grid_rule<LT, 8, true, 1>(a, grid, block, st)
+                                : launch_grid_rule<LT, 8, false, 1>(a, grid, block, st);
+            return l.mu_sym ? launch_grid_rule<LT, 8, true, 2>(a, grid, block, st)
+                            : launch_grid_rule<LT, 8, false, 2>(a, grid, block, st);
+        }
+        if (l.rule == 1)
+            return l.mu_sym ? launch_grid_rule<LT, 4, true, 1>(a, grid, block, st)
+                            : launch_grid_rule<LT, 4, false, 1>(a, grid, block, st);
+        return l.mu_sym ? launch_grid_rule<LT, 4, true, 2>(a, grid, block, st)
+                        : launch_grid_rule<LT, 4, false, 2>(a, grid, block, st);
+    }
     if (l.tc) {
         if (l.conn == 8)
             return l.mu_sym ? launch_grid_tc<LT, 8, true>(a, grid, block, st) : launch_grid_tc<LT, 8, false>(a, grid, block, st);

@@ -57,7 +57,12 @@ struct GridStepLaunch {
     const float2 *mu_in;     // device [LT][NPP] row pairs
     const uint4 *mu_tc;      // tensor-core form: device BF16 operand images of mu, mu^T
     bool tc;                 // BF16 tensor-core messages (else FP32)
-    const float *adapt_d;    // [B] adaptive binary step: eta_i = 1/(1 + d q_i0 q_i1); null = fixed eta
+    const float *adapt_d;    // [B] adaptive binary step: eta_i = 1/(1 + d q_i0 q_i1); null = fixed eta;
+                             // for rule 2 (Adam): d0 per instance
+    int rule;                // 0 fixed / adaptive, 1 momentum (Sec. 3.4), 2 Adam (Sec. 3.5); FP32 form only
+    float *mom, *vv;         // [B][N][LP] momentum average and second moment (rules 1, 2)
+    float gamma1, gamma2, eps;
+    int rule_first;          // 1 on the first step of a run (no history)
     double *partial;         // [B][nblk] per-tile free-energy partials (scratch)
     unsigned int *counter;   // [B] tiles finished in this launch (scratch, self-resetting)
     double *f_trace;         // [B][trace_cap]
