@@ -35,11 +35,11 @@ def model(oracle, d):
     return oracle.Model.grid(f64(d["U"]), f64(d["mu"]), f64(d["w"]), d["H"], d["W"], d["conn"])
 
 
-def run(binding, d, iters, **kw):
-    topo = binding.CRF_GRID8 if d["conn"] == 8 else binding.CRF_GRID4
-    with binding.CRF(topo, d["L"], d["H"], d["W"]) as crf:
-        crf.set_unary(d["U"])
-        crf.set_pairwise(d["mu"], d["w"])
+def run(binding, inst, iters, **kw):
+    topo = binding.CRF_GRID8 if inst["conn"] == 8 else binding.CRF_GRID4
+    with binding.CRF(topo, inst["L"], inst["H"], inst["W"]) as crf:
+        crf.set_unary(inst["U"])
+        crf.set_pairwise(inst["mu"], inst["w"])
         crf.iterate(iters, reset=True, **kw)
         s = crf.log_marginals()[0].astype(np.float64)
         trace = crf.free_energy_trace(iters)[0]
