@@ -68,6 +68,7 @@ def _load():
             "orc_parallel_prox": (None, [_vp, _d, _i32, _vp, _vp]),
             "orc_prox_step_adaptive": (_i32, [_vp, _d, _vp, _vp]),
             "orc_parallel_prox_momentum": (None, [_vp, _d, _d, _i32, _vp, _vp]),
+            "orc_parallel_adhoc": (None, [_vp, _d, _i32, _vp, _vp]),
             "orc_parallel_prox_adam": (None, [_vp, _d, _d, _d, _d, _i32, _vp, _vp]),
             "orc_parallel_prox_adaptive": (_i32, [_vp, _d, _i32, _vp, _vp]),
             "orc_prox_step_rows": (None, [_vp, _d, _vp, _vp, _i64, _vp]),
@@ -267,6 +268,13 @@ class Model:
         if _load().orc_parallel_prox_adaptive(self._h, float(d), int(iters), _ptr(s),
                                               _ptr(F) if trace else None) != 0:
             raise ValueError("the adaptive step is defined for binary models only")
+        return s, F
+
+    def parallel_adhoc(self, eta: float, iters: int, s=None):
+        """(s, F(q^t) for t = 0..iters) of ADHOC damping (Eq. related:parallel-update)."""
+        s = self.init_logq() if s is None else self._nl(s).copy()
+        F = np.zeros(iters + 1)
+        _load().orc_parallel_adhoc(self._h, float(eta), int(iters), _ptr(s), _ptr(F))
         return s, F
 
     def parallel_prox_momentum(self, eta: float, gamma1: float, iters: int, s=None):

@@ -576,6 +576,37 @@ void orc_parallel_prox_adam(const orc_model *m, double d0, double gamma1, double
     free(a);
 }
 
+/* ADHOC damping (Sec. 2.2.2, Eq. related:parallel-update): every variable
+ * moves towards the solution of its own coordinate update,
+ *   q^{t+1} = (1 - eta) q^t + eta softmax(-grad E(q^t)),
+ * the damping applied to mean parameters (the paper's baseline).  iters
+ * steps on s = log q in place; F_trace as in orc_parallel_prox. */
+void orc_parallel_adhoc(const orc_model *m, double eta, int32_t iters, double *s, double *F_trace)
+{
+    const int L = m->L;
+    const int64_t nl = m->n * L;
+    double *q = (double *)malloc(sizeof(double) * (size_t)nl);
+    double *g = (double *)malloc(sizeof(double) * (size_t)nl);
+    double *a = (double *)malloc(sizeof(double) * (size_t)L);
+    double *st = (double *)malloc(sizeof(double) * (size_t)L);
+    for (int32_t it = 0; it <= iters; ++it) {
+        for (int64_t k = 0; k < nl; ++k) q[k] = exp(s[k]);
+        if (F_trace) F_trace[it] = orc_free_energy(m, q);
+        if (it == iters) break;
+        orc_grad(m, q, g);
+        for (int64_t i = 0; i < m->n; ++i) {
+            for (int l = 0; l < L; ++l) a[l] = -g[i * L + l];
+            log_softmax(a, st, L);
+            for (int l = 0; l < L; ++l)
+                s[i * L + l] = log((1.0 - eta) * q[i * L + l] + eta * exp(st[l]));
+        }
+    }
+    free(q);
+    free(g);
+    free(a);
+    free(st);
+}
+
 /* SWEEP coordinate descent (Sec. 2.2.1, Eq. related:sweep-update): variables
  * in index (raster) order, each set to softmax(-grad E) computed from the
  * current values of all the others.  One call = sweeps full passes. */

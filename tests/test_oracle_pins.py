@@ -506,3 +506,40 @@ def test_momentum_and_adam_fixed_points_are_sweep_stationary(oracle_mod, rule):
         s, F = m.parallel_prox_adam(1 + lam, 0.99, 0.999, 1e-8, 6000)   # gamma1 = 0.99 settles slowly
     s2 = m.sweep(1, s)
     assert np.max(np.abs(np.exp(s2) - np.exp(s))) <= 1e-9
+
+
+# ---------------------------------------------------------------- P10 ---
+# ADHOC damping (Sec. 2.2.2, Eq. related:parallel-update).
+
+def test_adhoc_undamped_is_full_parallel(oracle_mod):
+    """eta = 1: both ADHOC and the natural-parameter step become
+    q^{t+1} = softmax(-grad E(q^t))."""
+    m, _ = small_grid(oracle_mod, 5, 6, 4, 8, seed=61, symmetric=False)
+    s1, _ = m.parallel_adhoc(1.0, 10)
+    s2, _ = m.parallel_prox(1.0, 10)
+    assert np.max(np.abs(np.exp(s1) - np.exp(s2))) <= 1e-13
+
+
+def test_adhoc_decoupled_closed_form(oracle_mod):
+    """Without edges q* = softmax(-U) is fixed, so ADHOC mixes in mean
+    parameters: q^t = (1-eta)^t q^0 + (1 - (1-eta)^t) q*, unlike the
+    natural-parameter step (checked to differ)."""
+    d = synth.random_grid(4, 5, 3, 4, seed=62)
+    U = _f64(d, "U")
+    m = oracle_mod.Model.grid(U, _f64(d, "mu"), 0.0 * _f64(d, "w"), 4, 5, 4)
+    eta, T = 0.3, 7
+    s0 = synth.random_logq(20, 3, seed=63).astype(np.float64)
+    s, _ = m.parallel_adhoc(eta, T, s0)
+    qs = np.exp(-U) / np.exp(-U).sum(axis=1, keepdims=True)
+    q = (1 - eta) ** T * np.exp(s0) + (1 - (1 - eta) ** T) * qs
+    assert np.max(np.abs(np.exp(s) - q)) <= 1e-12
+    s_ours, _ = m.parallel_prox(eta, T, s0)
+    assert np.max(np.abs(np.exp(s_ours) - q)) > 1e-3
+
+
+def test_adhoc_fixed_point_is_sweep_stationary(oracle_mod):
+    d = synth.binary_denoising(H=16, W=16, coupling=0.4, seed=7)
+    m = oracle_mod.Model.grid(_f64(d, "U"), _f64(d, "mu"), _f64(d, "w"), 16, 16, 4)
+    s, _ = m.parallel_adhoc(0.3, 1500)
+    s2 = m.sweep(1, s)
+    assert np.max(np.abs(np.exp(s2) - np.exp(s))) <= 1e-10
