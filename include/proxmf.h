@@ -138,8 +138,12 @@ typedef struct {
                             /* v' = gamma2 v + (1-gamma2) r^2, r the natural     */
                             /* gradient grad E + log q centred over labels, v    */
                             /* starting at 1 (Sec. 3.5, Eq. adamStepSize), eta   */
-                            /* ignored.  Rules 2 and 3: FP32 grids only; each    */
-                            /* mf_iterate call starts a new run (no history).    */
+                            /* ignored; MF_RULE_ADHOC (4): the paper's baseline  */
+                            /* damping of the mean parameters,                   */
+                            /* q' = (1-eta) q + eta softmax(-grad E) (Sec. 2.2.2,*/
+                            /* Eq. related:parallel-update).  Rules 2-4: FP32    */
+                            /* grids only; each mf_iterate call starts a new run */
+                            /* (no history).                                     */
     double d;               /* MF_RULE_ADAPTIVE, MF_RULE_ADAM: d > 0 as given;   */
                             /* d <= 0: the step-size constant max(Lambda, 0)     */
     double gamma1;          /* MF_RULE_MOMENTUM, MF_RULE_ADAM: in [0, 1]         */
@@ -147,12 +151,12 @@ typedef struct {
     double epsilon;         /* MF_RULE_ADAM: >= 0                                */
 } mf_params;
 
-enum { MF_RULE_FIXED = 0, MF_RULE_ADAPTIVE = 1, MF_RULE_MOMENTUM = 2, MF_RULE_ADAM = 3 };
+enum { MF_RULE_FIXED = 0, MF_RULE_ADAPTIVE = 1, MF_RULE_MOMENTUM = 2, MF_RULE_ADAM = 3, MF_RULE_ADHOC = 4 };
 
 /* mf_iterate -- run the parallel proximal iteration of Eq. method:update_natural.
  * rule = MF_RULE_ADAPTIVE on a model that is not a binary grid, and rules
- * MF_RULE_MOMENTUM / MF_RULE_ADAM on a fully connected or BF16 handle,
- * return CRF_E_UNSUPPORTED.
+ * MF_RULE_MOMENTUM / MF_RULE_ADAM / MF_RULE_ADHOC on a fully connected or
+ * BF16 handle, return CRF_E_UNSUPPORTED.
  * Each step computes grad E(q^t) (expected pairwise energy plus unaries),
  * takes the log-domain proximal step, renormalises every variable, and
  * records F(q^t).  iters_done (host, [batch], may be NULL) receives the

@@ -45,7 +45,7 @@ class crf_desc(C.Structure):
                 ("stream", C.c_void_p)]
 
 
-MF_RULE_FIXED, MF_RULE_ADAPTIVE, MF_RULE_MOMENTUM, MF_RULE_ADAM = 0, 1, 2, 3
+MF_RULE_FIXED, MF_RULE_ADAPTIVE, MF_RULE_MOMENTUM, MF_RULE_ADAM, MF_RULE_ADHOC = 0, 1, 2, 3, 4
 
 
 class mf_params(C.Structure):

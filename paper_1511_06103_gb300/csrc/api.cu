@@ -41,7 +41,7 @@ struct crf_s {
     float *adapt_d = nullptr;    // [B] d of the adaptive binary step (or d0 of Adam)
     bool adapt_active = false;   // set while mf_iterate runs the adaptive rule
     float *mom = nullptr, *vv = nullptr;   // [B][N][LP] momentum / Adam state (allocated on first use)
-    int rule_kernel = 0;         // 1 momentum, 2 Adam while mf_iterate runs them
+    int rule_kernel = 0;         // 1 momentum, 2 Adam, 3 ADHOC while mf_iterate runs them
     float gamma1 = 0.f, gamma2 = 0.f, eps = 0.f;
     float *eta_auto = nullptr;   // [B]
     double *Lambda = nullptr;    // [B]
@@ -659,7 +659,8 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
     if (!p || p->max_iters < 0 || p->rel_tol < 0 || !std::isfinite(p->eta) || p->eta > 1.0)
         return CRF_E_INVALID;
     if (!h->has_unary || !h->has_pairwise) return CRF_E_INVALID;
-    if (p->rule < MF_RULE_FIXED || p->rule > MF_RULE_ADAM) return CRF_E_INVALID;
+    if (p->rule < MF_RULE_FIXED || p->rule > MF_RULE_ADHOC) return CRF_E_INVALID;
+    if (p->rule == MF_RULE_ADHOC && (h->dense || h->bf16)) return CRF_E_UNSUPPORTED;
     if (p->rule == MF_RULE_MOMENTUM || p->rule == MF_RULE_ADAM) {
         if (h->dense || h->bf16) return CRF_E_UNSUPPORTED;
         if (!(p->gamma1 >= 0 && p->gamma1 <= 1)) return CRF_E_INVALID;
@@ -732,7 +733,7 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
         return cudaSuccess;
     };
     h->adapt_active = p->rule == MF_RULE_ADAPTIVE;
-    h->rule_kernel = p->rule == MF_RULE_MOMENTUM ? 1 : (p->rule == MF_RULE_ADAM ? 2 : 0);
+    h->rule_kernel = p->rule == MF_RULE_MOMENTUM ? 1 : (p->rule == MF_RULE_ADAM ? 2 : (p->rule == MF_RULE_ADHOC ? 3 : 0));
     h->gamma1 = (float)p->gamma1;
     h->gamma2 = (float)p->gamma2;
     h->eps = (float)p->epsilon;

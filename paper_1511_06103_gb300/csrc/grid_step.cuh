@@ -460,6 +460,39 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, co
             s[k] = av;
             mx = fmaxf(mx, fmaxf(av.x, av.y));
         }
+    } else if constexpr (RULE == 3) {
+        // ADHOC (Sec. 2.2.2, Eq. related:parallel-update): damping of the mean
+        // parameters, q' = (1 - eta) q + eta softmax(-g)
+        float gmx = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const float2 g = add2(u[k], m[k]);
+            const int l0 = 2 * k, l1 = 2 * k + 1;
+            if (!(MASK && l0 >= L)) gmx = fmaxf(gmx, -g.x);
+            if (!((MASK && l1 >= L) || l1 >= LT)) gmx = fmaxf(gmx, -g.y);
+        }
+        float zs = 0.f;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const float2 g = add2(u[k], m[k]);
+            const int l0 = 2 * k, l1 = 2 * k + 1;
+            if (!(MASK && l0 >= L)) zs += __expf(-g.x - gmx);
+            if (!((MASK && l1 >= L) || l1 >= LT)) zs += __expf(-g.y - gmx);
+        }
+        const float izs = 1.f / zs;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const float2 g = add2(u[k], m[k]);
+            const float2 h = add2(fma2(half, m[k], u[k]), s[k]);
+            f2 = fma2(qc[k], h, f2);
+            const int l0 = 2 * k, l1 = 2 * k + 1;
+            float2 av = make_float2(__logf(fmaf(1.f - eta, qc[k].x, eta * __expf(-g.x - gmx) * izs)),
+                                    __logf(fmaf(1.f - eta, qc[k].y, eta * __expf(-g.y - gmx) * izs)));
+            if ((MASK && l0 >= L)) av.x = -INFINITY;
+            if ((MASK && l1 >= L) || l1 >= LT) av.y = -INFINITY;
+            s[k] = av;
+            mx = fmaxf(mx, fmaxf(av.x, av.y));
+        }
     } else {
         // OURS-MOMENTUM (RULE 1, Sec. 3.4): the gradient is replaced by its
         // running average mo' = g1 mo + (1 - g1) g (mo' = g on the first step).
@@ -626,7 +659,7 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
     j.eta = a.eta[b];
     j.adaptive = RULE == 0 && a.adapt_d != nullptr;
     j.adapt_d = j.adaptive ? a.adapt_d[b] : 0.f;
-    j.mom = RULE ? a.mom + (size_t)b * N * LP : nullptr;
+    j.mom = (RULE == 1 || RULE == 2) ? a.mom + (size_t)b * N * LP : nullptr;
     j.vv = RULE == 2 ? a.vv + (size_t)b * N * LP : nullptr;
     j.gamma1 = a.gamma1;
     j.gamma2 = a.gamma2;
@@ -734,6 +767,13 @@ cudaError_t launch_grid_step_lt(const GridStepLaunch &l, cudaStream_t st) {
     a.eps = l.eps;
     a.rule_first = l.rule_first;
     dim3 grid(nbx, nby, l.B), block(GX, GY, 1);
+    if (l.rule == 3) {
+        if (l.conn == 8)
+            return l.mu_sym ? launch_grid_rule<LT, 8, true, 3>(a, grid, block, st)
+                            : launch_grid_rule<LT, 8, false, 3>(a, grid, block, st);
+        return l.mu_sym ? launch_grid_rule<LT, 4, true, 3>(a, grid, block, st)
+                        : launch_grid_rule<LT, 4, false, 3>(a, grid, block, st);
+    }
     if (l.rule == 1 || l.rule == 2) {
         if (l.conn == 8) {
             if (l.rule == 1)

@@ -59,7 +59,8 @@ struct GridStepLaunch {
     bool tc;                 // BF16 tensor-core messages (else FP32)
     const float *adapt_d;    // [B] adaptive binary step: eta_i = 1/(1 + d q_i0 q_i1); null = fixed eta;
                              // for rule 2 (Adam): d0 per instance
-    int rule;                // 0 fixed / adaptive, 1 momentum (Sec. 3.4), 2 Adam (Sec. 3.5); FP32 form only
+    int rule;                // 0 fixed / adaptive, 1 momentum (Sec. 3.4), 2 Adam (Sec. 3.5),
+                             // 3 ADHOC mean-parameter damping (Sec. 2.2.2); FP32 form only
     float *mom, *vv;         // [B][N][LP] momentum average and second moment (rules 1, 2)
     float gamma1, gamma2, eps;
     int rule_first;          // 1 on the first step of a run (no history)
