@@ -61,6 +61,9 @@ def parse():
     p.add_argument("--no-denoising", action="store_true",
                    help="skip the 64x64 binary denoising measurement")
     p.add_argument("--denoising-only", action="store_true")
+    p.add_argument("--no-eta-sweep", action="store_true",
+                   help="skip the step-parameter sensitivity sweep")
+    p.add_argument("--eta-sweep-only", action="store_true")
     p.add_argument("--no-grid-bf16", action="store_true",
                    help="skip the BF16 tensor-core form of the segmentation workload")
     p.add_argument("--grid-bf16-only", action="store_true")
@@ -378,6 +381,50 @@ def run_denoising(args, dev):
                         "eta = 1/(1+Lambda) (0.2383), back-to-back solves", "eta": float(eta[0]), **out}
 
 
+ETA_GRID = [float(x) for x in np.logspace(-2.5, 0.0, 11)]
+
+
+def run_eta_sweep(args, dev):
+    """Sensitivity to the step parameter (the synthetic counterpart of the
+    paper's comparison of OURS-FIXED / OURS-ADAPTIVE with ADHOC over
+    eta = 1/(1+d)): final F after a fixed number of steps for each eta of a
+    log grid, on the binary denoising model and on the segmentation grid.
+    Lower F (= KL up to log Z) is better."""
+    import torch
+
+    from paper_1511_06103_gb300 import binding, synth
+    stream = torch.cuda.current_stream(dev)
+    out = {"eta": ETA_GRID}
+    cases = (("denoising_64x64_L2", synth.binary_denoising(), binding.CRF_GRID4, 50),
+             ("segmentation_512x512_L21", synth.segmentation_grid(H=H, W=W, L=L, conn=CONN, seed=SEED),
+              binding.CRF_GRID8, ITERS))
+    for name, d, topo, iters in cases:
+        crf = binding.CRF(topo, d["L"], d["H"], d["W"], stream=stream.cuda_stream)
+        crf.set_unary(torch.from_numpy(d["U"]).to(dev))
+        crf.set_pairwise(torch.from_numpy(d["mu"]).to(dev), torch.from_numpy(d["w"]).to(dev))
+        lam, eta_c = crf.lipschitz()
+        res = {"iters": iters, "eta_constant": float(eta_c[0]), "fixed": [], "adhoc": []}
+        if d["L"] == 2:
+            res["adaptive"] = []
+        for e in ETA_GRID:
+            crf.iterate(iters, eta=e, reset=True, final_free_energy=True)
+            res["fixed"].append(float(crf.free_energy()[0]))
+            crf.iterate(iters, eta=e, reset=True, final_free_energy=True, rule=binding.MF_RULE_ADHOC)
+            res["adhoc"].append(float(crf.free_energy()[0]))
+            if d["L"] == 2:
+                crf.iterate(iters, reset=True, final_free_energy=True, rule=binding.MF_RULE_ADAPTIVE,
+                            d=max(1.0 / e - 1.0, 1e-6))
+                res["adaptive"].append(float(crf.free_energy()[0]))
+        crf.iterate(iters, eta=0.0, reset=True, final_free_energy=True)
+        res["F_at_eta_constant"] = float(crf.free_energy()[0])
+        for k in ("fixed", "adhoc", "adaptive"):
+            if k in res:
+                res[k + "_spread"] = max(res[k]) - min(res[k])
+        out[name] = res
+        crf.close()
+    return out
+
+
 UNR_B, UNR_SIDE, UNR_L, UNR_CONN, UNR_K = 16, 256, 21, 4, 10
 
 
@@ -576,6 +623,9 @@ def run_ours(args, world, rank, local):
     if args.serve_only:
         print(json.dumps({"serving": run_serving(max(1, args.serve_requests))}), flush=True)
         return
+    if args.eta_sweep_only:
+        print(json.dumps({"eta_sweep": run_eta_sweep(args, dev)}), flush=True)
+        return
     if args.denoising_only:
         print(json.dumps({"denoising": run_denoising(args, dev)}), flush=True)
         return
@@ -721,6 +771,9 @@ def run_ours(args, world, rank, local):
     denoise = None
     if not args.no_denoising and world == 1:
         denoise = run_denoising(args, dev)
+    eta_sweep = None
+    if not args.no_eta_sweep and world == 1:
+        eta_sweep = run_eta_sweep(args, dev)
     grid_prec = None
     if not args.no_grid_bf16 and world == 1:
         grid_prec = run_grid_precision(args, dev, peak)
@@ -759,6 +812,7 @@ def run_ours(args, world, rank, local):
             "wall_ms_timed": 1000 * (wall1 - wall0),
             "dense": dense,
             "denoising": denoise,
+            "eta_sweep": eta_sweep,
             "grid_precision": grid_prec,
             "unrolled": unrolled,
             "serving": serving,
