@@ -55,7 +55,9 @@ typedef enum {
 typedef enum {
     CRF_GRID4 = 0,          /* 4-connected H x W grid                         */
     CRF_GRID8 = 1,          /* 8-connected H x W grid                         */
-    CRF_DENSE_GAUSS = 2     /* fully connected, Gaussian kernel over features */
+    CRF_DENSE_GAUSS = 2,    /* fully connected, Gaussian kernel over features */
+    CRF_SPARSE = 3          /* general pairwise graph from an edge list       */
+                            /* (crf_set_graph); N = height*width variables    */
 } crf_topology;
 
 typedef enum {
@@ -70,7 +72,7 @@ typedef enum {
 
 typedef struct {
     int32_t topology;       /* crf_topology                                   */
-    int32_t n_labels;       /* L: 1..32 (grids), 1..24 (fully connected)      */
+    int32_t n_labels;       /* L: 1..32 (grids, sparse), 1..24 (fully connected) */
     int32_t batch;          /* independent instances with the same shape, >= 1 */
     int32_t precision;      /* crf_precision                                  */
     int64_t height;         /* grid rows; dense: N = height*width variables   */
@@ -111,6 +113,19 @@ crf_status crf_set_pairwise(crf_t h, const float *mu, const float *w_or_feats,
  * (each row should be a normalised log-distribution; it is used as given).
  * Checkpoint / resume, and identical starting points for parity checks. */
 crf_status crf_set_state(crf_t h, const float *logq, int is_device);
+
+/* crf_set_graph -- pairwise term of a CRF_SPARSE handle (Sec. 2.1, Eq.
+ * related:pairwise-mrf on an arbitrary edge set): n_edges oriented edges
+ * src[e] -> dst[e] (0 <= index < N, src != dst) with weights w[e] (finite)
+ * and mu [L][L] (cost of x_src = l, x_dst = l'), shared by all instances of
+ * the batch.  Arrays are device pointers if is_device = 1, else host.  The
+ * step-size constant of a sparse graph is replaced by a bound on it (no
+ * Lanczos): Lambda <= D max|eig(C mu C)| for symmetric mu, D the largest
+ * summed |w| of a variable's edges; (D_out + D_in) ||mu||_F otherwise.  The
+ * bound is >= Lambda, so eta = 1/(1+bound) keeps the descent guarantee.
+ * CRF_E_INVALID for a handle of another topology or a bad index. */
+crf_status crf_set_graph(crf_t h, const float *mu, int64_t n_edges, const int32_t *src, const int32_t *dst,
+                         const float *w, int32_t is_device);
 
 typedef struct {
     double eta;             /* > 0: fixed step eta (1 = FULL-PARALLEL);        */

@@ -24,7 +24,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # variant); the default is the in-tree build.
 LIB_PATH = os.environ.get("PROXMF_LIB") or os.path.join(HERE, "_build", "libproxmf.so")
 
-CRF_GRID4, CRF_GRID8, CRF_DENSE_GAUSS = 0, 1, 2
+CRF_GRID4, CRF_GRID8, CRF_DENSE_GAUSS, CRF_SPARSE = 0, 1, 2, 3
 CRF_FP32, CRF_BF16 = 0, 1
 
 STATUS = {
@@ -66,6 +66,7 @@ _SIGS = {
     "crf_set_unary": [_vp, _vp, _i],
     "crf_set_pairwise": [_vp, _vp, _vp, _vp, _i],
     "crf_set_state": [_vp, _vp, _i],
+    "crf_set_graph": [_vp, _vp, C.c_int64, _vp, _vp, _vp, C.c_int32],
     "mf_iterate": [_vp, C.POINTER(mf_params), _vp],
     "mf_free_energy": [_vp, _vp],
     "mf_free_energy_trace": [_vp, _vp, C.c_int32],
@@ -280,6 +281,18 @@ class CRF:
             th = np.ascontiguousarray(theta, np.float32)
             pt = th.ctypes.data
         crf_set_pairwise(self.h, pm, pw, pt, dw)
+
+    def set_graph(self, mu, src, dst, w) -> None:
+        """Pairwise term of a CRF_SPARSE handle: oriented edges src[e] -> dst[e]
+        with weights w[e] (host arrays), mu [L][L]."""
+        src = np.ascontiguousarray(src, np.int32)
+        dst = np.ascontiguousarray(dst, np.int32)
+        w = np.ascontiguousarray(w, np.float32)
+        mu = np.ascontiguousarray(mu, np.float32)
+        if not (src.shape == dst.shape == w.shape):
+            raise ValueError("src, dst and w must have the same length")
+        _call("crf_set_graph", self.h, mu.ctypes.data, int(src.size), src.ctypes.data, dst.ctypes.data,
+              w.ctypes.data, 0)
 
     def set_state(self, logq) -> None:
         p, dev, keep = _as_buffer(logq)

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -25,6 +26,10 @@ struct crf_s {
     float *w = nullptr;          // [B][N][nd] edge weights
     float2 *mu_pairs = nullptr;  // device [2][LT][NPP] mu column / row pairs
     uint8_t *mu_tc = nullptr;    // device BF16 operand images of mu, mu^T (grid, BF16 form)
+    // general graph (edge list)
+    bool sparse = false;
+    int *sp_out_ptr = nullptr, *sp_out_col = nullptr, *sp_in_ptr = nullptr, *sp_in_col = nullptr;
+    float *sp_out_w = nullptr, *sp_in_w = nullptr;
     // fully connected model
     bool dense = false;
     int N = 0;                   // variables per instance
@@ -122,6 +127,11 @@ void free_all(crf_t h) {
     if (h->status) cudaFree(h->status);
     if (h->mu_pairs) cudaFree(h->mu_pairs);
     if (h->mu_tc) cudaFree(h->mu_tc);
+    int *ip[] = {h->sp_out_ptr, h->sp_out_col, h->sp_in_ptr, h->sp_in_col};
+    for (int *p : ip)
+        if (p) cudaFree(p);
+    if (h->sp_out_w) cudaFree(h->sp_out_w);
+    if (h->sp_in_w) cudaFree(h->sp_in_w);
     float *fd[] = {h->K32, h->q32[0], h->q32[1], h->feats, h->mu_dev};
     for (float *p : fd)
         if (p) cudaFree(p);
@@ -236,6 +246,39 @@ DenseStepLaunch dense_args(crf_t h, const float *eta, int t, int update, double 
 // model.  fp32 = 1 forces the FP32 form (refinement steps, and every
 // free-energy-only pass, which is evaluated with FP32 messages).
 cudaError_t launch_step(crf_t h, const float *eta, int t, int update, double rel_tol, int fp32 = 0) {
+    if (h->sparse) {
+        SparseStepLaunch a{};
+        a.s_in = h->s[h->cur];
+        a.s_out = h->s[h->cur ^ 1];
+        a.q_in = h->q32[h->cur];
+        a.q_out = h->q32[h->cur ^ 1];
+        a.U = h->U;
+        a.out_ptr = h->sp_out_ptr;
+        a.out_col = h->sp_out_col;
+        a.out_w = h->sp_out_w;
+        a.in_ptr = h->sp_in_ptr;
+        a.in_col = h->sp_in_col;
+        a.in_w = h->sp_in_w;
+        a.mu = h->mu_dev;
+        a.eta = eta;
+        a.partial = h->partial;
+        a.counter = h->counter;
+        a.f_trace = h->ftrace;
+        a.f_cur = h->fcur;
+        a.done = (update && rel_tol > 0) ? h->done : nullptr;
+        a.status = h->status;
+        a.B = h->B;
+        a.N = h->N;
+        a.L = h->L;
+        a.LP = h->LP;
+        a.nblk = h->nblk;
+        a.t = t;
+        a.trace_cap = h->trace_cap;
+        a.update = update;
+        a.rel_tol = rel_tol;
+        a.sym = h->mu_sym;
+        return launch_sparse_step(a, h->st);
+    }
     if (h->dense) {
         DenseStepLaunch a = dense_args(h, eta, t, update, rel_tol);
         if (!update || rel_tol <= 0) a.done = nullptr;
@@ -251,13 +294,14 @@ cudaError_t launch_step(crf_t h, const float *eta, int t, int update, double rel
 // After the state buffer s[cur] changed outside a step: refresh the dense
 // model's q copies.
 cudaError_t refresh_q(crf_t h) {
-    if (!h->dense) return cudaSuccess;
+    if (!h->dense && !h->sparse) return cudaSuccess;
     h->launches++;
     return launch_dense_export_q(h->s[h->cur], h->q32[h->cur], h->qt16[h->cur], h->B, h->N, h->L, h->LP, h->st);
 }
 
 crf_status ensure_lambda(crf_t h) {
     if (h->lambda_valid) return CRF_OK;
+    if (h->sparse) return CRF_E_INVALID;   // set by crf_set_graph
     LipschitzJob job{};
     job.w = h->w;
     job.Kdense = h->dense ? h->K32 : nullptr;
@@ -365,6 +409,57 @@ void build_mu_pairs(const std::vector<float> &mu, int L, int LT, std::vector<flo
 
 }  // namespace proxmf
 
+namespace {
+
+// CSR of a graph given as (src, dst, w) triples: variable i's list holds
+// (dst, w) of the edges leaving i and, when `both`, (src, w) of those
+// entering it; otherwise `in_*` receives the entering edges separately.
+void build_csr(int N, int64_t E, const int32_t *src, const int32_t *dst, const float *w, bool both,
+                      std::vector<int> &optr, std::vector<int> &ocol, std::vector<float> &ow, std::vector<int> &iptr,
+                      std::vector<int> &icol, std::vector<float> &iw) {
+    optr.assign((size_t)N + 1, 0);
+    iptr.assign((size_t)N + 1, 0);
+    for (int64_t e = 0; e < E; ++e) {
+        optr[(size_t)src[e] + 1]++;
+        if (both)
+            optr[(size_t)dst[e] + 1]++;
+        else
+            iptr[(size_t)dst[e] + 1]++;
+    }
+    for (int i = 0; i < N; ++i) {
+        optr[(size_t)i + 1] += optr[i];
+        iptr[(size_t)i + 1] += iptr[i];
+    }
+    ocol.assign((size_t)optr[N], 0);
+    ow.assign((size_t)optr[N], 0.f);
+    icol.assign((size_t)iptr[N], 0);
+    iw.assign((size_t)iptr[N], 0.f);
+    std::vector<int> fo(optr.begin(), optr.end() - 1), fi(iptr.begin(), iptr.end() - 1);
+    for (int64_t e = 0; e < E; ++e) {
+        const int a = src[e], b = dst[e];
+        ocol[(size_t)fo[a]] = b;
+        ow[(size_t)fo[a]++] = w[e];
+        if (both) {
+            ocol[(size_t)fo[b]] = a;
+            ow[(size_t)fo[b]++] = w[e];
+        } else {
+            icol[(size_t)fi[b]] = a;
+            iw[(size_t)fi[b]++] = w[e];
+        }
+    }
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const std::vector<T> &v, cudaStream_t st) {
+    if (*dst) cudaFree(*dst);
+    *dst = nullptr;
+    cudaError_t e = dalloc(dst, v.size());
+    if (e == cudaSuccess && !v.empty()) e = cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    return e;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *crf_version(void) { return "proxmf 0.1 (sm_103a)"; }
@@ -391,15 +486,23 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
     if (d.n_labels < 1 || d.n_labels > kMaxLabels || d.batch < 1 || d.height < 1 || d.width < 1)
         return CRF_E_INVALID;
     if (d.precision != CRF_FP32 && d.precision != CRF_BF16) return CRF_E_INVALID;
-    if (d.topology != CRF_GRID4 && d.topology != CRF_GRID8 && d.topology != CRF_DENSE_GAUSS)
+    if (d.topology != CRF_GRID4 && d.topology != CRF_GRID8 && d.topology != CRF_DENSE_GAUSS &&
+        d.topology != CRF_SPARSE)
         return CRF_E_INVALID;
     const bool dense = d.topology == CRF_DENSE_GAUSS;
+    const bool sparse = d.topology == CRF_SPARSE;
+    if (sparse) {
+        if (d.precision != CRF_FP32) return CRF_E_UNSUPPORTED;
+        if ((long long)d.height * d.width >= (1ll << 31) || d.batch > 65535 ||
+            (long long)d.batch * d.height * d.width * storage_labels(d.n_labels) > (1ll << 40))
+            return CRF_E_INVALID;
+    }
     if (dense) {
         // the dense step keeps up to 24 labels per row; N x N weights per instance
         if (d.n_labels > 24) return CRF_E_UNSUPPORTED;
         const long long N = d.height * d.width;
         if (N > 65536 || d.batch > 65535 || (long long)d.batch * N * N * 4 > (64ll << 30)) return CRF_E_INVALID;
-    } else {
+    } else if (!sparse) {
         // grid dimensions: y tiles <= 65535, batch <= 65535 (CUDA grid limits)
         if (d.height > 65535ll * GY || d.width > (1 << 24) || d.batch > 65535) return CRF_E_INVALID;
         if ((long long)d.batch * storage_labels(d.n_labels) * d.height * d.width > (1ll << 40))
@@ -427,6 +530,12 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
         h->nd = 0;
         h->nblk = dense_nblk(h->N);
     }
+    h->sparse = sparse;
+    if (sparse) {
+        h->nd = 0;
+        h->nblk = sparse_blocks(h->N);
+        h->conn = 0;
+    }
     h->mu.assign((size_t)h->L * h->L, 0.f);
 
     bool ok = true;
@@ -434,6 +543,10 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
     ok = ok && dalloc(&h->s[0], n_padded(h)) == cudaSuccess;
     ok = ok && dalloc(&h->s[1], n_padded(h)) == cudaSuccess;
     ok = ok && dalloc(&h->w, n_pix(h) * h->nd) == cudaSuccess;
+    if (sparse) {
+        ok = ok && dalloc(&h->q32[0], n_padded(h)) == cudaSuccess;
+        ok = ok && dalloc(&h->q32[1], n_padded(h)) == cudaSuccess;
+    }
     if (dense) {
         const size_t qn = n_padded(h) + 64 * (size_t)h->LP;   // rows past N read as zero
         ok = ok && dalloc(&h->K32, (size_t)h->B * h->N * h->N) == cudaSuccess;
@@ -577,6 +690,7 @@ crf_status crf_set_pairwise(crf_t h, const float *mu, const float *w_or_feats, c
     crf_status rc = check_handle(h);
     if (rc != CRF_OK) return rc;
     if (!mu || !w_or_feats) return CRF_E_INVALID;
+    if (h->sparse) return CRF_E_INVALID;   // crf_set_graph
     const size_t LL = (size_t)h->L * h->L;
     std::vector<float> m(LL);
     if (is_device) {
@@ -636,6 +750,84 @@ crf_status crf_set_pairwise(crf_t h, const float *mu, const float *w_or_feats, c
     return CRF_OK;
 }
 
+crf_status crf_set_graph(crf_t h, const float *mu, int64_t n_edges, const int32_t *src, const int32_t *dst,
+                         const float *w, int32_t is_device) {
+    crf_status rc = check_handle(h);
+    if (rc != CRF_OK) return rc;
+    if (!h->sparse || !mu || n_edges < 0 || n_edges > (1ll << 30) || (n_edges > 0 && (!src || !dst || !w)))
+        return CRF_E_INVALID;
+    const size_t LL = (size_t)h->L * h->L, E = (size_t)n_edges;
+    std::vector<float> m(LL), wv(E);
+    std::vector<int32_t> sv(E), dv(E);
+    const cudaMemcpyKind k = is_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    CK(h, cudaMemcpyAsync(m.data(), mu, LL * sizeof(float), k, h->st));
+    if (E) {
+        CK(h, cudaMemcpyAsync(sv.data(), src, E * sizeof(int32_t), k, h->st));
+        CK(h, cudaMemcpyAsync(dv.data(), dst, E * sizeof(int32_t), k, h->st));
+        CK(h, cudaMemcpyAsync(wv.data(), w, E * sizeof(float), k, h->st));
+    }
+    CK(h, cudaStreamSynchronize(h->st));
+    for (float v : m)
+        if (!std::isfinite(v)) return CRF_E_INVALID;
+    for (size_t e = 0; e < E; ++e)
+        if (sv[e] < 0 || sv[e] >= h->N || dv[e] < 0 || dv[e] >= h->N || sv[e] == dv[e] || !std::isfinite(wv[e]))
+            return CRF_E_INVALID;
+    bool sym = true;
+    for (int i = 0; i < h->L; ++i)
+        for (int j = i + 1; j < h->L; ++j)
+            if (m[(size_t)i * h->L + j] != m[(size_t)j * h->L + i]) sym = false;
+    std::vector<int> optr, ocol, iptr, icol;
+    std::vector<float> ow, iw;
+    build_csr(h->N, n_edges, sv.data(), dv.data(), wv.data(), sym, optr, ocol, ow, iptr, icol, iw);
+    CK(h, upload(&h->sp_out_ptr, optr, h->st));
+    CK(h, upload(&h->sp_out_col, ocol, h->st));
+    CK(h, upload(&h->sp_out_w, ow, h->st));
+    CK(h, upload(&h->sp_in_ptr, iptr, h->st));
+    CK(h, upload(&h->sp_in_col, icol, h->st));
+    CK(h, upload(&h->sp_in_w, iw, h->st));
+    CK(h, cudaMemcpyAsync(h->mu_dev, m.data(), LL * sizeof(float), cudaMemcpyHostToDevice, h->st));
+    // step bound (see proxmf.h): the largest summed |w| per variable, and
+    // the spectrum of C mu C (symmetric mu) or ||mu||_F
+    unsigned *deg = reinterpret_cast<unsigned *>(h->counter);   // counters are zero between launches
+    unsigned bits[2] = {0u, 0u};
+    CK(h, launch_sparse_degree(h->sp_out_ptr, h->sp_out_w, h->N, deg, h->st));
+    CK(h, cudaMemcpyAsync(&bits[0], deg, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
+    if (!sym) {
+        CK(h, launch_sparse_degree(h->sp_in_ptr, h->sp_in_w, h->N, deg, h->st));
+        CK(h, cudaMemcpyAsync(&bits[1], deg, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
+    }
+    double nu[2] = {0.0, 0.0};
+    if (sym) {
+        CK(h, launch_mu_tilde_extremes(h->mu_dev, h->L, h->Lambda, h->st));
+        CK(h, cudaMemcpyAsync(nu, h->Lambda, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    }
+    CK(h, cudaMemsetAsync(h->counter, 0, h->B * sizeof(unsigned), h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    float d0, d1;
+    std::memcpy(&d0, &bits[0], 4);
+    std::memcpy(&d1, &bits[1], 4);
+    double lam;
+    if (sym) {
+        lam = (double)d0 * std::max(std::fabs(nu[0]), std::fabs(nu[1]));
+    } else {
+        double fro = 0.0;
+        for (float v : m) fro += (double)v * v;
+        lam = ((double)d0 + (double)d1) * std::sqrt(fro);
+    }
+    std::vector<double> L(h->B, lam);
+    std::vector<float> eta(h->B, (float)(1.0 / (1.0 + std::max(lam, 0.0))));
+    CK(h, cudaMemcpyAsync(h->Lambda, L.data(), h->B * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    CK(h, cudaMemcpyAsync(h->eta_auto, eta.data(), h->B * sizeof(float), cudaMemcpyHostToDevice, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    h->launches += sym ? 2 : 2;
+    h->mu = m;
+    h->mu_sym = sym;
+    h->lambda_valid = true;
+    h->has_pairwise = true;
+    h->fcur_valid = false;
+    return CRF_OK;
+}
+
 crf_status crf_set_state(crf_t h, const float *logq, int is_device) {
     crf_status rc = check_handle(h);
     if (rc != CRF_OK) return rc;
@@ -660,9 +852,9 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
         return CRF_E_INVALID;
     if (!h->has_unary || !h->has_pairwise) return CRF_E_INVALID;
     if (p->rule < MF_RULE_FIXED || p->rule > MF_RULE_ADHOC) return CRF_E_INVALID;
-    if (p->rule == MF_RULE_ADHOC && (h->dense || h->bf16)) return CRF_E_UNSUPPORTED;
+    if (p->rule == MF_RULE_ADHOC && (h->dense || h->sparse || h->bf16)) return CRF_E_UNSUPPORTED;
     if (p->rule == MF_RULE_MOMENTUM || p->rule == MF_RULE_ADAM) {
-        if (h->dense || h->bf16) return CRF_E_UNSUPPORTED;
+        if (h->dense || h->sparse || h->bf16) return CRF_E_UNSUPPORTED;
         if (!(p->gamma1 >= 0 && p->gamma1 <= 1)) return CRF_E_INVALID;
         if (p->rule == MF_RULE_ADAM &&
             (!(p->gamma2 >= 0 && p->gamma2 <= 1) || !(p->epsilon >= 0) || !std::isfinite(p->epsilon) ||
@@ -686,7 +878,7 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
         }
     }
     if (p->rule == MF_RULE_ADAPTIVE) {
-        if (h->dense || h->L != 2) return CRF_E_UNSUPPORTED;
+        if (h->dense || h->sparse || h->L != 2) return CRF_E_UNSUPPORTED;
         if (!std::isfinite(p->d)) return CRF_E_INVALID;
         if (p->d > 0) {
             CK(h, launch_fill_eta(h->adapt_d, h->B, p->d, h->st));
@@ -911,7 +1103,7 @@ crf_status crf_launch_count(crf_t h, int64_t *n) {
 static crf_status unrolled_check(crf_t h, int32_t K) {
     crf_status rc = check_handle(h);
     if (rc != CRF_OK) return rc;
-    if (h->dense || h->L > kAdjointMaxLabels) return CRF_E_UNSUPPORTED;
+    if (h->dense || h->sparse || h->L > kAdjointMaxLabels) return CRF_E_UNSUPPORTED;
     if (h->H > 4 * 65535) return CRF_E_UNSUPPORTED;   // reverse-step grid: 4-row tiles in gridDim.y
     if (K < 1 || K > 4096) return CRF_E_INVALID;
     return CRF_OK;

@@ -194,6 +194,32 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
                             long long *launches_out);
 
 
+// General pairwise graphs (sparse.cu): CSR adjacency, one warp per variable.
+struct SparseStepLaunch {
+    const float *s_in;       // [B][N][LP] log q^t
+    float *s_out;            // [B][N][LP] log q^{t+1}
+    const float *q_in;       // [B][N][LP] q^t
+    float *q_out;            // [B][N][LP] q^{t+1}
+    const float *U;          // [B][N][LP]
+    const int *out_ptr, *out_col;   // adjacency: symmetric mu -> both directions of every edge
+    const float *out_w;
+    const int *in_ptr, *in_col;     // asymmetric mu: edges entering each variable
+    const float *in_w;
+    const float *mu;         // [L][L] device
+    const float *eta;        // [B]
+    double *partial;         // [B][nblk]
+    unsigned *counter;       // [B]
+    double *f_trace, *f_cur;
+    int *done, *status;
+    int B, N, L, LP, nblk;
+    int t, trace_cap, update;
+    double rel_tol;
+    bool sym;
+};
+int sparse_blocks(int N);
+cudaError_t launch_sparse_step(const SparseStepLaunch &a, cudaStream_t st);
+cudaError_t launch_sparse_degree(const int *ptr, const float *w, int N, unsigned *out_bits, cudaStream_t st);
+
 // Reverse mode through unrolled grid steps (adjoint.cu).  All arrays are in
 // the padded pixel-major layout of the step kernel; L <= 24.
 constexpr int kAdjointMaxLabels = 24;

@@ -1,0 +1,153 @@
+// sparse.cu -- the parallel proximal step on a general pairwise graph given
+// as an edge list (Sec. 2.1, Eq. related:pairwise-mrf with an arbitrary edge
+// set; the DBN-shaped layers of the paper's benchmarks are one instance).
+//
+// One warp per variable, one lane per label (L <= 32): the lanes walk the
+// variable's adjacency list in CSR form and accumulate the weighted
+// neighbour marginals with one coalesced 4*LP-byte read per neighbour, then
+//   m = mu S_out + mu^T S_in      (m = mu S for symmetric mu, S over both
+//                                  directions of every edge),
+// the L x L product with the other lanes' S through warp shuffles, and the
+// log-domain step, renormalisation and free-energy term of Eq.
+// method:update_natural as in the grid step.  q = exp(log q) of the new
+// state is written next to it, so that neighbours read q without
+// recomputing exponentials.  Free-energy partials are FP64 per block and
+// reduced in a fixed order by the last block of each instance.
+#include <cmath>
+
+#include "internal.h"
+
+namespace proxmf {
+
+namespace {
+
+constexpr int kSW = 8;               // variables (warps) per block
+constexpr int kST = kSW * 32;
+
+__global__ void __launch_bounds__(kST) sparse_step_kernel(const SparseStepLaunch a) {
+    __shared__ float mus[kMaxLabels * kMaxLabels];
+    __shared__ double red[kSW];
+    __shared__ int is_last;
+    const int b = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int N = a.N, L = a.L, LP = a.LP;
+    const int i = blockIdx.x * kSW + warp;
+    const size_t base = (size_t)b * N;
+    for (int e = threadIdx.x; e < L * L; e += kST) mus[e] = a.mu[e];
+
+    if (a.done != nullptr && a.done[b] != 0) {
+        // stopping rule met: carry the state through unchanged
+        if (a.update && i < N && lane < LP) {
+            const size_t o = (base + i) * LP + lane;
+            a.s_out[o] = a.s_in[o];
+            a.q_out[o] = a.q_in[o];
+        }
+        return;
+    }
+    __syncthreads();
+
+    const bool live = lane < L;
+    float f = 0.f;
+    if (i < N) {
+        const size_t o = (base + i) * LP + lane;
+        // a1: neighbour sums
+        float S = 0.f, T = 0.f;
+        for (int e = a.out_ptr[i]; e < a.out_ptr[i + 1]; ++e) {
+            const float qj = lane < LP ? __ldg(a.q_in + (base + a.out_col[e]) * LP + lane) : 0.f;
+            S = fmaf(a.out_w[e], qj, S);
+        }
+        if (!a.sym)
+            for (int e = a.in_ptr[i]; e < a.in_ptr[i + 1]; ++e) {
+                const float qk = lane < LP ? __ldg(a.q_in + (base + a.in_col[e]) * LP + lane) : 0.f;
+                T = fmaf(a.in_w[e], qk, T);
+            }
+        // m_l = sum_k mu[l][k] S_k (+ sum_k mu[k][l] T_k)
+        float m = 0.f;
+        for (int k = 0; k < L; ++k) {
+            const float Sk = __shfl_sync(0xffffffffu, S, k);
+            const float Tk = __shfl_sync(0xffffffffu, T, k);
+            if (live) {
+                m = fmaf(mus[lane * L + k], Sk, m);
+                if (!a.sym) m = fmaf(mus[k * L + lane], Tk, m);
+            }
+        }
+        // a2-a4
+        const float s = live ? a.s_in[o] : 0.f;
+        const float u = live ? a.U[o] : 0.f;
+        const float q = live ? a.q_in[o] : 0.f;
+        const float eta = a.eta[b];
+        f = live ? q * (u + 0.5f * m + s) : 0.f;
+        const float av = live ? fmaf(-eta, u + m, (1.f - eta) * s) : -INFINITY;
+        float mx = av;
+#pragma unroll
+        for (int w = 16; w > 0; w >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, w));
+        float z = live ? __expf(av - mx) : 0.f;
+#pragma unroll
+        for (int w = 16; w > 0; w >>= 1) z += __shfl_xor_sync(0xffffffffu, z, w);
+        const float sn = av - mx - __logf(z);
+        if (a.update && lane < LP) {
+            a.s_out[o] = live ? sn : kPadLogQ;
+            a.q_out[o] = live ? __expf(sn) : 0.f;
+        }
+    }
+    // a5: F partial of the block, FP64, fixed order
+    double fd = (double)f;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) fd += __shfl_down_sync(0xffffffffu, fd, w);
+    if (lane == 0) red[warp] = fd;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bs = 0.0;
+        for (int k = 0; k < kSW; ++k) bs += red[k];
+        a.partial[(size_t)b * a.nblk + blockIdx.x] = bs;
+        __threadfence();
+        is_last = atomicAdd(a.counter + b, 1u) == (unsigned)(a.nblk - 1);
+    }
+    __syncthreads();
+    if (!is_last || threadIdx.x != 0) return;
+    __threadfence();
+    double F = 0.0;
+    for (int k = 0; k < a.nblk; ++k) F += __ldcg(a.partial + (size_t)b * a.nblk + k);
+    a.f_cur[b] = F;
+    if (!isfinite(F)) atomicExch(a.status, -6);
+    if (a.update) {
+        if (a.t < a.trace_cap) a.f_trace[(size_t)b * a.trace_cap + a.t] = F;
+        if (a.rel_tol > 0.0 && a.t > 0 && a.t - 1 < a.trace_cap && a.done != nullptr) {
+            const double Fp = a.f_trace[(size_t)b * a.trace_cap + a.t - 1];
+            if (fabs(F - Fp) <= a.rel_tol * fabs(F)) a.done[b] = a.t + 1;
+        }
+    }
+    a.counter[b] = 0u;
+}
+
+// max over variables of the summed |w| of the adjacency lists (for the
+// step bound); scratch word as float bits (non-negative floats order as uints)
+__global__ void sparse_degree_kernel(const int *ptr, const float *w, int N, unsigned *out_bits) {
+    float best = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        float d = 0.f;
+        for (int e = ptr[i]; e < ptr[i + 1]; ++e) d += fabsf(w[e]);
+        best = fmaxf(best, d);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out_bits, __float_as_uint(best));
+}
+
+}  // namespace
+
+int sparse_blocks(int N) { return (N + kSW - 1) / kSW; }
+
+cudaError_t launch_sparse_step(const SparseStepLaunch &a, cudaStream_t st) {
+    dim3 grid(sparse_blocks(a.N), a.B);
+    sparse_step_kernel<<<grid, kST, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_degree(const int *ptr, const float *w, int N, unsigned *out_bits, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out_bits, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    sparse_degree_kernel<<<std::min((N + 255) / 256, 1024), 256, 0, st>>>(ptr, w, N, out_bits);
+    return cudaGetLastError();
+}
+
+}  // namespace proxmf

@@ -174,6 +174,35 @@ def unrolled_batch(B: int = 16, H: int = 256, W: int = 256, L: int = 21, conn: i
                 seed=seed)
 
 
+def random_graph(N: int, n_edges: int, L: int, seed: int, symmetric: bool = True,
+                 coupling_scale: float = 1.0) -> dict:
+    """General pairwise graph: n_edges oriented edges between distinct random
+    variables, weights U(0.2, 1), random (a)symmetric mu, random unaries."""
+    rng = np.random.default_rng(seed)
+    src = rng.integers(0, N, n_edges)
+    dst = (src + rng.integers(1, N, n_edges)) % N
+    w = rng.uniform(0.2, 1.0, n_edges)
+    m = symmetric_uniform(L, rng) if symmetric else rng.uniform(-1.0, 1.0, size=(L, L))
+    U = unary_from_logits(rng.normal(0.0, 2.0, size=(N, L)))
+    return dict(kind="sparse", N=N, L=L, U=_f32(U), mu=_f32(coupling_scale * m),
+                src=src.astype(np.int32), dst=dst.astype(np.int32), w=_f32(w), seed=seed)
+
+
+def dbn_layers(n_top: int = 256, n_bottom: int = 512, fan: int = 32, L: int = 2, seed: int = 11) -> dict:
+    """Bipartite graph shaped like the layers of a deep belief network: each
+    top variable connects to `fan` random bottom variables (weights U(0.2,1)),
+    Potts-like symmetric coupling, random unaries."""
+    rng = np.random.default_rng(seed)
+    src = np.repeat(np.arange(n_top), fan)
+    dst = np.concatenate([n_top + rng.choice(n_bottom, fan, replace=False) for _ in range(n_top)])
+    w = rng.uniform(0.2, 1.0, src.size)
+    N = n_top + n_bottom
+    U = unary_from_logits(rng.normal(0.0, 1.0, size=(N, L)))
+    m = 0.3 * symmetric_uniform(L, rng)
+    return dict(kind="sparse", N=N, L=L, U=_f32(U), mu=_f32(m), src=src.astype(np.int32),
+                dst=dst.astype(np.int32), w=_f32(w), seed=seed)
+
+
 def random_grid(H: int, W: int, L: int, conn: int, seed: int, symmetric: bool = True,
                 coupling_scale: float = 1.0, unary_scale: float = 2.0) -> dict:
     """Generic test instance: random unaries, random (a)symmetric mu, random w."""
