@@ -30,6 +30,7 @@ struct crf_s {
     bool sparse = false;
     int *sp_out_ptr = nullptr, *sp_out_col = nullptr, *sp_in_ptr = nullptr, *sp_in_col = nullptr;
     float *sp_out_w = nullptr, *sp_in_w = nullptr;
+    double *sp_nu = nullptr;     // [2] extreme eigenvalues of C mu C
     // fully connected model
     bool dense = false;
     int N = 0;                   // variables per instance
@@ -131,6 +132,7 @@ void free_all(crf_t h) {
     for (int *p : ip)
         if (p) cudaFree(p);
     if (h->sp_out_w) cudaFree(h->sp_out_w);
+    if (h->sp_nu) cudaFree(h->sp_nu);
     if (h->sp_in_w) cudaFree(h->sp_in_w);
     float *fd[] = {h->K32, h->q32[0], h->q32[1], h->feats, h->mu_dev};
     for (float *p : fd)
@@ -544,6 +546,7 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
     ok = ok && dalloc(&h->s[1], n_padded(h)) == cudaSuccess;
     ok = ok && dalloc(&h->w, n_pix(h) * h->nd) == cudaSuccess;
     if (sparse) {
+        ok = ok && dalloc(&h->sp_nu, 2) == cudaSuccess;
         ok = ok && dalloc(&h->q32[0], n_padded(h)) == cudaSuccess;
         ok = ok && dalloc(&h->q32[1], n_padded(h)) == cudaSuccess;
     }
@@ -759,14 +762,22 @@ crf_status crf_set_graph(crf_t h, const float *mu, int64_t n_edges, const int32_
     const size_t LL = (size_t)h->L * h->L, E = (size_t)n_edges;
     std::vector<float> m(LL), wv(E);
     std::vector<int32_t> sv(E), dv(E);
-    const cudaMemcpyKind k = is_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-    CK(h, cudaMemcpyAsync(m.data(), mu, LL * sizeof(float), k, h->st));
-    if (E) {
-        CK(h, cudaMemcpyAsync(sv.data(), src, E * sizeof(int32_t), k, h->st));
-        CK(h, cudaMemcpyAsync(dv.data(), dst, E * sizeof(int32_t), k, h->st));
-        CK(h, cudaMemcpyAsync(wv.data(), w, E * sizeof(float), k, h->st));
+    if (is_device) {
+        CK(h, cudaMemcpyAsync(m.data(), mu, LL * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+        if (E) {
+            CK(h, cudaMemcpyAsync(sv.data(), src, E * sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
+            CK(h, cudaMemcpyAsync(dv.data(), dst, E * sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
+            CK(h, cudaMemcpyAsync(wv.data(), w, E * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+        }
+        CK(h, cudaStreamSynchronize(h->st));
+    } else {
+        std::memcpy(m.data(), mu, LL * sizeof(float));
+        if (E) {
+            std::memcpy(sv.data(), src, E * sizeof(int32_t));
+            std::memcpy(dv.data(), dst, E * sizeof(int32_t));
+            std::memcpy(wv.data(), w, E * sizeof(float));
+        }
     }
-    CK(h, cudaStreamSynchronize(h->st));
     for (float v : m)
         if (!std::isfinite(v)) return CRF_E_INVALID;
     for (size_t e = 0; e < E; ++e)
@@ -798,8 +809,8 @@ crf_status crf_set_graph(crf_t h, const float *mu, int64_t n_edges, const int32_
     }
     double nu[2] = {0.0, 0.0};
     if (sym) {
-        CK(h, launch_mu_tilde_extremes(h->mu_dev, h->L, h->Lambda, h->st));
-        CK(h, cudaMemcpyAsync(nu, h->Lambda, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        CK(h, launch_mu_tilde_extremes(h->mu_dev, h->L, h->sp_nu, h->st));
+        CK(h, cudaMemcpyAsync(nu, h->sp_nu, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     }
     CK(h, cudaMemsetAsync(h->counter, 0, h->B * sizeof(unsigned), h->st));
     CK(h, cudaStreamSynchronize(h->st));
