@@ -274,10 +274,19 @@ __global__ void __launch_bounds__(kDT, 1) dense_step_f32_kernel(const __grid_con
     }
     __syncthreads();
     if (!is_last) return;
+    // last block of the instance: all threads sum fixed strided subsets of
+    // the partials, then a fixed-shape tree (deterministic)
     __threadfence();
+    double acc = 0.0;
+    for (int k = tid; k < a.nblk; k += kDT) acc += __ldcg(a.partial + (size_t)b * a.nblk + k);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    __syncthreads();   // red is reused
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
     if (tid == 0) {
         double F = 0.0;
-        for (int k = 0; k < a.nblk; ++k) F += __ldcg(a.partial + (size_t)b * a.nblk + k);
+        for (int k = 0; k < kDT / 32; ++k) F += red[k];
         a.f_cur[b] = F;
         if (!isfinite(F)) atomicExch(a.status, -6);
         if (a.update) {

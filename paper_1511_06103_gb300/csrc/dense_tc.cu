@@ -227,10 +227,20 @@ dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmK, const __grid_const
         is_last = atomicAdd(a.counter + b, 1u) == (unsigned)(a.ntiles - 1);
     }
     __syncthreads();
-    if (!is_last || tid != 0) return;
+    if (!is_last) return;
+    // last tile of the instance: all threads sum fixed strided subsets of the
+    // partials, then a fixed-shape tree (deterministic)
     __threadfence();
+    double acc = 0.0;
+    for (int k = tid; k < a.ntiles; k += kThreads) acc += __ldcg(a.partial + (size_t)b * a.ntiles + k);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    __syncthreads();   // red is reused
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (tid != 0) return;
     double F = 0.0;
-    for (int k = 0; k < a.ntiles; ++k) F += __ldcg(a.partial + (size_t)b * a.ntiles + k);
+    for (int k = 0; k < kThreads / 32; ++k) F += red[k];
     a.f_cur[b] = F;
     if (!isfinite(F)) atomicExch(a.status, -6);
     if (a.update) {

@@ -104,10 +104,20 @@ __global__ void __launch_bounds__(kST) sparse_step_kernel(const SparseStepLaunch
         is_last = atomicAdd(a.counter + b, 1u) == (unsigned)(a.nblk - 1);
     }
     __syncthreads();
-    if (!is_last || threadIdx.x != 0) return;
+    if (!is_last) return;
+    // last block of the instance: all threads reduce the partials, each a
+    // fixed strided subset, then a fixed-shape tree
     __threadfence();
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < a.nblk; k += kST) acc += __ldcg(a.partial + (size_t)b * a.nblk + k);
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, w);
+    __syncthreads();   // red is reused
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     double F = 0.0;
-    for (int k = 0; k < a.nblk; ++k) F += __ldcg(a.partial + (size_t)b * a.nblk + k);
+    for (int k = 0; k < kSW; ++k) F += red[k];
     a.f_cur[b] = F;
     if (!isfinite(F)) atomicExch(a.status, -6);
     if (a.update) {
