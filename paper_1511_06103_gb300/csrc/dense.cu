@@ -277,12 +277,12 @@ __global__ void __launch_bounds__(kDT, 1) dense_step_f32_kernel(const __grid_con
     // last block of the instance: all threads sum fixed strided subsets of
     // the partials, then a fixed-shape tree (deterministic)
     __threadfence();
-    double acc = 0.0;
-    for (int k = tid; k < a.nblk; k += kDT) acc += __ldcg(a.partial + (size_t)b * a.nblk + k);
+    double tot = 0.0;
+    for (int k = tid; k < a.nblk; k += kDT) tot += __ldcg(a.partial + (size_t)b * a.nblk + k);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    for (int off = 16; off > 0; off >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, off);
     __syncthreads();   // red is reused
-    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    if ((tid & 31) == 0) red[tid >> 5] = tot;
     __syncthreads();
     if (tid == 0) {
         double F = 0.0;
