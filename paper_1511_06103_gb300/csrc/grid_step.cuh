@@ -603,12 +603,8 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, co
 // and every broadcast load of a mu column pair feeds both L x L products.
 // Shared-memory traffic per pixel drops by about a third against one pixel
 // per thread, which the shared-memory pipe bounds.
-// One 32 x 8 tile of one instance on a 32 x 4 CTA (two pixels per thread):
-// a1-a4 for its pixels (state written when j.update), and the tile's FP64
-// free-energy partial, returned in thread 0.  All threads of the CTA must
-// call it; it may be called repeatedly by a persistent CTA.
 template <int LT, int CONN>
-__device__ __forceinline__ double grid_tile_pair(const TileJob &j, int bx, int by) {
+__global__ void __launch_bounds__(GT / 2, 3) grid_pair_kernel(const __grid_constant__ GridStepArgs a) {
     constexpr int LP = storage_labels(LT);
     constexpr int NP = (LT + 1) / 2;
     constexpr int NPP = (NP + 1) / 2 * 2;
@@ -622,23 +618,40 @@ __device__ __forceinline__ double grid_tile_pair(const TileJob &j, int bx, int b
     __shared__ __align__(16) float sown[GT * LS];
     __shared__ __align__(16) float2 mus[LT * NPP];
     __shared__ double red[NT / 32];
+    __shared__ int is_last;
 
+    const int b = blockIdx.z;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * GX + tx;
-    const int H = j.H, W = j.W, L = j.L;
-    const int x0 = bx * GX, y0 = by * GY;
+    const int H = a.H, W = a.W, L = a.L;
+    const size_t N = (size_t)H * W;
+    const size_t ib = (size_t)b * N;
+    const int x0 = blockIdx.x * GX, y0 = blockIdx.y * GY;
     const int x = x0 + tx;
     const int ya = y0 + 2 * ty;                     // pixel a; pixel b = ya + 1
     const bool in_a = x < W && ya < H, in_b = x < W && ya + 1 < H;
     const size_t pa = (size_t)ya * W + x, pb = pa + W;
 
-    __syncthreads();   // shared memory of a previous tile is no longer read
-    for (int i = tid; i < LT * NPP; i += NT) mus[i] = j.mu_out[i];
+    if (a.done != nullptr && a.done[b] != 0) {
+        if (a.update) {
+            float2 v[LP / 2];
+            if (in_a) {
+                load_px<LP>(v, a.s_in + (ib + pa) * LP);
+                store_px<LP>(a.s_out + (ib + pa) * LP, v);
+            }
+            if (in_b) {
+                load_px<LP>(v, a.s_in + (ib + pb) * LP);
+                store_px<LP>(a.s_out + (ib + pb) * LP, v);
+            }
+        }
+        return;
+    }
+    for (int i = tid; i < LT * NPP; i += NT) mus[i] = a.mu_out[i];
 
     // own log q of both pixels: q into the tile, log q kept in shared memory
     {
         float2 sv[LP / 2];
         if (in_a) {
-            load_px<LP>(sv, j.s_in + pa * LP);
+            load_px<LP>(sv, a.s_in + (ib + pa) * LP);
         } else {
 #pragma unroll
             for (int k = 0; k < LP / 2; ++k) sv[k] = splat2(kPadLogQ);
@@ -646,7 +659,7 @@ __device__ __forceinline__ double grid_tile_pair(const TileJob &j, int bx, int b
         put_cell<LP>(qt + ((2 * ty + 1) * TW + tx + 1) * LS, sv);
         store_px<LP>(sown + (2 * tid) * LS, sv);
         if (in_b) {
-            load_px<LP>(sv, j.s_in + pb * LP);
+            load_px<LP>(sv, a.s_in + (ib + pb) * LP);
         } else {
 #pragma unroll
             for (int k = 0; k < LP / 2; ++k) sv[k] = splat2(kPadLogQ);
@@ -670,7 +683,7 @@ __device__ __forceinline__ double grid_tile_pair(const TileJob &j, int bx, int b
         const int gy = y0 - 1 + hr, gx = x0 - 1 + hc;
         float2 h[LP / 2];
         if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-            load_px<LP>(h, j.s_in + ((size_t)gy * W + gx) * LP);
+            load_px<LP>(h, a.s_in + (ib + (size_t)gy * W + gx) * LP);
         } else {
 #pragma unroll
             for (int k = 0; k < LP / 2; ++k) h[k] = splat2(kPadLogQ);
@@ -683,7 +696,7 @@ __device__ __forceinline__ double grid_tile_pair(const TileJob &j, int bx, int b
     float woa[4] = {0.f, 0.f, 0.f, 0.f}, wia[4] = {0.f, 0.f, 0.f, 0.f};
     float wob[4] = {0.f, 0.f, 0.f, 0.f}, wib[4] = {0.f, 0.f, 0.f, 0.f};
     {
-        const float *wb = j.w;
+        const float *wb = a.w + ib * ND;
         auto weights = [&](bool in, size_t p, int yy, float *wo, float *wi) {
             if (!in) return;
             if (ND == 4) {
@@ -792,9 +805,9 @@ __device__ __forceinline__ double grid_tile_pair(const TileJob &j, int bx, int b
     }
 
     // a2-a4 for each pixel of the pair, and its free-energy term
-    const float eta_b = j.eta;
-    const bool adaptive = j.adaptive;
-    const float dd = j.adapt_d;
+    const float eta_b = a.eta[b];
+    const bool adaptive = a.adapt_d != nullptr;
+    const float dd = adaptive ? a.adapt_d[b] : 0.f;
     double fd = 0.0;
 #pragma unroll
     for (int which = 0; which < 2; ++which) {
@@ -814,7 +827,7 @@ __device__ __forceinline__ double grid_tile_pair(const TileJob &j, int bx, int b
             }
         }
         if (inside) {
-            load_px<LP>(u, j.U + p * LP);
+            load_px<LP>(u, a.U + (ib + p) * LP);
         } else {
 #pragma unroll
             for (int i = 0; i < LP / 2; ++i) u[i] = splat2(0.f);
@@ -842,7 +855,7 @@ __device__ __forceinline__ double grid_tile_pair(const TileJob &j, int bx, int b
 #pragma unroll
         for (int k = 0; k < NP; ++k) z += __expf(s[k].x - mx) + __expf(s[k].y - mx);
         const float2 nlse = splat2(-(mx + __logf(z)));
-        if (j.update && inside) {
+        if (a.update && inside) {
             float2 o[LP / 2];
 #pragma unroll
             for (int k = 0; k < LP / 2; ++k) {
@@ -855,66 +868,21 @@ __device__ __forceinline__ double grid_tile_pair(const TileJob &j, int bx, int b
                     o[k] = splat2(kPadLogQ);
                 }
             }
-            store_px<LP>(j.s_out + p * LP, o);
+            store_px<LP>(a.s_out + (ib + p) * LP, o);
         }
         if (inside) fd += (double)(f2.x + f2.y);
     }
 
-    // a5: F partial of the tile, FP64
+    // a5: F partial of the tile; the last tile of the instance reduces all
+    // partials in a fixed order
     fd = warp_sum_f64(fd);
     if ((tid & 31) == 0) red[tid >> 5] = fd;
     __syncthreads();
-    double bs = 0.0;
-    if (tid == 0) {
-#pragma unroll
-        for (int k = 0; k < NT / 32; ++k) bs += red[k];
-    }
-    return bs;
-}
-
-template <int LT, int CONN>
-__global__ void __launch_bounds__(GT / 2, 3) grid_pair_kernel(const __grid_constant__ GridStepArgs a) {
-    constexpr int LP = storage_labels(LT);
-    constexpr int ND = CONN == 8 ? 4 : 2;
-    constexpr int NT = GT / 2;
-    __shared__ double red[NT / 32];
-    __shared__ int is_last;
-    const int b = blockIdx.z;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * GX + tx;
-    const size_t N = (size_t)a.H * a.W;
-    const size_t ib = (size_t)b * N;
-    if (a.done != nullptr && a.done[b] != 0) {
-        // stopping rule met: carry the state through unchanged
-        if (a.update) {
-            const int x = blockIdx.x * GX + tx, ya = blockIdx.y * GY + 2 * ty;
-            float2 v[LP / 2];
-            for (int yy = ya; yy < ya + 2; ++yy)
-                if (x < a.W && yy < a.H) {
-                    const size_t p = (size_t)yy * a.W + x;
-                    load_px<LP>(v, a.s_in + (ib + p) * LP);
-                    store_px<LP>(a.s_out + (ib + p) * LP, v);
-                }
-        }
-        return;
-    }
-    TileJob j{};
-    j.s_in = a.s_in + ib * LP;
-    j.s_out = a.s_out + ib * LP;
-    j.U = a.U + ib * LP;
-    j.w = a.w + ib * ND;
-    j.mu_out = a.mu_out;
-    j.eta = a.eta[b];
-    j.adaptive = a.adapt_d != nullptr;
-    j.adapt_d = j.adaptive ? a.adapt_d[b] : 0.f;
-    j.L = a.L;
-    j.H = a.H;
-    j.W = a.W;
-    j.update = a.update;
-    const double bs = grid_tile_pair<LT, CONN>(j, blockIdx.x, blockIdx.y);
-
-    // the last tile of the instance reduces all partials in a fixed order
     const int blk = blockIdx.y * a.nbx + blockIdx.x;
     if (tid == 0) {
+        double bs = 0.0;
+#pragma unroll
+        for (int k = 0; k < NT / 32; ++k) bs += red[k];
         a.partial[(size_t)b * a.nblk + blk] = bs;
         __threadfence();
         const unsigned prev = atomicAdd(a.counter + b, 1u);
@@ -926,6 +894,7 @@ __global__ void __launch_bounds__(GT / 2, 3) grid_pair_kernel(const __grid_const
     double acc = 0.0;
     for (int k = tid; k < a.nblk; k += NT) acc += __ldcg(a.partial + (size_t)b * a.nblk + k);
     acc = warp_sum_f64(acc);
+    __syncthreads();
     if ((tid & 31) == 0) red[tid >> 5] = acc;
     __syncthreads();
     if (tid == 0) {

@@ -45,15 +45,11 @@ struct ServeBucket {
     int prefix[kMaxServeSlots + 1];   // tile offsets
 };
 
-// Symmetric mu runs the two-pixels-per-thread tile on 32 x 4 threads, the
-// same tile and reduction shapes as a single-instance solve, so that a
-// request's result does not depend on where it is solved.
 template <int LT, int CONN, bool SYM>
-__global__ void __launch_bounds__(SYM ? GT / 2 : GT, SYM ? 3 : ((LT >= 24) ? 1 : 2))
+__global__ void __launch_bounds__(GT, (LT >= 24) ? 1 : 2)
 serve_step_kernel(ServeSlot *slots, const ServeBucket *bucket, ServeResult *results) {
-    constexpr int NTH = SYM ? GT / 2 : GT;
     __shared__ int sh_slot, sh_local, sh_last;
-    __shared__ double red[NTH / 32];
+    __shared__ double red[GT / 32];
     const int tid = threadIdx.y * GX + threadIdx.x;
     const int count = bucket->count;
     const int total = bucket->prefix[count];
@@ -87,11 +83,7 @@ serve_step_kernel(ServeSlot *slots, const ServeBucket *bucket, ServeResult *resu
         j.H = sl.H;
         j.W = sl.W;
         j.update = 1;
-        double bs;
-        if constexpr (SYM)
-            bs = grid_tile_pair<LT, CONN>(j, local % sl.nbx, local / sl.nbx);
-        else
-            bs = grid_tile<LT, CONN, SYM>(j, local % sl.nbx, local / sl.nbx);
+        const double bs = grid_tile<LT, CONN, SYM>(j, local % sl.nbx, local / sl.nbx);
         if (tid == 0) {
             sl.partial[local] = bs;
             __threadfence();
@@ -101,14 +93,14 @@ serve_step_kernel(ServeSlot *slots, const ServeBucket *bucket, ServeResult *resu
         if (sh_last) {
             __threadfence();
             double acc = 0.0;
-            for (int k = tid; k < sl.nblk; k += NTH) acc += __ldcg(sl.partial + k);
+            for (int k = tid; k < sl.nblk; k += GT) acc += __ldcg(sl.partial + k);
             acc = warp_sum_f64(acc);
             if ((tid & 31) == 0) red[tid >> 5] = acc;
             __syncthreads();
             if (tid == 0) {
                 double F = 0.0;
 #pragma unroll
-                for (int k = 0; k < NTH / 32; ++k) F += red[k];
+                for (int k = 0; k < GT / 32; ++k) F += red[k];
                 *sl.counter = 0u;
                 const int nit = it + 1;
                 bool stop = nit >= sl.max_iters || !isfinite(F);
@@ -134,15 +126,15 @@ serve_step_kernel(ServeSlot *slots, const ServeBucket *bucket, ServeResult *resu
 template <int LT>
 cudaError_t launch_serve_lt(int conn, bool sym, ServeSlot *slots, const ServeBucket *bucket, ServeResult *res,
                             int grid, cudaStream_t st) {
-    dim3 block(GX, GY, 1), pblock(GX, GY / 2, 1);
+    dim3 block(GX, GY, 1);
     if (conn == 8) {
         if (sym)
-            serve_step_kernel<LT, 8, true><<<grid, pblock, 0, st>>>(slots, bucket, res);
+            serve_step_kernel<LT, 8, true><<<grid, block, 0, st>>>(slots, bucket, res);
         else
             serve_step_kernel<LT, 8, false><<<grid, block, 0, st>>>(slots, bucket, res);
     } else {
         if (sym)
-            serve_step_kernel<LT, 4, true><<<grid, pblock, 0, st>>>(slots, bucket, res);
+            serve_step_kernel<LT, 4, true><<<grid, block, 0, st>>>(slots, bucket, res);
         else
             serve_step_kernel<LT, 4, false><<<grid, block, 0, st>>>(slots, bucket, res);
     }
