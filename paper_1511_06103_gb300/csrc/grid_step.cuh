@@ -593,327 +593,6 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, co
     return bs;
 }
 
-// ---------------------------------------------------------------------------
-// Two pixels per thread (FP32 form, symmetric mu, fixed / adaptive rule).
-//
-// A CTA of 32 x 4 threads covers the same 32 x 8 tile; thread (tx, ty)
-// owns the vertically adjacent pixels (2 ty, tx) and (2 ty + 1, tx).  The
-// pair's neighbourhoods overlap: its 12 staged cells (rows 2ty-1 .. 2ty+2,
-// columns tx-1 .. tx+1) are each read once and feed both neighbour sums,
-// and every broadcast load of a mu column pair feeds both L x L products.
-// Shared-memory traffic per pixel drops by about a third against one pixel
-// per thread, which the shared-memory pipe bounds.
-template <int LT, int CONN>
-__global__ void __launch_bounds__(GT / 2, 3) grid_pair_kernel(const __grid_constant__ GridStepArgs a) {
-    constexpr int LP = storage_labels(LT);
-    constexpr int NP = (LT + 1) / 2;
-    constexpr int NPP = (NP + 1) / 2 * 2;
-    constexpr int ND = CONN == 8 ? 4 : 2;
-    constexpr int LS = tile_stride(LP);
-    constexpr int TW = GX + 2;
-    constexpr int HALO = 2 * TW + 2 * GY;
-    constexpr int NT = GT / 2;
-    constexpr bool MASK = (LT == LP);
-    __shared__ __align__(16) float qt[(GY + 2) * TW * LS];
-    __shared__ __align__(16) float sown[GT * LS];
-    __shared__ __align__(16) float2 mus[LT * NPP];
-    __shared__ double red[NT / 32];
-    __shared__ int is_last;
-
-    const int b = blockIdx.z;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * GX + tx;
-    const int H = a.H, W = a.W, L = a.L;
-    const size_t N = (size_t)H * W;
-    const size_t ib = (size_t)b * N;
-    const int x0 = blockIdx.x * GX, y0 = blockIdx.y * GY;
-    const int x = x0 + tx;
-    const int ya = y0 + 2 * ty;                     // pixel a; pixel b = ya + 1
-    const bool in_a = x < W && ya < H, in_b = x < W && ya + 1 < H;
-    const size_t pa = (size_t)ya * W + x, pb = pa + W;
-
-    if (a.done != nullptr && a.done[b] != 0) {
-        if (a.update) {
-            float2 v[LP / 2];
-            if (in_a) {
-                load_px<LP>(v, a.s_in + (ib + pa) * LP);
-                store_px<LP>(a.s_out + (ib + pa) * LP, v);
-            }
-            if (in_b) {
-                load_px<LP>(v, a.s_in + (ib + pb) * LP);
-                store_px<LP>(a.s_out + (ib + pb) * LP, v);
-            }
-        }
-        return;
-    }
-    for (int i = tid; i < LT * NPP; i += NT) mus[i] = a.mu_out[i];
-
-    // own log q of both pixels: q into the tile, log q kept in shared memory
-    {
-        float2 sv[LP / 2];
-        if (in_a) {
-            load_px<LP>(sv, a.s_in + (ib + pa) * LP);
-        } else {
-#pragma unroll
-            for (int k = 0; k < LP / 2; ++k) sv[k] = splat2(kPadLogQ);
-        }
-        put_cell<LP>(qt + ((2 * ty + 1) * TW + tx + 1) * LS, sv);
-        store_px<LP>(sown + (2 * tid) * LS, sv);
-        if (in_b) {
-            load_px<LP>(sv, a.s_in + (ib + pb) * LP);
-        } else {
-#pragma unroll
-            for (int k = 0; k < LP / 2; ++k) sv[k] = splat2(kPadLogQ);
-        }
-        put_cell<LP>(qt + ((2 * ty + 2) * TW + tx + 1) * LS, sv);
-        store_px<LP>(sown + (2 * tid + 1) * LS, sv);
-    }
-    if (tid < HALO) {
-        int hr, hc;
-        if (tid < TW) {
-            hr = 0;
-            hc = tid;
-        } else if (tid < 2 * TW) {
-            hr = GY + 1;
-            hc = tid - TW;
-        } else {
-            const int k = tid - 2 * TW;
-            hr = 1 + (k >> 1);
-            hc = (k & 1) ? TW - 1 : 0;
-        }
-        const int gy = y0 - 1 + hr, gx = x0 - 1 + hc;
-        float2 h[LP / 2];
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-            load_px<LP>(h, a.s_in + (ib + (size_t)gy * W + gx) * LP);
-        } else {
-#pragma unroll
-            for (int k = 0; k < LP / 2; ++k) h[k] = splat2(kPadLogQ);
-        }
-        put_cell<LP>(qt + (hr * TW + hc) * LS, h);
-    }
-
-    // edge weights: wo leaving the pixel, wi entering it (stored at the
-    // pixel that owns the edge); direction 0 right, 1 down, 2 down-right, 3 down-left
-    float woa[4] = {0.f, 0.f, 0.f, 0.f}, wia[4] = {0.f, 0.f, 0.f, 0.f};
-    float wob[4] = {0.f, 0.f, 0.f, 0.f}, wib[4] = {0.f, 0.f, 0.f, 0.f};
-    {
-        const float *wb = a.w + ib * ND;
-        auto weights = [&](bool in, size_t p, int yy, float *wo, float *wi) {
-            if (!in) return;
-            if (ND == 4) {
-                const float4 t = __ldg(reinterpret_cast<const float4 *>(wb + p * ND));
-                wo[0] = t.x;
-                wo[1] = t.y;
-                wo[2] = t.z;
-                wo[3] = t.w;
-            } else {
-                const float2 t = __ldg(reinterpret_cast<const float2 *>(wb + p * ND));
-                wo[0] = t.x;
-                wo[1] = t.y;
-            }
-            if (x > 0) wi[0] = __ldg(wb + (p - 1) * ND + 0);
-            if (yy > 0) wi[1] = __ldg(wb + (p - W) * ND + 1);
-            if (CONN == 8) {
-                if (x > 0 && yy > 0) wi[2] = __ldg(wb + (p - W - 1) * ND + 2);
-                if (x + 1 < W && yy > 0) wi[3] = __ldg(wb + (p - W + 1) * ND + 3);
-            }
-        };
-        weights(in_a, pa, ya, woa, wia);
-        weights(in_b, pb, ya + 1, wob, wib);
-    }
-    __syncthreads();
-
-    // a1: neighbour sums over the pair's 12 cells (rows r = -1..2 relative to
-    // pixel a, columns c = -1..1); weight of cell (r, c) for pixel a and b
-    float2 Sa[NP], Sb[NP], qa[NP], qb[NP];
-#pragma unroll
-    for (int k = 0; k < NP; ++k) Sa[k] = Sb[k] = splat2(0.f);
-#pragma unroll
-    for (int r = -1; r <= 2; ++r) {
-#pragma unroll
-        for (int c = -1; c <= 1; ++c) {
-            // pixel a = (0, 0): right (0,1) wo0, down (1,0) wo1, dr (1,1) wo2, dl (1,-1) wo3,
-            // left (0,-1) wi0, up (-1,0) wi1, ul (-1,-1) wi2, ur (-1,1) wi3
-            auto wt = [&](int rr, int cc, const float *wo, const float *wi) -> float {
-                if (rr == 0 && cc == 1) return wo[0];
-                if (rr == 1 && cc == 0) return wo[1];
-                if (rr == 0 && cc == -1) return wi[0];
-                if (rr == -1 && cc == 0) return wi[1];
-                if (CONN == 8) {
-                    if (rr == 1 && cc == 1) return wo[2];
-                    if (rr == 1 && cc == -1) return wo[3];
-                    if (rr == -1 && cc == -1) return wi[2];
-                    if (rr == -1 && cc == 1) return wi[3];
-                }
-                return 0.f;
-            };
-            const bool use_a = (r >= -1 && r <= 1) && !(r == 0 && c == 0) && (CONN == 8 || r == 0 || c == 0);
-            const bool use_b = (r >= 0 && r <= 2) && !(r == 1 && c == 0) && (CONN == 8 || r == 1 || c == 0);
-            const bool own_a = (r == 0 && c == 0), own_b = (r == 1 && c == 0);
-            if (!use_a && !use_b && !own_a && !own_b) continue;
-            const float *cell = qt + ((2 * ty + 1 + r) * TW + tx + 1 + c) * LS;
-            float2 v[NP];
-            if constexpr (NP == 1) {
-                v[0] = *reinterpret_cast<const float2 *>(cell);
-            } else {
-#pragma unroll
-                for (int i = 0; i < (NP + 1) / 2; ++i) {
-                    const float4 t = reinterpret_cast<const float4 *>(cell)[i];
-                    v[2 * i] = make_float2(t.x, t.y);
-                    if (2 * i + 1 < NP) v[2 * i + 1] = make_float2(t.z, t.w);
-                }
-            }
-            if (own_a) {
-#pragma unroll
-                for (int k = 0; k < NP; ++k) qa[k] = v[k];
-            }
-            if (own_b) {
-#pragma unroll
-                for (int k = 0; k < NP; ++k) qb[k] = v[k];
-            }
-            if (use_a) {
-                const float2 w2 = splat2(wt(r, c, woa, wia));
-#pragma unroll
-                for (int k = 0; k < NP; ++k) Sa[k] = fma2(w2, v[k], Sa[k]);
-            }
-            if (use_b) {
-                const float2 w2 = splat2(wt(r - 1, c, wob, wib));
-#pragma unroll
-                for (int k = 0; k < NP; ++k) Sb[k] = fma2(w2, v[k], Sb[k]);
-            }
-        }
-    }
-    // the L x L product for both pixels, one broadcast load per mu column pair
-    float2 ma[NP], mb[NP];
-#pragma unroll
-    for (int k = 0; k < NP; ++k) ma[k] = mb[k] = splat2(0.f);
-#pragma unroll
-    for (int k = 0; k < LT; ++k) {
-        const float2 sa = splat2((k & 1) ? Sa[k >> 1].y : Sa[k >> 1].x);
-        const float2 sb = splat2((k & 1) ? Sb[k >> 1].y : Sb[k >> 1].x);
-        const float4 *col = reinterpret_cast<const float4 *>(mus + k * NPP);
-#pragma unroll
-        for (int i = 0; i < (NP + 1) / 2; ++i) {
-            const float4 t = col[i];
-            const float2 c0 = make_float2(t.x, t.y), c1 = make_float2(t.z, t.w);
-            ma[2 * i] = fma2(c0, sa, ma[2 * i]);
-            mb[2 * i] = fma2(c0, sb, mb[2 * i]);
-            if (2 * i + 1 < NP) {
-                ma[2 * i + 1] = fma2(c1, sa, ma[2 * i + 1]);
-                mb[2 * i + 1] = fma2(c1, sb, mb[2 * i + 1]);
-            }
-        }
-    }
-
-    // a2-a4 for each pixel of the pair, and its free-energy term
-    const float eta_b = a.eta[b];
-    const bool adaptive = a.adapt_d != nullptr;
-    const float dd = adaptive ? a.adapt_d[b] : 0.f;
-    double fd = 0.0;
-#pragma unroll
-    for (int which = 0; which < 2; ++which) {
-        const bool inside = which ? in_b : in_a;
-        const size_t p = which ? pb : pa;
-        const float2 *m = which ? mb : ma;
-        const float2 *qc = which ? qb : qa;
-        float2 s[LP / 2], u[LP / 2];
-        if constexpr (LP == 2) {
-            s[0] = *reinterpret_cast<const float2 *>(sown + (2 * tid + which) * LS);
-        } else {
-#pragma unroll
-            for (int i = 0; i < LP / 4; ++i) {
-                const float4 v = reinterpret_cast<const float4 *>(sown + (2 * tid + which) * LS)[i];
-                s[2 * i] = make_float2(v.x, v.y);
-                s[2 * i + 1] = make_float2(v.z, v.w);
-            }
-        }
-        if (inside) {
-            load_px<LP>(u, a.U + (ib + p) * LP);
-        } else {
-#pragma unroll
-            for (int i = 0; i < LP / 2; ++i) u[i] = splat2(0.f);
-        }
-        float eta = eta_b;
-        if constexpr (LT == 2) {
-            if (adaptive) eta = 1.f / fmaf(dd * qc[0].x, qc[0].y, 1.f);
-        }
-        const float2 neta = splat2(-eta), ome = splat2(1.f - eta), half = splat2(0.5f);
-        float2 f2 = splat2(0.f);
-        float mx = -INFINITY;
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            const float2 g = add2(u[k], m[k]);
-            const float2 h = add2(fma2(half, m[k], u[k]), s[k]);
-            f2 = fma2(qc[k], h, f2);
-            float2 av = fma2(neta, g, mul2(ome, s[k]));
-            const int l0 = 2 * k, l1 = 2 * k + 1;
-            if ((MASK && l0 >= L)) av.x = -INFINITY;
-            if ((MASK && l1 >= L) || l1 >= LT) av.y = -INFINITY;
-            s[k] = av;
-            mx = fmaxf(mx, fmaxf(av.x, av.y));
-        }
-        float z = 0.f;
-#pragma unroll
-        for (int k = 0; k < NP; ++k) z += __expf(s[k].x - mx) + __expf(s[k].y - mx);
-        const float2 nlse = splat2(-(mx + __logf(z)));
-        if (a.update && inside) {
-            float2 o[LP / 2];
-#pragma unroll
-            for (int k = 0; k < LP / 2; ++k) {
-                if (k < NP) {
-                    o[k] = add2(s[k], nlse);
-                    const int l0 = 2 * k, l1 = 2 * k + 1;
-                    if ((MASK && l0 >= L)) o[k].x = kPadLogQ;
-                    if ((MASK && l1 >= L) || l1 >= LT) o[k].y = kPadLogQ;
-                } else {
-                    o[k] = splat2(kPadLogQ);
-                }
-            }
-            store_px<LP>(a.s_out + (ib + p) * LP, o);
-        }
-        if (inside) fd += (double)(f2.x + f2.y);
-    }
-
-    // a5: F partial of the tile; the last tile of the instance reduces all
-    // partials in a fixed order
-    fd = warp_sum_f64(fd);
-    if ((tid & 31) == 0) red[tid >> 5] = fd;
-    __syncthreads();
-    const int blk = blockIdx.y * a.nbx + blockIdx.x;
-    if (tid == 0) {
-        double bs = 0.0;
-#pragma unroll
-        for (int k = 0; k < NT / 32; ++k) bs += red[k];
-        a.partial[(size_t)b * a.nblk + blk] = bs;
-        __threadfence();
-        const unsigned prev = atomicAdd(a.counter + b, 1u);
-        is_last = (prev == (unsigned)(a.nblk - 1));
-    }
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    double acc = 0.0;
-    for (int k = tid; k < a.nblk; k += NT) acc += __ldcg(a.partial + (size_t)b * a.nblk + k);
-    acc = warp_sum_f64(acc);
-    __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = acc;
-    __syncthreads();
-    if (tid == 0) {
-        double F = 0.0;
-#pragma unroll
-        for (int k = 0; k < NT / 32; ++k) F += red[k];
-        a.f_cur[b] = F;
-        if (!isfinite(F)) atomicExch(a.status, -6);
-        if (a.update) {
-            if (a.t < a.trace_cap) a.f_trace[(size_t)b * a.trace_cap + a.t] = F;
-            if (a.rel_tol > 0.0 && a.t > 0 && a.t - 1 < a.trace_cap && a.done != nullptr) {
-                const double Fp = a.f_trace[(size_t)b * a.trace_cap + a.t - 1];
-                if (fabs(F - Fp) <= a.rel_tol * fabs(F)) a.done[b] = a.t + 1;
-            }
-        }
-        a.counter[b] = 0u;
-    }
-}
-
 // Dynamic shared memory of the tensor-core form: q tile, A and B operands.
 template <int LT, bool SYM>
 struct GridTcSmem {
@@ -1113,14 +792,6 @@ cudaError_t launch_grid_step_lt(const GridStepLaunch &l, cudaStream_t st) {
         if (l.conn == 8)
             return l.mu_sym ? launch_grid_tc<LT, 8, true>(a, grid, block, st) : launch_grid_tc<LT, 8, false>(a, grid, block, st);
         return l.mu_sym ? launch_grid_tc<LT, 4, true>(a, grid, block, st) : launch_grid_tc<LT, 4, false>(a, grid, block, st);
-    }
-    if (l.mu_sym) {
-        const dim3 pblock(GX, GY / 2, 1);
-        if (l.conn == 8)
-            grid_pair_kernel<LT, 8><<<grid, pblock, 0, st>>>(a);
-        else
-            grid_pair_kernel<LT, 4><<<grid, pblock, 0, st>>>(a);
-        return cudaGetLastError();
     }
     if (l.conn == 8) {
         if (l.mu_sym)
