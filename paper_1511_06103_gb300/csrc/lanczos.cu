@@ -368,9 +368,15 @@ __device__ int sturm_count(const double *a, const double *c, int n, double x, do
 
 // Extreme eigenvalues of the Lanczos tridiagonal of each instance, by
 // multisection: warp 0 finds the largest, warp 1 the smallest; each round the
-// 32 lanes test 32 interior points of the bracket.
+// 32 lanes test 32 interior points of the bracket.  With have_prev, the
+// values in rmin / rmax come from a shorter tridiagonal of the same run: by
+// interlacing they bound the new extremes from inside (the largest can only
+// grow, the smallest only shrink), so the first round tests points at
+// geometrically growing distances beyond them, which brackets the new value
+// to about its change since the last check and saves most rounds of FP64
+// Sturm sequences.
 __global__ void lz_ritz_kernel(const double *alpha, const double *beta, int ld, int kcur, const int *stop,
-                               double *rmin, double *rmax) {
+                               int have_prev, double *rmin, double *rmax) {
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int n = kcur;
@@ -387,8 +393,31 @@ __global__ void lz_ritz_kernel(const double *alpha, const double *beta, int ld, 
     }
     const double pivmin = 1e-300 + amax * 1e-300;
     const bool want_max = wid == 0;
+    if (have_prev) {
+        const double prev = want_max ? rmax[b] : rmin[b];
+        if (isfinite(prev) && prev > lo && prev < hi) {
+            const double delta = fmax(fabs(prev), 1e-300) * 1e-14;
+            const double x = want_max ? prev + delta * ldexp(1.0, lane) : prev - delta * ldexp(1.0, lane);
+            const int cnt = sturm_count(a, c, n, x, pivmin);
+            // max: the extreme lies beyond x  <=>  cnt < n ; min: <=> cnt >= 1... (cnt < 1 below x)
+            const bool beyond = want_max ? (cnt < n) : (cnt >= 1);
+            const unsigned m = __ballot_sync(0xffffffffu, beyond);
+            const int nb = __popc(m);   // the extreme lies beyond the first nb points
+            const double inner = nb == 0 ? prev : (want_max ? prev + delta * ldexp(1.0, nb - 1)
+                                                             : prev - delta * ldexp(1.0, nb - 1));
+            const double outer = nb == 32 ? (want_max ? hi : lo)
+                                          : (want_max ? prev + delta * ldexp(1.0, nb) : prev - delta * ldexp(1.0, nb));
+            if (want_max) {
+                lo = inner;
+                hi = fmin(outer, hi);
+            } else {
+                hi = inner;
+                lo = fmax(outer, lo);
+            }
+        }
+    }
     for (int round = 0; round < 64; ++round) {
-        if (!(hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)) + 1e-300)) break;
+        if (!(hi - lo > 1e-14 * fmax(fabs(lo), fabs(hi)) + 1e-300)) break;
         const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
         const int cnt = sturm_count(a, c, n, x, pivmin);
         // max: lambda_max >= x  <=>  cnt < n ; min: lambda_min < x  <=>  cnt >= 1
@@ -402,6 +431,7 @@ __global__ void lz_ritz_kernel(const double *alpha, const double *beta, int ld, 
         lo = nlo;
         hi = nhi;
     }
+    __syncthreads();   // both warps have read their previous values
     if (lane == 0) {
         if (want_max)
             rmax[b] = 0.5 * (lo + hi);
@@ -570,9 +600,11 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;
+    cudaEvent_t ev_mu = nullptr, ev_nu = nullptr;
     std::vector<double> hmin(B), hmax(B), pmin(B, NAN), pmax(B, NAN);
     std::vector<int> hstop(B);
     int k = 0;
+    int have_prev = 0;   // the Ritz values of the previous check bound the next ones
     dim3 gridp(g.nblk, B);
     const int nblk_dense = (job.W + kLzThreads / 32 - 1) / (kLzThreads / 32);
     S.ld = ld;
@@ -621,11 +653,23 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
     }
     LZ_CHECK(cudaStreamEndCapture(cap, &graph));
     LZ_CHECK(cudaGraphInstantiate(&exec, graph, 0));
+    if (job.mu_sym) {
+        // the small eigen-solve of C mu C runs on the side stream, overlapped
+        // with the Lanczos steps (it only needs mu, copied above)
+        LZ_CHECK(cudaEventCreateWithFlags(&ev_mu, cudaEventDisableTiming));
+        LZ_CHECK(cudaEventCreateWithFlags(&ev_nu, cudaEventDisableTiming));
+        LZ_CHECK(cudaEventRecord(ev_mu, st));
+        LZ_CHECK(cudaStreamWaitEvent(cap, ev_mu, 0));
+        mu_tilde_extremes_kernel<<<1, 32, 0, cap>>>(mu_dev, job.L, nu);
+        LZ_CHECK(cudaGetLastError());
+        LZ_CHECK(cudaEventRecord(ev_nu, cap));
+    }
     while (k < kmax) {
         LZ_CHECK(cudaGraphLaunch(exec, st));
         nl += 2 * kChunk;
         k = std::min(k + kChunk, kmax);
-        lz_ritz_kernel<<<B, 64, 0, st>>>(S.alpha, S.nrm, ld, k, S.stop, rmin, rmax);
+        lz_ritz_kernel<<<B, 64, 0, st>>>(S.alpha, S.nrm, ld, k, S.stop, have_prev, rmin, rmax);
+        have_prev = 1;
         LZ_CHECK(cudaGetLastError());
         nl += 1;
         LZ_CHECK(cudaMemcpyAsync(hmin.data(), rmin, B * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -643,10 +687,7 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
         }
         if (all) break;
     }
-    if (job.mu_sym) {
-        mu_tilde_extremes_kernel<<<1, 32, 0, st>>>(mu_dev, job.L, nu);
-        LZ_CHECK(cudaGetLastError());
-    }
+    if (job.mu_sym) LZ_CHECK(cudaStreamWaitEvent(st, ev_nu, 0));
     lz_finalize_kernel<<<(B + 127) / 128, 128, 0, st>>>(rmin, rmax, nu, job.mu_sym ? 1 : 0, B, job.Lambda,
                                                       job.eta);
     LZ_CHECK(cudaGetLastError());
@@ -654,6 +695,8 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
     if (steps_out) *steps_out = k;
     if (launches_out) *launches_out = nl;
 done:
+    if (ev_mu) cudaEventDestroy(ev_mu);
+    if (ev_nu) cudaEventDestroy(ev_nu);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (cap) cudaStreamDestroy(cap);
