@@ -25,6 +25,7 @@ struct crf_s {
     float *s[2] = {nullptr, nullptr};  // [B][N][LP] log q, ping-pong, padding kPadLogQ
     float *w = nullptr;          // [B][N][nd] edge weights
     float2 *mu_pairs = nullptr;  // device [2][LT][NPP] mu column / row pairs
+    std::vector<float2> mu_pairs_host;   // host copy of the same
     uint8_t *mu_tc = nullptr;    // device BF16 operand images of mu, mu^T (grid, BF16 form)
     // general graph (edge list)
     bool sparse = false;
@@ -188,6 +189,7 @@ GridStepLaunch step_args(crf_t h, const float *eta, int t, int update, double re
     a.mu_out = h->mu_pairs;
     a.mu_in = h->mu_pairs + (size_t)h->LT * mu_pair_slots(h->LT);
     a.mu_tc = reinterpret_cast<const uint4 *>(h->mu_tc);
+    a.mu_host = h->mu_pairs_host.empty() ? nullptr : h->mu_pairs_host.data();
     a.adapt_d = (h->adapt_active || (update && h->rule_kernel == 2)) ? h->adapt_d : nullptr;
     a.rule = update ? h->rule_kernel : 0;
     a.mom = h->mom;
@@ -718,6 +720,7 @@ crf_status crf_set_pairwise(crf_t h, const float *mu, const float *w_or_feats, c
     build_mu_pairs(m, h->L, h->LT, pairs);
     CK(h, cudaMemcpyAsync(h->mu_pairs, pairs.data(), pairs.size() * sizeof(float2), cudaMemcpyHostToDevice,
                           h->st));
+    h->mu_pairs_host = pairs;
     CK(h, cudaMemcpyAsync(h->mu_dev, m.data(), LL * sizeof(float), cudaMemcpyHostToDevice, h->st));
     std::vector<uint8_t> img;
     if (h->bf16) {

@@ -55,6 +55,8 @@ struct GridStepLaunch {
     const float *eta;        // [B] step per instance
     const float2 *mu_out;    // device [LT][NPP] column pairs (see mu_pair_slots)
     const float2 *mu_in;     // device [LT][NPP] row pairs
+    const float2 *mu_host;   // host copy of the column pairs (first LT * mu_pair_slots(LT)); required
+                             // for symmetric mu with LT <= 21 (copied into the launch parameters)
     const uint4 *mu_tc;      // tensor-core form: device BF16 operand images of mu, mu^T
     bool tc;                 // BF16 tensor-core messages (else FP32)
     const float *adapt_d;    // [B] adaptive binary step: eta_i = 1/(1 + d q_i0 q_i1); null = fixed eta;

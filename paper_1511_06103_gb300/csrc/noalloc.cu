@@ -115,6 +115,7 @@ extern "C" crf_status mf_grid_step_noalloc(int32_t topology, int32_t n_labels, i
     a.eta = eta_dev;
     a.mu_out = mu_dev;
     a.mu_in = mu_dev + (size_t)LT * NPP;
+    a.mu_host = pairs;
     a.partial = partial;
     a.counter = counter;
     a.f_trace = F_out;   // never written: trace_cap = 0
