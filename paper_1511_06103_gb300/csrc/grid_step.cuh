@@ -224,7 +224,9 @@ struct TileJob {
 // j.update), and the tile's free-energy partial, returned in thread 0.
 // All threads of the block must call it; it may be called repeatedly by a
 // persistent block (shared memory is reused).
-template <int LT, int CONN, bool SYM, bool TC = false, int RULE = 0>
+// PMU: the L x L product reads mu from j.mu_p (the launch's parameter bank,
+// see mu_in_params) instead of shared memory.
+template <int LT, int CONN, bool SYM, bool TC = false, int RULE = 0, bool PMU = false>
 __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, const TcTile *tcx = nullptr) {
     constexpr int LP = storage_labels(LT);           // floats per pixel in HBM
     constexpr int NP = (LT + 1) / 2;                 // label pairs in the arithmetic
@@ -251,7 +253,7 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, co
     const float *sin = j.s_in;
     __syncthreads();   // shared memory of a previous tile is no longer read
 
-    constexpr bool kParamMu = mu_in_params<LT, SYM, TC, RULE>();
+    constexpr bool kParamMu = PMU;
     // mu pairs into shared memory
     for (int i = tid; !TC && !kParamMu && i < LT * NPP; i += GT) {
         mus[0][i] = j.mu_out[i];
@@ -688,7 +690,8 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
     j.H = a.H;
     j.W = a.W;
     j.update = a.update;
-    const double bs = grid_tile<LT, CONN, SYM, TC, RULE>(j, blockIdx.x, blockIdx.y, &tct);
+    const double bs =
+        grid_tile<LT, CONN, SYM, TC, RULE, mu_in_params<LT, SYM, TC, RULE>()>(j, blockIdx.x, blockIdx.y, &tct);
     if constexpr (TC) {
         // every thread's TMEM reads finished before the block sync inside grid_tile
         tc::fence_after_sync();
