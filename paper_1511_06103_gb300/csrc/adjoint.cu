@@ -98,7 +98,7 @@ __device__ __forceinline__ void cp_async_row(float *dst, const float *src, int s
 }
 
 template <int LT, int CONN, bool SYM>
-__global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(const __grid_constant__ AdjointStep a) {
+__global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep a) {
     using C = AdjCfg<LT>;
     constexpr int LP = C::LP, VW = C::VW, LS = C::LS, LSS = C::LSS, TX = C::TX, HX = C::HX, NT = C::NT;
     constexpr int NP = LP / 2;                             // label pairs
@@ -136,14 +136,11 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(const __gri
         }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
-    // symmetric mu comes in the parameter bank (constant-bank FMA operands);
-    // otherwise mu and mu^T are staged in shared memory
-    const float *mup = SYM ? a.mu_p : mus;
-    for (int i = tid; !SYM && i < LP * LP; i += NT) {
+    for (int i = tid; i < LP * LP; i += NT) {
         const int r = i / LP, c = i - r * LP;
         const float v = (r < L && c < L) ? a.mu[r * L + c] : 0.f;
         mus[i] = v;
-        muT[c * LP + r] = v;
+        if (!SYM) muT[c * LP + r] = v;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
@@ -195,7 +192,7 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(const __gri
 #pragma unroll
             for (int l = 0; l < LP; l += VW) {
                 float m[VW];
-                vget<VW>(mup + k * LP + l, m);
+                vget<VW>(mus + k * LP + l, m);
 #pragma unroll
                 for (int u = 0; u < VW; u += 2) {
                     const float2 m2 = make_float2(m[u], m[u + 1]);
@@ -286,7 +283,7 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(const __gri
 #pragma unroll
             for (int l = 0; l < LP; l += VW) {
                 float m[VW];
-                vget<VW>(mup + k * LP + l, m);
+                vget<VW>(mus + k * LP + l, m);
 #pragma unroll
                 for (int u = 0; u < VW; u += 2)
                     h[(l + u) / 2] = pfma(make_float2(m[u], m[u + 1]), gk, h[(l + u) / 2]);

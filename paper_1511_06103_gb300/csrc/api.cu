@@ -1235,13 +1235,6 @@ crf_status mf_unrolled_backward(crf_t h, int32_t K, double eta, const float *ckp
     a.W = h->W;
     a.conn = h->conn;
     a.mu_sym = h->mu_sym;
-    {
-        const int LPa = storage_labels(h->L);
-        for (int i = 0; i < kAdjMuParam; ++i) {
-            const int r = i / LPa, c = i % LPa;
-            a.mu_p[i] = (i < LPa * LPa && r < h->L && c < h->L) ? h->mu[(size_t)r * h->L + c] : 0.f;
-        }
-    }
     if (h->profile) CK(h, cudaEventRecord(h->ev0, h->st));
     for (int t = K - 1, c = 0; t >= 0; --t, c ^= 1) {
         a.gs_in = gsb[c];

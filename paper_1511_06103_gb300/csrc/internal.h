@@ -225,9 +225,7 @@ cudaError_t launch_sparse_degree(const int *ptr, const float *w, int N, unsigned
 // Reverse mode through unrolled grid steps (adjoint.cu).  All arrays are in
 // the padded pixel-major layout of the step kernel; L <= 24.
 constexpr int kAdjointMaxLabels = 24;
-constexpr int kAdjMuParam = 24 * 24;
 struct AdjointStep {
-    float mu_p[kAdjMuParam]; // symmetric mu, [LP][LP] zero padded (parameter bank of the reverse step)
     const float *gs_in;      // [B][N][LP] d loss / d s^{t+1} (padding 0)
     float *gs_out;           // [B][N][LP] d loss / d s^t (padding written 0)
     float *dU;               // [B][N][LP] accumulated
