@@ -84,6 +84,28 @@ def dist_env():
     return world, rank, local
 
 
+def replica_seeds(rank: int, batch: int) -> list[int]:
+    """Seeds of the instances a rank solves: replicas draw disjoint instances
+    of the same recipe (weak scaling: the work per rank is fixed)."""
+    return [SEED + rank * batch + b for b in range(batch)]
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The slowest rank's time (the job finishes when it does)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -710,7 +732,7 @@ def run_ours(args, world, rank, local):
             print(json.dumps({"dense_precision": "bf16" if prec else "f32", **r}), flush=True)
         return
     B = args.batch
-    ds = [synth.segmentation_grid(H=H, W=W, L=L, conn=CONN, seed=SEED + rank * B + b) for b in range(B)]
+    ds = [synth.segmentation_grid(H=H, W=W, L=L, conn=CONN, seed=sd) for sd in replica_seeds(rank, B)]
     d = ds[0]
     U = torch.from_numpy(np.stack([x["U"] for x in ds])).to(dev)
     mu = torch.from_numpy(d["mu"]).to(dev)
@@ -760,13 +782,9 @@ def run_ours(args, world, rank, local):
     launches = crf.launch_count() - launches0
     crf.profile(False)
     step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     units_per_step = B * H * W * L * ITERS
-    value = world * units_per_step * args.steps / (total_ms / 1000.0)
+    value = job_throughput(units_per_step * args.steps, total_ms / 1000.0, world)
     F_final = float(crf.free_energy()[0])
     kern_ms = float(np.mean(loop_ms))
     peak, peak_kind = measured_peaks()
@@ -799,12 +817,8 @@ def run_ours(args, world, rank, local):
             t0 = time.perf_counter()
             e2e_step()
             times.append(time.perf_counter() - t0)
-        e2e_s = float(np.mean(times))
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * units_per_step / e2e_s, "unit": UNIT,
+        e2e_s = max_over_ranks(float(np.mean(times)), world, dev)
+        e2e = {"value": job_throughput(units_per_step, e2e_s, world), "unit": UNIT,
                "h2d_bytes_per_step": int(U_h.numel() * 4 + mu_h.numel() * 4 + w_h.numel() * 4),
                "d2h_bytes_per_step": int(q_h.numel() * 4 + 8),
                "ms_per_step": 1000 * e2e_s,
