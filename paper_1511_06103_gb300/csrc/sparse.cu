@@ -2,7 +2,8 @@
 // as an edge list (Sec. 2.1, Eq. related:pairwise-mrf with an arbitrary edge
 // set; the DBN-shaped layers of the paper's benchmarks are one instance).
 //
-// One warp per variable, one lane per label (L <= 32): the lanes walk the
+// One warp per variable at a time (four per warp), one lane per label
+// (L <= 32), the lane's row of mu held in registers: the lanes walk the
 // variable's adjacency list in CSR form and accumulate the weighted
 // neighbour marginals with one coalesced 4*LP-byte read per neighbour, then
 //   m = mu S_out + mu^T S_in      (m = mu S for symmetric mu, S over both
@@ -21,62 +22,96 @@ namespace proxmf {
 
 namespace {
 
-constexpr int kSW = 8;               // variables (warps) per block
+constexpr int kSW = 8;               // warps per block
 constexpr int kST = kSW * 32;
+constexpr int kVPW = 4;              // variables per warp (the lane's mu row is reused)
 
-__global__ void __launch_bounds__(kST) sparse_step_kernel(const SparseStepLaunch a) {
-    __shared__ float mus[kMaxLabels * kMaxLabels];
+// sum_e w_e q[col_e][lane] over one adjacency list, four entries in flight
+__device__ __forceinline__ float gather(const int *__restrict__ ptr, const int *__restrict__ col,
+                                        const float *__restrict__ wt, const float *__restrict__ q, size_t base,
+                                        int i, int lane, int LP) {
+    const int e0 = ptr[i], e1 = ptr[i + 1];
+    float acc = 0.f;
+    int e = e0;
+    for (; e + 4 <= e1; e += 4) {
+        const int c0 = col[e], c1 = col[e + 1], c2 = col[e + 2], c3 = col[e + 3];
+        const float w0 = wt[e], w1 = wt[e + 1], w2 = wt[e + 2], w3 = wt[e + 3];
+        if (lane < LP) {
+            const float q0 = __ldg(q + (base + c0) * LP + lane), q1 = __ldg(q + (base + c1) * LP + lane);
+            const float q2 = __ldg(q + (base + c2) * LP + lane), q3 = __ldg(q + (base + c3) * LP + lane);
+            acc = fmaf(w0, q0, acc);
+            acc = fmaf(w1, q1, acc);
+            acc = fmaf(w2, q2, acc);
+            acc = fmaf(w3, q3, acc);
+        }
+    }
+    for (; e < e1; ++e) {
+        const float qj = lane < LP ? __ldg(q + (base + col[e]) * LP + lane) : 0.f;
+        acc = fmaf(wt[e], qj, acc);
+    }
+    return acc;
+}
+
+template <bool SYM>
+__global__ void __launch_bounds__(kST, 3) sparse_step_kernel(const SparseStepLaunch a) {
     __shared__ double red[kSW];
     __shared__ int is_last;
     const int b = blockIdx.y;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int N = a.N, L = a.L, LP = a.LP;
-    const int i = blockIdx.x * kSW + warp;
     const size_t base = (size_t)b * N;
-    for (int e = threadIdx.x; e < L * L; e += kST) mus[e] = a.mu[e];
+    const int i0 = (blockIdx.x * kSW + warp) * kVPW;
 
     if (a.done != nullptr && a.done[b] != 0) {
         // stopping rule met: carry the state through unchanged
-        if (a.update && i < N && lane < LP) {
-            const size_t o = (base + i) * LP + lane;
-            a.s_out[o] = a.s_in[o];
-            a.q_out[o] = a.q_in[o];
+        for (int v = 0; v < kVPW; ++v) {
+            const int i = i0 + v;
+            if (a.update && i < N && lane < LP) {
+                const size_t o = (base + i) * LP + lane;
+                a.s_out[o] = a.s_in[o];
+                a.q_out[o] = a.q_in[o];
+            }
         }
         return;
     }
-    __syncthreads();
 
     const bool live = lane < L;
+    // this lane's row of mu (and column, for mu^T), kept in registers
+    float mrow[kMaxLabels], mcol[SYM ? 1 : kMaxLabels];
+#pragma unroll
+    for (int k = 0; k < kMaxLabels; ++k) {
+        mrow[k] = (live && k < L) ? a.mu[lane * L + k] : 0.f;
+        if (!SYM) mcol[k] = (live && k < L) ? a.mu[k * L + lane] : 0.f;
+    }
+    const float eta = a.eta[b];
     float f = 0.f;
-    if (i < N) {
+    for (int v = 0; v < kVPW; ++v) {
+        const int i = i0 + v;
+        if (i >= N) break;
         const size_t o = (base + i) * LP + lane;
-        // a1: neighbour sums
-        float S = 0.f, T = 0.f;
-        for (int e = a.out_ptr[i]; e < a.out_ptr[i + 1]; ++e) {
-            const float qj = lane < LP ? __ldg(a.q_in + (base + a.out_col[e]) * LP + lane) : 0.f;
-            S = fmaf(a.out_w[e], qj, S);
-        }
-        if (!a.sym)
-            for (int e = a.in_ptr[i]; e < a.in_ptr[i + 1]; ++e) {
-                const float qk = lane < LP ? __ldg(a.q_in + (base + a.in_col[e]) * LP + lane) : 0.f;
-                T = fmaf(a.in_w[e], qk, T);
-            }
-        // m_l = sum_k mu[l][k] S_k (+ sum_k mu[k][l] T_k)
+        // a1: neighbour sums and m_l = sum_k mu[l][k] S_k (+ sum_k mu[k][l] T_k)
+        const float S = gather(a.out_ptr, a.out_col, a.out_w, a.q_in, base, i, lane, LP);
         float m = 0.f;
-        for (int k = 0; k < L; ++k) {
-            const float Sk = __shfl_sync(0xffffffffu, S, k);
-            const float Tk = __shfl_sync(0xffffffffu, T, k);
-            if (live) {
-                m = fmaf(mus[lane * L + k], Sk, m);
-                if (!a.sym) m = fmaf(mus[k * L + lane], Tk, m);
+        if constexpr (SYM) {
+#pragma unroll
+            for (int k = 0; k < kMaxLabels; ++k) {
+                if (k >= L) break;
+                m = fmaf(mrow[k], __shfl_sync(0xffffffffu, S, k), m);
+            }
+        } else {
+            const float T = gather(a.in_ptr, a.in_col, a.in_w, a.q_in, base, i, lane, LP);
+#pragma unroll
+            for (int k = 0; k < kMaxLabels; ++k) {
+                if (k >= L) break;
+                m = fmaf(mrow[k], __shfl_sync(0xffffffffu, S, k), m);
+                m = fmaf(mcol[SYM ? 0 : k], __shfl_sync(0xffffffffu, T, k), m);
             }
         }
         // a2-a4
         const float s = live ? a.s_in[o] : 0.f;
         const float u = live ? a.U[o] : 0.f;
         const float q = live ? a.q_in[o] : 0.f;
-        const float eta = a.eta[b];
-        f = live ? q * (u + 0.5f * m + s) : 0.f;
+        f += live ? q * (u + 0.5f * m + s) : 0.f;
         const float av = live ? fmaf(-eta, u + m, (1.f - eta) * s) : -INFINITY;
         float mx = av;
 #pragma unroll
@@ -145,11 +180,14 @@ __global__ void sparse_degree_kernel(const int *ptr, const float *w, int N, unsi
 
 }  // namespace
 
-int sparse_blocks(int N) { return (N + kSW - 1) / kSW; }
+int sparse_blocks(int N) { return (N + kSW * kVPW - 1) / (kSW * kVPW); }
 
 cudaError_t launch_sparse_step(const SparseStepLaunch &a, cudaStream_t st) {
     dim3 grid(sparse_blocks(a.N), a.B);
-    sparse_step_kernel<<<grid, kST, 0, st>>>(a);
+    if (a.sym)
+        sparse_step_kernel<true><<<grid, kST, 0, st>>>(a);
+    else
+        sparse_step_kernel<false><<<grid, kST, 0, st>>>(a);
     return cudaGetLastError();
 }
 
