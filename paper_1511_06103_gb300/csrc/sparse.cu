@@ -2,8 +2,7 @@
 // as an edge list (Sec. 2.1, Eq. related:pairwise-mrf with an arbitrary edge
 // set; the DBN-shaped layers of the paper's benchmarks are one instance).
 //
-// One warp per variable at a time (four per warp), one lane per label
-// (L <= 32), the lane's row of mu held in registers: the lanes walk the
+// One warp per variable, one lane per label (L <= 32): the lanes walk the
 // variable's adjacency list in CSR form and accumulate the weighted
 // neighbour marginals with one coalesced 4*LP-byte read per neighbour, then
 //   m = mu S_out + mu^T S_in      (m = mu S for symmetric mu, S over both
@@ -24,7 +23,7 @@ namespace {
 
 constexpr int kSW = 8;               // warps per block
 constexpr int kST = kSW * 32;
-constexpr int kVPW = 4;              // variables per warp (the lane's mu row is reused)
+constexpr int kVPW = 1;              // variables per warp
 
 // sum_e w_e q[col_e][lane] over one adjacency list, four entries in flight
 __device__ __forceinline__ float gather(const int *__restrict__ ptr, const int *__restrict__ col,
@@ -53,7 +52,7 @@ __device__ __forceinline__ float gather(const int *__restrict__ ptr, const int *
 }
 
 template <bool SYM>
-__global__ void __launch_bounds__(kST, 3) sparse_step_kernel(const SparseStepLaunch a) {
+__global__ void __launch_bounds__(kST) sparse_step_kernel(const SparseStepLaunch a) {
     __shared__ double red[kSW];
     __shared__ int is_last;
     const int b = blockIdx.y;
@@ -76,13 +75,9 @@ __global__ void __launch_bounds__(kST, 3) sparse_step_kernel(const SparseStepLau
     }
 
     const bool live = lane < L;
-    // this lane's row of mu (and column, for mu^T), kept in registers
-    float mrow[kMaxLabels], mcol[SYM ? 1 : kMaxLabels];
-#pragma unroll
-    for (int k = 0; k < kMaxLabels; ++k) {
-        mrow[k] = (live && k < L) ? a.mu[lane * L + k] : 0.f;
-        if (!SYM) mcol[k] = (live && k < L) ? a.mu[k * L + lane] : 0.f;
-    }
+    __shared__ float mus[kMaxLabels * kMaxLabels];
+    for (int e = threadIdx.x; e < L * L; e += kST) mus[e] = a.mu[e];
+    __syncthreads();
     const float eta = a.eta[b];
     float f = 0.f;
     for (int v = 0; v < kVPW; ++v) {
@@ -93,18 +88,16 @@ __global__ void __launch_bounds__(kST, 3) sparse_step_kernel(const SparseStepLau
         const float S = gather(a.out_ptr, a.out_col, a.out_w, a.q_in, base, i, lane, LP);
         float m = 0.f;
         if constexpr (SYM) {
-#pragma unroll
-            for (int k = 0; k < kMaxLabels; ++k) {
-                if (k >= L) break;
-                m = fmaf(mrow[k], __shfl_sync(0xffffffffu, S, k), m);
+            for (int k = 0; k < L; ++k) {
+                const float Sk = __shfl_sync(0xffffffffu, S, k);
+                if (live) m = fmaf(mus[lane * L + k], Sk, m);
             }
         } else {
             const float T = gather(a.in_ptr, a.in_col, a.in_w, a.q_in, base, i, lane, LP);
-#pragma unroll
-            for (int k = 0; k < kMaxLabels; ++k) {
-                if (k >= L) break;
-                m = fmaf(mrow[k], __shfl_sync(0xffffffffu, S, k), m);
-                m = fmaf(mcol[SYM ? 0 : k], __shfl_sync(0xffffffffu, T, k), m);
+            for (int k = 0; k < L; ++k) {
+                const float Sk = __shfl_sync(0xffffffffu, S, k);
+                const float Tk = __shfl_sync(0xffffffffu, T, k);
+                if (live) m = fmaf(mus[lane * L + k], Sk, fmaf(mus[k * L + lane], Tk, m));
             }
         }
         // a2-a4
