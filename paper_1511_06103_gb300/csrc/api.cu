@@ -320,7 +320,7 @@ crf_status ensure_lambda(crf_t h) {
     job.Lambda = h->Lambda;
     job.eta = h->eta_auto;
     job.max_steps = 4000;
-    job.tol = 1e-10;   // relative change of the extreme Ritz values between checks
+    job.tol = 1e-9;    // relative change of the extreme Ritz values between checks
     int steps = 0;
     long long nl = 0;
     const int rc = estimate_lipschitz_grid(job, h->st, &steps, &nl);
