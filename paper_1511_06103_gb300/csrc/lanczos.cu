@@ -24,6 +24,7 @@
 // to the extreme eigenvalues from inside.  Every instance of a batch gets its
 // own constant.  All arithmetic is on the device; the host only sequences
 // launches and reads back convergence flags.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -134,11 +135,19 @@ __device__ __forceinline__ double *lz_buf(const LzState &s, int i) {
     return i == 0 ? s.R0 : (i == 1 ? s.R1 : s.R2);
 }
 
+// FP64 copy of the pixel-major edge weights for the scalar form (FP64 is the
+// slow pipe on this part: converting once instead of every step halves the
+// FP64 work of a Lanczos step).
+__global__ void lz_weights_f64_kernel(const float *__restrict__ w, double *__restrict__ wd, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        wd[i] = (double)w[i];
+}
+
 // Step part A: t = A v_k into R[(k+1) % 3] and alpha_k = v_k . t, with
 // A = W (scalar form) or C H C (full form).
 // Scalar form (symmetric mu): t = W v_k, one value per pixel.
 __global__ void __launch_bounds__(kLzThreads)
-lz_step_a_scalar_kernel(LzState st, const float *__restrict__ w, LzGeom g) {
+lz_step_a_scalar_kernel(LzState st, const double *__restrict__ w, LzGeom g) {
     const int b = blockIdx.y;
     const int k = *st.kdev;
     if (st.stop[b] || k >= st.ld - 1) return;
@@ -150,18 +159,16 @@ lz_step_a_scalar_kernel(LzState st, const float *__restrict__ w, LzGeom g) {
     double dot = 0.0;
     if (p < g.H * g.W) {
         const int y = p / g.W, x = p - y * g.W;
-        const float *wb = w + (size_t)b * g.H * g.W * nd;
+        const double *wb = w + (size_t)b * g.H * g.W * nd;
         double acc = 0.0;
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
             if (d >= nd) break;
             const int dy = d == 0 ? 0 : 1, dx = d == 0 ? 1 : (d == 1 ? 0 : (d == 2 ? 1 : -1));
             const int yo = y + dy, xo = x + dx;
-            if (yo < g.H && xo >= 0 && xo < g.W)
-                acc += (double)wb[((size_t)y * g.W + x) * nd + d] * v[(size_t)yo * g.P + xo];
+            if (yo < g.H && xo >= 0 && xo < g.W) acc = fma(wb[((size_t)y * g.W + x) * nd + d], v[(size_t)yo * g.P + xo], acc);
             const int yi = y - dy, xi = x - dx;
-            if (yi >= 0 && xi >= 0 && xi < g.W)
-                acc += (double)wb[((size_t)yi * g.W + xi) * nd + d] * v[(size_t)yi * g.P + xi];
+            if (yi >= 0 && xi >= 0 && xi < g.W) acc = fma(wb[((size_t)yi * g.W + xi) * nd + d], v[(size_t)yi * g.P + xi], acc);
         }
         const double r = acc * inv;
         out[(size_t)y * g.P + x] = r;
@@ -284,16 +291,17 @@ lz_step_b_kernel(LzState st, LzGeom g) {
         const double nk = st.nrm[(size_t)b * st.ld + k];
         const double ik = 1.0 / nk;
         const double im = k > 0 ? 1.0 / st.nrm[(size_t)b * st.ld + k - 1] : 0.0;
+        const double ca = a * ik, cm = nk * im;   // coefficients of u_k and u_{k-1}
         const int p = blockIdx.x * blockDim.x + threadIdx.x;
         if (p < g.H * g.W) {
             const int y = p / g.W, x = p - y * g.W;
             const size_t off = (size_t)b * g.Lv * plane + (size_t)y * g.P + x;
             for (int l = 0; l < g.Lv; ++l) {
                 const size_t i = off + l * plane;
-                double r = t[i] - a * (uk[i] * ik);
-                if (k > 0) r -= nk * (um[i] * im);
+                double r = fma(-ca, uk[i], t[i]);
+                if (k > 0) r = fma(-cm, um[i], r);
                 t[i] = r;
-                nrm2 += r * r;
+                nrm2 = fma(r, r, nrm2);
             }
         }
     }
@@ -596,6 +604,7 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
     int rc = 0;
     LzState S{};
     double *rmin = nullptr, *rmax = nullptr, *nu = nullptr;
+    double *wd = nullptr;        // FP64 edge weights (scalar form)
     float *mu_dev = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -624,6 +633,13 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
     LZ_CHECK(cudaMallocAsync((void **)&rmax, (size_t)B * sizeof(double), st));
     LZ_CHECK(cudaMallocAsync((void **)&nu, 2 * sizeof(double), st));
     LZ_CHECK(cudaMallocAsync((void **)&mu_dev, (size_t)job.L * job.L * sizeof(float), st));
+    if (!job.Kdense && g.Lv == 1) {
+        const size_t nw = (size_t)B * job.H * job.W * (job.conn == 8 ? 4 : 2);
+        LZ_CHECK(cudaMallocAsync((void **)&wd, nw * sizeof(double), st));
+        lz_weights_f64_kernel<<<(int)std::min<size_t>((nw + 255) / 256, 4096), 256, 0, st>>>(job.w, wd, nw);
+        LZ_CHECK(cudaGetLastError());
+        nl += 1;
+    }
     LZ_CHECK(cudaMemsetAsync(S.alpha, 0, (size_t)B * ld * sizeof(double), st));
     LZ_CHECK(cudaMemsetAsync(S.nrm, 0, (size_t)B * (ld + 1) * sizeof(double), st));
     LZ_CHECK(cudaMemsetAsync(S.counter, 0, (size_t)(B + 1) * sizeof(unsigned), st));
@@ -646,7 +662,7 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
         if (job.Kdense)
             lz_step_a_dense_kernel<<<dim3(nblk_dense, B), kLzThreads, 0, cap>>>(S, job.Kdense, g, nblk_dense);
         else if (g.Lv == 1)
-            lz_step_a_scalar_kernel<<<gridp, kLzThreads, 0, cap>>>(S, job.w, g);
+            lz_step_a_scalar_kernel<<<gridp, kLzThreads, 0, cap>>>(S, wd, g);
         else
             lz_step_a_kernel<<<gridp, kLzThreads, 0, cap>>>(S, job.w, mu_dev, g);
         lz_step_b_kernel<<<gridp, kLzThreads, 0, cap>>>(S, g);
@@ -700,7 +716,7 @@ done:
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (cap) cudaStreamDestroy(cap);
-    double *ds[] = {S.R0, S.R1, S.R2, S.alpha, S.nrm, S.partial, rmin, rmax, nu};
+    double *ds[] = {S.R0, S.R1, S.R2, S.alpha, S.nrm, S.partial, rmin, rmax, nu, wd};
     for (double *p : ds)
         if (p) cudaFreeAsync(p, st);
     if (S.counter) cudaFreeAsync(S.counter, st);
