@@ -224,9 +224,10 @@ struct TileJob {
 // j.update), and the tile's free-energy partial, returned in thread 0.
 // All threads of the block must call it; it may be called repeatedly by a
 // persistent block (shared memory is reused).
-// PMU: the L x L product reads mu from j.mu_p (the launch's parameter bank,
-// see mu_in_params) instead of shared memory.
-template <int LT, int CONN, bool SYM, bool TC = false, int RULE = 0, bool PMU = false>
+// With mu_in_params the L x L product reads mu from j.mu_p (the launch's
+// parameter bank, or global memory for the serving step) instead of shared
+// memory.
+template <int LT, int CONN, bool SYM, bool TC = false, int RULE = 0>
 __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, const TcTile *tcx = nullptr) {
     constexpr int LP = storage_labels(LT);           // floats per pixel in HBM
     constexpr int NP = (LT + 1) / 2;                 // label pairs in the arithmetic
@@ -253,7 +254,7 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, co
     const float *sin = j.s_in;
     __syncthreads();   // shared memory of a previous tile is no longer read
 
-    constexpr bool kParamMu = PMU;
+    constexpr bool kParamMu = mu_in_params<LT, SYM, TC, RULE>();
     // mu pairs into shared memory
     for (int i = tid; !TC && !kParamMu && i < LT * NPP; i += GT) {
         mus[0][i] = j.mu_out[i];
@@ -690,8 +691,7 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
     j.H = a.H;
     j.W = a.W;
     j.update = a.update;
-    const double bs =
-        grid_tile<LT, CONN, SYM, TC, RULE, mu_in_params<LT, SYM, TC, RULE>()>(j, blockIdx.x, blockIdx.y, &tct);
+    const double bs = grid_tile<LT, CONN, SYM, TC, RULE>(j, blockIdx.x, blockIdx.y, &tct);
     if constexpr (TC) {
         // every thread's TMEM reads finished before the block sync inside grid_tile
         tc::fence_after_sync();

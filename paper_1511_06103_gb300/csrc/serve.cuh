@@ -76,6 +76,7 @@ serve_step_kernel(ServeSlot *slots, const ServeBucket *bucket, ServeResult *resu
         j.w = sl.w;
         j.mu_out = sl.mu_out;
         j.mu_in = sl.mu_in;
+        j.mu_p = sl.mu_out;   // the serving step reads the column pairs from global memory
         j.eta = *sl.eta;
         j.adaptive = false;
         j.adapt_d = 0.f;
