@@ -625,7 +625,7 @@ struct GridTcSmem {
 };
 
 template <int LT, int CONN, bool SYM, bool TC, int RULE = 0>
-__global__ void __launch_bounds__(GT, (LT >= 24 || RULE == 2) ? 1 : (RULE ? 2 : 3))
+__global__ void __launch_bounds__(GT, (RULE == 2) ? 1 : ((LT >= 24 || RULE) ? 2 : 3))
 grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
     constexpr int LP = storage_labels(LT);
     __shared__ double red[GT / 32];
