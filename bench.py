@@ -356,6 +356,31 @@ def run_grid_precision(args, dev, peak):
                                   "bytes_per_launch": bl},
                      "final_F": float(crf.free_energy()[0]), "q": crf.marginals()}
         crf.close()
+    # the same comparison across label counts (step launch time, 100 steps)
+    sweep = {}
+    for Ls in (8, 16, 24, 32):
+        ds = synth.segmentation_grid(H=H, W=W, L=Ls, conn=CONN, seed=SEED)
+        row = {}
+        for name, prec, iters, refine in (("f32", binding.CRF_FP32, ITERS, 0), ("bf16_tc", binding.CRF_BF16, ITERS - 2, 2)):
+            crf = binding.CRF(binding.CRF_GRID8, Ls, H, W, precision=prec, stream=stream.cuda_stream)
+            crf.set_unary(torch.from_numpy(ds["U"]).to(dev))
+            crf.set_pairwise(torch.from_numpy(ds["mu"]).to(dev), torch.from_numpy(ds["w"]).to(dev))
+            crf.lipschitz()
+            for _ in range(2):
+                crf.iterate(iters, eta=0.0, reset=True, refine_fp32=refine)
+            crf.profile(True)
+            ks = []
+            for _ in range(3):
+                flush.zero_()
+                crf.iterate(iters, eta=0.0, reset=True, refine_fp32=refine)
+                ms, n = crf.profile_read()
+                ks.append(ms / n)
+            crf.profile(False)
+            row[name + "_launch_us"] = 1000.0 * float(np.mean(ks))
+            crf.close()
+        row["bf16_speedup"] = row["f32_launch_us"] / row["bf16_tc_launch_us"]
+        sweep[str(Ls)] = row
+    out["label_sweep"] = sweep
     q32, q16 = out["f32"].pop("q"), out["bf16_tc"].pop("q")
     return {"workload": WORKLOAD + "; FP32 form vs BF16 tensor-core messages (98 + 2 FP32 refinement steps)",
             **out, "bf16_speedup": out["bf16_tc"]["value"] / out["f32"]["value"],
