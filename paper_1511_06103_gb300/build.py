@@ -69,7 +69,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     with cf.ThreadPoolExecutor(max_workers=n) as ex:
         list(ex.map(compile_one, srcs, objs))
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

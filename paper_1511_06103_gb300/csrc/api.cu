@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/proxmf.h"
+#include "nvtx_range.h"
 #include "internal.h"
 
 using namespace proxmf;
@@ -483,6 +484,7 @@ const char *crf_error_string(crf_status s) {
 }
 
 crf_status crf_create(const crf_desc *desc, crf_t *out) {
+    PROXMF_RANGE("crf_create");
     if (!out) return CRF_E_INVALID;
     *out = nullptr;
     if (!desc) return CRF_E_INVALID;
@@ -629,6 +631,7 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
 }
 
 crf_status crf_destroy(crf_t h) {
+    PROXMF_RANGE("crf_destroy");
     if (!h) return CRF_OK;
     cudaStreamSynchronize(h->st);
     free_all(h);
@@ -637,6 +640,7 @@ crf_status crf_destroy(crf_t h) {
 }
 
 crf_status crf_set_unary(crf_t h, const float *U, int is_device) {
+    PROXMF_RANGE("crf_set_unary");
     crf_status rc = check_handle(h);
     if (rc != CRF_OK) return rc;
     if (!U) return CRF_E_INVALID;
@@ -692,6 +696,7 @@ static crf_status set_pairwise_dense(crf_t h, const std::vector<float> &m, const
 
 crf_status crf_set_pairwise(crf_t h, const float *mu, const float *w_or_feats, const float *theta,
                             int is_device) {
+    PROXMF_RANGE("crf_set_pairwise");
     crf_status rc = check_handle(h);
     if (rc != CRF_OK) return rc;
     if (!mu || !w_or_feats) return CRF_E_INVALID;
@@ -758,6 +763,7 @@ crf_status crf_set_pairwise(crf_t h, const float *mu, const float *w_or_feats, c
 
 crf_status crf_set_graph(crf_t h, const float *mu, int64_t n_edges, const int32_t *src, const int32_t *dst,
                          const float *w, int32_t is_device) {
+    PROXMF_RANGE("crf_set_graph");
     crf_status rc = check_handle(h);
     if (rc != CRF_OK) return rc;
     if (!h->sparse || !mu || n_edges < 0 || n_edges > (1ll << 30) || (n_edges > 0 && (!src || !dst || !w)))
@@ -843,6 +849,7 @@ crf_status crf_set_graph(crf_t h, const float *mu, int64_t n_edges, const int32_
 }
 
 crf_status crf_set_state(crf_t h, const float *logq, int is_device) {
+    PROXMF_RANGE("crf_set_state");
     crf_status rc = check_handle(h);
     if (rc != CRF_OK) return rc;
     if (!logq) return CRF_E_INVALID;
@@ -860,6 +867,7 @@ crf_status crf_set_state(crf_t h, const float *logq, int is_device) {
 }
 
 crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
+    PROXMF_RANGE("mf_iterate");
     crf_status rc = check_handle(h);
     if (rc != CRF_OK) return rc;
     if (!p || p->max_iters < 0 || p->rel_tol < 0 || !std::isfinite(p->eta) || p->eta > 1.0)
@@ -1014,6 +1022,7 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
 }
 
 crf_status mf_free_energy(crf_t h, double *F) {
+    PROXMF_RANGE("mf_free_energy");
     crf_status rc = check_handle(h);
     if (rc != CRF_OK) return rc;
     if (!F) return CRF_E_INVALID;
@@ -1030,6 +1039,7 @@ crf_status mf_free_energy(crf_t h, double *F) {
 }
 
 crf_status mf_free_energy_trace(crf_t h, double *F, int32_t n) {
+    PROXMF_RANGE("mf_free_energy_trace");
     crf_status rc = check_handle(h);
     if (rc != CRF_OK) return rc;
     if (!F || n < 0 || n > h->last_iters || n > h->trace_cap) return CRF_E_INVALID;
@@ -1057,10 +1067,12 @@ static crf_status export_state(crf_t h, float *dst, int is_device, int mode) {
 crf_status mf_marginals(crf_t h, float *q, int is_device) { return export_state(h, q, is_device, CONV_EXP); }
 
 crf_status mf_log_marginals(crf_t h, float *logq, int is_device) {
+    PROXMF_RANGE("mf_log_marginals");
     return export_state(h, logq, is_device, CONV_COPY);
 }
 
 crf_status mf_lipschitz(crf_t h, double *Lambda, double *eta) {
+    PROXMF_RANGE("mf_lipschitz");
     crf_status rc = check_handle(h);
     if (rc != CRF_OK) return rc;
     if (!h->has_pairwise) return CRF_E_INVALID;
@@ -1148,6 +1160,7 @@ crf_status mf_unrolled_checkpoint_floats(crf_t h, int32_t K, int64_t *n_floats) 
 }
 
 crf_status mf_unrolled_forward(crf_t h, int32_t K, double eta, float *ckpt) {
+    PROXMF_RANGE("mf_unrolled_forward");
     crf_status rc = unrolled_check(h, K);
     if (rc != CRF_OK) return rc;
     if (!ckpt || ((uintptr_t)ckpt & 15)) return CRF_E_INVALID;
@@ -1182,6 +1195,7 @@ crf_status mf_unrolled_forward(crf_t h, int32_t K, double eta, float *ckpt) {
 
 crf_status mf_unrolled_backward(crf_t h, int32_t K, double eta, const float *ckpt, const float *dlogq,
                                 float *dU, float *dmu, float *dw, int32_t is_device) {
+    PROXMF_RANGE("mf_unrolled_backward");
     crf_status rc = unrolled_check(h, K);
     if (rc != CRF_OK) return rc;
     if (!ckpt || !dlogq || ((uintptr_t)ckpt & 15)) return CRF_E_INVALID;

@@ -22,6 +22,7 @@
 #include <mutex>
 
 #include "../../include/proxmf.h"
+#include "nvtx_range.h"
 #include "internal.h"
 
 namespace {
@@ -60,6 +61,7 @@ extern "C" crf_status mf_grid_step_noalloc(int32_t topology, int32_t n_labels, i
                                            int64_t width, const float *U, const float *w,
                                            const float *mu, const float *logq_in, float *logq_out,
                                            double eta, double *F_out, void *stream) {
+    PROXMF_RANGE("mf_grid_step_noalloc");
     using namespace proxmf;
     if (topology != CRF_GRID4 && topology != CRF_GRID8) return CRF_E_INVALID;
     if (n_labels < 1 || n_labels > kMaxLabels || height < 1 || width < 1) return CRF_E_INVALID;

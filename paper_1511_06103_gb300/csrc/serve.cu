@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "../../include/proxmf.h"
+#include "nvtx_range.h"
 #include "serve.cuh"
 
 using namespace proxmf;
@@ -378,6 +379,7 @@ cudaError_t launch_eta_bound(const float *w, int H, int W, int nd, const float *
 extern "C" {
 
 crf_status mf_server_create(int64_t budget_bytes, int32_t max_slots, void *stream, mf_server_t *out) {
+    PROXMF_RANGE("mf_server_create");
     if (!out) return CRF_E_INVALID;
     *out = nullptr;
     if (budget_bytes <= 0 || max_slots < 1 || max_slots > kMaxServeSlots) return CRF_E_INVALID;
@@ -419,8 +421,9 @@ crf_status mf_server_create(int64_t budget_bytes, int32_t max_slots, void *strea
 }
 
 crf_status mf_server_destroy(mf_server_t s) {
+    PROXMF_RANGE("mf_server_destroy");
     if (!s) return CRF_OK;
-    if (s->st || true) cudaStreamSynchronize(s->st);
+    cudaStreamSynchronize(s->st);
     if (s->exec) cudaGraphExecDestroy(s->exec);
     if (s->graph) cudaGraphDestroy(s->graph);
     if (s->cap) cudaStreamDestroy(s->cap);
@@ -437,6 +440,7 @@ crf_status mf_server_destroy(mf_server_t s) {
 
 crf_status mf_server_submit(mf_server_t s, const crf_desc *d, const float *U, const float *mu, const float *w,
                             const mf_params *p, float *q_out, uint64_t *ticket) {
+    PROXMF_RANGE("mf_server_submit");
     if (!s || !d || !U || !mu || !w || !p || !ticket) return CRF_E_INVALID;
     if (s->broken) return CRF_E_STATE;
     if (d->topology != CRF_GRID4 && d->topology != CRF_GRID8) return CRF_E_INVALID;
@@ -472,6 +476,7 @@ crf_status mf_server_submit(mf_server_t s, const crf_desc *d, const float *U, co
 }
 
 crf_status mf_server_step(mf_server_t s, int32_t iters, int32_t *in_flight, int32_t *queued) {
+    PROXMF_RANGE("mf_server_step");
     if (!s || iters < 0) return CRF_E_INVALID;
     if (s->broken) return CRF_E_STATE;
     crf_status rc;
@@ -545,6 +550,7 @@ crf_status mf_server_poll(mf_server_t s, uint64_t ticket, int32_t *state, double
 }
 
 crf_status mf_server_sync(mf_server_t s) {
+    PROXMF_RANGE("mf_server_sync");
     if (!s) return CRF_E_INVALID;
     if (s->broken) return CRF_E_STATE;
     SCK(cudaStreamSynchronize(s->st));

@@ -294,3 +294,22 @@ def test_graph_replay_matches_eager(env, rel_tol):
         assert np.array_equal(a[1], b[1])
         if a[2] is not None:
             assert np.array_equal(a[2], b[2])
+
+
+def test_device_allocation_failure_is_reported(env):
+    """A handle whose arrays exceed device memory fails with CRF_E_OOM (a
+    failed cudaMalloc, nothing launched) and leaves the context usable: a
+    handle created afterwards still matches the oracle.  The request is
+    64 x 8192 x 8192 pixels x 24 stored labels x 4 bytes = 412 GB per array,
+    within the size limits of the ABI but above the 288 GB of the device."""
+    binding, oracle, torch = env
+    with pytest.raises(binding.ProxMFError) as e:
+        binding.CRF(binding.CRF_GRID8, 21, 8192, 8192, batch=64)
+    assert e.value.status == -2
+    with pytest.raises(binding.ProxMFError) as e:
+        binding.Server(1 << 42)
+    assert e.value.status == -2
+    d = synth.random_grid(9, 14, 3, 8, seed=31, symmetric=True)
+    s_ref = oracle_model(oracle, d).prox_step(0.5, oracle_model(oracle, d).init_logq())
+    s, _, _ = gpu_run(binding, torch, d, 0.5, 1)
+    assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q
