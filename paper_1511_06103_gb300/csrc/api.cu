@@ -326,6 +326,7 @@ crf_status ensure_lambda(crf_t h) {
     long long nl = 0;
     const int rc = estimate_lipschitz_grid(job, h->st, &steps, &nl);
     h->launches += nl;
+    if (rc == -5) return CRF_E_TIMEOUT;   // a bounded wait ran out; the handle stays usable
     if (rc != 0) return fail_cuda(h, cudaErrorUnknown);
     h->lanczos_steps = steps;
     h->lambda_valid = true;

@@ -346,6 +346,190 @@ lz_step_b_kernel(LzState st, LzGeom g) {
     }
 }
 
+// ---- cooperative form: a whole chunk of scalar-form steps in one launch ----
+//
+// One block per SM (or fewer), every block of an instance owning a fixed
+// strided set of pixels; the two reductions of a step (alpha_k and |u_{k+1}|)
+// are block partials summed in a fixed order by every block after a grid
+// barrier, so all blocks hold the same alpha_k and beta_k and no launch or
+// last-block tail separates the steps.  1/|u_k| and the recurrence
+// coefficients are formed once per block and step: FP64 division is a long
+// sequence on the narrow FP64 pipe of this part.
+
+constexpr int kCoopThreads = 512;
+constexpr long long kLzWaitCycles = 4000000000ll;   // ~2 s at 2 GHz per barrier wait
+
+struct LzCoop {
+    unsigned *bar;   // [0] arrivals, [1] generation
+    int *abort;      // set once a barrier wait ran out; every later barrier fails
+    double *part;    // [2][B][gx] block partials of alpha_k and |u_{k+1}|^2
+    int gx;          // blocks per instance
+};
+
+// Grid-wide barrier of a cooperative launch with a bounded wait.  Thread 0
+// arrives on the counter; the last arrival resets it and advances the
+// generation word that the others poll.  Returns false in every thread of
+// the block when this or another block's wait ran out.
+__device__ bool coop_barrier(const LzCoop &c, unsigned nblocks) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = c.bar + 1;
+        volatile int *ab = c.abort;
+        int good = *ab == 0;
+        if (good) {
+            const unsigned g0 = *gen;
+            __threadfence();
+            if (atomicAdd(c.bar, 1u) == nblocks - 1) {
+                atomicExch(c.bar, 0u);
+                __threadfence();
+                atomicAdd(c.bar + 1, 1u);
+            } else {
+                const long long t0 = clock64();
+                while (*gen == g0) {
+                    if (*ab != 0) {
+                        good = 0;
+                        break;
+                    }
+                    if (clock64() - t0 > kLzWaitCycles) {
+                        atomicExch(c.abort, 1);
+                        good = 0;
+                        break;
+                    }
+                }
+            }
+            __threadfence();
+        }
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Sum of n partials in a fixed order (strided per thread, fixed-shape warp
+// tree, warps in index order); every thread gets the same value.
+__device__ double coop_sum(const double *p, int n, double *red, double *out) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < n; i += kCoopThreads) a += __ldcg(p + i);
+    a = warp_sum(a);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < kCoopThreads / 32; ++k) s += red[k];
+        *out = s;
+    }
+    __syncthreads();
+    return *out;
+}
+
+// Block total of v into part[slot] (thread 0 writes).
+__device__ void coop_partial(double v, double *red, double *part) {
+    v = warp_sum(v);
+    __syncthreads();   // red may still be read by a previous coop_sum
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < kCoopThreads / 32; ++k) s += red[k];
+        __stcg(part, s);
+    }
+}
+
+// Steps k0 .. k1-1 of the scalar form (t = W v_k, symmetric weighted
+// adjacency of the grid), same recurrence and stopping rule as the
+// two-kernel form above.  Vectors written inside the launch are read through
+// L2 only (__ldcg): L1 is not coherent across blocks.
+__global__ void __launch_bounds__(kCoopThreads, 1)
+lz_chunk_scalar_kernel(LzState st, const double *__restrict__ w, LzGeom g, LzCoop c, int k0, int k1) {
+    __shared__ double red[kCoopThreads / 32];
+    __shared__ double sh[4];
+    const int b = blockIdx.y, bx = blockIdx.x, tid = threadIdx.x;
+    const unsigned nblocks = gridDim.x * gridDim.y;
+    const int N = g.H * g.W;
+    const int nd = g.conn == 8 ? 4 : 2;
+    const size_t base = (size_t)b * N;
+    const double *wb = w + base * nd;
+    double *pa = c.part + (size_t)b * c.gx;
+    double *pb = c.part + ((size_t)g.B + b) * c.gx;
+    const size_t ld = (size_t)st.ld;
+    bool active = st.stop[b] == 0;
+    double nk = st.nrm[b * ld + k0];   // |u_k|
+    if (tid == 0) {
+        sh[0] = active ? 1.0 / nk : 0.0;
+        sh[1] = active && k0 > 0 ? nk / st.nrm[b * ld + k0 - 1] : 0.0;
+    }
+    __syncthreads();
+    for (int k = k0; k < k1; ++k) {
+        const double inv = sh[0], cm = sh[1];
+        const double *v = lz_buf(st, k % 3) + base;
+        double *t = lz_buf(st, (k + 1) % 3) + base;
+        const double *um = lz_buf(st, (k + 2) % 3) + base;
+        // t = W v_k and the partial of alpha_k = v_k . t
+        double dot = 0.0;
+        if (active) {
+            for (int p = bx * kCoopThreads + tid; p < N; p += c.gx * kCoopThreads) {
+                const int y = p / g.W, x = p - y * g.W;
+                double acc = 0.0;
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    if (d >= nd) break;
+                    const int dy = d == 0 ? 0 : 1, dx = d == 0 ? 1 : (d == 1 ? 0 : (d == 2 ? 1 : -1));
+                    const int yo = y + dy, xo = x + dx;
+                    if (yo < g.H && xo >= 0 && xo < g.W)
+                        acc = fma(__ldg(wb + (size_t)p * nd + d), __ldcg(v + (size_t)yo * g.W + xo), acc);
+                    const int yi = y - dy, xi = x - dx;
+                    if (yi >= 0 && xi >= 0 && xi < g.W) {
+                        const size_t q = (size_t)yi * g.W + xi;
+                        acc = fma(__ldg(wb + q * nd + d), __ldcg(v + q), acc);
+                    }
+                }
+                const double r = acc * inv;
+                __stcg(t + p, r);
+                dot = fma(r, __ldcg(v + p), dot);
+            }
+        }
+        coop_partial(dot * inv, red, pa + bx);
+        if (!coop_barrier(c, nblocks)) return;
+        const double alpha = coop_sum(pa, c.gx, red, sh + 2);
+        // u_{k+1} = t - alpha_k v_k - |u_k| v_{k-1} and its squared norm
+        double n2 = 0.0;
+        if (active) {
+            const double ca = alpha * inv;
+            for (int p = bx * kCoopThreads + tid; p < N; p += c.gx * kCoopThreads) {
+                double r = fma(-ca, __ldcg(v + p), __ldcg(t + p));
+                if (k > 0) r = fma(-cm, __ldcg(um + p), r);
+                __stcg(t + p, r);
+                n2 = fma(r, r, n2);
+            }
+        }
+        coop_partial(n2, red, pb + bx);
+        if (!coop_barrier(c, nblocks)) return;
+        const double s = coop_sum(pb, c.gx, red, sh + 3);
+        if (active) {
+            // every block derives the same values from the same sums
+            if (tid == 0) {
+                const double bk = sqrt(s);
+                const double ref = fabs(alpha) + nk;
+                const bool brk = !(bk > 1e-13 * ref) || !(bk > 1e-300);
+                if (bx == 0) {
+                    st.alpha[b * ld + k] = alpha;
+                    st.nrm[b * ld + k + 1] = bk;
+                    if (brk) st.stop[b] = k + 1;
+                }
+                sh[0] = brk ? 0.0 : 1.0 / bk;
+                sh[1] = bk / nk;
+                sh[2] = brk ? 1.0 : 0.0;
+                sh[3] = bk;
+            }
+            __syncthreads();
+            if (sh[2] != 0.0) active = false;
+            nk = sh[3];
+            __syncthreads();   // sh is rewritten by the next step's sums
+        }
+    }
+}
+
 // nrm[0] = |u_0| (start vector).
 __global__ void __launch_bounds__(kLzThreads) lz_norm0_kernel(LzState st, LzGeom g) {
     const int b = blockIdx.y;
@@ -361,180 +545,206 @@ __global__ void __launch_bounds__(kLzThreads) lz_norm0_kernel(LzState st, LzGeom
     if (instance_reduce(n2, st.partial, st.counter, b, g.nblk, &tot)) st.nrm[(size_t)b * st.ld] = sqrt(tot);
 }
 
-// Sturm count: number of eigenvalues of the symmetric tridiagonal (a, c) < x.
-__device__ int sturm_count(const double *a, const double *c, int n, double x, double pivmin) {
+// ---- extreme eigenvalues of symmetric tridiagonal matrices ----
+
+constexpr int kRitzThreads = 128;
+
+// Number of eigenvalues below x of the symmetric tridiagonal T with diagonal
+// a[0..n) and squared off-diagonals c2 (c2[i] couples rows i-1 and i;
+// c2[0] = 0).  It is the number of negative pivots of T - x I = L D L^T,
+// read off as the sign changes along the leading principal minors
+// p_i = det(T_{0..i} - x I) = (a_i - x) p_{i-1} - c2_i p_{i-2}: three FP64
+// operations per row and no division (FP64 division is a long sequence on
+// the narrow FP64 pipe).  A zero minor stands for the tiny pivot -tiny (a
+// zero pivot counted negative, as in bisection with a minimum pivot), and
+// the latest pair of minors is rescaled by 2^-+448 whenever both leave
+// [2^-448, 2^448]; signs and exponents are read as integers.
+__device__ int sturm_count_minors(const double *a, const double *c2, int n, double x, double tiny) {
     int cnt = 0;
-    double d = 1.0;
+    bool neg_prev = false;
+    double pm2 = 0.0, pm1 = 1.0;
     for (int i = 0; i < n; ++i) {
-        const double off = i > 0 ? c[i - 1] * c[i - 1] / d : 0.0;
-        d = a[i] - x - off;
-        if (fabs(d) < pivmin) d = -pivmin;
-        if (d < 0.0) ++cnt;
+        double pi = fma(a[i] - x, pm1, -c2[i] * pm2);
+        if ((__double_as_longlong(pi) << 1) == 0) pi = -tiny * pm1;
+        const int hi = __double2hiint(pi), hm = __double2hiint(pm1);
+        const bool neg = hi < 0;
+        cnt += neg != neg_prev;
+        neg_prev = neg;
+        const int em = max((hi >> 20) & 0x7FF, (hm >> 20) & 0x7FF);
+        pm2 = pm1;
+        pm1 = pi;
+        if (em > 1023 + 448) {
+            pm1 *= 0x1p-448;
+            pm2 *= 0x1p-448;
+        } else if (em < 1023 - 448) {
+            pm1 *= 0x1p+448;
+            pm2 *= 0x1p+448;
+        }
     }
     return cnt;
 }
 
-// Extreme eigenvalues of the Lanczos tridiagonal of each instance, by
-// multisection: warp 0 finds the largest, warp 1 the smallest; each round the
-// 32 lanes test 32 interior points of the bracket.  With have_prev, the
-// values in rmin / rmax come from a shorter tridiagonal of the same run: by
-// interlacing they bound the new extremes from inside (the largest can only
-// grow, the smallest only shrink), so the first round tests points at
-// geometrically growing distances beyond them, which brackets the new value
-// to about its change since the last check and saves most rounds of FP64
-// Sturm sequences.
-__global__ void lz_ritz_kernel(const double *alpha, const double *beta, int ld, int kcur, const int *stop,
-                               int have_prev, double *rmin, double *rmax) {
-    const int b = blockIdx.x;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int n = kcur;
-    if (stop[b] && stop[b] < n) n = stop[b];
-    if (n <= 0) return;
-    const double *a = alpha + (size_t)b * ld;
-    const double *c = beta + (size_t)b * ld + 1;   // beta_k = nrm[k+1]
+// Largest (want_max) or smallest eigenvalue of the symmetric tridiagonal
+// (a, c2) in shared memory, by multisection: each round the kRitzThreads
+// threads of the block test as many interior points of the bracket.  Every
+// thread of the block calls it and gets the same value.  A finite prev
+// inside the Gershgorin interval bounds the wanted extreme from inside (by
+// interlacing, the Ritz value of a shorter Lanczos run): the first round then
+// tests points at growing distances beyond it, which brackets the extreme to
+// about its change since prev and saves most of the rounds.
+__device__ double tridiag_extreme(const double *a, const double *c2, int n, bool want_max, double prev,
+                                  double *red) {
+    const int tid = threadIdx.x;
+    // Gershgorin interval
     double lo = INFINITY, hi = -INFINITY, amax = 0.0;
-    for (int i = 0; i < n; ++i) {
-        const double r = (i > 0 ? fabs(c[i - 1]) : 0.0) + (i + 1 < n ? fabs(c[i]) : 0.0);
+    for (int i = tid; i < n; i += kRitzThreads) {
+        const double r = sqrt(c2[i]) + (i + 1 < n ? sqrt(c2[i + 1]) : 0.0);
         lo = fmin(lo, a[i] - r);
         hi = fmax(hi, a[i] + r);
         amax = fmax(amax, fabs(a[i]) + r);
     }
-    const double pivmin = 1e-300 + amax * 1e-300;
-    const bool want_max = wid == 0;
-    if (have_prev) {
-        const double prev = want_max ? rmax[b] : rmin[b];
-        if (isfinite(prev) && prev > lo && prev < hi) {
-            const double delta = fmax(fabs(prev), 1e-300) * 1e-14;
-            const double x = want_max ? prev + delta * ldexp(1.0, lane) : prev - delta * ldexp(1.0, lane);
-            const int cnt = sturm_count(a, c, n, x, pivmin);
-            // max: the extreme lies beyond x  <=>  cnt < n ; min: <=> cnt >= 1... (cnt < 1 below x)
-            const bool beyond = want_max ? (cnt < n) : (cnt >= 1);
-            const unsigned m = __ballot_sync(0xffffffffu, beyond);
-            const int nb = __popc(m);   // the extreme lies beyond the first nb points
-            const double inner = nb == 0 ? prev : (want_max ? prev + delta * ldexp(1.0, nb - 1)
-                                                             : prev - delta * ldexp(1.0, nb - 1));
-            const double outer = nb == 32 ? (want_max ? hi : lo)
-                                          : (want_max ? prev + delta * ldexp(1.0, nb) : prev - delta * ldexp(1.0, nb));
-            if (want_max) {
-                lo = inner;
-                hi = fmin(outer, hi);
-            } else {
-                hi = inner;
-                lo = fmax(outer, lo);
-            }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    }
+    if ((tid & 31) == 0) {
+        red[tid >> 5] = lo;
+        red[4 + (tid >> 5)] = hi;
+        red[8 + (tid >> 5)] = amax;
+    }
+    __syncthreads();
+    lo = fmin(fmin(red[0], red[1]), fmin(red[2], red[3]));
+    hi = fmax(fmax(red[4], red[5]), fmax(red[6], red[7]));
+    amax = fmax(fmax(red[8], red[9]), fmax(red[10], red[11]));
+    const double tiny = fmax(amax, 1e-280) * 0x1p-200;
+    if (isfinite(prev) && prev > lo && prev < hi) {
+        const double delta = fmax(fabs(prev), 1e-300) * 1e-14;
+        const double sc = exp2(0.5 * tid);
+        const double x = want_max ? prev + delta * sc : prev - delta * sc;
+        const int cnt = sturm_count_minors(a, c2, n, x, tiny);
+        // the extreme lies beyond x: max <=> fewer than n below x; min <=> at least one below x
+        const int nb = __syncthreads_count(want_max ? (cnt < n) : (cnt >= 1));
+        const double inner = nb == 0 ? prev : prev + (want_max ? 1.0 : -1.0) * delta * exp2(0.5 * (nb - 1));
+        const double outer = nb == kRitzThreads ? (want_max ? hi : lo)
+                                                : prev + (want_max ? 1.0 : -1.0) * delta * exp2(0.5 * nb);
+        if (want_max) {
+            lo = inner;
+            hi = fmin(outer, hi);
+        } else {
+            hi = inner;
+            lo = fmax(outer, lo);
         }
     }
     for (int round = 0; round < 64; ++round) {
         if (!(hi - lo > 1e-14 * fmax(fabs(lo), fabs(hi)) + 1e-300)) break;
-        const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-        const int cnt = sturm_count(a, c, n, x, pivmin);
-        // max: lambda_max >= x  <=>  cnt < n ; min: lambda_min < x  <=>  cnt >= 1
-        const bool below = want_max ? (cnt < n) : (cnt < 1);
-        const unsigned m = __ballot_sync(0xffffffffu, below);
-        // "below" holds for a prefix of lanes (counts grow with x)
-        const int nb = __popc(m);
-        const double step = (hi - lo) / 33.0;
+        const double step = (hi - lo) / (double)(kRitzThreads + 1);
+        const double x = lo + step * (double)(tid + 1);
+        const int cnt = sturm_count_minors(a, c2, n, x, tiny);
+        // "below the extreme" holds for a prefix of the points
+        const int nb = __syncthreads_count(want_max ? (cnt < n) : (cnt < 1));
         const double nlo = nb > 0 ? lo + step * nb : lo;
-        const double nhi = nb < 32 ? lo + step * (nb + 1) : hi;
+        const double nhi = nb < kRitzThreads ? lo + step * (nb + 1) : hi;
         lo = nlo;
         hi = nhi;
     }
-    __syncthreads();   // both warps have read their previous values
-    if (lane == 0) {
-        if (want_max)
-            rmax[b] = 0.5 * (lo + hi);
-        else
-            rmin[b] = 0.5 * (lo + hi);
-    }
+    return 0.5 * (lo + hi);
 }
 
-// Extreme eigenvalues of C mu C (L x L, symmetric part) by cyclic Jacobi.
-// One warp: lane 0 computes each rotation, all lanes apply it to the rows and
-// columns of the matrix held in shared memory.
-__global__ void mu_tilde_extremes_kernel(const float *mu, int L, double *nu) {
-    __shared__ double A[kMaxLabels * kMaxLabels];
-    __shared__ double rm[kMaxLabels], cm[kMaxLabels];
-    __shared__ double cs_sn[2];
-    __shared__ int stop_flag;
-    const int lane = threadIdx.x;
-    if (lane < L) {
-        double r = 0.0, c = 0.0;
-        for (int j = 0; j < L; ++j) {
-            r += 0.5 * ((double)mu[lane * L + j] + (double)mu[j * L + lane]) / L;
-            c += 0.5 * ((double)mu[j * L + lane] + (double)mu[lane * L + j]) / L;
-        }
-        rm[lane] = r;
-        cm[lane] = c;
+// Extreme eigenvalues of the Lanczos tridiagonal of each instance: block
+// (b, 0) the largest, block (b, 1) the smallest.  With have_prev, rmin /
+// rmax hold the values of a shorter run of the same instance.
+__global__ void __launch_bounds__(kRitzThreads)
+lz_ritz_kernel(const double *alpha, const double *beta, int ld, int kcur, const int *stop, int have_prev,
+               double *rmin, double *rmax) {
+    extern __shared__ double tri[];   // a[n], c2[n]
+    __shared__ double red[12];
+    const int b = blockIdx.x;
+    const bool want_max = blockIdx.y == 0;
+    int n = kcur;
+    if (stop[b] && stop[b] < n) n = stop[b];
+    if (n <= 0) return;
+    double *a = tri, *c2 = tri + n;
+    for (int i = threadIdx.x; i < n; i += kRitzThreads) {
+        a[i] = alpha[(size_t)b * ld + i];
+        const double c = i > 0 ? beta[(size_t)b * ld + i] : 0.0;   // beta_{i-1} = nrm[i]
+        c2[i] = c * c;
     }
-    __syncwarp();
-    double tm = 0.0;
-    for (int j = 0; j < L; ++j) tm += rm[j] / L;
-    for (int i = 0; i < L; ++i)
+    __syncthreads();
+    double *slot = want_max ? rmax + b : rmin + b;
+    const double r = tridiag_extreme(a, c2, n, want_max, have_prev ? *slot : NAN, red);
+    if (threadIdx.x == 0) *slot = r;
+}
+
+// Extreme eigenvalues nu_min, nu_max of C mu_s C (mu_s the symmetric part of
+// mu, C the centring projector over labels), FP64.  Block 0 returns the
+// largest, block 1 the smallest.  Warp 0 reduces the matrix to tridiagonal
+// form by Householder reflections (lane i owns row i; reductions are
+// shuffle-down trees broadcast from lane 0, so every lane uses the same
+// values), then the block bisects.
+__global__ void __launch_bounds__(kRitzThreads) mu_tilde_extremes_kernel(const float *mu, int L, double *nu) {
+    __shared__ double A[kMaxLabels][kMaxLabels + 1];
+    __shared__ double v[kMaxLabels], q[kMaxLabels], rm[kMaxLabels];
+    __shared__ double a[kMaxLabels], c2[kMaxLabels];
+    __shared__ double red[12];
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        if (lane < L) {
+            double r = 0.0;
+            for (int j = 0; j < L; ++j) r += 0.5 * ((double)mu[lane * L + j] + (double)mu[j * L + lane]);
+            rm[lane] = r / L;   // row mean of mu_s (= column mean: mu_s is symmetric)
+        }
+        __syncwarp();
+        double tm = 0.0;
+        for (int j = 0; j < L; ++j) tm += rm[j];
+        tm /= L;
         if (lane < L)
-            A[i * L + lane] =
-                0.5 * ((double)mu[i * L + lane] + (double)mu[lane * L + i]) - rm[i] - cm[lane] + tm;
-    __syncwarp();
-    for (int sweep = 0; sweep < 60; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        if (lane < L)
-            for (int j = 0; j < L; ++j) {
-                const double v = A[lane * L + j] * A[lane * L + j];
-                tot += v;
-                if (j != lane) off += v;
+            for (int j = 0; j < L; ++j)
+                A[lane][j] = 0.5 * ((double)mu[lane * L + j] + (double)mu[j * L + lane]) - rm[lane] - rm[j] + tm;
+        __syncwarp();
+        for (int k = 0; k + 2 < L; ++k) {
+            const double xi = (lane > k + 1 && lane < L) ? A[lane][k] : 0.0;
+            const double tail = __shfl_sync(0xffffffffu, warp_sum(xi * xi), 0);
+            if (tail == 0.0) continue;   // column k is already reduced
+            const double x1 = A[k + 1][k];
+            const double nrm = sqrt(x1 * x1 + tail);
+            const double alpha = x1 > 0.0 ? -nrm : nrm;
+            const double h = nrm * nrm - x1 * alpha;   // v^T v / 2
+            const double vi = lane == k + 1 ? x1 - alpha : xi;
+            v[lane] = vi;
+            __syncwarp();
+            double pi = 0.0;
+            if (lane > k && lane < L) {
+                for (int j = k + 1; j < L; ++j) pi = fma(A[lane][j], v[j], pi);
+                pi /= h;
             }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            off += __shfl_xor_sync(0xffffffffu, off, o);
-            tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        }
-        // off-diagonal mass below (1e-13 |A|)^2: the diagonal then holds the
-        // eigenvalues to ~1e-26 relative (the error is second order in it)
-        if (off <= 1e-26 * (tot > 0 ? tot : 1.0)) break;
-        const double tiny = 1e-18 * sqrt(tot);
-        for (int p = 0; p < L; ++p)
-            for (int r = p + 1; r < L; ++r) {
-                if (lane == 0) {
-                    const double apr = A[p * L + r];
-                    if (fabs(apr) <= tiny) {
-                        stop_flag = 1;
-                    } else {
-                        stop_flag = 0;
-                        const double theta = (A[r * L + r] - A[p * L + p]) / (2.0 * apr);
-                        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                        const double c = 1.0 / sqrt(t * t + 1.0);
-                        cs_sn[0] = c;
-                        cs_sn[1] = t * c;
-                    }
-                }
-                __syncwarp();
-                if (stop_flag) {
-                    __syncwarp();
-                    continue;
-                }
-                const double c = cs_sn[0], sn = cs_sn[1];
-                if (lane < L) {
-                    const double akp = A[lane * L + p], akr = A[lane * L + r];
-                    A[lane * L + p] = c * akp - sn * akr;
-                    A[lane * L + r] = sn * akp + c * akr;
-                }
-                __syncwarp();
-                if (lane < L) {
-                    const double apk = A[p * L + lane], ark = A[r * L + lane];
-                    A[p * L + lane] = c * apk - sn * ark;
-                    A[r * L + lane] = sn * apk + c * ark;
-                }
-                __syncwarp();
+            const double K = __shfl_sync(0xffffffffu, warp_sum(vi * pi), 0) / (2.0 * h);
+            const double qi = pi - K * vi;
+            q[lane] = qi;
+            __syncwarp();
+            if (lane > k && lane < L)
+                for (int j = k + 1; j < L; ++j) A[lane][j] -= fma(vi, q[j], qi * v[j]);
+            __syncwarp();
+            if (lane > k + 1 && lane < L) {
+                A[lane][k] = 0.0;
+                A[k][lane] = 0.0;
             }
-    }
-    if (lane == 0) {
-        double lo = INFINITY, hi = -INFINITY;
-        for (int i = 0; i < L; ++i) {
-            lo = fmin(lo, A[i * L + i]);
-            hi = fmax(hi, A[i * L + i]);
+            if (lane == k + 1) {
+                A[lane][k] = alpha;
+                A[k][lane] = alpha;
+            }
+            __syncwarp();
         }
-        nu[0] = lo;
-        nu[1] = hi;
+        if (lane < L) {
+            a[lane] = A[lane][lane];
+            c2[lane] = lane > 0 ? A[lane][lane - 1] * A[lane][lane - 1] : 0.0;
+        }
     }
+    __syncthreads();
+    const bool want_max = blockIdx.x == 0;
+    const double r = tridiag_extreme(a, c2, L, want_max, NAN, red);
+    if (tid == 0) nu[want_max ? 1 : 0] = r;
 }
 
 // Lambda_b and eta_b = 1/(1 + max(Lambda_b, 0)).
@@ -563,7 +773,7 @@ __global__ void set_lambda_zero_kernel(int B, double *Lambda, float *eta) {
 }  // namespace
 
 cudaError_t launch_mu_tilde_extremes(const float *mu_dev, int L, double *nu, cudaStream_t st) {
-    mu_tilde_extremes_kernel<<<1, 32, 0, st>>>(mu_dev, L, nu);
+    mu_tilde_extremes_kernel<<<2, kRitzThreads, 0, st>>>(mu_dev, L, nu);
     return cudaGetLastError();
 }
 
@@ -614,6 +824,10 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
     std::vector<int> hstop(B);
     int k = 0;
     int have_prev = 0;   // the Ritz values of the previous check bound the next ones
+    // cooperative form (scalar W): one launch per chunk of steps
+    bool coop = false;
+    LzCoop C{};
+    int habort = 0;
     dim3 gridp(g.nblk, B);
     const int nblk_dense = (job.W + kLzThreads / 32 - 1) / (kLzThreads / 32);
     S.ld = ld;
@@ -655,20 +869,43 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
     LZ_CHECK(cudaGetLastError());
     nl += 2;
 
-    // one graph of kChunk steps, captured once and replayed
     LZ_CHECK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    LZ_CHECK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < kChunk; ++i) {
-        if (job.Kdense)
-            lz_step_a_dense_kernel<<<dim3(nblk_dense, B), kLzThreads, 0, cap>>>(S, job.Kdense, g, nblk_dense);
-        else if (g.Lv == 1)
-            lz_step_a_scalar_kernel<<<gridp, kLzThreads, 0, cap>>>(S, wd, g);
-        else
-            lz_step_a_kernel<<<gridp, kLzThreads, 0, cap>>>(S, job.w, mu_dev, g);
-        lz_step_b_kernel<<<gridp, kLzThreads, 0, cap>>>(S, g);
+    if (!job.Kdense && g.Lv == 1) {
+        // all blocks must be resident at once: at most one per SM and instance
+        int dev = 0, sms = 0, coop_ok = 0, occ = 0;
+        LZ_CHECK(cudaGetDevice(&dev));
+        LZ_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        LZ_CHECK(cudaDeviceGetAttribute(&coop_ok, cudaDevAttrCooperativeLaunch, dev));
+        LZ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lz_chunk_scalar_kernel, kCoopThreads, 0));
+        const int need = (job.H * job.W + kCoopThreads - 1) / kCoopThreads;
+        if (coop_ok && occ >= 1 && B <= sms * occ) {
+            C.gx = std::max(1, std::min(need, B <= sms ? sms / B : 1));
+            coop = true;
+        }
     }
-    LZ_CHECK(cudaStreamEndCapture(cap, &graph));
-    LZ_CHECK(cudaGraphInstantiate(&exec, graph, 0));
+    if (coop) {
+        LZ_CHECK(cudaMallocAsync((void **)&C.bar, 2 * sizeof(unsigned), st));
+        LZ_CHECK(cudaMallocAsync((void **)&C.abort, sizeof(int), st));
+        LZ_CHECK(cudaMallocAsync((void **)&C.part, (size_t)2 * B * C.gx * sizeof(double), st));
+        LZ_CHECK(cudaMemsetAsync(C.bar, 0, 2 * sizeof(unsigned), st));
+        LZ_CHECK(cudaMemsetAsync(C.abort, 0, sizeof(int), st));
+    } else {
+        // one graph of kChunk steps, captured once and replayed
+        LZ_CHECK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        for (int i = 0; i < kChunk; ++i) {
+            if (job.Kdense)
+                lz_step_a_dense_kernel<<<dim3(nblk_dense, B), kLzThreads, 0, cap>>>(S, job.Kdense, g, nblk_dense);
+            else if (g.Lv == 1)
+                lz_step_a_scalar_kernel<<<gridp, kLzThreads, 0, cap>>>(S, wd, g);
+            else
+                lz_step_a_kernel<<<gridp, kLzThreads, 0, cap>>>(S, job.w, mu_dev, g);
+            lz_step_b_kernel<<<gridp, kLzThreads, 0, cap>>>(S, g);
+        }
+        LZ_CHECK(cudaStreamEndCapture(cap, &graph));
+        LZ_CHECK(cudaGraphInstantiate(&exec, graph, 0));
+    }
+    LZ_CHECK(cudaFuncSetAttribute(lz_ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(2 * ld * sizeof(double))));
     if (job.mu_sym) {
         // the small eigen-solve of C mu C runs on the side stream, overlapped
         // with the Lanczos steps (it only needs mu, copied above)
@@ -676,22 +913,36 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
         LZ_CHECK(cudaEventCreateWithFlags(&ev_nu, cudaEventDisableTiming));
         LZ_CHECK(cudaEventRecord(ev_mu, st));
         LZ_CHECK(cudaStreamWaitEvent(cap, ev_mu, 0));
-        mu_tilde_extremes_kernel<<<1, 32, 0, cap>>>(mu_dev, job.L, nu);
+        mu_tilde_extremes_kernel<<<2, kRitzThreads, 0, cap>>>(mu_dev, job.L, nu);
         LZ_CHECK(cudaGetLastError());
         LZ_CHECK(cudaEventRecord(ev_nu, cap));
     }
     while (k < kmax) {
-        LZ_CHECK(cudaGraphLaunch(exec, st));
-        nl += 2 * kChunk;
+        if (coop) {
+            int k0 = k, k1 = std::min(k + kChunk, kmax);
+            void *args[] = {&S, &wd, &g, &C, &k0, &k1};
+            LZ_CHECK(cudaLaunchCooperativeKernel((const void *)lz_chunk_scalar_kernel, dim3(C.gx, B),
+                                                 dim3(kCoopThreads), args, 0, st));
+            nl += 1;
+        } else {
+            LZ_CHECK(cudaGraphLaunch(exec, st));
+            nl += 2 * kChunk;
+        }
         k = std::min(k + kChunk, kmax);
-        lz_ritz_kernel<<<B, 64, 0, st>>>(S.alpha, S.nrm, ld, k, S.stop, have_prev, rmin, rmax);
+        lz_ritz_kernel<<<dim3(B, 2), kRitzThreads, 2 * ld * sizeof(double), st>>>(S.alpha, S.nrm, ld, k, S.stop,
+                                                                                  have_prev, rmin, rmax);
         have_prev = 1;
         LZ_CHECK(cudaGetLastError());
         nl += 1;
         LZ_CHECK(cudaMemcpyAsync(hmin.data(), rmin, B * sizeof(double), cudaMemcpyDeviceToHost, st));
         LZ_CHECK(cudaMemcpyAsync(hmax.data(), rmax, B * sizeof(double), cudaMemcpyDeviceToHost, st));
         LZ_CHECK(cudaMemcpyAsync(hstop.data(), S.stop, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (coop) LZ_CHECK(cudaMemcpyAsync(&habort, C.abort, sizeof(int), cudaMemcpyDeviceToHost, st));
         LZ_CHECK(cudaStreamSynchronize(st));
+        if (habort != 0) {
+            rc = -5;   // a barrier wait ran out
+            goto done;
+        }
         bool all = true;
         for (int b = 0; b < B; ++b) {
             const double sc = fmax(fmax(fabs(hmin[b]), fabs(hmax[b])), 1e-300);
@@ -722,6 +973,9 @@ done:
     if (S.counter) cudaFreeAsync(S.counter, st);
     if (S.stop) cudaFreeAsync(S.stop, st);
     if (S.kdev) cudaFreeAsync(S.kdev, st);
+    if (C.bar) cudaFreeAsync(C.bar, st);
+    if (C.abort) cudaFreeAsync(C.abort, st);
+    if (C.part) cudaFreeAsync(C.part, st);
     if (mu_dev) cudaFreeAsync(mu_dev, st);
     return rc;
 }

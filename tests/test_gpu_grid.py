@@ -313,3 +313,24 @@ def test_device_allocation_failure_is_reported(env):
     s_ref = oracle_model(oracle, d).prox_step(0.5, oracle_model(oracle, d).init_logq())
     s, _, _ = gpu_run(binding, torch, d, 0.5, 1)
     assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q
+
+
+@pytest.mark.parametrize("B,Hh,Ww,L,conn", [(5, 9, 11, 3, 8), (2, 1, 13, 4, 4), (3, 16, 5, 5, 8)])
+def test_step_constant_batch_vs_dense_eigensolve(env, B, Hh, Ww, L, conn):
+    """Every instance of a batch gets its own constant (symmetric mu: the
+    scalar Lanczos form, one cooperative launch per chunk of steps), equal to
+    the top eigenvalue of its tangent-projected Hessian."""
+    binding, oracle, torch = env
+    ds = [synth.random_grid(Hh, Ww, L, conn, seed=900 + 7 * i, symmetric=True, coupling_scale=1.3)
+          for i in range(B)]
+    for d in ds:
+        d["mu"] = ds[0]["mu"]
+    topo_ = binding.CRF_GRID8 if conn == 8 else binding.CRF_GRID4
+    with binding.CRF(topo_, L, Hh, Ww, batch=B) as crf:
+        crf.set_unary(np.stack([d["U"] for d in ds]))
+        crf.set_pairwise(ds[0]["mu"], np.stack([d["w"] for d in ds]))
+        lam, eta = crf.lipschitz()
+    for i, d in enumerate(ds):
+        ref = oracle_model(oracle, d).hessian_eigenvalues(projected=True)[-1]
+        assert math.isclose(lam[i], ref, rel_tol=1e-8, abs_tol=1e-12)
+        assert math.isclose(eta[i], 1.0 / (1.0 + max(ref, 0.0)), rel_tol=1e-6)
