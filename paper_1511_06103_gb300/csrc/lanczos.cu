@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "internal.h"
@@ -138,6 +139,16 @@ __device__ __forceinline__ double *lz_buf(const LzState &s, int i) {
 // FP64 copy of the pixel-major edge weights for the scalar form (FP64 is the
 // slow pipe on this part: converting once instead of every step halves the
 // FP64 work of a Lanczos step).
+// max |w| as float bits (non-negative floats order as unsigned integers)
+__global__ void lz_absmax_kernel(const float *__restrict__ w, size_t n, unsigned *out_bits) {
+    float m = 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(w[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out_bits, __float_as_uint(m));
+}
+
 __global__ void lz_weights_f64_kernel(const float *__restrict__ w, double *__restrict__ wd, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         wd[i] = (double)w[i];
@@ -346,15 +357,96 @@ lz_step_b_kernel(LzState st, LzGeom g) {
     }
 }
 
+// ---- double-float arithmetic ----
+//
+// FP64 issues at 2 lanes per clock per SM on this part against 128 for FP32,
+// so the arithmetic of the scalar Lanczos steps and of the Sturm sequences is
+// carried in double-float: a value is the unevaluated sum h + l of two floats
+// with |l| <= ulp(h) / 2, about 48 significant bits.  The error-free
+// transformations are Knuth's two-sum, Dekker's fast two-sum (|a| >= |b|)
+// and the FMA form of Dekker's exact product; sums of products accumulate
+// the rounding errors of the running sum in a second float (the compensated
+// dot product of Ogita, Rump and Oishi, 2005).  The _rn intrinsics keep the
+// compiler from contracting or reassociating these sequences.
+
+struct df {
+    float h, l;
+};
+
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// (s, e) with s = fl(a + b) and a + b = s + e exactly
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ df df_from(double v) {
+    const float h = __double2float_rn(v);
+    return {h, __double2float_rn(v - (double)h)};
+}
+
+__device__ __forceinline__ double df_to(df x) { return (double)x.h + (double)x.l; }
+
+__device__ __forceinline__ df df_add(df x, df y) {
+    float s, e;
+    two_sum(x.h, y.h, s, e);
+    return df_fast_two_sum(s, __fadd_rn(e, __fadd_rn(x.l, y.l)));
+}
+
+__device__ __forceinline__ df df_mul(df x, df y) {
+    const float p = __fmul_rn(x.h, y.h);
+    float e = __fmaf_rn(x.h, y.h, -p);
+    e = __fmaf_rn(x.h, y.l, e);
+    e = __fmaf_rn(x.l, y.h, e);
+    return df_fast_two_sum(p, e);
+}
+
+// running compensated sum (sh, sl) += a * b
+__device__ __forceinline__ void acc_prod(float &sh, float &sl, df a, df b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float pe = __fmaf_rn(a.h, b.h, -p);
+    pe = __fmaf_rn(a.h, b.l, pe);
+    pe = __fmaf_rn(a.l, b.h, pe);
+    float s, e;
+    two_sum(sh, p, s, e);
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(e, pe));
+}
+
+// running compensated sum (sh, sl) += w * b, w a float
+__device__ __forceinline__ void acc_prod_f(float &sh, float &sl, float w, df b) {
+    const float p = __fmul_rn(w, b.h);
+    const float pe = __fmaf_rn(w, b.l, __fmaf_rn(w, b.h, -p));
+    float s, e;
+    two_sum(sh, p, s, e);
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(e, pe));
+}
+
+__device__ __forceinline__ df warp_sum_df(df v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const df u = {__shfl_down_sync(0xffffffffu, v.h, o), __shfl_down_sync(0xffffffffu, v.l, o)};
+        v = df_add(v, u);
+    }
+    return v;
+}
+
 // ---- cooperative form: a whole chunk of scalar-form steps in one launch ----
 //
 // One block per SM (or fewer), every block of an instance owning a fixed
 // strided set of pixels; the two reductions of a step (alpha_k and |u_{k+1}|)
-// are block partials summed in a fixed order by every block after a grid
-// barrier, so all blocks hold the same alpha_k and beta_k and no launch or
-// last-block tail separates the steps.  1/|u_k| and the recurrence
-// coefficients are formed once per block and step: FP64 division is a long
-// sequence on the narrow FP64 pipe of this part.
+// are block partials summed in a fixed order after a grid barrier by every
+// block, so all blocks hold the same alpha_k and beta_k and no launch or
+// last-block tail separates the steps.  The vectors u_k are stored as
+// double-float pairs (same 8 bytes as an FP64 value); the step's scalars are
+// FP64, formed once per block (FP64 division is a long sequence on the
+// narrow FP64 pipe).
 
 constexpr int kCoopThreads = 512;
 constexpr long long kLzWaitCycles = 4000000000ll;   // ~2 s at 2 GHz per barrier wait
@@ -366,68 +458,72 @@ struct LzCoop {
     int gx;          // blocks per instance
 };
 
-// Grid-wide barrier of a cooperative launch with a bounded wait.  Thread 0
-// arrives on the counter; the last arrival resets it and advances the
-// generation word that the others poll.  Returns false in every thread of
-// the block when this or another block's wait ran out.
+// Grid-wide barrier of a cooperative launch with a bounded wait, run by one
+// thread per block.  The thread arrives on the counter with an acquire-
+// release atomic (its block's earlier writes, ordered before it by the
+// block barrier, are released with it); the last arrival resets the counter
+// and advances the generation word with a release, which the others poll
+// with acquire loads.  Returns false when this or another block's wait ran
+// out of its clock budget (the abort word is then set for everyone).
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ bool grid_arrive_wait(const LzCoop &c, unsigned nblocks) {
+    volatile int *ab = c.abort;
+    if (*ab != 0) return false;
+    const unsigned g0 = ld_acquire(c.bar + 1);
+    if (atom_add_acq_rel(c.bar, 1u) == nblocks - 1) {
+        atomicExch(c.bar, 0u);
+        red_add_release(c.bar + 1, 1u);
+        return true;
+    }
+    const long long t0 = clock64();
+    while (ld_acquire(c.bar + 1) == g0) {
+        if (*ab != 0) return false;
+        if (clock64() - t0 > kLzWaitCycles) {
+            atomicExch(c.abort, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+// The same as a block-level call: every thread returns the outcome.
 __device__ bool coop_barrier(const LzCoop &c, unsigned nblocks) {
     __shared__ int ok;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *gen = c.bar + 1;
-        volatile int *ab = c.abort;
-        int good = *ab == 0;
-        if (good) {
-            const unsigned g0 = *gen;
-            __threadfence();
-            if (atomicAdd(c.bar, 1u) == nblocks - 1) {
-                atomicExch(c.bar, 0u);
-                __threadfence();
-                atomicAdd(c.bar + 1, 1u);
-            } else {
-                const long long t0 = clock64();
-                while (*gen == g0) {
-                    if (*ab != 0) {
-                        good = 0;
-                        break;
-                    }
-                    if (clock64() - t0 > kLzWaitCycles) {
-                        atomicExch(c.abort, 1);
-                        good = 0;
-                        break;
-                    }
-                }
-            }
-            __threadfence();
-        }
-        ok = good;
-    }
+    if (threadIdx.x == 0) ok = grid_arrive_wait(c, nblocks) ? 1 : 0;
     __syncthreads();
     return ok != 0;
 }
 
-// Sum of n partials in a fixed order (strided per thread, fixed-shape warp
-// tree, warps in index order); every thread gets the same value.
-__device__ double coop_sum(const double *p, int n, double *red, double *out) {
+// Sum of the n partials of an instance in a fixed order by warp 0 (strided
+// per lane, fixed-shape tree); the value is returned in thread 0.
+__device__ double coop_sum(const double *p, int n) {
+    if (threadIdx.x >= 32) return 0.0;
     double a = 0.0;
-    for (int i = threadIdx.x; i < n; i += kCoopThreads) a += __ldcg(p + i);
-    a = warp_sum(a);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < kCoopThreads / 32; ++k) s += red[k];
-        *out = s;
-    }
-    __syncthreads();
-    return *out;
+    for (int i = threadIdx.x; i < n; i += 32) a += __ldcg(p + i);
+    return warp_sum(a);
 }
 
-// Block total of v into part[slot] (thread 0 writes).
-__device__ void coop_partial(double v, double *red, double *part) {
-    v = warp_sum(v);
-    __syncthreads();   // red may still be read by a previous coop_sum
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+// Block total of the threads' double-float values into *part (thread 0):
+// double-float warp trees, then the warps' FP64 values in index order.
+__device__ void coop_partial(df v, double *red, double *part) {
+    v = warp_sum_df(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = df_to(v);
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
@@ -436,80 +532,307 @@ __device__ void coop_partial(double v, double *red, double *part) {
     }
 }
 
-// Steps k0 .. k1-1 of the scalar form (t = W v_k, symmetric weighted
-// adjacency of the grid), same recurrence and stopping rule as the
-// two-kernel form above.  Vectors written inside the launch are read through
-// L2 only (__ldcg): L1 is not coherent across blocks.
+// (W u)_p of the scalar form: the weighted neighbour sum over the grid's
+// edges at pixel p, compensated, from the FP32 pixel-major weights (read
+// only, through L1).  The vector u comes from global memory (read through L2:
+// it is written inside the launch and L1 is not coherent across blocks) or,
+// with STAGE, from the shared-memory copy of pixels lo.. of the instance.
+template <bool STAGE>
+__device__ __forceinline__ df w_times(const float *__restrict__ wb, const float2 *u, int lo, const LzGeom &g,
+                                      int nd, int p) {
+    const int y = p / g.W, x = p - y * g.W;
+    float ah = 0.f, al = 0.f;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        if (d >= nd) break;
+        const int dy = d == 0 ? 0 : 1, dx = d == 0 ? 1 : (d == 1 ? 0 : (d == 2 ? 1 : -1));
+        const int yo = y + dy, xo = x + dx;
+        if (yo < g.H && xo >= 0 && xo < g.W) {
+            const int q = yo * g.W + xo;
+            const float2 v = STAGE ? u[q - lo] : __ldcg(u + q);
+            acc_prod_f(ah, al, __ldg(wb + (size_t)p * nd + d), df{v.x, v.y});
+        }
+        const int yi = y - dy, xi = x - dx;
+        if (yi >= 0 && xi >= 0 && xi < g.W) {
+            const int q = yi * g.W + xi;
+            const float2 v = STAGE ? u[q - lo] : __ldcg(u + q);
+            acc_prod_f(ah, al, __ldg(wb + (size_t)q * nd + d), df{v.x, v.y});
+        }
+    }
+    return df_fast_two_sum(ah, al);
+}
+
+// The step's scalars, formed in FP64 by thread 0 of every block (all blocks
+// hold the same sums, so they agree) and handed to the block as double-float
+// pairs in shared memory; no other thread touches the FP64 pipe.
+struct CoopScalars {
+    float inv_h, inv_l;   // 1 / |u_k|
+    float cm_h, cm_l;     // -|u_k| / |u_{k-1}|
+    float ca_h, ca_l;     // -alpha_k / |u_k|
+    int brk;              // the instance stopped at this step
+};
+
+struct CoopThread0 {      // FP64 state, meaningful in thread 0
+    double nk, inv, alpha;
+};
+
+__device__ __forceinline__ void coop_scalars_init(const LzState &st, int b, int k0, bool active, CoopScalars &cs,
+                                                  CoopThread0 &t0) {
+    const size_t ld = (size_t)st.ld;
+    t0.nk = st.nrm[b * ld + k0];
+    t0.inv = active ? 1.0 / t0.nk : 0.0;
+    t0.alpha = 0.0;
+    const df a = df_from(t0.inv), m = df_from(active && k0 > 0 ? -t0.nk / st.nrm[b * ld + k0 - 1] : 0.0);
+    cs.inv_h = a.h;
+    cs.inv_l = a.l;
+    cs.cm_h = m.h;
+    cs.cm_l = m.l;
+    cs.ca_h = cs.ca_l = 0.f;
+    cs.brk = 0;
+}
+
+// after the alpha reduction (s = sum of t . u_k over the instance)
+__device__ __forceinline__ void coop_scalars_alpha(double s, CoopScalars &cs, CoopThread0 &t0) {
+    t0.alpha = s * t0.inv;
+    const df ca = df_from(-t0.alpha * t0.inv);
+    cs.ca_h = ca.h;
+    cs.ca_l = ca.l;
+}
+
+// after the norm reduction (s = |u_{k+1}|^2): record alpha_k and beta_k,
+// apply the stopping rule, form the next step's scalars
+__device__ __forceinline__ void coop_scalars_beta(double s, const LzState &st, int b, int bx, int k, CoopScalars &cs,
+                                                  CoopThread0 &t0) {
+    const size_t ld = (size_t)st.ld;
+    const double bk = sqrt(s);
+    const double ref = fabs(t0.alpha) + t0.nk;
+    const bool brk = !(bk > 1e-13 * ref) || !(bk > 1e-300);
+    if (bx == 0) {
+        st.alpha[b * ld + k] = t0.alpha;
+        st.nrm[b * ld + k + 1] = bk;
+        if (brk) st.stop[b] = k + 1;
+    }
+    t0.inv = brk ? 0.0 : 1.0 / bk;
+    const df a = df_from(t0.inv), m = df_from(-bk / t0.nk);
+    cs.inv_h = a.h;
+    cs.inv_l = a.l;
+    cs.cm_h = m.h;
+    cs.cm_l = m.l;
+    cs.brk = brk ? 1 : 0;
+    t0.nk = bk;
+}
+
+// Steps k0 .. k1-1 of the scalar form (t = W v_k, W the symmetric weighted
+// adjacency of the grid), any size: each thread strides over the pixels of
+// its instance and every vector travels through L2 (t in the u_{k+1}
+// buffer).  The recurrence and stopping rule are those of the two-kernel
+// FP64 form above.
 __global__ void __launch_bounds__(kCoopThreads, 1)
-lz_chunk_scalar_kernel(LzState st, const double *__restrict__ w, LzGeom g, LzCoop c, int k0, int k1) {
+lz_chunk_strided_kernel(LzState st, const float *__restrict__ w, LzGeom g, LzCoop c, int k0, int k1, int) {
     __shared__ double red[kCoopThreads / 32];
-    __shared__ double sh[4];
+    __shared__ CoopScalars cs;
     const int b = blockIdx.y, bx = blockIdx.x, tid = threadIdx.x;
     const unsigned nblocks = gridDim.x * gridDim.y;
     const int N = g.H * g.W;
     const int nd = g.conn == 8 ? 4 : 2;
     const size_t base = (size_t)b * N;
-    const double *wb = w + base * nd;
+    const float *wb = w + base * nd;
+    double *pa = c.part + (size_t)b * c.gx;
+    double *pb = c.part + ((size_t)g.B + b) * c.gx;
+    const int p0 = bx * kCoopThreads + tid, stride = c.gx * kCoopThreads;
+    bool active = st.stop[b] == 0;
+    CoopThread0 t0{};
+    if (tid == 0) coop_scalars_init(st, b, k0, active, cs, t0);
+    __syncthreads();
+    for (int k = k0; k < k1; ++k) {
+        const df inv = {cs.inv_h, cs.inv_l}, cm = {cs.cm_h, cs.cm_l};
+        const float2 *v = reinterpret_cast<const float2 *>(lz_buf(st, k % 3)) + base;
+        float2 *t = reinterpret_cast<float2 *>(lz_buf(st, (k + 1) % 3)) + base;
+        const float2 *vm = reinterpret_cast<const float2 *>(lz_buf(st, (k + 2) % 3)) + base;
+        // t = W v_k = (W u_k) / |u_k| and the partial of alpha_k |u_k| = t . u_k
+        float dh = 0.f, dl = 0.f;
+        if (active) {
+            for (int p = p0; p < N; p += stride) {
+                const df r = df_mul(w_times<false>(wb, v, 0, g, nd, p), inv);
+                __stcg(t + p, make_float2(r.h, r.l));
+                const float2 u = __ldcg(v + p);
+                acc_prod(dh, dl, r, df{u.x, u.y});
+            }
+        }
+        coop_partial(df_fast_two_sum(dh, dl), red, pa + bx);
+        if (!coop_barrier(c, nblocks)) return;
+        const double sa = coop_sum(pa, c.gx);
+        if (tid == 0 && active) coop_scalars_alpha(sa, cs, t0);
+        __syncthreads();
+        // u_{k+1} = t - alpha_k v_k - |u_k| v_{k-1} and its squared norm
+        float nh = 0.f, nl = 0.f;
+        if (active) {
+            const df ca = {cs.ca_h, cs.ca_l};
+            for (int p = p0; p < N; p += stride) {
+                const float2 tp = __ldcg(t + p), u = __ldcg(v + p);
+                float rh = tp.x, rl = tp.y;
+                acc_prod(rh, rl, ca, df{u.x, u.y});
+                if (k > 0) {
+                    const float2 m2 = __ldcg(vm + p);
+                    acc_prod(rh, rl, cm, df{m2.x, m2.y});
+                }
+                const df r = df_fast_two_sum(rh, rl);
+                __stcg(t + p, make_float2(r.h, r.l));
+                acc_prod(nh, nl, r, r);
+            }
+        }
+        coop_partial(df_fast_two_sum(nh, nl), red, pb + bx);
+        if (!coop_barrier(c, nblocks)) return;
+        const double sb = coop_sum(pb, c.gx);
+        if (tid == 0 && active) coop_scalars_beta(sb, st, b, bx, k, cs, t0);
+        __syncthreads();
+        if (cs.brk != 0) active = false;
+    }
+}
+
+// Steps k0 .. k1-1 of the scalar form with the vectors staged in shared
+// memory.  Block bx of an instance owns the contiguous pixels [ps, pe);
+// every neighbour of them lies in [ps - W - 1, pe + W + 1), which the block
+// keeps in shared memory: its own part is written there by the update, the
+// two halo strips are loaded from L2 once per step.  Warp 0 runs the control
+// path (grid barriers, fixed-order sums, the FP64 scalars, which it forms
+// while the other warps load the halo); warps 1.. own at most PPT pixels per
+// thread and keep u_k, u_{k-1} and t of them in registers.  The product is
+// taken of the unnormalised u_k (t' = W u_k, alpha_k = t'.u_k / |u_k|^2), so
+// that the new norm is needed only by the update.
+constexpr int kCoopWorkers = kCoopThreads - 32;
+
+template <int PPT>
+__global__ void __launch_bounds__(kCoopThreads, 1)
+lz_chunk_tile_kernel(LzState st, const float *__restrict__ w, LzGeom g, LzCoop c, int k0, int k1, int chunk) {
+    extern __shared__ float2 stage[];
+    __shared__ double red[kCoopThreads / 32];
+    __shared__ float fs[8];   // c1 = 1/|u_k| (h, l), c3 = -|u_k|/|u_{k-1}| (h, l), c2 = -alpha_k/|u_k| (h, l)
+    __shared__ int flags[2];  // [0] grid barrier outcome, [1] the instance stopped
+    const int b = blockIdx.y, bx = blockIdx.x, tid = threadIdx.x, warp = tid >> 5;
+    const unsigned nblocks = gridDim.x * gridDim.y;
+    const int N = g.H * g.W, W = g.W;
+    const int nd = g.conn == 8 ? 4 : 2;
+    const size_t base = (size_t)b * N;
+    const float *wb = w + base * nd;
     double *pa = c.part + (size_t)b * c.gx;
     double *pb = c.part + ((size_t)g.B + b) * c.gx;
     const size_t ld = (size_t)st.ld;
+    const int ps = min(N, bx * chunk), pe = min(N, ps + chunk);
+    const int lo = max(0, ps - W - 1), hi = min(N, pe + W + 1);
+    const int wt = tid - 32;
     bool active = st.stop[b] == 0;
-    double nk = st.nrm[b * ld + k0];   // |u_k|
+    // thread 0: FP64 state (norms of u_k, u_{k-1}; 1/|u_k|^2 and 1/|u_k|)
+    double nk = 0.0, inv = 0.0, inv_s = 0.0, alpha = 0.0;
     if (tid == 0) {
-        sh[0] = active ? 1.0 / nk : 0.0;
-        sh[1] = active && k0 > 0 ? nk / st.nrm[b * ld + k0 - 1] : 0.0;
+        nk = st.nrm[b * ld + k0];
+        inv = active ? 1.0 / nk : 0.0;
+        inv_s = inv * inv;
+        const df a = df_from(inv), m = df_from(active && k0 > 0 ? -nk / st.nrm[b * ld + k0 - 1] : 0.0);
+        fs[0] = a.h;
+        fs[1] = a.l;
+        fs[2] = m.h;
+        fs[3] = m.l;
+        flags[1] = 0;
+    }
+    df uk[PPT], um[PPT], tt[PPT];
+    {
+        const float2 *v0 = reinterpret_cast<const float2 *>(lz_buf(st, k0 % 3)) + base;
+        const float2 *v1 = reinterpret_cast<const float2 *>(lz_buf(st, (k0 + 2) % 3)) + base;
+        for (int q = lo + tid; q < hi; q += kCoopThreads) stage[q - lo] = __ldcg(v0 + q);
+        if (wt >= 0) {
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                const int p = ps + wt + j * kCoopWorkers;
+                const float2 a = p < pe ? __ldcg(v0 + p) : make_float2(0.f, 0.f);
+                const float2 m = p < pe ? __ldcg(v1 + p) : make_float2(0.f, 0.f);
+                uk[j] = df{a.x, a.y};
+                um[j] = df{m.x, m.y};
+                tt[j] = df{0.f, 0.f};
+            }
+        }
     }
     __syncthreads();
     for (int k = k0; k < k1; ++k) {
-        const double inv = sh[0], cm = sh[1];
-        const double *v = lz_buf(st, k % 3) + base;
-        double *t = lz_buf(st, (k + 1) % 3) + base;
-        const double *um = lz_buf(st, (k + 2) % 3) + base;
-        // t = W v_k and the partial of alpha_k = v_k . t
-        double dot = 0.0;
-        if (active) {
-            for (int p = bx * kCoopThreads + tid; p < N; p += c.gx * kCoopThreads) {
-                const int y = p / g.W, x = p - y * g.W;
-                double acc = 0.0;
+        float2 *unext = reinterpret_cast<float2 *>(lz_buf(st, (k + 1) % 3)) + base;
+        // t' = W u_k and the partial of t' . u_k (workers)
+        if (wt >= 0) {
+            float dh = 0.f, dl = 0.f;
+            if (active) {
 #pragma unroll
-                for (int d = 0; d < 4; ++d) {
-                    if (d >= nd) break;
-                    const int dy = d == 0 ? 0 : 1, dx = d == 0 ? 1 : (d == 1 ? 0 : (d == 2 ? 1 : -1));
-                    const int yo = y + dy, xo = x + dx;
-                    if (yo < g.H && xo >= 0 && xo < g.W)
-                        acc = fma(__ldg(wb + (size_t)p * nd + d), __ldcg(v + (size_t)yo * g.W + xo), acc);
-                    const int yi = y - dy, xi = x - dx;
-                    if (yi >= 0 && xi >= 0 && xi < g.W) {
-                        const size_t q = (size_t)yi * g.W + xi;
-                        acc = fma(__ldg(wb + q * nd + d), __ldcg(v + q), acc);
+                for (int j = 0; j < PPT; ++j) {
+                    const int p = ps + wt + j * kCoopWorkers;
+                    if (p < pe) {
+                        tt[j] = w_times<true>(wb, stage, lo, g, nd, p);
+                        acc_prod(dh, dl, tt[j], uk[j]);
                     }
                 }
-                const double r = acc * inv;
-                __stcg(t + p, r);
-                dot = fma(r, __ldcg(v + p), dot);
             }
+            const df d = warp_sum_df(df_fast_two_sum(dh, dl));
+            if ((tid & 31) == 0) red[warp] = df_to(d);
         }
-        coop_partial(dot * inv, red, pa + bx);
-        if (!coop_barrier(c, nblocks)) return;
-        const double alpha = coop_sum(pa, c.gx, red, sh + 2);
-        // u_{k+1} = t - alpha_k v_k - |u_k| v_{k-1} and its squared norm
-        double n2 = 0.0;
-        if (active) {
-            const double ca = alpha * inv;
-            for (int p = bx * kCoopThreads + tid; p < N; p += c.gx * kCoopThreads) {
-                double r = fma(-ca, __ldcg(v + p), __ldcg(t + p));
-                if (k > 0) r = fma(-cm, __ldcg(um + p), r);
-                __stcg(t + p, r);
-                n2 = fma(r, r, n2);
-            }
-        }
-        coop_partial(n2, red, pb + bx);
-        if (!coop_barrier(c, nblocks)) return;
-        const double s = coop_sum(pb, c.gx, red, sh + 3);
-        if (active) {
-            // every block derives the same values from the same sums
+        __syncthreads();
+        if (warp == 0) {
             if (tid == 0) {
-                const double bk = sqrt(s);
+                double sp = 0.0;
+                for (int i = 1; i < kCoopThreads / 32; ++i) sp += red[i];
+                __stcg(pa + bx, sp);
+                flags[0] = grid_arrive_wait(c, nblocks) ? 1 : 0;
+            }
+            __syncwarp();
+            const double sa = coop_sum(pa, c.gx);
+            if (tid == 0 && active) {
+                alpha = sa * inv_s;
+                const df c2 = df_from(-alpha * inv);
+                fs[4] = c2.h;
+                fs[5] = c2.l;
+            }
+        }
+        __syncthreads();
+        if (flags[0] == 0) return;
+        // u_{k+1} = c1 t' + c2 u_k + c3 u_{k-1} (workers): registers, stage, L2
+        if (wt >= 0) {
+            float nh = 0.f, nl = 0.f;
+            if (active) {
+                const df c1 = {fs[0], fs[1]}, c3 = {fs[2], fs[3]}, c2 = {fs[4], fs[5]};
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) {
+                    const int p = ps + wt + j * kCoopWorkers;
+                    if (p < pe) {
+                        float rh = 0.f, rl = 0.f;
+                        acc_prod(rh, rl, c1, tt[j]);
+                        acc_prod(rh, rl, c2, uk[j]);
+                        if (k > 0) acc_prod(rh, rl, c3, um[j]);
+                        const df r = df_fast_two_sum(rh, rl);
+                        const float2 r2 = make_float2(r.h, r.l);
+                        __stcg(unext + p, r2);
+                        stage[p - lo] = r2;
+                        acc_prod(nh, nl, r, r);
+                        um[j] = uk[j];
+                        uk[j] = r;
+                    }
+                }
+            }
+            const df n2 = warp_sum_df(df_fast_two_sum(nh, nl));
+            if ((tid & 31) == 0) red[warp] = df_to(n2);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            if (tid == 0) {
+                double sp = 0.0;
+                for (int i = 1; i < kCoopThreads / 32; ++i) sp += red[i];
+                __stcg(pb + bx, sp);
+                flags[0] = grid_arrive_wait(c, nblocks) ? 1 : 0;
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        if (flags[0] == 0) return;
+        if (warp == 0) {
+            // |u_{k+1}|^2; alpha_k and beta_k recorded, the next step's scalars
+            const double sb = coop_sum(pb, c.gx);
+            if (tid == 0 && active) {
+                const double bk = sqrt(sb);
                 const double ref = fabs(alpha) + nk;
                 const bool brk = !(bk > 1e-13 * ref) || !(bk > 1e-300);
                 if (bx == 0) {
@@ -517,16 +840,32 @@ lz_chunk_scalar_kernel(LzState st, const double *__restrict__ w, LzGeom g, LzCoo
                     st.nrm[b * ld + k + 1] = bk;
                     if (brk) st.stop[b] = k + 1;
                 }
-                sh[0] = brk ? 0.0 : 1.0 / bk;
-                sh[1] = bk / nk;
-                sh[2] = brk ? 1.0 : 0.0;
-                sh[3] = bk;
+                inv = brk ? 0.0 : 1.0 / bk;
+                inv_s = inv * inv;
+                const df a = df_from(inv), m = df_from(-bk / nk);
+                fs[0] = a.h;
+                fs[1] = a.l;
+                fs[2] = m.h;
+                fs[3] = m.l;
+                flags[1] = brk ? 1 : 0;
+                nk = bk;
             }
-            __syncthreads();
-            if (sh[2] != 0.0) active = false;
-            nk = sh[3];
-            __syncthreads();   // sh is rewritten by the next step's sums
+        } else if (active) {
+            // halo strips of u_{k+1} from L2 (the own part is already staged)
+            const float2 *un = unext;
+            for (int q = lo + wt; q < ps; q += kCoopWorkers) stage[q - lo] = __ldcg(un + q);
+            for (int q = pe + wt; q < hi; q += kCoopWorkers) stage[q - lo] = __ldcg(un + q);
         }
+        __syncthreads();
+        if (flags[1] != 0) active = false;
+    }
+}
+
+// In-place FP64 -> double-float conversion of the start vector (same 8 bytes).
+__global__ void lz_split_kernel(double *v, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const df x = df_from(v[i]);
+        reinterpret_cast<float2 *>(v)[i] = make_float2(x.h, x.l);
     }
 }
 
@@ -551,49 +890,52 @@ constexpr int kRitzThreads = 128;
 
 // Number of eigenvalues below x of the symmetric tridiagonal T with diagonal
 // a[0..n) and squared off-diagonals c2 (c2[i] couples rows i-1 and i;
-// c2[0] = 0).  It is the number of negative pivots of T - x I = L D L^T,
+// c2[0] = 0), scaled so that its entries are at most 1 in magnitude, in
+// double-float.  It is the number of negative pivots of T - x I = L D L^T,
 // read off as the sign changes along the leading principal minors
-// p_i = det(T_{0..i} - x I) = (a_i - x) p_{i-1} - c2_i p_{i-2}: three FP64
-// operations per row and no division (FP64 division is a long sequence on
-// the narrow FP64 pipe).  A zero minor stands for the tiny pivot -tiny (a
-// zero pivot counted negative, as in bisection with a minimum pivot), and
-// the latest pair of minors is rescaled by 2^-+448 whenever both leave
-// [2^-448, 2^448]; signs and exponents are read as integers.
-__device__ int sturm_count_minors(const double *a, const double *c2, int n, double x, double tiny) {
+// p_i = det(T_{0..i} - x I) = (a_i - x) p_{i-1} - c2_i p_{i-2} (no
+// divisions).  A zero minor stands for the tiny pivot -2^-60 (a zero pivot
+// counted negative, as in bisection with a minimum pivot), and the latest
+// pair of minors is rescaled by 2^-+40 whenever both leave [2^-40, 2^40].
+__device__ int sturm_count_df(const float2 *a, const float2 *c2, int n, df x) {
     int cnt = 0;
     bool neg_prev = false;
-    double pm2 = 0.0, pm1 = 1.0;
+    df pm2 = {0.f, 0.f}, pm1 = {1.f, 0.f};
     for (int i = 0; i < n; ++i) {
-        double pi = fma(a[i] - x, pm1, -c2[i] * pm2);
-        if ((__double_as_longlong(pi) << 1) == 0) pi = -tiny * pm1;
-        const int hi = __double2hiint(pi), hm = __double2hiint(pm1);
-        const bool neg = hi < 0;
+        const float2 ai = a[i], ci = c2[i];
+        const df d = df_add(df{ai.x, ai.y}, df{-x.h, -x.l});
+        float ph = 0.f, pl = 0.f;
+        acc_prod(ph, pl, d, pm1);
+        acc_prod(ph, pl, df{-ci.x, -ci.y}, pm2);
+        df pi = df_fast_two_sum(ph, pl);
+        if (pi.h == 0.f) pi = df{-0x1p-60f * pm1.h, -0x1p-60f * pm1.l};
+        const bool neg = pi.h < 0.f;
         cnt += neg != neg_prev;
         neg_prev = neg;
-        const int em = max((hi >> 20) & 0x7FF, (hm >> 20) & 0x7FF);
+        const float m = fmaxf(fabsf(pi.h), fabsf(pm1.h));
         pm2 = pm1;
         pm1 = pi;
-        if (em > 1023 + 448) {
-            pm1 *= 0x1p-448;
-            pm2 *= 0x1p-448;
-        } else if (em < 1023 - 448) {
-            pm1 *= 0x1p+448;
-            pm2 *= 0x1p+448;
+        if (m > 0x1p40f) {
+            pm1 = df{pm1.h * 0x1p-40f, pm1.l * 0x1p-40f};
+            pm2 = df{pm2.h * 0x1p-40f, pm2.l * 0x1p-40f};
+        } else if (m < 0x1p-40f) {
+            pm1 = df{pm1.h * 0x1p40f, pm1.l * 0x1p40f};
+            pm2 = df{pm2.h * 0x1p40f, pm2.l * 0x1p40f};
         }
     }
     return cnt;
 }
 
 // Largest (want_max) or smallest eigenvalue of the symmetric tridiagonal
-// (a, c2) in shared memory, by multisection: each round the kRitzThreads
-// threads of the block test as many interior points of the bracket.  Every
-// thread of the block calls it and gets the same value.  A finite prev
-// inside the Gershgorin interval bounds the wanted extreme from inside (by
-// interlacing, the Ritz value of a shorter Lanczos run): the first round then
-// tests points at growing distances beyond it, which brackets the extreme to
-// about its change since prev and saves most of the rounds.
-__device__ double tridiag_extreme(const double *a, const double *c2, int n, bool want_max, double prev,
-                                  double *red) {
+// (a, c2) in shared memory (FP64, overwritten by a scaled double-float copy),
+// by multisection: each round the kRitzThreads threads of the block test as
+// many interior points of the bracket.  Every thread of the block calls it
+// and gets the same value.  A finite prev inside the Gershgorin interval
+// bounds the wanted extreme from inside (by interlacing, the Ritz value of a
+// shorter Lanczos run): the first round then tests points at growing
+// distances beyond it, which brackets the extreme to about its change since
+// prev and saves most of the rounds.
+__device__ double tridiag_extreme(double *a, double *c2, int n, bool want_max, double prev, double *red) {
     const int tid = threadIdx.x;
     // Gershgorin interval
     double lo = INFINITY, hi = -INFINITY, amax = 0.0;
@@ -618,12 +960,23 @@ __device__ double tridiag_extreme(const double *a, const double *c2, int n, bool
     lo = fmin(fmin(red[0], red[1]), fmin(red[2], red[3]));
     hi = fmax(fmax(red[4], red[5]), fmax(red[6], red[7]));
     amax = fmax(fmax(red[8], red[9]), fmax(red[10], red[11]));
-    const double tiny = fmax(amax, 1e-280) * 0x1p-200;
+    // scale by a power of two sigma >= amax (exact), then to double-float in place
+    int e = 0;
+    frexp(amax, &e);
+    const double sigma = amax > 0.0 && isfinite(amax) ? ldexp(1.0, e) : 1.0;
+    const double is = 1.0 / sigma, is2 = is * is;
+    float2 *af = reinterpret_cast<float2 *>(a), *cf = reinterpret_cast<float2 *>(c2);
+    for (int i = tid; i < n; i += kRitzThreads) {
+        const df x = df_from(a[i] * is), y = df_from(c2[i] * is2);
+        af[i] = make_float2(x.h, x.l);
+        cf[i] = make_float2(y.h, y.l);
+    }
+    __syncthreads();
     if (isfinite(prev) && prev > lo && prev < hi) {
         const double delta = fmax(fabs(prev), 1e-300) * 1e-14;
         const double sc = exp2(0.5 * tid);
         const double x = want_max ? prev + delta * sc : prev - delta * sc;
-        const int cnt = sturm_count_minors(a, c2, n, x, tiny);
+        const int cnt = sturm_count_df(af, cf, n, df_from(x * is));
         // the extreme lies beyond x: max <=> fewer than n below x; min <=> at least one below x
         const int nb = __syncthreads_count(want_max ? (cnt < n) : (cnt >= 1));
         const double inner = nb == 0 ? prev : prev + (want_max ? 1.0 : -1.0) * delta * exp2(0.5 * (nb - 1));
@@ -638,10 +991,10 @@ __device__ double tridiag_extreme(const double *a, const double *c2, int n, bool
         }
     }
     for (int round = 0; round < 64; ++round) {
-        if (!(hi - lo > 1e-14 * fmax(fabs(lo), fabs(hi)) + 1e-300)) break;
+        if (!(hi - lo > 1e-13 * fmax(fabs(lo), fabs(hi)) + 1e-300)) break;
         const double step = (hi - lo) / (double)(kRitzThreads + 1);
         const double x = lo + step * (double)(tid + 1);
-        const int cnt = sturm_count_minors(a, c2, n, x, tiny);
+        const int cnt = sturm_count_df(af, cf, n, df_from(x * is));
         // "below the extreme" holds for a prefix of the points
         const int nb = __syncthreads_count(want_max ? (cnt < n) : (cnt < 1));
         const double nlo = nb > 0 ? lo + step * nb : lo;
@@ -828,6 +1181,11 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
     bool coop = false;
     LzCoop C{};
     int habort = 0;
+    unsigned *wmax = nullptr, hwmax = 0;
+    const void *coop_fn = nullptr;
+    int coop_chunk = 0;          // pixels per block (tiled form)
+    size_t coop_smem = 0;
+    const size_t nw = (size_t)B * job.H * job.W * (job.conn == 8 ? 4 : 2);
     dim3 gridp(g.nblk, B);
     const int nblk_dense = (job.W + kLzThreads / 32 - 1) / (kLzThreads / 32);
     S.ld = ld;
@@ -848,10 +1206,12 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
     LZ_CHECK(cudaMallocAsync((void **)&nu, 2 * sizeof(double), st));
     LZ_CHECK(cudaMallocAsync((void **)&mu_dev, (size_t)job.L * job.L * sizeof(float), st));
     if (!job.Kdense && g.Lv == 1) {
-        const size_t nw = (size_t)B * job.H * job.W * (job.conn == 8 ? 4 : 2);
-        LZ_CHECK(cudaMallocAsync((void **)&wd, nw * sizeof(double), st));
-        lz_weights_f64_kernel<<<(int)std::min<size_t>((nw + 255) / 256, 4096), 256, 0, st>>>(job.w, wd, nw);
+        // the weights' magnitude decides whether the double-float form fits
+        LZ_CHECK(cudaMallocAsync((void **)&wmax, sizeof(unsigned), st));
+        LZ_CHECK(cudaMemsetAsync(wmax, 0, sizeof(unsigned), st));
+        lz_absmax_kernel<<<(int)std::min<size_t>((nw + 255) / 256, 1024), 256, 0, st>>>(job.w, nw, wmax);
         LZ_CHECK(cudaGetLastError());
+        LZ_CHECK(cudaMemcpyAsync(&hwmax, wmax, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         nl += 1;
     }
     LZ_CHECK(cudaMemsetAsync(S.alpha, 0, (size_t)B * ld * sizeof(double), st));
@@ -863,26 +1223,61 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
                              cudaMemcpyHostToDevice, st));
     LZ_CHECK(cudaStreamSynchronize(st));  // mu_host is pageable and owned by the caller
 
+    if (!job.Kdense && g.Lv == 1) {
+        // double-float vectors need |w| well inside the FP32 range (products
+        // and squared norms stay finite, low parts stay normal); all blocks
+        // of the cooperative launch must be resident at once: at most one per
+        // SM and instance
+        float wm = 0.f;
+        std::memcpy(&wm, &hwmax, sizeof(float));
+        int dev = 0, sms = 0, coop_ok = 0, occ = 0;
+        LZ_CHECK(cudaGetDevice(&dev));
+        LZ_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        LZ_CHECK(cudaDeviceGetAttribute(&coop_ok, cudaDevAttrCooperativeLaunch, dev));
+        const int N = job.H * job.W;
+        const int need = (N + kCoopThreads - 1) / kCoopThreads;
+        // two SMs stay free for the label-space eigen-solve on the side stream
+        const int avail = job.mu_sym && sms > 4 ? sms - 2 : sms;
+        C.gx = std::max(1, std::min(need, B <= avail ? avail / B : 1));
+        // contiguous pixel ranges staged in shared memory with their halo
+        // rows when both fit (at most 8 pixels per worker thread); else the
+        // strided form with every vector in L2
+        coop_chunk = (N + C.gx - 1) / C.gx;
+        const long long ppt = (coop_chunk + kCoopWorkers - 1) / kCoopWorkers;
+        coop_smem = (size_t)(coop_chunk + 2 * (long long)job.W + 2) * sizeof(float2);
+        if (ppt > 8 || coop_smem > (size_t)200 * 1024) {
+            coop_fn = (const void *)lz_chunk_strided_kernel;
+            coop_smem = 0;
+        } else {
+            coop_fn = ppt <= 1   ? (const void *)lz_chunk_tile_kernel<1>
+                      : ppt <= 2 ? (const void *)lz_chunk_tile_kernel<2>
+                      : ppt <= 4 ? (const void *)lz_chunk_tile_kernel<4>
+                                 : (const void *)lz_chunk_tile_kernel<8>;
+            LZ_CHECK(cudaFuncSetAttribute(coop_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coop_smem));
+        }
+        LZ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, coop_fn, kCoopThreads, coop_smem));
+        if (coop_ok && occ >= 1 && B <= sms * occ && wm >= 0x1p-40f && wm <= 0x1p40f) {
+            coop = true;
+        } else {
+            LZ_CHECK(cudaMallocAsync((void **)&wd, nw * sizeof(double), st));
+            lz_weights_f64_kernel<<<(int)std::min<size_t>((nw + 255) / 256, 4096), 256, 0, st>>>(job.w, wd, nw);
+            LZ_CHECK(cudaGetLastError());
+            nl += 1;
+        }
+    }
+
     lz_init_kernel<<<gridp, kLzThreads, 0, st>>>(S.R0, g, 0x5eed5eedull);
     LZ_CHECK(cudaGetLastError());
     lz_norm0_kernel<<<gridp, kLzThreads, 0, st>>>(S, g);
     LZ_CHECK(cudaGetLastError());
     nl += 2;
+    if (coop) {
+        lz_split_kernel<<<(int)std::min<size_t>((vec + 255) / 256, 4096), 256, 0, st>>>(S.R0, vec);
+        LZ_CHECK(cudaGetLastError());
+        nl += 1;
+    }
 
     LZ_CHECK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    if (!job.Kdense && g.Lv == 1) {
-        // all blocks must be resident at once: at most one per SM and instance
-        int dev = 0, sms = 0, coop_ok = 0, occ = 0;
-        LZ_CHECK(cudaGetDevice(&dev));
-        LZ_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        LZ_CHECK(cudaDeviceGetAttribute(&coop_ok, cudaDevAttrCooperativeLaunch, dev));
-        LZ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lz_chunk_scalar_kernel, kCoopThreads, 0));
-        const int need = (job.H * job.W + kCoopThreads - 1) / kCoopThreads;
-        if (coop_ok && occ >= 1 && B <= sms * occ) {
-            C.gx = std::max(1, std::min(need, B <= sms ? sms / B : 1));
-            coop = true;
-        }
-    }
     if (coop) {
         LZ_CHECK(cudaMallocAsync((void **)&C.bar, 2 * sizeof(unsigned), st));
         LZ_CHECK(cudaMallocAsync((void **)&C.abort, sizeof(int), st));
@@ -920,9 +1315,10 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
     while (k < kmax) {
         if (coop) {
             int k0 = k, k1 = std::min(k + kChunk, kmax);
-            void *args[] = {&S, &wd, &g, &C, &k0, &k1};
-            LZ_CHECK(cudaLaunchCooperativeKernel((const void *)lz_chunk_scalar_kernel, dim3(C.gx, B),
-                                                 dim3(kCoopThreads), args, 0, st));
+            const float *wf = job.w;
+            int chunk = coop_chunk;
+            void *args[] = {&S, &wf, &g, &C, &k0, &k1, &chunk};
+            LZ_CHECK(cudaLaunchCooperativeKernel(coop_fn, dim3(C.gx, B), dim3(kCoopThreads), args, coop_smem, st));
             nl += 1;
         } else {
             LZ_CHECK(cudaGraphLaunch(exec, st));
@@ -973,6 +1369,7 @@ done:
     if (S.counter) cudaFreeAsync(S.counter, st);
     if (S.stop) cudaFreeAsync(S.stop, st);
     if (S.kdev) cudaFreeAsync(S.kdev, st);
+    if (wmax) cudaFreeAsync(wmax, st);
     if (C.bar) cudaFreeAsync(C.bar, st);
     if (C.abort) cudaFreeAsync(C.abort, st);
     if (C.part) cudaFreeAsync(C.part, st);
