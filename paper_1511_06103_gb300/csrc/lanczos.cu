@@ -690,28 +690,34 @@ lz_chunk_strided_kernel(LzState st, const float *__restrict__ w, LzGeom g, LzCoo
     }
 }
 
-// Steps k0 .. k1-1 of the scalar form with the vectors staged in shared
-// memory.  Block bx of an instance owns the contiguous pixels [ps, pe);
-// every neighbour of them lies in [ps - W - 1, pe + W + 1), which the block
-// keeps in shared memory: its own part is written there by the update, the
-// two halo strips are loaded from L2 once per step.  Warp 0 runs the control
-// path (grid barriers, fixed-order sums, the FP64 scalars, which it forms
-// while the other warps load the halo); warps 1.. own at most PPT pixels per
-// thread and keep u_k, u_{k-1} and t of them in registers.  The product is
-// taken of the unnormalised u_k (t' = W u_k, alpha_k = t'.u_k / |u_k|^2), so
-// that the new norm is needed only by the update.
+// Steps k0 .. k1-1 of the scalar form with one grid barrier per step.
+// Block bx of an instance owns the contiguous pixels [ps, pe); with
+// R1 = W + 1 every neighbour of a pixel p lies in [p - R1, p + R1].  The
+// block keeps u_k and u_{k-1} in shared memory over [ps - 2 R1, pe + 2 R1)
+// and advances them redundantly on the ring [ps - R1, pe + R1) too, with the
+// same arithmetic as the owning blocks (so the copies agree bit for bit):
+// the next product then needs no other block's new values, and the one
+// barrier of a step serves both the reductions and the visibility of the
+// vectors written one step earlier, from which the outer ring is reloaded.
+// With the unnormalised u_k, t' = W u_k, one reduction gives
+// alpha_k = t'.u_k / |u_k|^2 and |u_k| = beta_{k-1} together, and
+//   u_{k+1} = (t' - alpha_k u_k) / |u_k| - (|u_k| / |u_{k-1}|) u_{k-1}.
+// nrm[k] = |u_k| is recorded at step k; a collapsed |u_k| stops the
+// instance with k rows, as in the other forms.  Warp 0 runs the control
+// path (barrier, fixed-order sums, FP64 scalars); warps 1.. own at most PPT
+// pixels per thread.
 constexpr int kCoopWorkers = kCoopThreads - 32;
 
 template <int PPT>
 __global__ void __launch_bounds__(kCoopThreads, 1)
-lz_chunk_tile_kernel(LzState st, const float *__restrict__ w, LzGeom g, LzCoop c, int k0, int k1, int chunk) {
+lz_chunk_halo_kernel(LzState st, const float *__restrict__ w, LzGeom g, LzCoop c, int k0, int k1, int chunk) {
     extern __shared__ float2 stage[];
-    __shared__ double red[kCoopThreads / 32];
-    __shared__ float fs[8];   // c1 = 1/|u_k| (h, l), c3 = -|u_k|/|u_{k-1}| (h, l), c2 = -alpha_k/|u_k| (h, l)
+    __shared__ double red[2 * (kCoopThreads / 32)];
+    __shared__ float fs[6];   // c1 = 1/|u_k|, c2 = -alpha_k/|u_k|, c3 = -|u_k|/|u_{k-1}| (h, l)
     __shared__ int flags[2];  // [0] grid barrier outcome, [1] the instance stopped
     const int b = blockIdx.y, bx = blockIdx.x, tid = threadIdx.x, warp = tid >> 5;
     const unsigned nblocks = gridDim.x * gridDim.y;
-    const int N = g.H * g.W, W = g.W;
+    const int N = g.H * g.W, R1 = g.W + 1;
     const int nd = g.conn == 8 ? 4 : 2;
     const size_t base = (size_t)b * N;
     const float *wb = w + base * nd;
@@ -719,145 +725,146 @@ lz_chunk_tile_kernel(LzState st, const float *__restrict__ w, LzGeom g, LzCoop c
     double *pb = c.part + ((size_t)g.B + b) * c.gx;
     const size_t ld = (size_t)st.ld;
     const int ps = min(N, bx * chunk), pe = min(N, ps + chunk);
-    const int lo = max(0, ps - W - 1), hi = min(N, pe + W + 1);
+    const int lo1 = max(0, ps - R1), hi1 = min(N, pe + R1);
+    const int lo2 = max(0, ps - 2 * R1), hi2 = min(N, pe + 2 * R1);
+    const int nl1 = ps - lo1, nring = nl1 + (hi1 - pe);
     const int wt = tid - 32;
+    float2 *su = stage, *sm = stage + (chunk + 4 * R1);   // u_k, u_{k-1} over [lo2, hi2)
     bool active = st.stop[b] == 0;
-    // thread 0: FP64 state (norms of u_k, u_{k-1}; 1/|u_k|^2 and 1/|u_k|)
-    double nk = 0.0, inv = 0.0, inv_s = 0.0, alpha = 0.0;
+    // thread 0: |u_{k-1}|, its reciprocal and alpha_{k-1}
+    double n_prev = 0.0, a_prev = 0.0, inv_prev = 0.0;
     if (tid == 0) {
-        nk = st.nrm[b * ld + k0];
-        inv = active ? 1.0 / nk : 0.0;
-        inv_s = inv * inv;
-        const df a = df_from(inv), m = df_from(active && k0 > 0 ? -nk / st.nrm[b * ld + k0 - 1] : 0.0);
-        fs[0] = a.h;
-        fs[1] = a.l;
-        fs[2] = m.h;
-        fs[3] = m.l;
+        n_prev = k0 > 0 ? st.nrm[b * ld + k0 - 1] : 0.0;
+        a_prev = k0 > 0 ? st.alpha[b * ld + k0 - 1] : 0.0;
+        inv_prev = k0 > 0 ? 1.0 / n_prev : 0.0;
         flags[1] = 0;
     }
-    df uk[PPT], um[PPT], tt[PPT];
     {
         const float2 *v0 = reinterpret_cast<const float2 *>(lz_buf(st, k0 % 3)) + base;
         const float2 *v1 = reinterpret_cast<const float2 *>(lz_buf(st, (k0 + 2) % 3)) + base;
-        for (int q = lo + tid; q < hi; q += kCoopThreads) stage[q - lo] = __ldcg(v0 + q);
-        if (wt >= 0) {
-#pragma unroll
-            for (int j = 0; j < PPT; ++j) {
-                const int p = ps + wt + j * kCoopWorkers;
-                const float2 a = p < pe ? __ldcg(v0 + p) : make_float2(0.f, 0.f);
-                const float2 m = p < pe ? __ldcg(v1 + p) : make_float2(0.f, 0.f);
-                uk[j] = df{a.x, a.y};
-                um[j] = df{m.x, m.y};
-                tt[j] = df{0.f, 0.f};
-            }
-        }
+        for (int q = lo2 + tid; q < hi2; q += kCoopThreads) su[q - lo2] = __ldcg(v0 + q);
+        for (int q = lo1 + tid; q < hi1; q += kCoopThreads) sm[q - lo2] = __ldcg(v1 + q);
     }
+    df tt[PPT];
     __syncthreads();
     for (int k = k0; k < k1; ++k) {
+        const float2 *ucur = reinterpret_cast<const float2 *>(lz_buf(st, k % 3)) + base;
         float2 *unext = reinterpret_cast<float2 *>(lz_buf(st, (k + 1) % 3)) + base;
-        // t' = W u_k and the partial of t' . u_k (workers)
+        // t' = W u_k on the own pixels, partials of t'.u_k and |u_k|^2 (workers)
         if (wt >= 0) {
-            float dh = 0.f, dl = 0.f;
+            float dh = 0.f, dl = 0.f, nh = 0.f, nl = 0.f;
             if (active) {
 #pragma unroll
                 for (int j = 0; j < PPT; ++j) {
                     const int p = ps + wt + j * kCoopWorkers;
                     if (p < pe) {
-                        tt[j] = w_times<true>(wb, stage, lo, g, nd, p);
-                        acc_prod(dh, dl, tt[j], uk[j]);
+                        tt[j] = w_times<true>(wb, su, lo2, g, nd, p);
+                        const float2 u2 = su[p - lo2];
+                        const df u = {u2.x, u2.y};
+                        acc_prod(dh, dl, tt[j], u);
+                        acc_prod(nh, nl, u, u);
                     }
                 }
             }
             const df d = warp_sum_df(df_fast_two_sum(dh, dl));
-            if ((tid & 31) == 0) red[warp] = df_to(d);
+            const df n = warp_sum_df(df_fast_two_sum(nh, nl));
+            if ((tid & 31) == 0) {
+                red[warp] = df_to(d);
+                red[16 + warp] = df_to(n);
+            }
         }
         __syncthreads();
         if (warp == 0) {
-            if (tid == 0) {
-                double sp = 0.0;
-                for (int i = 1; i < kCoopThreads / 32; ++i) sp += red[i];
-                __stcg(pa + bx, sp);
+            // block partials: the warps' values by a fixed-shape tree
+            const int lane = tid;
+            double sd = lane >= 1 && lane < kCoopThreads / 32 ? red[lane] : 0.0;
+            double sn = lane >= 1 && lane < kCoopThreads / 32 ? red[16 + lane] : 0.0;
+            sd = warp_sum(sd);
+            sn = warp_sum(sn);
+            if (lane == 0) {
+                __stcg(pa + bx, sd);
+                __stcg(pb + bx, sn);
                 flags[0] = grid_arrive_wait(c, nblocks) ? 1 : 0;
-            }
-            __syncwarp();
-            const double sa = coop_sum(pa, c.gx);
-            if (tid == 0 && active) {
-                alpha = sa * inv_s;
-                const df c2 = df_from(-alpha * inv);
-                fs[4] = c2.h;
-                fs[5] = c2.l;
             }
         }
         __syncthreads();
         if (flags[0] == 0) return;
-        // u_{k+1} = c1 t' + c2 u_k + c3 u_{k-1} (workers): registers, stage, L2
-        if (wt >= 0) {
-            float nh = 0.f, nl = 0.f;
-            if (active) {
-                const df c1 = {fs[0], fs[1]}, c3 = {fs[2], fs[3]}, c2 = {fs[4], fs[5]};
-#pragma unroll
-                for (int j = 0; j < PPT; ++j) {
-                    const int p = ps + wt + j * kCoopWorkers;
-                    if (p < pe) {
-                        float rh = 0.f, rl = 0.f;
-                        acc_prod(rh, rl, c1, tt[j]);
-                        acc_prod(rh, rl, c2, uk[j]);
-                        if (k > 0) acc_prod(rh, rl, c3, um[j]);
-                        const df r = df_fast_two_sum(rh, rl);
-                        const float2 r2 = make_float2(r.h, r.l);
-                        __stcg(unext + p, r2);
-                        stage[p - lo] = r2;
-                        acc_prod(nh, nl, r, r);
-                        um[j] = uk[j];
-                        uk[j] = r;
-                    }
-                }
-            }
-            const df n2 = warp_sum_df(df_fast_two_sum(nh, nl));
-            if ((tid & 31) == 0) red[warp] = df_to(n2);
-        }
-        __syncthreads();
         if (warp == 0) {
-            if (tid == 0) {
-                double sp = 0.0;
-                for (int i = 1; i < kCoopThreads / 32; ++i) sp += red[i];
-                __stcg(pb + bx, sp);
-                flags[0] = grid_arrive_wait(c, nblocks) ? 1 : 0;
+            // both sums of the instance in one pass over the partials
+            double sd = 0.0, sn = 0.0;
+            for (int i = tid; i < c.gx; i += 32) {
+                sd += __ldcg(pa + i);
+                sn += __ldcg(pb + i);
             }
-            __syncwarp();
-        }
-        __syncthreads();
-        if (flags[0] == 0) return;
-        if (warp == 0) {
-            // |u_{k+1}|^2; alpha_k and beta_k recorded, the next step's scalars
-            const double sb = coop_sum(pb, c.gx);
+            sd = warp_sum(sd);
+            sn = warp_sum(sn);
             if (tid == 0 && active) {
-                const double bk = sqrt(sb);
-                const double ref = fabs(alpha) + nk;
-                const bool brk = !(bk > 1e-13 * ref) || !(bk > 1e-300);
+                // one reciprocal square root; the rest are products
+                const double inv = rsqrt(sn);
+                const double nk = sn * inv;
+                const bool brk = !(nk > 1e-300) || (k > 0 && !(nk > 1e-13 * (fabs(a_prev) + n_prev)));
+                const double alpha = sd * inv * inv;
                 if (bx == 0) {
-                    st.alpha[b * ld + k] = alpha;
-                    st.nrm[b * ld + k + 1] = bk;
-                    if (brk) st.stop[b] = k + 1;
+                    if (k > 0) st.nrm[b * ld + k] = nk;
+                    if (brk)
+                        st.stop[b] = k;
+                    else
+                        st.alpha[b * ld + k] = alpha;
                 }
-                inv = brk ? 0.0 : 1.0 / bk;
-                inv_s = inv * inv;
-                const df a = df_from(inv), m = df_from(-bk / nk);
-                fs[0] = a.h;
-                fs[1] = a.l;
-                fs[2] = m.h;
-                fs[3] = m.l;
+                const df c1 = df_from(inv), c2 = df_from(-alpha * inv), c3 = df_from(k > 0 ? -nk * inv_prev : 0.0);
+                fs[0] = c1.h;
+                fs[1] = c1.l;
+                fs[2] = c2.h;
+                fs[3] = c2.l;
+                fs[4] = c3.h;
+                fs[5] = c3.l;
                 flags[1] = brk ? 1 : 0;
-                nk = bk;
+                a_prev = alpha;
+                n_prev = nk;
+                inv_prev = inv;
             }
         } else if (active) {
-            // halo strips of u_{k+1} from L2 (the own part is already staged)
-            const float2 *un = unext;
-            for (int q = lo + wt; q < ps; q += kCoopWorkers) stage[q - lo] = __ldcg(un + q);
-            for (int q = pe + wt; q < hi; q += kCoopWorkers) stage[q - lo] = __ldcg(un + q);
+            // outer ring of u_k from L2: written by its owners at step k - 1,
+            // visible since this step's barrier
+            for (int q = lo2 + wt; q < lo1; q += kCoopWorkers) su[q - lo2] = __ldcg(ucur + q);
+            for (int q = hi1 + wt; q < hi2; q += kCoopWorkers) su[q - lo2] = __ldcg(ucur + q);
         }
         __syncthreads();
         if (flags[1] != 0) active = false;
+        // u_{k+1} on the own pixels (also to L2) and on the inner ring, into sm
+        if (wt >= 0 && active) {
+            const df c1 = {fs[0], fs[1]}, c2 = {fs[2], fs[3]}, c3 = {fs[4], fs[5]};
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                const int p = ps + wt + j * kCoopWorkers;
+                if (p < pe) {
+                    const float2 u = su[p - lo2], m = sm[p - lo2];
+                    float rh = 0.f, rl = 0.f;
+                    acc_prod(rh, rl, c1, tt[j]);
+                    acc_prod(rh, rl, c2, df{u.x, u.y});
+                    acc_prod(rh, rl, c3, df{m.x, m.y});
+                    const df r = df_fast_two_sum(rh, rl);
+                    const float2 r2 = make_float2(r.h, r.l);
+                    sm[p - lo2] = r2;
+                    __stcg(unext + p, r2);
+                }
+            }
+            for (int i = wt; i < nring; i += kCoopWorkers) {
+                const int q = i < nl1 ? lo1 + i : pe + (i - nl1);
+                const df t = w_times<true>(wb, su, lo2, g, nd, q);
+                const float2 u = su[q - lo2], m = sm[q - lo2];
+                float rh = 0.f, rl = 0.f;
+                acc_prod(rh, rl, c1, t);
+                acc_prod(rh, rl, c2, df{u.x, u.y});
+                acc_prod(rh, rl, c3, df{m.x, m.y});
+                const df r = df_fast_two_sum(rh, rl);
+                sm[q - lo2] = make_float2(r.h, r.l);
+            }
+        }
+        __syncthreads();
+        float2 *tmp = su;
+        su = sm;
+        sm = tmp;
     }
 }
 
@@ -1244,15 +1251,15 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
         // strided form with every vector in L2
         coop_chunk = (N + C.gx - 1) / C.gx;
         const long long ppt = (coop_chunk + kCoopWorkers - 1) / kCoopWorkers;
-        coop_smem = (size_t)(coop_chunk + 2 * (long long)job.W + 2) * sizeof(float2);
+        coop_smem = (size_t)2 * (coop_chunk + 4 * ((long long)job.W + 1)) * sizeof(float2);
         if (ppt > 8 || coop_smem > (size_t)200 * 1024) {
             coop_fn = (const void *)lz_chunk_strided_kernel;
             coop_smem = 0;
         } else {
-            coop_fn = ppt <= 1   ? (const void *)lz_chunk_tile_kernel<1>
-                      : ppt <= 2 ? (const void *)lz_chunk_tile_kernel<2>
-                      : ppt <= 4 ? (const void *)lz_chunk_tile_kernel<4>
-                                 : (const void *)lz_chunk_tile_kernel<8>;
+            coop_fn = ppt <= 1   ? (const void *)lz_chunk_halo_kernel<1>
+                      : ppt <= 2 ? (const void *)lz_chunk_halo_kernel<2>
+                      : ppt <= 4 ? (const void *)lz_chunk_halo_kernel<4>
+                                 : (const void *)lz_chunk_halo_kernel<8>;
             LZ_CHECK(cudaFuncSetAttribute(coop_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coop_smem));
         }
         LZ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, coop_fn, kCoopThreads, coop_smem));
