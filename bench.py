@@ -72,6 +72,8 @@ def parse():
     p.add_argument("--no-unrolled", action="store_true",
                    help="skip the unrolled-inference (forward + reverse) measurement")
     p.add_argument("--unrolled-only", action="store_true")
+    p.add_argument("--setup-only", action="store_true",
+                   help="time only the step-size constant of the benchmark instance (profiling)")
     p.add_argument("--batch", type=int, default=1,
                    help="instances per GPU (1 = the benchmark workload; >1 for profiling captures)")
     return p.parse_args()
@@ -717,6 +719,34 @@ def run_serving(n_req, max_iters=1000, rel_tol=1e-6):
             "mean_iters": float(np.mean(list(iters_run.values())))}
 
 
+def run_setup(args, dev, stream):
+    """The step-size constant of the benchmark instance alone (step a7), as a
+    user pays it for every new pairwise term; warmup + steps repetitions."""
+    import torch
+
+    from paper_1511_06103_gb300 import binding, synth
+    d = synth.segmentation_grid(H=H, W=W, L=L, conn=CONN, seed=SEED)
+    crf = binding.CRF(binding.CRF_GRID8, L, H, W, stream=stream.cuda_stream)
+    crf.set_unary(torch.from_numpy(d["U"][None]).to(dev))
+    mu_d = torch.from_numpy(d["mu"]).to(dev)
+    w_d = torch.from_numpy(d["w"][None]).to(dev)
+    times, launches = [], []
+    lam = None
+    for i in range(args.warmup + args.steps):
+        crf.set_pairwise(mu_d, w_d)
+        torch.cuda.synchronize()
+        n0 = crf.launch_count()
+        t0 = time.perf_counter()
+        lam, _ = crf.lipschitz()     # returns host values: synchronises
+        if i >= args.warmup:
+            times.append(1000 * (time.perf_counter() - t0))
+            launches.append(crf.launch_count() - n0)
+    crf.close()
+    return {"workload": "step-size constant (Lanczos on the 512x512 8-connected weights, label-space "
+                        "eigen-solve of mu, L=21)", "ms_median": statistics.median(times),
+            "ms_min": min(times), "launches": launches[-1], "Lambda": float(lam[0]), "reps": len(times)}
+
+
 def run_ours(args, world, rank, local):
     import torch
     import torch.distributed as dist
@@ -748,6 +778,9 @@ def run_ours(args, world, rank, local):
         peak, _ = measured_peaks()
         print(json.dumps({"unrolled": {"f32": run_unrolled(args, dev, peak),
                                        "bf16_tc": run_unrolled(args, dev, peak, 1)}}), flush=True)
+        return
+    if args.setup_only:
+        print(json.dumps({"setup": run_setup(args, dev, stream)}), flush=True)
         return
     if args.dense_only:
         peak, _ = measured_peaks()
@@ -843,21 +876,38 @@ def run_ours(args, world, rank, local):
             e2e_step()
             times.append(time.perf_counter() - t0)
         e2e_s = max_over_ranks(float(np.mean(times)), world, dev)
+
+        # one more pass, synchronised between its phases (outside the timed loop)
+        def phase_ms(f):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            f()
+            torch.cuda.synchronize()
+            return 1000 * (time.perf_counter() - t)
+
+        flush.zero_()
+        phases = {"upload_unary": phase_ms(lambda: crf.set_unary(U_h)),
+                  "upload_pairwise": phase_ms(lambda: crf.set_pairwise(mu_h, w_h)),
+                  "step_size_setup": phase_ms(lambda: crf.lipschitz()),
+                  "iterations": phase_ms(lambda: crf.iterate(ITERS, eta=0.0, final_free_energy=True)),
+                  "download": phase_ms(lambda: (crf.marginals(q_h), crf.free_energy()))}
         e2e = {"value": job_throughput(units_per_step, e2e_s, world), "unit": UNIT,
                "h2d_bytes_per_step": int(U_h.numel() * 4 + mu_h.numel() * 4 + w_h.numel() * 4),
                "d2h_bytes_per_step": int(q_h.numel() * 4 + 8),
                "ms_per_step": 1000 * e2e_s,
-               "includes": "H2D of U and w, step-size constant (Lanczos), 100 iterations, D2H of q and F"}
+               "includes": "H2D of U and w, step-size constant (Lanczos), 100 iterations, D2H of q and F",
+               "phases_ms": phases}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        side, iters = 160, ITERS
+        # the whole instance of the timed workload (one solve, about 10 s of CPU work)
+        side, iters = H, ITERS
         rate, dt, _ = oracle_solve_rate(side, iters)
         cpu = {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": f"{side}x{side} crop of the same recipe (L=21, 8-connected), {iters} iterations, "
-                         f"F every iteration; {dt:.1f} s of CPU work"}
+               "sample": f"one full {side}x{side} instance of the same recipe (L=21, 8-connected, seed {SEED}), "
+                         f"{iters} iterations, F every iteration; {dt:.1f} s of CPU work"}
 
     clocks = clk.summary()
     dense = None
