@@ -690,17 +690,39 @@ lz_chunk_strided_kernel(LzState st, const float *__restrict__ w, LzGeom g, LzCoo
     }
 }
 
+// (W u) at stage index i with weights and vector staged in shared memory:
+// ws holds the pixel-major weights of the edges leaving each pixel (right,
+// down, down-right, down-left; zero for edges that leave the image) and u the
+// double-float vector, both zero outside the instance.  On the linear pixel
+// index the neighbour in direction d is i + off_d and the edge entering from
+// the opposite side comes from i - off_d; a pair that is not a grid edge
+// (a row wrap) always carries a zero weight, so no bounds tests are needed.
+template <int ND>
+__device__ __forceinline__ df w_times_staged(const float *__restrict__ ws, const float2 *__restrict__ u, int i,
+                                             int W) {
+    float ah = 0.f, al = 0.f;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        const int off = d == 0 ? 1 : (d == 1 ? W : (d == 2 ? W + 1 : W - 1));
+        const float2 vo = u[i + off], vi = u[i - off];
+        acc_prod_f(ah, al, ws[i * 4 + d], df{vo.x, vo.y});
+        acc_prod_f(ah, al, ws[(i - off) * 4 + d], df{vi.x, vi.y});
+    }
+    return df_fast_two_sum(ah, al);
+}
+
 // Steps k0 .. k1-1 of the scalar form with one grid barrier per step.
 // Block bx of an instance owns the contiguous pixels [ps, pe); with
 // R1 = W + 1 every neighbour of a pixel p lies in [p - R1, p + R1].  The
-// block keeps u_k and u_{k-1} in shared memory over [ps - 2 R1, pe + 2 R1)
-// and advances them redundantly on the ring [ps - R1, pe + R1) too, with the
-// same arithmetic as the owning blocks (so the copies agree bit for bit):
-// the next product then needs no other block's new values, and the one
-// barrier of a step serves both the reductions and the visibility of the
-// vectors written one step earlier, from which the outer ring is reloaded.
-// With the unnormalised u_k, t' = W u_k, one reduction gives
-// alpha_k = t'.u_k / |u_k|^2 and |u_k| = beta_{k-1} together, and
+// block keeps u_k, u_{k-1} and the edge weights in shared memory over
+// [ps - 2 R1, pe + 2 R1) and advances u redundantly on the ring
+// [ps - R1, pe + R1) too, with the same arithmetic as the owning blocks (so
+// the copies agree bit for bit): the next product then needs no other
+// block's new values, and the one barrier of a step serves both the
+// reductions and the visibility of the vectors written one step earlier,
+// from which the outer ring is reloaded.  With the unnormalised u_k,
+// t' = W u_k, one reduction gives alpha_k = t'.u_k / |u_k|^2 and
+// |u_k| = beta_{k-1} together, and
 //   u_{k+1} = (t' - alpha_k u_k) / |u_k| - (|u_k| / |u_{k-1}|) u_{k-1}.
 // nrm[k] = |u_k| is recorded at step k; a collapsed |u_k| stops the
 // instance with k rows, as in the other forms.  Warp 0 runs the control
@@ -708,28 +730,30 @@ lz_chunk_strided_kernel(LzState st, const float *__restrict__ w, LzGeom g, LzCoo
 // pixels per thread.
 constexpr int kCoopWorkers = kCoopThreads - 32;
 
-template <int PPT>
+template <int PPT, int ND>
 __global__ void __launch_bounds__(kCoopThreads, 1)
 lz_chunk_halo_kernel(LzState st, const float *__restrict__ w, LzGeom g, LzCoop c, int k0, int k1, int chunk) {
-    extern __shared__ float2 stage[];
+    extern __shared__ float4 smem4[];
     __shared__ double red[2 * (kCoopThreads / 32)];
     __shared__ float fs[6];   // c1 = 1/|u_k|, c2 = -alpha_k/|u_k|, c3 = -|u_k|/|u_{k-1}| (h, l)
     __shared__ int flags[2];  // [0] grid barrier outcome, [1] the instance stopped
     const int b = blockIdx.y, bx = blockIdx.x, tid = threadIdx.x, warp = tid >> 5;
     const unsigned nblocks = gridDim.x * gridDim.y;
-    const int N = g.H * g.W, R1 = g.W + 1;
-    const int nd = g.conn == 8 ? 4 : 2;
+    const int N = g.H * g.W, W = g.W, R1 = g.W + 1;
     const size_t base = (size_t)b * N;
-    const float *wb = w + base * nd;
+    const float *wb = w + base * ND;
     double *pa = c.part + (size_t)b * c.gx;
     double *pb = c.part + ((size_t)g.B + b) * c.gx;
     const size_t ld = (size_t)st.ld;
     const int ps = min(N, bx * chunk), pe = min(N, ps + chunk);
+    const int o2 = ps - 2 * R1;                 // pixel of stage index 0 (may be negative)
+    const int S = chunk + 4 * R1;               // stage entries
     const int lo1 = max(0, ps - R1), hi1 = min(N, pe + R1);
     const int lo2 = max(0, ps - 2 * R1), hi2 = min(N, pe + 2 * R1);
     const int nl1 = ps - lo1, nring = nl1 + (hi1 - pe);
     const int wt = tid - 32;
-    float2 *su = stage, *sm = stage + (chunk + 4 * R1);   // u_k, u_{k-1} over [lo2, hi2)
+    float *ws = reinterpret_cast<float *>(smem4);                               // [S][4] weights
+    float2 *su = reinterpret_cast<float2 *>(smem4 + S), *sm = su + S;          // u_k, u_{k-1}
     bool active = st.stop[b] == 0;
     // thread 0: |u_{k-1}|, its reciprocal and alpha_{k-1}
     double n_prev = 0.0, a_prev = 0.0, inv_prev = 0.0;
@@ -742,8 +766,15 @@ lz_chunk_halo_kernel(LzState st, const float *__restrict__ w, LzGeom g, LzCoop c
     {
         const float2 *v0 = reinterpret_cast<const float2 *>(lz_buf(st, k0 % 3)) + base;
         const float2 *v1 = reinterpret_cast<const float2 *>(lz_buf(st, (k0 + 2) % 3)) + base;
-        for (int q = lo2 + tid; q < hi2; q += kCoopThreads) su[q - lo2] = __ldcg(v0 + q);
-        for (int q = lo1 + tid; q < hi1; q += kCoopThreads) sm[q - lo2] = __ldcg(v1 + q);
+        const float2 z = make_float2(0.f, 0.f);
+        for (int i = tid; i < S; i += kCoopThreads) {
+            const int q = o2 + i;
+            const bool in = q >= 0 && q < N;
+            su[i] = in && q < hi2 ? __ldcg(v0 + q) : z;
+            sm[i] = in && q >= lo1 && q < hi1 ? __ldcg(v1 + q) : z;
+#pragma unroll
+            for (int d = 0; d < 4; ++d) ws[i * 4 + d] = in && d < ND ? __ldg(wb + (size_t)q * ND + d) : 0.f;
+        }
     }
     df tt[PPT];
     __syncthreads();
@@ -758,8 +789,8 @@ lz_chunk_halo_kernel(LzState st, const float *__restrict__ w, LzGeom g, LzCoop c
                 for (int j = 0; j < PPT; ++j) {
                     const int p = ps + wt + j * kCoopWorkers;
                     if (p < pe) {
-                        tt[j] = w_times<true>(wb, su, lo2, g, nd, p);
-                        const float2 u2 = su[p - lo2];
+                        tt[j] = w_times_staged<ND>(ws, su, p - o2, W);
+                        const float2 u2 = su[p - o2];
                         const df u = {u2.x, u2.y};
                         acc_prod(dh, dl, tt[j], u);
                         acc_prod(nh, nl, u, u);
@@ -826,8 +857,8 @@ lz_chunk_halo_kernel(LzState st, const float *__restrict__ w, LzGeom g, LzCoop c
         } else if (active) {
             // outer ring of u_k from L2: written by its owners at step k - 1,
             // visible since this step's barrier
-            for (int q = lo2 + wt; q < lo1; q += kCoopWorkers) su[q - lo2] = __ldcg(ucur + q);
-            for (int q = hi1 + wt; q < hi2; q += kCoopWorkers) su[q - lo2] = __ldcg(ucur + q);
+            for (int q = lo2 + wt; q < lo1; q += kCoopWorkers) su[q - o2] = __ldcg(ucur + q);
+            for (int q = hi1 + wt; q < hi2; q += kCoopWorkers) su[q - o2] = __ldcg(ucur + q);
         }
         __syncthreads();
         if (flags[1] != 0) active = false;
@@ -838,27 +869,27 @@ lz_chunk_halo_kernel(LzState st, const float *__restrict__ w, LzGeom g, LzCoop c
             for (int j = 0; j < PPT; ++j) {
                 const int p = ps + wt + j * kCoopWorkers;
                 if (p < pe) {
-                    const float2 u = su[p - lo2], m = sm[p - lo2];
+                    const float2 u = su[p - o2], m = sm[p - o2];
                     float rh = 0.f, rl = 0.f;
                     acc_prod(rh, rl, c1, tt[j]);
                     acc_prod(rh, rl, c2, df{u.x, u.y});
                     acc_prod(rh, rl, c3, df{m.x, m.y});
                     const df r = df_fast_two_sum(rh, rl);
                     const float2 r2 = make_float2(r.h, r.l);
-                    sm[p - lo2] = r2;
+                    sm[p - o2] = r2;
                     __stcg(unext + p, r2);
                 }
             }
             for (int i = wt; i < nring; i += kCoopWorkers) {
                 const int q = i < nl1 ? lo1 + i : pe + (i - nl1);
-                const df t = w_times<true>(wb, su, lo2, g, nd, q);
-                const float2 u = su[q - lo2], m = sm[q - lo2];
+                const df t = w_times_staged<ND>(ws, su, q - o2, W);
+                const float2 u = su[q - o2], m = sm[q - o2];
                 float rh = 0.f, rl = 0.f;
                 acc_prod(rh, rl, c1, t);
                 acc_prod(rh, rl, c2, df{u.x, u.y});
                 acc_prod(rh, rl, c3, df{m.x, m.y});
                 const df r = df_fast_two_sum(rh, rl);
-                sm[q - lo2] = make_float2(r.h, r.l);
+                sm[q - o2] = make_float2(r.h, r.l);
             }
         }
         __syncthreads();
@@ -1251,15 +1282,17 @@ int estimate_lipschitz_grid(const LipschitzJob &job, cudaStream_t st, int *steps
         // strided form with every vector in L2
         coop_chunk = (N + C.gx - 1) / C.gx;
         const long long ppt = (coop_chunk + kCoopWorkers - 1) / kCoopWorkers;
-        coop_smem = (size_t)2 * (coop_chunk + 4 * ((long long)job.W + 1)) * sizeof(float2);
-        if (ppt > 8 || coop_smem > (size_t)200 * 1024) {
+        // weights (4 floats) and two double-float vectors per staged pixel
+        coop_smem = (size_t)(coop_chunk + 4 * ((long long)job.W + 1)) * (4 * sizeof(float) + 2 * sizeof(float2));
+        if (ppt > 8 || coop_smem > (size_t)220 * 1024) {
             coop_fn = (const void *)lz_chunk_strided_kernel;
             coop_smem = 0;
         } else {
-            coop_fn = ppt <= 1   ? (const void *)lz_chunk_halo_kernel<1>
-                      : ppt <= 2 ? (const void *)lz_chunk_halo_kernel<2>
-                      : ppt <= 4 ? (const void *)lz_chunk_halo_kernel<4>
-                                 : (const void *)lz_chunk_halo_kernel<8>;
+            const bool c8 = job.conn == 8;
+            coop_fn = ppt <= 1   ? (c8 ? (const void *)lz_chunk_halo_kernel<1, 4> : (const void *)lz_chunk_halo_kernel<1, 2>)
+                      : ppt <= 2 ? (c8 ? (const void *)lz_chunk_halo_kernel<2, 4> : (const void *)lz_chunk_halo_kernel<2, 2>)
+                      : ppt <= 4 ? (c8 ? (const void *)lz_chunk_halo_kernel<4, 4> : (const void *)lz_chunk_halo_kernel<4, 2>)
+                                 : (c8 ? (const void *)lz_chunk_halo_kernel<8, 4> : (const void *)lz_chunk_halo_kernel<8, 2>);
             LZ_CHECK(cudaFuncSetAttribute(coop_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coop_smem));
         }
         LZ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, coop_fn, kCoopThreads, coop_smem));
