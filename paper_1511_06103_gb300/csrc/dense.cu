@@ -17,8 +17,8 @@
 // chunks (32-byte sectors per thread), transposed through shared memory so
 // that each thread's 4 rows x 6 labels micro-tile is fed by one 128-bit and
 // three 64-bit shared loads per k, and the 256 threads split each chunk four
-// ways along k.  The next chunks are prefetched into registers while the
-// current one is multiplied.  The epilogue (mu product, update,
+// ways along k.  The next eight chunks (64 KB per SM) are prefetched into
+// registers while the current one is multiplied.  The epilogue (mu product, update,
 // renormalisation, free energy) runs on the CTA's 64 rows.
 #include <cmath>
 
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kDT, 1) dense_step_f32_kernel(const __grid_con
 
     const int nchunk = (N + kDK - 1) / kDK;
     // register ring of kDepth chunks in flight: chunk x lives in slot x % kDepth
-    constexpr int kDepth = 4;
+    constexpr int kDepth = 8;
     float4 pa[kDepth], pb[kDepth], pq[kDepth];
 #pragma unroll
     for (int d = 0; d < kDepth; ++d) pq[d] = make_float4(0.f, 0.f, 0.f, 0.f);
