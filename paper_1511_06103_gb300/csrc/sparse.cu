@@ -4,7 +4,8 @@
 //
 // One warp per variable, one lane per label (L <= 32): the lanes walk the
 // variable's adjacency list in CSR form and accumulate the weighted
-// neighbour marginals with one coalesced 4*LP-byte read per neighbour, then
+// neighbour marginals with one coalesced 4*LP-byte read per neighbour (for
+// L <= 8 the lanes split the list instead and reduce in a fixed order), then
 //   m = mu S_out + mu^T S_in      (m = mu S for symmetric mu, S over both
 //                                  directions of every edge),
 // the L x L product with the other lanes' S through warp shuffles, and the
@@ -51,7 +52,51 @@ __device__ __forceinline__ float gather(const int *__restrict__ ptr, const int *
     return acc;
 }
 
-template <bool SYM>
+// The same sums for few labels (L <= LM): the lanes split the adjacency
+// list instead (lane j takes entries j, j + 32, ...), each keeping the L
+// partial sums, which a fixed-shape tree brings to lane 0 and a broadcast
+// hands to every lane.  Returns lane's own label sum (0 past L).
+template <int LM>
+__device__ __forceinline__ float gather_edges(const int *__restrict__ ptr, const int *__restrict__ col,
+                                              const float *__restrict__ wt, const float *__restrict__ q,
+                                              size_t base, int i, int lane, int L, int LP) {
+    float S[LM];
+#pragma unroll
+    for (int l = 0; l < LM; ++l) S[l] = 0.f;
+    const int e0 = ptr[i], e1 = ptr[i + 1];
+#pragma unroll 4
+    for (int e = e0 + lane; e < e1; e += 32) {
+        const float w = wt[e];
+        const float *qr = q + (base + col[e]) * LP;
+#pragma unroll
+        for (int l = 0; l < LM; ++l)
+            if (l < L) S[l] = fmaf(w, __ldg(qr + l), S[l]);
+    }
+    float mine = 0.f;
+#pragma unroll
+    for (int l = 0; l < LM; ++l) {
+        if (l >= L) break;   // warp-uniform
+        float v = S[l];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        v = __shfl_sync(0xffffffffu, v, 0);
+        if (lane == l) mine = v;
+    }
+    return mine;
+}
+
+// Neighbour sums of variable i for lane's label: label-parallel for many
+// labels, edge-parallel for few (LM > 0).
+template <int LM>
+__device__ __forceinline__ float neighbour_sum(const int *ptr, const int *col, const float *wt, const float *q,
+                                               size_t base, int i, int lane, int L, int LP) {
+    if constexpr (LM > 0)
+        return gather_edges<LM>(ptr, col, wt, q, base, i, lane, L, LP);
+    else
+        return gather(ptr, col, wt, q, base, i, lane, LP);
+}
+
+template <bool SYM, int LM>
 __global__ void __launch_bounds__(kST) sparse_step_kernel(const SparseStepLaunch a) {
     __shared__ double red[kSW];
     __shared__ int is_last;
@@ -85,7 +130,7 @@ __global__ void __launch_bounds__(kST) sparse_step_kernel(const SparseStepLaunch
         if (i >= N) break;
         const size_t o = (base + i) * LP + lane;
         // a1: neighbour sums and m_l = sum_k mu[l][k] S_k (+ sum_k mu[k][l] T_k)
-        const float S = gather(a.out_ptr, a.out_col, a.out_w, a.q_in, base, i, lane, LP);
+        const float S = neighbour_sum<LM>(a.out_ptr, a.out_col, a.out_w, a.q_in, base, i, lane, L, LP);
         float m = 0.f;
         if constexpr (SYM) {
             for (int k = 0; k < L; ++k) {
@@ -93,7 +138,7 @@ __global__ void __launch_bounds__(kST) sparse_step_kernel(const SparseStepLaunch
                 if (live) m = fmaf(mus[lane * L + k], Sk, m);
             }
         } else {
-            const float T = gather(a.in_ptr, a.in_col, a.in_w, a.q_in, base, i, lane, LP);
+            const float T = neighbour_sum<LM>(a.in_ptr, a.in_col, a.in_w, a.q_in, base, i, lane, L, LP);
             for (int k = 0; k < L; ++k) {
                 const float Sk = __shfl_sync(0xffffffffu, S, k);
                 const float Tk = __shfl_sync(0xffffffffu, T, k);
@@ -177,10 +222,18 @@ int sparse_blocks(int N) { return (N + kSW * kVPW - 1) / (kSW * kVPW); }
 
 cudaError_t launch_sparse_step(const SparseStepLaunch &a, cudaStream_t st) {
     dim3 grid(sparse_blocks(a.N), a.B);
-    if (a.sym)
-        sparse_step_kernel<true><<<grid, kST, 0, st>>>(a);
-    else
-        sparse_step_kernel<false><<<grid, kST, 0, st>>>(a);
+    // up to 8 labels the lanes split the adjacency lists instead of the labels
+    if (a.L <= 8) {
+        if (a.sym)
+            sparse_step_kernel<true, 8><<<grid, kST, 0, st>>>(a);
+        else
+            sparse_step_kernel<false, 8><<<grid, kST, 0, st>>>(a);
+    } else {
+        if (a.sym)
+            sparse_step_kernel<true, 0><<<grid, kST, 0, st>>>(a);
+        else
+            sparse_step_kernel<false, 0><<<grid, kST, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

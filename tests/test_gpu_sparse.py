@@ -44,7 +44,10 @@ def crf_for(binding, d, batch=1):
 
 
 @pytest.mark.parametrize("N,E,L,sym", [(500, 2000, 3, True), (500, 2000, 5, False), (333, 1500, 21, True),
-                                       (257, 900, 32, False), (40, 0, 4, True), (1, 0, 2, True)])
+                                       (257, 900, 32, False), (40, 0, 4, True), (1, 0, 2, True),
+                                       # degrees above 32: several entries per lane in the
+                                       # edge-parallel sums (L <= 8), and its largest L
+                                       (300, 12000, 8, False), (200, 9000, 2, True), (150, 6000, 9, True)])
 def test_sparse_single_step(env, N, E, L, sym):
     binding, oracle, torch = env
     d = synth.random_graph(N, E, L, seed=N + E + L, symmetric=sym)
