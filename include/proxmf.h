@@ -198,7 +198,11 @@ crf_status mf_log_marginals(crf_t h, float *logq, int is_device);
  * constant Hessian of E restricted to the tangent space of the simplex
  * product, Sec. 3.2) and eta = 1/(1+max(Lambda,0)), one per instance: host
  * arrays [batch] (either may be NULL).  Computed on the device by a Lanczos
- * iteration on first use after crf_set_pairwise; synchronises the stream. */
+ * iteration on first use after crf_set_pairwise (also by mf_iterate with
+ * eta <= 0); synchronises the stream.  On grids with symmetric mu the
+ * Lanczos chain runs as cooperative launches whose grid barriers wait at
+ * most ~2 s each: a wait that runs out returns CRF_E_TIMEOUT, leaves the
+ * constant unset and the handle usable. */
 crf_status mf_lipschitz(crf_t h, double *Lambda, double *eta);
 
 /* mf_profile -- enable (1) or disable (0) event timing of the iteration

@@ -345,7 +345,9 @@ lz_step_b_kernel(LzState st, LzGeom g) {
     st.counter[b] = 0u;
     if (active) {
         const double bk = sqrt(s);
-        const double ref = fabs(st.alpha[(size_t)b * st.ld + k]) + st.nrm[(size_t)b * st.ld + k];
+        // breakdown scale |alpha_k| + beta_{k-1}; at k = 0, |alpha_0| + beta_0
+        // (nrm[0] is the start vector's norm, unrelated to the matrix scale)
+        const double ref = fabs(st.alpha[(size_t)b * st.ld + k]) + (k > 0 ? st.nrm[(size_t)b * st.ld + k] : bk);
         st.nrm[(size_t)b * st.ld + k + 1] = bk;
         if (!(bk > 1e-13 * ref) || !(bk > 1e-300)) st.stop[b] = k + 1;
     }
@@ -605,7 +607,7 @@ __device__ __forceinline__ void coop_scalars_beta(double s, const LzState &st, i
                                                   CoopThread0 &t0) {
     const size_t ld = (size_t)st.ld;
     const double bk = sqrt(s);
-    const double ref = fabs(t0.alpha) + t0.nk;
+    const double ref = fabs(t0.alpha) + (k > 0 ? t0.nk : bk);   // as in the two-kernel form
     const bool brk = !(bk > 1e-13 * ref) || !(bk > 1e-300);
     if (bx == 0) {
         st.alpha[b * ld + k] = t0.alpha;
@@ -833,7 +835,9 @@ lz_chunk_halo_kernel(LzState st, const float *__restrict__ w, LzGeom g, LzCoop c
                 // one reciprocal square root; the rest are products
                 const double inv = rsqrt(sn);
                 const double nk = sn * inv;
-                const bool brk = !(nk > 1e-300) || (k > 0 && !(nk > 1e-13 * (fabs(a_prev) + n_prev)));
+                // beta_{k-1} against |alpha_{k-1}| + beta_{k-2} (beta_0 itself at k = 1)
+                const bool brk =
+                    !(nk > 1e-300) || (k > 0 && !(nk > 1e-13 * (fabs(a_prev) + (k > 1 ? n_prev : nk))));
                 const double alpha = sd * inv * inv;
                 if (bx == 0) {
                     if (k > 0) st.nrm[b * ld + k] = nk;

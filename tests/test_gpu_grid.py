@@ -334,3 +334,52 @@ def test_step_constant_batch_vs_dense_eigensolve(env, B, Hh, Ww, L, conn):
         ref = oracle_model(oracle, d).hessian_eigenvalues(projected=True)[-1]
         assert math.isclose(lam[i], ref, rel_tol=1e-8, abs_tol=1e-12)
         assert math.isclose(eta[i], 1.0 / (1.0 + max(ref, 0.0)), rel_tol=1e-6)
+
+
+def _lipschitz(binding, d, B=1, w_scale=1.0, ds=None):
+    ds = ds or [d]
+    topo_ = binding.CRF_GRID8 if d["conn"] == 8 else binding.CRF_GRID4
+    with binding.CRF(topo_, d["L"], d["H"], d["W"], batch=B) as crf:
+        crf.set_unary(np.stack([x["U"] for x in ds]) if B > 1 else d["U"])
+        w = np.stack([x["w"] for x in ds]) if B > 1 else d["w"]
+        crf.set_pairwise(d["mu"], (w * w_scale).astype(np.float32))
+        lam, _ = crf.lipschitz()
+    return lam
+
+
+def test_step_constant_large_batch_strided_form(env):
+    """40 instances of 128 x 128: too many pixels per block for the shared-
+    memory form, so the cooperative launch takes the strided form; every
+    instance's constant equals the one its single-instance handle (staged
+    form) computes."""
+    binding, oracle, torch = env
+    ds = [synth.random_grid(128, 128, 5, 8, seed=1200 + i, symmetric=True) for i in range(40)]
+    for d in ds:
+        d["mu"] = ds[0]["mu"]
+    lam_b = _lipschitz(binding, ds[0], B=40, ds=ds)
+    for i in (0, 17, 39):
+        lam_1 = _lipschitz(binding, ds[i])
+        assert math.isclose(lam_b[i], lam_1[0], rel_tol=1e-8)
+
+
+def test_step_constant_fp64_form_for_extreme_weights(env):
+    """Weights scaled by 2^-45 fall outside the double-float range test and
+    take the FP64 two-kernel form; Lambda scales exactly with the weights."""
+    binding, oracle, torch = env
+    d = synth.random_grid(61, 47, 6, 8, seed=1300, symmetric=True)
+    lam = _lipschitz(binding, d)[0]
+    lam_s = _lipschitz(binding, d, w_scale=2.0 ** -45)[0]
+    assert math.isclose(lam_s * 2.0 ** 45, lam, rel_tol=1e-8)
+
+
+def test_step_constant_fp64_form_for_many_instances(env):
+    """More instances than SMs: the FP64 two-kernel form runs (no
+    cooperative launch); each constant equals the dense eigen-solve."""
+    binding, oracle, torch = env
+    ds = [synth.random_grid(5, 6, 3, 8, seed=1400 + i, symmetric=True) for i in range(160)]
+    for d in ds:
+        d["mu"] = ds[0]["mu"]
+    lam = _lipschitz(binding, ds[0], B=160, ds=ds)
+    for i in (0, 81, 159):
+        ref = oracle_model(oracle, ds[i]).hessian_eigenvalues(projected=True)[-1]
+        assert math.isclose(lam[i], ref, rel_tol=1e-8, abs_tol=1e-12)
