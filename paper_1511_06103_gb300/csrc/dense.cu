@@ -13,12 +13,14 @@
 // K is materialised once per model ([B][N][N], FP32 here; BF16 for the
 // tensor-core form in dense_tc.cu), so a step streams it from HBM: the FP32
 // form reads 4 N^2 bytes per iteration and is bound by HBM bandwidth.
-// A CTA owns 64 rows of K and all label columns; K is read in 32 x 64
-// chunks (32-byte sectors per thread), transposed through shared memory so
-// that each thread's 4 rows x 6 labels micro-tile is fed by one 128-bit and
-// three 64-bit shared loads per k, and the 256 threads split each chunk four
-// ways along k.  The next eight chunks (64 KB per SM) are prefetched into
-// registers while the current one is multiplied.  The epilogue (mu product, update,
+// A CTA owns 64 rows of K and all label columns; K is read in 64 x 32
+// chunks, copied asynchronously (cp.async, 16 bytes per copy, coalesced
+// along the rows) into a padded row-major shared-memory tile.  Each thread
+// owns 4 rows (16 apart) x 6 labels and the four k of its slice of a chunk:
+// one 128-bit shared load per row and three 64-bit loads of q per k feed
+// 12 paired FMAs per k; the 512 threads split each chunk eight ways along k.
+// A ring of six chunks (K and Q, 74 KB) is in flight per SM while one is
+// multiplied.  The epilogue (mu product, update,
 // renormalisation, free energy) runs on the CTA's 64 rows.
 #include <cmath>
 
@@ -32,8 +34,16 @@ namespace {
 
 constexpr int kDR = 64;        // rows of K per CTA
 constexpr int kDK = 32;        // k per chunk
-constexpr int kDT = 256;       // threads per CTA
-constexpr int kKsStride = kDR + 4;
+constexpr int kDT = 512;       // threads per CTA
+constexpr int kSlices = kDT / 64;   // k slices of a chunk (64 threads each)
+constexpr int kStages = 6;     // chunks in flight in the shared-memory ring
+
+constexpr int kKsRow = kDK + 4;   // padded K tile row (16-byte aligned, conflict-free 128-bit reads)
+
+template <int LP>
+constexpr size_t dense_f32_dyn_smem() {
+    return (size_t)kStages * (kDR * kKsRow + kDK * LP) * sizeof(float);
+}
 
 // ---------------------------------------------------------------- K build --
 
@@ -107,13 +117,44 @@ struct DenseStepArgs {
 
 namespace {
 
+// cp.async helpers: 4-byte copy with zero fill when !valid (no bytes read),
+// 16-byte copy, group commit and wait.
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(gmem), "r"(valid ? 4 : 0) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+}
+
+// 16-byte copy of the first nbytes (0..16) of the source, the rest zero
+__device__ __forceinline__ void cp_async16z(void *smem, const void *gmem, int nbytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem), "r"(nbytes) : "memory");
+}
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 template <int LP>
 __global__ void __launch_bounds__(kDT, 1) dense_step_f32_kernel(const __grid_constant__ DenseStepArgs a) {
     constexpr int NC = (LP + 5) / 6;             // column groups of 6 (last may be partial)
     constexpr int CG = 4;                        // column groups handled by the thread grid
     static_assert(NC <= CG, "LP <= 24");
-    __shared__ __align__(16) float Ks[2][kDK][kKsStride];
-    __shared__ __align__(16) float Qs[2][kDK][LP];
+    extern __shared__ __align__(16) float dsm[];
+    float *Ks = dsm;                                     // [kStages][kDR][kKsRow]  (row-major K tile)
+    float *Qs = Ks + (size_t)kStages * kDR * kKsRow;     // [kStages][kDK][LP]
     __shared__ __align__(16) float Sred[kDR][LP + 1];
     __shared__ float mus[kMaxLabels * kMaxLabels];
     __shared__ double red[kDT / 32];
@@ -141,13 +182,20 @@ __global__ void __launch_bounds__(kDT, 1) dense_step_f32_kernel(const __grid_con
 
     for (int i = tid; i < L * L; i += kDT) mus[(i / L) * kMaxLabels + (i % L)] = a.mu[i];
 
-    // micro-tile: rows 4*ig .. 4*ig+3, label columns 6*cg .. 6*cg+5, k slice ks
+    // micro-tile: rows ig + 16 r (r < 4), label columns 6*cg .. 6*cg+5, the
+    // four k of slice ks of each chunk
     const int ig = tid & 15, cg = (tid >> 4) & 3, ks = tid >> 6;
-    // loader mapping: warp w loads rows (w & 1)*32 + lane, k = 8*(w >> 1) .. +7
-    const int lw = tid >> 5, lane = tid & 31;
-    const int lrow = (lw & 1) * 32 + lane, lk = 8 * (lw >> 1);
-    const int grow = min(row0 + lrow, N - 1);
-    const float *ksrc = Kb + (size_t)grow * N + lk;
+    // loader: row tid >> 3, k = 4 * (tid & 7) .. +3 of the chunk: one 16-byte
+    // asynchronous copy (rows of K start on 16-byte boundaries when N % 4 == 0;
+    // otherwise four 4-byte copies), zero past N
+    const int lrow = tid >> 3, lk = 4 * (tid & 7);
+    const bool rvalid = row0 + lrow < N;
+    const float *ksrc = Kb + (size_t)(rvalid ? row0 + lrow : 0) * N;
+    const bool vec16 = (N & 3) == 0;
+    // Q chunk in 16-byte pieces (8-byte for LP = 2: an instance's rows then
+    // start on an 8-byte boundary only); rows past N read the zero padding
+    constexpr int kQV = LP % 4 == 0 ? 4 : 2;
+    constexpr int kQn = kDK * LP / kQV;
 
     float2 acc[4][3];
 #pragma unroll
@@ -156,80 +204,78 @@ __global__ void __launch_bounds__(kDT, 1) dense_step_f32_kernel(const __grid_con
         for (int c = 0; c < 3; ++c) acc[r][c] = splat2(0.f);
 
     const int nchunk = (N + kDK - 1) / kDK;
-    // register ring of kDepth chunks in flight: chunk x lives in slot x % kDepth
-    constexpr int kDepth = 8;
-    float4 pa[kDepth], pb[kDepth], pq[kDepth];
-#pragma unroll
-    for (int d = 0; d < kDepth; ++d) pq[d] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const bool qloader = tid < kDK * LP / 4;
-    const int qk = qloader ? (tid * 4) / LP : 0, ql = qloader ? (tid * 4) % LP : 0;
-    auto load_chunk = [&](int c, float4 &ra, float4 &rb, float4 &rq) {
-        const int k0 = c * kDK;
-        if (k0 + lk + 8 <= N && (N % 4) == 0) {
-            ra = __ldg(reinterpret_cast<const float4 *>(ksrc + k0));
-            rb = __ldg(reinterpret_cast<const float4 *>(ksrc + k0) + 1);
+    auto issue = [&](int c) {
+        const int stg = c % kStages, k0 = c * kDK;
+        float *kd = Ks + (size_t)stg * kDR * kKsRow + lrow * kKsRow + lk;
+        const int k = k0 + lk;
+        if (vec16) {
+            const int nb = rvalid ? max(0, min(16, 4 * (N - k))) : 0;
+            cp_async16z(kd, nb > 0 ? ksrc + k : Kb, nb);
         } else {
-            float t[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) t[e] = (k0 + lk + e < N) ? __ldg(ksrc + k0 + e) : 0.f;
-            ra = make_float4(t[0], t[1], t[2], t[3]);
-            rb = make_float4(t[4], t[5], t[6], t[7]);
+            for (int e = 0; e < 4; ++e) {
+                const bool v = rvalid && k + e < N;
+                cp_async4(kd + e, v ? ksrc + k + e : Kb, v);
+            }
         }
-        if (row0 + lrow >= N) ra = rb = make_float4(0.f, 0.f, 0.f, 0.f);
-        // q rows past N read the zero padding of the buffer (multiplied by K = 0)
-        if (qloader) rq = __ldg(reinterpret_cast<const float4 *>(qb + (size_t)(k0 + qk) * LP + ql));
+        if (tid < kQn) {
+            float *qd = Qs + (size_t)stg * kDK * LP + kQV * tid;
+            const float *qsrc = qb + (size_t)k0 * LP + kQV * tid;
+            if constexpr (kQV == 4)
+                cp_async16(qd, qsrc);
+            else
+                cp_async8(qd, qsrc);
+        }
     };
-    auto store_chunk = [&](int buf, const float4 &ra, const float4 &rb, const float4 &rq) {
-        const float v[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
-#pragma unroll
-        for (int e = 0; e < 8; ++e) Ks[buf][lk + e][lrow] = v[e];
-        if (qloader) *reinterpret_cast<float4 *>(&Qs[buf][qk][ql]) = rq;
-    };
-    auto compute_chunk = [&](int buf) {
+    auto compute = [&](int stg) {
         if (cg >= NC) return;
+        const float *kb = Ks + (size_t)stg * kDR * kKsRow + ks * (kDK / kSlices);
+        const float *qs = Qs + (size_t)stg * kDK * LP + ks * (kDK / kSlices) * LP;
+        float kr[4][4];
 #pragma unroll
-        for (int kk = 0; kk < kDK / 4; ++kk) {
-            const int k = ks * (kDK / 4) + kk;
-            const float4 kv = *reinterpret_cast<const float4 *>(&Ks[buf][k][4 * ig]);
-            const float kr[4] = {kv.x, kv.y, kv.z, kv.w};
+        for (int r = 0; r < 4; ++r) {
+            const float4 kv = *reinterpret_cast<const float4 *>(kb + (ig + 16 * r) * kKsRow);
+            kr[r][0] = kv.x;
+            kr[r][1] = kv.y;
+            kr[r][2] = kv.z;
+            kr[r][3] = kv.w;
+        }
+#pragma unroll
+        for (int kk = 0; kk < kDK / kSlices; ++kk) {
             float2 qv[3];
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
                 const int col = 6 * cg + 2 * p;
-                qv[p] = col + 1 < LP ? *reinterpret_cast<const float2 *>(&Qs[buf][k][col]) : splat2(0.f);
+                qv[p] = col + 1 < LP ? *reinterpret_cast<const float2 *>(qs + kk * LP + col) : splat2(0.f);
             }
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const float2 kk2 = splat2(kr[r]);
+                const float2 kk2 = splat2(kr[r][kk]);
 #pragma unroll
                 for (int p = 0; p < 3; ++p) acc[r][p] = fma2(kk2, qv[p], acc[r][p]);
             }
         }
     };
 
+    // multistage ring: chunk c lands in stage c % kStages; the copy of chunk
+    // c + kStages - 1 goes into the stage computed one iteration earlier
 #pragma unroll
-    for (int d = 0; d < kDepth; ++d)
-        if (d < nchunk) load_chunk(d, pa[d], pb[d], pq[d]);
-    store_chunk(0, pa[0], pb[0], pq[0]);
-    __syncthreads();
-    for (int c = 0; c < nchunk; c += kDepth) {
-#pragma unroll
-        for (int d = 0; d < kDepth; ++d) {
-            const int cc = c + d;
-            if (cc < nchunk) {
-                compute_chunk(cc & 1);
-                constexpr int dummy = 0;
-                (void)dummy;
-                const int nx = (d + 1) % kDepth;
-                if (cc + 1 < nchunk) store_chunk((cc + 1) & 1, pa[nx], pb[nx], pq[nx]);
-                if (cc + kDepth < nchunk) load_chunk(cc + kDepth, pa[d], pb[d], pq[d]);
-                __syncthreads();
-            }
-        }
+    for (int c = 0; c < kStages - 1; ++c) {
+        if (c < nchunk) issue(c);
+        cp_async_commit();
     }
+    for (int c = 0; c < nchunk; ++c) {
+        cp_async_wait<kStages - 2>();
+        __syncthreads();
+        compute(c % kStages);
+        if (c + kStages - 1 < nchunk) issue(c + kStages - 1);
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+    __syncthreads();
 
-    // reduce the four k slices: slice 0 writes, 1..3 add, in a fixed order
-    for (int sl = 0; sl < 4; ++sl) {
+    // reduce the k slices: slice 0 writes, the others add, in a fixed order
+    for (int sl = 0; sl < kSlices; ++sl) {
         if (ks == sl && cg < NC) {
 #pragma unroll
             for (int r = 0; r < 4; ++r)
@@ -237,7 +283,7 @@ __global__ void __launch_bounds__(kDT, 1) dense_step_f32_kernel(const __grid_con
                 for (int p = 0; p < 3; ++p) {
                     const int col = 6 * cg + 2 * p;
                     if (col + 1 < LP) {
-                        float *d = &Sred[4 * ig + r][col];
+                        float *d = &Sred[ig + 16 * r][col];
                         if (sl == 0) {
                             d[0] = acc[r][p].x;
                             d[1] = acc[r][p].y;
@@ -323,6 +369,24 @@ cudaError_t launch_dense_export_q(const float *s, float *q32, __nv_bfloat16 *qt1
 
 int dense_nblk(int N) { return (N + kDR - 1) / kDR; }
 
+namespace {
+
+template <int LP>
+cudaError_t launch_f32(dim3 grid, const DenseStepArgs &a, cudaStream_t st) {
+    constexpr size_t smem = dense_f32_dyn_smem<LP>();
+    static bool attr = false;   // the opt-in above 48 KB, once per process and label count
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(dense_step_f32_kernel<LP>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dense_step_f32_kernel<LP><<<grid, kDT, smem, st>>>(a);
+    return cudaSuccess;
+}
+
+}  // namespace
+
 cudaError_t launch_dense_step_f32(const DenseStepLaunch &l, cudaStream_t st) {
     DenseStepArgs a;
     a.K = l.K32;
@@ -349,16 +413,18 @@ cudaError_t launch_dense_step_f32(const DenseStepLaunch &l, cudaStream_t st) {
     a.update = l.update;
     a.rel_tol = l.rel_tol;
     dim3 grid(a.nblk, l.B);
+    cudaError_t e = cudaSuccess;
     switch (storage_labels(l.L)) {
-    case 2: dense_step_f32_kernel<2><<<grid, kDT, 0, st>>>(a); break;
-    case 4: dense_step_f32_kernel<4><<<grid, kDT, 0, st>>>(a); break;
-    case 8: dense_step_f32_kernel<8><<<grid, kDT, 0, st>>>(a); break;
-    case 12: dense_step_f32_kernel<12><<<grid, kDT, 0, st>>>(a); break;
-    case 16: dense_step_f32_kernel<16><<<grid, kDT, 0, st>>>(a); break;
-    case 20: dense_step_f32_kernel<20><<<grid, kDT, 0, st>>>(a); break;
-    case 24: dense_step_f32_kernel<24><<<grid, kDT, 0, st>>>(a); break;
+    case 2: e = launch_f32<2>(grid, a, st); break;
+    case 4: e = launch_f32<4>(grid, a, st); break;
+    case 8: e = launch_f32<8>(grid, a, st); break;
+    case 12: e = launch_f32<12>(grid, a, st); break;
+    case 16: e = launch_f32<16>(grid, a, st); break;
+    case 20: e = launch_f32<20>(grid, a, st); break;
+    case 24: e = launch_f32<24>(grid, a, st); break;
     default: return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

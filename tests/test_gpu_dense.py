@@ -118,12 +118,15 @@ def test_dense_step_constant(env):
     assert math.isclose(lam[0], lam_ref, rel_tol=2e-6)
 
 
-def test_dense_batch_independent(env):
+@pytest.mark.parametrize("side,L,B", [(8, 5, 2), (9, 2, 3)])
+def test_dense_batch_independent(env, side, L, B):
+    """Instances of a batch solve as they do alone (9 x 9, L = 2: odd N with
+    two stored labels, so later instances start off a 16-byte boundary)."""
     binding, oracle, torch = env
-    ds = [synth.dense_gaussian(side=8, L=5, seed=40 + i) for i in range(2)]
+    ds = [synth.dense_gaussian(side=side, L=L, seed=40 + i) for i in range(B)]
     for d in ds:
         d["mu"] = ds[0]["mu"]
-    with binding.CRF(binding.CRF_DENSE_GAUSS, 5, 8, 8, batch=2) as crf:
+    with binding.CRF(binding.CRF_DENSE_GAUSS, L, side, side, batch=B) as crf:
         crf.set_unary(np.stack([d["U"] for d in ds]))
         crf.set_pairwise(ds[0]["mu"], np.stack([d["feats"] for d in ds]), theta=np.array(ds[0]["theta"], np.float32))
         crf.iterate(10, eta=0.3)
