@@ -392,16 +392,18 @@ def run_grid_precision(args, dev, peak):
 
 def run_denoising(args, dev):
     """Binary denoising CRF, 64 x 64, L = 2, 4-connected, 50 steps at the
-    step-size constant: device time per solve with launches issued one by
-    one and with the step loop replayed as a CUDA graph."""
+    step-size constant: device time per solve with the whole loop in one
+    cluster launch (the default), with one launch per step replayed as a
+    CUDA graph, and with launches issued one by one."""
     import torch
 
     from paper_1511_06103_gb300 import binding, synth
     d = synth.binary_denoising()
     stream = torch.cuda.current_stream(dev)
     out = {}
-    for mode in ("eager", "graph"):
+    for mode in ("resident", "graph", "eager"):
         crf = binding.CRF(binding.CRF_GRID4, 2, 64, 64, stream=stream.cuda_stream)
+        crf.use_resident(mode == "resident")
         crf.use_graphs(mode == "graph")
         crf.set_unary(torch.from_numpy(d["U"]).to(dev))
         crf.set_pairwise(torch.from_numpy(d["mu"]).to(dev), torch.from_numpy(d["w"]).to(dev))

@@ -217,6 +217,16 @@ crf_status mf_profile(crf_t h, int32_t enable);
  * the loop's end event. */
 crf_status mf_profile_read(crf_t h, double *loop_ms, int32_t *launches);
 
+/* mf_use_resident -- 1 (the default): mf_iterate on a grid handle whose
+ * iterates fit in the shared memory of a thread-block cluster (up to 8 CTAs
+ * per instance, each holding a slab of rows: 4 x rows x W x L_stored floats
+ * <= 200 KB per CTA, L <= 16), FP32 form, fixed rule and at least two steps
+ * runs the whole loop in one launch (a cluster barrier between steps) and
+ * records it as one launch; 0: one launch per step.  Same traces, stopping
+ * rule and final state, up to FP32 rounding.  Returns CRF_E_INVALID for a
+ * null handle. */
+crf_status mf_use_resident(crf_t h, int32_t enable);
+
 /* mf_use_graphs -- 1: mf_iterate records its step launches into a CUDA
  * graph the first time a configuration (max_iters, refine_fp32, rel_tol, the
  * step-size source, the parity of the state buffers) is seen and replays the

@@ -84,6 +84,7 @@ _SIGS = {
     "mf_profile_read": [_vp, _vp, _vp],
     "crf_launch_count": [_vp, _vp],
     "mf_use_graphs": [_vp, C.c_int32],
+    "mf_use_resident": [_vp, C.c_int32],
     "mf_unrolled_checkpoint_floats": [_vp, C.c_int32, _vp],
     "mf_unrolled_forward": [_vp, C.c_int32, C.c_double, _vp],
     "mf_unrolled_backward": [_vp, C.c_int32, C.c_double, _vp, _vp, _vp, _vp, _vp, C.c_int32],
@@ -346,6 +347,10 @@ class CRF:
 
     def use_graphs(self, enable: bool = True) -> None:
         _call("mf_use_graphs", self.h, int(bool(enable)))
+
+    def use_resident(self, enable: bool = True) -> None:
+        """Small grids: the whole iteration loop in one launch (the default)."""
+        _call("mf_use_resident", self.h, int(bool(enable)))
 
     def checkpoint_floats(self, K: int) -> int:
         return mf_unrolled_checkpoint_floats(self.h, K)

@@ -65,6 +65,7 @@ struct crf_s {
     int cur = 0;
     std::vector<float> mu;
     bool mu_sym = true;
+    bool use_resident = true;    // small grids: one launch per mf_iterate (grid_resident.cu)
     bool has_unary = false, has_pairwise = false, lambda_valid = false, broken = false;
     int lanczos_steps = 0;
     bool profile = false;
@@ -952,8 +953,12 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
     h->gamma1 = (float)p->gamma1;
     h->gamma2 = (float)p->gamma2;
     h->eps = (float)p->epsilon;
+    // small grids: the whole loop in one launch, one thread-block cluster per
+    // instance with the iterates in shared memory (fixed rule, FP32)
+    const bool resident = h->use_resident && !h->dense && !h->sparse && !h->bf16 && p->rule == MF_RULE_FIXED &&
+                          nsteps >= 2 && grid_resident_fits(h->H, h->W, h->L, h->LP);
     cudaGraphExec_t exec = nullptr;
-    if (h->use_graphs && nsteps > 0) {
+    if (h->use_graphs && nsteps > 0 && !resident) {
         for (auto &g : h->graphs)
             if (g.iters == p->max_iters && g.refine == refine && g.cur == h->cur && g.rel_tol == p->rel_tol &&
                 g.eta == eta && g.rule == p->rule && g.gamma1 == p->gamma1 && g.gamma2 == p->gamma2 &&
@@ -989,7 +994,34 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
         }
     }
     if (h->profile) CK(h, cudaEventRecord(h->ev0, h->st));
-    if (exec) {
+    if (resident) {
+        h->adapt_active = false;
+        h->rule_kernel = 0;
+        if (p->rel_tol > 0) CK(h, cudaMemsetAsync(h->done, 0, h->B * sizeof(int), h->st));
+        GridResidentLaunch ra{};
+        ra.s_in = h->s[h->cur];
+        ra.s_out = h->s[h->cur ^ (nsteps & 1)];   // where the step-by-step loop would leave it
+        ra.U = h->U;
+        ra.w = h->w;
+        ra.mu = h->mu_dev;
+        ra.eta = eta;
+        ra.f_trace = h->ftrace;
+        ra.f_cur = h->fcur;
+        ra.done = h->done;
+        ra.status = h->status;
+        ra.B = h->B;
+        ra.H = h->H;
+        ra.W = h->W;
+        ra.L = h->L;
+        ra.LP = h->LP;
+        ra.conn = h->conn;
+        ra.mu_sym = h->mu_sym ? 1 : 0;
+        ra.nsteps = nsteps;
+        ra.trace_cap = h->trace_cap;
+        ra.rel_tol = p->rel_tol;
+        CK(h, launch_grid_resident(ra, h->st));
+        h->cur ^= nsteps & 1;
+    } else if (exec) {
         h->adapt_active = false;
         h->rule_kernel = 0;
         CK(h, cudaGraphLaunch(exec, h->st));
@@ -1000,10 +1032,10 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
         h->rule_kernel = 0;
         CK(h, e);
     }
-    h->launches += nsteps;
+    h->launches += resident ? 1 : nsteps;
     if (h->profile) {
         CK(h, cudaEventRecord(h->ev1, h->st));
-        h->prof_launches = p->max_iters + refine;
+        h->prof_launches = resident ? 1 : p->max_iters + refine;
         h->prof_valid = true;
     }
     h->last_iters = p->max_iters + refine;
@@ -1109,6 +1141,13 @@ crf_status mf_profile_read(crf_t h, double *loop_ms, int32_t *launches) {
     CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
     if (loop_ms) *loop_ms = ms;
     if (launches) *launches = h->prof_launches;
+    return CRF_OK;
+}
+
+crf_status mf_use_resident(crf_t h, int32_t enable) {
+    const crf_status rc = check_handle(h);
+    if (rc != CRF_OK) return rc;
+    h->use_resident = enable != 0;
     return CRF_OK;
 }
 

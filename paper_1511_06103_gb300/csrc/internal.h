@@ -47,6 +47,29 @@ constexpr int kTcImageBytes = 2 * 32 * 32 * 2;   // mu and mu^T images at the la
 // Everything one launch of the grid step needs.  State and unaries are
 // pixel-major [B][N][storage_labels(L)], N = H*W, pixel p = y*W + x; edge
 // weights are [B][N][n_dirs] with zero on edges that leave the image.
+// The whole iteration loop of a small grid instance in one launch, one
+// thread-block cluster per instance with the iterates in shared memory
+// (grid_resident.cu).
+constexpr size_t kResidentMaxSmem = 200 * 1024;
+constexpr int kResidentCtas = 8;   // CTAs per instance (one cluster), rows split among them
+struct GridResidentLaunch {
+    const float *s_in;       // [B][N][LP] log q^0 (padding kPadLogQ)
+    float *s_out;            // [B][N][LP] log q after the loop (may equal s_in)
+    const float *U;          // [B][N][LP]
+    const float *w;          // [B][N][n_dirs] pixel-major edge weights
+    const float *mu;         // [L][L] device
+    const float *eta;        // [B]
+    double *f_trace;         // [B][trace_cap]: F(q^t) of each step
+    double *f_cur;           // [B]: F of the last iterate read
+    int *done;               // [B]: step count at which the stopping rule held
+    int *status;
+    int B, H, W, L, LP, conn, mu_sym, nsteps, trace_cap;
+    double rel_tol;
+};
+size_t grid_resident_smem(int H, int W, int L, int LP);
+bool grid_resident_fits(int H, int W, int L, int LP);
+cudaError_t launch_grid_resident(const GridResidentLaunch &a, cudaStream_t st);
+
 struct GridStepLaunch {
     const float *s_in;       // log q^t
     float *s_out;            // log q^{t+1}

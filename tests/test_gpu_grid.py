@@ -277,6 +277,7 @@ def test_graph_replay_matches_eager(env, rel_tol):
     for graphs in (False, True):
         with make(binding, torch, d) as crf:
             crf.use_graphs(graphs)
+            crf.use_resident(False)   # the step-by-step loop (eager or replayed)
             crf.set_unary(d["U"])
             crf.set_pairwise(d["mu"], d["w"])
             out = []
@@ -383,3 +384,45 @@ def test_step_constant_fp64_form_for_many_instances(env):
     for i in (0, 81, 159):
         ref = oracle_model(oracle, ds[i]).hessian_eigenvalues(projected=True)[-1]
         assert math.isclose(lam[i], ref, rel_tol=1e-8, abs_tol=1e-12)
+
+
+@pytest.mark.parametrize("Hh,Ww,L,conn,sym,B", [(64, 64, 2, 4, True, 1), (37, 45, 3, 8, False, 2),
+                                              (21, 30, 8, 8, True, 1), (19, 23, 13, 4, False, 3),
+                                              (1, 1, 2, 8, True, 1), (7, 1, 5, 8, False, 1)])
+def test_resident_loop_matches_step_loop(env, Hh, Ww, L, conn, sym, B):
+    """The one-launch loop of small grids against the launch-per-step loop:
+    states, free-energy traces, stop counts and the final F agree to FP32
+    rounding, and the trajectory against the oracle's."""
+    binding, oracle, torch = env
+    ds = [synth.random_grid(Hh, Ww, L, conn, seed=1500 + 11 * i + L, symmetric=sym) for i in range(B)]
+    for d in ds:
+        d["mu"] = ds[0]["mu"]
+    topo_ = binding.CRF_GRID8 if conn == 8 else binding.CRF_GRID4
+    out = []
+    for resident in (True, False):
+        with binding.CRF(topo_, L, Hh, Ww, batch=B) as crf:
+            crf.use_resident(resident)
+            crf.set_unary(np.stack([d["U"] for d in ds]) if B > 1 else ds[0]["U"])
+            crf.set_pairwise(ds[0]["mu"], np.stack([d["w"] for d in ds]) if B > 1 else ds[0]["w"])
+            crf.iterate(40, eta=0.35, final_free_energy=True)
+            out.append((crf.log_marginals().astype(np.float64), crf.free_energy_trace(40),
+                        crf.free_energy()))
+            crf.iterate(9, eta=0.3, reset=True)   # odd count: the final buffer flips
+            out.append((crf.log_marginals().astype(np.float64), crf.free_energy_trace(9), None))
+            its = crf.iterate(400, eta=0.35, reset=True, rel_tol=1e-6, want_iters=True)
+            out.append((None, None, its.copy()))
+    (s_r, tr_r, F_r), (s9_r, tr9_r, _), (_, _, it_r), (s_s, tr_s, F_s), (s9_s, tr9_s, _), (_, _, it_s) = out
+    # the stopping rule fires at the same step, up to a tie decided by rounding
+    assert np.abs(it_r.astype(int) - it_s.astype(int)).max() <= 1
+    assert np.abs(np.exp(s_r) - np.exp(s_s)).max() <= 2e-5
+    assert np.abs(np.exp(s9_r) - np.exp(s9_s)).max() <= 2e-5
+    for b in range(B):
+        scale = max(1.0, float(np.abs(tr_s[b]).max()))
+        assert np.abs(tr_r[b] - tr_s[b]).max() <= 1e-5 * scale
+        assert abs(F_r[b] - F_s[b]) <= 1e-5 * max(1.0, abs(F_s[b]))
+        assert np.abs(tr9_r[b] - tr9_s[b]).max() <= 1e-5 * max(1.0, float(np.abs(tr9_s[b]).max()))
+    # against the oracle, 9 steps from q^0
+    d = ds[0]
+    s_ref, F_ref = oracle_model(oracle, d).parallel_prox(0.3, 9)
+    assert np.abs(np.exp(s9_r[0]) - np.exp(s_ref)).max() <= TOL_Q
+    assert np.abs(tr9_r[0] - F_ref[:9]).max() <= 1e-5 * max(1.0, float(np.abs(F_ref).max()))

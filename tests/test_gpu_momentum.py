@@ -35,9 +35,10 @@ def model(oracle, d):
     return oracle.Model.grid(f64(d["U"]), f64(d["mu"]), f64(d["w"]), d["H"], d["W"], d["conn"])
 
 
-def run(binding, inst, iters, **kw):
+def run(binding, inst, iters, resident=True, **kw):
     topo = binding.CRF_GRID8 if inst["conn"] == 8 else binding.CRF_GRID4
     with binding.CRF(topo, inst["L"], inst["H"], inst["W"]) as crf:
+        crf.use_resident(resident)
         crf.set_unary(inst["U"])
         crf.set_pairwise(inst["mu"], inst["w"])
         crf.iterate(iters, reset=True, **kw)
@@ -89,7 +90,7 @@ def test_momentum_without_memory_is_the_fixed_step_bitwise(env):
     binding, oracle, torch = env
     d = synth.random_grid(19, 45, 8, 8, seed=9, symmetric=False)
     a = run(binding, d, 20, eta=0.3, rule=binding.MF_RULE_MOMENTUM, gamma1=0.0)
-    b = run(binding, d, 20, eta=0.3)
+    b = run(binding, d, 20, resident=False, eta=0.3)   # the same (step-by-step) kernel
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 

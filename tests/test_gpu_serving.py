@@ -42,6 +42,7 @@ def requests(n, seed=0):
 def solve_alone(binding, d, rel_tol, max_iters):
     topo = binding.CRF_GRID8 if d["conn"] == 8 else binding.CRF_GRID4
     with binding.CRF(topo, d["L"], d["H"], d["W"]) as crf:
+        crf.use_resident(False)   # the serving loop shares the step-by-step kernel's arithmetic
         crf.set_unary(d["U"])
         crf.set_pairwise(d["mu"], d["w"])
         it = crf.iterate(max_iters, eta=d["eta"], rel_tol=rel_tol, want_iters=True)[0]
