@@ -158,22 +158,26 @@ __global__ void __launch_bounds__(NT, 1) grid_resident_kernel(const GridResident
             }
         }
         cluster.sync();   // the new iterate and every CTA's partial are visible cluster-wide
-        if (tid == 0) {
-            df tot = {0.f, 0.f};
-            for (int j = 0; j < nc; ++j) {
-                const float *ph = cluster.map_shared_rank(part_h, j), *pl = cluster.map_shared_rank(part_l, j);
-                tot = df_add(tot, df{ph[t & 1], pl[t & 1]});
+        if (tid < 32) {
+            // lane j reads rank j's partial; a fixed-shape tree sums them
+            df v = {0.f, 0.f};
+            if (tid < nc) {
+                const float *ph = cluster.map_shared_rank(part_h, tid), *pl = cluster.map_shared_rank(part_l, tid);
+                v = df{ph[t & 1], pl[t & 1]};
             }
-            const double F = df_to(tot);
-            const bool stop = a.rel_tol > 0.0 && t > 0 && fabs(F - f_prev) <= a.rel_tol * fabs(F);
-            if (r == 0) {
-                if (t < a.trace_cap) a.f_trace[(size_t)b * a.trace_cap + t] = F;
-                a.f_cur[b] = F;
-                if (!isfinite(F)) atomicExch(a.status, -6);
-                if (stop) a.done[b] = t + 1;
+            v = warp_sum_df(v);
+            if (tid == 0) {
+                const double F = df_to(v);
+                const bool stop = a.rel_tol > 0.0 && t > 0 && fabs(F - f_prev) <= a.rel_tol * fabs(F);
+                if (r == 0) {
+                    if (t < a.trace_cap) a.f_trace[(size_t)b * a.trace_cap + t] = F;
+                    a.f_cur[b] = F;
+                    if (!isfinite(F)) atomicExch(a.status, -6);
+                    if (stop) a.done[b] = t + 1;
+                }
+                stop_flag = stop ? 1 : 0;
+                f_prev = F;
             }
-            stop_flag = stop ? 1 : 0;
-            f_prev = F;
         }
         __syncthreads();
         float *ts = sc, *tq = qc;
