@@ -457,12 +457,10 @@ __device__ void coop_partial(df v, double *red, double *part) {
 
 // (W u)_p of the scalar form: the weighted neighbour sum over the grid's
 // edges at pixel p, compensated, from the FP32 pixel-major weights (read
-// only, through L1).  The vector u comes from global memory (read through L2:
-// it is written inside the launch and L1 is not coherent across blocks) or,
-// with STAGE, from the shared-memory copy of pixels lo.. of the instance.
-template <bool STAGE>
-__device__ __forceinline__ df w_times(const float *__restrict__ wb, const float2 *u, int lo, const LzGeom &g,
-                                      int nd, int p) {
+// only, through L1) and the double-float vector u (read through L2: it is
+// written inside the launch and L1 is not coherent across blocks).
+__device__ __forceinline__ df w_times(const float *__restrict__ wb, const float2 *u, const LzGeom &g, int nd,
+                                      int p) {
     const int y = p / g.W, x = p - y * g.W;
     float ah = 0.f, al = 0.f;
 #pragma unroll
@@ -472,13 +470,13 @@ __device__ __forceinline__ df w_times(const float *__restrict__ wb, const float2
         const int yo = y + dy, xo = x + dx;
         if (yo < g.H && xo >= 0 && xo < g.W) {
             const int q = yo * g.W + xo;
-            const float2 v = STAGE ? u[q - lo] : __ldcg(u + q);
+            const float2 v = __ldcg(u + q);
             acc_prod_f(ah, al, __ldg(wb + (size_t)p * nd + d), df{v.x, v.y});
         }
         const int yi = y - dy, xi = x - dx;
         if (yi >= 0 && xi >= 0 && xi < g.W) {
             const int q = yi * g.W + xi;
-            const float2 v = STAGE ? u[q - lo] : __ldcg(u + q);
+            const float2 v = __ldcg(u + q);
             acc_prod_f(ah, al, __ldg(wb + (size_t)q * nd + d), df{v.x, v.y});
         }
     }
@@ -576,7 +574,7 @@ lz_chunk_strided_kernel(LzState st, const float *__restrict__ w, LzGeom g, LzCoo
         float dh = 0.f, dl = 0.f;
         if (active) {
             for (int p = p0; p < N; p += stride) {
-                const df r = df_mul(w_times<false>(wb, v, 0, g, nd, p), inv);
+                const df r = df_mul(w_times(wb, v, g, nd, p), inv);
                 __stcg(t + p, make_float2(r.h, r.l));
                 const float2 u = __ldcg(v + p);
                 acc_prod(dh, dl, r, df{u.x, u.y});
