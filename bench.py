@@ -55,7 +55,7 @@ def parse():
                    help="skip the fully connected (N=9216, L=21) FP32 / BF16 measurements")
     p.add_argument("--dense-only", action="store_true",
                    help="run only the fully connected measurements (profiling captures)")
-    p.add_argument("--serve-requests", type=int, default=128,
+    p.add_argument("--serve-requests", type=int, default=512,
                    help="requests of the serving measurement (0 skips it)")
     p.add_argument("--serve-only", action="store_true")
     p.add_argument("--no-denoising", action="store_true",
@@ -658,9 +658,9 @@ def serving_requests(n, seed=7):
 
 
 def run_serving(n_req, max_iters=1000, rel_tol=1e-6):
-    """Continuous batching with Poisson arrivals at 0.8x the saturated rate;
-    p50/p99 latency (arrival to result) and throughput, against the same
-    requests solved one at a time."""
+    """Continuous batching with Poisson arrivals at 0.8x (and 0.5x) the
+    saturated rate; p50/p99 latency (arrival to result) and throughput,
+    against the same requests solved one at a time."""
     from paper_1511_06103_gb300 import binding
     reqs = serving_requests(n_req)
     budget = 16 << 30
@@ -698,6 +698,12 @@ def run_serving(n_req, max_iters=1000, rel_tol=1e-6):
     arrivals = np.cumsum(np.random.default_rng(11).exponential(1.0 / rate, size=len(reqs)))
     with binding.Server(budget, max_slots=128) as srv:
         t_run, lat, iters_run = drive(srv, arrivals)
+    # the same requests at half the saturated rate
+    rate_half = 0.5 * len(reqs) / t_sat
+    arrivals_half = np.cumsum(np.random.default_rng(12).exponential(1.0 / rate_half, size=len(reqs)))
+    with binding.Server(budget, max_slots=128) as srv:
+        t_half, lat_half, _ = drive(srv, arrivals_half)
+    ms_half = np.array(sorted(lat_half.values())) * 1000
     upd = sum(r["H"] * r["W"] * r["L"] * iters_run[k] for k, r in enumerate(reqs))
     t1 = time.perf_counter()
     with binding.Server(budget, max_slots=1) as srv:           # one at a time
@@ -710,7 +716,7 @@ def run_serving(n_req, max_iters=1000, rel_tol=1e-6):
     t_one = time.perf_counter() - t1
     ms = np.array(sorted(lat.values())) * 1000
     return {"workload": f"{len(reqs)} grid-CRF requests, square side log-uniform in [64,512] (8 sizes), "
-                        "L in {2,8,21}, Poisson arrivals at 0.8x the saturated rate, retirement at "
+                        "L in {2,8,21}, Poisson arrivals at 0.8x (and 0.5x) the saturated rate, retirement at "
                         "dF/|F| <= 1e-6 or 1000 steps, step size from the degree bound",
             "requests": len(reqs), "arrival_rate_rps": rate, "saturated_s": t_sat, "run_s": t_run,
             "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
@@ -718,6 +724,10 @@ def run_serving(n_req, max_iters=1000, rel_tol=1e-6):
             "throughput_rps": len(reqs) / t_run, "updates_per_s": upd / t_run,
             "saturated_throughput_rps": len(reqs) / t_sat,
             "one_at_a_time": {"s": t_one, "throughput_rps": len(reqs) / t_one, "updates_per_s": upd / t_one},
+            "half_load": {"arrival_rate_rps": rate_half, "run_s": t_half,
+                          "latency_ms": {"p50": float(np.percentile(ms_half, 50)),
+                                         "p99": float(np.percentile(ms_half, 99)), "mean": float(ms_half.mean())},
+                          "throughput_rps": len(reqs) / t_half},
             "mean_iters": float(np.mean(list(iters_run.values())))}
 
 
