@@ -359,13 +359,10 @@ template <int LT, int CONN, bool SYM>
 cudaError_t launch_adj(const AdjointStep &a, cudaStream_t st) {
     using C = AdjCfg<LT>;
     const size_t smem = C::smem_bytes(SYM);
-    static bool attr = false;   // set once per instantiation (first use on this device)
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(adj_step_kernel<LT, CONN, SYM>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // set once per instantiation (thread-safe initialisation of a function-local static)
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(adj_step_kernel<LT, CONN, SYM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
     dim3 grid((a.W + C::TX - 1) / C::TX, (a.H + C::TY - 1) / C::TY, a.B);
     adj_step_kernel<LT, CONN, SYM><<<grid, C::NT, smem, st>>>(a);
     return cudaGetLastError();

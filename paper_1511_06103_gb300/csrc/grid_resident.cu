@@ -193,14 +193,11 @@ __global__ void __launch_bounds__(NT, 1) grid_resident_kernel(const GridResident
 
 template <int LT, int NT>
 cudaError_t launch_resident(const GridResidentLaunch &a, int nc, size_t smem, cudaStream_t st) {
-    static bool attr = false;   // the opt-in above 48 KB, once per process and label tile
-    if (!attr) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(grid_resident_kernel<LT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kResidentMaxSmem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // the opt-in above 48 KB, once per process and label tile (thread-safe
+    // initialisation of a function-local static)
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        grid_resident_kernel<LT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResidentMaxSmem);
+    if (attr != cudaSuccess) return attr;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nc, a.B, 1);
     cfg.blockDim = dim3(NT, 1, 1);

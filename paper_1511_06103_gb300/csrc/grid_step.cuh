@@ -735,13 +735,10 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
 template <int LT, int CONN, bool SYM>
 cudaError_t launch_grid_tc(const GridStepArgs &a, dim3 grid, dim3 block, cudaStream_t st) {
     constexpr int bytes = GridTcSmem<LT, SYM>::bytes;
-    static bool attr = false;   // set once per instantiation
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(grid_prox_step_kernel<LT, CONN, SYM, true>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // set once per instantiation (thread-safe initialisation of a function-local static)
+    static const cudaError_t attr = cudaFuncSetAttribute(grid_prox_step_kernel<LT, CONN, SYM, true>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (attr != cudaSuccess) return attr;
     grid_prox_step_kernel<LT, CONN, SYM, true><<<grid, block, bytes, st>>>(a);
     return cudaGetLastError();
 }
