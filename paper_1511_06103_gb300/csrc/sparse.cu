@@ -24,7 +24,10 @@ namespace {
 
 constexpr int kSW = 8;               // warps per block
 constexpr int kST = kSW * 32;
-constexpr int kVPW = 1;              // variables per warp
+// Variables per warp: more per warp for large graphs (fewer blocks, so fewer
+// FP64 block partials for the last block to sum: FP64 is the narrow pipe of
+// this part), one per warp for small ones (enough warps to fill the SMs).
+__host__ __device__ inline int sparse_vpw(int N) { return N >= 131072 ? 8 : (N >= 8192 ? 4 : 1); }
 
 // sum_e w_e q[col_e][lane] over one adjacency list, four entries in flight
 __device__ __forceinline__ float gather(const int *__restrict__ ptr, const int *__restrict__ col,
@@ -104,11 +107,12 @@ __global__ void __launch_bounds__(kST) sparse_step_kernel(const SparseStepLaunch
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int N = a.N, L = a.L, LP = a.LP;
     const size_t base = (size_t)b * N;
-    const int i0 = (blockIdx.x * kSW + warp) * kVPW;
+    const int vpw = sparse_vpw(N);
+    const int i0 = (blockIdx.x * kSW + warp) * vpw;
 
     if (a.done != nullptr && a.done[b] != 0) {
         // stopping rule met: carry the state through unchanged
-        for (int v = 0; v < kVPW; ++v) {
+        for (int v = 0; v < vpw; ++v) {
             const int i = i0 + v;
             if (a.update && i < N && lane < LP) {
                 const size_t o = (base + i) * LP + lane;
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(kST) sparse_step_kernel(const SparseStepLaunch
     __syncthreads();
     const float eta = a.eta[b];
     float f = 0.f;
-    for (int v = 0; v < kVPW; ++v) {
+    for (int v = 0; v < vpw; ++v) {
         const int i = i0 + v;
         if (i >= N) break;
         const size_t o = (base + i) * LP + lane;
@@ -218,7 +222,7 @@ __global__ void sparse_degree_kernel(const int *ptr, const float *w, int N, unsi
 
 }  // namespace
 
-int sparse_blocks(int N) { return (N + kSW * kVPW - 1) / (kSW * kVPW); }
+int sparse_blocks(int N) { return (N + kSW * sparse_vpw(N) - 1) / (kSW * sparse_vpw(N)); }
 
 cudaError_t launch_sparse_step(const SparseStepLaunch &a, cudaStream_t st) {
     dim3 grid(sparse_blocks(a.N), a.B);

@@ -120,3 +120,29 @@ def test_sparse_batch_and_errors(env):
             crf.set_graph(d["mu"], d["src"], np.full_like(d["dst"], 200), d["w"])
         with pytest.raises(binding.ProxMFError, match="INVALID"):
             crf.set_pairwise(d["mu"], np.zeros((2, 10, 20), np.float32))
+
+
+@pytest.mark.parametrize("N,E,L,sym,rows", [(9000, 36000, 5, False, None), (140000, 560000, 3, True, 3000)])
+def test_sparse_step_several_variables_per_warp(env, N, E, L, sym, rows):
+    """Graphs large enough that a warp takes 4 (N >= 8192) or 8 (N >= 131072)
+    variables in turn: one step against the oracle (all rows, or a sample of
+    rows at the larger size, which also exercises the last block's sum over
+    fewer partials)."""
+    binding, oracle, torch = env
+    d = synth.random_graph(N, E, L, seed=N % 97 + L, symmetric=sym)
+    s0 = synth.random_logq(N, L, seed=L + 1)
+    m = model(oracle, d)
+    with crf_for(binding, d) as crf:
+        crf.set_state(s0)
+        crf.iterate(1, eta=0.35)
+        s = crf.log_marginals()[0].astype(np.float64)
+        F_gpu = crf.free_energy_trace(1)[0][0]
+    if rows is None:
+        s_ref = m.prox_step(0.35, f64(s0))
+        assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= 1e-6
+    else:
+        idx = np.random.default_rng(5).choice(N, size=rows, replace=False)
+        s_ref = m.prox_step_rows(0.35, f64(s0), idx)
+        assert np.abs(np.exp(s[idx]) - np.exp(s_ref)).max() <= 1e-6
+    F_ref = m.free_energy(np.exp(f64(s0)))
+    assert f_close(F_gpu, F_ref, N)
