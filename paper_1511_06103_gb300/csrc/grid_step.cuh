@@ -39,6 +39,7 @@
 #include <cuda_bf16.h>
 
 #include "f32x2.cuh"
+#include "dfloat.cuh"
 #include "internal.h"
 #include "tc_common.cuh"
 
@@ -599,10 +600,10 @@ __device__ __forceinline__ double grid_tile(const TileJob &j, int bx, int by, co
         store_px<LP>(j.s_out + p * LP, o);
     }
 
-    // a5: F partial of this tile, FP64
-    double fd = inside ? (double)(f2.x + f2.y) : 0.0;
-    fd = warp_sum_f64(fd);
-    if ((tid & 31) == 0) red[tid >> 5] = fd;
+    // a5: F partial of this tile: double-float warp trees (FP64 is the narrow
+    // pipe of this part), one FP64 value per warp, the warps in FP64
+    const df fw = warp_sum_df(df{inside ? f2.x + f2.y : 0.f, 0.f});
+    if ((tid & 31) == 0) red[tid >> 5] = df_to(fw);
     if constexpr (TC) tc::fence_before_sync();   // TMEM reads done before the block syncs
     __syncthreads();
     double bs = 0.0;

@@ -16,6 +16,7 @@
 // reduced in a fixed order by the last block of each instance.
 #include <cmath>
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace proxmf {
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(kST) sparse_step_kernel(const SparseStepLaunch
     for (int e = threadIdx.x; e < L * L; e += kST) mus[e] = a.mu[e];
     __syncthreads();
     const float eta = a.eta[b];
-    float f = 0.f;
+    float fh = 0.f, fl = 0.f;   // compensated sum of this lane's F terms
     for (int v = 0; v < vpw; ++v) {
         const int i = i0 + v;
         if (i >= N) break;
@@ -153,7 +154,12 @@ __global__ void __launch_bounds__(kST) sparse_step_kernel(const SparseStepLaunch
         const float s = live ? a.s_in[o] : 0.f;
         const float u = live ? a.U[o] : 0.f;
         const float q = live ? a.q_in[o] : 0.f;
-        f += live ? q * (u + 0.5f * m + s) : 0.f;
+        {
+            float se, ee;
+            two_sum(fh, live ? q * (u + 0.5f * m + s) : 0.f, se, ee);
+            fh = se;
+            fl = __fadd_rn(fl, ee);
+        }
         const float av = live ? fmaf(-eta, u + m, (1.f - eta) * s) : -INFINITY;
         float mx = av;
 #pragma unroll
@@ -168,10 +174,9 @@ __global__ void __launch_bounds__(kST) sparse_step_kernel(const SparseStepLaunch
         }
     }
     // a5: F partial of the block, FP64, fixed order
-    double fd = (double)f;
-#pragma unroll
-    for (int w = 16; w > 0; w >>= 1) fd += __shfl_down_sync(0xffffffffu, fd, w);
-    if (lane == 0) red[warp] = fd;
+    // double-float warp tree (FP64 is the narrow pipe), one FP64 value per warp
+    const df fw = warp_sum_df(df_fast_two_sum(fh, fl));
+    if (lane == 0) red[warp] = df_to(fw);
     __syncthreads();
     if (threadIdx.x == 0) {
         double bs = 0.0;
