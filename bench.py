@@ -236,7 +236,7 @@ def run_reference(args, world, rank):
 
 # dram__bytes_read.sum + dram__bytes_write.sum of grid_prox_step_kernel<21,8,sym>
 # per instance-launch (4-instance capture / 4, see profiles/)
-GRID_TRAFFIC_PER_INSTANCE = (218155008 + 72081152) // 4
+GRID_TRAFFIC_PER_INSTANCE = (218156544 + 71829504) // 4
 
 
 def algorithmic_bytes_per_launch() -> int:
