@@ -9,6 +9,9 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/proxmf.h"
 #include "nvtx_range.h"
 #include "internal.h"
@@ -95,6 +98,43 @@ struct crf_s {
 };
 
 namespace {
+
+// The device address of a host buffer of `bytes` bytes when it lies inside
+// one page-locked, mapped allocation (cudaHostAlloc / cudaHostRegister, e.g. a
+// pinned tensor), else null: pageable memory, or a range that cannot be
+// verified.  The layout kernels then read or write the caller's buffer
+// directly over the CPU-GPU link instead of going through a staging copy;
+// the range check keeps them inside the allocation.
+void *pinned_device_ptr(const void *p, size_t bytes) {
+    if (((uintptr_t)p & 3) != 0) return nullptr;   // the kernels access it as floats
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr) return nullptr;
+    static const PFN_cuPointerGetAttribute_v4000 get_attr = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            (void)cudaGetLastError();
+            fn = nullptr;
+        }
+        return reinterpret_cast<PFN_cuPointerGetAttribute_v4000>(fn);
+    }();
+    if (!get_attr) return nullptr;
+    const CUdeviceptr dp = (CUdeviceptr)(uintptr_t)at.devicePointer;
+    CUdeviceptr start = 0;
+    size_t size = 0;
+    if (get_attr(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, dp) != CUDA_SUCCESS ||
+        get_attr(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, dp) != CUDA_SUCCESS)
+        return nullptr;
+    if (size == 0 || dp < start || dp - start > size || bytes > size - (dp - start)) return nullptr;
+    return at.devicePointer;
+}
+
 
 crf_status fail_cuda(crf_t h, cudaError_t e) {
     if (e == cudaSuccess) return CRF_OK;
@@ -648,8 +688,13 @@ crf_status crf_set_unary(crf_t h, const float *U, int is_device) {
     if (!U) return CRF_E_INVALID;
     const float *src = U;
     if (!is_device) {
-        CK(h, cudaMemcpyAsync(h->staging, U, n_rows(h) * sizeof(float), cudaMemcpyHostToDevice, h->st));
-        src = h->staging;
+        const size_t bytes = n_rows(h) * sizeof(float);
+        if (const void *dp = pinned_device_ptr(U, bytes)) {
+            src = static_cast<const float *>(dp);   // read in place by the layout kernel
+        } else {
+            CK(h, cudaMemcpyAsync(h->staging, U, bytes, cudaMemcpyHostToDevice, h->st));
+            src = h->staging;
+        }
     }
     CK(h, launch_rows_to_padded(src, h->U, (long long)n_pix(h), h->L, h->LP, 0.f, h->st));
     CK(h, launch_init_logq(h->U, h->s[0], (long long)n_pix(h), h->L, h->LP, h->st));
@@ -1087,13 +1132,19 @@ static crf_status export_state(crf_t h, float *dst, int is_device, int mode) {
     crf_status rc = check_handle(h);
     if (rc != CRF_OK) return rc;
     if (!dst) return CRF_E_INVALID;
-    float *out = is_device ? dst : h->staging;
+    const size_t bytes = n_rows(h) * sizeof(float);
+    float *out = dst;
+    bool staged = false;
+    if (!is_device) {
+        // pinned host memory is written in place by the layout kernel
+        out = static_cast<float *>(pinned_device_ptr(dst, bytes));
+        staged = out == nullptr;
+        if (staged) out = h->staging;
+    }
     CK(h, launch_padded_to_rows(h->s[h->cur], out, (long long)n_pix(h), h->L, h->LP, mode, h->st));
     h->launches++;
-    if (!is_device) {
-        CK(h, cudaMemcpyAsync(dst, h->staging, n_rows(h) * sizeof(float), cudaMemcpyDeviceToHost, h->st));
-        CK(h, cudaStreamSynchronize(h->st));
-    }
+    if (staged) CK(h, cudaMemcpyAsync(dst, h->staging, bytes, cudaMemcpyDeviceToHost, h->st));
+    if (!is_device) CK(h, cudaStreamSynchronize(h->st));
     return CRF_OK;
 }
 
