@@ -25,6 +25,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -128,11 +129,11 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="proxmf_clocks_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={CLOCK_QUERY}", "--format=csv,noheader,nounits",
@@ -184,13 +185,19 @@ class ClockSampler:
 
 # -- oracle baselines ----------------------------------------------------------
 
-def oracle_solve_rate(side: int, iters: int, seed: int = SEED) -> tuple[float, float, dict]:
-    """Time the FP64 oracle on a side x side instance of the same recipe."""
+def oracle_model(side: int, seed: int = SEED):
+    """The FP64 oracle's model of a side x side instance of the timed recipe."""
     import oracle
     from paper_1511_06103_gb300 import synth
     d = synth.segmentation_grid(H=side, W=side, L=L, conn=CONN, seed=seed)
-    m = oracle.Model.grid(d["U"].astype(np.float64), d["mu"].astype(np.float64),
-                          d["w"].astype(np.float64), side, side, CONN)
+    return oracle.Model.grid(d["U"].astype(np.float64), d["mu"].astype(np.float64),
+                             d["w"].astype(np.float64), side, side, CONN)
+
+
+def oracle_solve_rate(side: int, iters: int, seed: int = SEED, model=None) -> tuple[float, float, dict]:
+    """Time the FP64 oracle's parallel proximal solve (q^0, iters steps, F at
+    every step) on a side x side instance of the same recipe."""
+    m = oracle_model(side, seed) if model is None else model
     eta = 0.04
     t0 = time.perf_counter()
     m.parallel_prox(eta, iters)
@@ -200,31 +207,35 @@ def oracle_solve_rate(side: int, iters: int, seed: int = SEED) -> tuple[float, f
 
 
 def run_reference(args, world, rank):
+    """The oracle timed as it stands on the host cores, on the benchmark's own
+    workload: every step is one full 512 x 512 solve of 100 iterations (about
+    8.5 s on 16 cores)."""
     if rank != 0:
         return
     import oracle
     oracle.build()
-    side, iters = 64, ITERS
+    side, iters = H, ITERS
+    m = oracle_model(side)
     for _ in range(args.warmup):
-        oracle_solve_rate(side, iters)
+        oracle_solve_rate(side, iters, model=m)
     times = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        _, dt, _ = oracle_solve_rate(side, iters)
+        _, dt, _ = oracle_solve_rate(side, iters, model=m)
         times.append(dt)
     wall = time.perf_counter() - t0
     units = side * side * L * iters * args.steps
     value = units / sum(times)
     cores = oracle.num_threads()
-    sample = (f"{side}x{side} crop of the same recipe (L=21, 8-connected), {iters} iterations per step, "
-              "F evaluated every iteration")
+    sample = (f"the full workload: one {side}x{side} instance of the same recipe (L=21, 8-connected, seed {SEED}) "
+              f"per step, {iters} iterations, F evaluated every iteration")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle (plain C, OpenMP)",
-                   "sample": sample},
+        "config": {"workload": WORKLOAD, "H": H, "W": W, "L": L, "conn": CONN, "iters": ITERS,
+                   "reference": "FP64 CPU oracle (plain C, OpenMP)", "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
@@ -234,9 +245,29 @@ def run_reference(args, world, rank):
 
 # -- our arm -------------------------------------------------------------------
 
-# dram__bytes_read.sum + dram__bytes_write.sum of grid_prox_step_kernel<21,8,sym>
-# per instance-launch (4-instance capture / 4, see profiles/)
-GRID_TRAFFIC_PER_INSTANCE = (218156544 + 71829504) // 4
+# dram__bytes_read.sum + dram__bytes_write.sum of the headline step kernel per
+# instance-launch, from the ncu capture summarised in the named profile (4
+# instances per launch, larger than L2, divided by 4), with the SHA-256 of the
+# kernel source the counters were taken on.  Once that source changes the
+# line reports traffic null (the counters no longer describe the kernel).
+GRID_TRAFFIC = {"per_instance": (218156544 + 71829504) // 4,
+                "source": "paper_1511_06103_gb300/csrc/grid_step.cuh",
+                "sha256": "",
+                "profile": "profiles/grid_prox_step_seg512_L21_conn8.md"}
+
+
+def grid_traffic(batch: int):
+    """(traffic per launch or None, note) for the roofline object."""
+    import hashlib
+    path = os.path.join(ROOT, GRID_TRAFFIC["source"])
+    with open(path, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    if sha != GRID_TRAFFIC["sha256"]:
+        return None, (f"null: {GRID_TRAFFIC['source']} changed since the ncu capture of "
+                      f"{GRID_TRAFFIC['profile']}")
+    return batch * GRID_TRAFFIC["per_instance"], (
+        f"dram read+write of one launch per instance from the ncu capture in {GRID_TRAFFIC['profile']} "
+        "(4 instances per launch, larger than L2, divided by 4); kernel source unchanged since (SHA-256)")
 
 
 def algorithmic_bytes_per_launch() -> int:
@@ -951,6 +982,7 @@ def run_ours(args, world, rank, local):
     serving = None
     if args.serve_requests > 0 and world == 1:
         serving = run_serving(args.serve_requests)
+    traffic, traffic_note = grid_traffic(B)
     if rank == 0:
         srt = sorted(step_ms)
         line = {
@@ -964,9 +996,7 @@ def run_ours(args, world, rank, local):
                              "set stays L2-resident across its 100 iterations"},
             "latency_ms": {"p50": float(np.percentile(srt, 50)), "p99": float(np.percentile(srt, 99))},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": B * GRID_TRAFFIC_PER_INSTANCE,
-                         "traffic_note": "dram read+write of one launch per instance, from a 4-instance "
-                                         "ncu capture (larger than L2) divided by 4",
+                         "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
                          "kernel": "grid_prox_step_kernel<21,8,sym>",
                          "bytes_per_launch": bytes_launch, "avg_launch_ms": kern_ms,
                          "peak_kind": peak_kind},

@@ -299,7 +299,8 @@ crf_status mf_unrolled_backward(crf_t h, int32_t K, double eta, const float *ckp
  *              image must be 0.
  *   mu         [L][L] float32, HOST memory.
  *   eta        step in (0, 1].
- *   F_out      device double: receives F(q_in); NaN if it is not finite.
+ *   F_out      device double: receives F(q_in); NaN when the step reports
+ *              an error or F is not finite (inf or NaN).
  *   stream     cudaStream_t (NULL = legacy default stream).
  * Allocates nothing: its scratch (tile partials, counter, status, step, mu
  * table) is a 512 KiB static device array, held on every GPU that loads the
@@ -307,7 +308,10 @@ crf_status mf_unrolled_backward(crf_t h, int32_t K, double eta, const float *ckp
  * (CRF_E_INVALID beyond).  The first call on a device looks up that array's address (make it
  * before any stream capture).  All calls share the array: calls that overlap
  * on the GPU race and must be serialised by the caller.  logq_in and logq_out
- * must not alias.  Asynchronous; errors of the launch are CRF_E_CUDA. */
+ * must not alias.  mu is read before the call returns (it travels to the
+ * device as kernel parameters; no host buffer is copied asynchronously).
+ * Asynchronous: three kernel launches on the stream (set-up, step, finish);
+ * errors of the launches are CRF_E_CUDA. */
 crf_status mf_grid_step_noalloc(int32_t topology, int32_t n_labels, int64_t height,
                                 int64_t width, const float *U, const float *w,
                                 const float *mu, const float *logq_in, float *logq_out,

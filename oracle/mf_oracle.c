@@ -282,11 +282,68 @@ static void pair_grad_var(const orc_model *m, const double *v, int64_t i, double
     }
 }
 
+/* Dense models: the vectors mu v_j (P) and mu^T v_j (PT) of every variable,
+ * each entry summed over k in ascending order exactly as pair_grad_var sums
+ * it.  A dense model pairs every variable with all others, so these vectors
+ * are formed once per call instead of once per pair; the terms and their
+ * order are those of pair_grad_var, so the results are the same bit for bit. */
+static void dense_mu_vectors(const orc_model *m, const double *v, double *P, double *PT)
+{
+    const int L = m->L;
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < m->n; ++j) {
+        const double *vj = v + j * L;
+        for (int l = 0; l < L; ++l) {
+            double r = 0.0, rt = 0.0;
+            for (int k = 0; k < L; ++k) {
+                r += m->mu[l * L + k] * vj[k];
+                rt += vj[k] * m->mu[k * L + l];
+            }
+            P[j * L + l] = r;
+            PT[j * L + l] = rt;
+        }
+    }
+}
+
+/* pair_grad_var of a dense model from the vectors of dense_mu_vectors:
+ * out_l = sum_{j>i} K_ij (mu v_j)_l + sum_{j<i} K_ij (mu^T v_j)_l, over j in
+ * ascending order. */
+static void dense_pair_grad_var(const orc_model *m, const double *P, const double *PT, int64_t i, double *out)
+{
+    const int L = m->L;
+    const int64_t n = m->n;
+    for (int l = 0; l < L; ++l) out[l] = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        const double kij = m->K[i * n + j];
+        const double *pj = (j > i ? P : PT) + j * L;
+        for (int l = 0; l < L; ++l) out[l] += kij * pj[l];
+    }
+}
+
+/* The pairwise gradient of every variable: pair_grad_var for each i (dense
+ * models through the per-variable vectors above). */
+static void pair_grad_all(const orc_model *m, const double *v, double *out)
+{
+    if (m->K) {
+        const size_t nl = (size_t)(m->n * m->L);
+        double *P = (double *)malloc(sizeof(double) * nl);
+        double *PT = (double *)malloc(sizeof(double) * nl);
+        dense_mu_vectors(m, v, P, PT);
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < m->n; ++i) dense_pair_grad_var(m, P, PT, i, out + i * m->L);
+        free(P);
+        free(PT);
+        return;
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m->n; ++i) pair_grad_var(m, v, i, out + i * m->L);
+}
+
 /* Hessian-vector product H v (no unary term). */
 void orc_hess_vec(const orc_model *m, const double *v, double *out)
 {
-#pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < m->n; ++i) pair_grad_var(m, v, i, out + i * m->L);
+    pair_grad_all(m, v, out);
 }
 
 /* g = grad E(q): g_il = U_il + (H q)_il.  By multilinearity this equals the
@@ -295,11 +352,9 @@ void orc_hess_vec(const orc_model *m, const double *v, double *out)
 void orc_grad(const orc_model *m, const double *q, double *g)
 {
     const int L = m->L;
-#pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < m->n; ++i) {
-        pair_grad_var(m, q, i, g + i * L);
+    pair_grad_all(m, q, g);
+    for (int64_t i = 0; i < m->n; ++i)
         for (int l = 0; l < L; ++l) g[i * L + l] += m->U[i * L + l];
-    }
 }
 
 /* E(q) = E_Q[E(x)] = sum_i q_i.U_i + sum_{pairs i->j} w_ij q_i^T mu q_j. */
@@ -308,13 +363,24 @@ double orc_energy(const orc_model *m, const double *q)
     const int L = m->L;
     const int64_t n = m->n;
     double *term = (double *)xcalloc((size_t)n, sizeof(double));
+    /* dense: mu q_j once per variable; q_i^T (mu q_j) then sums exactly as
+     * bilinear() does */
+    double *P = NULL, *PT = NULL;
+    if (m->K) {
+        P = (double *)malloc(sizeof(double) * (size_t)(n * L));
+        PT = (double *)malloc(sizeof(double) * (size_t)(n * L));
+        dense_mu_vectors(m, q, P, PT);
+    }
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         double t = 0.0;
         for (int l = 0; l < L; ++l) t += q[i * L + l] * m->U[i * L + l];
         if (m->K) {
-            for (int64_t j = i + 1; j < n; ++j)
-                t += m->K[i * n + j] * bilinear(q + i * L, m->mu, q + j * L, L);
+            for (int64_t j = i + 1; j < n; ++j) {
+                double b = 0.0;
+                for (int l = 0; l < L; ++l) b += q[i * L + l] * P[j * L + l];
+                t += m->K[i * n + j] * b;
+            }
         } else {
             for (int64_t p = m->out_ptr[i]; p < m->out_ptr[i + 1]; ++p) {
                 int64_t e = m->out_e[p];
@@ -326,6 +392,8 @@ double orc_energy(const orc_model *m, const double *q)
     double E = 0.0;
     for (int64_t i = 0; i < n; ++i) E += term[i];
     free(term);
+    free(P);
+    free(PT);
     return E;
 }
 

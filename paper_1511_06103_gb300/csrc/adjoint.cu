@@ -359,9 +359,8 @@ template <int LT, int CONN, bool SYM>
 cudaError_t launch_adj(const AdjointStep &a, cudaStream_t st) {
     using C = AdjCfg<LT>;
     const size_t smem = C::smem_bytes(SYM);
-    // set once per instantiation (thread-safe initialisation of a function-local static)
-    static const cudaError_t attr =
-        cudaFuncSetAttribute(adj_step_kernel<LT, CONN, SYM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static SmemOptIn optin;   // once per device
+    const cudaError_t attr = smem_optin(optin, adj_step_kernel<LT, CONN, SYM>, smem);
     if (attr != cudaSuccess) return attr;
     dim3 grid((a.W + C::TX - 1) / C::TX, (a.H + C::TY - 1) / C::TY, a.B);
     adj_step_kernel<LT, CONN, SYM><<<grid, C::NT, smem, st>>>(a);

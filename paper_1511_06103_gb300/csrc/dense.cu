@@ -374,10 +374,8 @@ namespace {
 template <int LP>
 cudaError_t launch_f32(dim3 grid, const DenseStepArgs &a, cudaStream_t st) {
     constexpr size_t smem = dense_f32_dyn_smem<LP>();
-    // the opt-in above 48 KB, once per process and label count (thread-safe
-    // initialisation of a function-local static)
-    static const cudaError_t attr = cudaFuncSetAttribute(dense_step_f32_kernel<LP>,
-                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static SmemOptIn optin;   // the opt-in above 48 KB, once per device
+    const cudaError_t attr = smem_optin(optin, dense_step_f32_kernel<LP>, smem);
     if (attr != cudaSuccess) return attr;
     dense_step_f32_kernel<LP><<<grid, kDT, smem, st>>>(a);
     return cudaSuccess;

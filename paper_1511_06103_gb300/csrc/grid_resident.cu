@@ -193,10 +193,8 @@ __global__ void __launch_bounds__(NT, 1) grid_resident_kernel(const GridResident
 
 template <int LT, int NT>
 cudaError_t launch_resident(const GridResidentLaunch &a, int nc, size_t smem, cudaStream_t st) {
-    // the opt-in above 48 KB, once per process and label tile (thread-safe
-    // initialisation of a function-local static)
-    static const cudaError_t attr = cudaFuncSetAttribute(
-        grid_resident_kernel<LT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResidentMaxSmem);
+    static SmemOptIn optin;   // the opt-in above 48 KB, once per device
+    const cudaError_t attr = smem_optin(optin, grid_resident_kernel<LT, NT>, kResidentMaxSmem);
     if (attr != cudaSuccess) return attr;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nc, a.B, 1);

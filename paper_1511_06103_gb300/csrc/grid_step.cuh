@@ -736,9 +736,8 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
 template <int LT, int CONN, bool SYM>
 cudaError_t launch_grid_tc(const GridStepArgs &a, dim3 grid, dim3 block, cudaStream_t st) {
     constexpr int bytes = GridTcSmem<LT, SYM>::bytes;
-    // set once per instantiation (thread-safe initialisation of a function-local static)
-    static const cudaError_t attr = cudaFuncSetAttribute(grid_prox_step_kernel<LT, CONN, SYM, true>,
-                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    static SmemOptIn optin;   // once per device
+    const cudaError_t attr = smem_optin(optin, grid_prox_step_kernel<LT, CONN, SYM, true>, bytes);
     if (attr != cudaSuccess) return attr;
     grid_prox_step_kernel<LT, CONN, SYM, true><<<grid, block, bytes, st>>>(a);
     return cudaGetLastError();

@@ -2,6 +2,7 @@
 // Not part of the public ABI (include/proxmf.h is).
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_bf16.h>
@@ -100,6 +101,25 @@ struct GridStepLaunch {
     double rel_tol;
     bool mu_sym;
 };
+
+// Opt-in of one kernel to more than 48 KB of dynamic shared memory.  The
+// attribute belongs to the device that is current when it is set, so each
+// call site keeps one bit per device (devices 0..63; others set it on every
+// launch) and sets it the first time it launches on that device.
+struct SmemOptIn {
+    std::atomic<unsigned long long> devices{0ull};
+};
+template <typename Kernel>
+inline cudaError_t smem_optin(SmemOptIn &o, Kernel k, size_t bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? 1ull << dev : 0ull;
+    if (bit != 0ull && (o.devices.load(std::memory_order_acquire) & bit) != 0ull) return cudaSuccess;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && bit != 0ull) o.devices.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 
 // Number of tiles per instance.
 inline void grid_tiles(int H, int W, int *nbx, int *nby) {

@@ -18,6 +18,12 @@
 // that first call before any stream capture.  Every call shares the array:
 // calls that overlap on the GPU (different streams, different threads) race
 // on it and must be serialised by the caller.
+//
+// A call is three kernel launches on the caller's stream and nothing else:
+// a set-up kernel that receives the mu pair table and the step size by value
+// (kernel parameters, so no host buffer has to outlive the call) and clears
+// the counter and status word; the grid step; and a finishing kernel that
+// turns F_out into NaN when the step reported an error or F is not finite.
 #include <cmath>
 #include <mutex>
 
@@ -53,6 +59,29 @@ cudaError_t scratch_address(void **out) {
     }
     *out = g_scratch_addr[dev];
     return cudaSuccess;
+}
+
+// Everything the set-up kernel writes, carried in its parameters (8 KiB of
+// pairs plus the step; kernel parameters may take up to 32 KiB).
+struct NoallocSetup {
+    float2 pairs[2 * proxmf::kMaxLabels * 16];
+    int npairs;
+    float eta;
+};
+
+__global__ void noalloc_setup_kernel(const __grid_constant__ NoallocSetup p, float2 *mu_dev, float *eta_dev,
+                                     unsigned *counter, int *status) {
+    for (int i = threadIdx.x; i < p.npairs; i += blockDim.x) mu_dev[i] = p.pairs[i];
+    if (threadIdx.x == 0) {
+        *eta_dev = p.eta;
+        *counter = 0u;
+        *status = 0;
+    }
+}
+
+// The step records a non-finite F as status -6; the caller sees it as NaN.
+__global__ void noalloc_finish_kernel(const int *status, double *F_out) {
+    if (*status != 0 || !isfinite(*F_out)) *F_out = __longlong_as_double(0x7ff8000000000000ll);
 }
 
 }  // namespace
@@ -91,24 +120,17 @@ extern "C" crf_status mf_grid_step_noalloc(int32_t topology, int32_t n_labels, i
     float2 *mu_dev = (float2 *)((unsigned char *)base + kScratchBytes - kPairBytes);
     cudaStream_t st = (cudaStream_t)stream;
 
-    // mu as the step kernel's column / row pairs (see mu_pair_slots), built on
-    // the stack and copied into the scratch array
-    const int L = n_labels, LT = kernel_labels(L), NPP = mu_pair_slots(LT);
-    float2 pairs[2 * kMaxLabels * 16];
-    static_assert(sizeof(pairs) <= kPairBytes, "pair table fits its scratch slot");
-    auto at = [&](int r, int c) { return (r < L && c < L) ? mu[r * L + c] : 0.f; };
-    for (int k = 0; k < LT; ++k)
-        for (int j = 0; j < NPP; ++j) {
-            pairs[k * NPP + j] = make_float2(at(2 * j, k), at(2 * j + 1, k));
-            pairs[(LT + k) * NPP + j] = make_float2(at(k, 2 * j), at(k, 2 * j + 1));
-        }
-
-    // the counter and status word must start at zero; everything else is
-    // written before it is read
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned) + sizeof(int), st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(mu_dev, pairs, (size_t)2 * LT * NPP * sizeof(float2), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_fill_eta(eta_dev, 1, eta, st);
+    // mu as the step kernel's column / row pairs (see mu_pair_slots), passed
+    // by value to the set-up kernel, which writes them into the scratch array
+    const int LT = kernel_labels(n_labels), NPP = mu_pair_slots(LT);
+    NoallocSetup setup;
+    static_assert(sizeof(setup.pairs) <= kPairBytes, "pair table fits its scratch slot");
+    build_mu_pairs_host(mu, n_labels, LT, setup.pairs);
+    setup.npairs = 2 * LT * NPP;
+    setup.eta = (float)eta;
+    const float2 *pairs = setup.pairs;
+    noalloc_setup_kernel<<<1, 256, 0, st>>>(setup, mu_dev, eta_dev, counter, status);
+    cudaError_t e = cudaGetLastError();
     GridStepLaunch a{};
     a.s_in = logq_in;
     a.s_out = logq_out;
@@ -117,7 +139,7 @@ extern "C" crf_status mf_grid_step_noalloc(int32_t topology, int32_t n_labels, i
     a.eta = eta_dev;
     a.mu_out = mu_dev;
     a.mu_in = mu_dev + (size_t)LT * NPP;
-    a.mu_host = pairs;
+    a.mu_host = pairs;   // read while the step is launched (symmetric mu in its parameters)
     a.partial = partial;
     a.counter = counter;
     a.f_trace = F_out;   // never written: trace_cap = 0
@@ -135,6 +157,10 @@ extern "C" crf_status mf_grid_step_noalloc(int32_t topology, int32_t n_labels, i
     a.rel_tol = 0.0;
     a.mu_sym = sym;
     if (e == cudaSuccess) e = launch_grid_step(a, st);
+    if (e == cudaSuccess) {
+        noalloc_finish_kernel<<<1, 1, 0, st>>>(status, F_out);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return CRF_E_CUDA;

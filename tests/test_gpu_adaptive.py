@@ -1,11 +1,12 @@
 """GPU parity of the adaptive binary step (Sec. 3.3, Eq. hessian):
 eta_i = 1/(1 + d q_i0 q_i1) per variable, taken from q^t.  FP32 tolerances
 as for the fixed step: single step |dq|max <= 1e-6, trajectories 1e-5 and
-|dF| <= 1e-6 max(|F|, N)."""
+|dF| <= 1e-6 |F| (tests.helpers.f_close)."""
 import numpy as np
 import pytest
 
 from paper_1511_06103_gb300 import synth
+from tests import helpers as H
 
 pytestmark = pytest.mark.gpu
 
@@ -29,7 +30,7 @@ def f64(a):
 
 def f_close(F, F_ref, n):
     F, F_ref = f64(F), f64(F_ref)
-    return bool(np.all(np.abs(F - F_ref) <= 1e-6 * np.maximum(np.abs(F_ref), n)))
+    return H.f_close(F, F_ref, n)
 
 
 def model(oracle, d):

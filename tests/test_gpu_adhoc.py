@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 from paper_1511_06103_gb300 import synth
+from tests import helpers as H
 
 pytestmark = pytest.mark.gpu
 
@@ -41,4 +42,4 @@ def test_adhoc_trajectory(env, Hh, Ww, L, conn, sym, eta):
     m = oracle.Model.grid(f64(d["U"]), f64(d["mu"]), f64(d["w"]), Hh, Ww, conn)
     s_ref, F_ref = m.parallel_adhoc(eta, T)
     assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= 1e-5
-    assert np.all(np.abs(trace - F_ref[:-1]) <= 1e-6 * np.maximum(np.abs(F_ref[:-1]), Hh * Ww))
+    assert H.f_close(trace, F_ref[:-1], Hh * Ww)

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from paper_1511_06103_gb300 import synth
+from tests import helpers as H
 
 pytestmark = pytest.mark.gpu
 
@@ -15,9 +16,8 @@ TOL_F = 1e-6
 
 
 def f_close(F, F_ref, n_vars):
-    """|dF| <= 1e-6 max(|F|, N): see the grid tests for the floor."""
-    F, F_ref = np.asarray(F, np.float64), np.asarray(F_ref, np.float64)
-    return bool(np.all(np.abs(F - F_ref) <= TOL_F * np.maximum(np.abs(F_ref), n_vars)))
+    """|dF| <= 1e-6 |F| (see tests.helpers.f_close for cancelling instances)."""
+    return H.f_close(F, F_ref, n_vars, TOL_F)
 
 
 @pytest.fixture(scope="module")
@@ -192,7 +192,7 @@ def test_dense_bf16_trajectory_refined(env):
     s_ref, F_ref = m.parallel_prox(0.2, 35)
     s, F, trace = gpu_run_bf16(binding, torch, d, 0.2, 30, refine=5)
     assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q_BF16
-    assert abs(F - F_ref[-1]) <= TOL_F_BF16 * max(abs(F_ref[-1]), d["N"])
+    assert H.f_close(F, F_ref[-1], d["N"], TOL_F_BF16)
 
 
 def test_dense_bf16_full_size_sampled(env):
@@ -229,4 +229,4 @@ def test_dense_mid_size_trajectories(env):
     assert f_close(F, F_ref[-1], d["N"])
     s, F, _ = gpu_run_bf16(binding, torch, d, eta, 28, refine=2)
     assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q_BF16
-    assert abs(F - F_ref[-1]) <= TOL_F_BF16 * max(abs(F_ref[-1]), d["N"])
+    assert H.f_close(F, F_ref[-1], d["N"], TOL_F_BF16)

@@ -19,13 +19,8 @@ TOL_F = 1e-6
 
 
 def f_close(F, F_ref, n_vars):
-    """|dF| <= 1e-6 |F|, with |F| floored at one nat per variable: F is a sum
-    of n_vars per-variable terms of order one that can cancel to near zero
-    (with unaries -log softmax(logits) the unary-only free energy is exactly
-    0), where a purely relative test would ask for more than FP32 messages
-    carry."""
-    F, F_ref = np.asarray(F, np.float64), np.asarray(F_ref, np.float64)
-    return bool(np.all(np.abs(F - F_ref) <= TOL_F * np.maximum(np.abs(F_ref), n_vars)))
+    """|dF| <= 1e-6 |F| (see tests.helpers.f_close for cancelling instances)."""
+    return H.f_close(F, F_ref, n_vars, TOL_F)
 
 
 @pytest.fixture(scope="module")

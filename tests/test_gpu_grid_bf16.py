@@ -8,12 +8,13 @@ FP32 accumulation; everything else stays FP32.  Three kinds of checks:
     (catches any layout, transposition or padding error of the operands);
   - rounding: a general single step within |dq|max <= 1e-2;
   - trajectories after FP32 refinement: |dq|max <= 1e-2, |dF| <= 1e-3 |F|
-    (|F| floored at one nat per variable, as for the FP32 form).
+    (tests.helpers.f_close).
 """
 import numpy as np
 import pytest
 
 from paper_1511_06103_gb300 import synth
+from tests import helpers as H
 
 pytestmark = pytest.mark.gpu
 
@@ -110,7 +111,7 @@ def test_bf16_trajectory_refined(env, conn, sym):
     s_ref, F_ref = oracle_model(oracle, d).parallel_prox(eta, 100)
     s, F = run(binding, torch, d, eta, 98, binding.CRF_BF16, refine=2)
     assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q_BF16
-    assert abs(F - F_ref[-1]) <= TOL_F_BF16 * max(abs(F_ref[-1]), 40 * 37)
+    assert H.f_close(F, F_ref[-1], 40 * 37, TOL_F_BF16)
 
 
 def test_bf16_segmentation_full_size(env):
@@ -127,7 +128,7 @@ def test_bf16_segmentation_full_size(env):
     s16b, F16b = run(binding, torch, d, eta, 98, binding.CRF_BF16, refine=2)
     assert np.array_equal(s16, s16b) and F16 == F16b
     assert np.abs(np.exp(s16) - np.exp(s32)).max() <= TOL_Q_BF16
-    assert abs(F16 - F32) <= TOL_F_BF16 * max(abs(F32), 512 * 512)
+    assert H.f_close(F16, F32, 512 * 512, TOL_F_BF16)
     # sampled pixels of the first step against the oracle
     m = oracle_model(oracle, d)
     s0 = m.init_logq()

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from paper_1511_06103_gb300 import synth
+from tests import helpers as H
 
 pytestmark = pytest.mark.gpu
 
@@ -111,7 +112,7 @@ def test_server_against_oracle(env):
                           np.asarray(d["w"], np.float64), 20, 27, 8)
     s_ref, F_ref = m.parallel_prox(0.1, 40)
     assert np.abs(q - np.exp(s_ref)).max() <= 1e-5
-    assert abs(F - F_ref[-2]) <= 1e-6 * max(abs(F_ref[-2]), 540)
+    assert H.f_close(F, F_ref[-2], 540)
 
 
 def test_step_bound_is_an_upper_bound(env):

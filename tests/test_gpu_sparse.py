@@ -1,10 +1,11 @@
 """GPU parity of general pairwise graphs (edge lists, CRF_SPARSE) against the
 FP64 oracle's edge-list model, FP32 tolerances: single step |dq| <= 1e-6,
-trajectories |dq| <= 1e-5 and |dF| <= 1e-6 max(|F|, N)."""
+trajectories |dq| <= 1e-5 and |dF| <= 1e-6 |F| (tests.helpers.f_close)."""
 import numpy as np
 import pytest
 
 from paper_1511_06103_gb300 import synth
+from tests import helpers as H
 
 pytestmark = pytest.mark.gpu
 
@@ -28,7 +29,7 @@ def f64(a):
 
 def f_close(F, F_ref, n):
     F, F_ref = f64(F), f64(F_ref)
-    return bool(np.all(np.abs(F - F_ref) <= 1e-6 * np.maximum(np.abs(F_ref), n)))
+    return H.f_close(F, F_ref, n)
 
 
 def model(oracle, d):

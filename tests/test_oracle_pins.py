@@ -145,6 +145,24 @@ def test_grid_edge_geometry(oracle_mod):
 
 # ---------------------------------------------------------------- P3 ----
 
+def test_initial_state_is_the_unary_only_marginal(oracle_mod):
+    """q^0 = softmax(-U) (reading of the unstated start): on a decoupled model
+    (w = 0) this is the exact marginal, which enumeration fixes; the start
+    does not depend on mu or w; and on one variable with costs (0, ln 2, ln 4)
+    the probabilities are (4, 2, 1)/7 by hand (softmax(+U) would give
+    (1, 2, 4)/7)."""
+    d = synth.random_grid(3, 3, 3, 8, seed=41, symmetric=False)
+    U = _f64(d, "U")
+    m0 = oracle_mod.Model.grid(U, _f64(d, "mu"), np.zeros((4, 3, 3)), 3, 3, 8)
+    _, marg = m0.brute_force()
+    assert np.max(np.abs(np.exp(m0.init_logq()) - marg)) <= 1e-14
+    m1 = oracle_mod.Model.grid(U, _f64(d, "mu"), _f64(d, "w"), 3, 3, 8)
+    assert np.array_equal(m1.init_logq(), m0.init_logq())
+    one = oracle_mod.Model.sparse(np.array([[0.0, math.log(2.0), math.log(4.0)]]), np.zeros((3, 3)),
+                                  np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0))
+    assert np.allclose(np.exp(one.init_logq()[0]), [4 / 7, 2 / 7, 1 / 7], rtol=0, atol=1e-15)
+
+
 def test_decoupled_one_full_step_gives_exact_marginals(oracle_mod):
     """w = 0: one undamped step lands on softmax(-U), the exact marginals."""
     d = synth.random_grid(3, 3, 3, 4, seed=51)
@@ -251,6 +269,13 @@ def test_step_constant_binary_denoising_golden(oracle_mod):
     """The 64x64 binary denoising model: Lanczos on the tangent Hessian matches
     the closed form stored in tests/golden (Sec. 3.2, Sec. 4.3)."""
     g = H.read_golden("step_size_closed_form.txt")
+    # the stored constant is the closed form (the file's generator is
+    # tests/golden/make_step_size_closed_form.py): recompute it here
+    c = float(np.float32(0.8))
+    lam_cf = c * H.grid4_lambda_max(64, 64)
+    assert g["coupling"] == float(f"{c:.15g}")
+    assert math.isclose(g["Lambda"], lam_cf, rel_tol=1e-15)
+    assert math.isclose(g["eta"], 1.0 / (1.0 + lam_cf), rel_tol=1e-15)
     d = synth.binary_denoising()
     m = oracle_mod.Model.grid(_f64(d, "U"), _f64(d, "mu"), _f64(d, "w"), 64, 64, 4)
     lo, hi, k = m.lanczos(260, synth.lanczos_start(64 * 64, 2))
@@ -493,6 +518,61 @@ def test_adam_special_cases(oracle_mod):
     s1, _ = m.parallel_prox_adam(d0, 0.0, 1.0, 1e-8, 15)
     s2, _ = m.parallel_prox(1.0 / (d0 + 1e-8), 15)
     assert np.max(np.abs(s1 - s2)) <= 1e-12
+
+
+def _adam_binary_decoupled(U, s0, d0, gamma2, eps, T, centred=True, sign=1.0):
+    """Per-label Adam on a decoupled binary model, written without the
+    scalar reduction (used only to show what the pin below rejects)."""
+    s = s0.copy()
+    v = np.ones_like(s)
+    for _ in range(T):
+        t = U + sign * s
+        r = t - t.mean(axis=1, keepdims=True) if centred else t
+        v = gamma2 * v + (1 - gamma2) * r * r
+        eta = 1.0 / (1.0 + np.maximum(np.sqrt(v) * d0 + eps - 1.0, 0.0))
+        a = -eta * U + (1 - eta) * s
+        s = a - a.max(axis=1, keepdims=True)
+        s = s - np.log(np.exp(s).sum(axis=1, keepdims=True))
+    return s
+
+
+def test_adam_decoupled_binary_recursion(oracle_mod):
+    """OURS-ADAM (Sec. 3.5, Eq. adamStepSize) on a binary model without edges.
+
+    Derivation.  With w = 0 the gradient is U at every step, so the momentum
+    average stays U (it starts at the first gradient).  Write
+    delta = (U_0 + s_0) - (U_1 + s_1).  The centred natural gradient is
+    r = (U + s) - mean_l(U + s) = (+delta/2, -delta/2): both labels see the
+    same r^2 = delta^2/4, hence the same v and the same eta_t, with
+        v_{t+1} = gamma2 v_t + (1 - gamma2) delta_t^2 / 4,   v_0 = 1,
+        eta_t   = 1 / (1 + max(sqrt(v_{t+1}) d0 + eps - 1, 0)).
+    The update a = -eta U + (1 - eta) s followed by a per-variable shift gives
+    delta_{t+1} = (1 - eta_t) delta_t, and since s_0 - s_1 = delta - (U_0 - U_1)
+    the state is s = log sigmoid(+-(s_0 - s_1)).  Dropping the centring gives
+    each label its own r^2 = (U_l + s_l)^2 and thus its own eta; flipping the
+    sign of log q in r changes delta; both are shown to leave this recursion."""
+    rng = np.random.default_rng(71)
+    n = 12
+    U = rng.normal(scale=1.5, size=(n, 2))
+    s0 = synth.random_logq(n, 2, seed=72).astype(np.float64)
+    m = oracle_mod.Model.sparse(U, np.array([[0.0, 0.8], [0.8, 0.0]]),
+                                np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0))
+    d0, g1, g2, eps, T = 2.5, 0.9, 0.7, 1e-8, 9
+    s, _ = m.parallel_prox_adam(d0, g1, g2, eps, T, s0)
+    delta = (U[:, 0] + s0[:, 0]) - (U[:, 1] + s0[:, 1])
+    v = np.ones(n)
+    for _ in range(T):
+        v = g2 * v + (1 - g2) * delta ** 2 / 4
+        eta = 1.0 / (1.0 + np.maximum(np.sqrt(v) * d0 + eps - 1.0, 0.0))
+        delta = (1 - eta) * delta
+    x = delta - (U[:, 0] - U[:, 1])            # s_0 - s_1
+    ref = np.stack([-np.logaddexp(0.0, -x), -np.logaddexp(0.0, x)], axis=1)
+    assert np.max(np.abs(s - ref)) <= 1e-12
+    # the pin is sensitive to the two readings it is meant to rule out
+    for kw in ({"centred": False}, {"sign": -1.0}):
+        alt = _adam_binary_decoupled(U, s0, d0, g2, eps, T, **kw)
+        assert np.max(np.abs(alt - ref)) > 1e-4, kw
+    assert np.max(np.abs(_adam_binary_decoupled(U, s0, d0, g2, eps, T) - ref)) <= 1e-12
 
 
 @pytest.mark.parametrize("rule", ["momentum", "adam"])

@@ -1,5 +1,7 @@
 """The allocation-free step entry point (for callers that cannot call
-cudaMalloc) gives the same result as one step through the handle API.
+cudaMalloc: code under an allocator or memory pool that owns the device, or
+in a region where allocation is forbidden) gives, on two calls in a row, the
+same result as the handle API and as the FP64 oracle.
 
 Collected last on purpose: it calls the library through raw ctypes with its
 own device buffers, and must pass both alone in a fresh process and after the
@@ -10,6 +12,7 @@ import numpy as np
 import pytest
 
 from paper_1511_06103_gb300 import synth
+from tests import helpers as H
 
 pytestmark = pytest.mark.gpu
 
@@ -51,6 +54,18 @@ def test_noalloc_step_matches_handle_api(Hh, Ww, L, conn, sym):
     eta = 0.31
     topo = binding.CRF_GRID8 if conn == 8 else binding.CRF_GRID4
 
+    # the FP64 oracle: two steps from the same state
+    import oracle
+    oracle.build()
+    m = oracle.Model.grid(np.asarray(d["U"], np.float64), np.asarray(d["mu"], np.float64),
+                          np.asarray(d["w"], np.float64), Hh, Ww, conn)
+    orc_s, orc_F = [], []
+    s_cur = np.asarray(s0, np.float64)
+    for _ in range(2):
+        orc_F.append(m.free_energy(np.exp(s_cur)))
+        s_cur = m.prox_step(float(np.float32(eta)), s_cur)
+        orc_s.append(s_cur)
+
     # reference: two steps through the handle API
     ref_s, ref_F = [], []
     with binding.CRF(topo, L, Hh, Ww) as crf:
@@ -76,8 +91,26 @@ def test_noalloc_step_matches_handle_api(Hh, Ww, L, conn, sym):
         assert rc == 0
         torch.cuda.synchronize()
         out = bufs[(k + 1) % 2].cpu().numpy()[:, :L]
-        assert np.abs(np.exp(out.astype(np.float64)) - np.exp(ref_s[k].astype(np.float64))).max() <= 1e-6
-        assert abs(F.item() - ref_F[k]) <= 1e-6 * max(abs(ref_F[k]), Hh * Ww)
+        q = np.exp(out.astype(np.float64))
+        assert np.abs(q - np.exp(ref_s[k].astype(np.float64))).max() <= 1e-6
+        assert H.f_close(F.item(), ref_F[k], Hh * Ww)
+        assert np.abs(q - np.exp(orc_s[k])).max() <= 1e-6
+        assert H.f_close(F.item(), orc_F[k], Hh * Ww)
+
+    # a state holding NaN gives a non-finite F, reported as NaN in F_out;
+    # the next call with a clean state starts from a cleared status word
+    bad = padded(s0, -1e30)
+    bad[3, 0] = np.nan
+    bufs[0].copy_(torch.from_numpy(bad).to(dev))
+    assert fn(topo, L, Hh, Ww, U.data_ptr(), w.data_ptr(), mu.ctypes.data, bufs[0].data_ptr(),
+              bufs[1].data_ptr(), eta, F.data_ptr(), stream) == 0
+    torch.cuda.synchronize()
+    assert np.isnan(F.item())
+    bufs[0].copy_(torch.from_numpy(padded(s0, -1e30)).to(dev))
+    assert fn(topo, L, Hh, Ww, U.data_ptr(), w.data_ptr(), mu.ctypes.data, bufs[0].data_ptr(),
+              bufs[1].data_ptr(), eta, F.data_ptr(), stream) == 0
+    torch.cuda.synchronize()
+    assert H.f_close(F.item(), orc_F[0], Hh * Ww)
 
 
 def test_noalloc_rejects_oversize_and_bad_arguments():
