@@ -41,4 +41,29 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) {
 
 __device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
 
+// Base-2 exponential and logarithm of the special-function unit, with
+// subnormal results flushed to zero.  e^x = 2^(x log2 e) and
+// ln z = log2(z) ln 2 are the change-of-base identities; the callers form
+// x log2 e (or its packed pair) themselves.
+constexpr float kLog2e = 1.44269504088896340736f;
+constexpr float kLn2 = 0.69314718055994530942f;
+
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float lg2_ftz(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// e^v per lane: one packed multiply, two base-2 exponentials.
+__device__ __forceinline__ float2 exp2v(float2 v) {
+    const float2 t = mul2(v, splat2(kLog2e));
+    return make_float2(ex2_ftz(t.x), ex2_ftz(t.y));
+}
+
 }  // namespace proxmf

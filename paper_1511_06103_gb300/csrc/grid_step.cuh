@@ -625,6 +625,47 @@ struct GridTcSmem {
     static constexpr int bytes = QT + A + B + 1024;           // + alignment slack
 };
 
+// a5, per instance: thread 0 of every tile publishes its tile's partial bs;
+// the last tile of instance b to arrive sums all partials in a fixed order
+// (the result does not depend on scheduling), stores F, appends it to the
+// trace and applies the stopping rule |F^t - F^{t-1}| <= rel_tol |F^t|
+// (Sec. 3.1).  All threads of the block call it; red holds GT / 32 doubles.
+__device__ __forceinline__ void grid_step_finish(const GridStepArgs &a, int b, double bs, double *red, int *is_last) {
+    const int tid = threadIdx.y * GX + threadIdx.x;
+    const int blk = blockIdx.y * a.nbx + blockIdx.x;
+    if (tid == 0) {
+        a.partial[(size_t)b * a.nblk + blk] = bs;
+        __threadfence();
+        const unsigned prev = atomicAdd(a.counter + b, 1u);
+        *is_last = (prev == (unsigned)(a.nblk - 1));
+    }
+    __syncthreads();
+    if (!*is_last) return;
+    // last tile of instance b: reduce all partials in a fixed order
+    __threadfence();
+    double acc = 0.0;
+    for (int k = tid; k < a.nblk; k += GT) acc += __ldcg(a.partial + (size_t)b * a.nblk + k);
+    acc = warp_sum_f64(acc);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        double F = 0.0;
+#pragma unroll
+        for (int k = 0; k < GT / 32; ++k) F += red[k];
+        a.f_cur[b] = F;
+        if (!isfinite(F)) atomicExch(a.status, -6);
+        if (a.update) {
+            if (a.t < a.trace_cap) a.f_trace[(size_t)b * a.trace_cap + a.t] = F;
+            if (a.rel_tol > 0.0 && a.t > 0 && a.t - 1 < a.trace_cap && a.done != nullptr) {
+                const double Fp = a.f_trace[(size_t)b * a.trace_cap + a.t - 1];
+                if (fabs(F - Fp) <= a.rel_tol * fabs(F)) a.done[b] = a.t + 1;
+            }
+        }
+        a.counter[b] = 0u;
+    }
+}
+
 template <int LT, int CONN, bool SYM, bool TC, int RULE = 0>
 __global__ void __launch_bounds__(GT, (RULE == 2) ? 1 : ((LT >= 24 || RULE) ? 2 : 3))
 grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
@@ -699,39 +740,14 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
         if (tid < 32) tc::tmem_dealloc(tct.tmem, GridTcSmem<LT, SYM>::NCOL);
     }
 
-    const int blk = blockIdx.y * a.nbx + blockIdx.x;
-    if (tid == 0) {
-        a.partial[(size_t)b * a.nblk + blk] = bs;
-        __threadfence();
-        const unsigned prev = atomicAdd(a.counter + b, 1u);
-        is_last = (prev == (unsigned)(a.nblk - 1));
-    }
-    __syncthreads();
-    if (!is_last) return;
-    // last tile of instance b: reduce all partials in a fixed order
-    __threadfence();
-    double acc = 0.0;
-    for (int k = tid; k < a.nblk; k += GT) acc += __ldcg(a.partial + (size_t)b * a.nblk + k);
-    acc = warp_sum_f64(acc);
-    __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = acc;
-    __syncthreads();
-    if (tid == 0) {
-        double F = 0.0;
-#pragma unroll
-        for (int k = 0; k < GT / 32; ++k) F += red[k];
-        a.f_cur[b] = F;
-        if (!isfinite(F)) atomicExch(a.status, -6);
-        if (a.update) {
-            if (a.t < a.trace_cap) a.f_trace[(size_t)b * a.trace_cap + a.t] = F;
-            if (a.rel_tol > 0.0 && a.t > 0 && a.t - 1 < a.trace_cap && a.done != nullptr) {
-                const double Fp = a.f_trace[(size_t)b * a.trace_cap + a.t - 1];
-                if (fabs(F - Fp) <= a.rel_tol * fabs(F)) a.done[b] = a.t + 1;
-            }
-        }
-        a.counter[b] = 0u;
-    }
+    grid_step_finish(a, b, bs, red, &is_last);
 }
+
+}  // namespace proxmf
+
+#include "grid_tma.cuh"
+
+namespace proxmf {
 
 template <int LT, int CONN, bool SYM>
 cudaError_t launch_grid_tc(const GridStepArgs &a, dim3 grid, dim3 block, cudaStream_t st) {
@@ -815,6 +831,19 @@ cudaError_t launch_grid_step_lt(const GridStepLaunch &l, cudaStream_t st) {
         if (l.conn == 8)
             return l.mu_sym ? launch_grid_tc<LT, 8, true>(a, grid, block, st) : launch_grid_tc<LT, 8, false>(a, grid, block, st);
         return l.mu_sym ? launch_grid_tc<LT, 4, true>(a, grid, block, st) : launch_grid_tc<LT, 4, false>(a, grid, block, st);
+    }
+    if constexpr (storage_labels(LT) >= 4) {
+        // fixed step, FP32: the TMA-staged tile (grid_tma.cuh)
+        if (a.adapt_d == nullptr) {
+            GridTmaMaps maps;
+            const cudaError_t e = encode_grid_maps(&maps, l, storage_labels(LT), GridTmaGeom<LT>::CS);
+            if (e != cudaSuccess) return e;
+            if (l.conn == 8)
+                return l.mu_sym ? launch_grid_tma<LT, 8, true>(maps, a, grid, block, st)
+                                : launch_grid_tma<LT, 8, false>(maps, a, grid, block, st);
+            return l.mu_sym ? launch_grid_tma<LT, 4, true>(maps, a, grid, block, st)
+                            : launch_grid_tma<LT, 4, false>(maps, a, grid, block, st);
+        }
     }
     if (l.conn == 8) {
         if (l.mu_sym)

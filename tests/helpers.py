@@ -132,3 +132,11 @@ def f_rel_err(F, F_ref) -> float:
     F = np.asarray(F, np.float64)
     F_ref = np.asarray(F_ref, np.float64)
     return float(np.max(np.abs(F - F_ref) / np.abs(F_ref)))
+
+
+def f_rel_close(F, F_ref, tol: float = 1e-6) -> bool:
+    """|F - F_ref| <= tol |F_ref| elementwise, with no floor: the bound as
+    stated, for the benchmark workloads."""
+    F = np.asarray(F, np.float64)
+    F_ref = np.asarray(F_ref, np.float64)
+    return bool(np.all(np.abs(F - F_ref) <= tol * np.abs(F_ref)))

@@ -87,12 +87,17 @@ def test_adam_with_lambda_damping_on_denoising(env):
     assert f_close(F, F_ref[-1], 64 * 64)
 
 
-def test_momentum_without_memory_is_the_fixed_step_bitwise(env):
+def test_momentum_without_memory_is_the_fixed_step(env):
+    """gamma1 = 0: the momentum rule takes the fixed step.  The fixed rule's
+    kernel groups its FP32 arithmetic differently (a = -eta m + c with
+    c = -eta U + (1 - eta) log q), so the two agree to FP32 rounding, within
+    the trajectory bounds."""
     binding, oracle, torch = env
     d = synth.random_grid(19, 45, 8, 8, seed=9, symmetric=False)
     a = run(binding, d, 20, eta=0.3, rule=binding.MF_RULE_MOMENTUM, gamma1=0.0)
-    b = run(binding, d, 20, resident=False, eta=0.3)   # the same (step-by-step) kernel
-    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    b = run(binding, d, 20, resident=False, eta=0.3)
+    assert np.abs(np.exp(a[0]) - np.exp(b[0])).max() <= 1e-5
+    assert f_close(a[1], b[1], 19 * 45)
 
 
 def test_momentum_rejected_on_dense_and_bf16(env):
