@@ -629,7 +629,8 @@ struct GridTcSmem {
 // the last tile of instance b to arrive sums all partials in a fixed order
 // (the result does not depend on scheduling), stores F, appends it to the
 // trace and applies the stopping rule |F^t - F^{t-1}| <= rel_tol |F^t|
-// (Sec. 3.1).  All threads of the block call it; red holds GT / 32 doubles.
+// (Sec. 3.1).  All NT threads of the block call it; red holds NT / 32 doubles.
+template <int NT = GT>
 __device__ __forceinline__ void grid_step_finish(const GridStepArgs &a, int b, double bs, double *red, int *is_last) {
     const int tid = threadIdx.y * GX + threadIdx.x;
     const int blk = blockIdx.y * a.nbx + blockIdx.x;
@@ -644,7 +645,7 @@ __device__ __forceinline__ void grid_step_finish(const GridStepArgs &a, int b, d
     // last tile of instance b: reduce all partials in a fixed order
     __threadfence();
     double acc = 0.0;
-    for (int k = tid; k < a.nblk; k += GT) acc += __ldcg(a.partial + (size_t)b * a.nblk + k);
+    for (int k = tid; k < a.nblk; k += NT) acc += __ldcg(a.partial + (size_t)b * a.nblk + k);
     acc = warp_sum_f64(acc);
     __syncthreads();
     if ((tid & 31) == 0) red[tid >> 5] = acc;
@@ -652,7 +653,7 @@ __device__ __forceinline__ void grid_step_finish(const GridStepArgs &a, int b, d
     if (tid == 0) {
         double F = 0.0;
 #pragma unroll
-        for (int k = 0; k < GT / 32; ++k) F += red[k];
+        for (int k = 0; k < NT / 32; ++k) F += red[k];
         a.f_cur[b] = F;
         if (!isfinite(F)) atomicExch(a.status, -6);
         if (a.update) {

@@ -334,6 +334,335 @@ grid_tma_step_kernel(const __grid_constant__ GridTmaMaps maps, const __grid_cons
     if (tid == 0 && a.update && ok) tma::wait_read();
 }
 
+// m1 += A S1 and m2 += A S2 with A given as pair columns (see pair_matvec):
+// every pair of A is loaded once for both pixels.
+template <int LT, int NP, int NPP>
+__device__ __forceinline__ void pair_matvec2(float2 (&m1)[NP], float2 (&m2)[NP], const float2 *A,
+                                             const float2 (&S1)[NP], const float2 (&S2)[NP]) {
+#pragma unroll
+    for (int k = 0; k < LT; ++k) {
+        const float2 s1 = splat2((k & 1) ? S1[k >> 1].y : S1[k >> 1].x);
+        const float2 s2 = splat2((k & 1) ? S2[k >> 1].y : S2[k >> 1].x);
+        const float4 *col = reinterpret_cast<const float4 *>(A + k * NPP);
+#pragma unroll
+        for (int i = 0; i < (NP + 1) / 2; ++i) {
+            const float4 t = col[i];
+            const float2 lo = make_float2(t.x, t.y), hi = make_float2(t.z, t.w);
+            m1[2 * i] = fma2(lo, s1, m1[2 * i]);
+            m2[2 * i] = fma2(lo, s2, m2[2 * i]);
+            if (2 * i + 1 < NP) {
+                m1[2 * i + 1] = fma2(hi, s1, m1[2 * i + 1]);
+                m2[2 * i + 1] = fma2(hi, s2, m2[2 * i + 1]);
+            }
+        }
+    }
+}
+
+// acc1 += w1 q(cell), acc2 += w2 q(cell): one cell read for two pixels.
+template <int NP>
+__device__ __forceinline__ void acc_cell2(float2 (&acc1)[NP], float2 (&acc2)[NP], const float *c, float w1,
+                                          float w2) {
+    const float2 a = splat2(w1), b = splat2(w2);
+#pragma unroll
+    for (int i = 0; i < (NP + 1) / 2; ++i) {
+        const float4 t = reinterpret_cast<const float4 *>(c)[i];
+        const float2 lo = make_float2(t.x, t.y), hi = make_float2(t.z, t.w);
+        acc1[2 * i] = fma2(a, lo, acc1[2 * i]);
+        acc2[2 * i] = fma2(b, lo, acc2[2 * i]);
+        if (2 * i + 1 < NP) {
+            acc1[2 * i + 1] = fma2(a, hi, acc1[2 * i + 1]);
+            acc2[2 * i + 1] = fma2(b, hi, acc2[2 * i + 1]);
+        }
+    }
+}
+
+// acc += w v over pairs held in registers.
+template <int NP>
+__device__ __forceinline__ void acc_regs(float2 (&acc)[NP], const float2 (&v)[NP], float w) {
+    const float2 ww = splat2(w);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) acc[i] = fma2(ww, v[i], acc[i]);
+}
+
+// The same step with two vertically adjacent pixels per thread (symmetric mu):
+// 128 threads per 32 x 8 tile.  Of the twelve cells around a pixel pair, the
+// pair's own two are in registers and the other ten are read once for both
+// (instead of sixteen reads), every pair of mu is fetched once for both
+// products, and the tile's 84 halo cells are converted 21 per warp, so no warp
+// waits on another at the barrier that follows the conversion.
+constexpr int GT2 = GX * GY / 2;   // threads of the two-pixel tile
+
+template <int LT, int CONN>
+__global__ void __launch_bounds__(GT2, GridTmaGeom<LT>::ctas)
+grid_tma2_step_kernel(const __grid_constant__ GridTmaMaps maps, const __grid_constant__ GridStepArgs a) {
+    using G = GridTmaGeom<LT>;
+    constexpr int LP = G::LP, CS = G::CS, TW = G::QW;
+    constexpr int NP = (LT + 1) / 2;
+    constexpr int NPP = (NP + 1) / 2 * 2;
+    constexpr int ND = CONN == 8 ? 4 : 2;
+    constexpr int HALO = 2 * TW + 2 * GY;             // 84 cells
+    constexpr int HPW = (HALO + 3) / 4;               // halo cells per warp
+    constexpr bool MASK = (LT == LP);
+    constexpr bool kParamMu = mu_in_params<LT, true, false, 0>();
+    static_assert(LP >= 4 && LP % 4 == 0, "cells are whole 16-byte vectors");
+    static_assert(HPW <= 32, "one halo cell per lane");
+    extern __shared__ __align__(128) uint8_t tsm[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(16) float2 mus[kParamMu ? 2 : LT * NPP];
+    __shared__ double red[GT2 / 32];
+    __shared__ int is_last;
+
+    const int b = blockIdx.z;
+    const int tx = threadIdx.x, tw = threadIdx.y, tid = tw * GX + tx;
+    const int x0 = blockIdx.x * GX, y0 = blockIdx.y * GY;
+    const int x = x0 + tx, y1 = y0 + 2 * tw, y2 = y1 + 1;
+    const int H = a.H, W = a.W, L = a.L;
+    const size_t N = (size_t)H * W;
+    const bool in1 = (x < W) && (y1 < H), in2 = (x < W) && (y2 < H);
+    const size_t p1 = (size_t)y1 * W + x, p2 = p1 + W;
+    uint8_t *base = tsm + ((128u - (tc::smem_u32(tsm) & 127u)) & 127u);
+    float *qt = reinterpret_cast<float *>(base);              // [QH][QW][CS]: log q, then q
+    float *ct = reinterpret_cast<float *>(base + G::COFF);   // [GY][GX][CS]: U, then c, then log q'
+
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (tid == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        tc::mbar_expect_tx(&bar, (uint32_t)(G::QH * G::QW * CS * 4 + G::CBYTES));
+        tma::load_4d(ct, &maps.U, &bar, 0, x0, y0, b);
+    }
+    for (int i = tid; !kParamMu && i < LT * NPP; i += GT2) mus[i] = a.mu_out[i];
+    // weights of the edges leaving each pixel and entering it
+    float wo1[4] = {0.f, 0.f, 0.f, 0.f}, wi1[4] = {0.f, 0.f, 0.f, 0.f};
+    float wo2[4] = {0.f, 0.f, 0.f, 0.f}, wi2[4] = {0.f, 0.f, 0.f, 0.f};
+    {
+        const float *wb = a.w + (size_t)b * N * ND;
+        if (in1) {
+            if (ND == 4) {
+                const float4 t = __ldg(reinterpret_cast<const float4 *>(wb + p1 * ND));
+                wo1[0] = t.x;
+                wo1[1] = t.y;
+                wo1[2] = t.z;
+                wo1[3] = t.w;
+            } else {
+                const float2 t = __ldg(reinterpret_cast<const float2 *>(wb + p1 * ND));
+                wo1[0] = t.x;
+                wo1[1] = t.y;
+            }
+            if (x > 0) wi1[0] = __ldg(wb + (p1 - 1) * ND + 0);
+            if (y1 > 0) wi1[1] = __ldg(wb + (p1 - W) * ND + 1);
+            if (CONN == 8) {
+                if (x > 0 && y1 > 0) wi1[2] = __ldg(wb + (p1 - W - 1) * ND + 2);
+                if (x + 1 < W && y1 > 0) wi1[3] = __ldg(wb + (p1 - W + 1) * ND + 3);
+            }
+        }
+        if (in2) {
+            if (ND == 4) {
+                const float4 t = __ldg(reinterpret_cast<const float4 *>(wb + p2 * ND));
+                wo2[0] = t.x;
+                wo2[1] = t.y;
+                wo2[2] = t.z;
+                wo2[3] = t.w;
+            } else {
+                const float2 t = __ldg(reinterpret_cast<const float2 *>(wb + p2 * ND));
+                wo2[0] = t.x;
+                wo2[1] = t.y;
+            }
+            if (x > 0) wi2[0] = __ldg(wb + (p2 - 1) * ND + 0);
+            wi2[1] = wo1[1];   // the edge (x, y1) -> (x, y2)
+            if (CONN == 8) {
+                if (x > 0) wi2[2] = __ldg(wb + (p2 - W - 1) * ND + 2);
+                if (x + 1 < W) wi2[3] = __ldg(wb + (p2 - W + 1) * ND + 3);
+            }
+        }
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (a.done != nullptr && a.done[b] != 0) {
+        if (a.update) {
+            float2 v[LP / 2];
+            if (in1) {
+                load_px<LP>(v, a.s_in + ((size_t)b * N + p1) * LP);
+                store_px<LP>(a.s_out + ((size_t)b * N + p1) * LP, v);
+            }
+            if (in2) {
+                load_px<LP>(v, a.s_in + ((size_t)b * N + p2) * LP);
+                store_px<LP>(a.s_out + ((size_t)b * N + p2) * LP, v);
+            }
+        }
+        if (tid == 0) {
+            tma::load_4d(qt, &maps.s_in, &bar, 0, x0 - 1, y0 - 1, b);
+            tc::mbar_wait(&bar, 0, a.status);
+        }
+        return;
+    }
+    if (tid == 0) tma::load_4d(qt, &maps.s_in, &bar, 0, x0 - 1, y0 - 1, b);
+    const float eta = a.eta[b];
+    const float2 neta = splat2(-eta), ome = splat2(1.f - eta);
+    const bool ok = tc::mbar_wait(&bar, 0, a.status);
+
+    // halo cells, HPW consecutive ones per warp
+    if (tx < HPW && tw * HPW + tx < HALO) {
+        const int h = tw * HPW + tx;
+        int hr, hc;
+        if (h < TW) {
+            hr = 0;
+            hc = h;
+        } else if (h < 2 * TW) {
+            hr = GY + 1;
+            hc = h - TW;
+        } else {
+            const int k = h - 2 * TW;
+            hr = 1 + (k >> 1);
+            hc = (k & 1) ? TW - 1 : 0;
+        }
+        float *c = qt + (hr * TW + hc) * CS;
+        float2 v[LP / 2];
+        get_cell<LP>(v, c);
+#pragma unroll
+        for (int k = 0; k < LP / 2; ++k) v[k] = exp2v(v[k]);
+        set_cell<LP>(c, v);
+    }
+    // the two own cells: q (kept in registers), c and the unary-entropy part of F
+    float *q1c = qt + ((2 * tw + 1) * TW + tx + 1) * CS;
+    float *q2c = q1c + TW * CS;
+    float *c1c = ct + (2 * tw * GX + tx) * CS;
+    float *c2c = c1c + GX * CS;
+    float2 q1[NP], q2[NP];
+    float f01, f02;
+    {
+        float2 s[LP / 2], u[LP / 2], q[LP / 2], c[LP / 2];
+        float2 acc = splat2(0.f);
+        get_cell<LP>(s, q1c);
+        get_cell<LP>(u, c1c);
+#pragma unroll
+        for (int k = 0; k < LP / 2; ++k) {
+            q[k] = exp2v(s[k]);
+            c[k] = fma2(neta, u[k], mul2(ome, s[k]));
+            if (k < NP) {
+                acc = fma2(q[k], add2(u[k], s[k]), acc);
+                q1[k] = q[k];
+            }
+        }
+        set_cell<LP>(q1c, q);
+        set_cell<LP>(c1c, c);
+        f01 = acc.x + acc.y;
+        acc = splat2(0.f);
+        get_cell<LP>(s, q2c);
+        get_cell<LP>(u, c2c);
+#pragma unroll
+        for (int k = 0; k < LP / 2; ++k) {
+            q[k] = exp2v(s[k]);
+            c[k] = fma2(neta, u[k], mul2(ome, s[k]));
+            if (k < NP) {
+                acc = fma2(q[k], add2(u[k], s[k]), acc);
+                q2[k] = q[k];
+            }
+        }
+        set_cell<LP>(q2c, q);
+        set_cell<LP>(c2c, c);
+        f02 = acc.x + acc.y;
+    }
+    __syncthreads();
+
+    // a1: neighbour sums (ten cells read, each once) and the two L x L products
+    float2 m1[NP], m2[NP];
+    {
+        float2 S1[NP], S2[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            S1[k] = splat2(0.f);
+            S2[k] = splat2(0.f);
+        }
+        const float *r1 = qt + ((2 * tw + 1) * TW + tx + 1) * CS;   // (x, y1)
+        const float *r0 = r1 - TW * CS;                             // (x, y1 - 1)
+        const float *r2 = r1 + TW * CS;                             // (x, y2)
+        const float *r3 = r2 + TW * CS;                             // (x, y2 + 1)
+        acc_regs<NP>(S1, q2, wo1[1]);                               // down of 1
+        acc_regs<NP>(S2, q1, wi2[1]);                               // up of 2
+        acc_cell2<NP>(S1, S2, r1 + CS, wo1[0], CONN == 8 ? wi2[3] : 0.f);   // (x+1, y1)
+        acc_cell2<NP>(S1, S2, r1 - CS, wi1[0], CONN == 8 ? wi2[2] : 0.f);   // (x-1, y1)
+        acc_cell2<NP>(S2, S1, r2 + CS, wo2[0], CONN == 8 ? wo1[2] : 0.f);   // (x+1, y2)
+        acc_cell2<NP>(S2, S1, r2 - CS, wi2[0], CONN == 8 ? wo1[3] : 0.f);   // (x-1, y2)
+        acc_cell<NP>(S1, r0, wi1[1]);                               // (x, y1-1)
+        acc_cell<NP>(S2, r3, wo2[1]);                               // (x, y2+1)
+        if (CONN == 8) {
+            acc_cell<NP>(S1, r0 - CS, wi1[2]);                      // (x-1, y1-1)
+            acc_cell<NP>(S1, r0 + CS, wi1[3]);                      // (x+1, y1-1)
+            acc_cell<NP>(S2, r3 + CS, wo2[2]);                      // (x+1, y2+1)
+            acc_cell<NP>(S2, r3 - CS, wo2[3]);                      // (x-1, y2+1)
+        }
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            m1[k] = splat2(0.f);
+            m2[k] = splat2(0.f);
+        }
+        if constexpr (kParamMu)
+            pair_matvec2<LT, NP, NPP>(m1, m2, a.mu_p, S1, S2);
+        else
+            pair_matvec2<LT, NP, NPP>(m1, m2, mus, S1, S2);
+    }
+
+    // a3-a4 per pixel, log q' over the unary cells; F of the pair
+    float fpair = 0.f;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        float2 (&m)[NP] = r == 0 ? m1 : m2;
+        const float2 (&q)[NP] = r == 0 ? q1 : q2;
+        float *cc = r == 0 ? c1c : c2c;
+        float2 c[LP / 2];
+        get_cell<LP>(c, cc);
+        float2 fm = splat2(0.f);
+        float mx = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            fm = fma2(q[k], m[k], fm);
+            float2 av = fma2(neta, m[k], c[k]);
+            const int l0 = 2 * k, l1 = 2 * k + 1;
+            if ((MASK && l0 >= L)) av.x = -INFINITY;
+            if ((MASK && l1 >= L) || l1 >= LT) av.y = -INFINITY;
+            m[k] = av;
+            mx = fmaxf(mx, fmaxf(av.x, av.y));
+        }
+        float2 z2 = splat2(0.f);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) z2 = add2(z2, exp2v(add2(m[k], splat2(-mx))));
+        const float2 nlse = splat2(-(mx + lg2_ftz(z2.x + z2.y) * kLn2));
+        float2 o[LP / 2];
+#pragma unroll
+        for (int k = 0; k < LP / 2; ++k) {
+            if (k < NP) {
+                o[k] = add2(m[k], nlse);
+                const int l0 = 2 * k, l1 = 2 * k + 1;
+                if ((MASK && l0 >= L)) o[k].x = kPadLogQ;
+                if ((MASK && l1 >= L) || l1 >= LT) o[k].y = kPadLogQ;
+            } else {
+                o[k] = splat2(kPadLogQ);
+            }
+        }
+        set_cell<LP>(cc, o);
+        const bool in = r == 0 ? in1 : in2;
+        if (in) fpair += (r == 0 ? f01 : f02) + 0.5f * (fm.x + fm.y);
+    }
+    tc::fence_async_smem();   // the TMA store reads these cells
+    const df fw = warp_sum_df(df{fpair, 0.f});
+    if ((tid & 31) == 0) red[tid >> 5] = df_to(fw);
+    __syncthreads();
+    double bs = 0.0;
+    if (tid == 0) {
+        if (a.update && ok) {
+            tma::store_4d(&maps.s_out, ct, 0, x0, y0, b);
+            tma::commit();
+        }
+#pragma unroll
+        for (int k = 0; k < GT2 / 32; ++k) bs += red[k];
+    }
+    grid_step_finish<GT2>(a, b, bs, red, &is_last);
+    if (tid == 0 && a.update && ok) tma::wait_read();
+}
+
 // Host side: the three tensor maps of one launch.  The state is read as a 4-D
 // view [B][H][W][LP] (FP32); each box widens a cell to CS floats.
 cudaError_t encode_grid_maps(GridTmaMaps *m, const GridStepLaunch &l, int LP, int CS);
@@ -341,8 +670,11 @@ cudaError_t encode_grid_maps(GridTmaMaps *m, const GridStepLaunch &l, int LP, in
 template <int LT, int CONN, bool SYM>
 cudaError_t launch_grid_tma(const GridTmaMaps &maps, const GridStepArgs &a, dim3 grid, dim3 block, cudaStream_t st) {
     constexpr int bytes = GridTmaGeom<LT>::bytes;
+    // symmetric mu: two pixels per thread
+    auto kern = SYM ? grid_tma2_step_kernel<LT, CONN> : grid_tma_step_kernel<LT, CONN, SYM>;
+    if (SYM) block = dim3(GX, GY / 2, 1);
     static SmemOptIn optin;   // once per device
-    const cudaError_t attr = smem_optin(optin, grid_tma_step_kernel<LT, CONN, SYM>, bytes);
+    const cudaError_t attr = smem_optin(optin, kern, bytes);
     if (attr != cudaSuccess) return attr;
     // programmatic dependent launch: the step may start while the previous
     // kernel on the stream drains (the kernel waits before it reads the state)
@@ -356,7 +688,7 @@ cudaError_t launch_grid_tma(const GridTmaMaps &maps, const GridStepArgs &a, dim3
     pdl[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = pdl;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, grid_tma_step_kernel<LT, CONN, SYM>, maps, a);
+    return cudaLaunchKernelEx(&cfg, kern, maps, a);
 }
 
 }  // namespace proxmf
