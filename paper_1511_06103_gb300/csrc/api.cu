@@ -31,6 +31,7 @@ struct crf_s {
     float2 *mu_pairs = nullptr;  // device [2][LT][NPP] mu column / row pairs
     std::vector<float2> mu_pairs_host;   // host copy of the same
     uint8_t *mu_tc = nullptr;    // device BF16 operand images of mu, mu^T (grid, BF16 form)
+    __nv_bfloat16 *U16 = nullptr;  // [B][N][u16_pitch(LP)] unaries in BF16 (grid, BF16 form)
     // general graph (edge list)
     bool sparse = false;
     int *sp_out_ptr = nullptr, *sp_out_col = nullptr, *sp_in_ptr = nullptr, *sp_in_col = nullptr;
@@ -180,7 +181,7 @@ void free_all(crf_t h) {
     float *fd[] = {h->K32, h->q32[0], h->q32[1], h->feats, h->mu_dev};
     for (float *p : fd)
         if (p) cudaFree(p);
-    __nv_bfloat16 *bd[] = {h->K16, h->qt16[0], h->qt16[1]};
+    __nv_bfloat16 *bd[] = {h->K16, h->qt16[0], h->qt16[1], h->U16};
     for (__nv_bfloat16 *p : bd)
         if (p) cudaFree(p);
     if (h->tcb.split_part) cudaFree(h->tcb.split_part);
@@ -231,6 +232,7 @@ GridStepLaunch step_args(crf_t h, const float *eta, int t, int update, double re
     a.mu_out = h->mu_pairs;
     a.mu_in = h->mu_pairs + (size_t)h->LT * mu_pair_slots(h->LT);
     a.mu_tc = reinterpret_cast<const uint4 *>(h->mu_tc);
+    a.U16 = h->U16;
     a.mu_host = h->mu_pairs_host.empty() ? nullptr : h->mu_pairs_host.data();
     a.adapt_d = (h->adapt_active || (update && h->rule_kernel == 2)) ? h->adapt_d : nullptr;
     a.rule = update ? h->rule_kernel : 0;
@@ -627,6 +629,11 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
         h->bf16 = true;
         ok = ok && dalloc(&h->mu_tc, kTcImageBytes) == cudaSuccess;
         if (ok) ok = cudaMemsetAsync(h->mu_tc, 0, kTcImageBytes, h->st) == cudaSuccess;
+        if (!sparse) {
+            const size_t nu = n_pix(h) * u16_pitch(h->LP);
+            ok = ok && dalloc(&h->U16, nu) == cudaSuccess;
+            if (ok) ok = cudaMemsetAsync(h->U16, 0, nu * sizeof(__nv_bfloat16), h->st) == cudaSuccess;
+        }
     }
     ok = ok && dalloc(&h->eta_fixed, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->adapt_d, h->B) == cudaSuccess;
@@ -699,6 +706,10 @@ crf_status crf_set_unary(crf_t h, const float *U, int is_device) {
     CK(h, launch_rows_to_padded(src, h->U, (long long)n_pix(h), h->L, h->LP, 0.f, h->st));
     CK(h, launch_init_logq(h->U, h->s[0], (long long)n_pix(h), h->L, h->LP, h->st));
     h->launches += 2;
+    if (h->U16) {   // the BF16 form's unaries
+        CK(h, launch_to_bf16(h->U, h->U16, (long long)n_pix(h), h->LP, u16_pitch(h->LP), h->st));
+        h->launches++;
+    }
     h->cur = 0;
     CK(h, refresh_q(h));
     h->fcur_valid = false;

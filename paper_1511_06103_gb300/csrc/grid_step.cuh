@@ -828,6 +828,17 @@ cudaError_t launch_grid_step_lt(const GridStepLaunch &l, cudaStream_t st) {
         return l.mu_sym ? launch_grid_rule<LT, 4, true, 2>(a, grid, block, st)
                         : launch_grid_rule<LT, 4, false, 2>(a, grid, block, st);
     }
+    if constexpr (storage_labels(LT) >= 4) {
+        // BF16 form, symmetric mu: TMA-staged tiles with BF16 gather and unaries
+        if (l.tc && l.mu_sym && l.U16 != nullptr && l.rule == 0 && l.adapt_d == nullptr) {
+            using TG = GridTmaTcGeom<LT>;
+            GridTmaTcMaps maps;
+            const cudaError_t e = encode_grid_tc_maps(&maps, l, TG::LP, TG::CS, TG::C16, TG::UP);
+            if (e != cudaSuccess) return e;
+            return l.conn == 8 ? launch_grid_tma_tc<LT, 8>(maps, a, grid, st)
+                               : launch_grid_tma_tc<LT, 4>(maps, a, grid, st);
+        }
+    }
     if (l.tc) {
         if (l.conn == 8)
             return l.mu_sym ? launch_grid_tc<LT, 8, true>(a, grid, block, st) : launch_grid_tc<LT, 8, false>(a, grid, block, st);

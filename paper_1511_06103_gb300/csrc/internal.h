@@ -82,6 +82,7 @@ struct GridStepLaunch {
     const float2 *mu_host;   // host copy of the column pairs (first LT * mu_pair_slots(LT)); required
                              // for symmetric mu with LT <= 21 (copied into the launch parameters)
     const uint4 *mu_tc;      // tensor-core form: device BF16 operand images of mu, mu^T
+    const __nv_bfloat16 *U16;  // tensor-core form: unaries in BF16, [B][N][u16_pitch(LP)] (may be null)
     bool tc;                 // BF16 tensor-core messages (else FP32)
     const float *adapt_d;    // [B] adaptive binary step: eta_i = 1/(1 + d q_i0 q_i1); null = fixed eta;
                              // for rule 2 (Adam): d0 per instance
@@ -179,6 +180,12 @@ cudaError_t launch_weights_to_pixel_major(const float *src, float *dst, int B, i
 cudaError_t launch_init_logq(const float *U, float *s, long long rows, int L, int LP, cudaStream_t st);
 // eta[b] = value for all b.
 cudaError_t launch_fill_eta(float *eta, int B, double value, cudaStream_t st);
+// BF16 unaries of the tensor-core grid step: LP labels padded to a multiple
+// of 8 (whole 16-byte rows for the TMA).
+__host__ __device__ constexpr int u16_pitch(int LP) { return (LP + 7) / 8 * 8; }
+// dst[r][0..pitch) = src[r][0..LP) rounded to BF16 (nearest even), zero past LP.
+cudaError_t launch_to_bf16(const float *src, __nv_bfloat16 *dst, long long rows, int LP, int pitch,
+                           cudaStream_t st);
 // d[b] = max(Lambda[b], 0) (FP32)
 cudaError_t launch_lambda_to_d(const double *Lambda, float *d, int B, cudaStream_t st);
 

@@ -124,6 +124,24 @@ cudaError_t launch_lambda_to_d(const double *Lambda, float *d, int B, cudaStream
     return cudaGetLastError();
 }
 
+__global__ void to_bf16_kernel(const float *__restrict__ src, __nv_bfloat16 *__restrict__ dst, long long rows,
+                               int LP, int pitch) {
+    const long long n = rows * pitch;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / pitch;
+        const int l = (int)(i - r * pitch);
+        dst[i] = __float2bfloat16_rn(l < LP ? src[r * LP + l] : 0.f);
+    }
+}
+
+cudaError_t launch_to_bf16(const float *src, __nv_bfloat16 *dst, long long rows, int LP, int pitch,
+                           cudaStream_t st) {
+    const long long blocks = (rows * pitch + 255) / 256;
+    to_bf16_kernel<<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, st>>>(src, dst, rows, LP, pitch);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fill_eta(float *eta, int B, double value, cudaStream_t st) {
     fill_eta_kernel<<<(B + 127) / 128, 128, 0, st>>>(eta, B, (float)value);
     return cudaGetLastError();
