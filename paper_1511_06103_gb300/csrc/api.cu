@@ -391,22 +391,6 @@ crf_status read_status(crf_t h) {
 
 namespace proxmf {
 
-cudaError_t launch_serve(int LT, int conn, bool sym, ServeSlot *slots, const ServeBucket *bucket,
-                         ServeResult *res, int grid, cudaStream_t st) {
-    switch (LT) {
-    case 2: return launch_serve_l2(conn, sym, slots, bucket, res, grid, st);
-    case 4: return launch_serve_l4(conn, sym, slots, bucket, res, grid, st);
-    case 8: return launch_serve_l8(conn, sym, slots, bucket, res, grid, st);
-    case 12: return launch_serve_l12(conn, sym, slots, bucket, res, grid, st);
-    case 16: return launch_serve_l16(conn, sym, slots, bucket, res, grid, st);
-    case 20: return launch_serve_l20(conn, sym, slots, bucket, res, grid, st);
-    case 21: return launch_serve_l21(conn, sym, slots, bucket, res, grid, st);
-    case 24: return launch_serve_l24(conn, sym, slots, bucket, res, grid, st);
-    case 28: return launch_serve_l28(conn, sym, slots, bucket, res, grid, st);
-    default: return launch_serve_l32(conn, sym, slots, bucket, res, grid, st);
-    }
-}
-
 cudaError_t launch_grid_step(const GridStepLaunch &a, cudaStream_t st) {
     switch (kernel_labels(a.L)) {
     case 2: return launch_grid_step_l2(a, st);

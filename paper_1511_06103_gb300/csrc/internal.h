@@ -132,22 +132,6 @@ inline void grid_tiles(int H, int W, int *nbx, int *nby) {
 // Column / row pairs of mu for a kernel label count LT (api.cu).
 void build_mu_pairs_host(const float *mu, int L, int LT, float2 *out);
 
-// Serving (serve.cuh, serve.cu): persistent per-bucket step over a slot table.
-struct ServeSlot;
-struct ServeBucket;
-struct ServeResult;
-cudaError_t launch_serve(int LT, int conn, bool sym, ServeSlot *slots, const ServeBucket *bucket,
-                         ServeResult *res, int grid, cudaStream_t st);
-cudaError_t launch_serve_l2(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
-cudaError_t launch_serve_l4(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
-cudaError_t launch_serve_l8(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
-cudaError_t launch_serve_l12(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
-cudaError_t launch_serve_l16(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
-cudaError_t launch_serve_l20(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
-cudaError_t launch_serve_l21(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
-cudaError_t launch_serve_l24(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
-cudaError_t launch_serve_l28(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
-cudaError_t launch_serve_l32(int conn, bool sym, ServeSlot *, const ServeBucket *, ServeResult *, int, cudaStream_t);
 // Step-size bound for serving: eta = 1/(1 + D max|nu|), D the largest weighted
 // degree, nu the eigenvalues of C mu C (symmetric mu).
 cudaError_t launch_eta_bound(const float *w, int H, int W, int nd, const float *mu, int L, float *eta,

@@ -4,14 +4,23 @@
 // grid CRFs of any size, label count and connectivity) are copied on submit
 // and queued; each step the server
 //   1. retires the slots whose stopping rule fired (flags in host-mapped
-//      memory): copies q out and returns the slot and its pool memory;
+//      memory): queues the copy of q out and returns the slot and its pool
+//      memory (later work on the stream is ordered after the copy);
 //   2. admits queued requests in arrival order while a slot and pool memory
 //      (first-fit) are free: uploads and converts the data, builds q^0 and
-//      the step size on the device, and registers the slot in its bucket;
-//   3. replays a CUDA graph holding one persistent launch per bucket
-//      (serve.cuh) for the requested number of iterations.
+//      the step size on the device, and enters the slot in the tile table;
+//   3. replays a CUDA graph holding one persistent launch over the tiles of
+//      every running request (serve.cuh), once per requested iteration.
 // Requests therefore join and leave between iterations while the others keep
 // running, and every request's arithmetic is that of a solve on its own.
+//
+// No step waits for the device except to recycle host staging memory: the
+// uploads of an admission and the download of a result go through a ring of
+// page-locked host memory (cudaMemcpyAsync from pageable memory would
+// synchronise the stream, and with it every admission, with the iterations
+// already queued); an event per block says when the ring may reuse it and
+// when a result has reached its q_out.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -71,21 +80,110 @@ private:
     size_t used_ = 0;
 };
 
+// Ring of page-locked host memory: blocks are handed out in FIFO order and
+// come back when the event recorded after their last copy has completed.
+class PinnedRing {
+public:
+    bool init(size_t size) {
+        size_ = size;
+        return cudaHostAlloc((void **)&base_, size, cudaHostAllocDefault) == cudaSuccess;
+    }
+    ~PinnedRing() {
+        for (auto &b : live_) cudaEventDestroy(b.ev);
+        for (cudaEvent_t e : spare_) cudaEventDestroy(e);
+        if (base_) cudaFreeHost(base_);
+    }
+    size_t size() const { return size_; }
+    // A block of `bytes` (256-byte aligned), waiting for the oldest blocks to
+    // be released if the ring is full.  nullptr if it can never fit.
+    unsigned char *acquire(size_t bytes) {
+        bytes = (bytes + 255) / 256 * 256;
+        if (bytes > size_) return nullptr;
+        for (;;) {
+            reclaim(false);
+            size_t off;
+            if (fits(bytes, &off)) {
+                pending_off_ = off;
+                pending_bytes_ = bytes;
+                return base_ + off;
+            }
+            if (live_.empty()) return nullptr;
+            cudaEventSynchronize(live_.front().ev);
+        }
+    }
+    // Seal the block handed out last: its copies were issued on st.
+    cudaError_t seal(cudaStream_t st) {
+        cudaEvent_t e = nullptr;
+        if (!spare_.empty()) {
+            e = spare_.back();
+            spare_.pop_back();
+        } else if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            return cudaErrorMemoryAllocation;
+        }
+        const cudaError_t r = cudaEventRecord(e, st);
+        live_.push_back({pending_off_, pending_bytes_, e});
+        return r;
+    }
+    cudaEvent_t last_event() const { return live_.back().ev; }
+    void reclaim(bool all) {
+        while (!live_.empty() && (all || cudaEventQuery(live_.front().ev) == cudaSuccess)) {
+            if (all) cudaEventSynchronize(live_.front().ev);
+            spare_.push_back(live_.front().ev);
+            live_.pop_front();
+        }
+        (void)cudaGetLastError();   // a query of an unfinished event is not an error
+    }
+
+private:
+    bool fits(size_t bytes, size_t *off) const {
+        if (live_.empty()) {
+            *off = 0;
+            return true;
+        }
+        const size_t start = live_.front().off, end = live_.back().off + live_.back().bytes;
+        if (end > start || (end == start && live_.size() == 0)) {
+            if (size_ - end >= bytes) {
+                *off = end;
+                return true;
+            }
+            if (start >= bytes) {
+                *off = 0;
+                return true;
+            }
+            return false;
+        }
+        if (start - end >= bytes) {
+            *off = end;
+            return true;
+        }
+        return false;
+    }
+    struct Block {
+        size_t off, bytes;
+        cudaEvent_t ev;
+    };
+    unsigned char *base_ = nullptr;
+    size_t size_ = 0;
+    std::deque<Block> live_;
+    std::vector<cudaEvent_t> spare_;
+    size_t pending_off_ = 0, pending_bytes_ = 0;
+};
+
 struct Request {
     uint64_t ticket = 0;
     int H = 0, W = 0, L = 0, conn = 4;
     std::vector<float> U, mu, w;
     mf_params p{};
     float *q_out = nullptr;
-    int state = 0;               // 0 queued, 1 running, 2 done
+    int state = 0;               // 0 queued, 1 running, 3 result on its way to q_out, 2 done
     int slot = -1;
     size_t off = 0, bytes = 0;
     double F = 0.0;
     int iters = 0;
     bool sym = true;
+    const unsigned char *q_host = nullptr;   // pinned copy of q while state 3
+    cudaEvent_t q_ready = nullptr;
 };
-
-constexpr int kMaxBuckets = 64;
 
 }  // namespace
 
@@ -96,24 +194,27 @@ struct mf_server_s {
     int max_slots = 0;
     unsigned char *pool_base = nullptr;
     Pool *pool = nullptr;
+    PinnedRing ring;
     ServeSlot *d_slots = nullptr;
-    ServeBucket *d_buckets = nullptr;
+    ServeTable *d_table = nullptr;
+    ServeTable *h_table[2] = {nullptr, nullptr};   // page-locked, alternating uploads
+    cudaEvent_t table_ev[2] = {nullptr, nullptr};
+    int table_buf = 0;
+    bool table_dirty = false;
     ServeResult *h_res = nullptr, *d_res = nullptr;   // host-mapped
     double *d_scratch = nullptr;
     float *staging = nullptr;
     size_t staging_floats = 0;
-    std::vector<ServeBucket> h_buckets;
-    std::vector<int> bucket_lt, bucket_conn, bucket_sym;
-    std::vector<bool> bucket_dirty;
     std::vector<int> slot_ticket;
     std::deque<uint64_t> queue;
+    std::deque<uint64_t> outgoing;   // results in flight to q_out, in order
     std::unordered_map<uint64_t, Request> reqs;
     uint64_t next_ticket = 1;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    bool graph_stale = true;
+    size_t graph_smem = 0;           // dynamic shared memory the graph's launch was recorded with
     bool broken = false;
-    int grid_small = 0, grid_large = 0;
+    int sms = 0;
 };
 
 namespace {
@@ -158,41 +259,56 @@ SlotLayout layout_for(const Request &r) {
     return l;
 }
 
-int bucket_for(mf_server_t s, int LT, int conn, bool sym) {
-    for (size_t b = 0; b < s->bucket_lt.size(); ++b)
-        if (s->bucket_lt[b] == LT && s->bucket_conn[b] == conn && s->bucket_sym[b] == (int)sym) return (int)b;
-    if ((int)s->bucket_lt.size() >= kMaxBuckets) return -1;
-    s->bucket_lt.push_back(LT);
-    s->bucket_conn.push_back(conn);
-    s->bucket_sym.push_back(sym ? 1 : 0);
-    s->bucket_dirty.push_back(true);
-    s->graph_stale = true;
-    return (int)s->bucket_lt.size() - 1;
+// Host bytes an admission stages: U and w rows, mu pairs, mu, eta, the slot.
+size_t admit_staging_bytes(const Request &r) {
+    const size_t N = (size_t)r.H * r.W;
+    const int LT = kernel_labels(r.L), nd = r.conn == 8 ? 4 : 2;
+    return align256(N * r.L * 4) + align256(N * nd * 4) + align256((size_t)2 * LT * mu_pair_slots(LT) * 8) +
+           align256((size_t)r.L * r.L * 4) + 256 + align256(sizeof(ServeSlot));
 }
 
-void bucket_rebuild(mf_server_t s, int b, const std::vector<ServeSlot> &hs) {
-    (void)hs;
-    ServeBucket &bk = s->h_buckets[b];
-    int k = 0, acc = 0;
+// The tile table over every running slot (slot order), into the next
+// page-locked buffer and up to the device.
+crf_status upload_table(mf_server_t s) {
+    const int k = s->table_buf;
+    SCK(cudaEventSynchronize(s->table_ev[k]));   // the previous upload from this buffer is done
+    ServeTable &t = *s->h_table[k];
+    int n = 0, acc = 0;
     for (int si = 0; si < s->max_slots; ++si) {
-        const int t = s->slot_ticket[si];
-        if (t == 0) continue;
-        const Request &r = s->reqs.at((uint64_t)t);
+        const uint64_t tk = (uint64_t)s->slot_ticket[si];
+        if (!tk) continue;
+        const Request &r = s->reqs.at(tk);
         if (r.state != 1) continue;
-        if (bucket_for(s, kernel_labels(r.L), r.conn, r.sym) != b) continue;
         int nbx, nby;
         grid_tiles(r.H, r.W, &nbx, &nby);
-        bk.slots[k] = si;
-        bk.prefix[k] = acc;
+        t.slots[n] = si;
+        t.prefix[n] = acc;
         acc += nbx * nby;
-        ++k;
+        ++n;
     }
-    bk.count = k;
-    bk.prefix[k] = acc;
-    s->bucket_dirty[b] = true;
+    t.count = n;
+    t.prefix[n] = acc;
+    const size_t bytes = offsetof(ServeTable, prefix) + (size_t)(n + 1) * sizeof(int);
+    SCK(cudaMemcpyAsync(s->d_table, &t, bytes, cudaMemcpyHostToDevice, s->st));
+    SCK(cudaEventRecord(s->table_ev[k], s->st));
+    s->table_buf ^= 1;
+    s->table_dirty = false;
+    return CRF_OK;
 }
 
-crf_status capture_graph(mf_server_t s) {
+// Dynamic shared memory of the serving launch: the largest class running.
+size_t needed_smem(mf_server_t s) {
+    size_t m = 0;
+    for (int si = 0; si < s->max_slots; ++si) {
+        const uint64_t tk = (uint64_t)s->slot_ticket[si];
+        if (!tk) continue;
+        const Request &r = s->reqs.at(tk);
+        if (r.state == 1) m = std::max(m, serve_tile_smem(kernel_labels(r.L)));
+    }
+    return m;
+}
+
+crf_status capture_graph(mf_server_t s, size_t smem) {
     if (s->exec) {
         cudaGraphExecDestroy(s->exec);
         s->exec = nullptr;
@@ -201,21 +317,22 @@ crf_status capture_graph(mf_server_t s) {
         cudaGraphDestroy(s->graph);
         s->graph = nullptr;
     }
+    // persistent grid: every SM, as many blocks as fit with this shared memory
+    int per_sm = 0;
+    SCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_step_kernel, GT, smem));
+    const int grid = s->sms * std::max(per_sm, 1);
     SCK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
-    for (size_t b = 0; b < s->bucket_lt.size(); ++b) {
-        const int grid = s->bucket_lt[b] >= 24 ? s->grid_large : s->grid_small;
-        const cudaError_t e = launch_serve(s->bucket_lt[b], s->bucket_conn[b], s->bucket_sym[b] != 0, s->d_slots,
-                                           s->d_buckets + b, s->d_res, grid, s->cap);
-        if (e != cudaSuccess) {
-            cudaGraph_t g;
-            cudaStreamEndCapture(s->cap, &g);
-            if (g) cudaGraphDestroy(g);
-            return srv_cuda(s, e);
-        }
+    serve_step_kernel<<<grid, dim3(GX, GY, 1), smem, s->cap>>>(s->d_slots, s->d_table, s->d_res);
+    const cudaError_t e = cudaGetLastError();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return srv_cuda(s, e != cudaSuccess ? e : e2);
     }
-    SCK(cudaStreamEndCapture(s->cap, &s->graph));
+    s->graph = g;
     SCK(cudaGraphInstantiate(&s->exec, s->graph, 0));
-    s->graph_stale = false;
+    s->graph_smem = smem;
     return CRF_OK;
 }
 
@@ -242,26 +359,41 @@ crf_status admit(mf_server_t s, Request &r, int si) {
     float *U = (float *)(base + l.U), *s0 = (float *)(base + l.s0), *s1 = (float *)(base + l.s1);
     float *w = (float *)(base + l.w), *mu = (float *)(base + l.mu), *eta = (float *)(base + l.eta);
     float2 *pairs = (float2 *)(base + l.pairs);
-    SCK(cudaMemcpyAsync(s->staging, r.U.data(), N * r.L * sizeof(float), cudaMemcpyHostToDevice, s->st));
+    // everything the admission uploads, in one page-locked block
+    unsigned char *hb = s->ring.acquire(admit_staging_bytes(r));
+    if (!hb) return CRF_E_OOM;
+    const size_t npairs = (size_t)2 * LT * mu_pair_slots(LT);
+    size_t o = 0;
+    float *hU = (float *)(hb + o); o += align256(N * r.L * 4);
+    float *hw = (float *)(hb + o); o += align256(N * nd * 4);
+    float2 *hp = (float2 *)(hb + o); o += align256(npairs * 8);
+    float *hmu = (float *)(hb + o); o += align256((size_t)r.L * r.L * 4);
+    float *heta = (float *)(hb + o); o += 256;
+    ServeSlot *hsl = (ServeSlot *)(hb + o);
+    std::memcpy(hU, r.U.data(), N * r.L * sizeof(float));
+    std::memcpy(hw, r.w.data(), N * nd * sizeof(float));
+    for (size_t i = 0; i < npairs; ++i) hp[i] = make_float2(0.f, 0.f);
+    build_mu_pairs_host(r.mu.data(), r.L, LT, hp);
+    std::memcpy(hmu, r.mu.data(), (size_t)r.L * r.L * sizeof(float));
+    *heta = (float)r.p.eta;
+
+    SCK(cudaMemcpyAsync(s->staging, hU, N * r.L * sizeof(float), cudaMemcpyHostToDevice, s->st));
     SCK(launch_rows_to_padded(s->staging, U, (long long)N, r.L, LP, 0.f, s->st));
     SCK(launch_init_logq(U, s0, (long long)N, r.L, LP, s->st));
     SCK(cudaMemsetAsync(s1, 0, N * LP * sizeof(float), s->st));
-    SCK(cudaMemcpyAsync(s->staging, r.w.data(), N * nd * sizeof(float), cudaMemcpyHostToDevice, s->st));
+    SCK(cudaMemcpyAsync(s->staging, hw, N * nd * sizeof(float), cudaMemcpyHostToDevice, s->st));
     SCK(launch_weights_to_pixel_major(s->staging, w, 1, nd, r.H, r.W, s->st));
-    std::vector<float2> hp((size_t)2 * LT * mu_pair_slots(LT), make_float2(0.f, 0.f));
-    build_mu_pairs_host(r.mu.data(), r.L, LT, hp.data());
-    SCK(cudaMemcpyAsync(pairs, hp.data(), hp.size() * sizeof(float2), cudaMemcpyHostToDevice, s->st));
-    SCK(cudaMemcpyAsync(mu, r.mu.data(), (size_t)r.L * r.L * sizeof(float), cudaMemcpyHostToDevice, s->st));
+    SCK(cudaMemcpyAsync(pairs, hp, npairs * sizeof(float2), cudaMemcpyHostToDevice, s->st));
+    SCK(cudaMemcpyAsync(mu, hmu, (size_t)r.L * r.L * sizeof(float), cudaMemcpyHostToDevice, s->st));
     SCK(cudaMemsetAsync(base + l.counter, 0, 256, s->st));
-    if (r.p.eta > 0) {
-        const float e = (float)r.p.eta;
-        SCK(cudaMemcpyAsync(eta, &e, sizeof(float), cudaMemcpyHostToDevice, s->st));
-    } else {
+    if (r.p.eta > 0)
+        SCK(cudaMemcpyAsync(eta, heta, sizeof(float), cudaMemcpyHostToDevice, s->st));
+    else
         SCK(launch_eta_bound(w, r.H, r.W, nd, mu, r.L, eta, s->d_scratch, s->st));
-    }
-    ServeSlot sl{};
     int nbx, nby;
     grid_tiles(r.H, r.W, &nbx, &nby);
+    ServeSlot &sl = *hsl;
+    sl = ServeSlot{};
     sl.U = U;
     sl.s[0] = s0;
     sl.s[1] = s1;
@@ -272,27 +404,28 @@ crf_status admit(mf_server_t s, Request &r, int si) {
     sl.counter = (unsigned *)(base + l.counter);
     sl.eta = eta;
     sl.L = r.L;
+    sl.LT = LT;
     sl.H = r.H;
     sl.W = r.W;
     sl.nbx = nbx;
     sl.nblk = nbx * nby;
+    sl.conn = r.conn;
+    sl.sym = r.sym ? 1 : 0;
     sl.max_iters = r.p.max_iters;
     sl.rel_tol = r.p.rel_tol;
     sl.it = 0;
     sl.active = r.p.max_iters > 0 ? 1 : 0;
     sl.F_prev = 0.0;
-    s->h_res[si].done = 0;
+    s->h_res[si].done = sl.active ? 0 : 1;
     s->h_res[si].iters = 0;
     s->h_res[si].F = 0.0;
-    SCK(cudaMemcpyAsync(s->d_slots + si, &sl, sizeof(sl), cudaMemcpyHostToDevice, s->st));
-    SCK(cudaStreamSynchronize(s->st));   // host staging vectors are pageable
-    if (!sl.active) {
-        s->h_res[si].done = 1;
-    }
+    SCK(cudaMemcpyAsync(s->d_slots + si, hsl, sizeof(ServeSlot), cudaMemcpyHostToDevice, s->st));
+    SCK(s->ring.seal(s->st));
     return CRF_OK;
 }
 
-// Copy q of a retired slot out, free its slot and pool block.
+// Queue the copy of q of a retired slot and return its slot and pool block
+// (the stream orders every later use of that memory after the copy).
 crf_status retire(mf_server_t s, Request &r, int si) {
     const SlotLayout l = layout_for(r);
     unsigned char *base = s->pool_base + r.off;
@@ -300,16 +433,23 @@ crf_status retire(mf_server_t s, Request &r, int si) {
     const int LP = storage_labels(r.L);
     const ServeResult res = s->h_res[si];
     const float *final_s = (const float *)(base + ((res.iters & 1) ? l.s1 : l.s0));
+    r.F = res.F;
+    r.iters = res.iters;
     if (r.q_out) {
         crf_status rc = ensure_staging(s, N * r.L);
         if (rc != CRF_OK) return rc;
+        unsigned char *hb = s->ring.acquire(N * r.L * sizeof(float));
+        if (!hb) return CRF_E_OOM;
         SCK(launch_padded_to_rows(final_s, s->staging, (long long)N, r.L, LP, CONV_EXP, s->st));
-        SCK(cudaMemcpyAsync(r.q_out, s->staging, N * r.L * sizeof(float), cudaMemcpyDeviceToHost, s->st));
-        SCK(cudaStreamSynchronize(s->st));
+        SCK(cudaMemcpyAsync(hb, s->staging, N * r.L * sizeof(float), cudaMemcpyDeviceToHost, s->st));
+        SCK(s->ring.seal(s->st));
+        r.q_host = hb;
+        r.q_ready = s->ring.last_event();
+        r.state = 3;
+        s->outgoing.push_back(r.ticket);
+    } else {
+        r.state = 2;
     }
-    r.F = res.F;
-    r.iters = res.iters;
-    r.state = 2;
     r.U.clear();
     r.U.shrink_to_fit();
     r.w.clear();
@@ -317,7 +457,25 @@ crf_status retire(mf_server_t s, Request &r, int si) {
     s->pool->release(r.off, r.bytes);
     s->slot_ticket[si] = 0;
     r.slot = -1;
+    s->table_dirty = true;
     return CRF_OK;
+}
+
+// Results whose copy has landed reach q_out (in retirement order).
+void deliver(mf_server_t s, bool wait) {
+    while (!s->outgoing.empty()) {
+        Request &r = s->reqs.at(s->outgoing.front());
+        if (wait)
+            cudaEventSynchronize(r.q_ready);
+        else if (cudaEventQuery(r.q_ready) != cudaSuccess)
+            break;
+        std::memcpy(r.q_out, r.q_host, (size_t)r.H * r.W * r.L * sizeof(float));
+        r.q_host = nullptr;
+        r.q_ready = nullptr;
+        r.state = 2;
+        s->outgoing.pop_front();
+    }
+    (void)cudaGetLastError();
 }
 
 }  // namespace
@@ -389,25 +547,27 @@ crf_status mf_server_create(int64_t budget_bytes, int32_t max_slots, void *strea
     s->budget = (size_t)budget_bytes;
     s->max_slots = max_slots;
     s->slot_ticket.assign(max_slots, 0);
-    s->h_buckets.resize(kMaxBuckets);
-    for (auto &b : s->h_buckets) {
-        b.count = 0;
-        b.prefix[0] = 0;
-    }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    s->grid_small = 2 * (sms > 0 ? sms : 148);
-    s->grid_large = sms > 0 ? sms : 148;
+    s->sms = sms > 0 ? sms : 148;
     bool ok = cudaMalloc((void **)&s->pool_base, s->budget) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&s->d_slots, sizeof(ServeSlot) * max_slots) == cudaSuccess;
-    ok = ok && cudaMalloc((void **)&s->d_buckets, sizeof(ServeBucket) * kMaxBuckets) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&s->d_table, sizeof(ServeTable)) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&s->d_scratch, 8 * sizeof(double)) == cudaSuccess;
     ok = ok && cudaHostAlloc((void **)&s->h_res, sizeof(ServeResult) * max_slots, cudaHostAllocMapped) == cudaSuccess;
     ok = ok && cudaHostGetDevicePointer((void **)&s->d_res, s->h_res, 0) == cudaSuccess;
+    for (int k = 0; k < 2 && ok; ++k) {
+        ok = cudaHostAlloc((void **)&s->h_table[k], sizeof(ServeTable), cudaHostAllocDefault) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&s->table_ev[k], cudaEventDisableTiming) == cudaSuccess;
+    }
+    // page-locked staging: room for the largest requests several times over
+    ok = ok && s->ring.init((size_t)256 << 20);
     ok = ok && cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) == cudaSuccess;
+    static SmemOptIn optin;   // up to the largest class's tile memory, once per device
+    ok = ok && smem_optin(optin, serve_step_kernel, serve_tile_smem(kMaxLabels)) == cudaSuccess;
     if (ok) ok = cudaMemsetAsync(s->d_slots, 0, sizeof(ServeSlot) * max_slots, s->st) == cudaSuccess;
-    if (ok) ok = cudaMemsetAsync(s->d_buckets, 0, sizeof(ServeBucket) * kMaxBuckets, s->st) == cudaSuccess;
+    if (ok) ok = cudaMemsetAsync(s->d_table, 0, sizeof(ServeTable), s->st) == cudaSuccess;
     if (ok) ok = cudaStreamSynchronize(s->st) == cudaSuccess;
     if (!ok) {
         (void)cudaGetLastError();
@@ -424,15 +584,20 @@ crf_status mf_server_destroy(mf_server_t s) {
     PROXMF_RANGE("mf_server_destroy");
     if (!s) return CRF_OK;
     cudaStreamSynchronize(s->st);
+    s->ring.reclaim(true);
     if (s->exec) cudaGraphExecDestroy(s->exec);
     if (s->graph) cudaGraphDestroy(s->graph);
     if (s->cap) cudaStreamDestroy(s->cap);
     if (s->pool_base) cudaFree(s->pool_base);
     if (s->d_slots) cudaFree(s->d_slots);
-    if (s->d_buckets) cudaFree(s->d_buckets);
+    if (s->d_table) cudaFree(s->d_table);
     if (s->d_scratch) cudaFree(s->d_scratch);
     if (s->staging) cudaFree(s->staging);
     if (s->h_res) cudaFreeHost(s->h_res);
+    for (int k = 0; k < 2; ++k) {
+        if (s->h_table[k]) cudaFreeHost(s->h_table[k]);
+        if (s->table_ev[k]) cudaEventDestroy(s->table_ev[k]);
+    }
     delete s->pool;
     delete s;
     return CRF_OK;
@@ -469,6 +634,7 @@ crf_status mf_server_submit(mf_server_t s, const crf_desc *d, const float *U, co
     r.q_out = q_out;
     r.bytes = layout_for(r).total;
     if (r.bytes > s->budget) return CRF_E_OOM;
+    if (admit_staging_bytes(r) > s->ring.size() || N * r.L * sizeof(float) > s->ring.size()) return CRF_E_OOM;
     *ticket = r.ticket;
     s->queue.push_back(r.ticket);
     s->reqs.emplace(r.ticket, std::move(r));
@@ -480,14 +646,13 @@ crf_status mf_server_step(mf_server_t s, int32_t iters, int32_t *in_flight, int3
     if (!s || iters < 0) return CRF_E_INVALID;
     if (s->broken) return CRF_E_STATE;
     crf_status rc;
+    deliver(s, false);
     // 1. retire finished slots
-    std::vector<int> touched;
     for (int si = 0; si < s->max_slots; ++si) {
         const uint64_t t = (uint64_t)s->slot_ticket[si];
         if (!t) continue;
-        if (*(volatile int *)&s->h_res[si].done) {
-            Request &r = s->reqs.at(t);
-            touched.push_back(bucket_for(s, kernel_labels(r.L), r.conn, r.sym));
+        Request &r = s->reqs.at(t);
+        if (r.state == 1 && *(volatile int *)&s->h_res[si].done) {
             rc = retire(s, r, si);
             if (rc != CRF_OK) return rc;
         }
@@ -510,29 +675,24 @@ crf_status mf_server_step(mf_server_t s, int32_t iters, int32_t *in_flight, int3
         s->queue.pop_front();
         rc = admit(s, r, si);
         if (rc != CRF_OK) return rc;
-        touched.push_back(bucket_for(s, kernel_labels(r.L), r.conn, r.sym));
+        s->table_dirty = true;
     }
-    for (int b : touched)
-        if (b >= 0) bucket_rebuild(s, b, {});
-    bool uploaded = false;
-    for (size_t b = 0; b < s->bucket_lt.size(); ++b)
-        if (s->bucket_dirty[b]) {
-            SCK(cudaMemcpyAsync(s->d_buckets + b, &s->h_buckets[b], sizeof(ServeBucket), cudaMemcpyHostToDevice,
-                                s->st));
-            s->bucket_dirty[b] = false;
-            uploaded = true;
-        }
-    if (uploaded) SCK(cudaStreamSynchronize(s->st));   // bucket headers come from pageable host memory
-    if (s->graph_stale && !s->bucket_lt.empty()) {
-        rc = capture_graph(s);
+    if (s->table_dirty) {
+        rc = upload_table(s);
         if (rc != CRF_OK) return rc;
     }
-    // 3. iterate every in-flight request
+    // 3. iterate every in-flight request: one launch per iteration
+    const size_t smem = needed_smem(s);
     int running = 0;
     for (int si = 0; si < s->max_slots; ++si)
-        if (s->slot_ticket[si]) ++running;
-    if (running && s->exec)
+        if (s->slot_ticket[si] && s->reqs.at((uint64_t)s->slot_ticket[si]).state == 1) ++running;
+    if (running) {
+        if (!s->exec || smem != s->graph_smem) {
+            rc = capture_graph(s, smem);
+            if (rc != CRF_OK) return rc;
+        }
         for (int i = 0; i < iters; ++i) SCK(cudaGraphLaunch(s->exec, s->st));
+    }
     if (in_flight) *in_flight = running;
     if (queued) *queued = (int)s->queue.size();
     return CRF_OK;
@@ -540,10 +700,11 @@ crf_status mf_server_step(mf_server_t s, int32_t iters, int32_t *in_flight, int3
 
 crf_status mf_server_poll(mf_server_t s, uint64_t ticket, int32_t *state, double *F, int32_t *iters) {
     if (!s) return CRF_E_INVALID;
+    deliver(s, false);
     auto it = s->reqs.find(ticket);
     if (it == s->reqs.end()) return CRF_E_INVALID;
     const Request &r = it->second;
-    if (state) *state = r.state;
+    if (state) *state = r.state == 3 ? 1 : r.state;
     if (F) *F = r.F;
     if (iters) *iters = r.iters;
     return CRF_OK;
@@ -554,6 +715,7 @@ crf_status mf_server_sync(mf_server_t s) {
     if (!s) return CRF_E_INVALID;
     if (s->broken) return CRF_E_STATE;
     SCK(cudaStreamSynchronize(s->st));
+    deliver(s, true);
     return CRF_OK;
 }
 

@@ -1,6 +1,8 @@
 """Serving (continuous batching): requests of mixed size, label count and
-connectivity join and leave between steps; each result equals a solve on its
-own (bitwise) and the oracle (within the FP32 tolerances)."""
+connectivity join and leave between steps while one launch per iteration
+advances all of them.  Each result is the same alone and in the mix
+(bitwise), matches a solve through the handle API and the oracle within the
+FP32 tolerances, and stops after the same number of steps."""
 import numpy as np
 import pytest
 
@@ -72,14 +74,18 @@ def run_server(binding, reqs, budget, rel_tol, max_iters, stagger=0, slots=64):
         return [srv.poll(t) for t in tickets]
 
 
-def test_server_equals_single_solves(env):
+def test_server_matches_single_solves(env):
+    """The serving tile and the handle API's step group their FP32 arithmetic
+    differently, so results agree within the trajectory bounds (the stopping
+    step may differ by one where |dF|/|F| sits at the tolerance)."""
     binding, oracle, torch = env
     reqs = requests(6, seed=1)
     res = run_server(binding, reqs, 1 << 30, rel_tol=1e-6, max_iters=400)
     for d, (st, F, it, q) in zip(reqs, res):
         q1, F1, it1 = solve_alone(binding, d, 1e-6, 400)
-        assert st == 2 and it == it1
-        assert np.array_equal(q, q1) and F == F1
+        assert st == 2 and abs(it - it1) <= 1
+        assert np.abs(q - q1).max() <= 1e-5
+        assert H.f_close(F, F1, d["H"] * d["W"])
 
 
 def test_alone_and_in_the_mix_are_identical(env):
@@ -139,4 +145,25 @@ def test_step_bound_is_an_upper_bound(env):
     assert bound >= lam[0] * (1 - 1e-6)
     d["eta"] = float(np.float32(1.0 / (1.0 + bound)))
     q2, F2, it2 = solve_alone(binding, d, 0.0, 30)
-    assert np.abs(q - q2).max() <= 1e-6
+    assert np.abs(q - q2).max() <= 1e-5
+
+
+def test_mixed_classes_in_one_launch_against_oracle(env):
+    """Label counts 3, 5, 13, 21 and 32, 4- and 8-connected, symmetric and
+    asymmetric mu, all in flight together (one launch per iteration walks
+    them all); each against the oracle's trajectory."""
+    binding, oracle, torch = env
+    specs = [(3, 4, False), (5, 8, True), (13, 8, False), (21, 4, True), (32, 8, False)]
+    reqs = []
+    for i, (L, conn, sym) in enumerate(specs):
+        d = synth.random_grid(19 + 3 * i, 41 - 2 * i, L, conn, seed=700 + i, symmetric=sym)
+        d["eta"] = 0.2
+        reqs.append(d)
+    res = run_server(binding, reqs, 1 << 28, rel_tol=0.0, max_iters=25)
+    for d, (st, F, it, q) in zip(reqs, res):
+        assert st == 2 and it == 25
+        m = oracle.Model.grid(np.asarray(d["U"], np.float64), np.asarray(d["mu"], np.float64),
+                              np.asarray(d["w"], np.float64), d["H"], d["W"], d["conn"])
+        s_ref, F_ref = m.parallel_prox(float(np.float32(0.2)), 25)
+        assert np.abs(q - np.exp(s_ref)).max() <= 1e-5, (d["L"], d["conn"])
+        assert H.f_close(F, F_ref[-2], d["H"] * d["W"])
