@@ -41,7 +41,7 @@ struct crf_s {
     bool dense = false;
     int N = 0;                   // variables per instance
     float *K32 = nullptr;        // [B][N][N]
-    __nv_bfloat16 *K16 = nullptr;  // [B][N][N] (tensor-core form)
+    __nv_bfloat16 *K16 = nullptr;  // [B][tiles][chunks][128 x 64] swizzled blocks (tensor-core form)
     float *q32[2] = {nullptr, nullptr};            // [B][N][LP] + padding
     __nv_bfloat16 *qt16[2] = {nullptr, nullptr};   // [B][32][N]
     float *feats = nullptr;      // [B][N][5]
@@ -596,7 +596,7 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
             h->bf16 = true;
             const size_t pitch = dense_tc_pitch(h->N);
             const size_t tiles = (size_t)h->B * dense_tc_tiles(h->N);
-            ok = ok && dalloc(&h->K16, (size_t)h->B * h->N * pitch) == cudaSuccess;
+            ok = ok && dalloc(&h->K16, tiles * 128 * pitch) == cudaSuccess;   // every instance's tiles x 128 rows
             ok = ok && dalloc(&h->qt16[0], (size_t)h->B * 32 * pitch) == cudaSuccess;
             ok = ok && dalloc(&h->qt16[1], (size_t)h->B * 32 * pitch) == cudaSuccess;
             ok = ok && dalloc(&h->tcb.split_part, tiles * 2 * 128 * 32) == cudaSuccess;

@@ -76,6 +76,45 @@ __global__ void dense_kernel_build_kernel(const float *__restrict__ feats, T *__
     }
 }
 
+// The BF16 copy of K for the tensor-core step, in blocks of 128 rows by 64
+// columns: block (tile, chunk) of instance b starts at element
+// ((b * nchunk + chunk) * ntiles + tile) * 8192 (chunk-major, so the blocks
+// that all row tiles read at the same moment lie side by side in memory and
+// spread over every memory channel) and holds row r, column k at
+// byte r * 128 + (((k / 8) ^ (r % 8)) * 16) + (k % 8) * 2 -- the 128-byte
+// swizzled K-major layout the MMA reads from shared memory, so one block is
+// one contiguous 16 KiB bulk copy.  Rows and columns past N are zero.
+__global__ void dense_kernel_build_tiled_kernel(const float *__restrict__ feats, __nv_bfloat16 *__restrict__ K,
+                                                int N, int ntiles, int nchunk, float inv2p, float inv2c) {
+    const int b = blockIdx.z;
+    const int i = blockIdx.y;                 // row, < ntiles * 128
+    const float *f = feats + (size_t)b * N * 5;
+    const bool row_ok = i < N;
+    float xi = 0.f, yi = 0.f, ri = 0.f, gi = 0.f, bi = 0.f;
+    if (row_ok) {
+        xi = f[i * 5 + 0];
+        yi = f[i * 5 + 1];
+        ri = f[i * 5 + 2];
+        gi = f[i * 5 + 3];
+        bi = f[i * 5 + 4];
+    }
+    const int tile = i / 128, r = i % 128;
+    uint8_t *tb = reinterpret_cast<uint8_t *>(K) + ((size_t)b * nchunk * ntiles + tile) * 16384 + (size_t)r * 128;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nchunk * 64; j += gridDim.x * blockDim.x) {
+        float v = 0.f;
+        if (row_ok && j < N && j != i) {
+            const float dx = xi - f[j * 5 + 0], dy = yi - f[j * 5 + 1];
+            const float dr = ri - f[j * 5 + 2], dg = gi - f[j * 5 + 3], db = bi - f[j * 5 + 4];
+            const float p2 = dx * dx + dy * dy, c2 = dr * dr + dg * dg + db * db;
+            v = expf(-p2 * inv2p - c2 * inv2c);
+        }
+        const int chunk = j / 64, k = j % 64;
+        *reinterpret_cast<__nv_bfloat16 *>(tb + (size_t)chunk * ntiles * 16384 + (((k >> 3) ^ (r & 7)) << 4) +
+                                           (k & 7) * 2) =
+            __float2bfloat16_rn(v);
+    }
+}
+
 // q = exp(log q) as FP32 rows [B][N][LP] (padding 0) and, if qt16 is given,
 // BF16 label-major [B][32][pitch] (labels >= L zero) for the tensor-core form.
 __global__ void dense_export_q_kernel(const float *__restrict__ s, float *__restrict__ q32,
@@ -156,7 +195,7 @@ __global__ void __launch_bounds__(kDT, 1) dense_step_f32_kernel(const __grid_con
     float *Ks = dsm;                                     // [kStages][kDR][kKsRow]  (row-major K tile)
     float *Qs = Ks + (size_t)kStages * kDR * kKsRow;     // [kStages][kDK][LP]
     __shared__ __align__(16) float Sred[kDR][LP + 1];
-    __shared__ float mus[kMaxLabels * kMaxLabels];
+    __shared__ __align__(16) float mus[kMaxLabels * kMaxLabels];   // mu^T, zero-padded
     __shared__ double red[kDT / 32];
     __shared__ int is_last;
 
@@ -180,7 +219,7 @@ __global__ void __launch_bounds__(kDT, 1) dense_step_f32_kernel(const __grid_con
         return;
     }
 
-    for (int i = tid; i < L * L; i += kDT) mus[(i / L) * kMaxLabels + (i % L)] = a.mu[i];
+    load_mu_transposed(mus, a.mu, L, tid, kDT);
 
     // micro-tile: rows ig + 16 r (r < 4), label columns 6*cg .. 6*cg+5, the
     // four k of slice ks of each chunk
@@ -354,8 +393,11 @@ cudaError_t launch_dense_kernel_build(const float *feats, float *K32, __nv_bfloa
     const float inv2c = (float)(1.0 / (2.0 * theta_rgb * theta_rgb));
     dim3 grid((N + 255) / 256 < 8 ? (N + 255) / 256 : 8, N, B);
     if (K32) dense_kernel_build_kernel<float><<<grid, 256, 0, st>>>(feats, K32, N, N, inv2p, inv2c);
-    if (K16)
-        dense_kernel_build_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(feats, K16, N, dense_tc_pitch(N), inv2p, inv2c);
+    if (K16) {
+        const int ntiles = dense_tc_tiles(N), nchunk = dense_tc_pitch(N) / 64;
+        dim3 g2((nchunk * 64 + 255) / 256 < 8 ? (nchunk * 64 + 255) / 256 : 8, ntiles * 128, B);
+        dense_kernel_build_tiled_kernel<<<g2, 256, 0, st>>>(feats, K16, N, ntiles, nchunk, inv2p, inv2c);
+    }
     return cudaGetLastError();
 }
 

@@ -9,11 +9,14 @@
 // and half of the k range (split-K 2, so N = 9216 gives 144 CTAs for the 152
 // SMs; a four-way split with two CTAs per SM measured slower, its serial
 // epilogue tail growing more than the streaming overlap gained).  Warp 0
-// lane 0 issues TMA loads of 128 x 64 BF16 tiles of K and 32 x 64 tiles of
-// Q^T (both K-major, 128-byte swizzle) into a 6-stage ring
-// guarded by mbarriers; warp 1 lane 0 issues tcgen05.mma (M=128, N=32, K=16,
-// kind::f16) into a 32-column TMEM accumulator and releases each stage with
-// tcgen05.commit.  The four warps then read the accumulator rows with
+// lane 0 fills a 10-stage ring guarded by mbarriers: each stage is one
+// 16 KiB bulk copy of a 128 x 64 block of K, which the library stores
+// pre-tiled and already in the 128-byte-swizzled K-major layout (so a stage
+// is one contiguous read from HBM instead of 128 rows of 128 bytes), and a
+// TMA load of the 32 x 64 tile of Q^T (128-byte swizzle); warp 1 lane 0
+// issues tcgen05.mma (M=128, N=32, K=16, kind::f16) into a 32-column TMEM
+// accumulator and releases each stage with tcgen05.commit.  The four warps
+// then read the accumulator rows with
 // tcgen05.ld (warp w owns TMEM lanes 32w..32w+31).  The k ranges of a tile
 // meet in global memory: the last CTA to finish sums the partials in range
 // order (so the result does not depend on which one finishes last) and runs
@@ -39,7 +42,7 @@ namespace {
 constexpr int kTM = 128;                 // rows per tile (MMA M)
 constexpr int kTN = 32;                  // label columns (MMA N)
 constexpr int kTK = 64;                  // k per stage (128 bytes of BF16)
-constexpr int kStages = 6;
+constexpr int kStages = 10;
 constexpr int kStageA = kTM * kTK * 2;   // 16 KiB
 constexpr int kStageB = kTN * kTK * 2;   // 4 KiB
 constexpr int kStageBytes = kStageA + kStageB;
@@ -52,6 +55,7 @@ using namespace tc;
 constexpr uint32_t kIdesc = idesc_bf16(kTM, kTN);
 
 struct DenseTcArgs {
+    const uint8_t *K16;      // [B][nchunk][ntiles] blocks of 128 x 64 BF16, 128-byte swizzled (dense.cu)
     const float *s_in;
     const float *U;
     float *s_out;
@@ -72,12 +76,11 @@ struct DenseTcArgs {
 
 template <int LP>
 __global__ void __launch_bounds__(kThreads, 1)
-dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmK, const __grid_constant__ CUtensorMap tmQ,
-                     const __grid_constant__ DenseTcArgs a) {
+dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ DenseTcArgs a) {
     extern __shared__ __align__(1024) uint8_t dsm[];
     __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], tmem_bar;
     __shared__ uint32_t tmem_slot;
-    __shared__ float mus[kMaxLabels * kMaxLabels];
+    __shared__ __align__(16) float mus[kMaxLabels * kMaxLabels];   // mu^T, zero-padded
     __shared__ double red[kThreads / 32];
     __shared__ int is_second, is_last, abort_flag;
 
@@ -107,7 +110,7 @@ dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmK, const __grid_const
     }
 
     uint8_t *ring = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
-    for (int i = tid; i < L * L; i += kThreads) mus[(i / L) * kMaxLabels + (i % L)] = a.mu[i];
+    load_mu_transposed(mus, a.mu, L, tid, kThreads);
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full_bar[s], 1);
@@ -135,7 +138,8 @@ dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmK, const __grid_const
             uint8_t *sa = ring + s * kStageBytes;
             mbar_expect_tx(&full_bar[s], kStageBytes);
             const int kc = (c_begin + c) * kTK;
-            tma_load_2d(sa, &tmK, &full_bar[s], kc, b * N + row0);
+            const uint8_t *blk = a.K16 + (((size_t)b * a.nchunk + (c_begin + c)) * a.ntiles + tile) * kStageA;
+            bulk_load(sa, blk, kStageA, &full_bar[s]);
             tma_load_2d(sa + kStageA, &tmQ, &full_bar[s], kc, b * 32);
             ++issued;
         }
@@ -198,9 +202,15 @@ dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmK, const __grid_const
 #pragma unroll
         for (int i = 0; i < 32; ++i) S[i] = 0.f;
         for (int sp = 0; sp < nsplit; ++sp) {
-            const float *part = a.split_part + ((tile_id * kSplit + sp) * kTM + r) * 32;
+            const float4 *part = reinterpret_cast<const float4 *>(a.split_part + ((tile_id * kSplit + sp) * kTM + r) * 32);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) S[i] += __ldcg(part + i);
+            for (int i = 0; i < 8; ++i) {
+                const float4 v = __ldcg(part + i);
+                S[4 * i] += v.x;
+                S[4 * i + 1] += v.y;
+                S[4 * i + 2] += v.z;
+                S[4 * i + 3] += v.w;
+            }
         }
         if (tid == 0) a.tile_count[tile_id] = 0u;
     }
@@ -285,13 +295,12 @@ int dense_tc_tiles(int N) { return (N + kTM - 1) / kTM; }
 int dense_tc_pitch(int N) { return (N + kTK - 1) / kTK * kTK; }
 
 cudaError_t launch_dense_step_tc(const DenseStepLaunch &l, const DenseTcBuffers &tb, cudaStream_t st) {
-    CUtensorMap tmK, tmQ;
+    CUtensorMap tmQ;
     const int Np = dense_tc_pitch(l.N);
-    cudaError_t e = encode_2d(&tmK, l.K16, (long long)l.B * l.N, Np, kTM);
-    if (e != cudaSuccess) return e;
-    e = encode_2d(&tmQ, l.qt_in, (long long)l.B * 32, Np, kTN);
+    cudaError_t e = encode_2d(&tmQ, l.qt_in, (long long)l.B * 32, Np, kTN);
     if (e != cudaSuccess) return e;
     DenseTcArgs a;
+    a.K16 = reinterpret_cast<const uint8_t *>(l.K16);
     a.s_in = l.s_in;
     a.U = l.U;
     a.s_out = l.s_out;
@@ -324,7 +333,7 @@ cudaError_t launch_dense_step_tc(const DenseStepLaunch &l, const DenseTcBuffers 
     case LPV:                                                                                                 \
         e = cudaFuncSetAttribute(dense_step_tc_kernel<LPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                       \
-        dense_step_tc_kernel<LPV><<<grid, kThreads, smem, st>>>(tmK, tmQ, a);                                 \
+        dense_step_tc_kernel<LPV><<<grid, kThreads, smem, st>>>(tmQ, a);                                      \
         break;
         PROXMF_TC_CASE(2)
         PROXMF_TC_CASE(4)

@@ -66,6 +66,15 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// Bulk copy of `bytes` contiguous bytes (16-byte aligned, a multiple of 16)
+// from global to shared memory, completing on the mbarrier's transaction count.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // Shared-memory matrix descriptor (descriptor version 1): start address,
 // leading / stride byte offsets and the layout type in bits 61-63
 // (0: no swizzle, 2: 128-byte swizzle).
