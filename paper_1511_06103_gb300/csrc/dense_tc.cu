@@ -93,23 +93,10 @@ dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_const
     const int c_begin = (a.nchunk * split) / nsplit, c_end = (a.nchunk * (split + 1)) / nsplit;
     const int nc = c_end - c_begin;
 
-    if (a.done != nullptr && a.done[b] != 0) {
-        // stopping rule met: carry the state through (split 0 copies)
-        if (a.update && split == 0)
-            for (int idx = tid; idx < kTM * LP; idx += kThreads) {
-                const int r = row0 + idx / LP;
-                if (r < N) {
-                    const size_t o = ((size_t)b * N + r) * LP + idx % LP;
-                    a.s_out[o] = a.s_in[o];
-                    const float q = idx % LP < L ? __expf(a.s_in[o]) : 0.f;
-                    a.q_out[o] = q;
-                    if (a.qt_out) a.qt_out[((size_t)b * 32 + idx % LP) * a.Np + r] = __float2bfloat16_rn(q);
-                }
-            }
-        return;
-    }
-
     uint8_t *ring = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
+    // The next step may be launched now (programmatic dependent launch); it
+    // takes the SMs this launch frees.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     load_mu_transposed(mus, a.mu, L, tid, kThreads);
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -127,6 +114,43 @@ dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_const
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = tmem_slot;
+    auto kblock = [&](int c) {
+        return a.K16 + (((size_t)b * a.nchunk + (c_begin + c)) * a.ntiles + tile) * kStageA;
+    };
+    // K does not change between steps: the first ring's worth of its blocks
+    // is requested before waiting for the previous step (which writes Q, the
+    // state and the stopping flags).  Their barriers only count the bytes
+    // here; the arrival comes with the Q tile below.
+    const int npre = nc < kStages ? nc : kStages;
+    if (warp == 0 && lane == 0)
+        for (int c = 0; c < npre; ++c) {
+            mbar_expect_tx_only(&full_bar[c], kStageA);
+            bulk_load(ring + c * kStageBytes, kblock(c), kStageA, &full_bar[c]);
+        }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+
+    if (a.done != nullptr && a.done[b] != 0) {
+        // stopping rule met: carry the state through (split 0 copies)
+        if (a.update && split == 0)
+            for (int idx = tid; idx < kTM * LP; idx += kThreads) {
+                const int r = row0 + idx / LP;
+                if (r < N) {
+                    const size_t o = ((size_t)b * N + r) * LP + idx % LP;
+                    a.s_out[o] = a.s_in[o];
+                    const float q = idx % LP < L ? __expf(a.s_in[o]) : 0.f;
+                    a.q_out[o] = q;
+                    if (a.qt_out) a.qt_out[((size_t)b * 32 + idx % LP) * a.Np + r] = __float2bfloat16_rn(q);
+                }
+            }
+        if (warp == 0 && lane == 0)
+            for (int c = 0; c < npre; ++c) {   // no copy into this CTA's memory outlives it
+                mbar_arrive(&full_bar[c]);
+                mbar_wait(&full_bar[c], 0, a.status);
+            }
+        __syncthreads();
+        if (warp == 0) tmem_dealloc(tmem, kTN);
+        return;
+    }
 
     if (warp == 0 && lane == 0 && nc > 0) {
         // producer: TMA loads into the ring
@@ -136,17 +160,23 @@ dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_const
             if (c >= kStages && !mbar_wait(&empty_bar[s], ((c / kStages) - 1) & 1, a.status)) break;
             if (abort_flag) break;
             uint8_t *sa = ring + s * kStageBytes;
-            mbar_expect_tx(&full_bar[s], kStageBytes);
             const int kc = (c_begin + c) * kTK;
-            const uint8_t *blk = a.K16 + (((size_t)b * a.nchunk + (c_begin + c)) * a.ntiles + tile) * kStageA;
-            bulk_load(sa, blk, kStageA, &full_bar[s]);
+            if (c < npre) {
+                mbar_expect_tx(&full_bar[s], kStageB);   // K already requested
+            } else {
+                mbar_expect_tx(&full_bar[s], kStageBytes);
+                bulk_load(sa, kblock(c), kStageA, &full_bar[s]);
+            }
             tma_load_2d(sa + kStageA, &tmQ, &full_bar[s], kc, b * 32);
             ++issued;
         }
         if (issued < nc) {
             abort_flag = 1;
-            // drain: wait (bounded) for the copies already issued
-            for (int c = (issued > kStages ? issued - kStages : 0); c < issued; ++c)
+            // complete the prefetched stages never armed, then drain (bounded)
+            // the copies already issued
+            for (int c = issued; c < npre; ++c) mbar_arrive(&full_bar[c]);
+            const int last = issued > npre ? issued : npre;
+            for (int c = (last > kStages ? last - kStages : 0); c < last; ++c)
                 mbar_wait(&full_bar[c % kStages], (c / kStages) & 1, a.status);
         }
     } else if (warp == 1 && lane == 0 && nc > 0) {
@@ -328,12 +358,25 @@ cudaError_t launch_dense_step_tc(const DenseStepLaunch &l, const DenseTcBuffers 
     const int nsplit = a.nchunk >= 2 * kSplit ? kSplit : 1;
     dim3 grid(a.ntiles, nsplit, l.B);
     const size_t smem = (size_t)kStages * kStageBytes + 1024;
+    // programmatic dependent launch: the step may start while the previous
+    // one drains (the kernel waits before it reads anything a step writes)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl;
+    cfg.numAttrs = 1;
     switch (storage_labels(l.L)) {
 #define PROXMF_TC_CASE(LPV)                                                                                   \
     case LPV:                                                                                                 \
         e = cudaFuncSetAttribute(dense_step_tc_kernel<LPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                       \
-        dense_step_tc_kernel<LPV><<<grid, kThreads, smem, st>>>(tmQ, a);                                      \
+        e = cudaLaunchKernelEx(&cfg, dense_step_tc_kernel<LPV>, tmQ, a);                                      \
+        if (e != cudaSuccess) return e;                                                                       \
         break;
         PROXMF_TC_CASE(2)
         PROXMF_TC_CASE(4)
