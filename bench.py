@@ -248,26 +248,36 @@ def run_reference(args, world, rank):
 # dram__bytes_read.sum + dram__bytes_write.sum of the headline step kernel per
 # instance-launch, from the ncu capture summarised in the named profile (4
 # instances per launch, larger than L2, divided by 4), with the SHA-256 of the
-# kernel source the counters were taken on.  Once that source changes the
+# kernel's source files the counters were taken on.  Once a source changes the
 # line reports traffic null (the counters no longer describe the kernel).
-GRID_TRAFFIC = {"per_instance": (218156544 + 71829504) // 4,
-                "source": "paper_1511_06103_gb300/csrc/grid_step.cuh",
-                "sha256": "",
+GRID_KERNEL = "grid_tma2_step_kernel<21,8>"
+GRID_TRAFFIC = {"per_instance": (218173184 + 73213696) // 4,
+                "sources": ["paper_1511_06103_gb300/csrc/grid_tma.cuh",
+                            "paper_1511_06103_gb300/csrc/grid_step.cuh",
+                            "paper_1511_06103_gb300/csrc/f32x2.cuh",
+                            "paper_1511_06103_gb300/csrc/tc_common.cuh",
+                            "paper_1511_06103_gb300/csrc/dfloat.cuh"],
+                "sha256": "5cef8b0fd642bde1bb07fd94ace20be0660b57de4cf8598c6636dcdc4d6e73c3",
                 "profile": "profiles/grid_prox_step_seg512_L21_conn8.md"}
+
+
+def grid_sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in GRID_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def grid_traffic(batch: int):
     """(traffic per launch or None, note) for the roofline object."""
-    import hashlib
-    path = os.path.join(ROOT, GRID_TRAFFIC["source"])
-    with open(path, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()
-    if sha != GRID_TRAFFIC["sha256"]:
-        return None, (f"null: {GRID_TRAFFIC['source']} changed since the ncu capture of "
+    if GRID_TRAFFIC["per_instance"] is None or grid_sources_sha() != GRID_TRAFFIC["sha256"]:
+        return None, (f"null: the step kernel's sources changed since the ncu capture of "
                       f"{GRID_TRAFFIC['profile']}")
     return batch * GRID_TRAFFIC["per_instance"], (
         f"dram read+write of one launch per instance from the ncu capture in {GRID_TRAFFIC['profile']} "
-        "(4 instances per launch, larger than L2, divided by 4); kernel source unchanged since (SHA-256)")
+        "(4 instances per launch, larger than L2, divided by 4); kernel sources unchanged since (SHA-256)")
 
 
 def algorithmic_bytes_per_launch() -> int:
@@ -666,7 +676,7 @@ def run_unrolled(args, dev, peak, precision=0):
             "roofline_forward": {"bound": "hbm", "achieved": fwd_bytes / (fwd_ms / 1000.0) / 1e9,
                                  "peak": peak, "unit": "GB/s",
                                  "frac": fwd_bytes / (fwd_ms / 1000.0) / 1e9 / peak,
-                                 "bytes_per_step": fwd_bytes, "kernel": "grid_prox_step_kernel<21,4,sym>"},
+                                 "bytes_per_step": fwd_bytes, "kernel": "grid_tma2_step_kernel<21,4>"},
             "launches_total": int(launches)}
 
 
@@ -1028,7 +1038,7 @@ def run_ours(args, world, rank, local):
             "latency_ms": {"p50": float(np.percentile(srt, 50)), "p99": float(np.percentile(srt, 99))},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
-                         "kernel": "grid_prox_step_kernel<21,8,sym>",
+                         "kernel": GRID_KERNEL,
                          "bytes_per_launch": bytes_launch, "avg_launch_ms": kern_ms,
                          "peak_kind": peak_kind},
             "cpu_baseline": cpu,

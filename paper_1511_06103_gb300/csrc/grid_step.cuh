@@ -747,6 +747,7 @@ grid_prox_step_kernel(const __grid_constant__ GridStepArgs a) {
 }  // namespace proxmf
 
 #include "grid_tma.cuh"
+#include "grid_tma_tc.cuh"
 
 namespace proxmf {
 
