@@ -57,7 +57,7 @@ struct crf_s {
     float gamma1 = 0.f, gamma2 = 0.f, eps = 0.f;
     float *eta_auto = nullptr;   // [B]
     double *Lambda = nullptr;    // [B]
-    double *partial = nullptr;   // [B][nblk] free-energy partials
+    double *partial = nullptr;   // [2][B][nblk] free-energy partials (two slots: deferred sums)
     unsigned *counter = nullptr; // [B]
     double *ftrace = nullptr;    // [B][trace_cap]
     double *fcur = nullptr;      // [B]
@@ -84,6 +84,7 @@ struct crf_s {
         double rel_tol, gamma1, gamma2, eps;
         const float *eta;
         cudaGraphExec_t exec;
+        int flushes;   // free-energy flush launches in the recorded loop
     };
     bool use_graphs = false;
     std::vector<GraphEntry> graphs;
@@ -293,7 +294,11 @@ DenseStepLaunch dense_args(crf_t h, const float *eta, int t, int update, double 
 // One step (update = 1) or a free-energy-only pass (update = 0) of either
 // model.  fp32 = 1 forces the FP32 form (refinement steps, and every
 // free-energy-only pass, which is evaluated with FP32 messages).
-cudaError_t launch_step(crf_t h, const float *eta, int t, int update, double rel_tol, int fp32 = 0) {
+// pending (step loops only): in/out, 1 while a deferring grid step's free
+// energy awaits its sum (see GridStepLaunch::defer); *flushes counts the
+// flush launches this adds.
+cudaError_t launch_step(crf_t h, const float *eta, int t, int update, double rel_tol, int fp32 = 0,
+                        int *pending = nullptr, int *flushes = nullptr) {
     if (h->sparse) {
         SparseStepLaunch a{};
         a.s_in = h->s[h->cur];
@@ -336,6 +341,19 @@ cudaError_t launch_step(crf_t h, const float *eta, int t, int update, double rel
     GridStepLaunch a = step_args(h, eta, t, update, rel_tol);
     if (!update || rel_tol <= 0) a.done = nullptr;
     a.tc = h->bf16 && update && !fp32;
+    if (pending) {
+        const int d = update && grid_step_uses_tma(a) ? 1 : 0;
+        if (*pending && !d) {
+            // the next kernel does not take the pending sum: flush it first
+            const cudaError_t e = launch_grid_f_flush(a, t - 1, h->st);
+            if (e != cudaSuccess) return e;
+            if (flushes) ++*flushes;
+            *pending = 0;
+        }
+        a.defer = d;
+        a.prev_pending = *pending;
+        *pending = d;
+    }
     return launch_grid_step(a, h->st);
 }
 
@@ -623,7 +641,7 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
     ok = ok && dalloc(&h->adapt_d, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->eta_auto, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->Lambda, h->B) == cudaSuccess;
-    ok = ok && dalloc(&h->partial, (size_t)h->B * h->nblk) == cudaSuccess;
+    ok = ok && dalloc(&h->partial, 2 * (size_t)h->B * h->nblk) == cudaSuccess;
     ok = ok && dalloc(&h->counter, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->fcur, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->done, h->B) == cudaSuccess;
@@ -976,15 +994,25 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
     if (rc != CRF_OK) return rc;
     const int nsteps = p->max_iters + refine;
     // the step loop: eager, or captured once per configuration and replayed
+    int loop_flushes = 0;   // free-energy flush launches of the loop
     auto body = [&]() -> cudaError_t {
         if (p->rel_tol > 0) {
             cudaError_t e = cudaMemsetAsync(h->done, 0, h->B * sizeof(int), h->st);
             if (e != cudaSuccess) return e;
         }
+        int pending = 0;
+        loop_flushes = 0;
         for (int t = 0; t < nsteps; ++t) {
-            cudaError_t e = launch_step(h, eta, t, 1, p->rel_tol, t >= p->max_iters);
+            cudaError_t e = launch_step(h, eta, t, 1, p->rel_tol, t >= p->max_iters, &pending, &loop_flushes);
             if (e != cudaSuccess) return e;
             h->cur ^= 1;
+        }
+        if (pending) {
+            GridStepLaunch a = step_args(h, eta, nsteps - 1, 1, p->rel_tol);
+            if (p->rel_tol <= 0) a.done = nullptr;
+            const cudaError_t e = launch_grid_f_flush(a, nsteps - 1, h->st);
+            if (e != cudaSuccess) return e;
+            ++loop_flushes;
         }
         return cudaSuccess;
     };
@@ -1002,8 +1030,10 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
         for (auto &g : h->graphs)
             if (g.iters == p->max_iters && g.refine == refine && g.cur == h->cur && g.rel_tol == p->rel_tol &&
                 g.eta == eta && g.rule == p->rule && g.gamma1 == p->gamma1 && g.gamma2 == p->gamma2 &&
-                g.eps == p->epsilon)
+                g.eps == p->epsilon) {
                 exec = g.exec;
+                loop_flushes = g.flushes;
+            }
         if (!exec) {
             const int cur0 = h->cur;
             if (!h->cap_st) CK(h, cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
@@ -1030,7 +1060,7 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
             }
             CK(h, e3);
             h->graphs.push_back({p->max_iters, refine, cur0, p->rule, p->rel_tol, p->gamma1, p->gamma2, p->epsilon,
-                                 eta, exec});
+                                 eta, exec, loop_flushes});
         }
     }
     if (h->profile) CK(h, cudaEventRecord(h->ev0, h->st));
@@ -1072,7 +1102,7 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
         h->rule_kernel = 0;
         CK(h, e);
     }
-    h->launches += resident ? 1 : nsteps;
+    h->launches += resident ? 1 : nsteps + loop_flushes;
     if (h->profile) {
         CK(h, cudaEventRecord(h->ev1, h->st));
         h->prof_launches = resident ? 1 : p->max_iters + refine;

@@ -80,6 +80,8 @@ struct GridStepArgs {
     int nbx, nblk;
     int t, trace_cap, update;
     double rel_tol;
+    size_t pslot;            // B * nblk: offset of the second slot of partial
+    int defer, prev_pending; // deferred free energy (see GridStepLaunch)
 };
 
 __device__ __forceinline__ double warp_sum_f64(double v) {
@@ -634,6 +636,11 @@ template <int NT = GT>
 __device__ __forceinline__ void grid_step_finish(const GridStepArgs &a, int b, double bs, double *red, int *is_last) {
     const int tid = threadIdx.y * GX + threadIdx.x;
     const int blk = blockIdx.y * a.nbx + blockIdx.x;
+    if (a.defer) {
+        // the next step (or the flush kernel) reduces this slot
+        if (tid == 0) a.partial[(size_t)(a.t & 1) * a.pslot + (size_t)b * a.nblk + blk] = bs;
+        return;
+    }
     if (tid == 0) {
         a.partial[(size_t)b * a.nblk + blk] = bs;
         __threadfence();
@@ -666,6 +673,62 @@ __device__ __forceinline__ void grid_step_finish(const GridStepArgs &a, int b, d
         a.counter[b] = 0u;
     }
 }
+
+// Sum of the n partials of one instance by the whole block, in a fixed order
+// (thread k takes k, k + NT, ...; warps in order), so that every block that
+// sums them gets the same value.
+template <int NT>
+__device__ __forceinline__ double sum_partials(const double *p, int n, double *red) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    for (int k = tid; k < n; k += NT) acc += __ldcg(p + k);
+    acc = warp_sum_f64(acc);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    double F = 0.0;
+#pragma unroll
+    for (int k = 0; k < NT / 32; ++k) F += red[k];
+    __syncthreads();   // red is reused
+    return F;
+}
+
+// F of step t_prev from its deferred partials: trace entry and F_cur (by the
+// writer block), and the stopping rule |F - F_prev| <= rel_tol |F|, which
+// every block that asks evaluates identically.
+// Returns true when instance b stops after step t_prev.
+template <int NT>
+__device__ __forceinline__ bool deferred_f(const GridStepArgs &a, int b, int t_prev, bool writer, double *red) {
+    const double F = sum_partials<NT>(a.partial + (size_t)(t_prev & 1) * a.pslot + (size_t)b * a.nblk, a.nblk, red);
+    bool stop = false;
+    if (a.done != nullptr && a.rel_tol > 0.0 && t_prev > 0 && t_prev - 1 < a.trace_cap) {
+        const double Fp = a.f_trace[(size_t)b * a.trace_cap + t_prev - 1];
+        stop = fabs(F - Fp) <= a.rel_tol * fabs(F);
+    }
+    if (writer && threadIdx.x == 0 && threadIdx.y == 0) {
+        a.f_cur[b] = F;
+        if (!isfinite(F)) atomicExch(a.status, -6);
+        if (t_prev < a.trace_cap) a.f_trace[(size_t)b * a.trace_cap + t_prev] = F;
+        if (stop) a.done[b] = t_prev + 1;
+    }
+    return stop;
+}
+
+// Start of a step after griddepcontrol.wait: true when instance b no longer
+// updates (stopped before, or the pending F of step t - 1 meets the rule).
+// The pending F is summed by tile (0, 0) alone when no stopping rule runs,
+// else by every tile, each of which needs the decision.
+template <int NT>
+__device__ __forceinline__ bool grid_step_prologue(const GridStepArgs &a, int b, double *red) {
+    if (a.done != nullptr && a.done[b] != 0) return true;
+    if (!a.prev_pending) return false;
+    const bool writer = blockIdx.x == 0 && blockIdx.y == 0;
+    const bool decide = a.done != nullptr && a.rel_tol > 0.0;
+    if (!writer && !decide) return false;
+    return deferred_f<NT>(a, b, a.t - 1, writer, red);
+}
+
+// The pending F of the last step of a loop (block b: instance b).
+__global__ void grid_f_flush_kernel(const __grid_constant__ GridStepArgs a);
 
 template <int LT, int CONN, bool SYM, bool TC, int RULE = 0>
 __global__ void __launch_bounds__(GT, (RULE == 2) ? 1 : ((LT >= 24 || RULE) ? 2 : 3))
@@ -794,6 +857,12 @@ cudaError_t launch_grid_step_lt(const GridStepLaunch &l, cudaStream_t st) {
     a.trace_cap = l.trace_cap;
     a.update = l.update;
     a.rel_tol = l.rel_tol;
+    a.pslot = (size_t)l.B * a.nblk;
+    a.defer = l.defer;
+    a.prev_pending = l.prev_pending;
+    // only the TMA-staged kernels take the deferred free energy
+    if ((l.defer || l.prev_pending) && !(storage_labels(LT) >= 4 && grid_step_uses_tma(l)))
+        return cudaErrorInvalidValue;
     a.mu_tc = l.mu_tc;
     a.adapt_d = l.adapt_d;
     if (l.mu_sym && LT <= kMuParamLT) {

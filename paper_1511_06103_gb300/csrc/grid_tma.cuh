@@ -173,21 +173,19 @@ grid_tma_step_kernel(const __grid_constant__ GridTmaMaps maps, const __grid_cons
     // the previous step (when it was launched as a programmatic dependency)
     // has finished and its writes are visible
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (a.done != nullptr && a.done[b] != 0) {
+    if (tid == 0) tma::load_4d(qt, &maps.s_in, &bar, 0, x0 - 1, y0 - 1, b);
+    // the pending F of the previous step is summed while the tile is in flight
+    if (grid_step_prologue<GT>(a, b, red)) {
         // stopped instance: carry the state through (keeps the ping-pong parity)
         if (a.update && inside) {
             float2 v[LP / 2];
             load_px<LP>(v, a.s_in + ((size_t)b * N + p) * LP);
             store_px<LP>(a.s_out + ((size_t)b * N + p) * LP, v);
         }
-        if (tid == 0) {
-            // complete the barrier's transaction before the tile leaves
-            tma::load_4d(qt, &maps.s_in, &bar, 0, x0 - 1, y0 - 1, b);
-            tc::mbar_wait(&bar, 0, a.status);
-        }
+        // complete the barrier's transaction before the tile leaves
+        if (tid == 0) tc::mbar_wait(&bar, 0, a.status);
         return;
     }
-    if (tid == 0) tma::load_4d(qt, &maps.s_in, &bar, 0, x0 - 1, y0 - 1, b);
     const float eta = a.eta[b];
     const float2 neta = splat2(-eta), ome = splat2(1.f - eta);
     const bool ok = tc::mbar_wait(&bar, 0, a.status);
@@ -480,7 +478,9 @@ grid_tma2_step_kernel(const __grid_constant__ GridTmaMaps maps, const __grid_con
         }
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (a.done != nullptr && a.done[b] != 0) {
+    if (tid == 0) tma::load_4d(qt, &maps.s_in, &bar, 0, x0 - 1, y0 - 1, b);
+    // the pending F of the previous step is summed while the tile is in flight
+    if (grid_step_prologue<GT2>(a, b, red)) {
         if (a.update) {
             float2 v[LP / 2];
             if (in1) {
@@ -492,13 +492,9 @@ grid_tma2_step_kernel(const __grid_constant__ GridTmaMaps maps, const __grid_con
                 store_px<LP>(a.s_out + ((size_t)b * N + p2) * LP, v);
             }
         }
-        if (tid == 0) {
-            tma::load_4d(qt, &maps.s_in, &bar, 0, x0 - 1, y0 - 1, b);
-            tc::mbar_wait(&bar, 0, a.status);
-        }
+        if (tid == 0) tc::mbar_wait(&bar, 0, a.status);
         return;
     }
-    if (tid == 0) tma::load_4d(qt, &maps.s_in, &bar, 0, x0 - 1, y0 - 1, b);
     const float eta = a.eta[b];
     const float2 neta = splat2(-eta), ome = splat2(1.f - eta);
     const bool ok = tc::mbar_wait(&bar, 0, a.status);

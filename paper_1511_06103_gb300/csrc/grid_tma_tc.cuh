@@ -224,7 +224,6 @@ grid_tma2_tc_step_kernel(const __grid_constant__ GridTmaTcMaps maps, const __gri
         }
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const bool stopped = a.done != nullptr && a.done[b] != 0;
     if (tid == 0) {
         tma::load_4d(rint, &maps.s_int, &bars[0], 0, x0, y0, b);
         tma::load_4d(rtop, &maps.s_row, &bars[0], 0, x0 - 1, y0 - 1, b);
@@ -232,6 +231,8 @@ grid_tma2_tc_step_kernel(const __grid_constant__ GridTmaTcMaps maps, const __gri
         tma::load_4d(rleft, &maps.s_col, &bars[0], 0, x0 - 1, y0, b);
         tma::load_4d(rright, &maps.s_col, &bars[0], 0, x0 + GX, y0, b);
     }
+    // the pending F of the previous step is summed while the tile is in flight
+    const bool stopped = grid_step_prologue<GT2>(a, b, red);
     if (stopped) {
         if (a.update) {
             float2 v[LP / 2];
