@@ -26,8 +26,16 @@
 #include <cmath>
 
 #include "internal.h"
+#include "tc_common.cuh"
+#include "tma_maps.h"
 
 namespace proxmf {
+
+// Tensor maps of one reverse step: d/ds^{t+1}, s^t and s^{t+1}, each read as
+// the 34 x 6 halo box of a 32 x 4 tile (labels >= 4 per pixel).
+struct AdjTmaMaps {
+    CUtensorMap gs, s, sn;
+};
 
 namespace {
 
@@ -42,9 +50,16 @@ struct AdjCfg {
     static constexpr int TS = VW;                           // dmu register tile TS x TS
     static constexpr int NTB = LP / TS, NTILE = NTB * NTB;
     static constexpr int NG = NT / NTILE > 0 ? NT / NTILE : 1;   // pixel groups of the dmu GEMM
+    // the halo rows are copied by the TMA (whole 16-byte label vectors) when LP >= 4
+    static constexpr bool TMA = LP >= 4;
     __host__ __device__ static constexpr int mu_floats(bool sym) { return (sym ? 1 : 2) * LP * LP; }
+    __host__ __device__ static constexpr int al(int v) { return (v + 31) / 32 * 32; }   // 128-byte offsets
+    // float offsets of the regions: mu, ga rows, q rows, S rows (raw s^{t+1} before), Gout rows
+    __host__ __device__ static constexpr int off_ga(bool sym) { return al(mu_floats(sym)); }
+    __host__ __device__ static constexpr int off_q(bool sym) { return off_ga(sym) + al(HR * LS); }
+    __host__ __device__ static constexpr int off_S(bool sym) { return off_q(sym) + al(HR * LS); }
     __host__ __device__ static constexpr size_t smem_bytes(bool sym) {
-        return sizeof(float) * ((size_t)mu_floats(sym) + 2 * (size_t)HR * LS + 2 * (size_t)NT * LSS);
+        return sizeof(float) * ((size_t)off_S(sym) + 2 * (size_t)NT * LSS) + 128;   // + base alignment
     }
     // the dmu reduction scratch reuses everything after mu
     static_assert(NG * LP * LP <= 2 * HR * LS + 2 * NT * LSS, "dmu scratch does not fit");
@@ -87,6 +102,16 @@ __device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
 // in registers from one phase of the kernel to the next.
 __device__ __forceinline__ void reload_fence() { asm volatile("" ::: "memory"); }
 
+// TMA copy of a 4-D box {c0, c1, c2, c3} into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                            int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+        "[%2];" ::"r"(tc::smem_u32(dst)),
+        "l"((uint64_t)map), "r"(tc::smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
 // 16- or 8-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros.
 template <int VW>
 __device__ __forceinline__ void cp_async_row(float *dst, const float *src, int src_bytes) {
@@ -98,17 +123,20 @@ __device__ __forceinline__ void cp_async_row(float *dst, const float *src, int s
 }
 
 template <int LT, int CONN, bool SYM>
-__global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep a) {
+__global__ void __launch_bounds__(AdjCfg<LT>::NT, 3)
+adj_step_kernel(const __grid_constant__ AdjTmaMaps maps, const __grid_constant__ AdjointStep a) {
     using C = AdjCfg<LT>;
     constexpr int LP = C::LP, VW = C::VW, LS = C::LS, LSS = C::LSS, TX = C::TX, HX = C::HX, NT = C::NT;
     constexpr int NP = LP / 2;                             // label pairs
     constexpr int ND = CONN == 8 ? 4 : 2;
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    float *smem = smem_raw + (((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u) >> 2);
     float *mus = smem;                                     // mu [LP][LP], row k = mu[k][.]
     float *muT = smem + LP * LP;                           // mu^T (asymmetric mu only)
-    float *sga = smem + C::mu_floats(SYM);                 // [HR][LS] ga of tile + halo
-    float *sq = sga + C::HR * LS;                          // [HR][LS] q^t of tile + halo
-    float *sS = sq + C::HR * LS;                           // [NT][LSS] S_i
+    float *sga = smem + C::off_ga(SYM);                    // [HR][LS] ga of tile + halo
+    float *sq = smem + C::off_q(SYM);                      // [HR][LS] q^t of tile + halo
+    float *sS = smem + C::off_S(SYM);                      // [NT][LSS] S_i
     float *sG = sS + NT * LSS;                             // [NT][LSS] sum_{i->j} w ga_j
     float *sraw = sS;                                      // [HR][LP] raw s^{t+1} (before S, G exist)
 
@@ -118,10 +146,36 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep
     const int H = a.H, W = a.W, L = a.L;
     const size_t N = (size_t)H * W;
     const size_t base = (size_t)b * N;
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if constexpr (C::TMA) {
+        if (tid == 0) {
+            tc::mbar_init(&bar, 1);
+            tc::mbar_init_fence();
+        }
+        __syncthreads();
+    }
+    // mu does not depend on the previous step: staged before the wait
+    for (int i = tid; i < LP * LP; i += NT) {
+        const int r = i / LP, c = i - r * LP;
+        const float v = (r < L && c < L) ? a.mu[r * L + c] : 0.f;
+        mus[i] = v;
+        if (!SYM) muT[c * LP + r] = v;
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const float eta = a.eta[b];
 
     // Phase 1a: raw rows of the tile and its halo, all copies in flight at
     // once (rows outside the image are zero-filled).
+    if constexpr (C::TMA) {
+        // three boxes of 34 x 6 pixels (labels LP..LS-1 of the ga and q rows zero-filled)
+        if (tid == 0) {
+            tc::mbar_expect_tx(&bar, (uint32_t)(4 * C::HR * (2 * LS + LP)));
+            tma_load_4d(sga, &maps.gs, &bar, 0, x0 - 1, y0 - 1, b);
+            tma_load_4d(sq, &maps.s, &bar, 0, x0 - 1, y0 - 1, b);
+            tma_load_4d(sraw, &maps.sn, &bar, 0, x0 - 1, y0 - 1, b);
+        }
+        tc::mbar_wait(&bar, 0, a.status);
+    } else {
     for (int r = tid; r < C::HR; r += NT) {
         const int hy = r / HX, hx = r - hy * HX;
         const int y = y0 - 1 + hy, x = x0 - 1 + hx;
@@ -136,13 +190,8 @@ __global__ void __launch_bounds__(AdjCfg<LT>::NT, 3) adj_step_kernel(AdjointStep
         }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
-    for (int i = tid; i < LP * LP; i += NT) {
-        const int r = i / LP, c = i - r * LP;
-        const float v = (r < L && c < L) ? a.mu[r * L + c] : 0.f;
-        mus[i] = v;
-        if (!SYM) muT[c * LP + r] = v;
-    }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
     __syncthreads();
     // Phase 1b: ga = gs - q' sum gs and q = exp(s) in place (padding -> 0).
     for (int r = tid; r < C::HR; r += NT) {
@@ -362,9 +411,26 @@ cudaError_t launch_adj(const AdjointStep &a, cudaStream_t st) {
     static SmemOptIn optin;   // once per device
     const cudaError_t attr = smem_optin(optin, adj_step_kernel<LT, CONN, SYM>, smem);
     if (attr != cudaSuccess) return attr;
-    dim3 grid((a.W + C::TX - 1) / C::TX, (a.H + C::TY - 1) / C::TY, a.B);
-    adj_step_kernel<LT, CONN, SYM><<<grid, C::NT, smem, st>>>(a);
-    return cudaGetLastError();
+    AdjTmaMaps maps{};
+    if constexpr (C::TMA) {
+        cudaError_t e = encode_state(&maps.gs, a.gs_in, a.B, a.H, a.W, C::LP, C::LS, C::HX, C::HY);
+        if (e == cudaSuccess) e = encode_state(&maps.s, a.s, a.B, a.H, a.W, C::LP, C::LS, C::HX, C::HY);
+        if (e == cudaSuccess) e = encode_state(&maps.sn, a.s_next, a.B, a.H, a.W, C::LP, C::LP, C::HX, C::HY);
+        if (e != cudaSuccess) return e;
+    }
+    // programmatic dependent launch: mu and the barrier are set up while the
+    // previous step drains (the kernel waits before it reads its inputs)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((a.W + C::TX - 1) / C::TX, (a.H + C::TY - 1) / C::TY, a.B);
+    cfg.blockDim = dim3(C::NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, adj_step_kernel<LT, CONN, SYM>, maps, a);
 }
 
 template <int LT>

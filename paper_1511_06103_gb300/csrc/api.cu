@@ -1359,6 +1359,7 @@ crf_status mf_unrolled_backward(crf_t h, int32_t K, double eta, const float *ckp
     a.w = h->w;
     a.mu = h->mu_dev;
     a.eta = e;
+    a.status = h->status;
     a.B = h->B;
     a.L = h->L;
     a.H = h->H;

@@ -286,6 +286,7 @@ struct AdjointStep {
     const float *w;          // [B][N][n_dirs]
     const float *mu;         // [L][L] device
     const float *eta;        // [B]
+    int *status;             // device error word (bounded waits)
     int B, L, H, W, conn;
     bool mu_sym;
 };

@@ -7,6 +7,7 @@
 #include <mutex>
 
 #include "grid_step.cuh"
+#include "tma_maps.h"
 
 namespace proxmf {
 
@@ -46,12 +47,12 @@ cudaError_t encode_4d(CUtensorMap *m, const void *base, CUtensorMapDataType dt, 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+}  // namespace
+
 cudaError_t encode_state(CUtensorMap *m, const float *base, int B, int H, int W, int LP, int box0, int box1,
                          int box2) {
     return encode_4d(m, base, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B, H, W, LP, box0, box1, box2);
 }
-
-}  // namespace
 
 cudaError_t encode_grid_maps(GridTmaMaps *m, const GridStepLaunch &l, int LP, int CS) {
     cudaError_t e = encode_state(&m->s_in, l.s_in, l.B, l.H, l.W, LP, CS, GX + 2, GY + 2);
