@@ -98,6 +98,20 @@ __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
 }
 __device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
 
+// The same pair FMA as one packed instruction (fma.rn.f32x2: every lane
+// rounds like fmaf), for the block GEMM of dmu, whose pairs come from vector
+// loads and do not need register moves.
+__device__ __forceinline__ float2 pfma_x2(float2 a, float2 b, float2 c) {
+    unsigned long long ra, rb, rc, rd;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rc) : "f"(c.x), "f"(c.y));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+    float2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+    return d;
+}
+
 // Keeps the compiler from carrying shared-memory loads (the L x L matrix)
 // in registers from one phase of the kernel to the next.
 __device__ __forceinline__ void reload_fence() { asm volatile("" ::: "memory"); }
@@ -381,8 +395,8 @@ adj_step_kernel(const __grid_constant__ AdjTmaMaps maps, const __grid_constant__
             for (int u = 0; u < TS; ++u)
 #pragma unroll
                 for (int v = 0; v < TS; v += 2)
-                    acc[u][v / 2] = pfma(splat2(ga[u]), make_float2(sv[v], sv[v + 1]),
-                                         pfma(splat2(qa[u]), make_float2(gv[v], gv[v + 1]), acc[u][v / 2]));
+                    acc[u][v / 2] = pfma_x2(splat2(ga[u]), make_float2(sv[v], sv[v + 1]),
+                                            pfma_x2(splat2(qa[u]), make_float2(gv[v], gv[v + 1]), acc[u][v / 2]));
         }
     }
     __syncthreads();
