@@ -49,11 +49,15 @@ struct GridTmaTcGeom {
     static constexpr int LEFT = al(BOT + ROW_B, 128);
     static constexpr int RIGHT = al(LEFT + COL_B, 128);
     static constexpr int U16 = al(RIGHT + COL_B, 128);
-    static constexpr int Q16 = al(U16 + U16_B, 1024);                      // also the A operand
-    static constexpr int BOP = al(Q16 + (Q16_B > 2 * AHALF ? Q16_B : 2 * AHALF), 1024);
+    static constexpr int Q16 = al(U16 + U16_B, 1024);
+    // the A operand lives over the halo and unary boxes, which the conversion
+    // consumes, where it fits (else after the q tile)
+    static constexpr bool A_OVER = U16 + U16_B - TOP >= 2 * AHALF;
+    static constexpr int AOP = A_OVER ? TOP : al(Q16 + Q16_B, 1024);
+    static constexpr int BOP = al(A_OVER ? Q16 + Q16_B : AOP + 2 * AHALF, 1024);
     static constexpr int B_B = KP * KP * 2;
     static constexpr int bytes = BOP + B_B + 1024;                          // + alignment slack
-    static constexpr uint32_t TX = INT_B + 2 * ROW_B + 2 * COL_B + U16_B;    // TMA bytes per tile
+    static constexpr uint32_t TX = INT_B + 2 * ROW_B + 2 * COL_B + U16_B + B_B;   // copy bytes per tile
     static constexpr int NCOL = 2 * KP < 32 ? 32 : 2 * KP;                  // TMEM columns
     static constexpr int ctas = (3 * (bytes + 1024 + 1024) <= 227 * 1024) ? 3 : 2;
 };
@@ -160,7 +164,7 @@ grid_tma2_tc_step_kernel(const __grid_constant__ GridTmaTcMaps maps, const __gri
     float *rright = reinterpret_cast<float *>(base + G::RIGHT);
     uint8_t *u16 = base + G::U16;
     uint8_t *q16 = base + G::Q16;
-    uint8_t *Aop = q16;
+    uint8_t *Aop = base + G::AOP;
     uint8_t *Bop = base + G::BOP;
 
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -170,15 +174,15 @@ grid_tma2_tc_step_kernel(const __grid_constant__ GridTmaTcMaps maps, const __gri
         tc::mbar_init_fence();
     }
     if (tid < 32) tc::tmem_alloc(&tmem_slot, G::NCOL);
-    for (int i = tid; i < G::B_B / 16; i += GT2) reinterpret_cast<uint4 *>(Bop)[i] = a.mu_tc[i];
-    tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
     if (tid == 0) {
+        // U and the BF16 image of mu (the B operand) do not depend on the previous step
         tc::mbar_expect_tx(&bars[0], G::TX);
         tma::load_4d(u16, &maps.U16, &bars[0], 0, x0, y0, b);
+        tc::bulk_load(Bop, a.mu_tc, (uint32_t)G::B_B, &bars[0]);
     }
     float wo1[4] = {0.f, 0.f, 0.f, 0.f}, wi1[4] = {0.f, 0.f, 0.f, 0.f};
     float wo2[4] = {0.f, 0.f, 0.f, 0.f}, wi2[4] = {0.f, 0.f, 0.f, 0.f};
@@ -352,7 +356,6 @@ grid_tma2_tc_step_kernel(const __grid_constant__ GridTmaTcMaps maps, const __gri
             acc_cell16<NP>(S2, r3 - C, wo2[3]);
         }
     }
-    __syncthreads();   // the q tile is read; it becomes the A operand
     {
         const int lane_row = 32 * tw + tx;   // this thread's TMEM lane
         uint8_t *arow = Aop + (lane_row >> 3) * G::SBO + (lane_row & 7) * 16;
