@@ -424,13 +424,14 @@ grid_tma2_step_kernel(const __grid_constant__ GridTmaMaps maps, const __grid_con
 
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (tid == 0) {
+        // both boxes are requested before anything else: U at once, log q as
+        // soon as the previous step has finished
         tc::mbar_init(&bar, 1);
         tc::mbar_init_fence();
-    }
-    __syncthreads();
-    if (tid == 0) {
         tc::mbar_expect_tx(&bar, (uint32_t)(G::QH * G::QW * CS * 4 + G::CBYTES));
         tma::load_4d(ct, &maps.U, &bar, 0, x0, y0, b);
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        tma::load_4d(qt, &maps.s_in, &bar, 0, x0 - 1, y0 - 1, b);
     }
     for (int i = tid; !kParamMu && i < LT * NPP; i += GT2) mus[i] = a.mu_out[i];
     // weights of the edges leaving each pixel and entering it
@@ -478,7 +479,7 @@ grid_tma2_step_kernel(const __grid_constant__ GridTmaMaps maps, const __grid_con
         }
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (tid == 0) tma::load_4d(qt, &maps.s_in, &bar, 0, x0 - 1, y0 - 1, b);
+    __syncthreads();   // the barrier is initialised before anyone waits on it
     // the pending F of the previous step is summed while the tile is in flight
     if (grid_step_prologue<GT2>(a, b, red)) {
         if (a.update) {
