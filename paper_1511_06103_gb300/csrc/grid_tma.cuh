@@ -132,16 +132,16 @@ grid_tma_step_kernel(const __grid_constant__ GridTmaMaps maps, const __grid_cons
     // The next step may be launched now (programmatic dependent launch): its
     // tiles take the SMs that this launch frees and wait below.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // U and the edge weights do not change between steps: they are fetched
+    // before the wait for the previous step; thread 0 requests both boxes
+    // before anything else
     if (tid == 0) {
         tc::mbar_init(&bar, 1);
         tc::mbar_init_fence();
-    }
-    __syncthreads();
-    // U and the edge weights do not change between steps: they are fetched
-    // before the wait for the previous step
-    if (tid == 0) {
         tc::mbar_expect_tx(&bar, (uint32_t)(G::QH * G::QW * CS * 4 + G::CBYTES));
         tma::load_4d(ct, &maps.U, &bar, 0, x0, y0, b);
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        tma::load_4d(qt, &maps.s_in, &bar, 0, x0 - 1, y0 - 1, b);
     }
     for (int i = tid; !kParamMu && i < LT * NPP; i += GT) {
         mus[0][i] = a.mu_out[i];
@@ -173,7 +173,7 @@ grid_tma_step_kernel(const __grid_constant__ GridTmaMaps maps, const __grid_cons
     // the previous step (when it was launched as a programmatic dependency)
     // has finished and its writes are visible
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (tid == 0) tma::load_4d(qt, &maps.s_in, &bar, 0, x0 - 1, y0 - 1, b);
+    __syncthreads();   // the barrier is initialised before anyone waits on it
     // the pending F of the previous step is summed while the tile is in flight
     if (grid_step_prologue<GT>(a, b, red)) {
         // stopped instance: carry the state through (keeps the ping-pong parity)
