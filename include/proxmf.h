@@ -29,6 +29,11 @@
  *   - A handle is used by one host thread at a time.
  *   - A CUDA error is reported as CRF_E_CUDA and makes the handle unusable
  *     (later calls return CRF_E_STATE).
+ *   - Every wait inside a kernel is bounded (about 2 s).  When a step
+ *     kernel's wait runs out, the call returns CRF_E_TIMEOUT and the handle
+ *     becomes unusable as well (copies or tensor-core operations it waited
+ *     for may still have been in flight): destroy it and create a new one.
+ *     The Lanczos grid barriers of mf_lipschitz are the exception (below).
  */
 #ifndef PROXMF_H
 #define PROXMF_H

@@ -400,6 +400,9 @@ crf_status read_status(crf_t h) {
     CK(h, cudaStreamSynchronize(h->st));
     if (s != 0) {
         CK(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
+        // a step kernel's bounded wait ran out: copies or MMAs it waited for
+        // may still have been in flight, so the handle is not used again
+        if (s == CRF_E_TIMEOUT) h->broken = true;
         return (crf_status)s;
     }
     return CRF_OK;

@@ -442,6 +442,13 @@ grid_tma2_tc_step_kernel(const __grid_constant__ GridTmaTcMaps maps, const __gri
     if ((tid & 31) == 0) red[tid >> 5] = df_to(fw);
     __syncthreads();
     if (tid < 32) {
+        // a wait that ran out: the copies and MMAs in flight get a second
+        // bounded wait before the TMEM columns are freed
+        if (tid == 0) {
+            if (!ok) tc::mbar_wait(&bars[0], 0, a.status);
+            if (!okm) tc::mbar_wait(&bars[1], 0, a.status);
+        }
+        __syncwarp();
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, G::NCOL);
     }
