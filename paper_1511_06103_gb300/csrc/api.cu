@@ -57,7 +57,7 @@ struct crf_s {
     float gamma1 = 0.f, gamma2 = 0.f, eps = 0.f;
     float *eta_auto = nullptr;   // [B]
     double *Lambda = nullptr;    // [B]
-    double *partial = nullptr;   // [2][B][nblk] free-energy partials (two slots: deferred sums)
+    double *partial = nullptr;   // [2][B][nblk][kMaxFParts] free-energy partials (two slots: deferred sums)
     unsigned *counter = nullptr; // [B]
     double *ftrace = nullptr;    // [B][trace_cap]
     double *fcur = nullptr;      // [B]
@@ -294,9 +294,9 @@ DenseStepLaunch dense_args(crf_t h, const float *eta, int t, int update, double 
 // One step (update = 1) or a free-energy-only pass (update = 0) of either
 // model.  fp32 = 1 forces the FP32 form (refinement steps, and every
 // free-energy-only pass, which is evaluated with FP32 messages).
-// pending (step loops only): in/out, 1 while a deferring grid step's free
-// energy awaits its sum (see GridStepLaunch::defer); *flushes counts the
-// flush launches this adds.
+// pending (step loops only): in/out, the partials per tile of a deferring
+// grid step whose free energy awaits its sum, else 0 (see
+// GridStepLaunch::defer); *flushes counts the flush launches this adds.
 cudaError_t launch_step(crf_t h, const float *eta, int t, int update, double rel_tol, int fp32 = 0,
                         int *pending = nullptr, int *flushes = nullptr) {
     if (h->sparse) {
@@ -342,10 +342,10 @@ cudaError_t launch_step(crf_t h, const float *eta, int t, int update, double rel
     if (!update || rel_tol <= 0) a.done = nullptr;
     a.tc = h->bf16 && update && !fp32;
     if (pending) {
-        const int d = update && grid_step_uses_tma(a) ? 1 : 0;
+        const int d = update ? grid_step_fparts(a) : 0;
         if (*pending && !d) {
             // the next kernel does not take the pending sum: flush it first
-            const cudaError_t e = launch_grid_f_flush(a, t - 1, h->st);
+            const cudaError_t e = launch_grid_f_flush(a, t - 1, *pending, h->st);
             if (e != cudaSuccess) return e;
             if (flushes) ++*flushes;
             *pending = 0;
@@ -644,7 +644,7 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
     ok = ok && dalloc(&h->adapt_d, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->eta_auto, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->Lambda, h->B) == cudaSuccess;
-    ok = ok && dalloc(&h->partial, 2 * (size_t)h->B * h->nblk) == cudaSuccess;
+    ok = ok && dalloc(&h->partial, 2 * (size_t)kMaxFParts * h->B * h->nblk) == cudaSuccess;
     ok = ok && dalloc(&h->counter, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->fcur, h->B) == cudaSuccess;
     ok = ok && dalloc(&h->done, h->B) == cudaSuccess;
@@ -1013,7 +1013,7 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
         if (pending) {
             GridStepLaunch a = step_args(h, eta, nsteps - 1, 1, p->rel_tol);
             if (p->rel_tol <= 0) a.done = nullptr;
-            const cudaError_t e = launch_grid_f_flush(a, nsteps - 1, h->st);
+            const cudaError_t e = launch_grid_f_flush(a, nsteps - 1, pending, h->st);
             if (e != cudaSuccess) return e;
             ++loop_flushes;
         }

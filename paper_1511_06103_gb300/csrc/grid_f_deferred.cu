@@ -13,16 +13,18 @@ __global__ void __launch_bounds__(128) grid_f_flush_kernel(const __grid_constant
     __shared__ double red[4];
     const int b = blockIdx.x;
     if (a.done != nullptr && a.done[b] != 0) return;   // the step copied a stopped instance: no partials
-    deferred_f<128>(a, b, a.t, true, red);
+    deferred_f<128>(a, b, a.t, a.prev_pending, true, red);
 }
 
-cudaError_t launch_grid_f_flush(const GridStepLaunch &l, int t, cudaStream_t st) {
+cudaError_t launch_grid_f_flush(const GridStepLaunch &l, int t, int parts, cudaStream_t st) {
+    if (parts < 1 || parts > kMaxFParts) return cudaErrorInvalidValue;
     GridStepArgs a{};
     int nbx, nby;
     grid_tiles(l.H, l.W, &nbx, &nby);
     a.nbx = nbx;
     a.nblk = nbx * nby;
-    a.pslot = (size_t)l.B * a.nblk;
+    a.pslot = (size_t)l.B * a.nblk * kMaxFParts;
+    a.prev_pending = parts;
     a.partial = l.partial;
     a.f_trace = l.f_trace;
     a.f_cur = l.f_cur;

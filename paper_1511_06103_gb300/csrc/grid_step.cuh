@@ -80,8 +80,8 @@ struct GridStepArgs {
     int nbx, nblk;
     int t, trace_cap, update;
     double rel_tol;
-    size_t pslot;            // B * nblk: offset of the second slot of partial
-    int defer, prev_pending; // deferred free energy (see GridStepLaunch)
+    size_t pslot;            // B * nblk * kMaxFParts: offset of the second slot of partial
+    int defer, prev_pending; // deferred free energy: partials per tile (see GridStepLaunch)
 };
 
 __device__ __forceinline__ double warp_sum_f64(double v) {
@@ -637,7 +637,7 @@ __device__ __forceinline__ void grid_step_finish(const GridStepArgs &a, int b, d
     const int tid = threadIdx.y * GX + threadIdx.x;
     const int blk = blockIdx.y * a.nbx + blockIdx.x;
     if (a.defer) {
-        // the next step (or the flush kernel) reduces this slot
+        // the next step (or the flush kernel) reduces this slot (one partial per tile)
         if (tid == 0) a.partial[(size_t)(a.t & 1) * a.pslot + (size_t)b * a.nblk + blk] = bs;
         return;
     }
@@ -697,8 +697,10 @@ __device__ __forceinline__ double sum_partials(const double *p, int n, double *r
 // every block that asks evaluates identically.
 // Returns true when instance b stops after step t_prev.
 template <int NT>
-__device__ __forceinline__ bool deferred_f(const GridStepArgs &a, int b, int t_prev, bool writer, double *red) {
-    const double F = sum_partials<NT>(a.partial + (size_t)(t_prev & 1) * a.pslot + (size_t)b * a.nblk, a.nblk, red);
+__device__ __forceinline__ bool deferred_f(const GridStepArgs &a, int b, int t_prev, int parts, bool writer,
+                                           double *red) {
+    const size_t n = (size_t)a.nblk * parts;   // partials of one instance, [nblk][parts]
+    const double F = sum_partials<NT>(a.partial + (size_t)(t_prev & 1) * a.pslot + (size_t)b * n, (int)n, red);
     bool stop = false;
     if (a.done != nullptr && a.rel_tol > 0.0 && t_prev > 0 && t_prev - 1 < a.trace_cap) {
         const double Fp = a.f_trace[(size_t)b * a.trace_cap + t_prev - 1];
@@ -724,7 +726,7 @@ __device__ __forceinline__ bool grid_step_prologue(const GridStepArgs &a, int b,
     const bool writer = blockIdx.x == 0 && blockIdx.y == 0;
     const bool decide = a.done != nullptr && a.rel_tol > 0.0;
     if (!writer && !decide) return false;
-    return deferred_f<NT>(a, b, a.t - 1, writer, red);
+    return deferred_f<NT>(a, b, a.t - 1, a.prev_pending, writer, red);
 }
 
 // The pending F of the last step of a loop (block b: instance b).
@@ -857,12 +859,15 @@ cudaError_t launch_grid_step_lt(const GridStepLaunch &l, cudaStream_t st) {
     a.trace_cap = l.trace_cap;
     a.update = l.update;
     a.rel_tol = l.rel_tol;
-    a.pslot = (size_t)l.B * a.nblk;
+    a.pslot = (size_t)l.B * a.nblk * kMaxFParts;
     a.defer = l.defer;
     a.prev_pending = l.prev_pending;
-    // only the TMA-staged kernels take the deferred free energy
+    // only the TMA-staged kernels take the deferred free energy, each with
+    // its own number of partials per tile
     if ((l.defer || l.prev_pending) && !(storage_labels(LT) >= 4 && grid_step_uses_tma(l)))
         return cudaErrorInvalidValue;
+    if (l.defer && l.defer != grid_step_fparts(l)) return cudaErrorInvalidValue;
+    if (l.prev_pending < 0 || l.prev_pending > kMaxFParts) return cudaErrorInvalidValue;
     a.mu_tc = l.mu_tc;
     a.adapt_d = l.adapt_d;
     if (l.mu_sym && LT <= kMuParamLT) {

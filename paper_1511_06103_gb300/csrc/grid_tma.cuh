@@ -38,6 +38,7 @@ struct GridTmaMaps {
     CUtensorMap s_in;    // log q^t, box {CS, GX + 2, GY + 2, 1}
     CUtensorMap U;       // unaries, box {CS, GX, GY, 1}
     CUtensorMap s_out;   // log q^{t+1}, box {CS, GX, GY, 1}
+    CUtensorMap s_out2;  // log q^{t+1}, box {CS, GX, 2, 1}: the two rows of one warp
 };
 
 template <int LT>
@@ -645,6 +646,21 @@ grid_tma2_step_kernel(const __grid_constant__ GridTmaMaps maps, const __grid_con
     }
     tc::fence_async_smem();   // the TMA store reads these cells
     const df fw = warp_sum_df(df{fpair, 0.f});
+    if (a.defer) {
+        // in a step loop each warp leaves on its own: its two rows by one TMA
+        // store, its F partial (summed by the next step), no block barrier
+        __syncwarp();
+        if (tx == 0) {
+            if (a.update && ok) {
+                tma::store_4d(&maps.s_out2, ct + 2 * tw * GX * CS, 0, x0, y0 + 2 * tw, b);
+                tma::commit();
+            }
+            const size_t blk = (size_t)blockIdx.y * a.nbx + blockIdx.x;
+            a.partial[(size_t)(a.t & 1) * a.pslot + ((size_t)b * a.nblk + blk) * a.defer + tw] = df_to(fw);
+            if (a.update && ok) tma::wait_read();
+        }
+        return;
+    }
     if ((tid & 31) == 0) red[tid >> 5] = df_to(fw);
     __syncthreads();
     double bs = 0.0;

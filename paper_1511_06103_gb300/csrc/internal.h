@@ -91,7 +91,7 @@ struct GridStepLaunch {
     float *mom, *vv;         // [B][N][LP] momentum average and second moment (rules 1, 2)
     float gamma1, gamma2, eps;
     int rule_first;          // 1 on the first step of a run (no history)
-    double *partial;         // [2][B][nblk] per-tile free-energy partials (scratch; slot t & 1 when deferred)
+    double *partial;         // [2][B][nblk][kMaxFParts] free-energy partials (scratch; slot t & 1 when deferred)
     unsigned int *counter;   // [B] tiles finished in this launch (scratch, self-resetting)
     double *f_trace;         // [B][trace_cap]
     double *f_cur;           // [B] F of the state read by this launch
@@ -101,10 +101,11 @@ struct GridStepLaunch {
     int t, trace_cap, update;
     double rel_tol;
     bool mu_sym;
-    // Deferred free energy (step loops of mf_iterate): with defer = 1 each
-    // tile stores its partial of step t in slot t & 1 of partial (two slots of
-    // [B][nblk]) and takes no ticket; prev_pending = 1 makes this launch
-    // reduce the partials of step t - 1 first (trace entry, stopping rule).
+    // Deferred free energy (step loops of mf_iterate): with defer = n > 0
+    // each tile stores n partials of step t (one per warp of the two-pixel
+    // kernel, else one) in slot t & 1 of partial and takes no ticket;
+    // prev_pending = n > 0 makes this launch first sum the n partials per
+    // tile of step t - 1 (trace entry, stopping rule).  0: none.
     int defer, prev_pending;
 };
 
@@ -160,11 +161,17 @@ cudaError_t launch_grid_step(const GridStepLaunch &a, cudaStream_t st);
 inline bool grid_step_uses_tma(const GridStepLaunch &l) {
     return l.L > 2 && l.rule == 0 && l.adapt_d == nullptr && (!l.tc || (l.mu_sym && l.U16 != nullptr));
 }
+// Free-energy partials per tile of a deferring launch: one per warp of the
+// two-pixel FP32 kernel (symmetric mu), one for the other TMA kernels.
+constexpr int kMaxFParts = 4;
+inline int grid_step_fparts(const GridStepLaunch &l) {
+    return grid_step_uses_tma(l) ? ((!l.tc && l.mu_sym) ? kMaxFParts : 1) : 0;
+}
 
 // The deferred free energy of step t (the last step of a loop, or of a run
 // of deferring steps): trace entry, F_cur and the stopping rule, one block per
 // instance (grid_f_deferred.cu).
-cudaError_t launch_grid_f_flush(const GridStepLaunch &l, int t, cudaStream_t st);
+cudaError_t launch_grid_f_flush(const GridStepLaunch &l, int t, int parts, cudaStream_t st);
 
 // Layout conversion and initialisation (layout.cu).
 // rows [B][N][L] <-> padded [B][N][LP]; pad fills the padding labels.

@@ -58,6 +58,7 @@ cudaError_t encode_grid_maps(GridTmaMaps *m, const GridStepLaunch &l, int LP, in
     cudaError_t e = encode_state(&m->s_in, l.s_in, l.B, l.H, l.W, LP, CS, GX + 2, GY + 2);
     if (e == cudaSuccess) e = encode_state(&m->U, l.U, l.B, l.H, l.W, LP, CS, GX, GY);
     if (e == cudaSuccess) e = encode_state(&m->s_out, l.s_out, l.B, l.H, l.W, LP, CS, GX, GY);
+    if (e == cudaSuccess) e = encode_state(&m->s_out2, l.s_out, l.B, l.H, l.W, LP, CS, GX, 2);
     return e;
 }
 
