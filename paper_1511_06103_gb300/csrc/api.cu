@@ -335,7 +335,21 @@ cudaError_t launch_step(crf_t h, const float *eta, int t, int update, double rel
     if (h->dense) {
         DenseStepLaunch a = dense_args(h, eta, t, update, rel_tol);
         if (!update || rel_tol <= 0) a.done = nullptr;
-        if (h->bf16 && update && !fp32) return launch_dense_step_tc(a, h->tcb, h->st);
+        const bool tc = h->bf16 && update && !fp32;
+        if (pending) {
+            // the tensor-core step defers its free energy (one partial per row tile)
+            const int d = tc ? 1 : 0;
+            if (*pending && !d) {
+                const cudaError_t e = launch_dense_f_flush(a, t - 1, h->st);
+                if (e != cudaSuccess) return e;
+                if (flushes) ++*flushes;
+                *pending = 0;
+            }
+            a.defer = d;
+            a.prev_pending = *pending;
+            *pending = d;
+        }
+        if (tc) return launch_dense_step_tc(a, h->tcb, h->st);
         return launch_dense_step_f32(a, h->st);
     }
     GridStepLaunch a = step_args(h, eta, t, update, rel_tol);
@@ -1011,9 +1025,16 @@ crf_status mf_iterate(crf_t h, const mf_params *p, int32_t *iters_done) {
             h->cur ^= 1;
         }
         if (pending) {
-            GridStepLaunch a = step_args(h, eta, nsteps - 1, 1, p->rel_tol);
-            if (p->rel_tol <= 0) a.done = nullptr;
-            const cudaError_t e = launch_grid_f_flush(a, nsteps - 1, pending, h->st);
+            cudaError_t e;
+            if (h->dense) {
+                DenseStepLaunch a = dense_args(h, eta, nsteps - 1, 1, p->rel_tol);
+                if (p->rel_tol <= 0) a.done = nullptr;
+                e = launch_dense_f_flush(a, nsteps - 1, h->st);
+            } else {
+                GridStepLaunch a = step_args(h, eta, nsteps - 1, 1, p->rel_tol);
+                if (p->rel_tol <= 0) a.done = nullptr;
+                e = launch_grid_f_flush(a, nsteps - 1, pending, h->st);
+            }
             if (e != cudaSuccess) return e;
             ++loop_flushes;
         }

@@ -72,7 +72,53 @@ struct DenseTcArgs {
     int N, Np, L, ntiles, nchunk;
     int t, trace_cap, update;
     double rel_tol;
+    int B, defer, prev_pending;   // deferred free energy (DenseStepLaunch): slots of [B][ntiles]
 };
+
+// Sum of the n row-tile partials of one instance by the whole block: thread
+// k takes k, k + kThreads, ...; shuffle-down trees; warps in order (the order
+// of the ticket form's last-tile sum, so F is the same bit for bit).
+__device__ __forceinline__ double dense_sum_partials(const double *p, int n, double *red) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double acc = 0.0;
+    for (int k = tid; k < n; k += kThreads) acc += __ldcg(p + k);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    double F = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) F += red[k];
+    __syncthreads();   // red is reused
+    return F;
+}
+
+// F of step t_prev from its deferred partials: trace entry and F_cur (by the
+// writer block) and the stopping rule, evaluated identically by every block
+// that asks.  True when instance b stops after step t_prev.
+__device__ __forceinline__ bool dense_deferred_f(const DenseTcArgs &a, int b, int t_prev, bool writer,
+                                                 double *red) {
+    const double F =
+        dense_sum_partials(a.partial + (size_t)(t_prev & 1) * a.B * a.ntiles + (size_t)b * a.ntiles, a.ntiles, red);
+    bool stop = false;
+    if (a.done != nullptr && a.rel_tol > 0.0 && t_prev > 0 && t_prev - 1 < a.trace_cap) {
+        const double Fp = a.f_trace[(size_t)b * a.trace_cap + t_prev - 1];
+        stop = fabs(F - Fp) <= a.rel_tol * fabs(F);
+    }
+    if (writer && threadIdx.x == 0) {
+        a.f_cur[b] = F;
+        if (!isfinite(F)) atomicExch(a.status, -6);
+        if (t_prev < a.trace_cap) a.f_trace[(size_t)b * a.trace_cap + t_prev] = F;
+        if (stop) a.done[b] = t_prev + 1;
+    }
+    return stop;
+}
+
+__global__ void __launch_bounds__(kThreads) dense_f_flush_kernel(const __grid_constant__ DenseTcArgs a) {
+    __shared__ double red[kThreads / 32];
+    const int b = blockIdx.x;
+    if (a.done != nullptr && a.done[b] != 0) return;   // the step copied a stopped instance: no partials
+    dense_deferred_f(a, b, a.t, true, red);
+}
 
 template <int LP>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -129,7 +175,17 @@ dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_const
         }
     asm volatile("griddepcontrol.wait;" ::: "memory");
 
-    if (a.done != nullptr && a.done[b] != 0) {
+    // stopped before, or the pending F of the previous step meets the rule:
+    // read once per block (the writer block of this launch may set done[b])
+    if (tid == 0) is_second = a.done != nullptr ? a.done[b] : 0;
+    __syncthreads();
+    bool stopped = is_second != 0;
+    __syncthreads();   // is_second is reused below
+    if (!stopped && a.prev_pending) {
+        const bool writer = tile == 0 && split == 0;
+        if (writer || (a.done != nullptr && a.rel_tol > 0.0)) stopped = dense_deferred_f(a, b, a.t - 1, writer, red);
+    }
+    if (stopped) {
         // stopping rule met: carry the state through (split 0 copies)
         if (a.update && split == 0)
             for (int idx = tid; idx < kTM * LP; idx += kThreads) {
@@ -259,6 +315,15 @@ dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_const
     for (int off = 16; off > 0; off >>= 1) fd += __shfl_down_sync(0xffffffffu, fd, off);
     if (lane == 0) red[warp] = fd;
     __syncthreads();
+    if (a.defer) {
+        // the next step (or the flush kernel) sums this slot
+        if (tid == 0) {
+            double bs = 0.0;
+            for (int k = 0; k < kThreads / 32; ++k) bs += red[k];
+            a.partial[(size_t)(a.t & 1) * a.B * a.ntiles + (size_t)b * a.ntiles + tile] = bs;
+        }
+        return;
+    }
     if (tid == 0) {
         double bs = 0.0;
         for (int k = 0; k < kThreads / 32; ++k) bs += red[k];
@@ -324,6 +389,25 @@ cudaError_t encode_2d(CUtensorMap *map, const void *base, long long rows, int Np
 int dense_tc_tiles(int N) { return (N + kTM - 1) / kTM; }
 int dense_tc_pitch(int N) { return (N + kTK - 1) / kTK * kTK; }
 
+cudaError_t launch_dense_f_flush(const DenseStepLaunch &l, int t, cudaStream_t st) {
+    DenseTcArgs a{};
+    a.partial = l.partial;
+    a.f_trace = l.f_trace;
+    a.f_cur = l.f_cur;
+    a.done = l.done;
+    a.status = l.status;
+    a.N = l.N;
+    a.L = l.L;
+    a.ntiles = dense_tc_tiles(l.N);
+    a.t = t;
+    a.trace_cap = l.trace_cap;
+    a.update = 1;
+    a.rel_tol = l.rel_tol;
+    a.B = l.B;
+    dense_f_flush_kernel<<<l.B, kThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dense_step_tc(const DenseStepLaunch &l, const DenseTcBuffers &tb, cudaStream_t st) {
     CUtensorMap tmQ;
     const int Np = dense_tc_pitch(l.N);
@@ -355,6 +439,9 @@ cudaError_t launch_dense_step_tc(const DenseStepLaunch &l, const DenseTcBuffers 
     a.trace_cap = l.trace_cap;
     a.update = l.update;
     a.rel_tol = l.rel_tol;
+    a.B = l.B;
+    a.defer = l.defer;
+    a.prev_pending = l.prev_pending;
     const int nsplit = a.nchunk >= 2 * kSplit ? kSplit : 1;
     dim3 grid(a.ntiles, nsplit, l.B);
     const size_t smem = (size_t)kStages * kStageBytes + 1024;

@@ -719,9 +719,15 @@ __device__ __forceinline__ bool deferred_f(const GridStepArgs &a, int b, int t_p
 // updates (stopped before, or the pending F of step t - 1 meets the rule).
 // The pending F is summed by tile (0, 0) alone when no stopping rule runs,
 // else by every tile, each of which needs the decision.
+// The block reads done[b] once (tile (0, 0) of this very launch may set it
+// while other tiles read it), so every thread takes the same branch; the
+// barrier also publishes the block's mbarrier initialisation.
 template <int NT>
 __device__ __forceinline__ bool grid_step_prologue(const GridStepArgs &a, int b, double *red) {
-    if (a.done != nullptr && a.done[b] != 0) return true;
+    __shared__ int done_b;
+    if (threadIdx.x == 0 && threadIdx.y == 0) done_b = a.done != nullptr ? a.done[b] : 0;
+    __syncthreads();
+    if (done_b != 0) return true;
     if (!a.prev_pending) return false;
     const bool writer = blockIdx.x == 0 && blockIdx.y == 0;
     const bool decide = a.done != nullptr && a.rel_tol > 0.0;

@@ -174,8 +174,8 @@ grid_tma_step_kernel(const __grid_constant__ GridTmaMaps maps, const __grid_cons
     // the previous step (when it was launched as a programmatic dependency)
     // has finished and its writes are visible
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    __syncthreads();   // the barrier is initialised before anyone waits on it
     // the pending F of the previous step is summed while the tile is in flight
+    // (the prologue's barrier also publishes the mbarrier initialisation)
     if (grid_step_prologue<GT>(a, b, red)) {
         // stopped instance: carry the state through (keeps the ping-pong parity)
         if (a.update && inside) {
@@ -480,8 +480,8 @@ grid_tma2_step_kernel(const __grid_constant__ GridTmaMaps maps, const __grid_con
         }
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    __syncthreads();   // the barrier is initialised before anyone waits on it
     // the pending F of the previous step is summed while the tile is in flight
+    // (the prologue's barrier also publishes the mbarrier initialisation)
     if (grid_step_prologue<GT2>(a, b, red)) {
         if (a.update) {
             float2 v[LP / 2];

@@ -209,14 +209,20 @@ struct DenseStepLaunch {
     __nv_bfloat16 *qt_out;       // [B][32][N] or null
     const float *eta;            // [B]
     const float *mu;             // [L][L] device
-    double *partial;             // [B][dense_nblk(N)]
+    double *partial;             // [B][dense_nblk(N)]; deferred: two slots of [B][dense_tc_tiles(N)]
     unsigned *counter;           // [B]
     double *f_trace, *f_cur;
     int *done, *status;
     int B, N, L;
     int t, trace_cap, update;
     double rel_tol;
+    // Deferred free energy of the tensor-core step in a loop (as for the
+    // grid step): defer = 1 stores the row tile's partial in slot t & 1 and
+    // takes no ticket; prev_pending = 1 sums step t - 1's partials first.
+    int defer, prev_pending;
 };
+// The pending free energy of tensor-core step t (dense_tc.cu).
+cudaError_t launch_dense_f_flush(const DenseStepLaunch &l, int t, cudaStream_t st);
 int dense_nblk(int N);
 int dense_tc_tiles(int N);
 int dense_tc_pitch(int N);   // row pitch (elements) of the BF16 K and q^T copies
