@@ -232,6 +232,16 @@ crf_status mf_profile_read(crf_t h, double *loop_ms, int32_t *launches);
  * null handle. */
 crf_status mf_use_resident(crf_t h, int32_t enable);
 
+/* mf_dense_on_the_fly -- dense handles of precision CRF_BF16 only: 1 makes
+ * the tensor-core steps compute the Gaussian weights w_ij of the fully
+ * connected model (crf_set_pairwise, dense) inside the kernel from the
+ * features instead of reading the BF16 copy of them made at crf_set_pairwise;
+ * 0 (the default) reads the copy.  Both round K to BF16 and
+ * accumulate the message in FP32; the weights agree to the rounding of the
+ * exponential.  FP32 steps (refinement) and the step constant keep using the
+ * FP32 K.  Returns CRF_E_UNSUPPORTED for other handles.  No synchronisation. */
+crf_status mf_dense_on_the_fly(crf_t h, int32_t enable);
+
 /* mf_use_graphs -- 1: mf_iterate records its step launches into a CUDA
  * graph the first time a configuration (max_iters, refine_fp32, rel_tol, the
  * step-size source, the parity of the state buffers) is seen and replays the

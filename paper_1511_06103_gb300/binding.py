@@ -85,6 +85,7 @@ _SIGS = {
     "crf_launch_count": [_vp, _vp],
     "mf_use_graphs": [_vp, C.c_int32],
     "mf_use_resident": [_vp, C.c_int32],
+    "mf_dense_on_the_fly": [_vp, C.c_int32],
     "mf_unrolled_checkpoint_floats": [_vp, C.c_int32, _vp],
     "mf_unrolled_forward": [_vp, C.c_int32, C.c_double, _vp],
     "mf_unrolled_backward": [_vp, C.c_int32, C.c_double, _vp, _vp, _vp, _vp, _vp, C.c_int32],
@@ -347,6 +348,10 @@ class CRF:
 
     def use_graphs(self, enable: bool = True) -> None:
         _call("mf_use_graphs", self.h, int(bool(enable)))
+
+    def dense_on_the_fly(self, enable: bool = True) -> None:
+        """BF16 dense handles: the tensor-core steps compute K in the kernel (mf_dense_on_the_fly)."""
+        _call("mf_dense_on_the_fly", self.h, int(bool(enable)))
 
     def use_resident(self, enable: bool = True) -> None:
         """Small grids: the whole iteration loop in one launch (the default)."""

@@ -45,6 +45,8 @@ struct crf_s {
     float *q32[2] = {nullptr, nullptr};            // [B][N][LP] + padding
     __nv_bfloat16 *qt16[2] = {nullptr, nullptr};   // [B][32][N]
     float *feats = nullptr;      // [B][N][5]
+    float *featsT = nullptr;     // BF16 dense handles: prescaled features per chunk (on-the-fly K)
+    bool dense_fly = false;      // tensor-core steps compute K in the kernel (mf_dense_on_the_fly)
     float *mu_dev = nullptr;     // [L][L]
     double theta[2] = {0.0, 0.0};
     bool bf16 = false;           // tensor-core form
@@ -179,7 +181,7 @@ void free_all(crf_t h) {
     if (h->sp_out_w) cudaFree(h->sp_out_w);
     if (h->sp_nu) cudaFree(h->sp_nu);
     if (h->sp_in_w) cudaFree(h->sp_in_w);
-    float *fd[] = {h->K32, h->q32[0], h->q32[1], h->feats, h->mu_dev};
+    float *fd[] = {h->K32, h->q32[0], h->q32[1], h->feats, h->featsT, h->mu_dev};
     for (float *p : fd)
         if (p) cudaFree(p);
     __nv_bfloat16 *bd[] = {h->K16, h->qt16[0], h->qt16[1], h->U16};
@@ -266,6 +268,7 @@ DenseStepLaunch dense_args(crf_t h, const float *eta, int t, int update, double 
     DenseStepLaunch a{};
     a.K32 = h->K32;
     a.K16 = h->K16;
+    a.featsT = h->dense_fly ? h->featsT : nullptr;
     a.q_in = h->q32[h->cur];
     a.qt_in = h->qt16[h->cur];
     a.s_in = h->s[h->cur];
@@ -636,6 +639,7 @@ crf_status crf_create(const crf_desc *desc, crf_t *out) {
             ok = ok && dalloc(&h->qt16[1], (size_t)h->B * 32 * pitch) == cudaSuccess;
             ok = ok && dalloc(&h->tcb.split_part, tiles * 2 * 128 * 32) == cudaSuccess;
             ok = ok && dalloc(&h->tcb.tile_count, tiles) == cudaSuccess;
+            ok = ok && dalloc(&h->featsT, (size_t)h->B * (pitch / 64) * 6 * 64) == cudaSuccess;
             if (ok)
                 ok = cudaMemsetAsync(h->qt16[0], 0, (size_t)h->B * 32 * pitch * 2, h->st) == cudaSuccess &&
                      cudaMemsetAsync(h->qt16[1], 0, (size_t)h->B * 32 * pitch * 2, h->st) == cudaSuccess &&
@@ -759,6 +763,7 @@ static crf_status set_pairwise_dense(crf_t h, const std::vector<float> &m, const
                           is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
     CK(h, cudaMemcpyAsync(h->mu_dev, m.data(), m.size() * sizeof(float), cudaMemcpyHostToDevice, h->st));
     CK(h, launch_dense_kernel_build(h->feats, h->K32, h->K16, h->B, h->N, th[0], th[1], h->st));
+    if (h->featsT) CK(h, launch_dense_fly_features(h->feats, h->featsT, h->B, h->N, th[0], th[1], h->st));
     h->launches += h->K16 ? 2 : 1;
     CK(h, cudaStreamSynchronize(h->st));   // m and a host feats buffer are pageable
     h->theta[0] = th[0];
@@ -1248,6 +1253,18 @@ crf_status mf_use_resident(crf_t h, int32_t enable) {
     const crf_status rc = check_handle(h);
     if (rc != CRF_OK) return rc;
     h->use_resident = enable != 0;
+    return CRF_OK;
+}
+
+crf_status mf_dense_on_the_fly(crf_t h, int32_t enable) {
+    const crf_status rc = check_handle(h);
+    if (rc != CRF_OK) return rc;
+    if (!h->dense || !h->bf16) return CRF_E_UNSUPPORTED;
+    if (h->dense_fly != (enable != 0)) {
+        for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);   // they recorded the other kernel
+        h->graphs.clear();
+    }
+    h->dense_fly = enable != 0;
     return CRF_OK;
 }
 

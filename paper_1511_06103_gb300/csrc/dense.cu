@@ -401,6 +401,53 @@ cudaError_t launch_dense_kernel_build(const float *feats, float *K32, __nv_bfloa
     return cudaGetLastError();
 }
 
+namespace {
+
+// One thread per (instance, chunk, column): the six rows of a chunk's column
+// (see launch_dense_fly_features).
+__global__ void dense_fly_features_kernel(const float *__restrict__ feats, float *__restrict__ featsT, int B, int N,
+                                          int nchunk, float sp, float sc) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)B * nchunk * 64) return;
+    const int j = (int)(idx % 64);
+    const long long bc = idx / 64;                 // b * nchunk + chunk
+    const int chunk = (int)(bc % nchunk), b = (int)(bc / nchunk);
+    const int J = chunk * 64 + j;
+    float *out = featsT + bc * 6 * 64 + j;
+    if (J >= N) {
+        for (int k = 0; k < 5; ++k) out[k * 64] = 0.f;
+        out[5 * 64] = -1e30f;
+        return;
+    }
+    const float *f = feats + ((size_t)b * N + J) * 5;
+    float g[5];
+    g[0] = sp * f[0];
+    g[1] = sp * f[1];
+    g[2] = sc * f[2];
+    g[3] = sc * f[3];
+    g[4] = sc * f[4];
+    float n2 = 0.f;
+    for (int k = 0; k < 5; ++k) {
+        out[k * 64] = 1.41421356f * g[k];
+        n2 = fmaf(g[k], g[k], n2);
+    }
+    out[5 * 64] = -n2;
+}
+
+}  // namespace
+
+cudaError_t launch_dense_fly_features(const float *feats, float *featsT, int B, int N, double theta_pos,
+                                      double theta_rgb, cudaStream_t st) {
+    // K = exp(-d^2 / (2 theta^2)) = 2^(-(s d)^2) with s = sqrt(log2(e) / (2 theta^2))
+    const double log2e = 1.4426950408889634;
+    const float sp = (float)std::sqrt(log2e / (2.0 * theta_pos * theta_pos));
+    const float sc = (float)std::sqrt(log2e / (2.0 * theta_rgb * theta_rgb));
+    const int nchunk = dense_tc_pitch(N) / 64;
+    const long long n = (long long)B * nchunk * 64;
+    dense_fly_features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(feats, featsT, B, N, nchunk, sp, sc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dense_export_q(const float *s, float *q32, __nv_bfloat16 *qt16, int B, int N, int L, int LP,
                                   cudaStream_t st) {
     const long long n = (long long)B * N * LP;

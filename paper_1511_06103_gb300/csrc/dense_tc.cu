@@ -63,6 +63,7 @@ struct DenseTcArgs {
     __nv_bfloat16 *qt_out;
     const float *eta;
     const float *mu;
+    const float *featsT;     // on-the-fly form: [B][nchunk][6][64] (dense_fly_features), else null
     float *split_part;       // [B][ntiles][kSplit][128][32]
     unsigned *tile_count;    // [B][ntiles]
     double *partial;         // [B][ntiles]
@@ -78,16 +79,17 @@ struct DenseTcArgs {
 // Sum of the n row-tile partials of one instance by the whole block: thread
 // k takes k, k + kThreads, ...; shuffle-down trees; warps in order (the order
 // of the ticket form's last-tile sum, so F is the same bit for bit).
+template <int NT>
 __device__ __forceinline__ double dense_sum_partials(const double *p, int n, double *red) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double acc = 0.0;
-    for (int k = tid; k < n; k += kThreads) acc += __ldcg(p + k);
+    for (int k = tid; k < n; k += NT) acc += __ldcg(p + k);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
     if (lane == 0) red[warp] = acc;
     __syncthreads();
     double F = 0.0;
-    for (int k = 0; k < kThreads / 32; ++k) F += red[k];
+    for (int k = 0; k < NT / 32; ++k) F += red[k];
     __syncthreads();   // red is reused
     return F;
 }
@@ -95,10 +97,11 @@ __device__ __forceinline__ double dense_sum_partials(const double *p, int n, dou
 // F of step t_prev from its deferred partials: trace entry and F_cur (by the
 // writer block) and the stopping rule, evaluated identically by every block
 // that asks.  True when instance b stops after step t_prev.
+template <int NT>
 __device__ __forceinline__ bool dense_deferred_f(const DenseTcArgs &a, int b, int t_prev, bool writer,
                                                  double *red) {
     const double F =
-        dense_sum_partials(a.partial + (size_t)(t_prev & 1) * a.B * a.ntiles + (size_t)b * a.ntiles, a.ntiles, red);
+        dense_sum_partials<NT>(a.partial + (size_t)(t_prev & 1) * a.B * a.ntiles + (size_t)b * a.ntiles, a.ntiles, red);
     bool stop = false;
     if (a.done != nullptr && a.rel_tol > 0.0 && t_prev > 0 && t_prev - 1 < a.trace_cap) {
         const double Fp = a.f_trace[(size_t)b * a.trace_cap + t_prev - 1];
@@ -117,7 +120,107 @@ __global__ void __launch_bounds__(kThreads) dense_f_flush_kernel(const __grid_co
     __shared__ double red[kThreads / 32];
     const int b = blockIdx.x;
     if (a.done != nullptr && a.done[b] != 0) return;   // the step copied a stopped instance: no partials
-    dense_deferred_f(a, b, a.t, true, red);
+    dense_deferred_f<kThreads>(a, b, a.t, true, red);
+}
+
+// The tile's rows after the product: the k ranges of a tile meet in global
+// memory (the last CTA to finish sums them in range order), then the row
+// epilogue of the tile's 128 rows and the tile's free-energy partial (kept for
+// the next step, or summed behind a ticket).  NT threads; the first kTM own a
+// row, the others only join the block barriers.
+template <int LP, int NT>
+__device__ __forceinline__ void dense_tc_tail(const DenseTcArgs &a, float (&S)[32], const float *mus, double *red,
+                                              int &is_second, int &is_last, int tile, int split, int b,
+                                              int nsplit) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = a.N, L = a.L;
+    const int row0 = tile * kTM;
+    const int r = tid;                // row within the tile (threads >= kTM only join the barriers)
+    const bool has_row = tid < kTM;
+    const size_t tile_id = (size_t)b * a.ntiles + tile;
+    if (nsplit > 1) {
+        float *mine = a.split_part + ((tile_id * kSplit + split) * kTM + r) * 32;
+#pragma unroll
+        for (int i = 0; i < 32 && has_row; i += 4)
+            *reinterpret_cast<float4 *>(mine + i) = make_float4(S[i], S[i + 1], S[i + 2], S[i + 3]);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) is_second = atomicAdd(a.tile_count + tile_id, 1u) == (unsigned)(nsplit - 1);
+        __syncthreads();
+        if (!is_second) return;
+        __threadfence();
+        // the last of the k ranges sums all partials in split order
+#pragma unroll
+        for (int i = 0; i < 32; ++i) S[i] = 0.f;
+        for (int sp = 0; sp < nsplit && has_row; ++sp) {
+            const float4 *part = reinterpret_cast<const float4 *>(a.split_part + ((tile_id * kSplit + sp) * kTM + r) * 32);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float4 v = __ldcg(part + i);
+                S[4 * i] += v.x;
+                S[4 * i + 1] += v.y;
+                S[4 * i + 2] += v.z;
+                S[4 * i + 3] += v.w;
+            }
+        }
+        if (tid == 0) a.tile_count[tile_id] = 0u;
+    }
+
+    // row epilogue on the tile's rows
+    float f = 0.f;
+    const int i = row0 + r;
+    if (has_row && i < N) {
+        const size_t o = ((size_t)b * N + i) * LP;
+        f = dense_row_update<LP>(S, mus, L, a.eta[b], a.s_in + o, a.U + o, a.s_out + o, a.q_out + o,
+                                 a.qt_out ? a.qt_out + (size_t)b * 32 * a.Np + i : nullptr, (size_t)a.Np,
+                                 a.update != 0);
+    }
+    double fd = (double)f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) fd += __shfl_down_sync(0xffffffffu, fd, off);
+    if (lane == 0) red[warp] = fd;
+    __syncthreads();
+    if (a.defer) {
+        // the next step (or the flush kernel) sums this slot
+        if (tid == 0) {
+            double bs = 0.0;
+            for (int k = 0; k < NT / 32; ++k) bs += red[k];
+            a.partial[(size_t)(a.t & 1) * a.B * a.ntiles + (size_t)b * a.ntiles + tile] = bs;
+        }
+        return;
+    }
+    if (tid == 0) {
+        double bs = 0.0;
+        for (int k = 0; k < NT / 32; ++k) bs += red[k];
+        a.partial[(size_t)b * a.ntiles + tile] = bs;
+        __threadfence();
+        is_last = atomicAdd(a.counter + b, 1u) == (unsigned)(a.ntiles - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    // last tile of the instance: all threads sum fixed strided subsets of the
+    // partials, then a fixed-shape tree (deterministic)
+    __threadfence();
+    double acc = 0.0;
+    for (int k = tid; k < a.ntiles; k += NT) acc += __ldcg(a.partial + (size_t)b * a.ntiles + k);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    __syncthreads();   // red is reused
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (tid != 0) return;
+    double F = 0.0;
+    for (int k = 0; k < NT / 32; ++k) F += red[k];
+    a.f_cur[b] = F;
+    if (!isfinite(F)) atomicExch(a.status, -6);
+    if (a.update) {
+        if (a.t < a.trace_cap) a.f_trace[(size_t)b * a.trace_cap + a.t] = F;
+        if (a.rel_tol > 0.0 && a.t > 0 && a.t - 1 < a.trace_cap && a.done != nullptr) {
+            const double Fp = a.f_trace[(size_t)b * a.trace_cap + a.t - 1];
+            if (fabs(F - Fp) <= a.rel_tol * fabs(F)) a.done[b] = a.t + 1;
+        }
+    }
+    a.counter[b] = 0u;
 }
 
 template <int LP>
@@ -183,7 +286,7 @@ dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_const
     __syncthreads();   // is_second is reused below
     if (!stopped && a.prev_pending) {
         const bool writer = tile == 0 && split == 0;
-        if (writer || (a.done != nullptr && a.rel_tol > 0.0)) stopped = dense_deferred_f(a, b, a.t - 1, writer, red);
+        if (writer || (a.done != nullptr && a.rel_tol > 0.0)) stopped = dense_deferred_f<kThreads>(a, b, a.t - 1, writer, red);
     }
     if (stopped) {
         // stopping rule met: carry the state through (split 0 copies)
@@ -271,91 +374,227 @@ dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_const
     if (warp == 0) tmem_dealloc(tmem, kTN);
     if (!ok || abort_flag) return;
 
-    const int r = warp * 32 + lane;   // row within the tile
-    const size_t tile_id = (size_t)b * a.ntiles + tile;
-    if (nsplit > 1) {
-        float *mine = a.split_part + ((tile_id * kSplit + split) * kTM + r) * 32;
-#pragma unroll
-        for (int i = 0; i < 32; i += 4)
-            *reinterpret_cast<float4 *>(mine + i) = make_float4(S[i], S[i + 1], S[i + 2], S[i + 3]);
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) is_second = atomicAdd(a.tile_count + tile_id, 1u) == (unsigned)(nsplit - 1);
-        __syncthreads();
-        if (!is_second) return;
-        __threadfence();
-        // the last of the k ranges sums all partials in split order
-#pragma unroll
-        for (int i = 0; i < 32; ++i) S[i] = 0.f;
-        for (int sp = 0; sp < nsplit; ++sp) {
-            const float4 *part = reinterpret_cast<const float4 *>(a.split_part + ((tile_id * kSplit + sp) * kTM + r) * 32);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float4 v = __ldcg(part + i);
-                S[4 * i] += v.x;
-                S[4 * i + 1] += v.y;
-                S[4 * i + 2] += v.z;
-                S[4 * i + 3] += v.w;
-            }
-        }
-        if (tid == 0) a.tile_count[tile_id] = 0u;
-    }
+    dense_tc_tail<LP, kThreads>(a, S, mus, red, is_second, is_last, tile, split, b, nsplit);
+}
 
-    // row epilogue on the tile's rows
-    float f = 0.f;
-    const int i = row0 + r;
-    if (i < N) {
-        const size_t o = ((size_t)b * N + i) * LP;
-        f = dense_row_update<LP>(S, mus, L, a.eta[b], a.s_in + o, a.U + o, a.s_out + o, a.q_out + o,
-                                 a.qt_out ? a.qt_out + (size_t)b * 32 * a.Np + i : nullptr, (size_t)a.Np,
-                                 a.update != 0);
-    }
-    double fd = (double)f;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) fd += __shfl_down_sync(0xffffffffu, fd, off);
-    if (lane == 0) red[warp] = fd;
-    __syncthreads();
-    if (a.defer) {
-        // the next step (or the flush kernel) sums this slot
-        if (tid == 0) {
-            double bs = 0.0;
-            for (int k = 0; k < kThreads / 32; ++k) bs += red[k];
-            a.partial[(size_t)(a.t & 1) * a.B * a.ntiles + (size_t)b * a.ntiles + tile] = bs;
+// ---------------------------------------------------------------------------
+// On-the-fly form: K is not read from memory but computed in the kernel.
+//
+// With features prescaled by s = sqrt(log2 e / (2 theta^2)) per group, the
+// Gaussian weight is K_ij = 2^(-|f_i - f_j|^2) = 2^(2 f_i.f_j - |f_i|^2 -
+// |f_j|^2) (zero on the diagonal).  Per chunk of 64 columns the library keeps
+// sqrt(2) f_j (5 rows of 64) and -|f_j|^2 (one row) side by side
+// (dense_fly_features), 1.5 KiB that one bulk copy brings into a stage with
+// the Q^T tile.  256 threads build the 128 x 64 BF16 block of K in the stage
+// -- thread t takes row t mod 128 and half t / 128 of the columns: three
+// packed FMAs and one exponential per weight -- in the 128-byte-swizzled
+// K-major layout of the materialised form, and thread 0 issues the same
+// tcgen05.mma chain.  The exponentials (ex2 of the special-function unit)
+// bound the step; no K bytes cross HBM.  Split-K, combine, row epilogue and
+// free energy are those of the materialised form (dense_tc_tail).
+constexpr int kFlyThreads = 256;
+constexpr int kFlyStages = 4;
+constexpr int kStageF = 6 * kTK * 4;                                       // 1.5 KiB
+constexpr int kFlyStageBytes = (kStageA + kStageB + kStageF + 1023) / 1024 * 1024;
+
+template <int LP>
+__global__ void __launch_bounds__(kFlyThreads, 1)
+dense_fly_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ DenseTcArgs a) {
+    extern __shared__ __align__(1024) uint8_t dsm[];
+    __shared__ __align__(8) uint64_t ld_bar[kFlyStages], a_bar[kFlyStages], empty_bar[kFlyStages], tmem_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(16) float mus[kMaxLabels * kMaxLabels];   // mu^T, zero-padded
+    __shared__ double red[kFlyThreads / 32];
+    __shared__ int is_second, is_last, abort_flag;
+
+    const int tile = blockIdx.x, split = blockIdx.y, b = blockIdx.z;
+    const int nsplit = gridDim.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const int N = a.N, L = a.L;
+    const int row0 = tile * kTM;
+    const int c_begin = (a.nchunk * split) / nsplit, c_end = (a.nchunk * (split + 1)) / nsplit;
+    const int nc = c_end - c_begin;
+    const int rr = tid & (kTM - 1), half = tid >> 7;   // row of the tile, half of a chunk's columns
+    const int i = row0 + rr;
+
+    uint8_t *ring = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    load_mu_transposed(mus, a.mu, L, tid, kFlyThreads);
+    if (tid == 0) {
+        for (int s = 0; s < kFlyStages; ++s) {
+            mbar_init(&ld_bar[s], 1);
+            mbar_init(&a_bar[s], kFlyThreads / 32);
+            mbar_init(&empty_bar[s], 1);
         }
+        mbar_init(&tmem_bar, 1);
+        abort_flag = 0;
+        mbar_init_fence();
+    }
+    if (warp == 0) tmem_alloc(&tmem_slot, kTN);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    auto fblock = [&](int c) { return a.featsT + ((size_t)b * a.nchunk + (c_begin + c)) * (kStageF / 4); };
+    // this thread's row: sqrt(2) f_i and -|f_i|^2 (rows past N get zeros; their results are not used)
+    float fi[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, ni = 0.f;
+    if (i < N) {
+        const float *fr = a.featsT + ((size_t)b * a.nchunk + i / kTK) * (kStageF / 4) + (i % kTK);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) fi[k] = __ldg(fr + k * kTK);
+        ni = __ldg(fr + 5 * kTK);
+    }
+    // the features do not change between steps: the first stages' blocks are
+    // requested before waiting for the previous step (which writes Q^T)
+    const int npre = nc < kFlyStages ? nc : kFlyStages;
+    if (tid == 0)
+        for (int c = 0; c < npre; ++c) {
+            mbar_expect_tx_only(&ld_bar[c], kStageF);
+            bulk_load(ring + c * kFlyStageBytes + kStageA + kStageB, fblock(c), kStageF, &ld_bar[c]);
+        }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+
+    if (tid == 0) is_second = a.done != nullptr ? a.done[b] : 0;
+    __syncthreads();
+    bool stopped = is_second != 0;
+    __syncthreads();   // is_second is reused below
+    if (!stopped && a.prev_pending) {
+        const bool writer = tile == 0 && split == 0;
+        if (writer || (a.done != nullptr && a.rel_tol > 0.0))
+            stopped = dense_deferred_f<kFlyThreads>(a, b, a.t - 1, writer, red);
+    }
+    if (stopped) {
+        // stopping rule met: carry the state through (split 0 copies)
+        if (a.update && split == 0)
+            for (int idx = tid; idx < kTM * LP; idx += kFlyThreads) {
+                const int r = row0 + idx / LP;
+                if (r < N) {
+                    const size_t o = ((size_t)b * N + r) * LP + idx % LP;
+                    a.s_out[o] = a.s_in[o];
+                    const float q = idx % LP < L ? __expf(a.s_in[o]) : 0.f;
+                    a.q_out[o] = q;
+                    if (a.qt_out) a.qt_out[((size_t)b * 32 + idx % LP) * a.Np + r] = __float2bfloat16_rn(q);
+                }
+            }
+        if (tid == 0)
+            for (int c = 0; c < npre; ++c) {   // no copy into this CTA's memory outlives it
+                mbar_arrive(&ld_bar[c]);
+                mbar_wait(&ld_bar[c], 0, a.status);
+            }
+        __syncthreads();
+        if (warp == 0) tmem_dealloc(tmem, kTN);
         return;
     }
-    if (tid == 0) {
-        double bs = 0.0;
-        for (int k = 0; k < kThreads / 32; ++k) bs += red[k];
-        a.partial[(size_t)b * a.ntiles + tile] = bs;
-        __threadfence();
-        is_last = atomicAdd(a.counter + b, 1u) == (unsigned)(a.ntiles - 1);
-    }
-    __syncthreads();
-    if (!is_last) return;
-    // last tile of the instance: all threads sum fixed strided subsets of the
-    // partials, then a fixed-shape tree (deterministic)
-    __threadfence();
-    double acc = 0.0;
-    for (int k = tid; k < a.ntiles; k += kThreads) acc += __ldcg(a.partial + (size_t)b * a.ntiles + k);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    __syncthreads();   // red is reused
-    if (lane == 0) red[warp] = acc;
-    __syncthreads();
-    if (tid != 0) return;
-    double F = 0.0;
-    for (int k = 0; k < kThreads / 32; ++k) F += red[k];
-    a.f_cur[b] = F;
-    if (!isfinite(F)) atomicExch(a.status, -6);
-    if (a.update) {
-        if (a.t < a.trace_cap) a.f_trace[(size_t)b * a.trace_cap + a.t] = F;
-        if (a.rel_tol > 0.0 && a.t > 0 && a.t - 1 < a.trace_cap && a.done != nullptr) {
-            const double Fp = a.f_trace[(size_t)b * a.trace_cap + a.t - 1];
-            if (fabs(F - Fp) <= a.rel_tol * fabs(F)) a.done[b] = a.t + 1;
+
+    volatile int *abort_v = &abort_flag;
+    if (tid == 0)
+        for (int c = 0; c < npre; ++c) {   // Q^T of the first stages (their features are on the way)
+            mbar_expect_tx(&ld_bar[c], kStageB);
+            tma_load_2d(ring + c * kFlyStageBytes + kStageA, &tmQ, &ld_bar[c], (c_begin + c) * kTK, b * 32);
         }
+    int issued = npre;   // chunks whose stage loads thread 0 has requested
+    int c = 0;
+    for (; c < nc; ++c) {
+        const int s = c % kFlyStages;
+        const uint32_t ph = (uint32_t)(c / kFlyStages) & 1u;
+        uint8_t *st = ring + s * kFlyStageBytes;
+        if (!mbar_wait(&ld_bar[s], ph, a.status)) *abort_v = 1;
+        if (!*abort_v) {
+            // K[i][j] for this thread's row and 32 columns of the chunk
+            const float *F = reinterpret_cast<const float *>(st + kStageA + kStageB);
+            const int dj = i - (c_begin + c) * kTK;   // the diagonal's column in this chunk
+            uint32_t w[16];
+#pragma unroll
+            for (int q4 = 0; q4 < 8; ++q4) {
+                const int j = half * 32 + q4 * 4;
+                const float4 nj = *reinterpret_cast<const float4 *>(F + 5 * kTK + j);
+                float2 e01 = add2(make_float2(nj.x, nj.y), splat2(ni));
+                float2 e23 = add2(make_float2(nj.z, nj.w), splat2(ni));
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const float4 fj = *reinterpret_cast<const float4 *>(F + k * kTK + j);
+                    const float2 fk = splat2(fi[k]);
+                    e01 = fma2(fk, make_float2(fj.x, fj.y), e01);
+                    e23 = fma2(fk, make_float2(fj.z, fj.w), e23);
+                }
+                float v0 = ex2_ftz(e01.x), v1 = ex2_ftz(e01.y), v2 = ex2_ftz(e23.x), v3 = ex2_ftz(e23.y);
+                if (j == dj) v0 = 0.f;
+                if (j + 1 == dj) v1 = 0.f;
+                if (j + 2 == dj) v2 = 0.f;
+                if (j + 3 == dj) v3 = 0.f;
+                const __nv_bfloat162 p01 = __floats2bfloat162_rn(v0, v1), p23 = __floats2bfloat162_rn(v2, v3);
+                w[2 * q4] = *reinterpret_cast<const uint32_t *>(&p01);
+                w[2 * q4 + 1] = *reinterpret_cast<const uint32_t *>(&p23);
+            }
+            // the row's 16-byte groups in the 128-byte-swizzled K-major layout
+            uint8_t *arow = st + rr * 128;
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                const int gg = half * 4 + g;
+                *reinterpret_cast<uint4 *>(arow + ((gg ^ (rr & 7)) << 4)) =
+                    make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
+            }
+        }
+        fence_async_smem();   // the tensor cores read the block
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&a_bar[s]);
+        if (tid == 0) {
+            if (!mbar_wait(&a_bar[s], ph, a.status)) *abort_v = 1;
+            if (!*abort_v) {
+                fence_after_sync();
+                const uint32_t sa = smem_u32(st);
+                const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + kStageA);
+#pragma unroll
+                for (int kk = 0; kk < kTK / 16; ++kk)
+                    mma_bf16(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), kIdesc,
+                             (c > 0 || kk > 0) ? 1u : 0u);
+            }
+            mma_commit(&empty_bar[s]);
+            // refill the stage of chunk c - 1, whose MMAs were issued an iteration ago
+            const int cn = c - 1 + kFlyStages;
+            if (c >= 1 && cn < nc && !*abort_v) {
+                const int sp = (c - 1) % kFlyStages;
+                if (mbar_wait(&empty_bar[sp], (uint32_t)((c - 1) / kFlyStages) & 1u, a.status)) {
+                    uint8_t *sn = ring + sp * kFlyStageBytes;
+                    mbar_expect_tx(&ld_bar[sp], kStageB + kStageF);
+                    tma_load_2d(sn + kStageA, &tmQ, &ld_bar[sp], (c_begin + cn) * kTK, b * 32);
+                    bulk_load(sn + kStageA + kStageB, fblock(cn), kStageF, &ld_bar[sp]);
+                    ++issued;
+                } else {
+                    *abort_v = 1;
+                }
+            }
+        }
+        if (*abort_v) break;
     }
-    a.counter[b] = 0u;
+    if (tid == 0) {
+        mma_commit(&tmem_bar);
+        // after an abort: the copies already requested land before the CTA leaves (bounded)
+        for (int cc = c; cc < issued; ++cc)
+            mbar_wait(&ld_bar[cc % kFlyStages], (uint32_t)(cc / kFlyStages) & 1u, a.status);
+    }
+    __syncwarp();
+
+    float S[32];
+    bool ok = true;
+    if (nc > 0) {
+        ok = mbar_wait(&tmem_bar, 0, a.status) && !*abort_v;
+        fence_after_sync();
+        if (ok && warp < kTM / 32) {
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), S);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) S[k] = 0.f;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) S[k] = 0.f;
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTN);
+    if (!ok || *abort_v) return;
+    dense_tc_tail<LP, kFlyThreads>(a, S, mus, red, is_second, is_last, tile, split, b, nsplit);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -422,6 +661,8 @@ cudaError_t launch_dense_step_tc(const DenseStepLaunch &l, const DenseTcBuffers 
     a.qt_out = l.qt_out;
     a.eta = l.eta;
     a.mu = l.mu;
+    a.featsT = l.featsT;
+    const bool fly = l.featsT != nullptr;   // K computed in the kernel
     a.split_part = tb.split_part;
     a.tile_count = tb.tile_count;
     a.partial = l.partial;
@@ -444,12 +685,12 @@ cudaError_t launch_dense_step_tc(const DenseStepLaunch &l, const DenseTcBuffers 
     a.prev_pending = l.prev_pending;
     const int nsplit = a.nchunk >= 2 * kSplit ? kSplit : 1;
     dim3 grid(a.ntiles, nsplit, l.B);
-    const size_t smem = (size_t)kStages * kStageBytes + 1024;
+    const size_t smem = fly ? (size_t)kFlyStages * kFlyStageBytes + 1024 : (size_t)kStages * kStageBytes + 1024;
     // programmatic dependent launch: the step may start while the previous
     // one drains (the kernel waits before it reads anything a step writes)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
-    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.blockDim = dim3(fly ? kFlyThreads : kThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute pdl[1];
@@ -459,12 +700,14 @@ cudaError_t launch_dense_step_tc(const DenseStepLaunch &l, const DenseTcBuffers 
     cfg.numAttrs = 1;
     switch (storage_labels(l.L)) {
 #define PROXMF_TC_CASE(LPV)                                                                                   \
-    case LPV:                                                                                                 \
-        e = cudaFuncSetAttribute(dense_step_tc_kernel<LPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    case LPV: {                                                                                               \
+        auto kern = fly ? dense_fly_tc_kernel<LPV> : dense_step_tc_kernel<LPV>;                               \
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);               \
         if (e != cudaSuccess) return e;                                                                       \
-        e = cudaLaunchKernelEx(&cfg, dense_step_tc_kernel<LPV>, tmQ, a);                                      \
+        e = cudaLaunchKernelEx(&cfg, kern, tmQ, a);                                                           \
         if (e != cudaSuccess) return e;                                                                       \
-        break;
+        break;                                                                                                \
+    }
         PROXMF_TC_CASE(2)
         PROXMF_TC_CASE(4)
         PROXMF_TC_CASE(8)

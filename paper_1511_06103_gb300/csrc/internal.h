@@ -209,6 +209,8 @@ struct DenseStepLaunch {
     __nv_bfloat16 *qt_out;       // [B][32][N] or null
     const float *eta;            // [B]
     const float *mu;             // [L][L] device
+    const float *featsT;         // tensor-core form computing K in the kernel: [B][nchunk][6][64]
+                                 // (launch_dense_fly_features), else null (K16 is read)
     double *partial;             // [B][dense_nblk(N)]; deferred: two slots of [B][dense_tc_tiles(N)]
     unsigned *counter;           // [B]
     double *f_trace, *f_cur;
@@ -223,6 +225,11 @@ struct DenseStepLaunch {
 };
 // The pending free energy of tensor-core step t (dense_tc.cu).
 cudaError_t launch_dense_f_flush(const DenseStepLaunch &l, int t, cudaStream_t st);
+// Prescaled features of the on-the-fly tensor-core form, per chunk of 64
+// columns: sqrt(2) s f_k (k = 0..4; s = sqrt(log2 e / (2 theta^2)) of the
+// position or colour group) and -|s f|^2; columns past N get 0 and -1e30.
+cudaError_t launch_dense_fly_features(const float *feats, float *featsT, int B, int N, double theta_pos,
+                                      double theta_rgb, cudaStream_t st);
 int dense_nblk(int N);
 int dense_tc_tiles(int N);
 int dense_tc_pitch(int N);   // row pitch (elements) of the BF16 K and q^T copies

@@ -129,9 +129,11 @@ def dense(env):
     return d, side, eta32, s_ref, F_ref
 
 
-def run_dense(binding, torch, d, side, iters, precision, refine=0):
+def run_dense(binding, torch, d, side, iters, precision, refine=0, fly=False):
     dev = torch.device("cuda:0")
     with binding.CRF(binding.CRF_DENSE_GAUSS, d["L"], side, side, precision=precision) as crf:
+        if fly:
+            crf.dense_on_the_fly(True)
         crf.set_unary(torch.from_numpy(d["U"]).to(dev))
         crf.set_pairwise(torch.from_numpy(d["mu"]).to(dev), torch.from_numpy(d["feats"]).to(dev),
                          theta=np.array(d["theta"], np.float32))
@@ -153,10 +155,11 @@ def test_dense_full_solve(env, dense):
     assert H.f_rel_close(F, F_ref[-1], TOL_F), H.f_rel_err(F, F_ref[-1])
 
 
-def test_dense_full_solve_bf16(env, dense):
+@pytest.mark.parametrize("fly", [False, True], ids=["stored_K", "K_in_kernel"])
+def test_dense_full_solve_bf16(env, dense, fly):
     binding, oracle, torch = env
     d, side, eta, s_ref, F_ref = dense
-    s, F, trace = run_dense(binding, torch, d, side, DENSE_ITERS - 2, binding.CRF_BF16, refine=2)
+    s, F, trace = run_dense(binding, torch, d, side, DENSE_ITERS - 2, binding.CRF_BF16, refine=2, fly=fly)
     dq = np.abs(np.exp(s) - np.exp(s_ref)).max()
     assert dq <= TOL_Q_BF16, dq
     assert H.f_rel_close(F, F_ref[-1], TOL_F_BF16), H.f_rel_err(F, F_ref[-1])

@@ -156,10 +156,11 @@ TOL_Q_BF16 = 1e-2
 TOL_F_BF16 = 1e-3
 
 
-def gpu_run_bf16(binding, torch, d, eta, iters, refine=0, s0=None):
+def gpu_run_bf16(binding, torch, d, eta, iters, refine=0, s0=None, fly=False):
     dev = torch.device("cuda:0")
     side = int(round(math.sqrt(d["N"])))
     with binding.CRF(binding.CRF_DENSE_GAUSS, d["L"], side, d["N"] // side, precision=binding.CRF_BF16) as crf:
+        crf.dense_on_the_fly(fly)
         crf.set_unary(torch.from_numpy(d["U"]).to(dev))
         crf.set_pairwise(torch.from_numpy(d["mu"]).to(dev), torch.from_numpy(d["feats"]).to(dev),
                          theta=np.array(d["theta"], np.float32))
@@ -230,3 +231,56 @@ def test_dense_mid_size_trajectories(env):
     s, F, _ = gpu_run_bf16(binding, torch, d, eta, 28, refine=2)
     assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q_BF16
     assert H.f_close(F, F_ref[-1], d["N"], TOL_F_BF16)
+
+
+# ------------------------------------------------ BF16 form, K computed in the kernel
+# The on-the-fly form builds each 128 x 64 block of K from the features in
+# the kernel (K_ij = 2^(-|s (f_i - f_j)|^2), zero diagonal) instead of reading
+# the BF16 copy: the same rounding to BF16 and the same tolerances.
+
+
+@pytest.mark.parametrize("side,L", [(10, 21), (12, 5), (9, 2), (13, 17)])
+def test_dense_on_the_fly_single_step(env, side, L):
+    binding, oracle, torch = env
+    d = synth.dense_gaussian(side=side, L=L, seed=side * 7 + L)
+    s0 = synth.random_logq(d["N"], L, seed=11 + L)
+    m = oracle_model(oracle, d)
+    s_ref = m.prox_step(0.3, f64(s0))
+    s, _, _ = gpu_run_bf16(binding, torch, d, 0.3, 1, s0=s0, fly=True)
+    assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q_BF16
+    assert np.all(np.isfinite(s))
+
+
+def test_dense_on_the_fly_trajectory_refined(env):
+    binding, oracle, torch = env
+    d = synth.dense_gaussian(side=16, L=21, seed=5)
+    m = oracle_model(oracle, d)
+    s_ref, F_ref = m.parallel_prox(0.2, 35)
+    s, F, trace = gpu_run_bf16(binding, torch, d, 0.2, 30, refine=5, fly=True)
+    assert np.abs(np.exp(s) - np.exp(s_ref)).max() <= TOL_Q_BF16
+    assert H.f_close(F, F_ref[-1], d["N"], TOL_F_BF16)
+    for t in range(35):
+        assert H.f_close(trace[t], F_ref[t], d["N"], 2e-2)
+
+
+def test_dense_on_the_fly_agrees_with_the_stored_copy(env):
+    """Both forms round K to BF16; the weights differ only where the two
+    exponentials round to neighbouring BF16 values, so one step from the same
+    state agrees far inside the BF16 tolerance, and repeated runs are
+    bit-identical."""
+    binding, oracle, torch = env
+    d = synth.dense_gaussian(side=20, L=21, seed=3)
+    s0 = synth.random_logq(d["N"], 21, seed=4)
+    s_a, F_a, _ = gpu_run_bf16(binding, torch, d, 0.3, 1, s0=s0, fly=False)
+    s_b, F_b, _ = gpu_run_bf16(binding, torch, d, 0.3, 1, s0=s0, fly=True)
+    s_c, F_c, _ = gpu_run_bf16(binding, torch, d, 0.3, 1, s0=s0, fly=True)
+    assert np.abs(np.exp(s_a) - np.exp(s_b)).max() <= 2e-3
+    assert np.array_equal(s_b, s_c) and F_b == F_c
+
+
+def test_dense_on_the_fly_rejected_on_fp32_handles(env):
+    binding, _, _ = env
+    d = synth.dense_gaussian(side=8, L=3, seed=1)
+    with make(binding, d) as crf:
+        with pytest.raises(binding.ProxMFError):
+            crf.dense_on_the_fly(True)
