@@ -242,7 +242,9 @@ dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_const
     const int c_begin = (a.nchunk * split) / nsplit, c_end = (a.nchunk * (split + 1)) / nsplit;
     const int nc = c_end - c_begin;
 
-    uint8_t *ring = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
+    // aligned by pointer arithmetic on the shared base, so that accesses
+    // through it stay shared-memory instructions
+    uint8_t *ring = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
     // The next step may be launched now (programmatic dependent launch); it
     // takes the SMs this launch frees.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -417,7 +419,9 @@ dense_fly_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_consta
     const int rr = tid & (kTM - 1), half = tid >> 7;   // row of the tile, half of a chunk's columns
     const int i = row0 + rr;
 
-    uint8_t *ring = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
+    // aligned by pointer arithmetic on the shared base, so that accesses
+    // through it stay shared-memory instructions
+    uint8_t *ring = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     load_mu_transposed(mus, a.mu, L, tid, kFlyThreads);
     if (tid == 0) {
