@@ -290,9 +290,17 @@ def algorithmic_bytes_per_launch() -> int:
 DENSE_SIDE, DENSE_L, DENSE_ITERS = 96, 21, 30
 
 
-def run_dense(args, dev, precision, peak):
+# Exponentials per second of the special-function unit: 16 results per clock
+# per SM (CUDA's throughput table for the base-2 exponential) x 152 SMs x the
+# 2070 MHz maximum SM clock.  The bound of the dense step that computes K in
+# the kernel (one exponential per weight).
+EX2_PEAK_G = 16 * 152 * 2070e6 / 1e9
+
+
+def run_dense(args, dev, precision, peak, fly=False):
     """Fully connected Gaussian CRF, N = 96 x 96 = 9216, L = 21, 30 iterations:
-    device-timed solves (q^0, 30 steps, final F) with the model resident."""
+    device-timed solves (q^0, 30 steps, final F) with the model resident.
+    fly: the BF16 tensor-core steps compute K in the kernel (no K bytes read)."""
     import torch
 
     from paper_1511_06103_gb300 import binding, synth
@@ -300,6 +308,8 @@ def run_dense(args, dev, precision, peak):
     stream = torch.cuda.current_stream(dev)
     crf = binding.CRF(binding.CRF_DENSE_GAUSS, DENSE_L, DENSE_SIDE, DENSE_SIDE, precision=precision,
                       stream=stream.cuda_stream)
+    if fly:
+        crf.dense_on_the_fly(True)
     crf.set_unary(torch.from_numpy(d["U"]).to(dev))
     crf.set_pairwise(torch.from_numpy(d["mu"]).to(dev), torch.from_numpy(d["feats"]).to(dev),
                      theta=np.array(d["theta"], np.float32))
@@ -350,6 +360,18 @@ def run_dense(args, dev, precision, peak):
     kbytes = N * N * (2 if precision == binding.CRF_BF16 else 4)
     kms_all = float(np.mean(kern))
     kms = float(np.mean(kern_only)) if kern_only else kms_all
+    if fly:
+        # N^2 weights, one exponential each, per launch
+        gexp = N * N / (kms / 1000.0) / 1e9
+        roof = {"bound": "alu", "achieved": gexp, "peak": EX2_PEAK_G, "unit": "Gexp/s",
+                "frac": gexp / EX2_PEAK_G, "exp_per_launch": N * N, "hbm_bytes_of_K": 0,
+                "note": "K computed in the kernel: bound by the base-2 exponentials of the special-function "
+                        "unit (peak: 16 per clock per SM x 152 SMs x 2070 MHz); launch time of the step kernel "
+                        "alone"}
+        return {"value": N * DENSE_L * iters / (ms_step / 1000.0), "unit": UNIT, "ms_per_solve": ms_step,
+                "iters": DENSE_ITERS, "refine_fp32": refine, "avg_launch_ms": kms,
+                "avg_launch_ms_with_refine": kms_all, "roofline": roof, "final_F": F, "eta": float(eta[0]),
+                "Lambda": float(lam[0]), "q": q}
     return {"value": N * DENSE_L * iters / (ms_step / 1000.0), "unit": UNIT, "ms_per_solve": ms_step,
             "iters": DENSE_ITERS, "refine_fp32": refine, "avg_launch_ms": kms, "avg_launch_ms_with_refine": kms_all,
             "roofline": {"bound": "hbm", "achieved": kbytes / (kms / 1000.0) / 1e9, "peak": peak,
@@ -868,10 +890,11 @@ def run_ours(args, world, rank, local):
         return
     if args.dense_only:
         peak, _ = measured_peaks()
-        for prec in (binding.CRF_FP32, binding.CRF_BF16):
-            r = run_dense(args, dev, prec, peak)
+        for prec, fly in ((binding.CRF_FP32, False), (binding.CRF_BF16, False), (binding.CRF_BF16, True)):
+            r = run_dense(args, dev, prec, peak, fly)
             r.pop("q")
-            print(json.dumps({"dense_precision": "bf16" if prec else "f32", **r}), flush=True)
+            print(json.dumps({"dense_precision": ("bf16" if prec else "f32") + ("_K_in_kernel" if fly else ""),
+                              **r}), flush=True)
         return
     B = args.batch
     ds = [synth.segmentation_grid(H=H, W=W, L=L, conn=CONN, seed=sd) for sd in replica_seeds(rank, B)]
@@ -998,13 +1021,20 @@ def run_ours(args, world, rank, local):
     if not args.no_dense and world == 1:
         r32 = run_dense(args, dev, binding.CRF_FP32, peak)
         r16 = run_dense(args, dev, binding.CRF_BF16, peak)
+        rfly = run_dense(args, dev, binding.CRF_BF16, peak, fly=True)
+        dq_fly = float(np.abs(r32["q"] - rfly.pop("q")).max())
         dq = float(np.abs(r32.pop("q") - r16.pop("q")).max())
         dense = {"workload": "fully connected Gaussian CRF, N=96x96=9216, L=21, 30 iterations "
                              "(theta_pos=3, theta_rgb=13), model resident; the BF16 form runs 28 "
                              "tensor-core steps and 2 FP32 refinement steps",
                  "f32": r32, "bf16_tc": r16, "bf16_speedup": r16["value"] / r32["value"],
                  "final_F_rel_diff": abs(r16["final_F"] - r32["final_F"]) / abs(r32["final_F"]),
-                 "q_max_abs_diff": dq}
+                 "q_max_abs_diff": dq,
+                 "bf16_tc_K_in_kernel": {**rfly,
+                                         "speedup_vs_f32": rfly["value"] / r32["value"],
+                                         "final_F_rel_diff_vs_f32": abs(rfly["final_F"] - r32["final_F"]) /
+                                         abs(r32["final_F"]),
+                                         "q_max_abs_diff_vs_f32": dq_fly}}
     denoise = None
     if not args.no_denoising and world == 1:
         denoise = run_denoising(args, dev)

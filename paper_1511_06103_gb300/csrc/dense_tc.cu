@@ -387,15 +387,20 @@ dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_const
 // |f_j|^2) (zero on the diagonal).  Per chunk of 64 columns the library keeps
 // sqrt(2) f_j (5 rows of 64) and -|f_j|^2 (one row) side by side
 // (dense_fly_features), 1.5 KiB that one bulk copy brings into a stage with
-// the Q^T tile.  256 threads build the 128 x 64 BF16 block of K in the stage
-// -- thread t takes row t mod 128 and half t / 128 of the columns: three
-// packed FMAs and one exponential per weight -- in the 128-byte-swizzled
-// K-major layout of the materialised form, and thread 0 issues the same
-// tcgen05.mma chain.  The exponentials (ex2 of the special-function unit)
-// bound the step; no K bytes cross HBM.  Split-K, combine, row epilogue and
-// free energy are those of the materialised form (dense_tc_tail).
-constexpr int kFlyThreads = 256;
-constexpr int kFlyStages = 4;
+// the Q^T tile.  Eight builder warps make the 128 x 64 BF16 block of K in
+// the stage -- thread t takes row t mod 128 and part t / 128 of the columns:
+// three packed FMAs and one exponential per weight -- in the 128-byte-swizzled
+// K-major layout of the materialised form, and one more warp issues the same
+// tcgen05.mma chain and the copies of the stages ahead.  No K bytes cross
+// HBM; the step is bound by the builders' instruction stream (loads of the
+// column features, packed FMAs, exponentials, conversions and the per-chunk
+// barriers), not by the special-function unit alone.  Split-K, combine, row
+// epilogue and free energy are those of the materialised form (dense_tc_tail).
+constexpr int kFlyBuilders = 256;                // eight warps build the blocks of K (sixteen measured slower)
+constexpr int kFlyParts = kFlyBuilders / kTM;     // column parts of a chunk, one per builder of a row
+constexpr int kFlyCols = kTK / kFlyParts;         // columns per builder and chunk
+constexpr int kFlyThreads = kFlyBuilders + 32;   // and one more issues the MMAs and copies
+constexpr int kFlyStages = 8;   // the copies of a stage take about two chunks' work to land
 constexpr int kStageF = 6 * kTK * 4;                                       // 1.5 KiB
 constexpr int kFlyStageBytes = (kStageA + kStageB + kStageF + 1023) / 1024 * 1024;
 
@@ -416,8 +421,8 @@ dense_fly_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_consta
     const int row0 = tile * kTM;
     const int c_begin = (a.nchunk * split) / nsplit, c_end = (a.nchunk * (split + 1)) / nsplit;
     const int nc = c_end - c_begin;
-    const int rr = tid & (kTM - 1), half = tid >> 7;   // row of the tile, half of a chunk's columns
-    const int i = row0 + rr;
+    const int rr = tid & (kTM - 1), half = tid >> 7;   // builders: row of the tile, part of a chunk's columns
+    const int i = tid < kFlyBuilders ? row0 + rr : N;
 
     // aligned by pointer arithmetic on the shared base, so that accesses
     // through it stay shared-memory instructions
@@ -427,7 +432,7 @@ dense_fly_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_consta
     if (tid == 0) {
         for (int s = 0; s < kFlyStages; ++s) {
             mbar_init(&ld_bar[s], 1);
-            mbar_init(&a_bar[s], kFlyThreads / 32);
+            mbar_init(&a_bar[s], kFlyBuilders / 32);
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&tmem_bar, 1);
@@ -491,62 +496,73 @@ dense_fly_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_consta
     }
 
     volatile int *abort_v = &abort_flag;
-    if (tid == 0)
-        for (int c = 0; c < npre; ++c) {   // Q^T of the first stages (their features are on the way)
-            mbar_expect_tx(&ld_bar[c], kStageB);
+    if (warp < kFlyBuilders / 32) {
+        // builders: the 128 x 64 block of K of each chunk
+        for (int c = 0; c < nc; ++c) {
+            const int s = c % kFlyStages;
+            const uint32_t ph = (uint32_t)(c / kFlyStages) & 1u;
+            uint8_t *st = ring + s * kFlyStageBytes;
+            if (!mbar_wait(&ld_bar[s], ph, a.status)) *abort_v = 1;
+            if (!*abort_v) {
+                // K[i][j] for this thread's row and kFlyCols columns of the chunk
+                const float *F = reinterpret_cast<const float *>(st + kStageA + kStageB);
+                const int dj = i - (c_begin + c) * kTK;                // the diagonal's column in this chunk
+                const bool diag = (unsigned)(dj - half * kFlyCols) < (unsigned)kFlyCols;   // in this thread's columns
+                uint32_t w[kFlyCols / 2];
+#pragma unroll
+                for (int q4 = 0; q4 < kFlyCols / 4; ++q4) {
+                    const int j = half * kFlyCols + q4 * 4;
+                    const float4 nj = *reinterpret_cast<const float4 *>(F + 5 * kTK + j);
+                    float2 e01 = add2(make_float2(nj.x, nj.y), splat2(ni));
+                    float2 e23 = add2(make_float2(nj.z, nj.w), splat2(ni));
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        const float4 fj = *reinterpret_cast<const float4 *>(F + k * kTK + j);
+                        const float2 fk = splat2(fi[k]);
+                        e01 = fma2(fk, make_float2(fj.x, fj.y), e01);
+                        e23 = fma2(fk, make_float2(fj.z, fj.w), e23);
+                    }
+                    float v0 = ex2_ftz(e01.x), v1 = ex2_ftz(e01.y), v2 = ex2_ftz(e23.x), v3 = ex2_ftz(e23.y);
+                    if (diag) {
+                        if (j == dj) v0 = 0.f;
+                        if (j + 1 == dj) v1 = 0.f;
+                        if (j + 2 == dj) v2 = 0.f;
+                        if (j + 3 == dj) v3 = 0.f;
+                    }
+                    const __nv_bfloat162 p01 = __floats2bfloat162_rn(v0, v1), p23 = __floats2bfloat162_rn(v2, v3);
+                    w[2 * q4] = *reinterpret_cast<const uint32_t *>(&p01);
+                    w[2 * q4 + 1] = *reinterpret_cast<const uint32_t *>(&p23);
+                }
+                // the row's 16-byte groups in the 128-byte-swizzled K-major layout
+                uint8_t *arow = st + rr * 128;
+#pragma unroll
+                for (int g = 0; g < kFlyCols / 8; ++g) {
+                    const int gg = half * (kFlyCols / 8) + g;
+                    *reinterpret_cast<uint4 *>(arow + ((gg ^ (rr & 7)) << 4)) =
+                        make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
+                }
+            }
+            fence_async_smem();   // the tensor cores read the block
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&a_bar[s]);
+            if (*abort_v) break;
+        }
+    } else if (lane == 0) {
+        // the issuer: Q^T of the first stages, then per chunk the MMAs and the
+        // copies of the chunk kFlyStages - 1 ahead
+        for (int c = 0; c < npre; ++c) {
+            mbar_expect_tx(&ld_bar[c], kStageB);   // arrives; the features were counted above
             tma_load_2d(ring + c * kFlyStageBytes + kStageA, &tmQ, &ld_bar[c], (c_begin + c) * kTK, b * 32);
         }
-    int issued = npre;   // chunks whose stage loads thread 0 has requested
-    int c = 0;
-    for (; c < nc; ++c) {
-        const int s = c % kFlyStages;
-        const uint32_t ph = (uint32_t)(c / kFlyStages) & 1u;
-        uint8_t *st = ring + s * kFlyStageBytes;
-        if (!mbar_wait(&ld_bar[s], ph, a.status)) *abort_v = 1;
-        if (!*abort_v) {
-            // K[i][j] for this thread's row and 32 columns of the chunk
-            const float *F = reinterpret_cast<const float *>(st + kStageA + kStageB);
-            const int dj = i - (c_begin + c) * kTK;   // the diagonal's column in this chunk
-            uint32_t w[16];
-#pragma unroll
-            for (int q4 = 0; q4 < 8; ++q4) {
-                const int j = half * 32 + q4 * 4;
-                const float4 nj = *reinterpret_cast<const float4 *>(F + 5 * kTK + j);
-                float2 e01 = add2(make_float2(nj.x, nj.y), splat2(ni));
-                float2 e23 = add2(make_float2(nj.z, nj.w), splat2(ni));
-#pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    const float4 fj = *reinterpret_cast<const float4 *>(F + k * kTK + j);
-                    const float2 fk = splat2(fi[k]);
-                    e01 = fma2(fk, make_float2(fj.x, fj.y), e01);
-                    e23 = fma2(fk, make_float2(fj.z, fj.w), e23);
-                }
-                float v0 = ex2_ftz(e01.x), v1 = ex2_ftz(e01.y), v2 = ex2_ftz(e23.x), v3 = ex2_ftz(e23.y);
-                if (j == dj) v0 = 0.f;
-                if (j + 1 == dj) v1 = 0.f;
-                if (j + 2 == dj) v2 = 0.f;
-                if (j + 3 == dj) v3 = 0.f;
-                const __nv_bfloat162 p01 = __floats2bfloat162_rn(v0, v1), p23 = __floats2bfloat162_rn(v2, v3);
-                w[2 * q4] = *reinterpret_cast<const uint32_t *>(&p01);
-                w[2 * q4 + 1] = *reinterpret_cast<const uint32_t *>(&p23);
-            }
-            // the row's 16-byte groups in the 128-byte-swizzled K-major layout
-            uint8_t *arow = st + rr * 128;
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                const int gg = half * 4 + g;
-                *reinterpret_cast<uint4 *>(arow + ((gg ^ (rr & 7)) << 4)) =
-                    make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
-            }
-        }
-        fence_async_smem();   // the tensor cores read the block
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&a_bar[s]);
-        if (tid == 0) {
+        int issued = npre;   // chunks whose stage copies have been requested
+        int c = 0;
+        for (; c < nc; ++c) {
+            const int s = c % kFlyStages;
+            const uint32_t ph = (uint32_t)(c / kFlyStages) & 1u;
             if (!mbar_wait(&a_bar[s], ph, a.status)) *abort_v = 1;
             if (!*abort_v) {
                 fence_after_sync();
-                const uint32_t sa = smem_u32(st);
+                const uint32_t sa = smem_u32(ring + s * kFlyStageBytes);
                 const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + kStageA);
 #pragma unroll
                 for (int kk = 0; kk < kTK / 16; ++kk)
@@ -568,10 +584,8 @@ dense_fly_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_consta
                     *abort_v = 1;
                 }
             }
+            if (*abort_v) break;
         }
-        if (*abort_v) break;
-    }
-    if (tid == 0) {
         mma_commit(&tmem_bar);
         // after an abort: the copies already requested land before the CTA leaves (bounded)
         for (int cc = c; cc < issued; ++cc)
