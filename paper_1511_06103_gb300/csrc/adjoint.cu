@@ -162,11 +162,17 @@ adj_step_kernel(const __grid_constant__ AdjTmaMaps maps, const __grid_constant__
     const size_t base = (size_t)b * N;
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if constexpr (C::TMA) {
+        // thread 0 requests the three boxes of 34 x 6 pixels before anything
+        // else (labels LP..LS-1 of the ga and q rows zero-filled)
         if (tid == 0) {
             tc::mbar_init(&bar, 1);
             tc::mbar_init_fence();
+            tc::mbar_expect_tx(&bar, (uint32_t)(4 * C::HR * (2 * LS + LP)));
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            tma_load_4d(sga, &maps.gs, &bar, 0, x0 - 1, y0 - 1, b);
+            tma_load_4d(sq, &maps.s, &bar, 0, x0 - 1, y0 - 1, b);
+            tma_load_4d(sraw, &maps.sn, &bar, 0, x0 - 1, y0 - 1, b);
         }
-        __syncthreads();
     }
     // mu does not depend on the previous step: staged before the wait
     for (int i = tid; i < LP * LP; i += NT) {
@@ -177,17 +183,29 @@ adj_step_kernel(const __grid_constant__ AdjTmaMaps maps, const __grid_constant__
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const float eta = a.eta[b];
+    // the accumulated gradients this tile adds to are read now, so that their
+    // loads are not on the tile's path at the end: the block's dmu partial and
+    // the own pixel's edge weights' gradient
+    constexpr int kDmuPer = (LT * LT + NT - 1) / NT;
+    const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    float dmu_prev[kDmuPer];
+#pragma unroll
+    for (int k = 0; k < kDmuPer; ++k) {
+        const int e = tid + k * NT;
+        dmu_prev[k] = e < L * L ? a.dmu_part[blk * L * L + e] : 0.f;
+    }
+    float dw_prev[ND];
+    {
+        const int px = x0 + tid % TX, py = y0 + tid / TX;
+        const size_t pp = base + (size_t)(px < W && py < H ? py : 0) * W + (px < W && py < H ? px : 0);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) dw_prev[d] = a.dw[pp * ND + d];
+    }
 
     // Phase 1a: raw rows of the tile and its halo, all copies in flight at
     // once (rows outside the image are zero-filled).
     if constexpr (C::TMA) {
-        // three boxes of 34 x 6 pixels (labels LP..LS-1 of the ga and q rows zero-filled)
-        if (tid == 0) {
-            tc::mbar_expect_tx(&bar, (uint32_t)(4 * C::HR * (2 * LS + LP)));
-            tma_load_4d(sga, &maps.gs, &bar, 0, x0 - 1, y0 - 1, b);
-            tma_load_4d(sq, &maps.s, &bar, 0, x0 - 1, y0 - 1, b);
-            tma_load_4d(sraw, &maps.sn, &bar, 0, x0 - 1, y0 - 1, b);
-        }
+        __syncthreads();   // the barrier is initialised before anyone waits on it
         tc::mbar_wait(&bar, 0, a.status);
     } else {
     for (int r = tid; r < C::HR; r += NT) {
@@ -290,7 +308,7 @@ adj_step_kernel(const __grid_constant__ AdjTmaMaps maps, const __grid_constant__
                     de = pfma(v1[j], q2, pfma(v2[j], g2, de));
                 }
             }
-            if (ok) a.dw[p * ND + d] += -eta * (de.x + de.y);
+            if (ok) a.dw[p * ND + d] = dw_prev[d] + -eta * (de.x + de.y);
         }
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
@@ -409,12 +427,14 @@ adj_step_kernel(const __grid_constant__ AdjTmaMaps maps, const __grid_constant__
                 *reinterpret_cast<float2 *>(red + (grp * LP + a0 + u) * LP + c0 + v) = acc[u][v / 2];
     }
     __syncthreads();
-    const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    for (int e = tid; e < L * L; e += NT) {
+#pragma unroll
+    for (int k = 0; k < kDmuPer; ++k) {
+        const int e = tid + k * NT;
+        if (e >= L * L) continue;
         const int ea = e / L, ec = e - ea * L;
         float t = 0.f;
         for (int g = 0; g < NG; ++g) t += red[(g * LP + ea) * LP + ec];
-        a.dmu_part[blk * L * L + e] += -eta * t;
+        a.dmu_part[blk * L * L + e] = dmu_prev[k] + -eta * t;
     }
 }
 
