@@ -29,9 +29,10 @@
 //  - The FP32 form keeps the pixel's own log q in shared memory and loads
 //    the unaries after the L x L product, so that three CTAs fit per SM
 //    (measured 4.5 % faster than two CTAs holding both in registers).
-//  - Free-energy partials are reduced per tile in FP64 and finished by the
-//    last tile of each instance in a fixed order, so F does not depend on
-//    scheduling or on the other instances of the batch.
+//  - Free-energy partials are reduced per tile in FP64 and summed in a fixed
+//    order -- by the next step of a loop (the deferred form below) or by the
+//    last tile of each instance -- so F does not depend on scheduling or on
+//    the other instances of the batch.
 #pragma once
 
 #include <cmath>
@@ -627,7 +628,8 @@ struct GridTcSmem {
     static constexpr int bytes = QT + A + B + 1024;           // + alignment slack
 };
 
-// a5, per instance: thread 0 of every tile publishes its tile's partial bs;
+// a5, per instance: thread 0 of every tile publishes its tile's partial bs.
+// In a loop (a.defer) that is all: the next step sums the slot.  Otherwise
 // the last tile of instance b to arrive sums all partials in a fixed order
 // (the result does not depend on scheduling), stores F, appends it to the
 // trace and applies the stopping rule |F^t - F^{t-1}| <= rel_tol |F^t|
