@@ -195,11 +195,14 @@ adj_step_kernel(const __grid_constant__ AdjTmaMaps maps, const __grid_constant__
         dmu_prev[k] = e < L * L ? a.dmu_part[blk * L * L + e] : 0.f;
     }
     float dw_prev[ND];
+    float du_prev[LP];   // the own pixel's dU, updated as soon as its ga exists
     {
         const int px = x0 + tid % TX, py = y0 + tid / TX;
         const size_t pp = base + (size_t)(px < W && py < H ? py : 0) * W + (px < W && py < H ? px : 0);
 #pragma unroll
         for (int d = 0; d < ND; ++d) dw_prev[d] = a.dw[pp * ND + d];
+#pragma unroll
+        for (int l = 0; l < LP; l += VW) vget<VW>(a.dU + pp * LP + l, du_prev + l);
     }
 
     // Phase 1a: raw rows of the tile and its halo, all copies in flight at
@@ -261,6 +264,17 @@ adj_step_kernel(const __grid_constant__ AdjTmaMaps maps, const __grid_constant__
     const int ri = (ty + 1) * HX + (tx + 1);
     const float *ga_i = sga + ri * LS;
     const float *q_i = sq + ri * LS;
+    if (act) {
+        // dU += -eta ga (the affine step), independent of the products below
+#pragma unroll
+        for (int l = 0; l < LP; l += VW) {
+            float gv[VW];
+            vget<VW>(ga_i + l, gv);
+#pragma unroll
+            for (int u = 0; u < VW; ++u) du_prev[l + u] = fmaf(-eta, gv[u], du_prev[l + u]);
+            vput<VW>(a.dU + p * LP + l, du_prev + l);
+        }
+    }
     float2 h[NP];
     {
         // v1 = mu^T ga_i, v2 = mu^T q_i
@@ -376,18 +390,15 @@ adj_step_kernel(const __grid_constant__ AdjTmaMaps maps, const __grid_constant__
         const float c1 = 1.f - eta;
 #pragma unroll
         for (int l = 0; l < LP; l += VW) {
-            float gv[VW], qv[VW], out[VW], du[VW];
+            float gv[VW], qv[VW], out[VW];
             vget<VW>(ga_i + l, gv);
             vget<VW>(q_i + l, qv);
-            vget<VW>(a.dU + o + l, du);
 #pragma unroll
             for (int u = 0; u < VW; ++u) {
                 const float hv = (u & 1) ? h[(l + u) / 2].y : h[(l + u) / 2].x;
                 out[u] = fmaf(c1, gv[u], -eta * qv[u] * hv);
-                du[u] = fmaf(-eta, gv[u], du[u]);
             }
             vput<VW>(a.gs_out + o + l, out);
-            vput<VW>(a.dU + o + l, du);
         }
     }
     __syncthreads();
