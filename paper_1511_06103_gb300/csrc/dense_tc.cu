@@ -388,8 +388,9 @@ dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_const
 // sqrt(2) f_j (5 rows of 64) and -|f_j|^2 (one row) side by side
 // (dense_fly_features), 1.5 KiB that one bulk copy brings into a stage with
 // the Q^T tile.  Eight builder warps make the 128 x 64 BF16 block of K in
-// the stage -- thread t takes row t mod 128 and part t / 128 of the columns:
-// three packed FMAs and one exponential per weight -- in the 128-byte-swizzled
+// the stage -- thread t takes rows t mod 64 and t mod 64 + 64 and part t / 64
+// of the columns, so each column's features serve two rows: three packed FMAs
+// and one exponential per weight -- in the 128-byte-swizzled
 // K-major layout of the materialised form, and one more warp issues the same
 // tcgen05.mma chain and the copies of the stages ahead.  No K bytes cross
 // HBM; the step is bound by the builders' instruction stream (loads of the
@@ -397,8 +398,8 @@ dense_step_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_const
 // barriers), not by the special-function unit alone.  Split-K, combine, row
 // epilogue and free energy are those of the materialised form (dense_tc_tail).
 constexpr int kFlyBuilders = 256;                // eight warps build the blocks of K (sixteen measured slower)
-constexpr int kFlyParts = kFlyBuilders / kTM;     // column parts of a chunk, one per builder of a row
-constexpr int kFlyCols = kTK / kFlyParts;         // columns per builder and chunk
+constexpr int kFlyParts = kFlyBuilders / (kTM / 2);   // column parts of a chunk; a builder takes two rows
+constexpr int kFlyCols = kTK / kFlyParts;              // columns per builder and chunk
 constexpr int kFlyThreads = kFlyBuilders + 32;   // and one more issues the MMAs and copies
 constexpr int kFlyStages = 8;   // the copies of a stage take about two chunks' work to land
 constexpr int kStageF = 6 * kTK * 4;                                       // 1.5 KiB
@@ -421,8 +422,9 @@ dense_fly_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_consta
     const int row0 = tile * kTM;
     const int c_begin = (a.nchunk * split) / nsplit, c_end = (a.nchunk * (split + 1)) / nsplit;
     const int nc = c_end - c_begin;
-    const int rr = tid & (kTM - 1), half = tid >> 7;   // builders: row of the tile, part of a chunk's columns
-    const int i = tid < kFlyBuilders ? row0 + rr : N;
+    // builders: rows rr and rr + 64 of the tile, part `half` of a chunk's columns
+    const int rr = tid & (kTM / 2 - 1), half = tid / (kTM / 2);
+    const int i = tid < kFlyBuilders ? row0 + rr : N, i2 = tid < kFlyBuilders ? i + kTM / 2 : N;
 
     // aligned by pointer arithmetic on the shared base, so that accesses
     // through it stay shared-memory instructions
@@ -445,13 +447,19 @@ dense_fly_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_consta
     fence_after_sync();
     const uint32_t tmem = tmem_slot;
     auto fblock = [&](int c) { return a.featsT + ((size_t)b * a.nchunk + (c_begin + c)) * (kStageF / 4); };
-    // this thread's row: sqrt(2) f_i and -|f_i|^2 (rows past N get zeros; their results are not used)
-    float fi[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, ni = 0.f;
+    // this thread's rows: sqrt(2) f_i and -|f_i|^2 (rows past N get zeros; their results are not used)
+    float fi[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, ni = 0.f, fi2[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, ni2 = 0.f;
     if (i < N) {
         const float *fr = a.featsT + ((size_t)b * a.nchunk + i / kTK) * (kStageF / 4) + (i % kTK);
 #pragma unroll
         for (int k = 0; k < 5; ++k) fi[k] = __ldg(fr + k * kTK);
         ni = __ldg(fr + 5 * kTK);
+    }
+    if (i2 < N) {
+        const float *fr = a.featsT + ((size_t)b * a.nchunk + i2 / kTK) * (kStageF / 4) + (i2 % kTK);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) fi2[k] = __ldg(fr + k * kTK);
+        ni2 = __ldg(fr + 5 * kTK);
     }
     // the features do not change between steps: the first stages' blocks are
     // requested before waiting for the previous step (which writes Q^T)
@@ -504,42 +512,60 @@ dense_fly_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_consta
             uint8_t *st = ring + s * kFlyStageBytes;
             if (!mbar_wait(&ld_bar[s], ph, a.status)) *abort_v = 1;
             if (!*abort_v) {
-                // K[i][j] for this thread's row and kFlyCols columns of the chunk
+                // K[i][j] for this thread's two rows and kFlyCols columns of the chunk
                 const float *F = reinterpret_cast<const float *>(st + kStageA + kStageB);
-                const int dj = i - (c_begin + c) * kTK;                // the diagonal's column in this chunk
-                const bool diag = (unsigned)(dj - half * kFlyCols) < (unsigned)kFlyCols;   // in this thread's columns
-                uint32_t w[kFlyCols / 2];
+                const int dj = i - (c_begin + c) * kTK, dj2 = dj + kTM / 2;   // the diagonal's columns
+                const bool diag = (unsigned)(dj - half * kFlyCols) < (unsigned)kFlyCols;
+                const bool diag2 = (unsigned)(dj2 - half * kFlyCols) < (unsigned)kFlyCols;
+                uint32_t w[kFlyCols / 2], w2[kFlyCols / 2];
 #pragma unroll
                 for (int q4 = 0; q4 < kFlyCols / 4; ++q4) {
                     const int j = half * kFlyCols + q4 * 4;
                     const float4 nj = *reinterpret_cast<const float4 *>(F + 5 * kTK + j);
                     float2 e01 = add2(make_float2(nj.x, nj.y), splat2(ni));
                     float2 e23 = add2(make_float2(nj.z, nj.w), splat2(ni));
+                    float2 g01 = add2(make_float2(nj.x, nj.y), splat2(ni2));
+                    float2 g23 = add2(make_float2(nj.z, nj.w), splat2(ni2));
 #pragma unroll
                     for (int k = 0; k < 5; ++k) {
                         const float4 fj = *reinterpret_cast<const float4 *>(F + k * kTK + j);
-                        const float2 fk = splat2(fi[k]);
-                        e01 = fma2(fk, make_float2(fj.x, fj.y), e01);
-                        e23 = fma2(fk, make_float2(fj.z, fj.w), e23);
+                        const float2 f01 = make_float2(fj.x, fj.y), f23 = make_float2(fj.z, fj.w);
+                        e01 = fma2(splat2(fi[k]), f01, e01);
+                        e23 = fma2(splat2(fi[k]), f23, e23);
+                        g01 = fma2(splat2(fi2[k]), f01, g01);
+                        g23 = fma2(splat2(fi2[k]), f23, g23);
                     }
                     float v0 = ex2_ftz(e01.x), v1 = ex2_ftz(e01.y), v2 = ex2_ftz(e23.x), v3 = ex2_ftz(e23.y);
+                    float u0 = ex2_ftz(g01.x), u1 = ex2_ftz(g01.y), u2 = ex2_ftz(g23.x), u3 = ex2_ftz(g23.y);
                     if (diag) {
                         if (j == dj) v0 = 0.f;
                         if (j + 1 == dj) v1 = 0.f;
                         if (j + 2 == dj) v2 = 0.f;
                         if (j + 3 == dj) v3 = 0.f;
                     }
+                    if (diag2) {
+                        if (j == dj2) u0 = 0.f;
+                        if (j + 1 == dj2) u1 = 0.f;
+                        if (j + 2 == dj2) u2 = 0.f;
+                        if (j + 3 == dj2) u3 = 0.f;
+                    }
                     const __nv_bfloat162 p01 = __floats2bfloat162_rn(v0, v1), p23 = __floats2bfloat162_rn(v2, v3);
+                    const __nv_bfloat162 r01 = __floats2bfloat162_rn(u0, u1), r23 = __floats2bfloat162_rn(u2, u3);
                     w[2 * q4] = *reinterpret_cast<const uint32_t *>(&p01);
                     w[2 * q4 + 1] = *reinterpret_cast<const uint32_t *>(&p23);
+                    w2[2 * q4] = *reinterpret_cast<const uint32_t *>(&r01);
+                    w2[2 * q4 + 1] = *reinterpret_cast<const uint32_t *>(&r23);
                 }
-                // the row's 16-byte groups in the 128-byte-swizzled K-major layout
-                uint8_t *arow = st + rr * 128;
+                // the rows' 16-byte groups in the 128-byte-swizzled K-major layout
+                const int rr2 = rr + kTM / 2;
+                uint8_t *arow = st + rr * 128, *arow2 = st + rr2 * 128;
 #pragma unroll
                 for (int g = 0; g < kFlyCols / 8; ++g) {
                     const int gg = half * (kFlyCols / 8) + g;
                     *reinterpret_cast<uint4 *>(arow + ((gg ^ (rr & 7)) << 4)) =
                         make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
+                    *reinterpret_cast<uint4 *>(arow2 + ((gg ^ (rr2 & 7)) << 4)) =
+                        make_uint4(w2[4 * g], w2[4 * g + 1], w2[4 * g + 2], w2[4 * g + 3]);
                 }
             }
             fence_async_smem();   // the tensor cores read the block
