@@ -1330,13 +1330,29 @@ crf_status mf_unrolled_forward(crf_t h, int32_t K, double eta, float *ckpt) {
     const size_t S = state_floats(h);
     CK(h, launch_init_logq(h->U, ckpt, (long long)n_pix(h), h->L, h->LP, h->st));
     if (h->profile) CK(h, cudaEventRecord(h->ev0, h->st));
+    int pending = 0, flushes = 0;   // deferred free energy, as in mf_iterate
     for (int t = 0; t < K; ++t) {
         GridStepLaunch a = step_args(h, e, t, 1, 0.0);
         a.done = nullptr;
         a.tc = h->bf16;   // BF16 handles: tensor-core messages in the forward steps
         a.s_in = ckpt + (size_t)t * S;
         a.s_out = ckpt + (size_t)(t + 1) * S;
+        const int d = grid_step_fparts(a);
+        if (pending && !d) {
+            CK(h, launch_grid_f_flush(a, t - 1, pending, h->st));
+            ++flushes;
+            pending = 0;
+        }
+        a.defer = d;
+        a.prev_pending = pending;
+        pending = d;
         CK(h, launch_grid_step(a, h->st));
+    }
+    if (pending) {
+        GridStepLaunch a = step_args(h, e, K - 1, 1, 0.0);
+        a.done = nullptr;
+        CK(h, launch_grid_f_flush(a, K - 1, pending, h->st));
+        ++flushes;
     }
     if (h->profile) {
         CK(h, cudaEventRecord(h->ev1, h->st));
@@ -1344,7 +1360,7 @@ crf_status mf_unrolled_forward(crf_t h, int32_t K, double eta, float *ckpt) {
         h->prof_valid = true;
     }
     CK(h, cudaMemcpyAsync(h->s[h->cur], ckpt + (size_t)K * S, S * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
-    h->launches += 1 + K;
+    h->launches += 1 + K + flushes;
     h->last_iters = K;
     h->fcur_valid = false;
     return CRF_OK;
